@@ -1,0 +1,86 @@
+"""Per-frame preprocessing (oracle, FP64).
+
+Sec. 4.1.1 caches, per frame, the low-resolution depth, the camera-space positions
+P^low and normals N^low; Sec. 4.3 evaluates the photometric term on the gradient of
+the luminance, I_i.  The paper gives no formulas for either, so this follows the
+readings below (pixel centres at integer coordinates, pinhole intrinsics fx, fy,
+cx, cy):
+
+* depth D is valid iff finite and depth_min < D < depth_max; invalid depth -> 0;
+* back-projection pi^-1(x, y, z) = ((x - cx) z / fx, (y - cy) z / fy, z);
+* normal n = normalize((P(x,y+1) - P(x,y-1)) x (P(x+1,y) - P(x-1,y))), which faces the
+  camera on every front-facing surface; invalid on the 1-pixel border, if the pixel or
+  any of its 4 neighbours has invalid depth, or if the cross product's norm < 1e-12;
+* I = ||grad L||_2 with central differences (f(x+1) - f(x-1)) / 2, defined on the
+  1-pixel interior (0 elsewhere);
+* grad I by central differences of I, defined on the 2-pixel interior (0 elsewhere).
+"""
+import numpy as np
+
+
+def valid_depth(D, depth_min, depth_max):
+    D = np.asarray(D, dtype=np.float64)
+    return np.isfinite(D) & (D > depth_min) & (D < depth_max)
+
+
+def backproject(D, fx, fy, cx, cy):
+    """Camera-space points P(x,y) = pi^-1(x, y, D(x,y)), shape (H,W,3), FP64."""
+    H, W = D.shape
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    z = np.asarray(D, dtype=np.float64)
+    return np.stack([(xs - cx) * z / fx, (ys - cy) * z / fy, z], axis=-1)
+
+
+def normals(D, valid, fx, fy, cx, cy):
+    """Per-pixel unit normals (H,W,3) and their validity mask (H,W)."""
+    H, W = D.shape
+    P = backproject(np.where(valid, D, 0.0), fx, fy, cx, cy)
+    n = np.zeros((H, W, 3))
+    ok = np.zeros((H, W), dtype=bool)
+    c = (slice(1, H - 1), slice(1, W - 1))
+    dy = P[2:, 1:-1] - P[:-2, 1:-1]
+    dx = P[1:-1, 2:] - P[1:-1, :-2]
+    cr = np.cross(dy, dx)
+    nrm = np.sqrt(np.sum(cr * cr, axis=-1))
+    nb = valid[c] & valid[2:, 1:-1] & valid[:-2, 1:-1] & valid[1:-1, 2:] & valid[1:-1, :-2]
+    good = nb & (nrm >= 1e-12)
+    inner = np.zeros_like(cr)
+    inner[good] = cr[good] / nrm[good][:, None]
+    n[c] = inner
+    ok[c] = good
+    return n, ok
+
+
+def intensity_gradient(L):
+    """I = ||grad L||_2 on the 1-pixel interior and grad I = (I_x, I_y) on the 2-pixel interior."""
+    L = np.asarray(L, dtype=np.float64)
+    H, W = L.shape
+    I = np.zeros((H, W))
+    gx = 0.5 * (L[1:-1, 2:] - L[1:-1, :-2])
+    gy = 0.5 * (L[2:, 1:-1] - L[:-2, 1:-1])
+    I[1:-1, 1:-1] = np.sqrt(gx * gx + gy * gy)
+    Ix = np.zeros((H, W))
+    Iy = np.zeros((H, W))
+    Ix[2:-2, 2:-2] = 0.5 * (I[2:-2, 3:-1] - I[2:-2, 1:-3])
+    Iy[2:-2, 2:-2] = 0.5 * (I[3:-1, 2:-2] - I[1:-3, 2:-2])
+    return I, Ix, Iy
+
+
+class Frame:
+    """A preprocessed frame: depth, validity, normals, I and grad I (all FP64)."""
+
+    def __init__(self, depth, lum, intr, depth_min=0.1, depth_max=10.0):
+        self.W, self.H = intr["W"], intr["H"]
+        self.fx, self.fy, self.cx, self.cy = intr["fx"], intr["fy"], intr["cx"], intr["cy"]
+        D = np.asarray(depth, dtype=np.float64)
+        self.valid = valid_depth(D, depth_min, depth_max)
+        self.D = np.where(self.valid, D, 0.0)
+        self.N, self.nvalid = normals(self.D, self.valid, self.fx, self.fy, self.cx, self.cy)
+        self.I, self.Ix, self.Iy = intensity_gradient(lum)
+        # FP32 copies for the association decisions (see association.py)
+        self.D32 = self.D.astype(np.float32)
+        self.N32 = self.N.astype(np.float32)
+
+
+def preprocess(problem_depth, problem_lum, intr, depth_min=0.1, depth_max=10.0):
+    return [Frame(d, l, intr, depth_min, depth_max) for d, l in zip(problem_depth, problem_lum)]

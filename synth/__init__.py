@@ -1,0 +1,7 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+Holds scene rendering, trajectories and correspondence sampling only; none of the
+pose solver's arithmetic lives here.
+"""
+from .configs import Problem, cfg1, cfg2, cfg3, chunk_problem, global_problem, chunk_batch, seed_for  # noqa: F401
+from . import scene  # noqa: F401

@@ -1,0 +1,504 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test ties one part of the oracle to something other than itself: closed
+forms, library routines, finite differences, invariants, brute force, or values
+printed in the paper (tests/golden/paper_constants.json).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.optimize
+from scipy.spatial.transform import Rotation
+
+import synth
+from synth import scene as sc
+from oracle import association, frames, lie, residuals, solver, system
+from oracle.system import SolveParams, SparsePair
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
+
+
+# ------------------------------------------------------------------ helpers
+
+def rand_pose(rng, rot_scale=0.3, trans_scale=0.5):
+    R = Rotation.from_rotvec(rng.normal(0, rot_scale, 3)).as_matrix()
+    return lie.to44(R, rng.normal(0, trans_scale, 3))
+
+
+def consistent_corr(rng, Ti, Tj, n, sigma=0.0):
+    """Points p in camera i and q = T_j^-1 T_i p (+ noise) in camera j, FP64."""
+    p = rng.uniform([-1, -1, 1], [1, 1, 3], size=(n, 3))
+    Tji = np.linalg.inv(Tj) @ Ti
+    q = p @ Tji[:3, :3].T + Tji[:3, 3] + rng.normal(0, sigma, size=(n, 3)) if sigma else p @ Tji[:3, :3].T + Tji[:3, 3]
+    return p, q
+
+
+def render_pair(rng, intr, scene, poses, noise=0.0):
+    depth_gt, lum = sc.render(scene, poses, intr)
+    depth = np.where((depth_gt > 0.5) & (depth_gt < 4.0), depth_gt + (rng.normal(0, noise, depth_gt.shape) if noise else 0), 0)
+    return depth.astype(np.float32), lum
+
+
+@pytest.fixture(scope="module")
+def room_frames():
+    """Three noise-free 80x60 renderings of a box room from nearby poses (GT known)."""
+    rng = np.random.default_rng(7)
+    intr = sc.intrinsics(80, 60)
+    start = lie.to44(sc.yaw_pitch_roll(0.3, 0.05, 0.0), np.array([0.0, 0.0, -0.5]))
+    room = sc.box_room(rng, (6.0, 2.8, 6.0), (20, 30), keep_clear=start[None, :3, 3], clear_radius=1.0)
+    poses = sc.smooth_walk(rng, 3, start, scene=room)
+    depth, lum = render_pair(rng, intr, room, poses)
+    fr = [frames.Frame(depth[k], lum[k], intr) for k in range(3)]
+    return intr, poses, fr, depth, lum
+
+
+# ------------------------------------------------------------- golden values
+
+def test_golden_constants_match_defaults():
+    g = json.load(open(GOLDEN))
+    p = SolveParams()
+    assert p.tau_dist == g["tau_d_m"]["value"]
+    assert p.tau_normal == g["tau_n"]["value"]
+    assert p.max_angle_deg == g["max_angle_deg"]["value"]
+    assert synth.cfg1().n_frames == g["n_chunk"]["value"]
+
+
+def test_fig11_variable_count():
+    """Sec. 7 (Fig. 11): 101 keyframes give 600 variables, i.e. 6 per frame with the first fixed."""
+    g = json.load(open(GOLDEN))
+    n = g["fig11_keyframes"]["value"]
+    S = system.System(n)
+    assert S.A.shape == (g["fig11_variables"]["value"],) * 2
+    assert 6 * (n - 1) == g["fig11_variables"]["value"]
+
+
+# ------------------------------------------------------------------ lie.py
+
+@pytest.mark.parametrize("scale", [1e-12, 1e-9, 1e-4, 0.3, 2.5])
+def test_exp_matches_matrix_exponential(scale):
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        w = rng.normal(size=3) * scale
+        E = scipy.linalg.expm(np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]]))
+        np.testing.assert_allclose(lie.exp_so3(w), E, atol=1e-14, rtol=0)
+
+
+def test_exp_is_rotation_and_skew_is_cross():
+    rng = np.random.default_rng(2)
+    w, u = rng.normal(size=3), rng.normal(size=3)
+    R = lie.exp_so3(w)
+    np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-14)
+    assert abs(np.linalg.det(R) - 1) < 1e-14
+    np.testing.assert_allclose(lie.skew(w) @ u, np.cross(w, u), atol=1e-15)
+
+
+# --------------------------------------------------------------- frames.py
+
+def test_normals_of_a_plane_are_exact():
+    """A noise-free plane: central-difference normals equal the plane normal, facing the camera."""
+    intr = sc.intrinsics(80, 60)
+    n_true = np.array([0.3, -0.2, -1.0])
+    n_true /= np.linalg.norm(n_true)
+    # plane n.X = -2.5 (camera at the origin on the side the normal points to)
+    ys, xs = np.mgrid[0:60, 0:80].astype(np.float64)
+    ray = np.stack([(xs - intr["cx"]) / intr["fx"], (ys - intr["cy"]) / intr["fy"], np.ones_like(xs)], -1)
+    z = -2.5 / (ray @ n_true)
+    f = frames.Frame(z, np.zeros((60, 80)), intr)
+    assert f.nvalid[1:-1, 1:-1].all() and not f.nvalid[0].any() and not f.nvalid[:, -1].any()
+    np.testing.assert_allclose(f.N[1:-1, 1:-1], np.broadcast_to(n_true, (58, 78, 3)), atol=1e-12)
+
+
+def test_normal_invalid_next_to_invalid_depth():
+    intr = sc.intrinsics(80, 60)
+    D = np.full((60, 80), 2.0)
+    D[30, 40] = 0.0
+    f = frames.Frame(D, np.zeros((60, 80)), intr)
+    for (y, x) in [(30, 40), (29, 40), (31, 40), (30, 39), (30, 41)]:
+        assert not f.nvalid[y, x]
+    assert f.nvalid[29, 39] and f.nvalid[32, 40]
+
+
+def test_intensity_gradient_closed_forms():
+    """L = c (x + y)^2: central differences are exact, |grad L| = 2 sqrt(2) c (x + y), grad I = 2 sqrt(2) c (1, 1)."""
+    ys, xs = np.mgrid[0:60, 0:80].astype(np.float64)
+    c = 1e-4
+    I, Ix, Iy = frames.intensity_gradient(c * (xs + ys) ** 2)
+    k = 2 * math.sqrt(2) * c
+    np.testing.assert_allclose(I[1:-1, 1:-1], k * (xs + ys)[1:-1, 1:-1], rtol=1e-12)
+    assert not I[0].any() and not I[:, 0].any()
+    np.testing.assert_allclose(Ix[2:-2, 2:-2], k, rtol=1e-10)
+    np.testing.assert_allclose(Iy[2:-2, 2:-2], k, rtol=1e-10)
+    assert not Ix[1].any() and not Iy[:, 1].any()
+    # a linear ramp has constant gradient magnitude and zero grad I
+    I2, Ix2, Iy2 = frames.intensity_gradient(0.01 * xs - 0.02 * ys)
+    np.testing.assert_allclose(I2[1:-1, 1:-1], math.hypot(0.01, 0.02), rtol=1e-12)
+    assert np.abs(Ix2).max() < 1e-15 and np.abs(Iy2).max() < 1e-15
+
+
+def test_depth_validity_range():
+    D = np.array([[0.05, 0.1, 0.5, 9.99, 10.0, np.nan, np.inf]])
+    np.testing.assert_array_equal(frames.valid_depth(D, 0.1, 10.0)[0], [False, False, True, True, False, False, False])
+
+
+# ----------------------------------------------------------- sparse residuals
+
+def test_sparse_zero_at_ground_truth():
+    rng = np.random.default_rng(3)
+    Ti, Tj = rand_pose(rng), rand_pose(rng)
+    p, q = consistent_corr(rng, Ti, Tj, 50)
+    r = residuals.sparse_residuals(Ti[:3, :3], Ti[:3, 3], Tj[:3, :3], Tj[:3, 3], p, q)
+    assert np.abs(r).max() < 1e-14
+    poses = np.stack([np.eye(4), np.linalg.inv(Ti) @ Tj])  # frame 0 = camera i as world
+    S = system.assemble([None, None], None, poses, [SparsePair(0, 1, p, q)], [], SolveParams(dense_on=False), 0.0)
+    assert S.e_sparse < 1e-26 and np.abs(S.b).max() < 1e-12
+
+
+def fd_check(fun, poses, idx, J_analytic, h=1e-6):
+    """Central differences of fun(poses) w.r.t. the 6 tangent coordinates of frame idx."""
+    J = np.zeros((len(fun(poses)), 6))
+    for c in range(6):
+        e = np.zeros(6)
+        e[c] = h
+        Pp, Pm = poses.copy(), poses.copy()
+        R, t = lie.apply_update(poses[idx][:3, :3], poses[idx][:3, 3], e)
+        Pp[idx] = lie.to44(R, t)
+        R, t = lie.apply_update(poses[idx][:3, :3], poses[idx][:3, 3], -e)
+        Pm[idx] = lie.to44(R, t)
+        J[:, c] = (fun(Pp) - fun(Pm)) / (2 * h)
+    scale = np.abs(J_analytic).max()
+    np.testing.assert_allclose(J, J_analytic, atol=2e-7 * scale, rtol=0)
+
+
+def test_sparse_jacobian_finite_differences():
+    rng = np.random.default_rng(4)
+    poses = np.stack([rand_pose(rng), rand_pose(rng)])
+    p = rng.normal(size=(20, 3))
+    q = rng.normal(size=(20, 3))
+
+    def f(P):
+        return residuals.sparse_residuals(P[0][:3, :3], P[0][:3, 3], P[1][:3, :3], P[1][:3, 3], p, q).ravel()
+
+    Ji, Jj = residuals.sparse_jacobians(poses[0][:3, :3], poses[0][:3, 3], poses[1][:3, :3], poses[1][:3, 3], p, q)
+    fd_check(f, poses, 0, Ji.reshape(-1, 6))
+    fd_check(f, poses, 1, Jj.reshape(-1, 6))
+
+
+# ------------------------------------------------------------ dense residuals
+
+def perturbed(poses, rng, rot=0.01, trans=0.01):
+    out = poses.copy()
+    for k in range(len(out)):
+        R, t = lie.apply_update(out[k][:3, :3], out[k][:3, 3], np.r_[rng.normal(0, rot, 3), rng.normal(0, trans, 3)])
+        out[k] = lie.to44(R, t)
+    return out
+
+
+def test_dense_geo_jacobian_finite_differences(room_frames):
+    intr, poses, fr, _, _ = room_frames
+    rng = np.random.default_rng(5)
+    P0 = perturbed(poses, rng)
+    M = association.pair_transform32(P0[0][:3, :3], P0[0][:3, 3], P0[1][:3, :3], P0[1][:3, 3])
+    asc = association.associate(fr[0], fr[1], M, intr)
+    assert asc["valid"].sum() > 500
+    d = residuals.dense_terms(fr[0], fr[1], P0[0][:3, :3], P0[0][:3, 3], P0[1][:3, :3], P0[1][:3, 3], asc)
+
+    def f(P):
+        return residuals.dense_residuals_only(fr[0], fr[1], P[0][:3, :3], P[0][:3, 3], P[1][:3, :3], P[1][:3, 3], asc)[0]
+
+    fd_check(f, P0, 0, d["J_geo_i"])
+    fd_check(f, P0, 1, d["J_geo_j"])
+
+
+def test_dense_photo_jacobian_finite_differences(room_frames):
+    """With L = c (x+y)^2 the intensity I is linear, so bilinear sampling and grad I are exact and
+    finite differences of r_p must equal -grad I^T Jpi dy/dtheta."""
+    intr, poses, fr, depth, _ = room_frames
+    ys, xs = np.mgrid[0:60, 0:80].astype(np.float64)
+    L = 1e-4 * (xs + ys) ** 2
+    f0 = frames.Frame(depth[0], L, intr)
+    f1 = frames.Frame(depth[1], L, intr)
+    rng = np.random.default_rng(6)
+    P0 = perturbed(poses, rng)
+    M = association.pair_transform32(P0[0][:3, :3], P0[0][:3, 3], P0[1][:3, :3], P0[1][:3, 3])
+    asc = association.associate(f0, f1, M, intr)
+    d = residuals.dense_terms(f0, f1, P0[0][:3, :3], P0[0][:3, 3], P0[1][:3, :3], P0[1][:3, 3], asc)
+
+    def f(P):
+        return residuals.dense_residuals_only(f0, f1, P[0][:3, :3], P[0][:3, 3], P[1][:3, :3], P[1][:3, 3], asc)[1]
+
+    fd_check(f, P0, 0, d["J_photo_i"])
+    fd_check(f, P0, 1, d["J_photo_j"])
+
+
+def test_dense_duplicate_frame_zero_residual(room_frames):
+    """Frame j = frame i at the identical pose: every associated pixel maps onto itself, r_g = r_p = 0."""
+    intr, poses, fr, _, _ = room_frames
+    P = np.stack([poses[1], poses[1]])
+    M = association.pair_transform32(P[0][:3, :3], P[0][:3, 3], P[1][:3, :3], P[1][:3, 3])
+    asc = association.associate(fr[1], fr[1], M, intr)
+    idx = np.flatnonzero(asc["valid"])
+    ys, xs = np.divmod(idx, 80)
+    np.testing.assert_array_equal(asc["nx"][idx], xs)
+    np.testing.assert_array_equal(asc["ny"][idx], ys)
+    d = residuals.dense_terms(fr[1], fr[1], P[0][:3, :3], P[0][:3, 3], P[1][:3, :3], P[1][:3, 3], asc)
+    assert np.abs(d["r_geo"]).max() == 0.0
+    assert np.abs(d["r_photo"]).max() < 1e-12
+    # every pixel with valid depth + normal strictly inside the 3-pixel border is associated
+    inner = fr[1].valid & fr[1].nvalid
+    inner[:3] = inner[-3:] = False
+    inner[:, :3] = inner[:, -3:] = False
+    assert np.all(asc["valid"][inner.ravel()])
+
+
+def test_dense_geo_vanishes_on_noise_free_surfaces_at_gt(room_frames):
+    """Noise-free renderings at GT: point-to-plane residuals vanish except at rare edge pixels;
+    a transposed relative transform or a sign error would break this."""
+    intr, poses, fr, _, _ = room_frames
+    M = association.pair_transform32(poses[0][:3, :3], poses[0][:3, 3], poses[2][:3, :3], poses[2][:3, 3])
+    asc = association.associate(fr[0], fr[2], M, intr)
+    d = residuals.dense_terms(fr[0], fr[2], poses[0][:3, :3], poses[0][:3, 3], poses[2][:3, :3], poses[2][:3, 3], asc)
+    assert len(d["r_geo"]) > 1500
+    assert np.median(np.abs(d["r_geo"])) < 1e-5
+    # shared mask: one photometric and one geometric residual per associated pixel (Sec. 4.4)
+    assert len(d["r_geo"]) == len(d["r_photo"])
+    M_bad = (M[0].T.copy(), M[1])
+    asc_bad = association.associate(fr[0], fr[2], M_bad, intr)
+    if asc_bad["valid"].sum() > 0:
+        d_bad = residuals.dense_terms(fr[0], fr[2], poses[0][:3, :3], poses[0][:3, 3], poses[2][:3, :3],
+                                      poses[2][:3, 3], asc_bad)
+        assert asc_bad["valid"].sum() < 0.9 * asc["valid"].sum() or np.median(np.abs(d_bad["r_geo"])) > 1e-4
+
+
+def test_plane_geo_residual_zero_for_any_pair():
+    """A textured plane rendered noise-free from two poses: r_g = 0 at GT for every associated pixel."""
+    rng = np.random.default_rng(8)
+    intr = sc.intrinsics(80, 60)
+    scene = sc.planar_scene(2, 3.0, rng)
+    poses = np.stack([lie.to44(np.eye(3), np.zeros(3)),
+                      lie.to44(Rotation.from_rotvec([0.02, -0.05, 0.01]).as_matrix(), np.array([0.1, -0.05, 0.2]))])
+    depth, lum = render_pair(rng, intr, scene, poses)
+    fr = [frames.Frame(depth[k], lum[k], intr) for k in range(2)]
+    M = association.pair_transform32(poses[0][:3, :3], poses[0][:3, 3], poses[1][:3, :3], poses[1][:3, 3])
+    asc = association.associate(fr[0], fr[1], M, intr)
+    d = residuals.dense_terms(fr[0], fr[1], poses[0][:3, :3], poses[0][:3, 3], poses[1][:3, :3], poses[1][:3, 3], asc)
+    assert len(d["r_geo"]) > 3000
+    assert np.abs(d["r_geo"]).max() < 2e-6  # float32 depth storage only
+
+
+# -------------------------------------------------------------- the system
+
+def stacked_residuals(fr, intr, poses, sparse_pairs, dense_assoc, params, wd):
+    """Weighted residual vector sqrt(w) r with frozen dense associations (test-side stacking)."""
+    out = []
+    for sp in sparse_pairs:
+        r = residuals.sparse_residuals(poses[sp.a][:3, :3], poses[sp.a][:3, 3], poses[sp.b][:3, :3],
+                                       poses[sp.b][:3, 3], sp.p, sp.q)
+        out.append(math.sqrt(params.w_sparse) * r.ravel())
+    for (i, j), asc in dense_assoc.items():
+        rg, rp = residuals.dense_residuals_only(fr[i], fr[j], poses[i][:3, :3], poses[i][:3, 3],
+                                                poses[j][:3, :3], poses[j][:3, 3], asc)
+        out.append(math.sqrt(wd * params.w_geo) * rg)
+        out.append(math.sqrt(wd * params.w_photo) * rp)
+    return np.concatenate(out)
+
+
+def test_normal_equations_equal_fd_jacobian_products(room_frames):
+    """A = J^T W J and b = -J^T W r with J from finite differences of the whole stacked
+    residual vector (gauge frame excluded): pins block placement, weights and gauge."""
+    intr, poses, fr, _, _ = room_frames
+    rng = np.random.default_rng(9)
+    P0 = perturbed(poses, rng, 0.005, 0.005)
+    sp = []
+    for (a, b) in [(0, 1), (0, 2), (1, 2)]:
+        p, q = consistent_corr(rng, poses[a], poses[b], 30, sigma=0.01)
+        sp.append(SparsePair(a, b, p, q))
+    params = SolveParams(w_sparse=1.3, w_geo=0.8, w_photo=0.0)
+    wd = 0.7
+    dense_pairs = [(0, 1), (1, 2)]
+    S = system.assemble(fr, intr, P0, sp, dense_pairs, params, wd)
+    assoc = {}
+    for (a, b) in dense_pairs:
+        for (i, j) in ((a, b), (b, a)):
+            M = association.pair_transform32(P0[i][:3, :3], P0[i][:3, 3], P0[j][:3, :3], P0[j][:3, 3])
+            assoc[(i, j)] = association.associate(fr[i], fr[j], M, intr)
+    f = lambda P: stacked_residuals(fr, intr, P, sp, assoc, params, wd)  # noqa: E731
+    r0 = f(P0)
+    J = np.zeros((len(r0), 12))
+    h = 1e-6
+    for fidx in (1, 2):
+        for c in range(6):
+            e = np.zeros(6)
+            e[c] = h
+            Pp, Pm = P0.copy(), P0.copy()
+            Pp[fidx] = lie.to44(*lie.apply_update(P0[fidx][:3, :3], P0[fidx][:3, 3], e))
+            Pm[fidx] = lie.to44(*lie.apply_update(P0[fidx][:3, :3], P0[fidx][:3, 3], -e))
+            J[:, 6 * (fidx - 1) + c] = (f(Pp) - f(Pm)) / (2 * h)
+    A_fd = J.T @ J
+    b_fd = -J.T @ r0
+    np.testing.assert_allclose(S.A, A_fd, atol=1e-6 * np.abs(A_fd).max(), rtol=0)
+    np.testing.assert_allclose(S.b, b_fd, atol=1e-6 * np.abs(b_fd).max(), rtol=0)
+    assert abs(S.energy - r0 @ r0) < 1e-10 * (r0 @ r0)
+    # residual count identity (Sec. 4.4): 3 per correspondence, 2 per associated pixel
+    n_px = sum(a["valid"].sum() for a in assoc.values())
+    assert S.n_sparse == 3 * sum(s.p.shape[0] for s in sp)
+    assert len(r0) == S.n_sparse + 2 * n_px
+
+
+def test_gauge_invariance_of_energy(room_frames):
+    intr, poses, fr, _, _ = room_frames
+    rng = np.random.default_rng(10)
+    P0 = perturbed(poses, rng)
+    sp = [SparsePair(0, 1, *consistent_corr(rng, poses[0], poses[1], 40, 0.01))]
+    params = SolveParams()
+    S = system.assemble(fr, intr, P0, sp, [(0, 1), (1, 2), (0, 2)], params, 0.5)
+    G = rand_pose(rng, 0.5, 1.0)
+    S2 = system.assemble(fr, intr, np.einsum("ab,kbc->kac", G, P0), sp, [(0, 1), (1, 2), (0, 2)], params, 0.5)
+    assert S.n_dense == S2.n_dense
+    assert abs(S.energy - S2.energy) < 1e-10 * S.energy
+
+
+def sparse_problem(rng, n, n_corr=40, sigma=0.01, spread=0.3):
+    gt = np.stack([np.eye(4)] + [rand_pose(rng, spread, spread) for _ in range(n - 1)])
+    sp = []
+    for a in range(n):
+        for b in range(a + 1, n):
+            p, q = consistent_corr(rng, gt[a], gt[b], n_corr, sigma)
+            sp.append(SparsePair(a, b, p, q))
+    return gt, sp
+
+
+def test_gn_iterates_are_gauge_covariant():
+    """Solving from G X0 gives G X_k for every Gauss-Newton iterate (block-Jacobi PCG)."""
+    rng = np.random.default_rng(11)
+    gt, sp = sparse_problem(rng, 4)
+    X0 = perturbed(gt, rng, 0.05, 0.05)
+    params = SolveParams(n_gn=3, n_pcg=5, dense_on=False)
+    r1 = solver.gauss_newton([None] * 4, None, X0, sp, params)
+    G = rand_pose(rng, 0.7, 2.0)
+    r2 = solver.gauss_newton([None] * 4, None, np.einsum("ab,kbc->kac", G, X0), sp, params)
+    for Pa, Pb in zip(r1.pose_history, r2.pose_history):
+        np.testing.assert_allclose(np.einsum("ab,kbc->kac", G, Pa), Pb, atol=1e-10)
+    np.testing.assert_allclose(r1.energy, r2.energy, rtol=1e-10)
+
+
+def kabsch(P, Q):
+    """Textbook Kabsch/Umeyama: R, t minimising sum ||P - (R Q + t)||^2."""
+    mp, mq = P.mean(0), Q.mean(0)
+    H = (Q - mq).T @ (P - mp)
+    U, _, Vt = np.linalg.svd(H)
+    D = np.diag([1, 1, np.sign(np.linalg.det(Vt.T @ U.T))])
+    R = Vt.T @ D @ U.T
+    return R, mp - R @ mq
+
+
+def test_two_frame_sparse_converges_to_kabsch():
+    """Sec. 4.1.1 cites Kabsch: with frame 0 fixed, the sparse-only optimum is the Kabsch fit."""
+    rng = np.random.default_rng(12)
+    gt, sp = sparse_problem(rng, 2, n_corr=100, sigma=0.02, spread=0.4)
+    sp[0].q[:5] += rng.normal(0, 0.5, (5, 3))  # outliers: still the L2 optimum
+    params = SolveParams(n_gn=12, n_pcg=6, dense_on=False)
+    res = solver.gauss_newton([None] * 2, None, np.stack([np.eye(4)] * 2), sp, params)
+    R, t = kabsch(sp[0].p, sp[0].q)
+    np.testing.assert_allclose(res.poses[1][:3, :3], R, atol=1e-10)
+    np.testing.assert_allclose(res.poses[1][:3, 3], t, atol=1e-10)
+
+
+def test_noise_free_recovers_ground_truth():
+    rng = np.random.default_rng(13)
+    for n in (2, 3):
+        gt, sp = sparse_problem(rng, n, sigma=0.0, spread=0.25)
+        res = solver.gauss_newton([None] * n, None, np.stack([np.eye(4)] * n), sp,
+                                  SolveParams(n_gn=10, n_pcg=6 * (n - 1), dense_on=False))
+        for k in range(n):
+            rot, tr = lie.pose_error(res.poses[k], gt[k])
+            assert rot < 1e-9 and tr < 1e-9
+
+
+def test_three_frame_noisy_matches_independent_least_squares():
+    """Brute force: scipy least_squares with a rotation-vector parameterisation and numeric
+    Jacobian reaches the same minimum as the oracle's Gauss-Newton."""
+    rng = np.random.default_rng(14)
+    gt, sp = sparse_problem(rng, 3, sigma=0.02, spread=0.2)
+
+    def fun(x):
+        T = [np.eye(4)]
+        for k in range(2):
+            T.append(lie.to44(Rotation.from_rotvec(x[6 * k:6 * k + 3]).as_matrix(), x[6 * k + 3:6 * k + 6]))
+        out = []
+        for s in sp:
+            out.append(((s.p @ T[s.a][:3, :3].T + T[s.a][:3, 3]) - (s.q @ T[s.b][:3, :3].T + T[s.b][:3, 3])).ravel())
+        return np.concatenate(out)
+
+    best = None
+    for trial in range(3):
+        x0 = rng.normal(0, 0.1, 12)
+        r = scipy.optimize.least_squares(fun, x0, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15)
+        if best is None or r.cost < best.cost:
+            best = r
+    res = solver.gauss_newton([None] * 3, None, np.stack([np.eye(4)] * 3), sp,
+                              SolveParams(n_gn=15, n_pcg=12, dense_on=False))
+    assert abs(res.energy[-1] - 2 * best.cost) < 1e-9 * res.energy[-1]
+    for k in range(2):
+        Rk = Rotation.from_rotvec(best.x[6 * k:6 * k + 3]).as_matrix()
+        np.testing.assert_allclose(res.poses[k + 1][:3, :3], Rk, atol=1e-7)
+        np.testing.assert_allclose(res.poses[k + 1][:3, 3], best.x[6 * k + 3:6 * k + 6], atol=1e-7)
+
+
+# --------------------------------------------------------------------- PCG
+
+@pytest.mark.parametrize("kind", ["block", "jacobi"])
+def test_pcg_equals_direct_solve_after_n_iterations(kind):
+    rng = np.random.default_rng(15)
+    gt, sp = sparse_problem(rng, 5, sigma=0.01)
+    S = system.assemble([None] * 5, None, perturbed(gt, rng), sp, [], SolveParams(dense_on=False), 0.0)
+    Minv, flags = solver.block_jacobi_inverse(S.A, kind)
+    assert all(f == "ok" for f in flags)
+    x, it = solver.pcg(S.A, S.b, Minv, 6 * 4 * 3)
+    xd = np.linalg.solve(S.A, S.b)
+    np.testing.assert_allclose(x, xd, rtol=0, atol=1e-8 * np.abs(xd).max())
+
+
+def test_block_jacobi_is_exact_inverse_of_diagonal_blocks():
+    rng = np.random.default_rng(16)
+    B = rng.normal(size=(12, 12))
+    A = B @ B.T + 12 * np.eye(12)
+    Minv, _ = solver.block_jacobi_inverse(A)
+    for k in range(2):
+        s = slice(6 * k, 6 * k + 6)
+        np.testing.assert_allclose(Minv[s, s] @ A[s, s], np.eye(6), atol=1e-12)
+    assert not Minv[:6, 6:].any()
+
+
+def test_empty_block_stays_zero():
+    """A frame with no constraints (Sec. 4.4.1: implicitly removed) gets a zero update."""
+    rng = np.random.default_rng(17)
+    gt, sp = sparse_problem(rng, 3, sigma=0.01)
+    sp = [s for s in sp if 2 not in (s.a, s.b)]
+    S = system.assemble([None] * 3, None, perturbed(gt, rng), sp, [], SolveParams(dense_on=False), 0.0)
+    Minv, flags = solver.block_jacobi_inverse(S.A)
+    assert flags == ["ok", "empty"]
+    x, _ = solver.pcg(S.A, S.b, Minv, 10)
+    assert not x[6:].any()
+
+
+def test_dense_pair_angle_gate():
+    """Sec. 4.3: dense pairs need camera angles within 60 degrees."""
+    R59 = Rotation.from_rotvec([0, np.deg2rad(59.0), 0]).as_matrix()
+    R61 = Rotation.from_rotvec([0, np.deg2rad(61.0), 0]).as_matrix()
+    P = np.stack([np.eye(4), lie.to44(R59, np.zeros(3)), lie.to44(R61, np.zeros(3))])
+    sp = [SparsePair(0, 1, np.zeros((3, 3)), np.zeros((3, 3))), SparsePair(0, 2, np.zeros((3, 3)), np.zeros((3, 3)))]
+    assert system.dense_pair_set(P, sp, 60.0) == [(0, 1)]
+
+
+def test_r_max_finds_the_worst_pair():
+    rng = np.random.default_rng(18)
+    gt, sp = sparse_problem(rng, 3, sigma=0.0)
+    sp[2].q[7] += np.array([0.0, 0.3, 0.4])
+    val, pair = solver.r_max(gt, sp)
+    assert pair == (sp[2].a, sp[2].b)
+    # the moved point is now 0.5 m away in camera b coordinates -> 0.5 m in world
+    assert abs(val - 0.5) < 1e-12
