@@ -1,0 +1,225 @@
+/*
+ * bf.h -- C ABI of the B300 global pose alignment library.
+ *
+ * The library implements the global pose alignment of BundleFusion (Dai et al.,
+ * "BundleFusion: Real-time Globally Consistent 3D Reconstruction using
+ * On-the-fly Surface Re-integration", Sec. 4.2-4.4): a Gauss-Newton solve whose
+ * normal equations J^T J dX = -J^T F are solved by a preconditioned conjugate
+ * gradient, over 6-DoF camera poses, minimising
+ *     E_align = w_sparse E_sparse + w_dense (w_photo E_photo + w_geo E_geo)
+ * in the paper's two-level form: chunk ("local") solves, then a global solve over
+ * chunk keyframes.
+ *
+ * Conventions (Sec. 4):
+ *   - A pose T_i maps camera i coordinates to world coordinates, p_w = R_i p + t_i.
+ *     Poses cross the ABI as 16 doubles, a row-major 4x4 matrix [R t; 0 0 0 1].
+ *   - Pixel (x, y) has its centre at integer coordinates; back-projection is
+ *     ((x - cx) z / fx, (y - cy) z / fy, z) with z the depth in metres.
+ *   - Images are row-major H x W float32 arrays, one per frame, frames contiguous.
+ *   - The first frame of every solve is the gauge frame and stays fixed (Sec. 4.3).
+ *
+ * Errors: every call returns a bf_status and never throws or aborts.  On failure
+ * bf_last_error() returns a message describing the most recent error of that
+ * context.  A context is not thread-safe: use one context per host thread or
+ * serialise the calls.  All device work of a context runs on its stream; calls
+ * that return results to host memory synchronise that stream before returning.
+ *
+ * Ownership: input buffers are read during the call and may be reused by the
+ * caller afterwards (host inputs are copied, device inputs are consumed on the
+ * context's stream before the call returns).  Output buffers are owned by the
+ * caller.  The library owns all device memory it allocates for a context and
+ * frees it in bf_destroy().
+ */
+#ifndef BF_H
+#define BF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_ctx bf_ctx;
+
+typedef enum {
+  BF_OK = 0,
+  BF_ERR_INVALID_ARG = 1,   /* bad pointer, size, id or parameter                         */
+  BF_ERR_OUT_OF_MEMORY = 2, /* the context's HBM budget or the device is exhausted         */
+  BF_ERR_CUDA = 3,          /* a CUDA runtime call failed; see bf_last_error()             */
+  BF_ERR_NOT_FOUND = 4,     /* an unknown frame id / ticket                                */
+  BF_ERR_SINGULAR = 5,      /* reserved: a 6x6 block was not SPD (reported as a stats flag) */
+  BF_ERR_TIMEOUT = 6,       /* a bounded wait (host or device) expired                     */
+  BF_ERR_BUSY = 7           /* the request queue is full                                   */
+} bf_status;
+
+enum { BF_PTR_HOST = 0, BF_PTR_DEVICE = 1 };
+
+/* Frame storage type of the preprocessed planes (depth, normal, I, grad I). */
+enum { BF_STORE_FP32 = 0, BF_STORE_BF16 = 1, BF_STORE_FP16 = 2 };
+
+/* PCG preconditioner: 6x6 block-Jacobi (default) or the paper's scalar Jacobi (Sec. 4.4). */
+enum { BF_PRECOND_BLOCK_JACOBI = 0, BF_PRECOND_JACOBI = 1 };
+
+/* Solver arithmetic.  Both evaluate residuals and Jacobians in FP32.
+ *   BF_PREC_MIXED: per-tile FP32 tree sums merged in FP64; 6x6 blocks, PCG dot products and
+ *                  the alpha/beta scalars in FP64; pose composition in FP64.
+ *   BF_PREC_FP32:  the plain path, FP32 throughout except the FP64 pose composition. */
+enum { BF_PREC_MIXED = 0, BF_PREC_FP32 = 1 };
+
+/* Stats flags */
+enum {
+  BF_FLAG_SINGULAR_BLOCK = 1, /* a diagonal 6x6 block was not SPD: scalar Jacobi used for it */
+  BF_FLAG_EMPTY_FRAME = 2,    /* a frame had no constraint: marked invalid, update kept at 0 (Sec. 4.4.1) */
+  BF_FLAG_PCG_BREAKDOWN = 4   /* PCG stopped early on p.Ap <= 0 */
+};
+
+typedef struct {
+  int device;               /* CUDA device ordinal                                      */
+  int width, height;        /* frame size (every frame of a context has this size)     */
+  double fx, fy, cx, cy;    /* pinhole intrinsics of that frame size                   */
+  float depth_min;          /* depth is valid iff finite and depth_min < D < depth_max */
+  float depth_max;
+  int storage;              /* BF_STORE_*                                              */
+  size_t hbm_budget_bytes;  /* cap on the context's device allocations, 0 = no cap     */
+  void *cuda_stream;        /* cudaStream_t to run on; NULL = the context creates one  */
+  int max_frames_hint;      /* initial frame-store capacity (grows on demand)          */
+} bf_config;
+
+typedef struct {
+  int n_gn;                 /* Gauss-Newton iterations (1..BF_MAX_GN)                  */
+  int n_pcg;                /* PCG iterations per Gauss-Newton iteration (>= 0)        */
+  double w_sparse, w_dense, w_photo, w_geo; /* energy weights (Sec. 4.3)               */
+  int dense_ramp;           /* w_dense(k) = w_dense (k+1)/n_gn if set (Sec. 4.3: linearly increased) */
+  double tau_dist;          /* dense distance gate, metres (default 0.15)              */
+  double tau_normal;        /* dense normal gate, cosine (default 0.9)                 */
+  double max_angle_deg;     /* dense pair set E: view directions within (default 60)   */
+  int precond;              /* BF_PRECOND_*                                            */
+  int dense_on;             /* evaluate the dense term (Sec. 4.3: the paper runs the global
+                               dense solve only at the end of scanning)               */
+  int warm_start;           /* local solves: start from the chunk's previous local poses */
+  int precision;            /* BF_PREC_*                                               */
+  int use_graph;            /* replay the Gauss-Newton loop as a captured CUDA graph   */
+  int tile_px;              /* source pixels per dense work item, 0 = autotuned        */
+} bf_solve_params;
+
+#define BF_MAX_GN 64
+
+typedef struct {
+  int n_gn_done;
+  double energy[BF_MAX_GN + 1];     /* before each GN step, then after the last one     */
+  double e_sparse[BF_MAX_GN + 1];   /* sum_corr w_c ||r||^2 (unweighted by w_sparse)    */
+  double e_photo[BF_MAX_GN + 1];    /* sum r_photo^2                                    */
+  double e_geo[BF_MAX_GN + 1];      /* sum r_geo^2                                      */
+  long long n_dense_valid[BF_MAX_GN + 1]; /* associated pixels over both directions   */
+  double r_max;                     /* largest ||T_i p - T_j q|| at the final poses      */
+  int r_max_pair[2];                /* frame ids of the pair holding it                  */
+  int n_frames, n_pairs, n_dense_pairs;
+  long long n_corr;
+  int flags;                        /* BF_FLAG_*                                         */
+  double ms;                        /* wall time of the solve on the host               */
+} bf_solve_stats;
+
+/* Fill defaults: 640x480 Kinect-like intrinsics scaled to 80x60, depth 0.1..10 m, FP32. */
+void bf_default_config(bf_config *cfg);
+/* Fill defaults: 4 GN x 10 PCG, w_sparse 1, w_dense 0.5, w_photo 0.1, w_geo 1, gates
+ * 0.15 m / 0.9 / 60 deg (Sec. 4.1.1 and 4.3), block-Jacobi, dense on, mixed precision. */
+void bf_default_params(bf_solve_params *p);
+const char *bf_status_string(bf_status s);
+
+/* Create a context on cfg->device.  *out receives the handle. */
+bf_status bf_create(const bf_config *cfg, bf_ctx **out);
+/* Destroy a context and free its device memory.  NULL is a no-op. */
+bf_status bf_destroy(bf_ctx *ctx);
+const char *bf_last_error(bf_ctx *ctx);
+
+/*
+ * Add (or replace) frames first_id .. first_id+n-1 (Sec. 4, input stream S = {f_i}).
+ *   depth, lum: n x H x W float32 (metres; luminance), host or device per ptr_kind.
+ *   init_pose:  n x 16 doubles (camera->world), host, nullable.  When given it becomes the
+ *               frame's world pose (initial estimate of a global solve).
+ * The frames are preprocessed on the device (Sec. 4.1.1 cached frames): validity, normals,
+ * I = |grad L| and grad I, stored per the context's storage type.
+ */
+bf_status bf_add_frames(bf_ctx *ctx, int first_id, int n, const float *depth, const float *lum,
+                        int ptr_kind, const double *init_pose);
+
+/*
+ * Append n sparse correspondences between frames frame_i != frame_j (Sec. 4.3, sparse term).
+ *   p_i: n x 3 float32 points in camera i; p_j: n x 3 float32 points in camera j.
+ *   weight: n float32 per-correspondence weights, nullable (= 1).
+ * Host or device per ptr_kind.  Frames need not exist yet.
+ */
+bf_status bf_add_correspondences(bf_ctx *ctx, int frame_i, int frame_j, int n, const float *p_i,
+                                 const float *p_j, const float *weight, int ptr_kind);
+/* Drop every correspondence of the unordered pair (i, j) (Sec. 4.4.1 pruning). */
+bf_status bf_remove_pair(bf_ctx *ctx, int frame_i, int frame_j);
+/* Drop all correspondences of the context. */
+bf_status bf_clear_correspondences(bf_ctx *ctx);
+
+/*
+ * Local (intra-chunk) solve, Sec. 4.2: frame_ids[0] is the chunk's keyframe and stays fixed;
+ * the other frames start at identity (or, with warm_start, at the chunk's previous local
+ * poses, Sec. 4.4).  Every correspondence pair within the chunk is used; the dense set E is
+ * the pairs within max_angle_deg at the initial poses.  Local poses are stored under chunk_id.
+ * stats: nullable.
+ */
+bf_status bf_solve_local(bf_ctx *ctx, int chunk_id, const int *frame_ids, int n,
+                         const bf_solve_params *params, bf_solve_stats *stats);
+
+/*
+ * Many independent local solves in one batched launch sequence (one problem per chunk).
+ *   chunk_ids: n_chunks ids; frame_ids: concatenated frame lists; offsets: n_chunks + 1.
+ *   stats: nullable, else n_chunks entries.
+ */
+bf_status bf_solve_local_batch(bf_ctx *ctx, int n_chunks, const int *chunk_ids, const int *frame_ids,
+                               const int *offsets, const bf_solve_params *params, bf_solve_stats *stats);
+
+/*
+ * Global (inter-chunk) solve over keyframes, Sec. 4.2: keyframe_ids[0] stays fixed.  A
+ * keyframe's initial pose is its world pose if it has one, else the previous keyframe's
+ * pose composed with the intra-chunk delta of the chunk that links them (Sec. 4.2).
+ * Afterwards every keyframe holds its optimised world pose.  stats: nullable.
+ */
+bf_status bf_solve_global(bf_ctx *ctx, const int *keyframe_ids, int n, const bf_solve_params *params,
+                          bf_solve_stats *stats);
+
+/*
+ * World poses of frames (n x 16 doubles, host).  A chunk member's pose is its keyframe's
+ * world pose composed with its local pose, T_kf T_local (Sec. 4.2); a frame outside any
+ * solved chunk returns its own world pose (identity if never set).
+ */
+bf_status bf_get_poses(bf_ctx *ctx, const int *frame_ids, int n, double *out);
+
+/*
+ * Normal equations at given poses without solving (Sec. 4.4: J^T J dX = -J^T F), for
+ * inspection and testing.  frame_ids[0] is the gauge.  poses: n x 16 host doubles.
+ *   A: (6(n-1))^2 host doubles, row-major; b: 6(n-1) host doubles (= -J^T W r);
+ *   energy4: host [E_total, e_sparse, e_photo, e_geo]; n_dense: host, nullable.
+ * The dense term uses w_dense as given (no ramp).
+ */
+bf_status bf_build_system(bf_ctx *ctx, const int *frame_ids, int n, const double *poses,
+                          const bf_solve_params *params, double *A, double *b, double *energy4,
+                          long long *n_dense);
+
+/*
+ * Preprocessed planes of one frame, as float32 host array 7 x H x W:
+ * depth (0 = invalid), normal x, y, z (0,0,0 = invalid), I, I_x, I_y.
+ */
+bf_status bf_get_frame_planes(bf_ctx *ctx, int frame_id, float *out);
+
+/*
+ * Dense association of frame_i's pixels into frame_j at the given poses (16 doubles each),
+ * as decided by the dense kernel: out_target[k] = ny*W + nx of the nearest target pixel, or -1
+ * if pixel k is rejected.  H*W int32 host output.
+ */
+bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const double *pose_i,
+                               const double *pose_j, const bf_solve_params *params, int32_t *out_target);
+
+/* Device bytes currently held by the context. */
+size_t bf_device_bytes(bf_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BF_H */

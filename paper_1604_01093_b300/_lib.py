@@ -1,0 +1,269 @@
+"""ctypes binding of libbf.so (include/bf.h).  Argument marshalling only.
+
+Every step of the solver runs in the CUDA library; this module only converts numpy
+arrays / torch tensors to pointers and the C structs to Python values.  If the
+library is missing the import fails loudly: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import pathlib
+
+import numpy as np
+
+_PKG = pathlib.Path(__file__).resolve().parent
+LIB_PATH = _PKG / "libbf.so"
+
+BF_OK = 0
+BF_PTR_HOST, BF_PTR_DEVICE = 0, 1
+BF_STORE_FP32, BF_STORE_BF16, BF_STORE_FP16 = 0, 1, 2
+BF_PRECOND_BLOCK_JACOBI, BF_PRECOND_JACOBI = 0, 1
+BF_PREC_MIXED, BF_PREC_FP32 = 0, 1
+BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
+BF_MAX_GN = 64
+
+STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_OUT_OF_MEMORY", 3: "BF_ERR_CUDA",
+          4: "BF_ERR_NOT_FOUND", 5: "BF_ERR_SINGULAR", 6: "BF_ERR_TIMEOUT", 7: "BF_ERR_BUSY"}
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("depth_min", ctypes.c_float), ("depth_max", ctypes.c_float), ("storage", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_size_t), ("cuda_stream", ctypes.c_void_p),
+                ("max_frames_hint", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("n_gn", ctypes.c_int), ("n_pcg", ctypes.c_int),
+                ("w_sparse", ctypes.c_double), ("w_dense", ctypes.c_double), ("w_photo", ctypes.c_double),
+                ("w_geo", ctypes.c_double), ("dense_ramp", ctypes.c_int), ("tau_dist", ctypes.c_double),
+                ("tau_normal", ctypes.c_double), ("max_angle_deg", ctypes.c_double), ("precond", ctypes.c_int),
+                ("dense_on", ctypes.c_int), ("warm_start", ctypes.c_int), ("precision", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("n_gn_done", ctypes.c_int),
+                ("energy", ctypes.c_double * (BF_MAX_GN + 1)), ("e_sparse", ctypes.c_double * (BF_MAX_GN + 1)),
+                ("e_photo", ctypes.c_double * (BF_MAX_GN + 1)), ("e_geo", ctypes.c_double * (BF_MAX_GN + 1)),
+                ("n_dense_valid", ctypes.c_longlong * (BF_MAX_GN + 1)),
+                ("r_max", ctypes.c_double), ("r_max_pair", ctypes.c_int * 2),
+                ("n_frames", ctypes.c_int), ("n_pairs", ctypes.c_int), ("n_dense_pairs", ctypes.c_int),
+                ("n_corr", ctypes.c_longlong), ("flags", ctypes.c_int), ("ms", ctypes.c_double)]
+
+    def to_dict(self):
+        k = self.n_gn_done + 1
+        return dict(n_gn=self.n_gn_done, energy=list(self.energy[:k]), e_sparse=list(self.e_sparse[:k]),
+                    e_photo=list(self.e_photo[:k]), e_geo=list(self.e_geo[:k]),
+                    n_dense=list(self.n_dense_valid[:k]), r_max=self.r_max, r_max_pair=tuple(self.r_max_pair),
+                    n_frames=self.n_frames, n_pairs=self.n_pairs, n_dense_pairs=self.n_dense_pairs,
+                    n_corr=self.n_corr, flags=self.flags, ms=self.ms)
+
+
+_lib = None
+
+
+def lib():
+    """Load libbf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1604_01093_b300.build.build()")
+    L = ctypes.CDLL(str(LIB_PATH))
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "bf_default_config": (None, [ctypes.POINTER(Config)]),
+        "bf_default_params": (None, [ctypes.POINTER(SolveParams)]),
+        "bf_status_string": (ctypes.c_char_p, [I]),
+        "bf_create": (I, [ctypes.POINTER(Config), ctypes.POINTER(P)]),
+        "bf_destroy": (I, [P]),
+        "bf_last_error": (ctypes.c_char_p, [P]),
+        "bf_add_frames": (I, [P, I, I, P, P, I, P]),
+        "bf_add_correspondences": (I, [P, I, I, I, P, P, P, I]),
+        "bf_remove_pair": (I, [P, I, I]),
+        "bf_clear_correspondences": (I, [P]),
+        "bf_solve_local": (I, [P, I, P, I, ctypes.POINTER(SolveParams), P]),
+        "bf_solve_local_batch": (I, [P, I, P, P, P, ctypes.POINTER(SolveParams), P]),
+        "bf_solve_global": (I, [P, P, I, ctypes.POINTER(SolveParams), P]),
+        "bf_get_poses": (I, [P, P, I, P]),
+        "bf_build_system": (I, [P, P, I, P, ctypes.POINTER(SolveParams), P, P, P, P]),
+        "bf_get_frame_planes": (I, [P, I, P]),
+        "bf_debug_association": (I, [P, I, I, P, P, ctypes.POINTER(SolveParams), P]),
+        "bf_device_bytes": (ctypes.c_size_t, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+# symbols declared in include/bf.h (checked by the CPU tests)
+EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_create", "bf_destroy",
+           "bf_last_error", "bf_add_frames", "bf_add_correspondences", "bf_remove_pair",
+           "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
+           "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes"]
+
+
+class BFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or a torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_device(a):
+    return a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def _f32(a):
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float32)
+    import torch
+    return a.to(torch.float32).contiguous()
+
+
+def default_params(**kw) -> SolveParams:
+    p = SolveParams()
+    lib().bf_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"unknown solve parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class Context:
+    """One library context (one frame size, one device, one stream)."""
+
+    def __init__(self, width=80, height=60, fx=None, fy=None, cx=None, cy=None, device=0, depth_min=0.1,
+                 depth_max=10.0, storage=BF_STORE_FP32, hbm_budget_bytes=0, stream=None, max_frames_hint=64):
+        L = lib()
+        cfg = Config()
+        L.bf_default_config(ctypes.byref(cfg))
+        s = width / 640.0
+        cfg.device, cfg.width, cfg.height = device, width, height
+        cfg.fx = 525.0 * s if fx is None else fx
+        cfg.fy = 525.0 * s if fy is None else fy
+        cfg.cx = (width - 1) / 2.0 if cx is None else cx
+        cfg.cy = (height - 1) / 2.0 if cy is None else cy
+        cfg.depth_min, cfg.depth_max, cfg.storage = depth_min, depth_max, storage
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        cfg.cuda_stream = stream
+        cfg.max_frames_hint = max_frames_hint
+        h = ctypes.c_void_p()
+        st = L.bf_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != BF_OK:
+            raise BFError(st, "bf_create failed")
+        self.h = h
+        self.cfg = cfg
+        self.W, self.H = width, height
+
+    def close(self):
+        if self.h:
+            lib().bf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != BF_OK:
+            raise BFError(st, lib().bf_last_error(self.h).decode())
+
+    # ---------------------------------------------------------------- inputs
+    def add_frames(self, first_id, depth, lum, init_pose=None):
+        depth, lum = _f32(depth), _f32(lum)
+        n = depth.shape[0]
+        kind = BF_PTR_DEVICE if _is_device(depth) else BF_PTR_HOST
+        init = None if init_pose is None else np.ascontiguousarray(init_pose, dtype=np.float64).reshape(n, 16)
+        self._check(lib().bf_add_frames(self.h, first_id, n, _ptr(depth), _ptr(lum), kind, _ptr(init)))
+
+    def add_correspondences(self, i, j, p_i, p_j, weight=None):
+        p_i, p_j = _f32(p_i), _f32(p_j)
+        w = None if weight is None else _f32(weight)
+        kind = BF_PTR_DEVICE if _is_device(p_i) else BF_PTR_HOST
+        self._check(lib().bf_add_correspondences(self.h, i, j, p_i.shape[0], _ptr(p_i), _ptr(p_j), _ptr(w), kind))
+
+    def remove_pair(self, i, j):
+        self._check(lib().bf_remove_pair(self.h, i, j))
+
+    def clear_correspondences(self):
+        self._check(lib().bf_clear_correspondences(self.h))
+
+    # ---------------------------------------------------------------- solves
+    def solve_local(self, chunk_id, frame_ids, params=None, **kw):
+        p = params or default_params(**kw)
+        ids = np.ascontiguousarray(frame_ids, dtype=np.int32)
+        st = SolveStats()
+        self._check(lib().bf_solve_local(self.h, chunk_id, _ptr(ids), len(ids), ctypes.byref(p), ctypes.byref(st)))
+        return st.to_dict()
+
+    def solve_local_batch(self, chunk_ids, frame_lists, params=None, **kw):
+        p = params or default_params(**kw)
+        cids = np.ascontiguousarray(chunk_ids, dtype=np.int32)
+        flat = np.ascontiguousarray(np.concatenate([np.asarray(f, dtype=np.int32) for f in frame_lists]))
+        off = np.zeros(len(frame_lists) + 1, dtype=np.int32)
+        off[1:] = np.cumsum([len(f) for f in frame_lists])
+        stats = (SolveStats * len(frame_lists))()
+        self._check(lib().bf_solve_local_batch(self.h, len(cids), _ptr(cids), _ptr(flat), _ptr(off), ctypes.byref(p),
+                                               ctypes.cast(stats, ctypes.c_void_p)))
+        return [s.to_dict() for s in stats]
+
+    def solve_global(self, keyframe_ids, params=None, **kw):
+        p = params or default_params(**kw)
+        ids = np.ascontiguousarray(keyframe_ids, dtype=np.int32)
+        st = SolveStats()
+        self._check(lib().bf_solve_global(self.h, _ptr(ids), len(ids), ctypes.byref(p), ctypes.byref(st)))
+        return st.to_dict()
+
+    def get_poses(self, frame_ids):
+        ids = np.ascontiguousarray(frame_ids, dtype=np.int32)
+        out = np.zeros((len(ids), 4, 4), dtype=np.float64)
+        self._check(lib().bf_get_poses(self.h, _ptr(ids), len(ids), _ptr(out)))
+        return out
+
+    # ------------------------------------------------------------ inspection
+    def build_system(self, frame_ids, poses, params=None, **kw):
+        p = params or default_params(**kw)
+        ids = np.ascontiguousarray(frame_ids, dtype=np.int32)
+        n = len(ids)
+        P = np.ascontiguousarray(poses, dtype=np.float64).reshape(n, 16)
+        m = 6 * (n - 1)
+        A = np.zeros((m, m))
+        b = np.zeros(m)
+        e4 = np.zeros(4)
+        nd = ctypes.c_longlong()
+        self._check(lib().bf_build_system(self.h, _ptr(ids), n, _ptr(P), ctypes.byref(p), _ptr(A), _ptr(b), _ptr(e4),
+                                          ctypes.byref(nd)))
+        return dict(A=A, b=b, energy=e4[0], e_sparse=e4[1], e_photo=e4[2], e_geo=e4[3], n_dense=nd.value)
+
+    def frame_planes(self, frame_id):
+        out = np.zeros((7, self.H, self.W), dtype=np.float32)
+        self._check(lib().bf_get_frame_planes(self.h, frame_id, _ptr(out)))
+        return out
+
+    def association(self, i, j, pose_i, pose_j, params=None, **kw):
+        p = params or default_params(**kw)
+        out = np.zeros(self.W * self.H, dtype=np.int32)
+        pi = np.ascontiguousarray(pose_i, dtype=np.float64).reshape(16)
+        pj = np.ascontiguousarray(pose_j, dtype=np.float64).reshape(16)
+        self._check(lib().bf_debug_association(self.h, i, j, _ptr(pi), _ptr(pj), ctypes.byref(p), _ptr(out)))
+        return out
+
+    def device_bytes(self):
+        return lib().bf_device_bytes(self.h)

@@ -1,0 +1,1141 @@
+// C ABI of the library: context, frame store, correspondence pool, solve orchestration.
+//
+// A solve (local, batched local or global) is flattened into one set of tables: frames of
+// all its problems, unordered pairs with correspondences, directed dense pairs split into
+// pixel tiles, correspondence segments, and per-frame incidence lists.  The Gauss-Newton loop
+// then runs on the context's stream as a fixed sequence of kernels per iteration
+// (Sec. 4.4: linearise, assemble J^T J and -J^T F, PCG, update), with the energy evaluated
+// before each step and after the last one.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "bf_internal.cuh"
+#include "bf.h"
+
+using namespace bf;
+
+namespace {
+
+struct FrameInfo {
+  int slot = -1;
+  bool has_world = false;
+  double world[12];      // R row-major, t
+  int member_of = -1;    // chunk whose non-first member this frame is (latest local solve)
+  int keyframe_of = -1;  // chunk whose first frame this frame is
+};
+
+struct Chunk {
+  std::vector<int> frames;
+  std::vector<std::array<double, 12>> local;  // pose relative to frames[0]
+};
+
+struct Seg {
+  int off, cnt;
+};
+
+typedef std::array<double, 12> Pose12;
+
+Pose12 ident12() { return Pose12{1, 0, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0}; }
+
+Pose12 from16(const double *m) {
+  return Pose12{m[0], m[1], m[2], m[4], m[5], m[6], m[8], m[9], m[10], m[3], m[7], m[11]};
+}
+void to16(const Pose12 &p, double *m) {
+  const double v[16] = {p[0], p[1], p[2], p[9], p[3], p[4], p[5], p[10], p[6], p[7], p[8], p[11], 0, 0, 0, 1};
+  std::memcpy(m, v, sizeof(v));
+}
+Pose12 compose(const Pose12 &A, const Pose12 &B) {  // A * B
+  Pose12 C;
+  for (int i = 0; i < 3; ++i) {
+    for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+    C[9 + i] = A[3 * i] * B[9] + A[3 * i + 1] * B[10] + A[3 * i + 2] * B[11] + A[9 + i];
+  }
+  return C;
+}
+
+inline uint64_t pair_key(int a, int b) {
+  const uint32_t lo = (uint32_t)std::min(a, b), hi = (uint32_t)std::max(a, b);
+  return ((uint64_t)lo << 32) | hi;
+}
+
+}  // namespace
+
+struct bf_ctx {
+  bf_config cfg{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  size_t bytes = 0;
+  Intr intr{};
+  // frame store
+  int cap = 0;
+  float4 *A = nullptr, *B = nullptr;
+  float *kx = nullptr, *ky = nullptr;
+  std::unordered_map<int, FrameInfo> frames;
+  std::vector<int> free_slots;
+  int next_slot = 0;
+  // staging for host frame uploads
+  float *stage = nullptr;
+  size_t stage_bytes = 0;
+  int *slot_dev = nullptr;
+  int slot_dev_cap = 0;
+  // correspondence pool
+  float4 *cP = nullptr, *cQ = nullptr;
+  long long ccap = 0, cused = 0;
+  std::unordered_map<uint64_t, std::vector<Seg>> corr;
+  std::unordered_map<int, Chunk> chunks;
+  // solve workspace arena
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+};
+
+// ------------------------------------------------------------------------------- helpers
+static bf_status fail(bf_ctx *c, bf_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+static bf_status cuda_fail(bf_ctx *c, cudaError_t e, const char *where) {
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? BF_ERR_OUT_OF_MEMORY : BF_ERR_CUDA,
+              std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+static bf_status dalloc(bf_ctx *c, void **p, size_t n, const char *what) {
+  *p = nullptr;
+  if (n == 0) return BF_OK;
+  if (c->cfg.hbm_budget_bytes && c->bytes + n > c->cfg.hbm_budget_bytes)
+    return fail(c, BF_ERR_OUT_OF_MEMORY, std::string("HBM budget exceeded allocating ") + what);
+  cudaError_t e = cudaMalloc(p, n);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(c, e, what);
+  }
+  c->bytes += n;
+  return BF_OK;
+}
+
+static void dfree(bf_ctx *c, void *p, size_t n) {
+  if (p) {
+    cudaFree(p);
+    c->bytes -= n;
+  }
+}
+
+static FrameStore frame_store(const bf_ctx *c) {
+  FrameStore fs;
+  fs.storage = c->cfg.storage;
+  fs.W = c->cfg.width;
+  fs.H = c->cfg.height;
+  fs.A = c->A;
+  fs.B = c->B;
+  fs.P16 = nullptr;
+  fs.kx = c->kx;
+  fs.ky = c->ky;
+  return fs;
+}
+
+// grow the frame store to hold at least n slots
+static bf_status ensure_frames(bf_ctx *c, int n) {
+  if (n <= c->cap) return BF_OK;
+  int ncap = std::max(n, std::max(2 * c->cap, c->cfg.max_frames_hint));
+  const size_t HW = (size_t)c->cfg.width * c->cfg.height;
+  float4 *nA = nullptr, *nB = nullptr;
+  bf_status s = dalloc(c, (void **)&nA, ncap * HW * sizeof(float4), "frame store");
+  if (s) return s;
+  s = dalloc(c, (void **)&nB, ncap * HW * sizeof(float4), "frame store");
+  if (s) {
+    dfree(c, nA, ncap * HW * sizeof(float4));
+    return s;
+  }
+  if (c->cap) {
+    CK(cudaMemcpyAsync(nA, c->A, c->cap * HW * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow frames");
+    CK(cudaMemcpyAsync(nB, c->B, c->cap * HW * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow frames");
+    CK(cudaStreamSynchronize(c->st), "grow frames");
+  }
+  dfree(c, c->A, c->cap * HW * sizeof(float4));
+  dfree(c, c->B, c->cap * HW * sizeof(float4));
+  c->A = nA;
+  c->B = nB;
+  c->cap = ncap;
+  return BF_OK;
+}
+
+static bf_status ensure_corr(bf_ctx *c, long long n) {
+  if (n <= c->ccap) return BF_OK;
+  long long ncap = std::max(n, std::max(2 * c->ccap, 1LL << 16));
+  if (ncap > 0x7fffffffLL) return fail(c, BF_ERR_INVALID_ARG, "correspondence pool exceeds 2^31 entries");
+  float4 *nP = nullptr, *nQ = nullptr;
+  bf_status s = dalloc(c, (void **)&nP, ncap * sizeof(float4), "correspondence pool");
+  if (s) return s;
+  s = dalloc(c, (void **)&nQ, ncap * sizeof(float4), "correspondence pool");
+  if (s) {
+    dfree(c, nP, ncap * sizeof(float4));
+    return s;
+  }
+  if (c->cused) {
+    CK(cudaMemcpyAsync(nP, c->cP, c->cused * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow pool");
+    CK(cudaMemcpyAsync(nQ, c->cQ, c->cused * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow pool");
+    CK(cudaStreamSynchronize(c->st), "grow pool");
+  }
+  dfree(c, c->cP, c->ccap * sizeof(float4));
+  dfree(c, c->cQ, c->ccap * sizeof(float4));
+  c->cP = nP;
+  c->cQ = nQ;
+  c->ccap = ncap;
+  return BF_OK;
+}
+
+// ------------------------------------------------------------------------------ config
+extern "C" void bf_default_config(bf_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->width = 80;
+  cfg->height = 60;
+  cfg->fx = cfg->fy = 525.0 * 80.0 / 640.0;
+  cfg->cx = (80 - 1) / 2.0;
+  cfg->cy = (60 - 1) / 2.0;
+  cfg->depth_min = 0.1f;
+  cfg->depth_max = 10.0f;
+  cfg->storage = BF_STORE_FP32;
+  cfg->hbm_budget_bytes = 0;
+  cfg->cuda_stream = nullptr;
+  cfg->max_frames_hint = 64;
+}
+
+extern "C" void bf_default_params(bf_solve_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->n_gn = 4;
+  p->n_pcg = 10;
+  p->w_sparse = 1.0;
+  p->w_dense = 0.5;
+  p->w_photo = 0.1;
+  p->w_geo = 1.0;
+  p->dense_ramp = 0;
+  p->tau_dist = 0.15;
+  p->tau_normal = 0.9;
+  p->max_angle_deg = 60.0;
+  p->precond = BF_PRECOND_BLOCK_JACOBI;
+  p->dense_on = 1;
+  p->warm_start = 0;
+  p->precision = BF_PREC_MIXED;
+  p->use_graph = 0;
+  p->tile_px = 0;
+}
+
+extern "C" const char *bf_status_string(bf_status s) {
+  switch (s) {
+    case BF_OK: return "ok";
+    case BF_ERR_INVALID_ARG: return "invalid argument";
+    case BF_ERR_OUT_OF_MEMORY: return "out of memory";
+    case BF_ERR_CUDA: return "CUDA error";
+    case BF_ERR_NOT_FOUND: return "not found";
+    case BF_ERR_SINGULAR: return "singular block";
+    case BF_ERR_TIMEOUT: return "timeout";
+    case BF_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+extern "C" const char *bf_last_error(bf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" size_t bf_device_bytes(bf_ctx *ctx) { return ctx ? ctx->bytes : 0; }
+
+extern "C" bf_status bf_create(const bf_config *cfg, bf_ctx **out) {
+  if (!cfg || !out) return BF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (cfg->width < 8 || cfg->height < 8 || cfg->width > 8192 || cfg->height > 8192) return BF_ERR_INVALID_ARG;
+  if (!(cfg->fx > 0) || !(cfg->fy > 0)) return BF_ERR_INVALID_ARG;
+  if (cfg->storage != BF_STORE_FP32) return BF_ERR_INVALID_ARG;
+  bf_ctx *c = new bf_ctx();
+  c->cfg = *cfg;
+  if (c->cfg.max_frames_hint <= 0) c->cfg.max_frames_hint = 64;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return BF_ERR_CUDA;
+  }
+  if (cfg->cuda_stream) {
+    c->st = (cudaStream_t)cfg->cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return BF_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  c->intr.fx = (float)cfg->fx;
+  c->intr.fy = (float)cfg->fy;
+  c->intr.cx = (float)cfg->cx;
+  c->intr.cy = (float)cfg->cy;
+  c->intr.W = cfg->width;
+  c->intr.H = cfg->height;
+  // kx[x] = fl32((x - cx) / fx), ky[y] = fl32((y - cy) / fy): FP64 then one rounding
+  std::vector<float> kx(cfg->width), ky(cfg->height);
+  for (int x = 0; x < cfg->width; ++x) kx[x] = (float)(((double)x - cfg->cx) / cfg->fx);
+  for (int y = 0; y < cfg->height; ++y) ky[y] = (float)(((double)y - cfg->cy) / cfg->fy);
+  bf_status s = dalloc(c, (void **)&c->kx, cfg->width * sizeof(float), "ray tables");
+  if (!s) s = dalloc(c, (void **)&c->ky, cfg->height * sizeof(float), "ray tables");
+  if (!s) {
+    if (cudaMemcpy(c->kx, kx.data(), kx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->ky, ky.data(), ky.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      s = BF_ERR_CUDA;
+    }
+  }
+  if (s) {
+    bf_destroy(c);
+    return s;
+  }
+  *out = c;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_destroy(bf_ctx *c) {
+  if (!c) return BF_OK;
+  if (c->st) cudaStreamSynchronize(c->st);
+  cudaFree(c->A);
+  cudaFree(c->B);
+  cudaFree(c->kx);
+  cudaFree(c->ky);
+  cudaFree(c->stage);
+  cudaFree(c->slot_dev);
+  cudaFree(c->cP);
+  cudaFree(c->cQ);
+  cudaFree(c->ws);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  cudaGetLastError();
+  delete c;
+  return BF_OK;
+}
+
+// ------------------------------------------------------------------------------- frames
+extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *depth, const float *lum,
+                                   int ptr_kind, const double *init_pose) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!depth || !lum)) || (ptr_kind != BF_PTR_HOST && ptr_kind != BF_PTR_DEVICE))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_add_frames: bad arguments");
+  if (first_id < 0 || (long long)first_id + n > 0x7fffffffLL)
+    return fail(c, BF_ERR_INVALID_ARG, "bf_add_frames: bad frame id range");
+  if (n == 0) return BF_OK;
+  const size_t HW = (size_t)c->cfg.width * c->cfg.height;
+  std::vector<int> slots(n);
+  int need = c->next_slot;
+  for (int k = 0; k < n; ++k) {
+    auto it = c->frames.find(first_id + k);
+    if (it == c->frames.end()) ++need;
+  }
+  bf_status s = ensure_frames(c, need);
+  if (s) return s;
+  for (int k = 0; k < n; ++k) {
+    FrameInfo &fi = c->frames[first_id + k];
+    if (fi.slot < 0) {
+      if (!c->free_slots.empty()) {
+        fi.slot = c->free_slots.back();
+        c->free_slots.pop_back();
+      } else {
+        fi.slot = c->next_slot++;
+      }
+    }
+    slots[k] = fi.slot;
+    if (init_pose) {
+      Pose12 p = from16(init_pose + 16 * k);
+      std::memcpy(fi.world, p.data(), sizeof(fi.world));
+      fi.has_world = true;
+    }
+  }
+  if (n > c->slot_dev_cap) {
+    dfree(c, c->slot_dev, (size_t)c->slot_dev_cap * sizeof(int));
+    c->slot_dev = nullptr;
+    c->slot_dev_cap = 0;
+    s = dalloc(c, (void **)&c->slot_dev, (size_t)std::max(n, 256) * sizeof(int), "slot table");
+    if (s) return s;
+    c->slot_dev_cap = std::max(n, 256);
+  }
+  CK(cudaMemcpyAsync(c->slot_dev, slots.data(), n * sizeof(int), cudaMemcpyHostToDevice, c->st), "slots");
+  const float *dptr = depth, *lptr = lum;
+  if (ptr_kind == BF_PTR_HOST) {
+    const size_t need_b = 2 * (size_t)n * HW * sizeof(float);
+    if (need_b > c->stage_bytes) {
+      dfree(c, c->stage, c->stage_bytes);
+      c->stage = nullptr;
+      c->stage_bytes = 0;
+      s = dalloc(c, (void **)&c->stage, need_b, "frame staging");
+      if (s) return s;
+      c->stage_bytes = need_b;
+    }
+    CK(cudaMemcpyAsync(c->stage, depth, n * HW * sizeof(float), cudaMemcpyHostToDevice, c->st), "upload depth");
+    CK(cudaMemcpyAsync(c->stage + n * HW, lum, n * HW * sizeof(float), cudaMemcpyHostToDevice, c->st),
+       "upload luminance");
+    dptr = c->stage;
+    lptr = c->stage + n * HW;
+  }
+  launch_preprocess(dptr, lptr, n, c->slot_dev, frame_store(c), c->A, c->B, nullptr, c->cfg.depth_min,
+                    c->cfg.depth_max, c->st);
+  CK(cudaGetLastError(), "preprocess launch");
+  if (ptr_kind == BF_PTR_HOST) CK(cudaStreamSynchronize(c->st), "preprocess");
+  return BF_OK;
+}
+
+extern "C" bf_status bf_get_frame_planes(bf_ctx *c, int frame_id, float *out) {
+  if (!c || !out) return BF_ERR_INVALID_ARG;
+  auto it = c->frames.find(frame_id);
+  if (it == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "unknown frame id");
+  const size_t HW = (size_t)c->cfg.width * c->cfg.height;
+  std::vector<float4> a(HW), b(HW);
+  CK(cudaMemcpyAsync(a.data(), c->A + it->second.slot * HW, HW * sizeof(float4), cudaMemcpyDeviceToHost, c->st),
+     "planes");
+  CK(cudaMemcpyAsync(b.data(), c->B + it->second.slot * HW, HW * sizeof(float4), cudaMemcpyDeviceToHost, c->st),
+     "planes");
+  CK(cudaStreamSynchronize(c->st), "planes");
+  for (size_t k = 0; k < HW; ++k) {
+    out[k] = a[k].x;
+    out[HW + k] = a[k].y;
+    out[2 * HW + k] = a[k].z;
+    out[3 * HW + k] = a[k].w;
+    out[4 * HW + k] = b[k].x;
+    out[5 * HW + k] = b[k].y;
+    out[6 * HW + k] = b[k].z;
+  }
+  return BF_OK;
+}
+
+// ---------------------------------------------------------------------- correspondences
+extern "C" bf_status bf_add_correspondences(bf_ctx *c, int frame_i, int frame_j, int n, const float *p_i,
+                                            const float *p_j, const float *weight, int ptr_kind) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (n < 0 || frame_i == frame_j || frame_i < 0 || frame_j < 0 || (n > 0 && (!p_i || !p_j)) ||
+      (ptr_kind != BF_PTR_HOST && ptr_kind != BF_PTR_DEVICE))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences: bad arguments");
+  if (n == 0) return BF_OK;
+  bf_status s = ensure_corr(c, c->cused + n);
+  if (s) return s;
+  const int swap = frame_i > frame_j ? 1 : 0;
+  if (ptr_kind == BF_PTR_HOST) {
+    std::vector<float4> P(n), Q(n);
+    const float *a = swap ? p_j : p_i;
+    const float *b = swap ? p_i : p_j;
+    for (int k = 0; k < n; ++k) {
+      P[k] = make_float4(a[3 * k], a[3 * k + 1], a[3 * k + 2], weight ? weight[k] : 1.f);
+      Q[k] = make_float4(b[3 * k], b[3 * k + 1], b[3 * k + 2], 0.f);
+    }
+    CK(cudaMemcpyAsync(c->cP + c->cused, P.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->st), "corr");
+    CK(cudaMemcpyAsync(c->cQ + c->cused, Q.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->st), "corr");
+    CK(cudaStreamSynchronize(c->st), "corr");
+  } else {
+    launch_pack_corr(p_i, p_j, weight, n, swap, c->cP + c->cused, c->cQ + c->cused, c->st);
+    CK(cudaGetLastError(), "pack corr");
+  }
+  c->corr[pair_key(frame_i, frame_j)].push_back(Seg{(int)c->cused, n});
+  c->cused += n;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_remove_pair(bf_ctx *c, int frame_i, int frame_j) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  auto it = c->corr.find(pair_key(frame_i, frame_j));
+  if (it == c->corr.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_remove_pair: no such pair");
+  c->corr.erase(it);
+  return BF_OK;
+}
+
+extern "C" bf_status bf_clear_correspondences(bf_ctx *c) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  c->corr.clear();
+  c->cused = 0;
+  return BF_OK;
+}
+
+// ------------------------------------------------------------------------- solve tables
+namespace {
+
+struct Problem {
+  std::vector<int> ids;
+  std::vector<Pose12> init;
+};
+
+struct HostTables {
+  int n_frames = 0, n_pairs = 0, n_dp = 0, n_tiles = 0, n_segs = 0, n_vars = 0, n_prob = 0;
+  std::vector<int> frame_slot, frame_var, pair_a, pair_b, pair_dp, pair_seg0, pair_seg1;
+  std::vector<int> dp_src, dp_dst, dp_pair, dp_dir, dp_tile0, dp_tile1, tile_dp, tile_px0, tile_px1;
+  std::vector<int> seg_pair, seg_off, seg_cnt, seg_swap, inc_off, inc, var_frame;
+  std::vector<int> prob_var0, prob_var1, prob_pair0, prob_pair1, prob_frame0;
+  std::vector<int> pair_ida, pair_idb;  // frame ids of the pair (for stats)
+  std::vector<double> pose;             // n_frames x 12
+  long long n_corr = 0;
+  std::vector<int> prob_npairs, prob_ndense;
+  std::vector<long long> prob_ncorr;
+};
+
+// Build the flattened tables of a set of problems.  force_dense: every pair gets both dense
+// directions (debug), else the Sec. 4.3 angle test on the initial poses selects E.
+bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm, HostTables &T) {
+  const int HW = c->cfg.width * c->cfg.height;
+  int tile_px = prm.tile_px > 0 ? prm.tile_px : std::min(HW, 4800);
+  T.n_prob = (int)probs.size();
+  std::vector<std::vector<std::pair<int, int>>> var_inc;  // per var: (pair, side)
+  const double cos_max = std::cos(prm.max_angle_deg * M_PI / 180.0);
+  for (int pi = 0; pi < T.n_prob; ++pi) {
+    const Problem &P = probs[pi];
+    const int n = (int)P.ids.size();
+    const int F0 = T.n_frames;
+    T.prob_frame0.push_back(F0);
+    T.prob_var0.push_back(T.n_vars);
+    std::unordered_map<int, int> loc;
+    loc.reserve(n * 2);
+    for (int k = 0; k < n; ++k) {
+      auto it = c->frames.find(P.ids[k]);
+      if (it == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "solve: unknown frame id " + std::to_string(P.ids[k]));
+      if (!loc.emplace(P.ids[k], k).second)
+        return fail(c, BF_ERR_INVALID_ARG, "solve: duplicate frame id " + std::to_string(P.ids[k]));
+      T.frame_slot.push_back(it->second.slot);
+      if (k == 0) {
+        T.frame_var.push_back(-1);
+      } else {
+        T.frame_var.push_back(T.n_vars);
+        T.var_frame.push_back(F0 + k);
+        var_inc.emplace_back();
+        ++T.n_vars;
+      }
+      for (int q = 0; q < 12; ++q) T.pose.push_back(P.init[k][q]);
+    }
+    T.n_frames += n;
+    T.prob_var1.push_back(T.n_vars);
+    // pairs with correspondences among the problem's frames
+    std::vector<std::array<int, 2>> plist;
+    if ((long long)n * (n - 1) / 2 <= (long long)c->corr.size()) {
+      for (int a = 0; a < n; ++a)
+        for (int b = a + 1; b < n; ++b)
+          if (c->corr.count(pair_key(P.ids[a], P.ids[b]))) plist.push_back({a, b});
+    } else {
+      for (auto &kv : c->corr) {
+        const int lo = (int)(kv.first >> 32), hi = (int)(kv.first & 0xffffffffu);
+        auto ia = loc.find(lo), ib = loc.find(hi);
+        if (ia == loc.end() || ib == loc.end()) continue;
+        plist.push_back({std::min(ia->second, ib->second), std::max(ia->second, ib->second)});
+      }
+      std::sort(plist.begin(), plist.end());
+    }
+    T.prob_pair0.push_back(T.n_pairs);
+    int ndense = 0;
+    long long ncorr = 0;
+    for (auto &ab : plist) {
+      const int a = ab[0], b = ab[1];
+      const int p = T.n_pairs++;
+      T.pair_a.push_back(F0 + a);
+      T.pair_b.push_back(F0 + b);
+      T.pair_ida.push_back(P.ids[a]);
+      T.pair_idb.push_back(P.ids[b]);
+      const auto &segs = c->corr[pair_key(P.ids[a], P.ids[b])];
+      T.pair_seg0.push_back(T.n_segs);
+      const int swap = P.ids[a] > P.ids[b] ? 1 : 0;  // pool stores the smaller id's point first
+      for (const Seg &sg : segs) {
+        T.seg_pair.push_back(p);
+        T.seg_off.push_back(sg.off);
+        T.seg_cnt.push_back(sg.cnt);
+        T.seg_swap.push_back(swap);
+        ncorr += sg.cnt;
+        ++T.n_segs;
+      }
+      T.pair_seg1.push_back(T.n_segs);
+      // dense set E: optical axes within max_angle at the initial poses (FP64)
+      bool dense = false;
+      if (prm.dense_on) {
+        const Pose12 &Pa = P.init[a], &Pb = P.init[b];
+        const double dot = (Pa[2] * Pb[2] + Pa[5] * Pb[5]) + Pa[8] * Pb[8];
+        dense = dot > cos_max;
+      }
+      for (int dir = 0; dir < 2; ++dir) {
+        if (!dense) {
+          T.pair_dp.push_back(-1);
+          continue;
+        }
+        const int d = T.n_dp++;
+        T.pair_dp.push_back(d);
+        T.dp_src.push_back(dir == 0 ? F0 + a : F0 + b);
+        T.dp_dst.push_back(dir == 0 ? F0 + b : F0 + a);
+        T.dp_pair.push_back(p);
+        T.dp_dir.push_back(dir);
+        T.dp_tile0.push_back(T.n_tiles);
+        for (int px = 0; px < HW; px += tile_px) {
+          T.tile_dp.push_back(d);
+          T.tile_px0.push_back(px);
+          T.tile_px1.push_back(std::min(HW, px + tile_px));
+          ++T.n_tiles;
+        }
+        T.dp_tile1.push_back(T.n_tiles);
+      }
+      if (dense) ++ndense;
+      if (a != 0) var_inc[T.frame_var[F0 + a]].push_back({p, 0});
+      if (b != 0) var_inc[T.frame_var[F0 + b]].push_back({p, 1});
+    }
+    T.prob_pair1.push_back(T.n_pairs);
+    T.prob_npairs.push_back((int)plist.size());
+    T.prob_ndense.push_back(ndense);
+    T.prob_ncorr.push_back(ncorr);
+    T.n_corr += ncorr;
+  }
+  T.inc_off.assign(T.n_vars + 1, 0);
+  for (int v = 0; v < T.n_vars; ++v) T.inc_off[v + 1] = T.inc_off[v] + (int)var_inc[v].size();
+  for (int v = 0; v < T.n_vars; ++v)
+    for (auto &e : var_inc[v]) T.inc.push_back(2 * e.first + e.second);
+  return BF_OK;
+}
+
+// Device arena: bump allocations aligned to 256 bytes.
+struct Arena {
+  char *base;
+  size_t off = 0;
+  template <typename X>
+  X *take(size_t n) {
+    X *p = (X *)(base + off);
+    off += (n * sizeof(X) + 255) & ~(size_t)255;
+    return p;
+  }
+};
+
+struct DevSolve {
+  Tables t;
+  double *pose;
+  float *pairM;
+  void *dpart, *spart;
+  float *srmax;
+  int *srarg;
+  void *pairblk, *pairen;
+  float *pairoff;
+  void *Dd, *rhs;
+  float *Df, *Minv;
+  int *vflags, *pflags;
+  float *x, *r, *z, *p, *q;
+  double *energy;  // (n_gn + 1) x n_prob x 4
+  int *assoc;
+};
+
+size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D, size_t acc_size, int HW,
+              bool want_assoc) {
+  Arena a{base};
+  int *ib = a.take<int>(n_int);
+  double *pose = a.take<double>(T.n_frames * 12);
+  float *pairM = a.take<float>((size_t)T.n_pairs * 24);
+  char *dpart = a.take<char>((size_t)T.n_tiles * NPART * acc_size);
+  char *spart = a.take<char>((size_t)T.n_segs * NPART * acc_size);
+  float *srmax = a.take<float>(T.n_segs);
+  int *srarg = a.take<int>(T.n_segs);
+  char *pairblk = a.take<char>((size_t)T.n_pairs * PAIRBLK * acc_size);
+  char *pairen = a.take<char>((size_t)T.n_pairs * PAIREN * acc_size);
+  float *pairoff = a.take<float>((size_t)T.n_pairs * 36);
+  char *Dd = a.take<char>((size_t)T.n_vars * 36 * acc_size);
+  char *rhs = a.take<char>((size_t)T.n_vars * 6 * acc_size);
+  float *Df = a.take<float>((size_t)T.n_vars * 36);
+  float *Minv = a.take<float>((size_t)T.n_vars * 36);
+  int *vflags = a.take<int>(T.n_vars);
+  int *pflags = a.take<int>(T.n_prob);
+  float *x = a.take<float>((size_t)T.n_vars * 6);
+  float *r = a.take<float>((size_t)T.n_vars * 6);
+  float *z = a.take<float>((size_t)T.n_vars * 6);
+  float *p = a.take<float>((size_t)T.n_vars * 6);
+  float *q = a.take<float>((size_t)T.n_vars * 6);
+  double *energy = a.take<double>((size_t)(n_gn + 1) * T.n_prob * PAIREN);
+  int *assoc = want_assoc ? a.take<int>(HW) : nullptr;
+  if (D) {
+    D->pose = pose;
+    D->pairM = pairM;
+    D->dpart = dpart;
+    D->spart = spart;
+    D->srmax = srmax;
+    D->srarg = srarg;
+    D->pairblk = pairblk;
+    D->pairen = pairen;
+    D->pairoff = pairoff;
+    D->Dd = Dd;
+    D->rhs = rhs;
+    D->Df = Df;
+    D->Minv = Minv;
+    D->vflags = vflags;
+    D->pflags = pflags;
+    D->x = x;
+    D->r = r;
+    D->z = z;
+    D->p = p;
+    D->q = q;
+    D->energy = energy;
+    D->assoc = assoc;
+    // table pointers into ib, in the order of pack_ints
+    int *w = ib;
+    auto nxt = [&](size_t n) {
+      int *r_ = w;
+      w += n;
+      return r_;
+    };
+    Tables &t = D->t;
+    t.n_frames = T.n_frames;
+    t.n_pairs = T.n_pairs;
+    t.n_dp = T.n_dp;
+    t.n_tiles = T.n_tiles;
+    t.n_segs = T.n_segs;
+    t.n_vars = T.n_vars;
+    t.n_prob = T.n_prob;
+    t.frame_slot = nxt(T.frame_slot.size());
+    t.frame_var = nxt(T.frame_var.size());
+    t.pair_a = nxt(T.pair_a.size());
+    t.pair_b = nxt(T.pair_b.size());
+    t.pair_dp = nxt(T.pair_dp.size());
+    t.pair_seg0 = nxt(T.pair_seg0.size());
+    t.pair_seg1 = nxt(T.pair_seg1.size());
+    t.dp_src = nxt(T.dp_src.size());
+    t.dp_dst = nxt(T.dp_dst.size());
+    t.dp_pair = nxt(T.dp_pair.size());
+    t.dp_dir = nxt(T.dp_dir.size());
+    t.dp_tile0 = nxt(T.dp_tile0.size());
+    t.dp_tile1 = nxt(T.dp_tile1.size());
+    t.tile_dp = nxt(T.tile_dp.size());
+    t.tile_px0 = nxt(T.tile_px0.size());
+    t.tile_px1 = nxt(T.tile_px1.size());
+    t.seg_pair = nxt(T.seg_pair.size());
+    t.seg_off = nxt(T.seg_off.size());
+    t.seg_cnt = nxt(T.seg_cnt.size());
+    t.seg_swap = nxt(T.seg_swap.size());
+    t.inc_off = nxt(T.inc_off.size());
+    t.inc = nxt(T.inc.size());
+    t.var_frame = nxt(T.var_frame.size());
+    t.prob_var0 = nxt(T.prob_var0.size());
+    t.prob_var1 = nxt(T.prob_var1.size());
+    t.prob_pair0 = nxt(T.prob_pair0.size());
+    t.prob_pair1 = nxt(T.prob_pair1.size());
+  }
+  return a.off;
+}
+
+std::vector<int> pack_ints(const HostTables &T) {
+  std::vector<int> v;
+  for (const std::vector<int> *x :
+       {&T.frame_slot, &T.frame_var, &T.pair_a, &T.pair_b, &T.pair_dp, &T.pair_seg0, &T.pair_seg1, &T.dp_src,
+        &T.dp_dst, &T.dp_pair, &T.dp_dir, &T.dp_tile0, &T.dp_tile1, &T.tile_dp, &T.tile_px0, &T.tile_px1,
+        &T.seg_pair, &T.seg_off, &T.seg_cnt, &T.seg_swap, &T.inc_off, &T.inc, &T.var_frame, &T.prob_var0,
+        &T.prob_var1, &T.prob_pair0, &T.prob_pair1})
+    v.insert(v.end(), x->begin(), x->end());
+  return v;
+}
+
+bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, bool want_assoc, DevSolve &D) {
+  const std::vector<int> ints = pack_ints(T);
+  const int HW = c->cfg.width * c->cfg.height;
+  const size_t need = layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc) + 256;
+  if (need > c->ws_bytes) {
+    const size_t nb = std::max(need, c->ws_bytes * 3 / 2);
+    CK(cudaStreamSynchronize(c->st), "workspace");
+    dfree(c, c->ws, c->ws_bytes);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+    bf_status s = dalloc(c, (void **)&c->ws, nb, "solve workspace");
+    if (s) return s;
+    c->ws_bytes = nb;
+  }
+  layout(T, n_gn, ints.size(), c->ws, &D, acc_size, HW, want_assoc);
+  if (!ints.empty())
+    CK(cudaMemcpyAsync((void *)D.t.frame_slot, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, c->st),
+       "upload tables");
+  CK(cudaMemcpyAsync(D.pose, T.pose.data(), T.pose.size() * sizeof(double), cudaMemcpyHostToDevice, c->st),
+     "upload poses");
+  if (T.n_prob) CK(cudaMemsetAsync(D.pflags, 0, T.n_prob * sizeof(int), c->st), "pflags");
+  return BF_OK;
+}
+
+// One Gauss-Newton iteration's linearisation: pair transforms, dense + sparse partials, merge.
+template <typename Acc>
+void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, int mode) {
+  const Tables &t = D.t;
+  Gates g;
+  g.tau_d2 = (float)(prm.tau_dist * prm.tau_dist);
+  g.tau_n = (float)prm.tau_normal;
+  launch_pair_xform(t, D.pose, D.pairM, c->st);
+  launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo), (float)(wd * prm.w_photo),
+                    (Acc *)D.dpart, nullptr, c->st);
+  launch_sparse<Acc>(mode, t, c->cP, c->cQ, D.pairM, (float)prm.w_sparse, (Acc *)D.spart, D.srmax, D.srarg, c->st);
+  launch_pair_merge<Acc, Acc>(t, D.pose, (const Acc *)D.dpart, (const Acc *)D.spart, (Acc *)D.pairblk,
+                              (Acc *)D.pairen, D.pairoff, c->st);
+}
+
+double wdense_at(const bf_solve_params &prm, int k) {
+  return prm.dense_ramp ? prm.w_dense * (k + 1) / prm.n_gn : prm.w_dense;
+}
+
+template <typename Acc>
+bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, DevSolve &D) {
+  const Tables &t = D.t;
+  for (int k = 0; k < prm.n_gn; ++k) {
+    const double wd = wdense_at(prm, k);
+    linearise<Acc>(c, D, prm, wd, MODE_ACCUM);
+    launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)k * T.n_prob * PAIREN, c->st);
+    launch_assemble<Acc>(t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv, D.vflags,
+                         c->st);
+    launch_pcg<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.q, prm.n_pcg, D.pflags,
+                    c->st);
+    launch_update(t, D.x, D.pose, c->st);
+  }
+  const double wd = prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense;
+  linearise<Acc>(c, D, prm, wd, MODE_ENERGY);
+  launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)prm.n_gn * T.n_prob * PAIREN, c->st);
+  CK(cudaGetLastError(), "solve launches");
+  return BF_OK;
+}
+
+bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
+  if (!p) return fail(c, BF_ERR_INVALID_ARG, "null solve params");
+  if (p->n_gn < 0 || p->n_gn > BF_MAX_GN || p->n_pcg < 0 || p->n_pcg > 100000)
+    return fail(c, BF_ERR_INVALID_ARG, "n_gn must be in [0, BF_MAX_GN] and n_pcg >= 0");
+  if (p->precision != BF_PREC_MIXED && p->precision != BF_PREC_FP32)
+    return fail(c, BF_ERR_INVALID_ARG, "unknown precision");
+  if (p->precond != BF_PRECOND_BLOCK_JACOBI && p->precond != BF_PRECOND_JACOBI)
+    return fail(c, BF_ERR_INVALID_ARG, "unknown preconditioner");
+  if (!(p->tau_dist > 0) || !std::isfinite(p->tau_normal) || !std::isfinite(p->max_angle_deg))
+    return fail(c, BF_ERR_INVALID_ARG, "bad gates");
+  if (p->tile_px < 0) return fail(c, BF_ERR_INVALID_ARG, "tile_px must be >= 0");
+  return BF_OK;
+}
+
+// Solve a set of problems; writes final poses per problem and stats.
+bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm,
+                         std::vector<std::vector<Pose12>> &out, bf_solve_stats *stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  HostTables T;
+  bf_status s = build_tables(c, probs, prm, T);
+  if (s) return s;
+  const bool mixed = prm.precision == BF_PREC_MIXED;
+  const size_t acc_size = mixed ? sizeof(double) : sizeof(float);
+  DevSolve D;
+  s = prepare(c, T, prm.n_gn, acc_size, false, D);
+  if (s) return s;
+  s = mixed ? run_gn<double>(c, T, prm, D) : run_gn<float>(c, T, prm, D);
+  if (s) return s;
+  std::vector<double> pose(T.pose.size()), energy((size_t)(prm.n_gn + 1) * T.n_prob * PAIREN);
+  std::vector<int> vflags(T.n_vars), pflags(T.n_prob), srarg(T.n_segs);
+  std::vector<float> srmax(T.n_segs);
+  CK(cudaMemcpyAsync(pose.data(), D.pose, pose.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st), "poses");
+  CK(cudaMemcpyAsync(energy.data(), D.energy, energy.size() * sizeof(double), cudaMemcpyDeviceToHost, c->st),
+     "energy");
+  if (T.n_vars)
+    CK(cudaMemcpyAsync(vflags.data(), D.vflags, T.n_vars * sizeof(int), cudaMemcpyDeviceToHost, c->st), "flags");
+  CK(cudaMemcpyAsync(pflags.data(), D.pflags, T.n_prob * sizeof(int), cudaMemcpyDeviceToHost, c->st), "flags");
+  if (T.n_segs) {
+    CK(cudaMemcpyAsync(srmax.data(), D.srmax, T.n_segs * sizeof(float), cudaMemcpyDeviceToHost, c->st), "rmax");
+    CK(cudaMemcpyAsync(srarg.data(), D.srarg, T.n_segs * sizeof(int), cudaMemcpyDeviceToHost, c->st), "rmax");
+  }
+  CK(cudaStreamSynchronize(c->st), "solve");
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  out.assign(T.n_prob, {});
+  for (int pi = 0; pi < T.n_prob; ++pi) {
+    const int F0 = T.prob_frame0[pi];
+    const int n = (int)probs[pi].ids.size();
+    for (int k = 0; k < n; ++k) {
+      Pose12 p;
+      for (int q = 0; q < 12; ++q) p[q] = pose[(size_t)(F0 + k) * 12 + q];
+      out[pi].push_back(p);
+    }
+    if (!stats) continue;
+    bf_solve_stats &S = stats[pi];
+    std::memset(&S, 0, sizeof(S));
+    S.n_gn_done = prm.n_gn;
+    for (int k = 0; k <= prm.n_gn; ++k) {
+      const double *e = &energy[((size_t)k * T.n_prob + pi) * PAIREN];
+      const double wd = k < prm.n_gn ? wdense_at(prm, k) : (prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense);
+      S.e_sparse[k] = e[0];
+      S.e_photo[k] = e[1];
+      S.e_geo[k] = e[2];
+      S.n_dense_valid[k] = (long long)llround(e[3]);
+      S.energy[k] = prm.w_sparse * e[0] + (prm.dense_on ? wd * (prm.w_photo * e[1] + prm.w_geo * e[2]) : 0.0);
+    }
+    S.r_max = -1.0;
+    S.r_max_pair[0] = S.r_max_pair[1] = -1;
+    for (int p = T.prob_pair0[pi]; p < T.prob_pair1[pi]; ++p)
+      for (int sg = T.pair_seg0[p]; sg < T.pair_seg1[p]; ++sg)
+        if (T.seg_cnt[sg] > 0 && (double)srmax[sg] > S.r_max) {
+          S.r_max = srmax[sg];
+          S.r_max_pair[0] = T.pair_ida[p];
+          S.r_max_pair[1] = T.pair_idb[p];
+        }
+    S.n_frames = n;
+    S.n_pairs = T.prob_npairs[pi];
+    S.n_dense_pairs = T.prob_ndense[pi];
+    S.n_corr = T.prob_ncorr[pi];
+    int fl = pflags[pi];
+    for (int v = T.prob_var0[pi]; v < T.prob_var1[pi]; ++v) fl |= vflags[v];
+    S.flags = fl;
+    S.ms = ms;
+  }
+  return BF_OK;
+}
+
+Pose12 world_of(bf_ctx *c, int id) {
+  auto it = c->frames.find(id);
+  if (it == c->frames.end()) return ident12();
+  const FrameInfo &f = it->second;
+  Pose12 w;
+  if (f.keyframe_of >= 0 && f.has_world) {
+    std::memcpy(w.data(), f.world, sizeof(f.world));
+    return w;
+  }
+  if (f.member_of >= 0) {
+    auto ch = c->chunks.find(f.member_of);
+    if (ch != c->chunks.end()) {
+      const Chunk &C = ch->second;
+      for (size_t k = 0; k < C.frames.size(); ++k)
+        if (C.frames[k] == id) return compose(world_of(c, C.frames[0]), C.local[k]);
+    }
+  }
+  if (f.has_world) {
+    std::memcpy(w.data(), f.world, sizeof(f.world));
+    return w;
+  }
+  return ident12();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- local solves
+static bf_status local_batch(bf_ctx *c, int n_chunks, const int *chunk_ids, const int *frame_ids, const int *offsets,
+                             const bf_solve_params *params, bf_solve_stats *stats) {
+  std::vector<Problem> probs(n_chunks);
+  for (int k = 0; k < n_chunks; ++k) {
+    const int n = offsets[k + 1] - offsets[k];
+    if (n < 1) return fail(c, BF_ERR_INVALID_ARG, "local solve: a chunk needs at least one frame");
+    Problem &P = probs[k];
+    P.ids.assign(frame_ids + offsets[k], frame_ids + offsets[k + 1]);
+    P.init.assign(n, ident12());
+    if (params->warm_start) {
+      auto ch = c->chunks.find(chunk_ids[k]);
+      if (ch != c->chunks.end())
+        for (int a = 1; a < n; ++a)
+          for (size_t b = 0; b < ch->second.frames.size(); ++b)
+            if (ch->second.frames[b] == P.ids[a]) P.init[a] = ch->second.local[b];
+    }
+  }
+  std::vector<std::vector<Pose12>> out;
+  bf_status s = solve_problems(c, probs, *params, out, stats);
+  if (s) return s;
+  for (int k = 0; k < n_chunks; ++k) {
+    Chunk &C = c->chunks[chunk_ids[k]];
+    C.frames = probs[k].ids;
+    C.local = out[k];
+    c->frames[C.frames[0]].keyframe_of = chunk_ids[k];
+    for (size_t a = 1; a < C.frames.size(); ++a) c->frames[C.frames[a]].member_of = chunk_ids[k];
+  }
+  return BF_OK;
+}
+
+extern "C" bf_status bf_solve_local(bf_ctx *c, int chunk_id, const int *frame_ids, int n,
+                                    const bf_solve_params *params, bf_solve_stats *stats) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (!frame_ids || n < 1) return fail(c, BF_ERR_INVALID_ARG, "bf_solve_local: bad frame list");
+  bf_status s = check_params(c, params);
+  if (s) return s;
+  const int off[2] = {0, n};
+  return local_batch(c, 1, &chunk_id, frame_ids, off, params, stats);
+}
+
+extern "C" bf_status bf_solve_local_batch(bf_ctx *c, int n_chunks, const int *chunk_ids, const int *frame_ids,
+                                          const int *offsets, const bf_solve_params *params, bf_solve_stats *stats) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (n_chunks < 0 || (n_chunks > 0 && (!chunk_ids || !frame_ids || !offsets)))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_solve_local_batch: bad arguments");
+  if (n_chunks == 0) return BF_OK;
+  bf_status s = check_params(c, params);
+  if (s) return s;
+  if (offsets[0] != 0) return fail(c, BF_ERR_INVALID_ARG, "bf_solve_local_batch: offsets[0] must be 0");
+  return local_batch(c, n_chunks, chunk_ids, frame_ids, offsets, params, stats);
+}
+
+// --------------------------------------------------------------------------- global solve
+extern "C" bf_status bf_solve_global(bf_ctx *c, const int *keyframe_ids, int n, const bf_solve_params *params,
+                                     bf_solve_stats *stats) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (!keyframe_ids || n < 1) return fail(c, BF_ERR_INVALID_ARG, "bf_solve_global: bad keyframe list");
+  bf_status s = check_params(c, params);
+  if (s) return s;
+  Problem P;
+  P.ids.assign(keyframe_ids, keyframe_ids + n);
+  for (int k = 0; k < n; ++k) {
+    auto it = c->frames.find(P.ids[k]);
+    if (it == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_solve_global: unknown keyframe id");
+    Pose12 init;
+    if (it->second.has_world) {
+      std::memcpy(init.data(), it->second.world, sizeof(it->second.world));
+    } else if (k == 0) {
+      init = ident12();
+    } else {
+      // previous keyframe's pose composed with the intra-chunk delta linking them (Sec. 4.2)
+      init = P.init[k - 1];
+      auto pit = c->frames.find(P.ids[k - 1]);
+      if (pit != c->frames.end() && pit->second.keyframe_of >= 0) {
+        auto ch = c->chunks.find(pit->second.keyframe_of);
+        if (ch != c->chunks.end())
+          for (size_t b = 0; b < ch->second.frames.size(); ++b)
+            if (ch->second.frames[b] == P.ids[k]) init = compose(P.init[k - 1], ch->second.local[b]);
+      }
+    }
+    P.init.push_back(init);
+  }
+  std::vector<Problem> probs{P};
+  std::vector<std::vector<Pose12>> out;
+  s = solve_problems(c, probs, *params, out, stats);
+  if (s) return s;
+  for (int k = 0; k < n; ++k) {
+    FrameInfo &f = c->frames[P.ids[k]];
+    std::memcpy(f.world, out[0][k].data(), sizeof(f.world));
+    f.has_world = true;
+  }
+  return BF_OK;
+}
+
+extern "C" bf_status bf_get_poses(bf_ctx *c, const int *frame_ids, int n, double *out) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (n < 0 || (n > 0 && (!frame_ids || !out))) return fail(c, BF_ERR_INVALID_ARG, "bf_get_poses: bad arguments");
+  for (int k = 0; k < n; ++k) {
+    if (!c->frames.count(frame_ids[k])) return fail(c, BF_ERR_NOT_FOUND, "bf_get_poses: unknown frame id");
+    to16(world_of(c, frame_ids[k]), out + 16 * k);
+  }
+  return BF_OK;
+}
+
+// ---------------------------------------------------------------------- system inspection
+template <typename Acc>
+static bf_status build_system_t(bf_ctx *c, const HostTables &T, DevSolve &D, const bf_solve_params &prm, double *A,
+                                double *b, double *energy4, long long *n_dense) {
+  linearise<Acc>(c, D, prm, prm.w_dense, MODE_ACCUM);
+  launch_energy_reduce<Acc>(D.t, (const Acc *)D.pairen, D.energy, c->st);
+  launch_assemble<Acc>(D.t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv, D.vflags,
+                       c->st);
+  CK(cudaGetLastError(), "build system launches");
+  std::vector<Acc> Dd((size_t)T.n_vars * 36), rhs((size_t)T.n_vars * 6), pb((size_t)T.n_pairs * PAIRBLK);
+  double en[PAIREN];
+  if (T.n_vars) {
+    CK(cudaMemcpyAsync(Dd.data(), D.Dd, Dd.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->st), "Dd");
+    CK(cudaMemcpyAsync(rhs.data(), D.rhs, rhs.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->st), "rhs");
+  }
+  if (T.n_pairs) CK(cudaMemcpyAsync(pb.data(), D.pairblk, pb.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->st), "pb");
+  CK(cudaMemcpyAsync(en, D.energy, sizeof(en), cudaMemcpyDeviceToHost, c->st), "energy");
+  CK(cudaStreamSynchronize(c->st), "build system");
+  const int m = 6 * T.n_vars;
+  std::fill(A, A + (size_t)m * m, 0.0);
+  for (int v = 0; v < T.n_vars; ++v) {
+    for (int i = 0; i < 6; ++i) {
+      b[6 * v + i] = (double)rhs[6 * v + i];
+      for (int j = 0; j < 6; ++j) A[(size_t)(6 * v + i) * m + 6 * v + j] = (double)Dd[36 * v + 6 * i + j];
+    }
+  }
+  for (int p = 0; p < T.n_pairs; ++p) {
+    const int va = T.frame_var[T.pair_a[p]], vb = T.frame_var[T.pair_b[p]];
+    if (va < 0 || vb < 0) continue;
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) {
+        const double x = (double)pb[(size_t)p * PAIRBLK + PB_AB + 6 * i + j];
+        A[(size_t)(6 * va + i) * m + 6 * vb + j] += x;
+        A[(size_t)(6 * vb + j) * m + 6 * va + i] += x;
+      }
+  }
+  energy4[1] = en[0];
+  energy4[2] = en[1];
+  energy4[3] = en[2];
+  energy4[0] = prm.w_sparse * en[0] + (prm.dense_on ? prm.w_dense * (prm.w_photo * en[1] + prm.w_geo * en[2]) : 0.0);
+  if (n_dense) *n_dense = (long long)llround(en[3]);
+  return BF_OK;
+}
+
+extern "C" bf_status bf_build_system(bf_ctx *c, const int *frame_ids, int n, const double *poses,
+                                     const bf_solve_params *params, double *A, double *b, double *energy4,
+                                     long long *n_dense) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (!frame_ids || n < 1 || !poses || !A || !b || !energy4)
+    return fail(c, BF_ERR_INVALID_ARG, "bf_build_system: bad arguments");
+  bf_status s = check_params(c, params);
+  if (s) return s;
+  Problem P;
+  P.ids.assign(frame_ids, frame_ids + n);
+  for (int k = 0; k < n; ++k) P.init.push_back(from16(poses + 16 * k));
+  HostTables T;
+  s = build_tables(c, {P}, *params, T);
+  if (s) return s;
+  const bool mixed = params->precision == BF_PREC_MIXED;
+  DevSolve D;
+  s = prepare(c, T, 0, mixed ? 8 : 4, false, D);
+  if (s) return s;
+  return mixed ? build_system_t<double>(c, T, D, *params, A, b, energy4, n_dense)
+               : build_system_t<float>(c, T, D, *params, A, b, energy4, n_dense);
+}
+
+extern "C" bf_status bf_debug_association(bf_ctx *c, int frame_i, int frame_j, const double *pose_i,
+                                          const double *pose_j, const bf_solve_params *params, int32_t *out_target) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (!pose_i || !pose_j || !out_target || frame_i == frame_j)
+    return fail(c, BF_ERR_INVALID_ARG, "bf_debug_association: bad arguments");
+  bf_status s = check_params(c, params);
+  if (s) return s;
+  auto fi = c->frames.find(frame_i), fj = c->frames.find(frame_j);
+  if (fi == c->frames.end() || fj == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "unknown frame id");
+  const int HW = c->cfg.width * c->cfg.height;
+  HostTables T;
+  T.n_frames = 2;
+  T.n_pairs = 1;
+  T.n_dp = 1;
+  T.n_prob = 1;
+  T.frame_slot = {fi->second.slot, fj->second.slot};
+  T.frame_var = {-1, -1};
+  T.pair_a = {0};
+  T.pair_b = {1};
+  T.pair_dp = {0, -1};
+  T.pair_seg0 = {0};
+  T.pair_seg1 = {0};
+  T.dp_src = {0};
+  T.dp_dst = {1};
+  T.dp_pair = {0};
+  T.dp_dir = {0};
+  T.dp_tile0 = {0};
+  const int tile_px = params->tile_px > 0 ? params->tile_px : std::min(HW, 4800);
+  for (int px = 0; px < HW; px += tile_px) {
+    T.tile_dp.push_back(0);
+    T.tile_px0.push_back(px);
+    T.tile_px1.push_back(std::min(HW, px + tile_px));
+    ++T.n_tiles;
+  }
+  T.dp_tile1 = {T.n_tiles};
+  T.n_vars = 0;
+  T.inc_off = {0};
+  T.prob_var0 = {0};
+  T.prob_var1 = {0};
+  T.prob_pair0 = {0};
+  T.prob_pair1 = {1};
+  const Pose12 a = from16(pose_i), b = from16(pose_j);
+  T.pose.assign(a.begin(), a.end());
+  T.pose.insert(T.pose.end(), b.begin(), b.end());
+  DevSolve D;
+  s = prepare(c, T, 0, 4, true, D);
+  if (s) return s;
+  Gates g;
+  g.tau_d2 = (float)(params->tau_dist * params->tau_dist);
+  g.tau_n = (float)params->tau_normal;
+  launch_pair_xform(D.t, D.pose, D.pairM, c->st);
+  launch_dense<float>(MODE_ASSOC, D.t, frame_store(c), c->intr, D.pairM, g, 0.f, 0.f, nullptr, D.assoc, c->st);
+  CK(cudaGetLastError(), "association launch");
+  CK(cudaMemcpyAsync(out_target, D.assoc, HW * sizeof(int), cudaMemcpyDeviceToHost, c->st), "association");
+  CK(cudaStreamSynchronize(c->st), "association");
+  return BF_OK;
+}

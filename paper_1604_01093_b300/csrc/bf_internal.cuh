@@ -1,0 +1,112 @@
+// Internal declarations shared by the library's CUDA translation units.
+//
+// Data layout in HBM (one context):
+//   frame store  A[slot][H*W] float4 = (D, n_x, n_y, n_z)   D = 0 marks invalid depth,
+//                                                            n = 0 marks an invalid normal
+//                B[slot][H*W] float4 = (I, I_x, I_y, 0)      I = |grad L| (Sec. 4.3)
+//   (BF16/FP16 storage packs the same 7 channels into 16 bytes per pixel, see Frames16.)
+//   correspondence pool  P[k] float4 = (p.xyz, w), Q[k] float4 = (q.xyz, 0), p in the camera
+//                of the pair's smaller frame id, q in the larger one's.
+//   per-solve workspace: tables (int32), poses (FP64, 12 per frame: R row-major, t),
+//                per-work-item partial sums, per-pair 6x6 blocks, per-frame blocks, PCG vectors.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace bf {
+
+// ---------------------------------------------------------------------------------------------
+// Partial sums of one work item (a dense tile or a sparse segment), in the coordinates of the
+// pair's target frame.  Every residual row r with weight w has a Jacobian of the form
+// [a, v, c, -v] over (dw_src, dt_src, dw_tgt, dt_tgt) (Sec. 4.3 terms all share it: the
+// translation parts are opposite), so J^T W J needs only six 3x3 sums and J^T W r three
+// 3-vectors.
+// ---------------------------------------------------------------------------------------------
+constexpr int NPART = 57;
+enum : int {
+  P_AA = 0,   // sym 3x3  sum w a a^T   (xx xy xz yy yz zz)
+  P_AV = 6,   // 3x3      sum w a v^T   (row-major)
+  P_VV = 15,  // sym 3x3  sum w v v^T
+  P_AC = 21,  // 3x3      sum w a c^T
+  P_VC = 30,  // 3x3      sum w v c^T
+  P_CC = 39,  // sym 3x3  sum w c c^T
+  P_GA = 45,  // sum w r a
+  P_GV = 48,  // sum w r v
+  P_GC = 51,  // sum w r c
+  P_E0 = 54,  // dense: sum r_geo^2        sparse: sum w_c ||r||^2
+  P_E1 = 55,  // dense: sum r_photo^2      sparse: 0
+  P_CNT = 56  // dense: associated pixels  sparse: correspondences
+};
+// Per-pair block record: A_aa, A_ab, A_bb (row-major 6x6), rhs_a, rhs_b (= -J^T W r).
+constexpr int PAIRBLK = 120;
+constexpr int PB_AA = 0, PB_AB = 36, PB_BB = 72, PB_RA = 108, PB_RB = 114;
+// Per-pair energy record: e_sparse, e_photo, e_geo, n_dense.
+constexpr int PAIREN = 4;
+
+struct Intr {
+  float fx, fy, cx, cy;  // FP32 roundings of the intrinsics
+  int W, H;
+};
+
+// Storage of the preprocessed planes.
+struct FrameStore {
+  int storage;            // BF_STORE_*
+  int W, H;
+  const float4 *A;        // FP32: [slot][HW] (D, n)
+  const float4 *B;        // FP32: [slot][HW] (I, Ix, Iy, 0)
+  const uint4 *P16;       // BF16/FP16: [slot][HW] 8 halves: D(hi,lo as fp32 split), n xyz, I, Ix, Iy
+  const float *kx, *ky;   // kx[x] = fl32((x - cx)/fx), ky[y] = fl32((y - cy)/fy)
+};
+
+// Flattened tables of one (batched) solve, all int32 device pointers.
+struct Tables {
+  int n_frames, n_pairs, n_dp, n_tiles, n_segs, n_vars, n_prob;
+  const int *frame_slot;            // [n_frames]
+  const int *frame_var;             // [n_frames]  var block index, -1 for a gauge frame
+  const int *pair_a, *pair_b;       // [n_pairs]   solve-frame indices, a has the smaller local index
+  const int *pair_dp;               // [n_pairs*2] directed pair a->b, b->a (or -1)
+  const int *pair_seg0, *pair_seg1; // [n_pairs]   segment range
+  const int *dp_src, *dp_dst, *dp_pair, *dp_dir;  // [n_dp]
+  const int *dp_tile0, *dp_tile1;   // [n_dp]      tile range
+  const int *tile_dp, *tile_px0, *tile_px1;       // [n_tiles]
+  const int *seg_pair, *seg_off, *seg_cnt, *seg_swap;  // [n_segs]
+  const int *inc_off, *inc;         // [n_vars+1], entries 2*pair + side (side 0: var is a)
+  const int *var_frame;             // [n_vars]
+  const int *prob_var0, *prob_var1, *prob_pair0, *prob_pair1;  // [n_prob]
+};
+
+struct Gates {
+  float tau_d2;   // fl32(tau_dist^2)
+  float tau_n;    // fl32(tau_normal)
+};
+
+enum { MODE_ACCUM = 0, MODE_ENERGY = 1, MODE_ASSOC = 2 };
+
+// ------------------------------------------------------------------ launch wrappers (host side)
+void launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
+                       float4 *A, float4 *B, uint4 *P16, float dmin, float dmax, cudaStream_t st);
+void launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, int swap, float4 *P, float4 *Q,
+                      cudaStream_t st);
+void launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st);
+template <typename Part>
+void launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
+                  float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st);
+template <typename Part>
+void launch_sparse(int mode, const Tables &t, const float4 *P, const float4 *Q, const float *pairM, float w_sparse,
+                   Part *part, float *seg_rmax, int *seg_rarg, cudaStream_t st);
+template <typename Acc, typename Part>
+void launch_pair_merge(const Tables &t, const double *pose, const Part *dpart, const Part *spart, Acc *pairblk,
+                       Acc *pairen, float *pairoff, cudaStream_t st);
+template <typename Acc>
+void launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, Acc *rhs, float *Df, float *Minv,
+                     int *vflags, cudaStream_t st);
+template <typename Acc>
+void launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
+                float *r, float *z, float *p, float *q, int n_pcg, int *pflags, cudaStream_t st);
+void launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st);
+template <typename Acc>
+void launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st);
+
+}  // namespace bf

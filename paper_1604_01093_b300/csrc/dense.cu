@@ -1,0 +1,207 @@
+// Dense photometric + geometric term: association, residuals, Jacobians and the per-tile
+// reduction of J^T W J and J^T W r (Sec. 4.3 E_photo / E_geo; Sec. 4.4: the dense system
+// matrix is precomputed once per non-linear iteration with local reductions, then only a
+// few scattered writes per pair).
+//
+// Work item = a tile of consecutive source pixels of one directed pair (i -> j).  Every
+// thread walks the tile with a block-sized stride (coalesced source reads), evaluates its
+// pixel entirely in registers and accumulates the 57 partial sums of the pair in FP32; the
+// CTA then reduces them by a fixed-order tree (warp shuffles, then warps in order) and writes
+// one record per tile.  Each run of sequential FP32 additions is at most ceil(tile/blockDim)
+// long; everything above a tile is summed in FP64 (mixed precision) by the pair merge.
+//
+// The association decisions (target pixel, bilinear taps, validity, gates) are computed with
+// explicitly rounded FP32 operations in a fixed order (no contraction), so a CPU restatement in
+// IEEE FP32 takes the same decisions.  Residuals and Jacobians are free FP32 arithmetic.
+//
+// Everything is evaluated in the coordinates of the target camera j with the pair transform
+// M = T_j^-1 T_i (y = R d + t); the merge rotates the sums to world coordinates with R_j.
+#include "bf_internal.cuh"
+
+namespace bf {
+
+#define FM __fmul_rn
+#define FA __fadd_rn
+#define FS __fsub_rn
+
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 cross3(V3 a, V3 b) {
+  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Accumulate one residual row (weight w, residual r, Jacobian [a, v, c, -v]) into acc.
+__device__ __forceinline__ void accum_row(float (&acc)[NPART], float w, float r, V3 a, V3 v, V3 c) {
+  const float wa0 = w * a.x, wa1 = w * a.y, wa2 = w * a.z;
+  const float wv0 = w * v.x, wv1 = w * v.y, wv2 = w * v.z;
+  const float wc0 = w * c.x, wc1 = w * c.y, wc2 = w * c.z;
+  // sym a a^T
+  acc[P_AA + 0] += wa0 * a.x; acc[P_AA + 1] += wa0 * a.y; acc[P_AA + 2] += wa0 * a.z;
+  acc[P_AA + 3] += wa1 * a.y; acc[P_AA + 4] += wa1 * a.z; acc[P_AA + 5] += wa2 * a.z;
+  // a v^T
+  acc[P_AV + 0] += wa0 * v.x; acc[P_AV + 1] += wa0 * v.y; acc[P_AV + 2] += wa0 * v.z;
+  acc[P_AV + 3] += wa1 * v.x; acc[P_AV + 4] += wa1 * v.y; acc[P_AV + 5] += wa1 * v.z;
+  acc[P_AV + 6] += wa2 * v.x; acc[P_AV + 7] += wa2 * v.y; acc[P_AV + 8] += wa2 * v.z;
+  // sym v v^T
+  acc[P_VV + 0] += wv0 * v.x; acc[P_VV + 1] += wv0 * v.y; acc[P_VV + 2] += wv0 * v.z;
+  acc[P_VV + 3] += wv1 * v.y; acc[P_VV + 4] += wv1 * v.z; acc[P_VV + 5] += wv2 * v.z;
+  // a c^T
+  acc[P_AC + 0] += wa0 * c.x; acc[P_AC + 1] += wa0 * c.y; acc[P_AC + 2] += wa0 * c.z;
+  acc[P_AC + 3] += wa1 * c.x; acc[P_AC + 4] += wa1 * c.y; acc[P_AC + 5] += wa1 * c.z;
+  acc[P_AC + 6] += wa2 * c.x; acc[P_AC + 7] += wa2 * c.y; acc[P_AC + 8] += wa2 * c.z;
+  // v c^T
+  acc[P_VC + 0] += wv0 * c.x; acc[P_VC + 1] += wv0 * c.y; acc[P_VC + 2] += wv0 * c.z;
+  acc[P_VC + 3] += wv1 * c.x; acc[P_VC + 4] += wv1 * c.y; acc[P_VC + 5] += wv1 * c.z;
+  acc[P_VC + 6] += wv2 * c.x; acc[P_VC + 7] += wv2 * c.y; acc[P_VC + 8] += wv2 * c.z;
+  // sym c c^T
+  acc[P_CC + 0] += wc0 * c.x; acc[P_CC + 1] += wc0 * c.y; acc[P_CC + 2] += wc0 * c.z;
+  acc[P_CC + 3] += wc1 * c.y; acc[P_CC + 4] += wc1 * c.z; acc[P_CC + 5] += wc2 * c.z;
+  // J^T W r
+  acc[P_GA + 0] += r * wa0; acc[P_GA + 1] += r * wa1; acc[P_GA + 2] += r * wa2;
+  acc[P_GV + 0] += r * wv0; acc[P_GV + 1] += r * wv1; acc[P_GV + 2] += r * wv2;
+  acc[P_GC + 0] += r * wc0; acc[P_GC + 1] += r * wc1; acc[P_GC + 2] += r * wc2;
+}
+
+// Fixed-order CTA reduction of NPART values; thread k < NPART writes out[k].
+template <int BS, typename Part>
+__device__ __forceinline__ void cta_reduce_store(float (&acc)[NPART], Part *__restrict__ out) {
+  constexpr int NW = BS / 32;
+  __shared__ float red[NW][NPART];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NPART; ++k) {
+    float v = acc[k];
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NPART) {
+    Part s = (Part)red[0][threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s += (Part)red[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+constexpr int DENSE_BS = 256;
+
+template <int MODE, typename Part>
+__global__ void __launch_bounds__(DENSE_BS, 2)
+    k_dense(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo, float w_photo,
+            Part *__restrict__ part, int *__restrict__ assoc) {
+  const int tile = blockIdx.x;
+  const int d = t.tile_dp[tile];
+  const int px0 = t.tile_px0[tile], px1 = t.tile_px1[tile];
+  const int W = in.W, H = in.H;
+  const long long HW = (long long)W * H;
+  const float4 *__restrict__ As = fs.A + (long long)t.frame_slot[t.dp_src[d]] * HW;
+  const float4 *__restrict__ Bs = fs.B + (long long)t.frame_slot[t.dp_src[d]] * HW;
+  const float4 *__restrict__ At = fs.A + (long long)t.frame_slot[t.dp_dst[d]] * HW;
+  const float4 *__restrict__ Bt = fs.B + (long long)t.frame_slot[t.dp_dst[d]] * HW;
+  const float *M = pairM + (t.dp_pair[d] * 2 + t.dp_dir[d]) * 12;
+  const float R00 = M[0], R01 = M[1], R02 = M[2], R10 = M[3], R11 = M[4], R12 = M[5];
+  const float R20 = M[6], R21 = M[7], R22 = M[8], t0 = M[9], t1 = M[10], t2 = M[11];
+  const float fx = in.fx, fy = in.fy, cx = in.cx, cy = in.cy;
+  const float Wm1 = (float)(W - 1), Hm1 = (float)(H - 1), Wm3 = (float)(W - 3), Hm3 = (float)(H - 3);
+
+  float acc[NPART];
+#pragma unroll
+  for (int k = 0; k < NPART; ++k) acc[k] = 0.f;
+
+  for (int px = px0 + threadIdx.x; px < px1; px += DENSE_BS) {
+    int tgt = -1;
+    const float4 a = As[px];
+    const bool nvalid = (a.y != 0.f) || (a.z != 0.f) || (a.w != 0.f);
+    if (a.x > 0.f && nvalid) {
+      const int y = px / W, x = px - y * W;
+      const float z = a.x;
+      // ---- association decisions, explicitly rounded FP32 in a fixed order ----
+      const float dx = FM(fs.kx[x], z), dy = FM(fs.ky[y], z), dz = z;
+      const float Y0 = FA(FA(FA(FM(R00, dx), FM(R01, dy)), FM(R02, dz)), t0);
+      const float Y1 = FA(FA(FA(FM(R10, dx), FM(R11, dy)), FM(R12, dz)), t1);
+      const float Y2 = FA(FA(FA(FM(R20, dx), FM(R21, dy)), FM(R22, dz)), t2);
+      if (Y2 > 0.f) {
+        const float ux = FA(FM(fx, __fdiv_rn(Y0, Y2)), cx);
+        const float uy = FA(FM(fy, __fdiv_rn(Y1, Y2)), cy);
+        const float nxf = floorf(FA(ux, 0.5f)), nyf = floorf(FA(uy, 0.5f));
+        const float bxf = floorf(ux), byf = floorf(uy);
+        if (nxf >= 0.f && nxf <= Wm1 && nyf >= 0.f && nyf <= Hm1 && bxf >= 2.f && FA(bxf, 1.f) <= Wm3 &&
+            byf >= 2.f && FA(byf, 1.f) <= Hm3) {
+          const int tx = (int)nxf, ty = (int)nyf;
+          const int tpx = ty * W + tx;
+          const float4 b = At[tpx];
+          const bool tnvalid = (b.y != 0.f) || (b.z != 0.f) || (b.w != 0.f);
+          if (b.x > 0.f && tnvalid) {
+            const float qx = FM(fs.kx[tx], b.x), qy = FM(fs.ky[ty], b.x), qz = b.x;
+            const float ex = FS(Y0, qx), ey = FS(Y1, qy), ez = FS(Y2, qz);
+            const float dist2 = FA(FA(FM(ex, ex), FM(ey, ey)), FM(ez, ez));
+            const float m0 = FA(FA(FM(R00, a.y), FM(R01, a.z)), FM(R02, a.w));
+            const float m1 = FA(FA(FM(R10, a.y), FM(R11, a.z)), FM(R12, a.w));
+            const float m2 = FA(FA(FM(R20, a.y), FM(R21, a.z)), FM(R22, a.w));
+            const float ndot = FA(FA(FM(m0, b.y), FM(m1, b.z)), FM(m2, b.w));
+            if (dist2 < g.tau_d2 && ndot > g.tau_n) {
+              tgt = tpx;
+              if (MODE != MODE_ASSOC) {
+                // ---- residuals and Jacobians (free FP32) in camera-j coordinates ----
+                const V3 m{m0, m1, m2}, e{ex, ey, ez}, q{qx, qy, qz}, Yv{Y0, Y1, Y2};
+                const V3 Rd{Y0 - t0, Y1 - t1, Y2 - t2};  // R_ji d
+                const float r_g = m0 * ex + m1 * ey + m2 * ez;
+                // bilinear taps of (I, Ix, Iy)
+                const int bx = (int)bxf, by = (int)byf;
+                const float wx = ux - bxf, wy = uy - byf;
+                const float4 c00 = Bt[by * W + bx], c01 = Bt[by * W + bx + 1];
+                const float4 c10 = Bt[(by + 1) * W + bx], c11 = Bt[(by + 1) * W + bx + 1];
+                const float w00 = (1.f - wx) * (1.f - wy), w01 = wx * (1.f - wy);
+                const float w10 = (1.f - wx) * wy, w11 = wx * wy;
+                const float Ij = w00 * c00.x + w01 * c01.x + w10 * c10.x + w11 * c11.x;
+                const float gxI = w00 * c00.y + w01 * c01.y + w10 * c10.y + w11 * c11.y;
+                const float gyI = w00 * c00.z + w01 * c01.z + w10 * c10.z + w11 * c11.z;
+                const float r_p = Bs[px].x - Ij;
+                acc[P_E0] += r_g * r_g;
+                acc[P_E1] += r_p * r_p;
+                acc[P_CNT] += 1.f;
+                if (MODE == MODE_ACCUM) {
+                  // geometric: v = m, a = m x e + (R d) x m, c = m x q
+                  const V3 mxe = cross3(m, e), rdxm = cross3(Rd, m);
+                  const V3 ag{mxe.x + rdxm.x, mxe.y + rdxm.y, mxe.z + rdxm.z};
+                  accum_row(acc, w_geo, r_g, ag, m, cross3(m, q));
+                  // photometric: g = d r_p / d y = -grad I^T Jpi(y); v = g, a = (R d) x g, c = g x y
+                  const float iz = 1.f / Y2;
+                  const float gfx = gxI * fx * iz, gfy = gyI * fy * iz;
+                  const V3 gv{-gfx, -gfy, (gfx * Y0 + gfy * Y1) * iz};
+                  accum_row(acc, w_photo, r_p, cross3(Rd, gv), gv, cross3(gv, Yv));
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+    if (MODE == MODE_ASSOC) assoc[px] = tgt;
+  }
+  if (MODE != MODE_ASSOC) cta_reduce_store<DENSE_BS, Part>(acc, part + (long long)tile * NPART);
+}
+
+template <typename Part>
+void launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
+                  float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st) {
+  if (t.n_tiles == 0) return;
+  if (mode == MODE_ACCUM)
+    k_dense<MODE_ACCUM, Part><<<t.n_tiles, DENSE_BS, 0, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+  else if (mode == MODE_ENERGY)
+    k_dense<MODE_ENERGY, Part><<<t.n_tiles, DENSE_BS, 0, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+  else
+    k_dense<MODE_ASSOC, Part><<<t.n_tiles, DENSE_BS, 0, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+}
+
+template void launch_dense<float>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
+                                  float, float *, int *, cudaStream_t);
+template void launch_dense<double>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
+                                   float, double *, int *, cudaStream_t);
+
+}  // namespace bf

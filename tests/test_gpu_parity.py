@@ -1,0 +1,283 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+Tolerances (spec numbers, and ones derived from the FP32 evaluation):
+* final poses: rotation <= 1e-4 rad, translation <= 1e-5 m;
+* per-iteration energy: relative error <= 1e-5;
+* association decisions are taken in FP32 with the same operation order on both sides,
+  so target pixels agree exactly except where the normal gate sits within FP32 rounding
+  of tau_n (the two sides round their normals independently);
+* assembled normal equations: FP32 per-pixel evaluation with FP64 merging, so entries
+  agree to ~1e-6 of the block's scale; tested at 2e-5 of the largest entry of A (b: of
+  the largest entry of b).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import association, frames as ofr, lie, solver, system
+from oracle.system import SolveParams
+
+pytestmark = pytest.mark.gpu
+
+ROT_TOL = 1e-4
+TRANS_TOL = 1e-5
+ENERGY_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1604_01093_b300 as bf
+    return bf
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return synth.cfg1()
+
+
+@pytest.fixture(scope="module")
+def cfg1_frames(cfg1):
+    return [ofr.Frame(cfg1.depth[k], cfg1.lum[k], cfg1.intr) for k in range(cfg1.n_frames)]
+
+
+def make_ctx(bf, prob, **kw):
+    intr = prob.intr
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], **kw)
+    ctx.add_frames(0, prob.depth, prob.lum, init_pose=prob.init)
+    for k, (i, j) in enumerate(prob.pairs):
+        p, q = prob.pair_corr(k)
+        ctx.add_correspondences(int(i), int(j), p, q)
+    return ctx
+
+
+def oracle_params(d):
+    return SolveParams(n_gn=d["n_gn"], n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"],
+                       w_photo=d["w_photo"], w_geo=d["w_geo"])
+
+
+def perturb(poses, seed, rot=0.01, trans=0.02):
+    rng = np.random.default_rng(seed)
+    out = poses.copy()
+    for k in range(1, len(out)):
+        R, t = lie.apply_update(out[k][:3, :3], out[k][:3, 3], np.r_[rng.normal(0, rot, 3), rng.normal(0, trans, 3)])
+        out[k] = lie.to44(R, t)
+    return out
+
+
+# ----------------------------------------------------------------------------- preprocessing
+
+def test_preprocess_matches_oracle(bf, cfg1, cfg1_frames):
+    ctx = make_ctx(bf, cfg1)
+    for k in (0, 5, 10):
+        P = ctx.frame_planes(k)
+        f = cfg1_frames[k]
+        np.testing.assert_array_equal(P[0] > 0, f.valid)
+        np.testing.assert_array_equal(P[0][f.valid], cfg1.depth[k][f.valid])
+        nvalid = np.any(P[1:4] != 0, axis=0)
+        np.testing.assert_array_equal(nvalid, f.nvalid)
+        np.testing.assert_allclose(np.moveaxis(P[1:4], 0, -1)[f.nvalid], f.N[f.nvalid], atol=2e-5)
+        np.testing.assert_allclose(P[4], f.I, atol=2e-6)
+        np.testing.assert_allclose(P[5], f.Ix, atol=2e-6)
+        np.testing.assert_allclose(P[6], f.Iy, atol=2e-6)
+
+
+# ------------------------------------------------------------------------------- association
+
+@pytest.mark.parametrize("pair", [(0, 1), (3, 0), (2, 9), (10, 4)])
+def test_association_decisions_match(bf, cfg1, cfg1_frames, pair):
+    ctx = make_ctx(bf, cfg1)
+    i, j = pair
+    for poses in (cfg1.gt, perturb(cfg1.gt, 3), perturb(cfg1.gt, 4, 0.03, 0.05)):
+        gpu = ctx.association(i, j, poses[i], poses[j])
+        M = association.pair_transform32(poses[i][:3, :3], poses[i][:3, 3], poses[j][:3, :3], poses[j][:3, 3])
+        a = association.associate(cfg1_frames[i], cfg1_frames[j], M, cfg1.intr)
+        ref = np.where(a["valid"], a["ny"] * cfg1.intr["W"] + a["nx"], -1)
+        mism = np.flatnonzero(gpu != ref)
+        assert (ref >= 0).sum() > 1000
+        assert len(mism) <= max(2, int(1e-3 * (ref >= 0).sum())), (len(mism), mism[:10])
+
+
+# ----------------------------------------------------------------------- normal equations
+
+WEIGHTS = {
+    "sparse_only": dict(w_sparse=1.0, w_dense=0.0, dense_on=0),
+    "geo_only": dict(w_sparse=0.0, w_dense=1.0, w_photo=0.0, w_geo=1.0),
+    "photo_only": dict(w_sparse=0.0, w_dense=1.0, w_photo=1.0, w_geo=0.0),
+    "full": dict(w_sparse=1.0, w_dense=0.5, w_photo=0.1, w_geo=1.0),
+}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("wname", list(WEIGHTS))
+def test_build_system_matches_oracle(bf, cfg1, cfg1_frames, wname, precision):
+    w = WEIGHTS[wname]
+    ctx = make_ctx(bf, cfg1)
+    poses = perturb(cfg1.gt, 11)
+    ids = list(range(cfg1.n_frames))
+    g = ctx.build_system(ids, poses, precision=precision, **w)
+    op = SolveParams(w_sparse=w["w_sparse"], w_dense=w["w_dense"], w_photo=w.get("w_photo", 0.1),
+                     w_geo=w.get("w_geo", 1.0), dense_on=bool(w.get("dense_on", 1)))
+    sp = solver.sparse_pairs_for(cfg1, ids)
+    dp = system.dense_pair_set(poses, sp, op.max_angle_deg) if op.dense_on else []
+    S = system.assemble(cfg1_frames, cfg1.intr, poses, sp, dp, op, op.w_dense)
+    tol = 2e-5 if precision == 0 else 2e-4
+    assert abs(g["n_dense"] - S.n_dense) <= max(2, 1e-4 * S.n_dense)
+    np.testing.assert_allclose(g["A"], S.A, rtol=0, atol=tol * np.abs(S.A).max())
+    np.testing.assert_allclose(g["b"], S.b, rtol=0, atol=tol * np.abs(S.b).max())
+    assert abs(g["energy"] - S.energy) <= (ENERGY_RTOL if precision == 0 else 1e-4) * S.energy
+
+
+def test_ragged_tiles_give_the_same_system(bf, cfg1, cfg1_frames):
+    """Tiles of 1100 px split 4800-px frames into 4 full tiles and a ragged 400-px tail."""
+    ctx = make_ctx(bf, cfg1)
+    poses = perturb(cfg1.gt, 12)
+    ids = list(range(cfg1.n_frames))
+    a = ctx.build_system(ids, poses, tile_px=1100)
+    b = ctx.build_system(ids, poses, tile_px=4800)
+    c = ctx.build_system(ids, poses, tile_px=97)
+    for x in (a, c):
+        np.testing.assert_allclose(x["A"], b["A"], rtol=0, atol=1e-5 * np.abs(b["A"]).max())
+        assert x["n_dense"] == b["n_dense"]
+
+
+# ------------------------------------------------------------------------------ full solves
+
+def compare_solve(res_gpu, poses_gpu, res_or, label):
+    e_g = np.array(res_gpu["energy"])
+    e_o = np.array(res_or.energy)
+    rel = np.abs(e_g - e_o) / np.abs(e_o)
+    assert rel.max() <= ENERGY_RTOL, (label, rel)
+    for k in range(len(poses_gpu)):
+        rot, tr = lie.pose_error(poses_gpu[k], res_or.poses[k])
+        assert rot <= ROT_TOL and tr <= TRANS_TOL, (label, k, rot, tr)
+
+
+@pytest.fixture(scope="module")
+def cfg1_oracle(cfg1, cfg1_frames):
+    prm = oracle_params(cfg1.solve)
+    return solver.gauss_newton(cfg1_frames, cfg1.intr, cfg1.init, solver.sparse_pairs_for(cfg1, range(11)), prm)
+
+
+def test_local_solve_matches_oracle(bf, cfg1, cfg1_oracle):
+    ctx = make_ctx(bf, cfg1)
+    st = ctx.solve_local(0, list(range(11)), **{k: v for k, v in cfg1.solve.items()})
+    poses = ctx.get_poses(list(range(11)))
+    compare_solve(st, poses, cfg1_oracle, "cfg1 mixed")
+    assert st["r_max_pair"] == tuple(cfg1_oracle.r_max_pair) or abs(st["r_max"] - cfg1_oracle.r_max) < 1e-6
+    assert abs(st["r_max"] - cfg1_oracle.r_max) <= 1e-5 * cfg1_oracle.r_max
+    assert st["n_dense"][0] == cfg1_oracle.n_dense[0] or abs(st["n_dense"][0] - cfg1_oracle.n_dense[0]) <= 2
+
+
+def test_local_solve_fp32_path_close_to_oracle(bf, cfg1, cfg1_oracle):
+    """The plain FP32 path: same algorithm, FP32 merges and PCG scalars."""
+    ctx = make_ctx(bf, cfg1)
+    st = ctx.solve_local(0, list(range(11)), precision=1, **{k: v for k, v in cfg1.solve.items()})
+    poses = ctx.get_poses(list(range(11)))
+    for k in range(11):
+        rot, tr = lie.pose_error(poses[k], cfg1_oracle.poses[k])
+        assert rot <= ROT_TOL and tr <= 1e-4
+    rel = np.abs(np.array(st["energy"]) - cfg1_oracle.energy) / np.array(cfg1_oracle.energy)
+    assert rel.max() <= 1e-4
+
+
+@pytest.mark.parametrize("seed,n", [(5, 3), (6, 7)])
+def test_short_chunks_match_oracle(bf, seed, n):
+    prob = synth.chunk_problem(seed, n, 80, 60, (50, 120), name=f"chunk{n}")
+    fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in range(n)]
+    prm = SolveParams(n_gn=3, n_pcg=8, w_dense=0.5)
+    ref = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm)
+    ctx = make_ctx(bf, prob)
+    st = ctx.solve_local(7, list(range(n)), n_gn=3, n_pcg=8, w_dense=0.5)
+    compare_solve(st, ctx.get_poses(list(range(n))), ref, f"chunk{n}")
+
+
+def test_batched_equals_alone(bf):
+    """Each chunk's result is identical alone and inside a batch (deterministic reductions)."""
+    prob = synth.chunk_batch(31, n_chunks=5, W=80, H=60, length=(3, 8), n_corr=(40, 80))
+    ctx = make_ctx(bf, prob)
+    ids = [c.tolist() for c in prob.chunks]
+    batch = ctx.solve_local_batch(list(range(100, 105)), ids, n_gn=3, n_pcg=6)
+    pb = [ctx.get_poses(c) for c in ids]
+    for k, c in enumerate(ids):
+        st = ctx.solve_local(200 + k, c, n_gn=3, n_pcg=6)
+        np.testing.assert_array_equal(ctx.get_poses(c), pb[k])
+        assert st["energy"] == batch[k]["energy"]
+
+
+@pytest.fixture(scope="module")
+def small_global():
+    return synth.global_problem(77, n_kf=48, outer=(12.0, 2.8, 9.0), inner=(6.0, 3.0), n_corr=(40, 100),
+                                name="global48")
+
+
+def test_global_solve_matches_oracle(bf, small_global):
+    prob = small_global
+    n = prob.n_frames
+    fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in range(n)]
+    prm = SolveParams(n_gn=4, n_pcg=20, w_dense=0.5)
+    ref = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm)
+    ctx = make_ctx(bf, prob)
+    st = ctx.solve_global(list(range(n)), n_gn=4, n_pcg=20, w_dense=0.5)
+    compare_solve(st, ctx.get_poses(list(range(n))), ref, "global48")
+    assert st["n_pairs"] == len(prob.pairs)
+
+
+# ------------------------------------------------------------------------- hierarchy, edges
+
+def test_keyframe_composition(bf):
+    """Sec. 4.2: chunk members' world poses are the keyframe's global pose composed with the local pose."""
+    prob = synth.chunk_batch(41, n_chunks=2, W=80, H=60, length=(4, 4), n_corr=(60, 60))
+    ctx = make_ctx(bf, prob)
+    c0, c1 = prob.chunks
+    ctx.solve_local(0, c0.tolist(), n_gn=2, n_pcg=6)
+    loc = ctx.get_poses(c0.tolist())
+    np.testing.assert_allclose(loc[0], np.eye(4), atol=0)
+    G = np.eye(4)
+    G[:3, 3] = [1.0, 2.0, 3.0]
+    ctx.add_frames(int(c0[0]), prob.depth[c0[:1]], prob.lum[c0[:1]], init_pose=G[None])
+    world = ctx.get_poses(c0.tolist())
+    for k in range(len(c0)):
+        np.testing.assert_allclose(world[k], G @ loc[k], atol=1e-12)
+
+
+def test_frame_without_constraints_stays_fixed(bf, cfg1):
+    ctx = make_ctx(bf, cfg1)
+    ctx.add_frames(50, cfg1.depth[:1], cfg1.lum[:1])
+    st = ctx.solve_local(1, [0, 1, 2, 50], n_gn=2, n_pcg=5, dense_on=0)
+    assert st["flags"] & bf.BF_FLAG_EMPTY_FRAME
+    np.testing.assert_allclose(ctx.get_poses([50])[0], np.eye(4), atol=0)
+
+
+def test_invalid_arguments(bf, cfg1):
+    ctx = make_ctx(bf, cfg1)
+    with pytest.raises(bf.BFError) as e:
+        ctx.solve_local(0, [0, 999], n_gn=1)
+    assert e.value.status == 4
+    with pytest.raises(bf.BFError) as e:
+        ctx.add_correspondences(3, 3, np.zeros((2, 3)), np.zeros((2, 3)))
+    assert e.value.status == 1
+    with pytest.raises(bf.BFError) as e:
+        ctx.solve_local(0, [0, 1, 1], n_gn=1)
+    assert e.value.status == 1
+    with pytest.raises(bf.BFError) as e:
+        ctx.solve_local(0, [0, 1], n_gn=bf._lib.BF_MAX_GN + 1)
+    assert e.value.status == 1
+
+
+def test_single_frame_and_empty_solves(bf, cfg1):
+    ctx = make_ctx(bf, cfg1)
+    st = ctx.solve_local(0, [3], n_gn=2)
+    assert st["n_pairs"] == 0 and st["energy"] == [0.0, 0.0, 0.0]
+    np.testing.assert_allclose(ctx.get_poses([3])[0], np.eye(4))
+    st = ctx.solve_local(0, [0, 1], n_gn=0)
+    assert len(st["energy"]) == 1
+
+
+def test_hbm_budget_refuses(bf, cfg1):
+    intr = cfg1.intr
+    ctx = bf.Context(intr["W"], intr["H"], hbm_budget_bytes=200_000, max_frames_hint=4)
+    with pytest.raises(bf.BFError) as e:
+        ctx.add_frames(0, cfg1.depth, cfg1.lum)
+    assert e.value.status == 2
