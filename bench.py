@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the global pose alignment solve (BundleFusion Sec. 4.2-4.4) on B300.
+
+Workload (default): the global solve over 300 keyframes at 80x60 along a ~60 m loop of a
+synthetic ring corridor, pairs with ground-truth overlap > 30 %, 64-256 correspondences
+per pair (sigma 1 cm, 5 % outliers), dense weight 0.5, 8 Gauss-Newton x 20 PCG
+iterations.  One step = the whole hot path once: frame preprocessing from device-resident
+raw depth/luminance, pair-set construction, 8 linearisations (dense + sparse terms,
+block reduction, assembly), 8 x 20 PCG iterations and pose updates, final energy and r_max.
+
+Metric: Gauss-Newton iterations per second (whole job over all ranks).  Extra fields:
+the plain FP32 one-solve-per-launch path on the same workload, chunk-solve latency
+p50/p99 (single 11-frame 80x60 chunks, optimised vs plain path), the roofline of the
+dominant kernel (dense term) and the FP64 oracle timed on the host cores.
+
+Under torchrun (N > 1) every rank solves its own replica (the global solve does not
+shard; chunk solves would): scaling "weak", no collective on the data path, the step
+time is the max over ranks.
+"""
+import argparse
+import json
+import os
+
+# the FP64 oracle leg runs on one BLAS thread (set before numpy loads its BLAS)
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+os.environ.setdefault("MKL_NUM_THREADS", "1")
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GN iterations/sec + chunk-solve p50/p99 latency vs plain GPU path; HBM GB/s frac"
+UNIT = "GN iterations/s"
+DENSE_BYTES_PER_PX = 48  # FP32: source D, n, I (20 B) + target D, n nearest (16 B) + I, grad I bilinear (12 B)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
+    ap.add_argument("--no-extras", action="store_true", help="skip plain-path, latency and CPU-baseline legs")
+    ap.add_argument("--profile-run", action="store_true", help="short run for ncu: no extras, no clocks")
+    return ap.parse_args()
+
+
+def workload():
+    import synth
+    prob = synth.cfg2()
+    prm = prob.solve
+    return prob, prm
+
+
+# ------------------------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------- CPU baseline
+def oracle_gn_iteration_rate(prob, prm, budget_s=15.0, max_pairs=None):
+    """Time the FP64 oracle's Gauss-Newton iteration on a bounded sample of pairs and scale.
+
+    The sample is the first k pairs (in pair order) with all their frames; assemble time is
+    scaled by n_pairs / k, the PCG over the full explicit system is timed as is.  Single
+    BLAS thread.  Returns (GN iterations/s, description, cores)."""
+    from oracle import frames as ofr, solver, system
+    from oracle.system import SolveParams
+
+    P = SolveParams(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"], w_dense=prm["w_dense"],
+                    w_photo=prm["w_photo"], w_geo=prm["w_geo"])
+    n = prob.n_frames
+    sp_all = solver.sparse_pairs_for(prob, range(n))
+    cache = {}
+    t0 = time.perf_counter()
+    done = 0
+    t_assemble = 0.0
+    for sp in sp_all:
+        if max_pairs is not None and done >= max_pairs:
+            break
+        if time.perf_counter() - t0 > budget_s:
+            break
+        ts = time.perf_counter()
+        for f in (sp.a, sp.b):
+            if f not in cache:
+                cache[f] = ofr.Frame(prob.depth[f], prob.lum[f], prob.intr)
+        fr = [cache.get(k) for k in range(n)]
+        dp = system.dense_pair_set(prob.init, [sp], P.max_angle_deg)
+        system.assemble(fr, prob.intr, prob.init, [sp], dp, P, P.w_dense)
+        t_assemble += time.perf_counter() - ts
+        done += 1
+    m = 6 * (n - 1)
+    rng = np.random.default_rng(0)
+    B = rng.normal(size=(m, m))
+    A = B @ B.T + m * np.eye(m)
+    b = rng.normal(size=m)
+    ts = time.perf_counter()
+    Minv, _ = solver.block_jacobi_inverse(A, "block")
+    solver.pcg(A, b, Minv, P.n_pcg)
+    t_pcg = time.perf_counter() - ts
+    per_iter = t_assemble * (len(sp_all) / max(done, 1)) + t_pcg
+    desc = (f"oracle GN iteration: system assembly over {done} of {len(sp_all)} pairs (dense both directions "
+            f"+ sparse) timed and scaled to all pairs, plus block-Jacobi PCG ({P.n_pcg} it.) over the full "
+            f"{m}x{m} system; numpy, 1 BLAS thread")
+    return 1.0 / per_iter, desc, 1
+
+
+# ------------------------------------------------------------------------------ reference
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    prob, prm = workload()
+    vals = []
+    desc = ""
+    for k in range(args.warmup + args.steps):
+        v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=4.0)
+        if k >= args.warmup:
+            vals.append(v)
+    value = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * prm["n_gn"] / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": prob.name, "keyframes": prob.n_frames,
+                                            "pairs": int(len(prob.pairs)), "n_gn": prm["n_gn"],
+                                            "n_pcg": prm["n_pcg"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import paper_1604_01093_b300 as bf
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    prob, prm = workload()
+    intr = prob.intr
+    n = prob.n_frames
+    ids = list(range(n))
+    precision = bf.BF_PREC_MIXED if args.precision == "mixed" else bf.BF_PREC_FP32
+    params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
+                               w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
+                               precision=precision)
+    stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
+    torch.cuda.set_stream(stream)
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
+                     stream=stream.cuda_stream, max_frames_hint=n)
+    depth_d = torch.from_numpy(prob.depth).to(dev)
+    lum_d = torch.from_numpy(prob.lum).to(dev)
+    pi_d = torch.from_numpy(prob.p_i).to(dev)
+    pj_d = torch.from_numpy(prob.p_j).to(dev)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_d, pj_d)
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
+
+    def step(p=params):
+        ctx.add_frames(0, depth_d, lum_d, init_pose=prob.init)
+        return ctx.solve_global(ids, p)
+
+    def timed(fn, k, profile=False):
+        times = []
+        if profile:
+            ctx.reset_profile()
+            ctx.set_profiling(True)
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        prof = None
+        if profile:
+            prof = ctx.profile()
+            ctx.set_profiling(False)
+        return times, out, prof
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize(dev)
+    clocks = None if args.profile_run else Clocks(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+    t_wall = time.perf_counter()
+    times, st, prof = timed(step, args.steps, profile=True)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop() if clocks else None
+    total_ms = sum(times)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    n_gn = prm["n_gn"]
+    value = n_gn * args.steps * world / (total_ms / 1000.0)
+    if args.profile_run:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "value": value, "ms_per_step": total_ms / args.steps}))
+        return
+
+    # roofline of the dominant kernel (dense term): algorithmic bytes per launch / event-timed duration
+    n_dp = 2 * st["n_dense_pairs"]
+    HW = intr["W"] * intr["H"]
+    dense = prof["kernels"]["dense"]
+    dense_ms = dense["ms"] / max(dense["count"], 1)
+    alg_bytes = DENSE_BYTES_PER_PX * n_dp * HW
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    achieved = alg_bytes / (dense_ms / 1000.0) / 1e9
+    gpu_launches = prof["launches"]
+    kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in prof["kernels"].values()), 1e-9), 4)
+                    for k, v in prof["kernels"].items() if v["count"]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": prob.name, "keyframes": n, "resolution": f"{intr['W']}x{intr['H']}",
+                       "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"],
+                       "directed_dense_pairs": n_dp, "correspondences": prob.n_corr, "n_gn": n_gn,
+                       "n_pcg": prm["n_pcg"], "precision": args.precision,
+                       "l2": "256 MB buffer written between timed steps (inputs < L2)",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": gpu_launches,
+            "roofline": {"bound": "hbm", "kernel": "k_dense", "achieved": achieved, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                         "avg_launch_ms": dense_ms, "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "kernel_time_share": kernel_share,
+            "final_energy": st["energy"][-1], "initial_energy": st["energy"][0]}
+    if clk:
+        line["clocks"] = clk
+
+    if not args.no_extras and rank == 0:
+        # e2e through the public API with host (pinned) buffers
+        depth_h = torch.from_numpy(prob.depth).pin_memory()
+        lum_h = torch.from_numpy(prob.lum).pin_memory()
+        pi_h = torch.from_numpy(prob.p_i).pin_memory()
+        pj_h = torch.from_numpy(prob.p_j).pin_memory()
+
+        def step_e2e():
+            ctx.add_frames(0, depth_h, lum_h, init_pose=prob.init)
+            ctx.clear_correspondences()
+            ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_h, pj_h)
+            s = ctx.solve_global(ids, params)
+            ctx.get_poses(ids)
+            return s
+
+        for _ in range(2):
+            step_e2e()
+        te, _, _ = timed(step_e2e, max(3, args.steps // 2))
+        h2d = prob.depth.nbytes + prob.lum.nbytes + 2 * 16 * prob.n_corr + prob.init.nbytes
+        d2h = n * 16 * 8 + n * 12 * 8
+        line["e2e"] = {"value": n_gn / (statistics.mean(te) / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(te)}
+        # restore device-resident correspondences
+        ctx.clear_correspondences()
+        ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_d, pj_d)
+
+        # plain FP32 one-solve-per-launch path on the same workload
+        plain = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
+                                  w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
+                                  precision=bf.BF_PREC_FP32)
+        for _ in range(2):
+            step(plain)
+        tp, stp, _ = timed(lambda: step(plain), max(3, args.steps // 2))
+        line["plain_fp32"] = {"value": n_gn / (statistics.mean(tp) / 1000.0), "unit": UNIT,
+                              "ms_per_step": statistics.mean(tp), "final_energy": stp["energy"][-1]}
+
+        line["chunk_latency"] = chunk_latency(bf, torch, dev)
+
+        v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def chunk_latency(bf, torch, dev, reps=40):
+    """Chunk-solve latency (call -> poses on the host) for single 11-frame 80x60 chunks."""
+    import synth
+    prob = synth.cfg1()
+    intr = prob.intr
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"],
+                     stream=torch.cuda.current_stream(dev).cuda_stream or None)
+    ctx.add_frames(0, prob.depth, prob.lum)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, prob.p_i, prob.p_j)
+    ids = list(range(prob.n_frames))
+    out = {"workload": prob.name, "n_gn": prob.solve["n_gn"], "n_pcg": prob.solve["n_pcg"], "reps": reps}
+    for name, prec in (("mixed", bf.BF_PREC_MIXED), ("plain_fp32", bf.BF_PREC_FP32)):
+        p = bf.default_params(precision=prec, **{k: v for k, v in prob.solve.items()})
+        for _ in range(5):
+            ctx.solve_local(0, ids, p)
+        lat = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            ctx.solve_local(0, ids, p)
+            ctx.get_poses(ids)
+            lat.append(1000.0 * (time.perf_counter() - t0))
+        lat.sort()
+        out[name] = {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                     "solves_per_s": 1000.0 / statistics.mean(lat)}
+    ctx.close()
+    return out
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

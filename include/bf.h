@@ -24,10 +24,11 @@
  * serialise the calls.  All device work of a context runs on its stream; calls
  * that return results to host memory synchronise that stream before returning.
  *
- * Ownership: input buffers are read during the call and may be reused by the
- * caller afterwards (host inputs are copied, device inputs are consumed on the
- * context's stream before the call returns).  Output buffers are owned by the
- * caller.  The library owns all device memory it allocates for a context and
+ * Ownership: host inputs are copied before the call returns and may be reused at
+ * once.  Device inputs are read by work enqueued on the context's stream: they must
+ * stay unchanged until that stream has executed the call's work (no extra
+ * synchronisation is needed when the caller works on the same stream).  Output
+ * buffers are owned by the caller.  The library owns all device memory it allocates for a context and
  * frees it in bf_destroy().
  */
 #ifndef BF_H
@@ -152,6 +153,15 @@ bf_status bf_add_frames(bf_ctx *ctx, int first_id, int n, const float *depth, co
  */
 bf_status bf_add_correspondences(bf_ctx *ctx, int frame_i, int frame_j, int n, const float *p_i,
                                  const float *p_j, const float *weight, int ptr_kind);
+/*
+ * Append correspondences of many pairs in one call (one host->device copy per array).
+ *   pair_ids: host, 2 x n_pairs frame ids (i, j) per pair; offsets: host, n_pairs + 1 prefix
+ *   counts; p_i, p_j: offsets[n_pairs] x 3 float32; weight: offsets[n_pairs] float32, nullable.
+ * p_i / p_j / weight are host or device per ptr_kind.  Equivalent to one
+ * bf_add_correspondences call per pair, in order.
+ */
+bf_status bf_add_correspondences_batch(bf_ctx *ctx, int n_pairs, const int *pair_ids, const int *offsets,
+                                       const float *p_i, const float *p_j, const float *weight, int ptr_kind);
 /* Drop every correspondence of the unordered pair (i, j) (Sec. 4.4.1 pruning). */
 bf_status bf_remove_pair(bf_ctx *ctx, int frame_i, int frame_j);
 /* Drop all correspondences of the context. */
@@ -215,6 +225,24 @@ bf_status bf_get_frame_planes(bf_ctx *ctx, int frame_id, float *out);
  */
 bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const double *pose_i,
                                const double *pose_j, const bf_solve_params *params, int32_t *out_target);
+
+/*
+ * Kernel accounting.  Every kernel the context launches is counted; with profiling enabled the
+ * context also records a CUDA event pair around each launch on its stream and sums the device
+ * time per kernel class.  bf_get_profile synchronises the stream.
+ */
+enum {
+  BF_K_PREPROCESS = 0, BF_K_XFORM, BF_K_DENSE, BF_K_SPARSE, BF_K_MERGE, BF_K_ASSEMBLE, BF_K_PCG, BF_K_UPDATE,
+  BF_K_ENERGY, BF_K_PACK, BF_NPROF
+};
+typedef struct {
+  long long launches;          /* kernels launched since the last reset (always counted)  */
+  long long count[BF_NPROF];   /* timed launches per class (profiling enabled)            */
+  double ms[BF_NPROF];         /* summed event-timed device milliseconds per class        */
+} bf_profile;
+bf_status bf_set_profiling(bf_ctx *ctx, int enable);
+bf_status bf_get_profile(bf_ctx *ctx, bf_profile *out);
+bf_status bf_reset_profile(bf_ctx *ctx);
 
 /* Device bytes currently held by the context. */
 size_t bf_device_bytes(bf_ctx *ctx);

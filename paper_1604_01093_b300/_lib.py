@@ -21,6 +21,8 @@ BF_PRECOND_BLOCK_JACOBI, BF_PRECOND_JACOBI = 0, 1
 BF_PREC_MIXED, BF_PREC_FP32 = 0, 1
 BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
 BF_MAX_GN = 64
+BF_NPROF = 10
+KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack"]
 
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_OUT_OF_MEMORY", 3: "BF_ERR_CUDA",
           4: "BF_ERR_NOT_FOUND", 5: "BF_ERR_SINGULAR", 6: "BF_ERR_TIMEOUT", 7: "BF_ERR_BUSY"}
@@ -61,6 +63,15 @@ class SolveStats(ctypes.Structure):
                     n_corr=self.n_corr, flags=self.flags, ms=self.ms)
 
 
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("count", ctypes.c_longlong * BF_NPROF),
+                ("ms", ctypes.c_double * BF_NPROF)]
+
+    def to_dict(self):
+        return dict(launches=self.launches,
+                    kernels={k: dict(count=self.count[i], ms=self.ms[i]) for i, k in enumerate(KERNEL_CLASSES)})
+
+
 _lib = None
 
 
@@ -82,6 +93,7 @@ def lib():
         "bf_last_error": (ctypes.c_char_p, [P]),
         "bf_add_frames": (I, [P, I, I, P, P, I, P]),
         "bf_add_correspondences": (I, [P, I, I, I, P, P, P, I]),
+        "bf_add_correspondences_batch": (I, [P, I, P, P, P, P, P, I]),
         "bf_remove_pair": (I, [P, I, I]),
         "bf_clear_correspondences": (I, [P]),
         "bf_solve_local": (I, [P, I, P, I, ctypes.POINTER(SolveParams), P]),
@@ -92,6 +104,9 @@ def lib():
         "bf_get_frame_planes": (I, [P, I, P]),
         "bf_debug_association": (I, [P, I, I, P, P, ctypes.POINTER(SolveParams), P]),
         "bf_device_bytes": (ctypes.c_size_t, [P]),
+        "bf_set_profiling": (I, [P, I]),
+        "bf_get_profile": (I, [P, ctypes.POINTER(Profile)]),
+        "bf_reset_profile": (I, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -103,7 +118,8 @@ def lib():
 
 # symbols declared in include/bf.h (checked by the CPU tests)
 EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_create", "bf_destroy",
-           "bf_last_error", "bf_add_frames", "bf_add_correspondences", "bf_remove_pair",
+           "bf_last_error", "bf_add_frames", "bf_add_correspondences", "bf_add_correspondences_batch",
+           "bf_remove_pair", "bf_set_profiling", "bf_get_profile", "bf_reset_profile",
            "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
            "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes"]
 
@@ -198,6 +214,27 @@ class Context:
         w = None if weight is None else _f32(weight)
         kind = BF_PTR_DEVICE if _is_device(p_i) else BF_PTR_HOST
         self._check(lib().bf_add_correspondences(self.h, i, j, p_i.shape[0], _ptr(p_i), _ptr(p_j), _ptr(w), kind))
+
+    def add_correspondences_batch(self, pair_ids, offsets, p_i, p_j, weight=None):
+        """All pairs at once: pair_ids (P,2), offsets (P+1,), p_i/p_j (C,3) host arrays or device tensors."""
+        ids = np.ascontiguousarray(pair_ids, dtype=np.int32).reshape(-1, 2)
+        off = np.ascontiguousarray(offsets, dtype=np.int32)
+        p_i, p_j = _f32(p_i), _f32(p_j)
+        w = None if weight is None else _f32(weight)
+        kind = BF_PTR_DEVICE if _is_device(p_i) else BF_PTR_HOST
+        self._check(lib().bf_add_correspondences_batch(self.h, ids.shape[0], _ptr(ids), _ptr(off), _ptr(p_i),
+                                                       _ptr(p_j), _ptr(w), kind))
+
+    def set_profiling(self, on=True):
+        self._check(lib().bf_set_profiling(self.h, 1 if on else 0))
+
+    def reset_profile(self):
+        self._check(lib().bf_reset_profile(self.h))
+
+    def profile(self):
+        p = Profile()
+        self._check(lib().bf_get_profile(self.h, ctypes.byref(p)))
+        return p.to_dict()
 
     def remove_pair(self, i, j):
         self._check(lib().bf_remove_pair(self.h, i, j))

@@ -94,6 +94,15 @@ struct bf_ctx {
   // solve workspace arena
   char *ws = nullptr;
   size_t ws_bytes = 0;
+  // kernel accounting
+  long long launches = 0;
+  bool prof = false;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  size_t rec_used = 0;
 };
 
 // ------------------------------------------------------------------------------- helpers
@@ -132,6 +141,34 @@ static void dfree(bf_ctx *c, void *p, size_t n) {
   if (p) {
     cudaFree(p);
     c->bytes -= n;
+  }
+}
+
+// Run one launch wrapper (returns the number of kernels it launched) with accounting.
+template <typename F>
+static void run_k(bf_ctx *c, int kind, F &&f) {
+  bf_ctx::Rec *r = nullptr;
+  if (c->prof) {
+    if (c->rec_used == c->recs.size()) {
+      bf_ctx::Rec nr{kind, nullptr, nullptr};
+      if (cudaEventCreate(&nr.a) != cudaSuccess || cudaEventCreate(&nr.b) != cudaSuccess) {
+        cudaGetLastError();
+        c->launches += f();
+        return;
+      }
+      c->recs.push_back(nr);
+    }
+    r = &c->recs[c->rec_used];
+    r->kind = kind;
+    cudaEventRecord(r->a, c->st);
+  }
+  const int n = f();
+  c->launches += n;
+  if (r) {
+    if (n > 0) {
+      cudaEventRecord(r->b, c->st);
+      ++c->rec_used;
+    }
   }
 }
 
@@ -321,6 +358,10 @@ extern "C" bf_status bf_destroy(bf_ctx *c) {
   cudaFree(c->cP);
   cudaFree(c->cQ);
   cudaFree(c->ws);
+  for (auto &r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   cudaGetLastError();
   delete c;
@@ -388,8 +429,10 @@ extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *
     dptr = c->stage;
     lptr = c->stage + n * HW;
   }
-  launch_preprocess(dptr, lptr, n, c->slot_dev, frame_store(c), c->A, c->B, nullptr, c->cfg.depth_min,
-                    c->cfg.depth_max, c->st);
+  run_k(c, BF_K_PREPROCESS, [&] {
+    return launch_preprocess(dptr, lptr, n, c->slot_dev, frame_store(c), c->A, c->B, nullptr, c->cfg.depth_min,
+                             c->cfg.depth_max, c->st);
+  });
   CK(cudaGetLastError(), "preprocess launch");
   if (ptr_kind == BF_PTR_HOST) CK(cudaStreamSynchronize(c->st), "preprocess");
   return BF_OK;
@@ -441,11 +484,101 @@ extern "C" bf_status bf_add_correspondences(bf_ctx *c, int frame_i, int frame_j,
     CK(cudaMemcpyAsync(c->cQ + c->cused, Q.data(), n * sizeof(float4), cudaMemcpyHostToDevice, c->st), "corr");
     CK(cudaStreamSynchronize(c->st), "corr");
   } else {
-    launch_pack_corr(p_i, p_j, weight, n, swap, c->cP + c->cused, c->cQ + c->cused, c->st);
+    run_k(c, BF_K_PACK,
+          [&] { return launch_pack_corr(p_i, p_j, weight, n, swap, c->cP + c->cused, c->cQ + c->cused, c->st); });
     CK(cudaGetLastError(), "pack corr");
   }
   c->corr[pair_key(frame_i, frame_j)].push_back(Seg{(int)c->cused, n});
   c->cused += n;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_add_correspondences_batch(bf_ctx *c, int n_pairs, const int *pair_ids, const int *offsets,
+                                                  const float *p_i, const float *p_j, const float *weight,
+                                                  int ptr_kind) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  if (n_pairs < 0 || (n_pairs > 0 && (!pair_ids || !offsets)) || (ptr_kind != BF_PTR_HOST && ptr_kind != BF_PTR_DEVICE))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences_batch: bad arguments");
+  if (n_pairs == 0) return BF_OK;
+  if (offsets[0] != 0) return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences_batch: offsets[0] must be 0");
+  for (int k = 0; k < n_pairs; ++k) {
+    if (offsets[k + 1] < offsets[k] || pair_ids[2 * k] == pair_ids[2 * k + 1] || pair_ids[2 * k] < 0 ||
+        pair_ids[2 * k + 1] < 0)
+      return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences_batch: bad pair " + std::to_string(k));
+  }
+  const long long total = offsets[n_pairs];
+  if (total == 0) return BF_OK;
+  if (!p_i || !p_j) return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences_batch: null points");
+  bf_status s = ensure_corr(c, c->cused + total);
+  if (s) return s;
+  if (ptr_kind == BF_PTR_HOST) {
+    std::vector<float4> P(total), Q(total);
+    for (int k = 0; k < n_pairs; ++k) {
+      const bool swap = pair_ids[2 * k] > pair_ids[2 * k + 1];
+      const float *a = swap ? p_j : p_i;
+      const float *b = swap ? p_i : p_j;
+      for (int m = offsets[k]; m < offsets[k + 1]; ++m) {
+        P[m] = make_float4(a[3 * m], a[3 * m + 1], a[3 * m + 2], weight ? weight[m] : 1.f);
+        Q[m] = make_float4(b[3 * m], b[3 * m + 1], b[3 * m + 2], 0.f);
+      }
+    }
+    CK(cudaMemcpyAsync(c->cP + c->cused, P.data(), total * sizeof(float4), cudaMemcpyHostToDevice, c->st), "corr");
+    CK(cudaMemcpyAsync(c->cQ + c->cused, Q.data(), total * sizeof(float4), cudaMemcpyHostToDevice, c->st), "corr");
+    CK(cudaStreamSynchronize(c->st), "corr");
+  } else {
+    // offsets and swap flags to the device (scratch), then one packing kernel
+    std::vector<int> meta(2 * (size_t)n_pairs + 1);
+    for (int k = 0; k <= n_pairs; ++k) meta[k] = offsets[k];
+    for (int k = 0; k < n_pairs; ++k) meta[n_pairs + 1 + k] = pair_ids[2 * k] > pair_ids[2 * k + 1] ? 1 : 0;
+    if ((int)meta.size() > c->slot_dev_cap) {
+      dfree(c, c->slot_dev, (size_t)c->slot_dev_cap * sizeof(int));
+      c->slot_dev = nullptr;
+      c->slot_dev_cap = 0;
+      s = dalloc(c, (void **)&c->slot_dev, meta.size() * sizeof(int), "scratch table");
+      if (s) return s;
+      c->slot_dev_cap = (int)meta.size();
+    }
+    CK(cudaMemcpyAsync(c->slot_dev, meta.data(), meta.size() * sizeof(int), cudaMemcpyHostToDevice, c->st), "meta");
+    run_k(c, BF_K_PACK, [&] {
+      return launch_pack_corr_batch(p_i, p_j, weight, (int)total, c->slot_dev, c->slot_dev + n_pairs + 1, n_pairs,
+                                    c->cP + c->cused, c->cQ + c->cused, c->st);
+    });
+    CK(cudaGetLastError(), "pack corr");
+    CK(cudaStreamSynchronize(c->st), "pack corr");
+  }
+  for (int k = 0; k < n_pairs; ++k) {
+    const int n = offsets[k + 1] - offsets[k];
+    if (n == 0) continue;
+    c->corr[pair_key(pair_ids[2 * k], pair_ids[2 * k + 1])].push_back(Seg{(int)(c->cused + offsets[k]), n});
+  }
+  c->cused += total;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_set_profiling(bf_ctx *c, int enable) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  c->prof = enable != 0;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_reset_profile(bf_ctx *c) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  c->launches = 0;
+  c->rec_used = 0;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_get_profile(bf_ctx *c, bf_profile *out) {
+  if (!c || !out) return BF_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  CK(cudaStreamSynchronize(c->st), "profile");
+  out->launches = c->launches;
+  for (size_t k = 0; k < c->rec_used; ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->recs[k].a, c->recs[k].b), "profile");
+    out->count[c->recs[k].kind] += 1;
+    out->ms[c->recs[k].kind] += ms;
+  }
   return BF_OK;
 }
 
@@ -624,10 +757,19 @@ struct DevSolve {
   void *Dd, *rhs;
   float *Df, *Minv;
   int *vflags, *pflags;
-  float *x, *r, *z, *p, *q;
+  float *x, *r, *z, *p, *q, *p1;
   double *energy;  // (n_gn + 1) x n_prob x 4
   int *assoc;
+  void *coop;      // cooperative PCG state (barrier, error flag, partials)
+  int coop_grid;   // > 0: one large problem solved by the cooperative PCG
 };
+
+// The cooperative multi-CTA PCG serves single-problem solves with at least this many free frames.
+constexpr int COOP_MIN_VARS = 32;
+
+int coop_grid_for(const HostTables &T) {
+  return (T.n_prob == 1 && T.n_vars >= COOP_MIN_VARS) ? coop_grid_size(T.n_vars) : 0;
+}
 
 size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D, size_t acc_size, int HW,
               bool want_assoc) {
@@ -653,6 +795,9 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
   float *z = a.take<float>((size_t)T.n_vars * 6);
   float *p = a.take<float>((size_t)T.n_vars * 6);
   float *q = a.take<float>((size_t)T.n_vars * 6);
+  float *p1 = a.take<float>((size_t)T.n_vars * 6);
+  const int cg = coop_grid_for(T);
+  void *coop = a.take<char>(cg > 0 ? coop_mem_bytes(cg) : 256);
   double *energy = a.take<double>((size_t)(n_gn + 1) * T.n_prob * PAIREN);
   int *assoc = want_assoc ? a.take<int>(HW) : nullptr;
   if (D) {
@@ -676,6 +821,9 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     D->z = z;
     D->p = p;
     D->q = q;
+    D->p1 = p1;
+    D->coop = coop;
+    D->coop_grid = cg;
     D->energy = energy;
     D->assoc = assoc;
     // table pointers into ib, in the order of pack_ints
@@ -766,12 +914,19 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
   Gates g;
   g.tau_d2 = (float)(prm.tau_dist * prm.tau_dist);
   g.tau_n = (float)prm.tau_normal;
-  launch_pair_xform(t, D.pose, D.pairM, c->st);
-  launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo), (float)(wd * prm.w_photo),
-                    (Acc *)D.dpart, nullptr, c->st);
-  launch_sparse<Acc>(mode, t, c->cP, c->cQ, D.pairM, (float)prm.w_sparse, (Acc *)D.spart, D.srmax, D.srarg, c->st);
-  launch_pair_merge<Acc, Acc>(t, D.pose, (const Acc *)D.dpart, (const Acc *)D.spart, (Acc *)D.pairblk,
-                              (Acc *)D.pairen, D.pairoff, c->st);
+  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->st); });
+  run_k(c, BF_K_DENSE, [&] {
+    return launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
+                             (float)(wd * prm.w_photo), (Acc *)D.dpart, nullptr, c->st);
+  });
+  run_k(c, BF_K_SPARSE, [&] {
+    return launch_sparse<Acc>(mode, t, c->cP, c->cQ, D.pairM, (float)prm.w_sparse, (Acc *)D.spart, D.srmax,
+                              D.srarg, c->st);
+  });
+  run_k(c, BF_K_MERGE, [&] {
+    return launch_pair_merge<Acc, Acc>(t, D.pose, (const Acc *)D.dpart, (const Acc *)D.spart, (Acc *)D.pairblk,
+                                       (Acc *)D.pairen, D.pairoff, c->st);
+  });
 }
 
 double wdense_at(const bf_solve_params &prm, int k) {
@@ -784,16 +939,31 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
   for (int k = 0; k < prm.n_gn; ++k) {
     const double wd = wdense_at(prm, k);
     linearise<Acc>(c, D, prm, wd, MODE_ACCUM);
-    launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)k * T.n_prob * PAIREN, c->st);
-    launch_assemble<Acc>(t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv, D.vflags,
-                         c->st);
-    launch_pcg<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.q, prm.n_pcg, D.pflags,
-                    c->st);
-    launch_update(t, D.x, D.pose, c->st);
+    run_k(c, BF_K_ENERGY, [&] {
+      return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)k * T.n_prob * PAIREN, c->st);
+    });
+    run_k(c, BF_K_ASSEMBLE, [&] {
+      return launch_assemble<Acc>(t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv,
+                                  D.vflags, c->st);
+    });
+    int pcg_rc = 0;
+    run_k(c, BF_K_PCG, [&] {
+      if (D.coop_grid > 0) {
+        pcg_rc = launch_pcg_coop<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.p1, D.q,
+                                      prm.n_pcg, D.pflags, D.coop, D.coop_grid, c->st);
+        return pcg_rc < 0 ? 0 : pcg_rc;
+      }
+      return launch_pcg<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.q, prm.n_pcg,
+                             D.pflags, c->st);
+    });
+    if (pcg_rc < 0) return cuda_fail(c, cudaGetLastError(), "cooperative PCG launch");
+    run_k(c, BF_K_UPDATE, [&] { return launch_update(t, D.x, D.pose, c->st); });
   }
   const double wd = prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense;
   linearise<Acc>(c, D, prm, wd, MODE_ENERGY);
-  launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)prm.n_gn * T.n_prob * PAIREN, c->st);
+  run_k(c, BF_K_ENERGY, [&] {
+    return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)prm.n_gn * T.n_prob * PAIREN, c->st);
+  });
   CK(cudaGetLastError(), "solve launches");
   return BF_OK;
 }
@@ -839,7 +1009,11 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
     CK(cudaMemcpyAsync(srmax.data(), D.srmax, T.n_segs * sizeof(float), cudaMemcpyDeviceToHost, c->st), "rmax");
     CK(cudaMemcpyAsync(srarg.data(), D.srarg, T.n_segs * sizeof(int), cudaMemcpyDeviceToHost, c->st), "rmax");
   }
+  int coop_err = 0;
+  if (D.coop_grid > 0)
+    CK(cudaMemcpyAsync(&coop_err, (char *)D.coop + 8, sizeof(int), cudaMemcpyDeviceToHost, c->st), "pcg status");
   CK(cudaStreamSynchronize(c->st), "solve");
+  if (coop_err) return fail(c, BF_ERR_TIMEOUT, "PCG grid barrier timed out");
   const double ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   out.assign(T.n_prob, {});
@@ -1021,9 +1195,11 @@ template <typename Acc>
 static bf_status build_system_t(bf_ctx *c, const HostTables &T, DevSolve &D, const bf_solve_params &prm, double *A,
                                 double *b, double *energy4, long long *n_dense) {
   linearise<Acc>(c, D, prm, prm.w_dense, MODE_ACCUM);
-  launch_energy_reduce<Acc>(D.t, (const Acc *)D.pairen, D.energy, c->st);
-  launch_assemble<Acc>(D.t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv, D.vflags,
-                       c->st);
+  run_k(c, BF_K_ENERGY, [&] { return launch_energy_reduce<Acc>(D.t, (const Acc *)D.pairen, D.energy, c->st); });
+  run_k(c, BF_K_ASSEMBLE, [&] {
+    return launch_assemble<Acc>(D.t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv,
+                                D.vflags, c->st);
+  });
   CK(cudaGetLastError(), "build system launches");
   std::vector<Acc> Dd((size_t)T.n_vars * 36), rhs((size_t)T.n_vars * 6), pb((size_t)T.n_pairs * PAIRBLK);
   double en[PAIREN];
@@ -1132,8 +1308,11 @@ extern "C" bf_status bf_debug_association(bf_ctx *c, int frame_i, int frame_j, c
   Gates g;
   g.tau_d2 = (float)(params->tau_dist * params->tau_dist);
   g.tau_n = (float)params->tau_normal;
-  launch_pair_xform(D.t, D.pose, D.pairM, c->st);
-  launch_dense<float>(MODE_ASSOC, D.t, frame_store(c), c->intr, D.pairM, g, 0.f, 0.f, nullptr, D.assoc, c->st);
+  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(D.t, D.pose, D.pairM, c->st); });
+  run_k(c, BF_K_DENSE, [&] {
+    return launch_dense<float>(MODE_ASSOC, D.t, frame_store(c), c->intr, D.pairM, g, 0.f, 0.f, nullptr, D.assoc,
+                               c->st);
+  });
   CK(cudaGetLastError(), "association launch");
   CK(cudaMemcpyAsync(out_target, D.assoc, HW * sizeof(int), cudaMemcpyDeviceToHost, c->st), "association");
   CK(cudaStreamSynchronize(c->st), "association");

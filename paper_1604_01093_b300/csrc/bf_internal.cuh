@@ -85,28 +85,39 @@ struct Gates {
 enum { MODE_ACCUM = 0, MODE_ENERGY = 1, MODE_ASSOC = 2 };
 
 // ------------------------------------------------------------------ launch wrappers (host side)
-void launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
+int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
                        float4 *A, float4 *B, uint4 *P16, float dmin, float dmax, cudaStream_t st);
-void launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, int swap, float4 *P, float4 *Q,
+int launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, int swap, float4 *P, float4 *Q,
                       cudaStream_t st);
-void launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st);
+int launch_pack_corr_batch(const float *p_i, const float *p_j, const float *w, int n_total, const int *off,
+                           const int *swap, int n_pairs, float4 *P, float4 *Q, cudaStream_t st);
+int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st);
 template <typename Part>
-void launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
+int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                   float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st);
 template <typename Part>
-void launch_sparse(int mode, const Tables &t, const float4 *P, const float4 *Q, const float *pairM, float w_sparse,
+int launch_sparse(int mode, const Tables &t, const float4 *P, const float4 *Q, const float *pairM, float w_sparse,
                    Part *part, float *seg_rmax, int *seg_rarg, cudaStream_t st);
 template <typename Acc, typename Part>
-void launch_pair_merge(const Tables &t, const double *pose, const Part *dpart, const Part *spart, Acc *pairblk,
+int launch_pair_merge(const Tables &t, const double *pose, const Part *dpart, const Part *spart, Acc *pairblk,
                        Acc *pairen, float *pairoff, cudaStream_t st);
 template <typename Acc>
-void launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, Acc *rhs, float *Df, float *Minv,
+int launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, Acc *rhs, float *Df, float *Minv,
                      int *vflags, cudaStream_t st);
 template <typename Acc>
-void launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
+int launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
                 float *r, float *z, float *p, float *q, int n_pcg, int *pflags, cudaStream_t st);
-void launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st);
+// One large problem over many CTAs (cooperative launch).  coop_mem: coop_mem_bytes(grid) bytes
+// of device memory (barrier state + per-CTA partials); its first 16 bytes are reset here.
+// Returns -1 if the cooperative launch was refused.
 template <typename Acc>
-void launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st);
+int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
+                    float *x, float *r, float *z, float *p0, float *p1, float *q, int n_pcg, int *pflags,
+                    void *coop_mem, int grid, cudaStream_t st);
+int coop_grid_size(int n_vars);
+size_t coop_mem_bytes(int grid);
+int launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st);
+template <typename Acc>
+int launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st);
 
 }  // namespace bf

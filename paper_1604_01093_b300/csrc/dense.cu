@@ -188,20 +188,21 @@ __global__ void __launch_bounds__(DENSE_BS, 2)
 }
 
 template <typename Part>
-void launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
+int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                   float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st) {
-  if (t.n_tiles == 0) return;
+  if (t.n_tiles == 0) return 0;
   if (mode == MODE_ACCUM)
     k_dense<MODE_ACCUM, Part><<<t.n_tiles, DENSE_BS, 0, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else if (mode == MODE_ENERGY)
     k_dense<MODE_ENERGY, Part><<<t.n_tiles, DENSE_BS, 0, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else
     k_dense<MODE_ASSOC, Part><<<t.n_tiles, DENSE_BS, 0, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+  return 1;
 }
 
-template void launch_dense<float>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
+template int launch_dense<float>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
                                   float, float *, int *, cudaStream_t);
-template void launch_dense<double>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
+template int launch_dense<double>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
                                    float, double *, int *, cudaStream_t);
 
 }  // namespace bf

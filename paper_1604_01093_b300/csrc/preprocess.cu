@@ -76,15 +76,16 @@ __global__ void k_pre2(int n, const int *__restrict__ slots, int W, int H, float
   Bf[pix] = b;
 }
 
-void launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
+int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
                        float4 *A, float4 *B, uint4 *P16, float dmin, float dmax, cudaStream_t st) {
   (void)P16;
   const long long total = (long long)n * fs.W * fs.H;
-  if (total == 0) return;
+  if (total == 0) return 0;
   const int bs = 256;
   const unsigned grid = (unsigned)((total + bs - 1) / bs);
   k_pre1<<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, A, B, dmin, dmax);
   k_pre2<<<grid, bs, 0, st>>>(n, slots_dev, fs.W, fs.H, B);
+  return 2;
 }
 
 // Correspondences into the pool as (p, w) / (q, 0) float4 pairs; swap exchanges p and q so that
@@ -100,10 +101,39 @@ __global__ void k_pack_corr(const float *__restrict__ p_i, const float *__restri
   Q[k] = make_float4(b[3 * k], b[3 * k + 1], b[3 * k + 2], 0.f);
 }
 
-void launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, int swap, float4 *P, float4 *Q,
+int launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, int swap, float4 *P, float4 *Q,
                       cudaStream_t st) {
-  if (n <= 0) return;
+  if (n <= 0) return 0;
   k_pack_corr<<<(n + 255) / 256, 256, 0, st>>>(p_i, p_j, w, n, swap, P, Q);
+  return 1;
+}
+
+// Batched variant: correspondence k belongs to the pair whose [off[p], off[p+1]) holds it
+// (binary search over n_pairs + 1 offsets); swap[p] as above.
+__global__ void k_pack_corr_batch(const float *__restrict__ p_i, const float *__restrict__ p_j,
+                                  const float *__restrict__ w, int n_total, const int *__restrict__ off,
+                                  const int *__restrict__ swap, int n_pairs, float4 *__restrict__ P,
+                                  float4 *__restrict__ Q) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_total) return;
+  int lo = 0, hi = n_pairs - 1;  // largest p with off[p] <= k
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  const bool s = swap[lo] != 0;
+  const float *a = s ? p_j : p_i;
+  const float *b = s ? p_i : p_j;
+  P[k] = make_float4(a[3 * k], a[3 * k + 1], a[3 * k + 2], w ? w[k] : 1.f);
+  Q[k] = make_float4(b[3 * k], b[3 * k + 1], b[3 * k + 2], 0.f);
+}
+
+int launch_pack_corr_batch(const float *p_i, const float *p_j, const float *w, int n_total, const int *off,
+                           const int *swap, int n_pairs, float4 *P, float4 *Q, cudaStream_t st) {
+  if (n_total <= 0 || n_pairs <= 0) return 0;
+  k_pack_corr_batch<<<(n_total + 255) / 256, 256, 0, st>>>(p_i, p_j, w, n_total, off, swap, n_pairs, P, Q);
+  return 1;
 }
 
 }  // namespace bf

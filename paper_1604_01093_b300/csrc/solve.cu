@@ -1,15 +1,21 @@
 // Linear-system assembly, block-Jacobi PCG and the pose update (Sec. 4.4).
 //
 //   k_pair_xform   per pair: T_b^-1 T_a and T_a^-1 T_b, FP64 with explicit rounding, stored FP32
-//   k_pair_merge   per pair: sum the pair's tile / segment partials (FP64 in mixed precision),
-//                  rotate them from target-camera to world coordinates and expand the
+//   k_pair_merge   warp per pair: sum the pair's tile / segment partials (FP64 in mixed
+//                  precision), rotate them from target-camera to world coordinates and expand the
 //                  [a, v, c, -v] sums into the 6x6 blocks A_aa, A_ab, A_bb and rhs_a, rhs_b
-//   k_assemble     per free frame: its diagonal block and rhs (sum over incident pairs, fixed
-//                  order) and the preconditioner: 6x6 Cholesky inverse (block-Jacobi) or the
+//   k_assemble     warp per free frame: its diagonal block and rhs (sum over incident pairs in a
+//                  fixed order) and the preconditioner: 6x6 Cholesky inverse (block-Jacobi) or the
 //                  inverse diagonal (Jacobi, the paper's choice)
-//   k_pcg          per problem, one CTA: exactly n_pcg PCG iterations from x = 0, stopping early
-//                  only if p.Ap <= 0 or r.z == 0; block-sparse matvec over the pair blocks
+//   k_pcg          one CTA per problem (batches of small problems): exactly n_pcg PCG
+//                  iterations from x = 0, stopping early only if p.Ap <= 0 or r.z == 0
+//   k_pcg_coop     one large problem over many CTAs (cooperative launch, all CTAs resident):
+//                  warp per frame, two grid barriers per iteration, deterministic dot products
 //   k_update       per free frame: R <- Exp(dw) R, t <- t + dt (FP64)
+//
+// The paper's solver (Sec. 4.4) sums the PCG scalars with warp shuffles plus global atomics in a
+// single kernel; here every dot product is reduced in a fixed order (warp tree, then CTA
+// partials summed in index order by every CTA) so results do not depend on scheduling.
 #include "bf_internal.cuh"
 
 namespace bf {
@@ -42,272 +48,305 @@ __global__ void k_pair_xform(int n_pairs, const int *__restrict__ pa, const int 
   }
 }
 
-void launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st) {
-  if (t.n_pairs == 0) return;
+int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st) {
+  if (t.n_pairs == 0) return 0;
   k_pair_xform<<<(t.n_pairs + 127) / 128, 128, 0, st>>>(t.n_pairs, t.pair_a, t.pair_b, pose, pairM);
+  return 1;
 }
 
 // ------------------------------------------------------------------------------- pair merge
-template <typename Acc>
-__device__ __forceinline__ void sym_get(const Acc *s, Acc (&m)[3][3]) {
-  m[0][0] = s[0]; m[0][1] = s[1]; m[0][2] = s[2];
-  m[1][0] = s[1]; m[1][1] = s[3]; m[1][2] = s[4];
-  m[2][0] = s[2]; m[2][1] = s[4]; m[2][2] = s[5];
-}
-template <typename Acc>
-__device__ __forceinline__ void full_get(const Acc *s, Acc (&m)[3][3]) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) m[i][j] = s[3 * i + j];
-}
-// X <- R X R^T
-template <typename Acc>
-__device__ __forceinline__ void rot33(const Acc (&R)[3][3], Acc (&X)[3][3]) {
-  Acc T[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) T[i][j] = R[i][0] * X[0][j] + R[i][1] * X[1][j] + R[i][2] * X[2][j];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) X[i][j] = T[i][0] * R[j][0] + T[i][1] * R[j][1] + T[i][2] * R[j][2];
-}
-template <typename Acc>
-__device__ __forceinline__ void rot3(const Acc (&R)[3][3], const Acc *v, Acc (&o)[3]) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i) o[i] = R[i][0] * v[0] + R[i][1] * v[1] + R[i][2] * v[2];
+// Rotated sums of one direction: 0..53 six 3x3 blocks (Saa, Sav, Svv, Sac, Svc, Scc, full
+// row-major), 54..62 the vectors ga, gv, gc.
+constexpr int NROT = 63;
+
+__device__ __forceinline__ int part_index(int blk, int m, int n) {
+  // position of element (m, n) of block blk in the NPART layout
+  const int sym = (m == n) ? (m == 0 ? 0 : (m == 1 ? 3 : 5)) : (m + n == 1 ? 1 : (m + n == 2 ? 2 : 4));
+  switch (blk) {
+    case 0: return P_AA + sym;
+    case 1: return P_AV + 3 * m + n;
+    case 2: return P_VV + sym;
+    case 3: return P_AC + 3 * m + n;
+    case 4: return P_VC + 3 * m + n;
+    default: return P_CC + sym;
+  }
 }
 
-// Add one direction's sums S (target-frame coordinates, rotated here by R = R_target) into the
-// pair's blocks.  src_is_a selects whether the source of the direction is frame a.
-template <typename Acc>
-__device__ void add_direction(const Acc *S, const Acc (&R)[3][3], bool src_is_a, Acc *blk) {
-  Acc Saa[3][3], Sav[3][3], Svv[3][3], Sac[3][3], Svc[3][3], Scc[3][3], ga[3], gv[3], gc[3];
-  sym_get(S + P_AA, Saa); full_get(S + P_AV, Sav); sym_get(S + P_VV, Svv);
-  full_get(S + P_AC, Sac); full_get(S + P_VC, Svc); sym_get(S + P_CC, Scc);
-  rot33(R, Saa); rot33(R, Sav); rot33(R, Svv); rot33(R, Sac); rot33(R, Svc); rot33(R, Scc);
-  rot3(R, S + P_GA, ga); rot3(R, S + P_GV, gv); rot3(R, S + P_GC, gc);
-  Acc *Ass = blk + (src_is_a ? PB_AA : PB_BB);
-  Acc *Att = blk + (src_is_a ? PB_BB : PB_AA);
-  Acc *Aab = blk + PB_AB;
-  Acc *rs = blk + (src_is_a ? PB_RA : PB_RB);
-  Acc *rt = blk + (src_is_a ? PB_RB : PB_RA);
+// For output slot s of a pair record and a direction whose source is frame a (src_is_a) or b,
+// the rotated element feeding it and its sign (0 sign: no contribution).
+__device__ __forceinline__ void slot_source(int s, bool src_is_a, int &idx, int &sign) {
+  enum { SAA = 0, SAV = 9, SVV = 18, SAC = 27, SVC = 36, SCC = 45, GA = 54, GV = 57, GC = 60 };
+  idx = 0;
+  sign = 0;
+  if (s < 108) {
+    const int blk = s / 36, e = s % 36;
+    int i = e / 6, j = e % 6;
+    int role;  // 0: A_ss, 1: A_tt, 2: A_st, 3: A_st^T
+    if (blk == 1) {
+      role = src_is_a ? 2 : 3;
+    } else {
+      const bool is_src = (blk == 0) == src_is_a;
+      role = is_src ? 0 : 1;
+    }
+    if (role == 3) {  // A_ab = A_st^T
+      const int tmp = i;
+      i = j;
+      j = tmp;
+      role = 2;
+    }
+    const bool ui = i < 3, uj = j < 3;
+    const int i3 = ui ? i : i - 3, j3 = uj ? j : j - 3;
+    if (role == 0) {  // [[Saa, Sav], [Sav^T, Svv]]
+      if (ui && uj) { idx = SAA + 3 * i3 + j3; sign = 1; }
+      else if (ui) { idx = SAV + 3 * i3 + j3; sign = 1; }
+      else if (uj) { idx = SAV + 3 * j3 + i3; sign = 1; }
+      else { idx = SVV + 3 * i3 + j3; sign = 1; }
+    } else if (role == 1) {  // [[Scc, -Svc^T], [-Svc, Svv]]
+      if (ui && uj) { idx = SCC + 3 * i3 + j3; sign = 1; }
+      else if (ui) { idx = SVC + 3 * j3 + i3; sign = -1; }
+      else if (uj) { idx = SVC + 3 * i3 + j3; sign = -1; }
+      else { idx = SVV + 3 * i3 + j3; sign = 1; }
+    } else {  // A_st = [[Sac, -Sav], [Svc, -Svv]]
+      if (ui && uj) { idx = SAC + 3 * i3 + j3; sign = 1; }
+      else if (ui) { idx = SAV + 3 * i3 + j3; sign = -1; }
+      else if (uj) { idx = SVC + 3 * i3 + j3; sign = 1; }
+      else { idx = SVV + 3 * i3 + j3; sign = -1; }
+    }
+  } else {
+    const int r = s - 108;
+    const bool is_a_rhs = r < 6;
+    const int c = r % 6;
+    const bool is_src = is_a_rhs == src_is_a;
+    if (is_src) {  // -(ga, gv)
+      idx = c < 3 ? GA + c : GV + c - 3;
+      sign = -1;
+    } else {  // -(gc, -gv)
+      idx = c < 3 ? GC + c : GV + c - 3;
+      sign = c < 3 ? -1 : 1;
+    }
+  }
+}
+
+constexpr int MERGE_WARPS = 4;
+
+template <typename Acc, typename Part>
+__global__ void __launch_bounds__(32 * MERGE_WARPS)
+    k_pair_merge(Tables t, const double *__restrict__ pose, const Part *__restrict__ dpart,
+                 const Part *__restrict__ spart, Acc *__restrict__ pairblk, Acc *__restrict__ pairen,
+                 float *__restrict__ pairoff) {
+  __shared__ Acc S_sh[MERGE_WARPS][NPART + 7];
+  __shared__ Acc rot_sh[MERGE_WARPS][NROT + 1];
+  __shared__ Acc R_sh[MERGE_WARPS][9];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = blockIdx.x * MERGE_WARPS + w;
+  if (p >= t.n_pairs) return;  // whole warp exits together
+  Acc *S = S_sh[w];
+  Acc *rot = rot_sh[w];
+  Acc *R = R_sh[w];
+  Acc out[4] = {0, 0, 0, 0};  // slots lane, lane+32, lane+64, lane+96
+  Acc en[4] = {0, 0, 0, 0};   // kept by lane 0: e_sparse, e_photo, e_geo, n_dense
+  for (int src = 0; src < 3; ++src) {
+    // src 0: dense a->b (target b), 1: dense b->a (target a), 2: sparse (target b, source a)
+    int k0, k1;
+    const Part *base;
+    if (src < 2) {
+      const int d = t.pair_dp[2 * p + src];
+      if (d < 0) continue;
+      k0 = t.dp_tile0[d];
+      k1 = t.dp_tile1[d];
+      base = dpart;
+    } else {
+      k0 = t.pair_seg0[p];
+      k1 = t.pair_seg1[p];
+      base = spart;
+      if (k1 <= k0) continue;
+    }
+    // sum the work items' partials (fixed order)
+    for (int k = lane; k < NPART; k += 32) {
+      Acc s = 0;
+      for (int it = k0; it < k1; ++it) s += (Acc)base[(long long)it * NPART + k];
+      S[k] = s;
+    }
+    const int tgt = (src == 1) ? t.pair_a[p] : t.pair_b[p];
+    if (lane < 9) R[lane] = (Acc)pose[12 * tgt + lane];
+    __syncwarp();
+    // rotate to world: blocks R X R^T, vectors R g
+    for (int e = lane; e < NROT; e += 32) {
+      Acc v = 0;
+      if (e < 54) {
+        const int blk = e / 9, i = (e % 9) / 3, j = e % 3;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
+        for (int m = 0; m < 3; ++m) {
+          Acc tm = 0;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      // A_ss = [[Saa, Sav], [Sav^T, Svv]]
-      Ass[6 * i + j] += Saa[i][j];
-      Ass[6 * i + 3 + j] += Sav[i][j];
-      Ass[6 * (3 + i) + j] += Sav[j][i];
-      Ass[6 * (3 + i) + 3 + j] += Svv[i][j];
-      // A_tt = [[Scc, -Svc^T], [-Svc, Svv]]
-      Att[6 * i + j] += Scc[i][j];
-      Att[6 * i + 3 + j] += -Svc[j][i];
-      Att[6 * (3 + i) + j] += -Svc[i][j];
-      Att[6 * (3 + i) + 3 + j] += Svv[i][j];
-      // A_st = [[Sac, -Sav], [Svc, -Svv]]  (rows source, cols target)
-      const Acc st00 = Sac[i][j], st01 = -Sav[i][j], st10 = Svc[i][j], st11 = -Svv[i][j];
-      if (src_is_a) {
-        Aab[6 * i + j] += st00;
-        Aab[6 * i + 3 + j] += st01;
-        Aab[6 * (3 + i) + j] += st10;
-        Aab[6 * (3 + i) + 3 + j] += st11;
-      } else {  // A_ab = A_st^T
-        Aab[6 * j + i] += st00;
-        Aab[6 * (3 + j) + i] += st01;
-        Aab[6 * j + 3 + i] += st10;
-        Aab[6 * (3 + j) + 3 + i] += st11;
+          for (int n = 0; n < 3; ++n) tm += S[part_index(blk, m, n)] * R[3 * j + n];
+          v += R[3 * i + m] * tm;
+        }
+      } else {
+        const int vec = (e - 54) / 3, i = (e - 54) % 3;
+        const int off = vec == 0 ? P_GA : (vec == 1 ? P_GV : P_GC);
+        v = R[3 * i] * S[off] + R[3 * i + 1] * S[off + 1] + R[3 * i + 2] * S[off + 2];
+      }
+      rot[e] = v;
+    }
+    __syncwarp();
+    const bool src_is_a = (src != 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int s = lane + 32 * q;
+      if (s < PAIRBLK) {
+        int idx, sign;
+        slot_source(s, src_is_a, idx, sign);
+        if (sign > 0) out[q] += rot[idx];
+        else if (sign < 0) out[q] -= rot[idx];
       }
     }
-    // rhs = -J^T W r : source (ga, gv), target (gc, -gv)
-    rs[i] -= ga[i];
-    rs[3 + i] -= gv[i];
-    rt[i] -= gc[i];
-    rt[3 + i] += gv[i];
+    if (lane == 0) {
+      if (src < 2) {
+        en[2] += S[P_E0];
+        en[1] += S[P_E1];
+        en[3] += S[P_CNT];
+      } else {
+        en[0] += S[P_E0];
+      }
+    }
+    __syncwarp();
   }
-}
-
-template <typename Acc>
-__device__ __forceinline__ void load_R(const double *T, Acc (&R)[3][3]) {
+  Acc *o = pairblk + (long long)p * PAIRBLK;
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int q = 0; q < 4; ++q) {
+    const int s = lane + 32 * q;
+    if (s < PAIRBLK) {
+      o[s] = out[q];
+      if (s >= PB_AB && s < PB_AB + 36) pairoff[(long long)p * 36 + s - PB_AB] = (float)out[q];
+    }
+  }
+  if (lane == 0) {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) R[i][j] = (Acc)T[3 * i + j];
+    for (int k = 0; k < PAIREN; ++k) pairen[(long long)p * PAIREN + k] = en[k];
+  }
 }
 
 template <typename Acc, typename Part>
-__global__ void k_pair_merge(Tables t, const double *__restrict__ pose, const Part *__restrict__ dpart,
-                             const Part *__restrict__ spart, Acc *__restrict__ pairblk, Acc *__restrict__ pairen,
-                             float *__restrict__ pairoff) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= t.n_pairs) return;
-  Acc blk[PAIRBLK];
-#pragma unroll
-  for (int k = 0; k < PAIRBLK; ++k) blk[k] = 0;
-  Acc en[PAIREN] = {0, 0, 0, 0};
-  const int fa = t.pair_a[p], fb = t.pair_b[p];
-  Acc Ra[3][3], Rb[3][3];
-  load_R(pose + 12 * fa, Ra);
-  load_R(pose + 12 * fb, Rb);
-  Acc S[NPART];
-  // dense directions
-#pragma unroll 1
-  for (int dir = 0; dir < 2; ++dir) {
-    const int d = t.pair_dp[2 * p + dir];
-    if (d < 0) continue;
-#pragma unroll
-    for (int k = 0; k < NPART; ++k) S[k] = 0;
-    for (int tl = t.dp_tile0[d]; tl < t.dp_tile1[d]; ++tl) {
-      const Part *src = dpart + (long long)tl * NPART;
-#pragma unroll
-      for (int k = 0; k < NPART; ++k) S[k] += (Acc)src[k];
-    }
-    add_direction<Acc>(S, dir == 0 ? Rb : Ra, dir == 0, blk);
-    en[2] += S[P_E0];
-    en[1] += S[P_E1];
-    en[3] += S[P_CNT];
-  }
-  // sparse segments (camera-b coordinates, source a)
-  if (t.pair_seg1[p] > t.pair_seg0[p]) {
-#pragma unroll
-    for (int k = 0; k < NPART; ++k) S[k] = 0;
-    for (int s = t.pair_seg0[p]; s < t.pair_seg1[p]; ++s) {
-      const Part *src = spart + (long long)s * NPART;
-#pragma unroll
-      for (int k = 0; k < NPART; ++k) S[k] += (Acc)src[k];
-    }
-    add_direction<Acc>(S, Rb, true, blk);
-    en[0] += S[P_E0];
-  }
-  Acc *out = pairblk + (long long)p * PAIRBLK;
-#pragma unroll
-  for (int k = 0; k < PAIRBLK; ++k) out[k] = blk[k];
-#pragma unroll
-  for (int k = 0; k < PAIREN; ++k) pairen[(long long)p * PAIREN + k] = en[k];
-#pragma unroll
-  for (int k = 0; k < 36; ++k) pairoff[(long long)p * 36 + k] = (float)blk[PB_AB + k];
+int launch_pair_merge(const Tables &t, const double *pose, const Part *dpart, const Part *spart, Acc *pairblk,
+                      Acc *pairen, float *pairoff, cudaStream_t st) {
+  if (t.n_pairs == 0) return 0;
+  k_pair_merge<Acc, Part><<<(t.n_pairs + MERGE_WARPS - 1) / MERGE_WARPS, 32 * MERGE_WARPS, 0, st>>>(
+      t, pose, dpart, spart, pairblk, pairen, pairoff);
+  return 1;
 }
-
-template <typename Acc, typename Part>
-void launch_pair_merge(const Tables &t, const double *pose, const Part *dpart, const Part *spart, Acc *pairblk,
-                       Acc *pairen, float *pairoff, cudaStream_t st) {
-  if (t.n_pairs == 0) return;
-  k_pair_merge<Acc, Part><<<(t.n_pairs + 63) / 64, 64, 0, st>>>(t, pose, dpart, spart, pairblk, pairen, pairoff);
-}
-template void launch_pair_merge<double, double>(const Tables &, const double *, const double *, const double *,
-                                                double *, double *, float *, cudaStream_t);
-template void launch_pair_merge<float, float>(const Tables &, const double *, const float *, const float *, float *,
-                                              float *, float *, cudaStream_t);
+template int launch_pair_merge<double, double>(const Tables &, const double *, const double *, const double *,
+                                               double *, double *, float *, cudaStream_t);
+template int launch_pair_merge<float, float>(const Tables &, const double *, const float *, const float *, float *,
+                                             float *, float *, cudaStream_t);
 
 // --------------------------------------------------------------------------------- assemble
+// 6x6 SPD inverse by Cholesky (FP64).  Returns false if the block is not positive definite.
+__device__ bool chol_inverse6(const double *D, double *Mi) {
+  double L[36];
+  for (int k = 0; k < 36; ++k) L[k] = 0.0;
+  for (int j = 0; j < 6; ++j) {
+    double s = D[6 * j + j];
+    for (int k = 0; k < j; ++k) s -= L[6 * j + k] * L[6 * j + k];
+    if (!(s > 0.0)) return false;
+    const double ljj = sqrt(s);
+    L[6 * j + j] = ljj;
+    for (int i = j + 1; i < 6; ++i) {
+      double u = D[6 * i + j];
+      for (int k = 0; k < j; ++k) u -= L[6 * i + k] * L[6 * j + k];
+      L[6 * i + j] = u / ljj;
+    }
+  }
+  double Li[36];
+  for (int k = 0; k < 36; ++k) Li[k] = 0.0;
+  for (int i = 0; i < 6; ++i) {
+    Li[6 * i + i] = 1.0 / L[6 * i + i];
+    for (int j = 0; j < i; ++j) {
+      double s = 0.0;
+      for (int k = j; k < i; ++k) s -= L[6 * i + k] * Li[6 * k + j];
+      Li[6 * i + j] = s / L[6 * i + i];
+    }
+  }
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) {
+      double s = 0.0;
+      for (int k = (i > j ? i : j); k < 6; ++k) s += Li[6 * k + i] * Li[6 * k + j];
+      Mi[6 * i + j] = s;
+    }
+  return true;
+}
+
+constexpr int ASM_WARPS = 4;
+
 template <typename Acc>
-__global__ void k_assemble(Tables t, const Acc *__restrict__ pairblk, int precond, Acc *__restrict__ Dd,
-                           Acc *__restrict__ rhs, float *__restrict__ Df, float *__restrict__ Minv,
-                           int *__restrict__ vflags) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(32 * ASM_WARPS)
+    k_assemble(Tables t, const Acc *__restrict__ pairblk, int precond, Acc *__restrict__ Dd, Acc *__restrict__ rhs,
+               float *__restrict__ Df, float *__restrict__ Minv, int *__restrict__ vflags) {
+  __shared__ double Dsh[ASM_WARPS][36];
+  __shared__ double Msh[ASM_WARPS][36];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int v = blockIdx.x * ASM_WARPS + w;
   if (v >= t.n_vars) return;
-  Acc D[36], r[6];
-#pragma unroll
-  for (int k = 0; k < 36; ++k) D[k] = 0;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) r[k] = 0;
-  for (int e = t.inc_off[v]; e < t.inc_off[v + 1]; ++e) {
-    const int ent = t.inc[e];
-    const int p = ent >> 1, side = ent & 1;
-    const Acc *b = pairblk + (long long)p * PAIRBLK;
-    const Acc *Dsrc = b + (side == 0 ? PB_AA : PB_BB);
-    const Acc *rsrc = b + (side == 0 ? PB_RA : PB_RB);
-#pragma unroll
-    for (int k = 0; k < 36; ++k) D[k] += Dsrc[k];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) r[k] += rsrc[k];
-  }
-  int flag = 0;
-  bool empty = true;
-#pragma unroll
-  for (int k = 0; k < 36; ++k) {
-    Dd[(long long)v * 36 + k] = D[k];
-    Df[(long long)v * 36 + k] = (float)D[k];
-    empty = empty && (D[k] == 0);
-  }
-#pragma unroll
-  for (int k = 0; k < 6; ++k) rhs[(long long)v * 6 + k] = r[k];
-  // preconditioner in FP64 regardless of Acc
-  double Mi[36];
-#pragma unroll
-  for (int k = 0; k < 36; ++k) Mi[k] = 0.0;
-  if (empty) {
-    flag = 2;  // BF_FLAG_EMPTY_FRAME
-  } else {
-    bool chol_ok = (precond == 0);
-    double L[36];
-    if (chol_ok) {
-#pragma unroll
-      for (int k = 0; k < 36; ++k) L[k] = 0.0;
-      for (int j = 0; j < 6 && chol_ok; ++j) {
-        double s = (double)D[6 * j + j];
-        for (int k = 0; k < j; ++k) s -= L[6 * j + k] * L[6 * j + k];
-        if (!(s > 0.0)) {
-          chol_ok = false;
-          break;
-        }
-        const double ljj = sqrt(s);
-        L[6 * j + j] = ljj;
-        for (int i = j + 1; i < 6; ++i) {
-          double u = (double)D[6 * i + j];
-          for (int k = 0; k < j; ++k) u -= L[6 * i + k] * L[6 * j + k];
-          L[6 * i + j] = u / ljj;
-        }
-      }
-      if (chol_ok) {
-        // inverse of L (lower), then M^-1 = L^-T L^-1
-        double Li[36];
-        for (int k = 0; k < 36; ++k) Li[k] = 0.0;
-        for (int i = 0; i < 6; ++i) {
-          Li[6 * i + i] = 1.0 / L[6 * i + i];
-          for (int j = 0; j < i; ++j) {
-            double s = 0.0;
-            for (int k = j; k < i; ++k) s -= L[6 * i + k] * Li[6 * k + j];
-            Li[6 * i + j] = s / L[6 * i + i];
-          }
-        }
-        for (int i = 0; i < 6; ++i)
-          for (int j = 0; j < 6; ++j) {
-            double s = 0.0;
-            for (int k = (i > j ? i : j); k < 6; ++k) s += Li[6 * k + i] * Li[6 * k + j];
-            Mi[6 * i + j] = s;
-          }
-      } else if (precond == 0) {
-        flag = 1;  // BF_FLAG_SINGULAR_BLOCK: fall back to the diagonal
-      }
+  const int e0 = t.inc_off[v], e1 = t.inc_off[v + 1];
+  // lane handles entries lane and lane + 32 of [D (36) | rhs (6)]
+  for (int k = lane; k < 42; k += 32) {
+    Acc s = 0;
+    for (int e = e0; e < e1; ++e) {
+      const int ent = t.inc[e];
+      const int p = ent >> 1, side = ent & 1;
+      const Acc *b = pairblk + (long long)p * PAIRBLK;
+      s += k < 36 ? b[(side == 0 ? PB_AA : PB_BB) + k] : b[(side == 0 ? PB_RA : PB_RB) + k - 36];
     }
-    if (!chol_ok) {
-      for (int k = 0; k < 6; ++k) {
-        const double d = (double)D[7 * k];
-        Mi[7 * k] = d > 0.0 ? 1.0 / d : 0.0;
-      }
+    if (k < 36) {
+      Dd[(long long)v * 36 + k] = s;
+      Df[(long long)v * 36 + k] = (float)s;
+      Dsh[w][k] = (double)s;
+    } else {
+      rhs[(long long)v * 6 + k - 36] = s;
     }
   }
-#pragma unroll
-  for (int k = 0; k < 36; ++k) Minv[(long long)v * 36 + k] = (float)Mi[k];
-  vflags[v] = flag;
+  __syncwarp();
+  if (lane == 0) {
+    int flag = 0;
+    bool empty = true;
+    for (int k = 0; k < 36; ++k) empty = empty && (Dsh[w][k] == 0.0);
+    for (int k = 0; k < 36; ++k) Msh[w][k] = 0.0;
+    if (empty) {
+      flag = 2;  // BF_FLAG_EMPTY_FRAME: zero inverse, the frame's update stays 0
+    } else {
+      bool ok = false;
+      if (precond == 0) {
+        ok = chol_inverse6(Dsh[w], Msh[w]);
+        if (!ok) flag = 1;  // BF_FLAG_SINGULAR_BLOCK: fall back to the diagonal
+      }
+      if (!ok) {
+        for (int k = 0; k < 36; ++k) Msh[w][k] = 0.0;
+        for (int k = 0; k < 6; ++k) {
+          const double d = Dsh[w][7 * k];
+          Msh[w][7 * k] = d > 0.0 ? 1.0 / d : 0.0;
+        }
+      }
+    }
+    vflags[v] = flag;
+  }
+  __syncwarp();
+  for (int k = lane; k < 36; k += 32) Minv[(long long)v * 36 + k] = (float)Msh[w][k];
 }
 
 template <typename Acc>
-void launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, Acc *rhs, float *Df, float *Minv,
-                     int *vflags, cudaStream_t st) {
-  if (t.n_vars == 0) return;
-  k_assemble<Acc><<<(t.n_vars + 63) / 64, 64, 0, st>>>(t, pairblk, precond, Dd, rhs, Df, Minv, vflags);
+int launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, Acc *rhs, float *Df, float *Minv,
+                    int *vflags, cudaStream_t st) {
+  if (t.n_vars == 0) return 0;
+  k_assemble<Acc><<<(t.n_vars + ASM_WARPS - 1) / ASM_WARPS, 32 * ASM_WARPS, 0, st>>>(t, pairblk, precond, Dd, rhs,
+                                                                                      Df, Minv, vflags);
+  return 1;
 }
-template void launch_assemble<double>(const Tables &, const double *, int, double *, double *, float *, float *,
-                                      int *, cudaStream_t);
-template void launch_assemble<float>(const Tables &, const float *, int, float *, float *, float *, float *, int *,
+template int launch_assemble<double>(const Tables &, const double *, int, double *, double *, float *, float *, int *,
                                      cudaStream_t);
+template int launch_assemble<float>(const Tables &, const float *, int, float *, float *, float *, float *, int *,
+                                    cudaStream_t);
 
-// -------------------------------------------------------------------------------------- PCG
+// ------------------------------------------------------------------------ PCG, one CTA/problem
 constexpr int PCG_BS = 256;
 
 template <typename Acc>
@@ -357,7 +396,6 @@ __global__ void __launch_bounds__(PCG_BS)
   int flag = 0;
   for (int it = 0; it < n_pcg; ++it) {
     if (rz == (Acc)0) break;
-    // q = A p ; loc = p . q
     loc = 0;
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
       const int v = u / 6, c = u % 6;
@@ -411,15 +449,258 @@ __global__ void __launch_bounds__(PCG_BS)
 }
 
 template <typename Acc>
-void launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
-                float *r, float *z, float *p, float *q, int n_pcg, int *pflags, cudaStream_t st) {
-  if (t.n_prob == 0) return;
+int launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
+               float *r, float *z, float *p, float *q, int n_pcg, int *pflags, cudaStream_t st) {
+  if (t.n_prob == 0) return 0;
   k_pcg<Acc><<<t.n_prob, PCG_BS, 0, st>>>(t, Df, pairoff, Minv, rhs, x, r, z, p, q, n_pcg, pflags);
+  return 1;
 }
-template void launch_pcg<double>(const Tables &, const float *, const float *, const float *, const double *, float *,
-                                 float *, float *, float *, float *, int, int *, cudaStream_t);
-template void launch_pcg<float>(const Tables &, const float *, const float *, const float *, const float *, float *,
+template int launch_pcg<double>(const Tables &, const float *, const float *, const float *, const double *, float *,
                                 float *, float *, float *, float *, int, int *, cudaStream_t);
+template int launch_pcg<float>(const Tables &, const float *, const float *, const float *, const float *, float *,
+                               float *, float *, float *, float *, int, int *, cudaStream_t);
+
+// ------------------------------------------------------------- PCG, one problem over the grid
+constexpr int COOP_BS = 256;
+constexpr int COOP_WARPS = COOP_BS / 32;
+// Spin limit of the grid barrier: ~2^22 polls with a 256 ns back-off, i.e. about a second.
+constexpr long long BARRIER_SPIN_LIMIT = 1LL << 22;
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  count/gen live in global
+// memory and start at 0.  A CTA whose wait exceeds the spin limit sets *err and returns false;
+// a CTA that sees *err set while waiting returns false too, so no CTA waits forever.
+__device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned nblocks, volatile int *err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd((unsigned *)gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (*err) {
+          ok = 0;
+          break;
+        }
+        if (++spins > BARRIER_SPIN_LIMIT) {
+          *err = 1;
+          ok = 0;
+          break;
+        }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+struct CoopState {
+  unsigned *count;
+  unsigned *gen;
+  int *err;
+  void *part_pq;  // [gridDim.x] Acc
+  void *part_rz;  // [gridDim.x] Acc
+};
+
+template <typename Acc>
+__device__ __forceinline__ Acc grid_total(const Acc *part, int n) {
+  Acc s = 0;
+  for (int k = 0; k < n; ++k) s += __ldcg(part + k);
+  return s;
+}
+
+template <typename Acc>
+__device__ __forceinline__ void cta_partial(Acc v, Acc *sh, Acc *part) {
+  // fixed-order CTA reduction of per-warp values (lane 0 of each warp holds its warp's value)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // sh may still be read by a previous call
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Acc s = 0;
+    for (int w = 0; w < COOP_WARPS; ++w) s += sh[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(COOP_BS)
+    k_pcg_coop(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff,
+               const float *__restrict__ Minv, const Acc *__restrict__ rhs, float *x, float *r, float *z, float *p0,
+               float *p1, float *q, int n_pcg, int *__restrict__ pflags, CoopState cs) {
+  __shared__ Acc sh[COOP_WARPS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x * COOP_WARPS + warp, nw = gridDim.x * COOP_WARPS;
+  const int v0 = t.prob_var0[0], v1 = t.prob_var1[0];
+  Acc *ppq = (Acc *)cs.part_pq, *prz = (Acc *)cs.part_rz;
+  volatile int *err = cs.err;
+  // init: x = 0, r = b, z = M^-1 r, p_old = 0 (the first direction is z)
+  Acc loc = 0;
+  for (int v = v0 + gw; v < v1; v += nw) {
+    if (lane < 6) {
+      float rr[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) rr[k] = (float)rhs[6 * v + k];
+      const float *M = Minv + (long long)v * 36 + 6 * lane;
+      const float zl = M[0] * rr[0] + M[1] * rr[1] + M[2] * rr[2] + M[3] * rr[3] + M[4] * rr[4] + M[5] * rr[5];
+      x[6 * v + lane] = 0.f;
+      r[6 * v + lane] = rr[lane];
+      z[6 * v + lane] = zl;
+      p0[6 * v + lane] = 0.f;
+      loc += (Acc)rr[lane] * (Acc)zl;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
+  cta_partial(loc, sh, prz);
+  if (!grid_barrier(cs.count, cs.gen, gridDim.x, err)) return;
+  Acc rz = grid_total(prz, gridDim.x);
+  Acc beta = 0;
+  int flag = 0;
+  float *pold = p0, *pnew = p1;
+  for (int it = 0; it < n_pcg; ++it) {
+    if (rz == (Acc)0) break;
+    // Phase A: p_new = z + beta p_old (own frames); q = A p_new with the neighbours' p_new formed
+    // on the fly from z and p_old (both final since the last barrier)
+    const float fb = (float)beta;
+    Acc lpq = 0;
+    for (int v = v0 + gw; v < v1; v += nw) {
+      float pn[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) pn[k] = __ldcg(z + 6 * v + k) + fb * __ldcg(pold + 6 * v + k);
+      float acc[6] = {0, 0, 0, 0, 0, 0};
+      for (int e = t.inc_off[v] + lane; e < t.inc_off[v + 1]; e += 32) {
+        const int ent = t.inc[e];
+        const int pr = ent >> 1, side = ent & 1;
+        const int ov = t.frame_var[side == 0 ? t.pair_b[pr] : t.pair_a[pr]];
+        if (ov < 0) continue;
+        float po[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) po[k] = __ldcg(z + 6 * ov + k) + fb * __ldcg(pold + 6 * ov + k);
+        const float *O = pairoff + (long long)pr * 36;
+        if (side == 0) {
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[c] += O[6 * c + k] * po[k];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[c] += O[6 * k + c] * po[k];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+      if (lane < 6) {
+        const float *Drow = Df + (long long)v * 36 + 6 * lane;
+        const float qc = acc[lane] + Drow[0] * pn[0] + Drow[1] * pn[1] + Drow[2] * pn[2] + Drow[3] * pn[3] +
+                         Drow[4] * pn[4] + Drow[5] * pn[5];
+        q[6 * v + lane] = qc;
+        pnew[6 * v + lane] = pn[lane];
+        lpq += (Acc)pn[lane] * (Acc)qc;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lpq += __shfl_xor_sync(0xffffffffu, lpq, o);
+    cta_partial(lpq, sh, ppq);
+    if (!grid_barrier(cs.count, cs.gen, gridDim.x, err)) return;
+    const Acc pq = grid_total(ppq, gridDim.x);
+    if (!(pq > (Acc)0)) {
+      flag |= 4;  // BF_FLAG_PCG_BREAKDOWN
+      break;
+    }
+    const Acc alpha = rz / pq;
+    // Phase B: x += alpha p_new, r -= alpha q, z = M^-1 r (own frames only, written by this warp)
+    Acc lrz = 0;
+    for (int v = v0 + gw; v < v1; v += nw) {
+      float rn[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) rn[k] = (float)((Acc)r[6 * v + k] - alpha * (Acc)q[6 * v + k]);
+      __syncwarp();
+      if (lane < 6) {
+        const float *M = Minv + (long long)v * 36 + 6 * lane;
+        const float zl = M[0] * rn[0] + M[1] * rn[1] + M[2] * rn[2] + M[3] * rn[3] + M[4] * rn[4] + M[5] * rn[5];
+        x[6 * v + lane] = (float)((Acc)x[6 * v + lane] + alpha * (Acc)pnew[6 * v + lane]);
+        r[6 * v + lane] = rn[lane];
+        z[6 * v + lane] = zl;
+        lrz += (Acc)rn[lane] * (Acc)zl;
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lrz += __shfl_xor_sync(0xffffffffu, lrz, o);
+    cta_partial(lrz, sh, prz);
+    if (!grid_barrier(cs.count, cs.gen, gridDim.x, err)) return;
+    const Acc rz_new = grid_total(prz, gridDim.x);
+    beta = rz_new / rz;
+    rz = rz_new;
+    float *tmp = pold;
+    pold = pnew;
+    pnew = tmp;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && pflags) pflags[0] |= flag;
+}
+
+int coop_max_grid() {
+  static int max_blocks = -1;
+  if (max_blocks < 0) {
+    int dev = 0, sms = 0, per_sm = 0, per_sm_f = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_coop<double>, COOP_BS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_pcg_coop<float>, COOP_BS, 0);
+    per_sm = per_sm < per_sm_f ? per_sm : per_sm_f;
+    max_blocks = sms * (per_sm < 1 ? 1 : per_sm);
+  }
+  return max_blocks;
+}
+
+int coop_grid_size(int n_vars) {
+  const int mx = coop_max_grid();
+  int want = (n_vars + COOP_WARPS - 1) / COOP_WARPS;
+  if (want < 1) want = 1;
+  return want < mx ? want : mx;
+}
+
+size_t coop_mem_bytes(int grid) { return 256 + 2 * 8 * (size_t)grid; }
+
+template <typename Acc>
+int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
+                    float *x, float *r, float *z, float *p0, float *p1, float *q, int n_pcg, int *pflags,
+                    void *coop_mem, int grid, cudaStream_t st) {
+  if (t.n_vars == 0) return 0;
+  CoopState cs;
+  char *m = (char *)coop_mem;
+  cs.count = (unsigned *)m;
+  cs.gen = (unsigned *)(m + 4);
+  cs.err = (int *)(m + 8);
+  cs.part_pq = m + 256;
+  cs.part_rz = m + 256 + 8 * (size_t)grid;
+  if (cudaMemsetAsync(m, 0, 16, st) != cudaSuccess) return -1;
+  Tables tt = t;
+  void *args[] = {&tt, &Df, &pairoff, &Minv, &rhs, &x, &r, &z, &p0, &p1, &q, &n_pcg, &pflags, &cs};
+  if (cudaLaunchCooperativeKernel((const void *)k_pcg_coop<Acc>, dim3(grid), dim3(COOP_BS), args, 0, st) !=
+      cudaSuccess)
+    return -1;
+  return 1;
+}
+template int launch_pcg_coop<double>(const Tables &, const float *, const float *, const float *, const double *,
+                                     float *, float *, float *, float *, float *, float *, int, int *, void *, int,
+                                     cudaStream_t);
+template int launch_pcg_coop<float>(const Tables &, const float *, const float *, const float *, const float *,
+                                    float *, float *, float *, float *, float *, float *, int, int *, void *, int,
+                                    cudaStream_t);
 
 // ----------------------------------------------------------------------------- pose update
 __global__ void k_update(int n_vars, const int *__restrict__ var_frame, const float *__restrict__ x,
@@ -454,27 +735,46 @@ __global__ void k_update(int n_vars, const int *__restrict__ var_frame, const fl
   T[11] += (double)x[6 * v + 5];
 }
 
-void launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st) {
-  if (t.n_vars == 0) return;
+int launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st) {
+  if (t.n_vars == 0) return 0;
   k_update<<<(t.n_vars + 127) / 128, 128, 0, st>>>(t.n_vars, t.var_frame, x, pose);
+  return 1;
 }
 
 // ------------------------------------------------------------------------- energy reduce
+constexpr int EN_BS = 256;
+
 template <typename Acc>
-__global__ void k_energy_reduce(Tables t, const Acc *__restrict__ pairen, double *__restrict__ out) {
+__global__ void __launch_bounds__(EN_BS) k_energy_reduce(Tables t, const Acc *__restrict__ pairen,
+                                                         double *__restrict__ out) {
+  __shared__ Acc sh[EN_BS / 32][PAIREN];
   const int prob = blockIdx.x;
-  if (threadIdx.x >= PAIREN) return;
-  Acc s = 0;
-  for (int p = t.prob_pair0[prob]; p < t.prob_pair1[prob]; ++p) s += pairen[(long long)p * PAIREN + threadIdx.x];
-  out[prob * PAIREN + threadIdx.x] = (double)s;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Acc s[PAIREN] = {0, 0, 0, 0};
+  for (int p = t.prob_pair0[prob] + threadIdx.x; p < t.prob_pair1[prob]; p += EN_BS)
+#pragma unroll
+    for (int k = 0; k < PAIREN; ++k) s[k] += pairen[(long long)p * PAIREN + k];
+#pragma unroll
+  for (int k = 0; k < PAIREN; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+    if (lane == 0) sh[warp][k] = s[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < PAIREN) {
+    Acc v = 0;
+    for (int w = 0; w < EN_BS / 32; ++w) v += sh[w][threadIdx.x];
+    out[prob * PAIREN + threadIdx.x] = (double)v;
+  }
 }
 
 template <typename Acc>
-void launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st) {
-  if (t.n_prob == 0) return;
-  k_energy_reduce<Acc><<<t.n_prob, 32, 0, st>>>(t, pairen, out);
+int launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st) {
+  if (t.n_prob == 0) return 0;
+  k_energy_reduce<Acc><<<t.n_prob, EN_BS, 0, st>>>(t, pairen, out);
+  return 1;
 }
-template void launch_energy_reduce<double>(const Tables &, const double *, double *, cudaStream_t);
-template void launch_energy_reduce<float>(const Tables &, const float *, double *, cudaStream_t);
+template int launch_energy_reduce<double>(const Tables &, const double *, double *, cudaStream_t);
+template int launch_energy_reduce<float>(const Tables &, const float *, double *, cudaStream_t);
 
 }  // namespace bf

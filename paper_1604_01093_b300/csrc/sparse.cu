@@ -162,18 +162,19 @@ __global__ void __launch_bounds__(SPARSE_BS)
 }
 
 template <typename Part>
-void launch_sparse(int mode, const Tables &t, const float4 *P, const float4 *Q, const float *pairM, float w_sparse,
+int launch_sparse(int mode, const Tables &t, const float4 *P, const float4 *Q, const float *pairM, float w_sparse,
                    Part *part, float *seg_rmax, int *seg_rarg, cudaStream_t st) {
-  if (t.n_segs == 0) return;
+  if (t.n_segs == 0) return 0;
   if (mode == MODE_ACCUM)
     k_sparse<MODE_ACCUM, Part><<<t.n_segs, SPARSE_BS, 0, st>>>(t, P, Q, pairM, w_sparse, part, seg_rmax, seg_rarg);
   else
     k_sparse<MODE_ENERGY, Part><<<t.n_segs, SPARSE_BS, 0, st>>>(t, P, Q, pairM, w_sparse, part, seg_rmax, seg_rarg);
+  return 1;
 }
 
-template void launch_sparse<float>(int, const Tables &, const float4 *, const float4 *, const float *, float, float *,
+template int launch_sparse<float>(int, const Tables &, const float4 *, const float4 *, const float *, float, float *,
                                    float *, int *, cudaStream_t);
-template void launch_sparse<double>(int, const Tables &, const float4 *, const float4 *, const float *, float,
+template int launch_sparse<double>(int, const Tables &, const float4 *, const float4 *, const float *, float,
                                     double *, float *, int *, cudaStream_t);
 
 }  // namespace bf

@@ -281,3 +281,42 @@ def test_hbm_budget_refuses(bf, cfg1):
     with pytest.raises(bf.BFError) as e:
         ctx.add_frames(0, cfg1.depth, cfg1.lum)
     assert e.value.status == 2
+
+
+def test_batch_correspondence_upload_equals_per_pair(bf, cfg1):
+    """bf_add_correspondences_batch (host and device inputs) == one bf_add_correspondences per pair."""
+    import torch
+    ref = make_ctx(bf, cfg1)
+    poses = perturb(cfg1.gt, 21)
+    ids = list(range(cfg1.n_frames))
+    a = ref.build_system(ids, poses)
+    pairs = cfg1.pairs.copy()
+    pairs[::2] = pairs[::2, ::-1]  # reversed order for half of the pairs: exercises the swap
+    pi, pj = cfg1.p_i.copy(), cfg1.p_j.copy()
+    for k in range(0, len(pairs), 2):
+        s = slice(cfg1.corr_off[k], cfg1.corr_off[k + 1])
+        pi[s], pj[s] = cfg1.p_j[s], cfg1.p_i[s]
+    for device in (False, True):
+        intr = cfg1.intr
+        ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"])
+        ctx.add_frames(0, cfg1.depth, cfg1.lum)
+        if device:
+            ctx.add_correspondences_batch(pairs, cfg1.corr_off, torch.from_numpy(pi).cuda(),
+                                          torch.from_numpy(pj).cuda())
+        else:
+            ctx.add_correspondences_batch(pairs, cfg1.corr_off, pi, pj)
+        b = ctx.build_system(ids, poses)
+        np.testing.assert_array_equal(a["A"], b["A"])
+        np.testing.assert_array_equal(a["b"], b["b"])
+
+
+def test_profiling_counts_launches(bf, cfg1):
+    ctx = make_ctx(bf, cfg1)
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    ctx.solve_local(0, list(range(11)), n_gn=2, n_pcg=4)
+    p = ctx.profile()
+    k = p["kernels"]
+    assert k["dense"]["count"] == 3 and k["pcg"]["count"] == 2 and k["update"]["count"] == 2
+    assert p["launches"] == sum(v["count"] for v in k.values())
+    assert k["dense"]["ms"] > 0
