@@ -102,7 +102,11 @@ typedef struct {
   int precision;            /* BF_PREC_*                                               */
   int use_graph;            /* replay the Gauss-Newton loop as a captured CUDA graph   */
   int tile_px;              /* source pixels per dense work item, 0 = autotuned        */
+  int pcg_variant;          /* BF_PCG_*: which PCG kernel runs (results agree to rounding) */
 } bf_solve_params;
+
+/* PCG kernels: AUTO picks CLUSTER for one large problem, else one CTA per problem. */
+enum { BF_PCG_AUTO = 0, BF_PCG_CTA = 1, BF_PCG_GRID = 2, BF_PCG_CLUSTER = 3 };
 
 #define BF_MAX_GN 64
 

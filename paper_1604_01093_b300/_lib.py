@@ -20,6 +20,7 @@ BF_STORE_FP32, BF_STORE_BF16, BF_STORE_FP16 = 0, 1, 2
 BF_PRECOND_BLOCK_JACOBI, BF_PRECOND_JACOBI = 0, 1
 BF_PREC_MIXED, BF_PREC_FP32 = 0, 1
 BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
+BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER = 0, 1, 2, 3
 BF_MAX_GN = 64
 BF_NPROF = 10
 KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack"]
@@ -42,7 +43,7 @@ class SolveParams(ctypes.Structure):
                 ("w_geo", ctypes.c_double), ("dense_ramp", ctypes.c_int), ("tau_dist", ctypes.c_double),
                 ("tau_normal", ctypes.c_double), ("max_angle_deg", ctypes.c_double), ("precond", ctypes.c_int),
                 ("dense_on", ctypes.c_int), ("warm_start", ctypes.c_int), ("precision", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int), ("pcg_variant", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):

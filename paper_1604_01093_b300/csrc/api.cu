@@ -609,7 +609,7 @@ struct HostTables {
   int n_frames = 0, n_pairs = 0, n_dp = 0, n_tiles = 0, n_segs = 0, n_vars = 0, n_prob = 0;
   std::vector<int> frame_slot, frame_var, pair_a, pair_b, pair_dp, pair_seg0, pair_seg1;
   std::vector<int> dp_src, dp_dst, dp_pair, dp_dir, dp_tile0, dp_tile1, tile_dp, tile_px0, tile_px1;
-  std::vector<int> seg_pair, seg_off, seg_cnt, seg_swap, inc_off, inc, var_frame;
+  std::vector<int> seg_pair, seg_off, seg_cnt, seg_swap, inc_off, inc, inc_ov, var_frame;
   std::vector<int> prob_var0, prob_var1, prob_pair0, prob_pair1, prob_frame0;
   std::vector<int> pair_ida, pair_idb;  // frame ids of the pair (for stats)
   std::vector<double> pose;             // n_frames x 12
@@ -729,7 +729,11 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
   T.inc_off.assign(T.n_vars + 1, 0);
   for (int v = 0; v < T.n_vars; ++v) T.inc_off[v + 1] = T.inc_off[v] + (int)var_inc[v].size();
   for (int v = 0; v < T.n_vars; ++v)
-    for (auto &e : var_inc[v]) T.inc.push_back(2 * e.first + e.second);
+    for (auto &e : var_inc[v]) {
+      T.inc.push_back(2 * e.first + e.second);
+      const int other = e.second == 0 ? T.pair_b[e.first] : T.pair_a[e.first];
+      T.inc_ov.push_back(T.frame_var[other]);
+    }
   return BF_OK;
 }
 
@@ -762,22 +766,37 @@ struct DevSolve {
   int *assoc;
   void *coop;      // cooperative PCG state (barrier, error flag, partials)
   int coop_grid;   // > 0: one large problem solved by the cooperative PCG
+  int cluster;     // > 0: one large problem solved on a thread-block cluster of this many CTAs
 };
 
 // The cooperative multi-CTA PCG serves single-problem solves with at least this many free frames.
 constexpr int COOP_MIN_VARS = 32;
 
-int coop_grid_for(const HostTables &T) {
-  return (T.n_prob == 1 && T.n_vars >= COOP_MIN_VARS) ? coop_grid_size(T.n_vars) : 0;
+// Cluster PCG (vectors replicated in shared memory) while the replicas fit.
+constexpr size_t CLUSTER_SMEM_MAX = 200 * 1024;
+
+int cluster_for(const HostTables &T, int variant) {
+  if (T.n_prob != 1 || T.n_vars == 0) return 0;
+  if (variant == BF_PCG_CTA || variant == BF_PCG_GRID) return 0;
+  if (variant == BF_PCG_AUTO && T.n_vars < COOP_MIN_VARS) return 0;
+  const int cl = cluster_size_max();
+  return cluster_smem_bytes(T.n_vars, cl) <= CLUSTER_SMEM_MAX ? cl : 0;
+}
+
+int coop_grid_for(const HostTables &T, int variant) {
+  if (T.n_prob != 1 || T.n_vars == 0 || variant == BF_PCG_CTA) return 0;
+  if (variant == BF_PCG_GRID) return coop_grid_size(T.n_vars);
+  if (variant == BF_PCG_AUTO && T.n_vars < COOP_MIN_VARS) return 0;
+  return cluster_for(T, variant) == 0 ? coop_grid_size(T.n_vars) : 0;
 }
 
 size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D, size_t acc_size, int HW,
-              bool want_assoc) {
+              bool want_assoc, int variant) {
   Arena a{base};
   int *ib = a.take<int>(n_int);
   double *pose = a.take<double>(T.n_frames * 12);
   float *pairM = a.take<float>((size_t)T.n_pairs * 24);
-  char *dpart = a.take<char>((size_t)T.n_tiles * NPART * acc_size);
+  char *dpart = a.take<char>((size_t)T.n_tiles * NPD * acc_size);
   char *spart = a.take<char>((size_t)T.n_segs * NPART * acc_size);
   float *srmax = a.take<float>(T.n_segs);
   int *srarg = a.take<int>(T.n_segs);
@@ -796,7 +815,7 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
   float *p = a.take<float>((size_t)T.n_vars * 6);
   float *q = a.take<float>((size_t)T.n_vars * 6);
   float *p1 = a.take<float>((size_t)T.n_vars * 6);
-  const int cg = coop_grid_for(T);
+  const int cg = coop_grid_for(T, variant);
   void *coop = a.take<char>(cg > 0 ? coop_mem_bytes(cg) : 256);
   double *energy = a.take<double>((size_t)(n_gn + 1) * T.n_prob * PAIREN);
   int *assoc = want_assoc ? a.take<int>(HW) : nullptr;
@@ -824,6 +843,7 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     D->p1 = p1;
     D->coop = coop;
     D->coop_grid = cg;
+    D->cluster = cluster_for(T, variant);
     D->energy = energy;
     D->assoc = assoc;
     // table pointers into ib, in the order of pack_ints
@@ -863,6 +883,7 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     t.seg_swap = nxt(T.seg_swap.size());
     t.inc_off = nxt(T.inc_off.size());
     t.inc = nxt(T.inc.size());
+    t.inc_ov = nxt(T.inc_ov.size());
     t.var_frame = nxt(T.var_frame.size());
     t.prob_var0 = nxt(T.prob_var0.size());
     t.prob_var1 = nxt(T.prob_var1.size());
@@ -877,16 +898,17 @@ std::vector<int> pack_ints(const HostTables &T) {
   for (const std::vector<int> *x :
        {&T.frame_slot, &T.frame_var, &T.pair_a, &T.pair_b, &T.pair_dp, &T.pair_seg0, &T.pair_seg1, &T.dp_src,
         &T.dp_dst, &T.dp_pair, &T.dp_dir, &T.dp_tile0, &T.dp_tile1, &T.tile_dp, &T.tile_px0, &T.tile_px1,
-        &T.seg_pair, &T.seg_off, &T.seg_cnt, &T.seg_swap, &T.inc_off, &T.inc, &T.var_frame, &T.prob_var0,
+        &T.seg_pair, &T.seg_off, &T.seg_cnt, &T.seg_swap, &T.inc_off, &T.inc, &T.inc_ov, &T.var_frame, &T.prob_var0,
         &T.prob_var1, &T.prob_pair0, &T.prob_pair1})
     v.insert(v.end(), x->begin(), x->end());
   return v;
 }
 
-bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, bool want_assoc, DevSolve &D) {
+bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, bool want_assoc, DevSolve &D,
+                  int variant = BF_PCG_AUTO) {
   const std::vector<int> ints = pack_ints(T);
   const int HW = c->cfg.width * c->cfg.height;
-  const size_t need = layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc) + 256;
+  const size_t need = layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc, variant) + 256;
   if (need > c->ws_bytes) {
     const size_t nb = std::max(need, c->ws_bytes * 3 / 2);
     CK(cudaStreamSynchronize(c->st), "workspace");
@@ -897,7 +919,7 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
     if (s) return s;
     c->ws_bytes = nb;
   }
-  layout(T, n_gn, ints.size(), c->ws, &D, acc_size, HW, want_assoc);
+  layout(T, n_gn, ints.size(), c->ws, &D, acc_size, HW, want_assoc, variant);
   if (!ints.empty())
     CK(cudaMemcpyAsync((void *)D.t.frame_slot, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, c->st),
        "upload tables");
@@ -948,6 +970,11 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
     });
     int pcg_rc = 0;
     run_k(c, BF_K_PCG, [&] {
+      if (D.cluster > 0) {
+        pcg_rc = launch_pcg_cluster<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, prm.n_pcg, D.pflags,
+                                         D.cluster, T.inc_off.data(), c->st);
+        return pcg_rc < 0 ? 0 : pcg_rc;
+      }
       if (D.coop_grid > 0) {
         pcg_rc = launch_pcg_coop<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.p1, D.q,
                                       prm.n_pcg, D.pflags, D.coop, D.coop_grid, c->st);
@@ -956,7 +983,7 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
       return launch_pcg<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.q, prm.n_pcg,
                              D.pflags, c->st);
     });
-    if (pcg_rc < 0) return cuda_fail(c, cudaGetLastError(), "cooperative PCG launch");
+    if (pcg_rc < 0) return cuda_fail(c, cudaGetLastError(), "PCG launch");
     run_k(c, BF_K_UPDATE, [&] { return launch_update(t, D.x, D.pose, c->st); });
   }
   const double wd = prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense;
@@ -979,6 +1006,8 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
   if (!(p->tau_dist > 0) || !std::isfinite(p->tau_normal) || !std::isfinite(p->max_angle_deg))
     return fail(c, BF_ERR_INVALID_ARG, "bad gates");
   if (p->tile_px < 0) return fail(c, BF_ERR_INVALID_ARG, "tile_px must be >= 0");
+  if (p->pcg_variant < BF_PCG_AUTO || p->pcg_variant > BF_PCG_CLUSTER)
+    return fail(c, BF_ERR_INVALID_ARG, "unknown pcg_variant");
   return BF_OK;
 }
 
@@ -992,7 +1021,7 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
   const bool mixed = prm.precision == BF_PREC_MIXED;
   const size_t acc_size = mixed ? sizeof(double) : sizeof(float);
   DevSolve D;
-  s = prepare(c, T, prm.n_gn, acc_size, false, D);
+  s = prepare(c, T, prm.n_gn, acc_size, false, D, prm.pcg_variant);
   if (s) return s;
   s = mixed ? run_gn<double>(c, T, prm, D) : run_gn<float>(c, T, prm, D);
   if (s) return s;

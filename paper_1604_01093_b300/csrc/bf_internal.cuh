@@ -39,6 +39,21 @@ enum : int {
   P_E1 = 55,  // dense: sum r_photo^2      sparse: 0
   P_CNT = 56  // dense: associated pixels  sparse: correspondences
 };
+// Dense partial sums of one tile (target-camera coordinates).  For both dense residuals the
+// source rotation Jacobian is a = v x t - c with t = t_ji the pair's translation in target
+// coordinates (geometric: a = n' x (t - q); photometric: a = (y - t) x g), so every sum that
+// involves a follows from the v / c sums and t; the pair merge rebuilds the NPART layout.
+constexpr int NPD = 30;
+enum : int {
+  D_VV = 0,   // sym 3x3 sum w v v^T
+  D_VC = 6,   // 3x3     sum w v c^T
+  D_CC = 15,  // sym 3x3 sum w c c^T
+  D_GV = 21,  // sum w r v
+  D_GC = 24,  // sum w r c
+  D_E0 = 27,  // sum r_geo^2
+  D_E1 = 28,  // sum r_photo^2
+  D_CNT = 29  // associated pixels
+};
 // Per-pair block record: A_aa, A_ab, A_bb (row-major 6x6), rhs_a, rhs_b (= -J^T W r).
 constexpr int PAIRBLK = 120;
 constexpr int PB_AA = 0, PB_AB = 36, PB_BB = 72, PB_RA = 108, PB_RB = 114;
@@ -73,6 +88,7 @@ struct Tables {
   const int *tile_dp, *tile_px0, *tile_px1;       // [n_tiles]
   const int *seg_pair, *seg_off, *seg_cnt, *seg_swap;  // [n_segs]
   const int *inc_off, *inc;         // [n_vars+1], entries 2*pair + side (side 0: var is a)
+  const int *inc_ov;                // [n_inc] var block of the pair's other frame, -1 for a gauge frame
   const int *var_frame;             // [n_vars]
   const int *prob_var0, *prob_var1, *prob_pair0, *prob_pair1;  // [n_prob]
 };
@@ -115,6 +131,13 @@ int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, cons
                     float *x, float *r, float *z, float *p0, float *p1, float *q, int n_pcg, int *pflags,
                     void *coop_mem, int grid, cudaStream_t st);
 int coop_grid_size(int n_vars);
+// One large problem on one thread-block cluster of cl CTAs (vectors replicated in shared memory).
+// Returns -1 if the launch was refused.
+template <typename Acc>
+int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
+                       float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, cudaStream_t st);
+size_t cluster_smem_bytes(int n_vars, int cl);
+int cluster_size_max();
 size_t coop_mem_bytes(int grid);
 int launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st);
 template <typename Acc>

@@ -5,9 +5,10 @@
 //
 // Work item = a tile of consecutive source pixels of one directed pair (i -> j).  Every
 // thread walks the tile with a block-sized stride (coalesced source reads), evaluates its
-// pixel entirely in registers and accumulates the 57 partial sums of the pair in FP32; the
-// CTA then reduces them by a fixed-order tree (warp shuffles, then warps in order) and writes
-// one record per tile.  Each run of sequential FP32 additions is at most ceil(tile/blockDim)
+// pixel entirely in registers and accumulates the pair's 30 partial sums in FP32 (only v / c
+// sums: the source rotation Jacobian a = v x t - c is rebuilt per pair by the merge); the CTA
+// then reduces them by a fixed-order tree (warp shuffles, then warps in order) and writes one
+// record per tile.  Each run of sequential FP32 additions is at most ceil(tile/blockDim)
 // long; everything above a tile is summed in FP64 (mixed precision) by the pair merge.
 //
 // The association decisions (target pixel, bilinear taps, validity, gates) are computed with
@@ -31,46 +32,29 @@ __device__ __forceinline__ V3 cross3(V3 a, V3 b) {
   return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
-// Accumulate one residual row (weight w, residual r, Jacobian [a, v, c, -v]) into acc.
-__device__ __forceinline__ void accum_row(float (&acc)[NPART], float w, float r, V3 a, V3 v, V3 c) {
-  const float wa0 = w * a.x, wa1 = w * a.y, wa2 = w * a.z;
+// Accumulate one dense residual row (weight w, residual r, Jacobian [v x t - c, v, c, -v]).
+__device__ __forceinline__ void accum_vc(float (&acc)[NPD], float w, float r, V3 v, V3 c) {
   const float wv0 = w * v.x, wv1 = w * v.y, wv2 = w * v.z;
   const float wc0 = w * c.x, wc1 = w * c.y, wc2 = w * c.z;
-  // sym a a^T
-  acc[P_AA + 0] += wa0 * a.x; acc[P_AA + 1] += wa0 * a.y; acc[P_AA + 2] += wa0 * a.z;
-  acc[P_AA + 3] += wa1 * a.y; acc[P_AA + 4] += wa1 * a.z; acc[P_AA + 5] += wa2 * a.z;
-  // a v^T
-  acc[P_AV + 0] += wa0 * v.x; acc[P_AV + 1] += wa0 * v.y; acc[P_AV + 2] += wa0 * v.z;
-  acc[P_AV + 3] += wa1 * v.x; acc[P_AV + 4] += wa1 * v.y; acc[P_AV + 5] += wa1 * v.z;
-  acc[P_AV + 6] += wa2 * v.x; acc[P_AV + 7] += wa2 * v.y; acc[P_AV + 8] += wa2 * v.z;
-  // sym v v^T
-  acc[P_VV + 0] += wv0 * v.x; acc[P_VV + 1] += wv0 * v.y; acc[P_VV + 2] += wv0 * v.z;
-  acc[P_VV + 3] += wv1 * v.y; acc[P_VV + 4] += wv1 * v.z; acc[P_VV + 5] += wv2 * v.z;
-  // a c^T
-  acc[P_AC + 0] += wa0 * c.x; acc[P_AC + 1] += wa0 * c.y; acc[P_AC + 2] += wa0 * c.z;
-  acc[P_AC + 3] += wa1 * c.x; acc[P_AC + 4] += wa1 * c.y; acc[P_AC + 5] += wa1 * c.z;
-  acc[P_AC + 6] += wa2 * c.x; acc[P_AC + 7] += wa2 * c.y; acc[P_AC + 8] += wa2 * c.z;
-  // v c^T
-  acc[P_VC + 0] += wv0 * c.x; acc[P_VC + 1] += wv0 * c.y; acc[P_VC + 2] += wv0 * c.z;
-  acc[P_VC + 3] += wv1 * c.x; acc[P_VC + 4] += wv1 * c.y; acc[P_VC + 5] += wv1 * c.z;
-  acc[P_VC + 6] += wv2 * c.x; acc[P_VC + 7] += wv2 * c.y; acc[P_VC + 8] += wv2 * c.z;
-  // sym c c^T
-  acc[P_CC + 0] += wc0 * c.x; acc[P_CC + 1] += wc0 * c.y; acc[P_CC + 2] += wc0 * c.z;
-  acc[P_CC + 3] += wc1 * c.y; acc[P_CC + 4] += wc1 * c.z; acc[P_CC + 5] += wc2 * c.z;
-  // J^T W r
-  acc[P_GA + 0] += r * wa0; acc[P_GA + 1] += r * wa1; acc[P_GA + 2] += r * wa2;
-  acc[P_GV + 0] += r * wv0; acc[P_GV + 1] += r * wv1; acc[P_GV + 2] += r * wv2;
-  acc[P_GC + 0] += r * wc0; acc[P_GC + 1] += r * wc1; acc[P_GC + 2] += r * wc2;
+  acc[D_VV + 0] += wv0 * v.x; acc[D_VV + 1] += wv0 * v.y; acc[D_VV + 2] += wv0 * v.z;
+  acc[D_VV + 3] += wv1 * v.y; acc[D_VV + 4] += wv1 * v.z; acc[D_VV + 5] += wv2 * v.z;
+  acc[D_VC + 0] += wv0 * c.x; acc[D_VC + 1] += wv0 * c.y; acc[D_VC + 2] += wv0 * c.z;
+  acc[D_VC + 3] += wv1 * c.x; acc[D_VC + 4] += wv1 * c.y; acc[D_VC + 5] += wv1 * c.z;
+  acc[D_VC + 6] += wv2 * c.x; acc[D_VC + 7] += wv2 * c.y; acc[D_VC + 8] += wv2 * c.z;
+  acc[D_CC + 0] += wc0 * c.x; acc[D_CC + 1] += wc0 * c.y; acc[D_CC + 2] += wc0 * c.z;
+  acc[D_CC + 3] += wc1 * c.y; acc[D_CC + 4] += wc1 * c.z; acc[D_CC + 5] += wc2 * c.z;
+  acc[D_GV + 0] += r * wv0; acc[D_GV + 1] += r * wv1; acc[D_GV + 2] += r * wv2;
+  acc[D_GC + 0] += r * wc0; acc[D_GC + 1] += r * wc1; acc[D_GC + 2] += r * wc2;
 }
 
-// Fixed-order CTA reduction of NPART values; thread k < NPART writes out[k].
-template <int BS, typename Part>
-__device__ __forceinline__ void cta_reduce_store(float (&acc)[NPART], Part *__restrict__ out) {
+// Fixed-order CTA reduction of N values; thread k < N writes out[k].
+template <int BS, int N, typename Part>
+__device__ __forceinline__ void cta_reduce_store(float (&acc)[N], Part *__restrict__ out) {
   constexpr int NW = BS / 32;
-  __shared__ float red[NW][NPART];
+  __shared__ float red[NW][N];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < NPART; ++k) {
+  for (int k = 0; k < N; ++k) {
     float v = acc[k];
     v += __shfl_xor_sync(0xffffffffu, v, 16);
     v += __shfl_xor_sync(0xffffffffu, v, 8);
@@ -80,7 +64,7 @@ __device__ __forceinline__ void cta_reduce_store(float (&acc)[NPART], Part *__re
     if (lane == 0) red[warp][k] = v;
   }
   __syncthreads();
-  if (threadIdx.x < NPART) {
+  if (threadIdx.x < N) {
     Part s = (Part)red[0][threadIdx.x];
 #pragma unroll
     for (int w = 1; w < NW; ++w) s += (Part)red[w][threadIdx.x];
@@ -91,7 +75,7 @@ __device__ __forceinline__ void cta_reduce_store(float (&acc)[NPART], Part *__re
 constexpr int DENSE_BS = 256;
 
 template <int MODE, typename Part>
-__global__ void __launch_bounds__(DENSE_BS, 2)
+__global__ void __launch_bounds__(DENSE_BS, 3)
     k_dense(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo, float w_photo,
             Part *__restrict__ part, int *__restrict__ assoc) {
   const int tile = blockIdx.x;
@@ -109,9 +93,9 @@ __global__ void __launch_bounds__(DENSE_BS, 2)
   const float fx = in.fx, fy = in.fy, cx = in.cx, cy = in.cy;
   const float Wm1 = (float)(W - 1), Hm1 = (float)(H - 1), Wm3 = (float)(W - 3), Hm3 = (float)(H - 3);
 
-  float acc[NPART];
+  float acc[NPD];
 #pragma unroll
-  for (int k = 0; k < NPART; ++k) acc[k] = 0.f;
+  for (int k = 0; k < NPD; ++k) acc[k] = 0.f;
 
   for (int px = px0 + threadIdx.x; px < px1; px += DENSE_BS) {
     int tgt = -1;
@@ -134,7 +118,16 @@ __global__ void __launch_bounds__(DENSE_BS, 2)
             byf >= 2.f && FA(byf, 1.f) <= Hm3) {
           const int tx = (int)nxf, ty = (int)nyf;
           const int tpx = ty * W + tx;
+          const int bx = (int)bxf, by = (int)byf;
+          // issue the target loads together: nearest (D, n) and the four (I, Ix, Iy) taps
           const float4 b = At[tpx];
+          float4 c00, c01, c10, c11;
+          if (MODE != MODE_ASSOC) {
+            c00 = Bt[by * W + bx];
+            c01 = Bt[by * W + bx + 1];
+            c10 = Bt[(by + 1) * W + bx];
+            c11 = Bt[(by + 1) * W + bx + 1];
+          }
           const bool tnvalid = (b.y != 0.f) || (b.z != 0.f) || (b.w != 0.f);
           if (b.x > 0.f && tnvalid) {
             const float qx = FM(fs.kx[tx], b.x), qy = FM(fs.ky[ty], b.x), qz = b.x;
@@ -148,33 +141,26 @@ __global__ void __launch_bounds__(DENSE_BS, 2)
               tgt = tpx;
               if (MODE != MODE_ASSOC) {
                 // ---- residuals and Jacobians (free FP32) in camera-j coordinates ----
-                const V3 m{m0, m1, m2}, e{ex, ey, ez}, q{qx, qy, qz}, Yv{Y0, Y1, Y2};
-                const V3 Rd{Y0 - t0, Y1 - t1, Y2 - t2};  // R_ji d
                 const float r_g = m0 * ex + m1 * ey + m2 * ez;
-                // bilinear taps of (I, Ix, Iy)
-                const int bx = (int)bxf, by = (int)byf;
                 const float wx = ux - bxf, wy = uy - byf;
-                const float4 c00 = Bt[by * W + bx], c01 = Bt[by * W + bx + 1];
-                const float4 c10 = Bt[(by + 1) * W + bx], c11 = Bt[(by + 1) * W + bx + 1];
                 const float w00 = (1.f - wx) * (1.f - wy), w01 = wx * (1.f - wy);
                 const float w10 = (1.f - wx) * wy, w11 = wx * wy;
                 const float Ij = w00 * c00.x + w01 * c01.x + w10 * c10.x + w11 * c11.x;
                 const float gxI = w00 * c00.y + w01 * c01.y + w10 * c10.y + w11 * c11.y;
                 const float gyI = w00 * c00.z + w01 * c01.z + w10 * c10.z + w11 * c11.z;
                 const float r_p = Bs[px].x - Ij;
-                acc[P_E0] += r_g * r_g;
-                acc[P_E1] += r_p * r_p;
-                acc[P_CNT] += 1.f;
+                acc[D_E0] += r_g * r_g;
+                acc[D_E1] += r_p * r_p;
+                acc[D_CNT] += 1.f;
                 if (MODE == MODE_ACCUM) {
-                  // geometric: v = m, a = m x e + (R d) x m, c = m x q
-                  const V3 mxe = cross3(m, e), rdxm = cross3(Rd, m);
-                  const V3 ag{mxe.x + rdxm.x, mxe.y + rdxm.y, mxe.z + rdxm.z};
-                  accum_row(acc, w_geo, r_g, ag, m, cross3(m, q));
-                  // photometric: g = d r_p / d y = -grad I^T Jpi(y); v = g, a = (R d) x g, c = g x y
+                  // geometric: v = m, c = m x q
+                  const V3 m{m0, m1, m2}, q{qx, qy, qz};
+                  accum_vc(acc, w_geo, r_g, m, cross3(m, q));
+                  // photometric: v = g = d r_p / d y = -grad I^T Jpi(y), c = g x y
                   const float iz = 1.f / Y2;
                   const float gfx = gxI * fx * iz, gfy = gyI * fy * iz;
                   const V3 gv{-gfx, -gfy, (gfx * Y0 + gfy * Y1) * iz};
-                  accum_row(acc, w_photo, r_p, cross3(Rd, gv), gv, cross3(gv, Yv));
+                  accum_vc(acc, w_photo, r_p, gv, cross3(gv, V3{Y0, Y1, Y2}));
                 }
               }
             }
@@ -184,7 +170,7 @@ __global__ void __launch_bounds__(DENSE_BS, 2)
     }
     if (MODE == MODE_ASSOC) assoc[px] = tgt;
   }
-  if (MODE != MODE_ASSOC) cta_reduce_store<DENSE_BS, Part>(acc, part + (long long)tile * NPART);
+  if (MODE != MODE_ASSOC) cta_reduce_store<DENSE_BS, NPD, Part>(acc, part + (long long)tile * NPD);
 }
 
 template <typename Part>

@@ -16,7 +16,17 @@
 // The paper's solver (Sec. 4.4) sums the PCG scalars with warp shuffles plus global atomics in a
 // single kernel; here every dot product is reduced in a fixed order (warp tree, then CTA
 // partials summed in index order by every CTA) so results do not depend on scheduling.
+// Precision (mixed mode): vectors and their element-wise updates are FP32; a dot product's
+// products are summed in FP32 within a warp (a 32-term tree) and everything above the warp,
+// plus alpha and beta, in FP64.  B300 issues FP64 at 1/64 of the FP32 rate, so per-element
+// FP64 arithmetic would dominate these latency-bound kernels.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
 #include "bf_internal.cuh"
+
+namespace cgx = cooperative_groups;
 
 namespace bf {
 
@@ -161,14 +171,76 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
       base = spart;
       if (k1 <= k0) continue;
     }
-    // sum the work items' partials (fixed order)
-    for (int k = lane; k < NPART; k += 32) {
-      Acc s = 0;
-      for (int it = k0; it < k1; ++it) s += (Acc)base[(long long)it * NPART + k];
-      S[k] = s;
-    }
     const int tgt = (src == 1) ? t.pair_a[p] : t.pair_b[p];
+    const int srcf = (src == 1) ? t.pair_b[p] : t.pair_a[p];
     if (lane < 9) R[lane] = (Acc)pose[12 * tgt + lane];
+    if (src < 2) {
+      // dense: sum the tiles' v / c sums (fixed order), then rebuild the a-sums with
+      // a = T v - c, T v = v x t, t = t_ji = R_j^T (t_i - t_j)
+      Acc *Sd = rot;  // scratch for the NPD sums
+      for (int k = lane; k < NPD; k += 32) {
+        Acc s = 0;
+        for (int it = k0; it < k1; ++it) s += (Acc)base[(long long)it * NPD + k];
+        Sd[k] = s;
+      }
+      __syncwarp();
+      Acc tt[3];
+      {
+        const double *Ti = pose + 12 * srcf, *Tj = pose + 12 * tgt;
+        const double d0 = Ti[9] - Tj[9], d1 = Ti[10] - Tj[10], d2 = Ti[11] - Tj[11];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) tt[m] = (Acc)(Tj[m] * d0 + Tj[3 + m] * d1 + Tj[6 + m] * d2);
+      }
+      const Acc T3[3][3] = {{0, tt[2], -tt[1]}, {-tt[2], 0, tt[0]}, {tt[1], -tt[0], 0}};
+      // copy the v / c sums into the NPART layout
+      for (int k = lane; k < 6; k += 32) {
+        S[P_VV + k] = Sd[D_VV + k];
+        S[P_CC + k] = Sd[D_CC + k];
+      }
+      for (int k = lane; k < 9; k += 32) S[P_VC + k] = Sd[D_VC + k];
+      if (lane < 3) {
+        S[P_GV + lane] = Sd[D_GV + lane];
+        S[P_GC + lane] = Sd[D_GC + lane];
+      }
+      if (lane == 0) {
+        S[P_E0] = Sd[D_E0];
+        S[P_E1] = Sd[D_E1];
+        S[P_CNT] = Sd[D_CNT];
+      }
+      __syncwarp();
+      // S_av = T S_vv - S_vc^T ; S_ac = T S_vc - S_cc ; g_a = T g_v - g_c
+      if (lane < 9) {
+        const int i = lane / 3, j = lane % 3;
+        Acc av = -S[P_VC + 3 * j + i], ac = -S[part_index(5, i, j)];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          av += T3[i][k] * S[part_index(2, k, j)];
+          ac += T3[i][k] * S[P_VC + 3 * k + j];
+        }
+        S[P_AV + lane] = av;
+        S[P_AC + lane] = ac;
+      } else if (lane < 12) {
+        const int i = lane - 9;
+        S[P_GA + i] = T3[i][0] * S[P_GV] + T3[i][1] * S[P_GV + 1] + T3[i][2] * S[P_GV + 2] - S[P_GC + i];
+      }
+      __syncwarp();
+      // S_aa = S_av T^T - S_ac (symmetric; upper triangle)
+      if (lane < 6) {
+        const int i = lane < 3 ? 0 : (lane < 5 ? 1 : 2);
+        const int j = lane < 3 ? lane : (lane < 5 ? lane - 2 : 2);
+        Acc aa = -S[P_AC + 3 * i + j];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) aa += S[P_AV + 3 * i + k] * T3[j][k];
+        S[P_AA + lane] = aa;
+      }
+    } else {
+      // sparse: full NPART sums per segment (fixed order)
+      for (int k = lane; k < NPART; k += 32) {
+        Acc s = 0;
+        for (int it = k0; it < k1; ++it) s += (Acc)base[(long long)it * NPART + k];
+        S[k] = s;
+      }
+    }
     __syncwarp();
     // rotate to world: blocks R X R^T, vectors R g
     for (int e = lane; e < NROT; e += 32) {
@@ -349,13 +421,14 @@ template int launch_assemble<float>(const Tables &, const float *, int, float *,
 // ------------------------------------------------------------------------ PCG, one CTA/problem
 constexpr int PCG_BS = 256;
 
+// Block sum: FP32 warp tree, then the warps' sums in Acc, fixed order; same value in every thread.
 template <typename Acc>
-__device__ __forceinline__ Acc cta_sum(Acc v, Acc *sh) {
+__device__ __forceinline__ Acc cta_sum(float v, Acc *sh) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();  // protect sh from a previous use
-  if (lane == 0) sh[warp] = v;
+  if (lane == 0) sh[warp] = (Acc)v;
   __syncthreads();
   Acc s = 0;
 #pragma unroll
@@ -385,18 +458,18 @@ __global__ void __launch_bounds__(PCG_BS)
     r[u] = (float)rhs[u];
   }
   __syncthreads();
-  Acc loc = 0;
+  float loc = 0.f;
   for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
     const float zu = precond_row(Minv, r, u / 6, u % 6);
     z[u] = zu;
     p[u] = zu;
-    loc += (Acc)r[u] * (Acc)zu;
+    loc += r[u] * zu;
   }
   Acc rz = cta_sum(loc, sh);
   int flag = 0;
   for (int it = 0; it < n_pcg; ++it) {
     if (rz == (Acc)0) break;
-    loc = 0;
+    loc = 0.f;
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
       const int v = u / 6, c = u % 6;
       const float *Drow = Df + (long long)v * 36 + 6 * c;
@@ -404,11 +477,10 @@ __global__ void __launch_bounds__(PCG_BS)
       float s = Drow[0] * pv[0] + Drow[1] * pv[1] + Drow[2] * pv[2] + Drow[3] * pv[3] + Drow[4] * pv[4] +
                 Drow[5] * pv[5];
       for (int e = t.inc_off[v]; e < t.inc_off[v + 1]; ++e) {
+        const int ov = t.inc_ov[e];
+        if (ov < 0) continue;
         const int ent = t.inc[e];
         const int pr = ent >> 1, side = ent & 1;
-        const int other = side == 0 ? t.pair_b[pr] : t.pair_a[pr];
-        const int ov = t.frame_var[other];
-        if (ov < 0) continue;
         const float *O = pairoff + (long long)pr * 36;
         const float *po = p + 6LL * ov;
         if (side == 0) {  // row of A_ab
@@ -420,29 +492,29 @@ __global__ void __launch_bounds__(PCG_BS)
         }
       }
       q[u] = s;
-      loc += (Acc)p[u] * (Acc)s;
+      loc += p[u] * s;
     }
     const Acc pq = cta_sum(loc, sh);
     if (!(pq > (Acc)0)) {
       flag |= 4;  // BF_FLAG_PCG_BREAKDOWN
       break;
     }
-    const Acc alpha = rz / pq;
+    const float fa = (float)(rz / pq);
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
-      x[u] = (float)((Acc)x[u] + alpha * (Acc)p[u]);
-      r[u] = (float)((Acc)r[u] - alpha * (Acc)q[u]);
+      x[u] += fa * p[u];
+      r[u] -= fa * q[u];
     }
     __syncthreads();
-    loc = 0;
+    loc = 0.f;
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
       const float zu = precond_row(Minv, r, u / 6, u % 6);
       z[u] = zu;
-      loc += (Acc)r[u] * (Acc)zu;
+      loc += r[u] * zu;
     }
     const Acc rz_new = cta_sum(loc, sh);
-    const Acc beta = rz_new / rz;
+    const float fb = (float)(rz_new / rz);
     rz = rz_new;
-    for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) p[u] = (float)((Acc)z[u] + beta * (Acc)p[u]);
+    for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) p[u] = z[u] + fb * p[u];
     __syncthreads();
   }
   if (threadIdx.x == 0 && pflags) pflags[prob] |= flag;
@@ -463,8 +535,10 @@ template int launch_pcg<float>(const Tables &, const float *, const float *, con
 // ------------------------------------------------------------- PCG, one problem over the grid
 constexpr int COOP_BS = 256;
 constexpr int COOP_WARPS = COOP_BS / 32;
-// Spin limit of the grid barrier: ~2^22 polls with a 256 ns back-off, i.e. about a second.
-constexpr long long BARRIER_SPIN_LIMIT = 1LL << 22;
+// Spin limit of the grid barrier: 2^24 polls, the first 2^12 without back-off, the rest with a
+// 64 ns back-off: about a second in all.
+constexpr long long BARRIER_SPIN_LIMIT = 1LL << 24;
+constexpr long long BARRIER_SPIN_FAST = 1LL << 12;
 
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  count/gen live in global
 // memory and start at 0.  A CTA whose wait exceeds the spin limit sets *err and returns false;
@@ -493,7 +567,7 @@ __device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned n
           ok = 0;
           break;
         }
-        __nanosleep(256);
+        if (spins > BARRIER_SPIN_FAST) __nanosleep(64);
       }
     }
     __threadfence();
@@ -510,10 +584,15 @@ struct CoopState {
   void *part_rz;  // [gridDim.x] Acc
 };
 
+// Sum of the per-CTA partials in a fixed order: lane l sums entries l, l+32, ... then a
+// butterfly over the warp; every warp of every CTA computes the identical value.
 template <typename Acc>
 __device__ __forceinline__ Acc grid_total(const Acc *part, int n) {
+  const int lane = threadIdx.x & 31;
   Acc s = 0;
-  for (int k = 0; k < n; ++k) s += __ldcg(part + k);
+  for (int k = lane; k < n; k += 32) s += __ldcg(part + k);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   return s;
 }
 
@@ -578,10 +657,10 @@ __global__ void __launch_bounds__(COOP_BS)
       for (int k = 0; k < 6; ++k) pn[k] = __ldcg(z + 6 * v + k) + fb * __ldcg(pold + 6 * v + k);
       float acc[6] = {0, 0, 0, 0, 0, 0};
       for (int e = t.inc_off[v] + lane; e < t.inc_off[v + 1]; e += 32) {
+        const int ov = t.inc_ov[e];
+        if (ov < 0) continue;
         const int ent = t.inc[e];
         const int pr = ent >> 1, side = ent & 1;
-        const int ov = t.frame_var[side == 0 ? t.pair_b[pr] : t.pair_a[pr]];
-        if (ov < 0) continue;
         float po[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) po[k] = __ldcg(z + 6 * ov + k) + fb * __ldcg(pold + 6 * ov + k);
@@ -776,5 +855,347 @@ int launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaSt
 }
 template int launch_energy_reduce<double>(const Tables &, const double *, double *, cudaStream_t);
 template int launch_energy_reduce<float>(const Tables &, const float *, double *, cudaStream_t);
+
+// ------------------------------------------------------ PCG, one problem on a thread-block cluster
+// One cluster of CL CTAs (up to 16, one per SM) solves one problem.  Every CTA keeps replicas of
+// the full z and p vectors in its shared memory; a CTA owns a contiguous range of frames and
+// broadcasts its frames' new z and p into every replica through distributed shared memory.
+// Two hardware cluster barriers per iteration separate the phases, and the per-CTA dot-product
+// partials are read from the other CTAs' shared memory and summed in rank order.
+constexpr int CL_BS = 512;
+constexpr int CL_WARPS = CL_BS / 32;
+
+// Sum of the CL per-CTA partials (slot k of each CTA's part array), read lane-parallel from the
+// cluster's shared memory and combined by a butterfly: identical in every lane of every CTA.
+template <typename Acc>
+__device__ __forceinline__ Acc cluster_total(cgx::cluster_group &cluster, Acc *part, int k, int CL) {
+  const int lane = threadIdx.x & 31;
+  Acc s = lane < CL ? cluster.map_shared_rank(part, lane)[k] : (Acc)0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+// Fixed-order CTA sum of one value per warp (lane 0 holds it) into part[k].
+template <typename Acc>
+__device__ __forceinline__ void cluster_partial(Acc v, Acc *wsum, Acc *part, int k) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Acc s = 0;
+    for (int w = 0; w < CL_WARPS; ++w) s += wsum[w];
+    part[k] = s;
+  }
+}
+
+// Shared-memory layout of one CTA (floats unless noted), per = frames owned per CTA:
+//   zp[per][12]              owned frames' z and p (interleaved: 3 float4 per frame); the other
+//                            CTAs read them remotely through distributed shared memory
+//   ox, orr, oq, opn [6 per] owned frames' x, r, q, p_new
+//   part (2 Acc)             pq, rz partials
+//   cache (optional):  sD[per][36] sM[per][36] sB[n_inc][36] sov[n_inc] (int: owner << 16 | index)
+//     sB = the pair's off-diagonal block as seen from the owned frame (A_ab, or A_ab^T)
+struct ClusterLayout {
+  int per, max_inc;
+  bool cache;
+};
+
+__host__ __device__ inline size_t cluster_bytes(int n_vars, int per, int max_inc, bool cache) {
+  (void)n_vars;
+  size_t b = (size_t)per * 12 * 4 + 4 * 6 * (size_t)per * 4;
+  b = (b + 15) & ~(size_t)15;
+  b += 2 * sizeof(double);
+  if (cache) b += (size_t)per * 72 * 4 + (size_t)max_inc * 37 * 4;
+  return b + 16;
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(CL_BS, 1)
+    k_pcg_cluster(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff,
+                  const float *__restrict__ Minv, const Acc *__restrict__ rhs, float *__restrict__ xg, int n_pcg,
+                  int *__restrict__ pflags, ClusterLayout L) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ const float4 *zp_rank[16];
+  cgx::cluster_group cluster = cgx::this_cluster();
+  const int rank = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int v0 = t.prob_var0[0], v1 = t.prob_var1[0];
+  const int nv = v1 - v0;
+  const int per = L.per;
+  const int o0 = min(nv, rank * per), o1 = min(nv, o0 + per);  // owned local var range
+  const int no = o1 - o0;
+  float *zp = (float *)smem_raw;
+  float *ox = zp + 12 * per;
+  float *orr = ox + 6 * per;
+  float *oq = orr + 6 * per;
+  float *opn = oq + 6 * per;
+  Acc *part = (Acc *)(((uintptr_t)(opn + 6 * per) + 15) & ~(uintptr_t)15);
+  float *sD = (float *)(part + 2);
+  float *sM = sD + 36 * per;
+  float *sB = sM + 36 * per;
+  int *sov = (int *)(sB + 36 * (size_t)L.max_inc);
+  __shared__ Acc wsum[CL_WARPS];
+  const int e_base = t.inc_off[v0 + o0];
+  if (threadIdx.x < CL) zp_rank[threadIdx.x] = (const float4 *)cluster.map_shared_rank(zp, (int)threadIdx.x);
+  if (L.cache) {
+    for (int u = threadIdx.x; u < 36 * no; u += CL_BS) {
+      sD[u] = Df[(long long)(v0 + o0) * 36 + u];
+      sM[u] = Minv[(long long)(v0 + o0) * 36 + u];
+    }
+    const int n_inc = t.inc_off[v0 + o1] - e_base;
+    for (int u = threadIdx.x; u < 36 * n_inc; u += CL_BS) {
+      const int e = u / 36, k = u % 36;
+      const int ent = t.inc[e_base + e];
+      const int pr = ent >> 1, side = ent & 1;
+      const int c = k / 6, j = k % 6;
+      sB[u] = side == 0 ? pairoff[(long long)pr * 36 + 6 * c + j] : pairoff[(long long)pr * 36 + 6 * j + c];
+    }
+    for (int e = threadIdx.x; e < n_inc; e += CL_BS) {
+      const int ov = t.inc_ov[e_base + e];
+      const int lo = ov - v0;
+      sov[e] = ov < 0 ? -1 : (((lo / per) << 16) | (lo % per));
+    }
+  }
+  // Frames are processed by 8-lane groups: group g of a warp owns frame base + g; within a group
+  // lane gl walks the frame's incidences gl, gl+8, ... and lanes gl < 6 own the frame's 6 rows.
+  const int g = lane >> 3, gl = lane & 7;
+  // init: x = 0, r = b, z = M^-1 r, p = 0 for owned frames
+  float loc = 0.f;
+  for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
+    const int lv = base + g;
+    const bool valid = lv < o1;
+    const int v = v0 + lv, k = lv - o0;
+    const float rown = (valid && gl < 6) ? (float)rhs[6 * v + gl] : 0.f;
+    float rr[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) rr[c] = __shfl_sync(0xffffffffu, rown, (lane & ~7) + c);
+    if (valid && gl < 6) {
+      const float *M = L.cache ? sM + 36 * k + 6 * gl : Minv + (long long)v * 36 + 6 * gl;
+      const float zl = M[0] * rr[0] + M[1] * rr[1] + M[2] * rr[2] + M[3] * rr[3] + M[4] * rr[4] + M[5] * rr[5];
+      ox[6 * k + gl] = 0.f;
+      orr[6 * k + gl] = rr[gl];
+      zp[12 * k + gl] = zl;
+      zp[12 * k + 6 + gl] = 0.f;
+      loc += rr[gl] * zl;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
+  cluster_partial((Acc)loc, wsum, part, 1);
+  cluster.sync();  // all CTAs running, owned z / p initialised
+  Acc rz = cluster_total(cluster, part, 1, CL);
+  Acc beta = 0;
+  int flag = 0;
+  for (int it = 0; it < n_pcg; ++it) {
+    if (rz == (Acc)0) break;
+    const float fb = (float)beta;
+    // Phase A: p_new = z + beta p (owned, kept in opn); q = A p_new, neighbours read remotely
+    float lpq = 0.f;
+    for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
+      const int lv = base + g;
+      const bool valid = lv < o1;
+      const int v = v0 + lv, k = lv - o0;
+      float acc[6] = {0, 0, 0, 0, 0, 0};
+      if (valid) {
+        const int e0 = t.inc_off[v], e1 = t.inc_off[v + 1];
+        for (int e = e0 + gl; e < e1; e += 8) {
+          int owner, idx;
+          const float *B;
+          bool trans = false;
+          if (L.cache) {
+            const int so = sov[e - e_base];
+            if (so < 0) continue;
+            owner = so >> 16;
+            idx = so & 0xffff;
+            B = sB + 36 * (e - e_base);
+          } else {
+            const int ov = t.inc_ov[e];
+            if (ov < 0) continue;
+            const int lo = ov - v0;
+            owner = lo / per;
+            idx = lo - owner * per;
+            const int ent = t.inc[e];
+            B = pairoff + (long long)(ent >> 1) * 36;
+            trans = (ent & 1) != 0;
+          }
+          const float4 *src = zp_rank[owner] + 3 * idx;
+          const float4 q0 = src[0], q1 = src[1], q2 = src[2];  // z0..z5 p0..p5
+          float po[6];
+          po[0] = q0.x + fb * q1.z;
+          po[1] = q0.y + fb * q1.w;
+          po[2] = q0.z + fb * q2.x;
+          po[3] = q0.w + fb * q2.y;
+          po[4] = q1.x + fb * q2.z;
+          po[5] = q1.y + fb * q2.w;
+          if (!trans) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+              for (int j = 0; j < 6; ++j) acc[c] += B[6 * c + j] * po[j];
+          } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+#pragma unroll
+              for (int j = 0; j < 6; ++j) acc[c] += B[6 * j + c] * po[j];
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 4);
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
+        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+      }
+      if (valid && gl < 6) {
+        float mine = acc[0];
+#pragma unroll
+        for (int c = 1; c < 6; ++c) mine = (gl == c) ? acc[c] : mine;
+        float pn[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) pn[c] = zp[12 * k + c] + fb * zp[12 * k + 6 + c];
+        const float *Drow = L.cache ? sD + 36 * k + 6 * gl : Df + (long long)v * 36 + 6 * gl;
+        const float qc = mine + Drow[0] * pn[0] + Drow[1] * pn[1] + Drow[2] * pn[2] + Drow[3] * pn[3] +
+                         Drow[4] * pn[4] + Drow[5] * pn[5];
+        float pmine = pn[0];
+#pragma unroll
+        for (int c = 1; c < 6; ++c) pmine = (gl == c) ? pn[c] : pmine;
+        oq[6 * k + gl] = qc;
+        opn[6 * k + gl] = pmine;
+        lpq += pmine * qc;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lpq += __shfl_xor_sync(0xffffffffu, lpq, o);
+    cluster_partial((Acc)lpq, wsum, part, 0);
+    cluster.sync();  // every CTA has finished reading the old z / p
+    const Acc pq = cluster_total(cluster, part, 0, CL);
+    if (!(pq > (Acc)0)) {
+      flag |= 4;  // BF_FLAG_PCG_BREAKDOWN
+      break;
+    }
+    const Acc alpha = rz / pq;
+    const float fa = (float)alpha;
+    // Phase B (local): x += alpha p_new, r -= alpha q, z = M^-1 r, p = p_new
+    float lrz = 0.f;
+    for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
+      const int lv = base + g;
+      const bool valid = lv < o1;
+      const int v = v0 + lv, k = lv - o0;
+      const float rn_own = (valid && gl < 6) ? orr[6 * k + gl] - fa * oq[6 * k + gl] : 0.f;
+      float rn[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) rn[c] = __shfl_sync(0xffffffffu, rn_own, (lane & ~7) + c);
+      if (valid && gl < 6) {
+        const float *M = L.cache ? sM + 36 * k + 6 * gl : Minv + (long long)v * 36 + 6 * gl;
+        const float zl = M[0] * rn[0] + M[1] * rn[1] + M[2] * rn[2] + M[3] * rn[3] + M[4] * rn[4] + M[5] * rn[5];
+        const float pl = opn[6 * k + gl];
+        ox[6 * k + gl] += fa * pl;
+        orr[6 * k + gl] = rn_own;
+        zp[12 * k + gl] = zl;
+        zp[12 * k + 6 + gl] = pl;
+        lrz += rn_own * zl;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lrz += __shfl_xor_sync(0xffffffffu, lrz, o);
+    cluster_partial((Acc)lrz, wsum, part, 1);
+    cluster.sync();  // the new z / p are visible cluster-wide
+    const Acc rz_new = cluster_total(cluster, part, 1, CL);
+    beta = rz_new / rz;
+    rz = rz_new;
+  }
+  // write the owned part of the solution
+  __syncthreads();
+  for (int u = threadIdx.x; u < 6 * no; u += CL_BS) xg[6 * (v0 + o0) + u] = ox[u];
+  if (rank == 0 && threadIdx.x == 0 && pflags) pflags[0] |= flag;
+  cluster.sync();  // keep every CTA's shared memory alive until remote reads are done
+}
+
+// Largest supported cluster (16 if the device allows non-portable sizes, else 8).
+static int g_cluster_max = -1;
+void cluster_size_override(int cl) { g_cluster_max = cl; }
+int cluster_size_max() {
+  int &cl = g_cluster_max;
+  if (cl < 0) {
+    cl = 0;
+    if (cudaFuncSetAttribute(k_pcg_cluster<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_pcg_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess)
+      cl = 16;
+    else
+      cl = 8;
+    cudaGetLastError();
+  }
+  return cl;
+}
+
+constexpr size_t CLUSTER_SMEM_LIMIT = 220 * 1024;
+
+// Shared-memory plan for n_vars frames on cl CTAs; inc_off is the host copy of the incidence
+// offsets (nullptr: no cache).  Returns 0 if even the replicas do not fit.
+static ClusterLayout cluster_layout(int n_vars, int cl, const int *inc_off, size_t *bytes) {
+  ClusterLayout L;
+  L.per = (n_vars + cl - 1) / cl;
+  L.max_inc = 0;
+  L.cache = false;
+  if (inc_off) {
+    for (int r = 0; r < cl; ++r) {
+      const int a = std::min(n_vars, r * L.per), b = std::min(n_vars, a + L.per);
+      L.max_inc = std::max(L.max_inc, inc_off[b] - inc_off[a]);
+    }
+    L.cache = cluster_bytes(n_vars, L.per, L.max_inc, true) <= CLUSTER_SMEM_LIMIT;
+  }
+  *bytes = cluster_bytes(n_vars, L.per, L.max_inc, L.cache);
+  return L;
+}
+
+size_t cluster_smem_bytes(int n_vars, int cl) {
+  size_t b;
+  cluster_layout(n_vars, cl, nullptr, &b);
+  return b;
+}
+
+template <typename Acc>
+int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
+                       float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, cudaStream_t st) {
+  if (t.n_vars == 0) return 0;
+  size_t smem = 0;
+  const ClusterLayout L = cluster_layout(t.n_vars, cl, inc_off_host, &smem);
+  static size_t smem_set[2] = {0, 0};
+  size_t &cur = smem_set[sizeof(Acc) == 8 ? 1 : 0];
+  if (smem > cur) {
+    if (cudaFuncSetAttribute(k_pcg_cluster<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CLUSTER_SMEM_LIMIT) !=
+        cudaSuccess)
+      return -1;
+    cur = CLUSTER_SMEM_LIMIT;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cl);
+  cfg.blockDim = dim3(CL_BS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_pcg_cluster<Acc>, t, Df, pairoff, Minv, rhs, x, n_pcg, pflags, L) != cudaSuccess) {
+    cudaGetLastError();
+    if (cl <= 8) return -1;
+    // the device refused the non-portable size: use the portable maximum from now on
+    cluster_size_override(8);
+    return launch_pcg_cluster<Acc>(t, Df, pairoff, Minv, rhs, x, n_pcg, pflags, 8, inc_off_host, st);
+  }
+  return 1;
+}
+template int launch_pcg_cluster<double>(const Tables &, const float *, const float *, const float *, const double *,
+                                        float *, int, int *, int, const int *, cudaStream_t);
+template int launch_pcg_cluster<float>(const Tables &, const float *, const float *, const float *, const float *,
+                                       float *, int, int *, int, const int *, cudaStream_t);
 
 }  // namespace bf

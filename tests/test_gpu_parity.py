@@ -320,3 +320,20 @@ def test_profiling_counts_launches(bf, cfg1):
     assert k["dense"]["count"] == 3 and k["pcg"]["count"] == 2 and k["update"]["count"] == 2
     assert p["launches"] == sum(v["count"] for v in k.values())
     assert k["dense"]["ms"] > 0
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3])
+def test_pcg_variants_agree(bf, small_global, variant):
+    """Per-problem CTA, grid-cooperative and cluster PCG kernels solve the same system to rounding."""
+    prob = small_global
+    n = prob.n_frames
+    ctx = make_ctx(bf, prob)
+    ref = ctx.solve_global(list(range(n)), n_gn=2, n_pcg=15, pcg_variant=1)
+    P_ref = ctx.get_poses(list(range(n)))
+    ctx.add_frames(0, prob.depth, prob.lum, init_pose=prob.init)
+    st = ctx.solve_global(list(range(n)), n_gn=2, n_pcg=15, pcg_variant=variant)
+    P = ctx.get_poses(list(range(n)))
+    for k in range(n):
+        rot, tr = lie.pose_error(P[k], P_ref[k])
+        assert rot < 1e-6 and tr < 1e-6
+    np.testing.assert_allclose(st["energy"], ref["energy"], rtol=1e-7)
