@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain-path, latency and CPU-baseline legs")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu: no extras, no clocks")
+    ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="PCG kernel: 0 auto, 1 one CTA per problem, 2 grid-cooperative, 3 cluster")
     return ap.parse_args()
 
 
@@ -200,7 +202,7 @@ def run_ours(args, rank, world, local_rank):
     precision = bf.BF_PREC_MIXED if args.precision == "mixed" else bf.BF_PREC_FP32
     params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
                                w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
-                               precision=precision)
+                               precision=precision, pcg_variant=args.pcg_variant)
     stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
     torch.cuda.set_stream(stream)
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
