@@ -41,6 +41,14 @@ import numpy as np  # noqa: E402
 METRIC = "GN iterations/sec + chunk-solve p50/p99 latency vs plain GPU path; HBM GB/s frac"
 UNIT = "GN iterations/s"
 DENSE_BYTES_PER_PX = 48  # FP32: source D, n, I (20 B) + target D, n nearest (16 B) + I, grad I bilinear (12 B)
+# FP32 flops of the dense kernel per directed source pixel on this workload: ncu FFMA x 2 + FADD + FMUL
+# of one ACCUM launch divided by its 21.84 M directed source pixels (profiles/k_dense_global300_80x60.md)
+DENSE_FLOPS_PER_PX = 139.0
+# DRAM bytes (read + write) of one dense ACCUM launch from the same ncu capture (cold cache); set to
+# None whenever k_dense changes until it is captured again
+DENSE_TRAFFIC_BYTES = 41.39e6 + 0.05e6
+# B300 FP32 peak: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
 def parse():
@@ -52,6 +60,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
     ap.add_argument("--no-extras", action="store_true", help="skip plain-path, latency and CPU-baseline legs")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu: no extras, no clocks")
+    ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="PCG kernel: 0 auto, 1 one CTA per problem, 2 grid-cooperative, 3 cluster")
     return ap.parse_args()
@@ -202,7 +211,10 @@ def run_ours(args, rank, world, local_rank):
     precision = bf.BF_PREC_MIXED if args.precision == "mixed" else bf.BF_PREC_FP32
     params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
                                w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
-                               precision=precision, pcg_variant=args.pcg_variant)
+                               precision=precision, pcg_variant=args.pcg_variant, use_graph=0 if args.no_graph else 1)
+    prof_params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
+                                    w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
+                                    precision=precision, pcg_variant=args.pcg_variant, use_graph=0)
     stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
     torch.cuda.set_stream(stream)
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
@@ -249,7 +261,9 @@ def run_ours(args, rank, world, local_rank):
     if clocks:
         clocks.start()
     t_wall = time.perf_counter()
-    times, st, prof = timed(step, args.steps, profile=True)
+    ctx.reset_profile()
+    times, st, _ = timed(step, args.steps)
+    launches = ctx.profile()["launches"]
     torch.cuda.synchronize(dev)
     if dist is not None:
         dist.barrier()
@@ -267,17 +281,23 @@ def run_ours(args, rank, world, local_rank):
             print(json.dumps({"profile_run": True, "value": value, "ms_per_step": total_ms / args.steps}))
         return
 
-    # roofline of the dominant kernel (dense term): algorithmic bytes per launch / event-timed duration
+    # per-kernel device times: a second pass, kernel by kernel, CUDA events around every launch on
+    # the context's stream (the graph replay above carries no events)
+    _, _, prof = timed(lambda: step(prof_params), max(3, args.steps // 2), profile=True)
+    # roofline of the dominant kernel (dense term, ACCUM launches): FP32 flops per launch / event time
     n_dp = 2 * st["n_dense_pairs"]
     HW = intr["W"] * intr["H"]
     dense = prof["kernels"]["dense"]
     dense_ms = dense["ms"] / max(dense["count"], 1)
-    alg_bytes = DENSE_BYTES_PER_PX * n_dp * HW
+    units = n_dp * HW
+    flops = DENSE_FLOPS_PER_PX * units
+    alg_bytes = DENSE_BYTES_PER_PX * units
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
-    achieved = alg_bytes / (dense_ms / 1000.0) / 1e9
-    gpu_launches = prof["launches"]
+    achieved_tf = flops / (dense_ms / 1000.0) / 1e12
+    achieved_gbs = alg_bytes / (dense_ms / 1000.0) / 1e9
+    gpu_launches = launches
     kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in prof["kernels"].values()), 1e-9), 4)
                     for k, v in prof["kernels"].items() if v["count"]}
 
@@ -285,16 +305,24 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": prob.name, "keyframes": n, "resolution": f"{intr['W']}x{intr['H']}",
+                       "cuda_graph": not args.no_graph,
                        "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"],
                        "directed_dense_pairs": n_dp, "correspondences": prob.n_corr, "n_gn": n_gn,
                        "n_pcg": prm["n_pcg"], "precision": args.precision,
                        "l2": "256 MB buffer written between timed steps (inputs < L2)",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": gpu_launches,
-            "roofline": {"bound": "hbm", "kernel": "k_dense", "achieved": achieved, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
-                         "avg_launch_ms": dense_ms, "algorithmic_bytes_per_launch": alg_bytes,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+            "roofline": {"bound": "alu", "kernel": "k_dense", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
+                         "traffic": DENSE_TRAFFIC_BYTES, "avg_launch_ms": dense_ms,
+                         "flops_per_launch": flops, "flops_per_directed_px": DENSE_FLOPS_PER_PX,
+                         "directed_px_per_launch": units,
+                         "peak_source": "derived FP32 peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz"},
+            "roofline_hbm_view": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": achieved_gbs / hbm_peak, "traffic": DENSE_TRAFFIC_BYTES,
+                                  "algorithmic_bytes_per_launch": alg_bytes,
+                                  "note": "48 B per directed source pixel; the 40 MB of frames stay in L2, "
+                                          "so DRAM traffic is the unique frame bytes (of measured)"},
             "kernel_time_share": kernel_share,
             "final_energy": st["energy"][-1], "initial_energy": st["energy"][0]}
     if clk:

@@ -75,7 +75,7 @@ __device__ __forceinline__ void cta_reduce_store(float (&acc)[N], Part *__restri
 constexpr int DENSE_BS = 256;
 
 template <int MODE, typename Part>
-__global__ void __launch_bounds__(DENSE_BS, 3)
+__global__ void __launch_bounds__(DENSE_BS, 4)
     k_dense(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo, float w_photo,
             Part *__restrict__ part, int *__restrict__ assoc) {
   const int tile = blockIdx.x;
@@ -97,9 +97,12 @@ __global__ void __launch_bounds__(DENSE_BS, 3)
 #pragma unroll
   for (int k = 0; k < NPD; ++k) acc[k] = 0.f;
 
+  float4 a_next = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (px0 + (int)threadIdx.x < px1) a_next = As[px0 + threadIdx.x];
   for (int px = px0 + threadIdx.x; px < px1; px += DENSE_BS) {
     int tgt = -1;
-    const float4 a = As[px];
+    const float4 a = a_next;  // prefetched one iteration ahead
+    if (px + DENSE_BS < px1) a_next = As[px + DENSE_BS];
     const bool nvalid = (a.y != 0.f) || (a.z != 0.f) || (a.w != 0.f);
     if (a.x > 0.f && nvalid) {
       const int y = px / W, x = px - y * W;
