@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip plain-path, latency and CPU-baseline legs")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu: no extras, no clocks")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
+    ap.add_argument("--tile-px", type=int, default=0,
+                    help="dense work item size in source pixels; 0 = automatic (target frame staged in shared memory)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="PCG kernel: 0 auto, 1 one CTA per problem, 2 grid-cooperative, 3 cluster")
     return ap.parse_args()
@@ -211,10 +213,12 @@ def run_ours(args, rank, world, local_rank):
     precision = bf.BF_PREC_MIXED if args.precision == "mixed" else bf.BF_PREC_FP32
     params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
                                w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
-                               precision=precision, pcg_variant=args.pcg_variant, use_graph=0 if args.no_graph else 1)
+                               precision=precision, pcg_variant=args.pcg_variant, use_graph=0 if args.no_graph else 1,
+                               tile_px=args.tile_px)
     prof_params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
                                     w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
-                                    precision=precision, pcg_variant=args.pcg_variant, use_graph=0)
+                                    precision=precision, pcg_variant=args.pcg_variant, use_graph=0,
+                                    tile_px=args.tile_px)
     stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
     torch.cuda.set_stream(stream)
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
@@ -305,7 +309,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": prob.name, "keyframes": n, "resolution": f"{intr['W']}x{intr['H']}",
-                       "cuda_graph": not args.no_graph,
+                       "cuda_graph": not args.no_graph, "tile_px": args.tile_px,
                        "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"],
                        "directed_dense_pairs": n_dp, "correspondences": prob.n_corr, "n_gn": n_gn,
                        "n_pcg": prm["n_pcg"], "precision": args.precision,

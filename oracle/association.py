@@ -18,8 +18,9 @@ Readings used (the paper gives no numbers for this pruning):
 
 Every one of these decisions turns a floating-point value into an integer or a
 boolean.  They are taken in IEEE FP32 with one rounding per operation, in the fixed
-order written below, the same precision and order as the GPU kernel, so that both
-sides take identical decisions on identical inputs.  The residual values
+order written below (the projection uses one correctly rounded reciprocal 1/y_z), the same
+precision and order as the GPU kernel, so that both sides take identical decisions on
+identical inputs.  The residual values
 themselves (residuals.py) are FP64.
 
 Per directed pair the relative transform M = T_j^-1 T_i is formed in FP64 with
@@ -71,9 +72,9 @@ def associate(fi, fj, M32, intr, tau_d=0.15, tau_n=0.9):
     Y = [((R[a, 0] * dx + R[a, 1] * dy) + R[a, 2] * dz) + t[a] for a in range(3)]
     ok &= Y[2] > f32(0)
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
-        Yz = np.where(ok, Y[2], f32(1))
-        ux = fx * (Y[0] / Yz) + cx
-        uy = fy * (Y[1] / Yz) + cy
+        iz = f32(1) / np.where(ok, Y[2], f32(1))
+        ux = fx * (Y[0] * iz) + cx
+        uy = fy * (Y[1] * iz) + cy
     ux = np.where(ok, ux, f32(-100))
     uy = np.where(ok, uy, f32(-100))
     nxf = np.floor(ux + f32(0.5))

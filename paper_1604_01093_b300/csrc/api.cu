@@ -623,6 +623,8 @@ struct HostTables {
   std::vector<int> dp_src, dp_dst, dp_pair, dp_dir, dp_tile0, dp_tile1, tile_dp, tile_px0, tile_px1;
   std::vector<int> seg_pair, seg_off, seg_cnt, seg_swap, inc_off, inc, inc_ov, var_frame;
   std::vector<int> prob_var0, prob_var1, prob_pair0, prob_pair1, prob_frame0;
+  int n_wi = 0;                        // target-staged dense work items (0: tiled kernel)
+  std::vector<int> wi_off, sw_dp, dp_dst_host;
   std::vector<int> pair_ida, pair_idb;  // frame ids of the pair (for stats)
   std::vector<double> pose;             // n_frames x 12
   long long n_corr = 0;
@@ -630,11 +632,17 @@ struct HostTables {
   std::vector<long long> prob_ncorr;
 };
 
+constexpr int STAGED_PAIRS_PER_ITEM = 4;
+
 // Build the flattened tables of a set of problems.  force_dense: every pair gets both dense
 // directions (debug), else the Sec. 4.3 angle test on the initial poses selects E.
 bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm, HostTables &T) {
   const int HW = c->cfg.width * c->cfg.height;
-  int tile_px = prm.tile_px > 0 ? prm.tile_px : std::min(HW, 4800);
+  // dense work decomposition: explicit tile_px -> tiles of that many pixels; automatic -> the
+  // target frame staged in shared memory when it fits (one partial per directed pair), else
+  // 4800-pixel tiles
+  const bool staged = prm.tile_px == 0 && dense_staged_fits(c->cfg.width, c->cfg.height);
+  int tile_px = prm.tile_px > 0 ? prm.tile_px : (staged ? HW : std::min(HW, 4800));
   T.n_prob = (int)probs.size();
   std::vector<std::vector<std::pair<int, int>>> var_inc;  // per var: (pair, side)
   const double cos_max = std::cos(prm.max_angle_deg * M_PI / 180.0);
@@ -727,6 +735,7 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
           ++T.n_tiles;
         }
         T.dp_tile1.push_back(T.n_tiles);
+        if (staged) T.dp_dst_host.push_back(dir == 0 ? F0 + b : F0 + a);
       }
       if (dense) ++ndense;
       if (a != 0) var_inc[T.frame_var[F0 + a]].push_back({p, 0});
@@ -737,6 +746,28 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
     T.prob_ndense.push_back(ndense);
     T.prob_ncorr.push_back(ncorr);
     T.n_corr += ncorr;
+  }
+  if (staged && T.n_dp > 0) {
+    // group the directed pairs by target frame, at most STAGED_PAIRS_PER_ITEM per work item (one per
+    // warp quad: many small items keep the one-CTA-per-SM grid balanced)
+    std::vector<int> order(T.n_dp);
+    for (int d = 0; d < T.n_dp; ++d) order[d] = d;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return T.dp_dst_host[x] < T.dp_dst_host[y]; });
+    T.wi_off.push_back(0);
+    int run = 0;
+    for (int k = 0; k < T.n_dp; ++k) {
+      if (k > 0 && (T.dp_dst_host[order[k]] != T.dp_dst_host[order[k - 1]] || run == STAGED_PAIRS_PER_ITEM)) {
+        T.wi_off.push_back(k);
+        run = 0;
+      }
+      T.sw_dp.push_back(order[k]);
+      ++run;
+    }
+    T.wi_off.push_back(T.n_dp);
+    T.n_wi = (int)T.wi_off.size() - 1;
+  } else {
+    T.wi_off.push_back(0);
   }
   T.inc_off.assign(T.n_vars + 1, 0);
   for (int v = 0; v < T.n_vars; ++v) T.inc_off[v + 1] = T.inc_off[v] + (int)var_inc[v].size();
@@ -777,6 +808,7 @@ struct DevSolve {
   double *energy;  // (n_gn + 1) x n_prob x 4
   int *assoc;
   void *coop;      // cooperative PCG state (barrier, error flag, partials)
+  int *derr;       // set by the staged dense kernel if its bulk copies did not land
   int coop_grid;   // > 0: one large problem solved by the cooperative PCG
   int cluster;     // > 0: one large problem solved on a thread-block cluster of this many CTAs
 };
@@ -830,6 +862,7 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
   const int cg = coop_grid_for(T, variant);
   void *coop = a.take<char>(cg > 0 ? coop_mem_bytes(cg) : 256);
   double *energy = a.take<double>((size_t)(n_gn + 1) * T.n_prob * PAIREN);
+  int *derr = a.take<int>(1);
   int *assoc = want_assoc ? a.take<int>(HW) : nullptr;
   if (D) {
     D->pose = pose;
@@ -857,6 +890,7 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     D->coop_grid = cg;
     D->cluster = cluster_for(T, variant);
     D->energy = energy;
+    D->derr = derr;
     D->assoc = assoc;
     // table pointers into ib, in the order of pack_ints
     int *w = ib;
@@ -901,6 +935,9 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     t.prob_var1 = nxt(T.prob_var1.size());
     t.prob_pair0 = nxt(T.prob_pair0.size());
     t.prob_pair1 = nxt(T.prob_pair1.size());
+    t.n_wi = T.n_wi;
+    t.wi_off = nxt(T.wi_off.size());
+    t.sw_dp = nxt(T.sw_dp.size());
   }
   return a.off;
 }
@@ -911,7 +948,7 @@ std::vector<int> pack_ints(const HostTables &T) {
        {&T.frame_slot, &T.frame_var, &T.pair_a, &T.pair_b, &T.pair_dp, &T.pair_seg0, &T.pair_seg1, &T.dp_src,
         &T.dp_dst, &T.dp_pair, &T.dp_dir, &T.dp_tile0, &T.dp_tile1, &T.tile_dp, &T.tile_px0, &T.tile_px1,
         &T.seg_pair, &T.seg_off, &T.seg_cnt, &T.seg_swap, &T.inc_off, &T.inc, &T.inc_ov, &T.var_frame, &T.prob_var0,
-        &T.prob_var1, &T.prob_pair0, &T.prob_pair1})
+        &T.prob_var1, &T.prob_pair0, &T.prob_pair1, &T.wi_off, &T.sw_dp})
     v.insert(v.end(), x->begin(), x->end());
   return v;
 }
@@ -959,6 +996,7 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
   CK(cudaMemcpyAsync(D.pose, c->pin, T.pose.size() * sizeof(double), cudaMemcpyHostToDevice, c->st),
      "upload poses");
   if (T.n_prob) CK(cudaMemsetAsync(D.pflags, 0, T.n_prob * sizeof(int), c->st), "pflags");
+  CK(cudaMemsetAsync(D.derr, 0, sizeof(int), c->st), "dense status");
   return BF_OK;
 }
 
@@ -971,6 +1009,9 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
   g.tau_n = (float)prm.tau_normal;
   run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->st); });
   run_k(c, BF_K_DENSE, [&] {
+    if (t.n_wi > 0)
+      return launch_dense_staged<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
+                                      (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, c->st);
     return launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
                              (float)(wd * prm.w_photo), (Acc *)D.dpart, nullptr, c->st);
   });
@@ -1124,9 +1165,10 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
     CK(cudaMemcpyAsync(pb + o_sm, D.srmax, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, c->st), "rmax");
     CK(cudaMemcpyAsync(pb + o_sa, D.srarg, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, c->st), "rmax");
   }
-  std::memset(pb + o_ce, 0, 4);
+  std::memset(pb + o_ce, 0, 8);
   if (D.coop_grid > 0)
     CK(cudaMemcpyAsync(pb + o_ce, (char *)D.coop + 8, sizeof(int), cudaMemcpyDeviceToHost, c->st), "pcg status");
+  CK(cudaMemcpyAsync(pb + o_ce + 4, D.derr, sizeof(int), cudaMemcpyDeviceToHost, c->st), "dense status");
   CK(cudaStreamSynchronize(c->st), "solve");
   std::vector<double> pose(n_pose), energy(n_en);
   std::vector<int> vflags(T.n_vars), pflags(T.n_prob), srarg(T.n_segs);
@@ -1139,9 +1181,11 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
     std::memcpy(srmax.data(), pb + o_sm, 4 * (size_t)T.n_segs);
     std::memcpy(srarg.data(), pb + o_sa, 4 * (size_t)T.n_segs);
   }
-  int coop_err = 0;
+  int coop_err = 0, dense_err = 0;
   std::memcpy(&coop_err, pb + o_ce, 4);
+  std::memcpy(&dense_err, pb + o_ce + 4, 4);
   if (coop_err) return fail(c, BF_ERR_TIMEOUT, "PCG grid barrier timed out");
+  if (dense_err) return fail(c, BF_ERR_TIMEOUT, "dense kernel: frame copy into shared memory timed out");
   const double ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   out.assign(T.n_prob, {});

@@ -91,6 +91,10 @@ struct Tables {
   const int *inc_ov;                // [n_inc] var block of the pair's other frame, -1 for a gauge frame
   const int *var_frame;             // [n_vars]
   const int *prob_var0, *prob_var1, *prob_pair0, *prob_pair1;  // [n_prob]
+  // target-staged dense work items (small frames): item w covers sw_dp[wi_off[w] .. wi_off[w+1]),
+  // directed pairs that share one target frame
+  int n_wi;
+  const int *wi_off, *sw_dp;
 };
 
 struct Gates {
@@ -107,6 +111,13 @@ int launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, 
                       cudaStream_t st);
 int launch_pack_corr_batch(const float *p_i, const float *p_j, const float *w, int n_total, const int *off,
                            const int *swap, int n_pairs, float4 *P, float4 *Q, cudaStream_t st);
+// Target-staged dense kernel (whole target frame in shared memory, loaded by TMA bulk copies).
+// Usable when dense_staged_fits(W, H); writes one partial per directed pair.  err: device int
+// set to 1 if a bulk copy did not complete within the wait limit.
+bool dense_staged_fits(int W, int H);
+template <typename Part>
+int launch_dense_staged(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
+                        float w_geo, float w_photo, Part *part, int *err, cudaStream_t st);
 int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st);
 template <typename Part>
 int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,

@@ -356,3 +356,17 @@ def test_graph_replay_equals_direct_launches(bf, small_global):
         Pb = ctx.get_poses(ids)
         np.testing.assert_array_equal(Pa, Pb)
         assert a["energy"] == b["energy"]
+
+
+def test_staged_and_tiled_dense_kernels_agree(bf, cfg1):
+    """Automatic decomposition (target frame staged in shared memory by TMA bulk copies) and the
+    tiled kernel build the same normal equations up to FP32 summation order."""
+    ctx = make_ctx(bf, cfg1)
+    poses = perturb(cfg1.gt, 23)
+    ids = list(range(cfg1.n_frames))
+    staged = ctx.build_system(ids, poses, tile_px=0)
+    tiled = ctx.build_system(ids, poses, tile_px=4800)
+    assert staged["n_dense"] == tiled["n_dense"]
+    np.testing.assert_allclose(staged["A"], tiled["A"], rtol=0, atol=1e-5 * np.abs(tiled["A"]).max())
+    np.testing.assert_allclose(staged["b"], tiled["b"], rtol=0, atol=1e-5 * np.abs(tiled["b"]).max())
+    assert abs(staged["energy"] - tiled["energy"]) <= 1e-6 * tiled["energy"]
