@@ -248,6 +248,31 @@ bf_status bf_set_profiling(bf_ctx *ctx, int enable);
 bf_status bf_get_profile(bf_ctx *ctx, bf_profile *out);
 bf_status bf_reset_profile(bf_ctx *ctx);
 
+/*
+ * Dense normal-equation blocks of one frame pair, computed without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot allocate at the
+ * point of use (code running while another component captures its stream into a CUDA graph,
+ * real-time loops that cannot afford cudaMalloc's implicit device-wide synchronisation, hosts
+ * whose memory manager already owns the device memory).  No context is involved and nothing is
+ * allocated: intermediates live in one fixed device array built into the library (about 1.25 MB
+ * per device, held until exit).
+ *   width, height: at most 160 x 120 (larger sizes return BF_ERR_INVALID_ARG);
+ *   fx, fy, cx, cy, depth_min, depth_max: as in bf_config;
+ *   depth_i, lum_i, depth_j, lum_j: device, H x W float32 each (raw frames);
+ *   pose_i, pose_j: host, 16 doubles each (camera -> world);
+ *   params: host; uses tau_dist, tau_normal, w_dense, w_photo, w_geo (no ramp, no angle test);
+ *   out: device, 124 doubles: A_ii, A_ij, A_jj (row-major 6x6), rhs_i, rhs_j (= -J^T W r),
+ *        then e_sparse (0), e_photo, e_geo, associated pixels, both directions i->j and j->i;
+ *   cuda_stream: cudaStream_t (NULL = legacy default stream); the call only enqueues work.
+ * The first call on a device looks up the array's device address: make it before any stream
+ * capture.  Every call on a device shares the array and leaves its contents behind; calls whose
+ * GPU work overlaps race on it, so order them on one stream.
+ */
+bf_status bf_dense_pair_noalloc(int width, int height, double fx, double fy, double cx, double cy, float depth_min,
+                                float depth_max, const float *depth_i, const float *lum_i, const float *depth_j,
+                                const float *lum_j, const double *pose_i, const double *pose_j,
+                                const bf_solve_params *params, double *out, void *cuda_stream);
+
 /* Device bytes currently held by the context. */
 size_t bf_device_bytes(bf_ctx *ctx);
 

@@ -108,6 +108,8 @@ def lib():
         "bf_set_profiling": (I, [P, I]),
         "bf_get_profile": (I, [P, ctypes.POINTER(Profile)]),
         "bf_reset_profile": (I, [P]),
+        "bf_dense_pair_noalloc": (I, [I, I, D, D, D, D, ctypes.c_float, ctypes.c_float, P, P, P, P, P, P,
+                                      ctypes.POINTER(SolveParams), P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -122,7 +124,8 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_last_error", "bf_add_frames", "bf_add_correspondences", "bf_add_correspondences_batch",
            "bf_remove_pair", "bf_set_profiling", "bf_get_profile", "bf_reset_profile",
            "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
-           "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes"]
+           "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes",
+           "bf_dense_pair_noalloc"]
 
 
 class BFError(RuntimeError):
@@ -305,3 +308,18 @@ class Context:
 
     def device_bytes(self):
         return lib().bf_device_bytes(self.h)
+
+
+def dense_pair_noalloc(depth_i, lum_i, depth_j, lum_j, pose_i, pose_j, out, width, height, fx, fy, cx, cy,
+                       depth_min=0.1, depth_max=10.0, stream=None, params=None, **kw):
+    """bf_dense_pair_noalloc: device tensors in, 124 doubles into the device tensor out.
+
+    For callers that cannot allocate device memory at the point of use; see include/bf.h."""
+    p = params or default_params(**kw)
+    pi = np.ascontiguousarray(pose_i, dtype=np.float64).reshape(16)
+    pj = np.ascontiguousarray(pose_j, dtype=np.float64).reshape(16)
+    st = lib().bf_dense_pair_noalloc(width, height, fx, fy, cx, cy, depth_min, depth_max, _ptr(depth_i), _ptr(lum_i),
+                                     _ptr(depth_j), _ptr(lum_j), _ptr(pi), _ptr(pj), ctypes.byref(p), _ptr(out),
+                                     stream)
+    if st != BF_OK:
+        raise BFError(st, "bf_dense_pair_noalloc failed")
