@@ -369,12 +369,104 @@ def run_ours(args, rank, world, local_rank):
                               "ms_per_step": statistics.mean(tp), "final_energy": stp["energy"][-1]}
 
         line["chunk_latency"] = chunk_latency(bf, torch, dev)
+        line["chunk_batch"] = chunk_batch_leg(bf, torch, dev, stream)
 
         v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256):
+    """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.
+
+    batched: all chunks in one launch sequence (one problem per chunk), mixed precision, replayed
+    as a CUDA graph; plain: one FP32 solve per chunk, kernel by kernel, no graph.  Each step
+    re-runs frame preprocessing from device-resident raw frames.  Chunk-solve latency: call ->
+    poses on the host; in the batched mode every chunk completes with its batch."""
+    import synth
+    prob = synth.cfg3(n_chunks=n_chunks)
+    intr = prob.intr
+    prm = prob.solve
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], stream=stream.cuda_stream,
+                     max_frames_hint=prob.n_frames)
+    depth_d = torch.from_numpy(prob.depth).to(dev)
+    lum_d = torch.from_numpy(prob.lum).to(dev)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                  torch.from_numpy(prob.p_j).to(dev))
+    ids = list(range(len(prob.chunks)))
+    lists = [c.tolist() for c in prob.chunks]
+    common = {k: prm[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
+    pb = bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=1, **common)
+    pp = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, **common)
+    gn_per_step = prm["n_gn"] * len(lists)
+
+    def run(fn, k):
+        ts = []
+        for _ in range(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts, out
+
+    def batched():
+        ctx.add_frames(0, depth_d, lum_d)
+        return ctx.solve_local_batch(ids, lists, pb)
+
+    lat = []
+
+    def plain():
+        ctx.add_frames(0, depth_d, lum_d)
+        torch.cuda.synchronize(dev)
+        out = []
+        for cid, lst in zip(ids, lists):
+            t0 = time.perf_counter()
+            out.append(ctx.solve_local(cid, lst, pp))
+            ctx.get_poses(lst)
+            lat.append(1000.0 * (time.perf_counter() - t0))
+        return out
+
+    run(batched, warmup)
+    tb, sb = run(batched, steps)
+    # dense kernel time in this workload (kernel by kernel, CUDA events around each launch)
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    ctx.add_frames(0, depth_d, lum_d)
+    ctx.solve_local_batch(ids, lists, bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=0, **common))
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    run(plain, 1)
+    lat.clear()
+    tp, _ = run(plain, max(1, steps - 1))
+    lat.sort()
+    HW = intr["W"] * intr["H"]
+    n_dp = 2 * sum(s["n_dense_pairs"] for s in sb)
+    dense = prof["kernels"]["dense"]
+    dense_ms = dense["ms"] / max(dense["count"], 1)
+    alg_bytes = DENSE_BYTES_PER_PX * n_dp * HW
+    out = {"workload": prob.name, "chunks": len(lists), "frames": prob.n_frames, "pairs": int(len(prob.pairs)),
+           "directed_dense_pairs": n_dp, "correspondences": prob.n_corr, "n_gn": prm["n_gn"], "n_pcg": prm["n_pcg"],
+           "batched": {"value": gn_per_step / (statistics.mean(tb) / 1000.0), "unit": UNIT,
+                       "ms_per_step": statistics.mean(tb),
+                       "solves_per_s": len(lists) / (statistics.mean(tb) / 1000.0),
+                       "chunk_latency_p50_ms": statistics.mean(tb), "chunk_latency_p99_ms": max(tb),
+                       "precision": "mixed", "cuda_graph": True},
+           "plain_fp32": {"value": gn_per_step / (statistics.mean(tp) / 1000.0), "unit": UNIT,
+                          "ms_per_step": statistics.mean(tp),
+                          "solves_per_s": len(lists) / (statistics.mean(tp) / 1000.0),
+                          "chunk_latency_p50_ms": lat[len(lat) // 2],
+                          "chunk_latency_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+           "dense_kernel": {"avg_launch_ms": dense_ms, "launches": dense["count"],
+                            "algorithmic_bytes_per_launch": alg_bytes,
+                            "algorithmic_GBps": alg_bytes / (dense_ms / 1000.0) / 1e9,
+                            "unique_frame_bytes": int(prob.n_frames * HW * 32)}}
+    ctx.close()
+    return out
 
 
 def chunk_latency(bf, torch, dev, reps=40):

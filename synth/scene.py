@@ -368,7 +368,8 @@ def sample_correspondences(rng, intr, depth_gt, depth_noisy, poses, i, j, n, sig
     A fraction outlier_frac of p_j is replaced by the back-projection of a random valid pixel of j.
     Returns (p_i, p_j, is_outlier) as float32 / bool arrays, or None if nothing of i is visible in j.
     """
-    ok, _, xs, ys = visible_mask(intr, depth_gt[i], depth_gt[j], poses[i], poses[j])
+    stride = 1 if intr["W"] <= 160 else 2  # candidates from every second pixel on large frames
+    ok, _, xs, ys = visible_mask(intr, depth_gt[i], depth_gt[j], poses[i], poses[j], stride=stride)
     ok &= depth_noisy[i][ys, xs] > 0
     cand = np.flatnonzero(ok.ravel())
     if len(cand) == 0:

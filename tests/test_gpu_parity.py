@@ -370,3 +370,24 @@ def test_staged_and_tiled_dense_kernels_agree(bf, cfg1):
     np.testing.assert_allclose(staged["A"], tiled["A"], rtol=0, atol=1e-5 * np.abs(tiled["A"]).max())
     np.testing.assert_allclose(staged["b"], tiled["b"], rtol=0, atol=1e-5 * np.abs(tiled["b"]).max())
     assert abs(staged["energy"] - tiled["energy"]) <= 1e-6 * tiled["energy"]
+
+
+@pytest.fixture(scope="module")
+def batch320():
+    return synth.chunk_batch(57, n_chunks=6, W=320, H=240, length=(3, 5), n_corr=(100, 200), name="batch320")
+
+
+def test_batched_chunks_320x240_match_oracle(bf, batch320):
+    """Full-resolution chunks (320x240, tiled dense kernel) solved in one batch; the two smallest
+    chunks are checked against the oracle."""
+    prob = batch320
+    ctx = make_ctx(bf, prob, max_frames_hint=prob.n_frames)
+    lists = [c.tolist() for c in prob.chunks]
+    stats = ctx.solve_local_batch(list(range(len(lists))), lists, n_gn=3, n_pcg=8, use_graph=1)
+    order = sorted(range(len(lists)), key=lambda k: len(lists[k]))[:2]
+    prm = SolveParams(n_gn=3, n_pcg=8)
+    for k in order:
+        ids = lists[k]
+        fr = [ofr.Frame(prob.depth[f], prob.lum[f], prob.intr) for f in ids]
+        ref = solver.gauss_newton(fr, prob.intr, prob.init[ids], solver.sparse_pairs_for(prob, ids), prm)
+        compare_solve(stats[k], ctx.get_poses(ids), ref, f"chunk {k} at 320x240")
