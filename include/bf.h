@@ -273,6 +273,39 @@ bf_status bf_dense_pair_noalloc(int width, int height, double fx, double fy, dou
                                 const float *lum_j, const double *pose_i, const double *pose_j,
                                 const bf_solve_params *params, double *out, void *cuda_stream);
 
+/*
+ * Serving (continuous batching on a persistent context).  Frames and correspondences are added as
+ * usual (bf_add_frames / bf_add_correspondences, which may be called while serving); requests
+ * name frame ids and are queued.  n_slots worker slots, each with its own stream and solve
+ * workspace, take batches from the head of the queue: consecutive local requests with identical
+ * parameters (up to max_batch) form one batched solve; a global request runs alone.  Batches of
+ * different slots overlap on the device.  Admission follows the context's HBM budget: a batch
+ * whose workspace would not fit is halved and the rest requeued.  A request's stats.ms is its
+ * latency from bf_submit to completion.  Results are also stored as by bf_solve_local /
+ * bf_solve_global (bf_get_poses sees them).  Adding frames that replace existing ids, growing the
+ * frame store or the correspondence pool, and clearing correspondences wait until no batch is on
+ * the device.
+ */
+enum { BF_REQ_LOCAL = 0, BF_REQ_GLOBAL = 1 };
+typedef struct {
+  int kind;                 /* BF_REQ_LOCAL or BF_REQ_GLOBAL                              */
+  int chunk_id;             /* local requests: chunk id the local poses are stored under   */
+  const int *frame_ids;     /* host, copied by bf_submit; [0] is the fixed frame           */
+  int n;
+  bf_solve_params params;   /* use_graph is ignored (batches differ from one another)      */
+} bf_request;
+/* Start n_slots (1..8) worker slots; max_batch local requests per batch; max_queue pending. */
+bf_status bf_serve_start(bf_ctx *ctx, int n_slots, int max_batch, int max_queue);
+/* Stop the workers after their current batch; pending requests complete with BF_ERR_BUSY.
+ * bf_destroy stops serving too. */
+bf_status bf_serve_stop(bf_ctx *ctx);
+/* Queue a request; BF_ERR_BUSY if max_queue requests are already pending. */
+bf_status bf_submit(bf_ctx *ctx, const bf_request *req, uint64_t *ticket);
+/* Wait up to timeout_ms (< 0: forever, 0: poll) for a request; returns its status, or
+ * BF_ERR_TIMEOUT if it has not completed (the ticket stays valid), BF_ERR_NOT_FOUND for an
+ * unknown or already collected ticket.  stats: nullable. */
+bf_status bf_wait(bf_ctx *ctx, uint64_t ticket, int timeout_ms, bf_solve_stats *stats);
+
 /* Device bytes currently held by the context. */
 size_t bf_device_bytes(bf_ctx *ctx);
 

@@ -64,6 +64,14 @@ class SolveStats(ctypes.Structure):
                     n_corr=self.n_corr, flags=self.flags, ms=self.ms)
 
 
+BF_REQ_LOCAL, BF_REQ_GLOBAL = 0, 1
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("chunk_id", ctypes.c_int), ("frame_ids", ctypes.c_void_p),
+                ("n", ctypes.c_int), ("params", SolveParams)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("count", ctypes.c_longlong * BF_NPROF),
                 ("ms", ctypes.c_double * BF_NPROF)]
@@ -108,6 +116,10 @@ def lib():
         "bf_set_profiling": (I, [P, I]),
         "bf_get_profile": (I, [P, ctypes.POINTER(Profile)]),
         "bf_reset_profile": (I, [P]),
+        "bf_serve_start": (I, [P, I, I, I]),
+        "bf_serve_stop": (I, [P]),
+        "bf_submit": (I, [P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+        "bf_wait": (I, [P, ctypes.c_uint64, I, P]),
         "bf_dense_pair_noalloc": (I, [I, I, D, D, D, D, ctypes.c_float, ctypes.c_float, P, P, P, P, P, P,
                                       ctypes.POINTER(SolveParams), P, P]),
     }
@@ -125,7 +137,7 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_remove_pair", "bf_set_profiling", "bf_get_profile", "bf_reset_profile",
            "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
            "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes",
-           "bf_dense_pair_noalloc"]
+           "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait"]
 
 
 class BFError(RuntimeError):
@@ -305,6 +317,31 @@ class Context:
         pj = np.ascontiguousarray(pose_j, dtype=np.float64).reshape(16)
         self._check(lib().bf_debug_association(self.h, i, j, _ptr(pi), _ptr(pj), ctypes.byref(p), _ptr(out)))
         return out
+
+    # --------------------------------------------------------------- serving
+    def serve_start(self, n_slots=2, max_batch=64, max_queue=1024):
+        self._check(lib().bf_serve_start(self.h, n_slots, max_batch, max_queue))
+
+    def serve_stop(self):
+        self._check(lib().bf_serve_stop(self.h))
+
+    def submit(self, frame_ids, kind=BF_REQ_LOCAL, chunk_id=0, params=None, **kw):
+        """Queue a request; returns its ticket (raises BFError with BF_ERR_BUSY if the queue is full)."""
+        ids = np.ascontiguousarray(frame_ids, dtype=np.int32)
+        r = Request()
+        r.kind, r.chunk_id, r.frame_ids, r.n = kind, chunk_id, ids.ctypes.data, len(ids)
+        r.params = params or default_params(**kw)
+        t = ctypes.c_uint64()
+        st = lib().bf_submit(self.h, ctypes.byref(r), ctypes.byref(t))
+        if st != BF_OK:
+            raise BFError(st, "bf_submit failed")
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """(status, stats dict or None): status BF_ERR_TIMEOUT (6) if not done within timeout_ms."""
+        st = SolveStats()
+        code = lib().bf_wait(self.h, ticket, timeout_ms, ctypes.byref(st))
+        return code, (st.to_dict() if code in (BF_OK,) else (st.to_dict() if code not in (4, 6) else None))
 
     def device_bytes(self):
         return lib().bf_device_bytes(self.h)

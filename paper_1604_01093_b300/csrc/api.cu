@@ -10,6 +10,11 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -67,6 +72,44 @@ inline uint64_t pair_key(int a, int b) {
 
 }  // namespace
 
+// Everything one solve in flight needs besides the shared frame store and correspondence pool:
+// a stream, the workspace arena, pinned staging and the cached Gauss-Newton graph.
+struct Exec {
+  cudaStream_t st = nullptr;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  unsigned char *pin = nullptr;
+  size_t pin_bytes = 0;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<unsigned char> gkey;
+  int gkernels = 0;
+  std::vector<int> last_ints;  // tables last uploaded into ws (skipped when unchanged)
+  const void *last_ws = nullptr;
+};
+
+// Serving: queued requests and the worker slots that run them.
+struct ServeReq {
+  int kind = 0, chunk_id = 0;
+  std::vector<int> ids;
+  bf_solve_params prm{};
+  bool done = false;
+  bf_status status = BF_OK;
+  bf_solve_stats stats{};
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Server {
+  std::mutex qm;
+  std::condition_variable qcv, dcv;
+  std::deque<uint64_t> pending;
+  std::unordered_map<uint64_t, ServeReq> reqs;
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  int max_batch = 64, max_queue = 1024;
+  std::vector<std::unique_ptr<Exec>> slots;
+  std::vector<std::thread> workers;
+};
+
 struct bf_ctx {
   bf_config cfg{};
   cudaStream_t st = nullptr;
@@ -91,9 +134,15 @@ struct bf_ctx {
   long long ccap = 0, cused = 0;
   std::unordered_map<uint64_t, std::vector<Seg>> corr;
   std::unordered_map<int, Chunk> chunks;
-  // solve workspace arena
-  char *ws = nullptr;
-  size_t ws_bytes = 0;
+  // solve executor in use (main, or a serving slot while it holds the context lock)
+  Exec main;
+  Exec *ex = &main;
+  // concurrency: every public call holds mu; serving slots release it while their GPU work runs
+  std::mutex mu;
+  std::condition_variable busy_cv;  // signalled when in_flight drops
+  int in_flight = 0;                // serving batches whose GPU work is running
+  cudaEvent_t data_ev = nullptr;    // recorded on the main stream after frame / correspondence uploads
+  std::unique_ptr<Server> srv;
   // kernel accounting
   long long launches = 0;
   bool prof = false;
@@ -103,16 +152,6 @@ struct bf_ctx {
   };
   std::vector<Rec> recs;
   size_t rec_used = 0;
-  // cached Gauss-Newton graph (replayed while tables, parameters and buffers are unchanged)
-  cudaGraphExec_t gexec = nullptr;
-  std::vector<unsigned char> gkey;
-  int gkernels = 0;
-  // tables last uploaded into the workspace (skipped when unchanged)
-  std::vector<int> last_ints;
-  const void *last_ws = nullptr;
-  // pinned host staging for per-solve uploads / downloads
-  unsigned char *pin = nullptr;
-  size_t pin_bytes = 0;
 };
 
 // ------------------------------------------------------------------------------- helpers
@@ -170,13 +209,13 @@ static void run_k(bf_ctx *c, int kind, F &&f) {
     }
     r = &c->recs[c->rec_used];
     r->kind = kind;
-    cudaEventRecord(r->a, c->st);
+    cudaEventRecord(r->a, c->ex->st);
   }
   const int n = f();
   c->launches += n;
   if (r) {
     if (n > 0) {
-      cudaEventRecord(r->b, c->st);
+      cudaEventRecord(r->b, c->ex->st);
       ++c->rec_used;
     }
   }
@@ -301,7 +340,11 @@ extern "C" const char *bf_status_string(bf_status s) {
 
 extern "C" const char *bf_last_error(bf_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-extern "C" size_t bf_device_bytes(bf_ctx *ctx) { return ctx ? ctx->bytes : 0; }
+extern "C" size_t bf_device_bytes(bf_ctx *ctx) {
+  if (!ctx) return 0;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  return ctx->bytes;
+}
 
 extern "C" bf_status bf_create(const bf_config *cfg, bf_ctx **out) {
   if (!cfg || !out) return BF_ERR_INVALID_ARG;
@@ -328,6 +371,13 @@ extern "C" bf_status bf_create(const bf_config *cfg, bf_ctx **out) {
       return BF_ERR_CUDA;
     }
     c->own_stream = true;
+  }
+  c->main.st = c->st;
+  if (cudaEventCreateWithFlags(&c->data_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->own_stream) cudaStreamDestroy(c->st);
+    delete c;
+    return BF_ERR_CUDA;
   }
   c->intr.fx = (float)cfg->fx;
   c->intr.fy = (float)cfg->fy;
@@ -356,8 +406,23 @@ extern "C" bf_status bf_create(const bf_config *cfg, bf_ctx **out) {
   return BF_OK;
 }
 
+static void free_exec(bf_ctx *c, Exec &e) {
+  if (e.ws) cudaFree(e.ws);
+  if (e.gexec) cudaGraphExecDestroy(e.gexec);
+  if (e.pin) cudaFreeHost(e.pin);
+  c->bytes -= e.ws_bytes;
+  e.ws = nullptr;
+  e.ws_bytes = 0;
+  e.gexec = nullptr;
+  e.pin = nullptr;
+  e.pin_bytes = 0;
+}
+
+extern "C" bf_status bf_serve_stop(bf_ctx *c);
+
 extern "C" bf_status bf_destroy(bf_ctx *c) {
   if (!c) return BF_OK;
+  bf_serve_stop(c);
   if (c->st) cudaStreamSynchronize(c->st);
   cudaFree(c->A);
   cudaFree(c->B);
@@ -367,13 +432,12 @@ extern "C" bf_status bf_destroy(bf_ctx *c) {
   cudaFree(c->slot_dev);
   cudaFree(c->cP);
   cudaFree(c->cQ);
-  cudaFree(c->ws);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
-  if (c->pin) cudaFreeHost(c->pin);
+  free_exec(c, c->main);
   for (auto &r : c->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  if (c->data_ev) cudaEventDestroy(c->data_ev);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
   cudaGetLastError();
   delete c;
@@ -384,6 +448,7 @@ extern "C" bf_status bf_destroy(bf_ctx *c) {
 extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *depth, const float *lum,
                                    int ptr_kind, const double *init_pose) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (n < 0 || (n > 0 && (!depth || !lum)) || (ptr_kind != BF_PTR_HOST && ptr_kind != BF_PTR_DEVICE))
     return fail(c, BF_ERR_INVALID_ARG, "bf_add_frames: bad arguments");
   if (first_id < 0 || (long long)first_id + n > 0x7fffffffLL)
@@ -392,10 +457,14 @@ extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *
   const size_t HW = (size_t)c->cfg.width * c->cfg.height;
   std::vector<int> slots(n);
   int need = c->next_slot;
+  bool replaces = false;
   for (int k = 0; k < n; ++k) {
     auto it = c->frames.find(first_id + k);
     if (it == c->frames.end()) ++need;
+    else replaces = true;
   }
+  // frames read by serving batches in flight must not move or change underneath them
+  if (replaces || need > c->cap) c->busy_cv.wait(lk, [&] { return c->in_flight == 0; });
   bf_status s = ensure_frames(c, need);
   if (s) return s;
   for (int k = 0; k < n; ++k) {
@@ -446,12 +515,14 @@ extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *
                              c->cfg.depth_max, c->st);
   });
   CK(cudaGetLastError(), "preprocess launch");
+  CK(cudaEventRecord(c->data_ev, c->st), "data event");
   if (ptr_kind == BF_PTR_HOST) CK(cudaStreamSynchronize(c->st), "preprocess");
   return BF_OK;
 }
 
 extern "C" bf_status bf_get_frame_planes(bf_ctx *c, int frame_id, float *out) {
   if (!c || !out) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   auto it = c->frames.find(frame_id);
   if (it == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "unknown frame id");
   const size_t HW = (size_t)c->cfg.width * c->cfg.height;
@@ -477,10 +548,12 @@ extern "C" bf_status bf_get_frame_planes(bf_ctx *c, int frame_id, float *out) {
 extern "C" bf_status bf_add_correspondences(bf_ctx *c, int frame_i, int frame_j, int n, const float *p_i,
                                             const float *p_j, const float *weight, int ptr_kind) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (n < 0 || frame_i == frame_j || frame_i < 0 || frame_j < 0 || (n > 0 && (!p_i || !p_j)) ||
       (ptr_kind != BF_PTR_HOST && ptr_kind != BF_PTR_DEVICE))
     return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences: bad arguments");
   if (n == 0) return BF_OK;
+  if (c->cused + n > c->ccap) c->busy_cv.wait(lk, [&] { return c->in_flight == 0; });
   bf_status s = ensure_corr(c, c->cused + n);
   if (s) return s;
   const int swap = frame_i > frame_j ? 1 : 0;
@@ -502,6 +575,7 @@ extern "C" bf_status bf_add_correspondences(bf_ctx *c, int frame_i, int frame_j,
   }
   c->corr[pair_key(frame_i, frame_j)].push_back(Seg{(int)c->cused, n});
   c->cused += n;
+  CK(cudaEventRecord(c->data_ev, c->st), "data event");
   return BF_OK;
 }
 
@@ -509,6 +583,7 @@ extern "C" bf_status bf_add_correspondences_batch(bf_ctx *c, int n_pairs, const 
                                                   const float *p_i, const float *p_j, const float *weight,
                                                   int ptr_kind) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (n_pairs < 0 || (n_pairs > 0 && (!pair_ids || !offsets)) || (ptr_kind != BF_PTR_HOST && ptr_kind != BF_PTR_DEVICE))
     return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences_batch: bad arguments");
   if (n_pairs == 0) return BF_OK;
@@ -521,6 +596,7 @@ extern "C" bf_status bf_add_correspondences_batch(bf_ctx *c, int n_pairs, const 
   const long long total = offsets[n_pairs];
   if (total == 0) return BF_OK;
   if (!p_i || !p_j) return fail(c, BF_ERR_INVALID_ARG, "bf_add_correspondences_batch: null points");
+  if (c->cused + total > c->ccap) c->busy_cv.wait(lk, [&] { return c->in_flight == 0; });
   bf_status s = ensure_corr(c, c->cused + total);
   if (s) return s;
   if (ptr_kind == BF_PTR_HOST) {
@@ -564,17 +640,20 @@ extern "C" bf_status bf_add_correspondences_batch(bf_ctx *c, int n_pairs, const 
     c->corr[pair_key(pair_ids[2 * k], pair_ids[2 * k + 1])].push_back(Seg{(int)(c->cused + offsets[k]), n});
   }
   c->cused += total;
+  CK(cudaEventRecord(c->data_ev, c->st), "data event");
   return BF_OK;
 }
 
 extern "C" bf_status bf_set_profiling(bf_ctx *c, int enable) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   c->prof = enable != 0;
   return BF_OK;
 }
 
 extern "C" bf_status bf_reset_profile(bf_ctx *c) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   c->launches = 0;
   c->rec_used = 0;
   return BF_OK;
@@ -582,6 +661,7 @@ extern "C" bf_status bf_reset_profile(bf_ctx *c) {
 
 extern "C" bf_status bf_get_profile(bf_ctx *c, bf_profile *out) {
   if (!c || !out) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   std::memset(out, 0, sizeof(*out));
   CK(cudaStreamSynchronize(c->st), "profile");
   out->launches = c->launches;
@@ -596,6 +676,7 @@ extern "C" bf_status bf_get_profile(bf_ctx *c, bf_profile *out) {
 
 extern "C" bf_status bf_remove_pair(bf_ctx *c, int frame_i, int frame_j) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   auto it = c->corr.find(pair_key(frame_i, frame_j));
   if (it == c->corr.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_remove_pair: no such pair");
   c->corr.erase(it);
@@ -604,6 +685,8 @@ extern "C" bf_status bf_remove_pair(bf_ctx *c, int frame_i, int frame_j) {
 
 extern "C" bf_status bf_clear_correspondences(bf_ctx *c) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  c->busy_cv.wait(lk, [&] { return c->in_flight == 0; });  // batches in flight still read the pool
   c->corr.clear();
   c->cused = 0;
   return BF_OK;
@@ -954,14 +1037,14 @@ std::vector<int> pack_ints(const HostTables &T) {
 }
 
 bf_status ensure_pinned(bf_ctx *c, size_t n) {
-  if (n <= c->pin_bytes) return BF_OK;
-  CK(cudaStreamSynchronize(c->st), "pinned staging");
-  if (c->pin) cudaFreeHost(c->pin);
-  c->pin = nullptr;
-  c->pin_bytes = 0;
+  if (n <= c->ex->pin_bytes) return BF_OK;
+  CK(cudaStreamSynchronize(c->ex->st), "pinned staging");
+  if (c->ex->pin) cudaFreeHost(c->ex->pin);
+  c->ex->pin = nullptr;
+  c->ex->pin_bytes = 0;
   const size_t nb = std::max(n, (size_t)1 << 16);
-  CK(cudaMallocHost((void **)&c->pin, nb), "pinned staging");
-  c->pin_bytes = nb;
+  CK(cudaMallocHost((void **)&c->ex->pin, nb), "pinned staging");
+  c->ex->pin_bytes = nb;
   return BF_OK;
 }
 
@@ -970,33 +1053,33 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
   const std::vector<int> ints = pack_ints(T);
   const int HW = c->cfg.width * c->cfg.height;
   const size_t need = layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc, variant) + 256;
-  if (need > c->ws_bytes) {
-    const size_t nb = std::max(need, c->ws_bytes * 3 / 2);
-    CK(cudaStreamSynchronize(c->st), "workspace");
-    dfree(c, c->ws, c->ws_bytes);
-    c->ws = nullptr;
-    c->ws_bytes = 0;
-    bf_status s = dalloc(c, (void **)&c->ws, nb, "solve workspace");
+  if (need > c->ex->ws_bytes) {
+    const size_t nb = std::max(need, c->ex->ws_bytes * 3 / 2);
+    CK(cudaStreamSynchronize(c->ex->st), "workspace");
+    dfree(c, c->ex->ws, c->ex->ws_bytes);
+    c->ex->ws = nullptr;
+    c->ex->ws_bytes = 0;
+    bf_status s = dalloc(c, (void **)&c->ex->ws, nb, "solve workspace");
     if (s) return s;
-    c->ws_bytes = nb;
+    c->ex->ws_bytes = nb;
   }
-  layout(T, n_gn, ints.size(), c->ws, &D, acc_size, HW, want_assoc, variant);
-  const bool same_tables = c->last_ws == (const void *)c->ws && c->last_ints == ints;
+  layout(T, n_gn, ints.size(), c->ex->ws, &D, acc_size, HW, want_assoc, variant);
+  const bool same_tables = c->ex->last_ws == (const void *)c->ex->ws && c->ex->last_ints == ints;
   if (!ints.empty() && !same_tables) {
-    CK(cudaMemcpyAsync((void *)D.t.frame_slot, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, c->st),
+    CK(cudaMemcpyAsync((void *)D.t.frame_slot, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, c->ex->st),
        "upload tables");
-    CK(cudaStreamSynchronize(c->st), "upload tables");
-    c->last_ints = ints;
-    c->last_ws = c->ws;
+    CK(cudaStreamSynchronize(c->ex->st), "upload tables");
+    c->ex->last_ints = ints;
+    c->ex->last_ws = c->ex->ws;
   }
   bf_status s = ensure_pinned(c, T.pose.size() * sizeof(double));
   if (s) return s;
-  CK(cudaStreamSynchronize(c->st), "pinned staging");  // the staging buffer may still feed a copy
-  std::memcpy(c->pin, T.pose.data(), T.pose.size() * sizeof(double));
-  CK(cudaMemcpyAsync(D.pose, c->pin, T.pose.size() * sizeof(double), cudaMemcpyHostToDevice, c->st),
+  CK(cudaStreamSynchronize(c->ex->st), "pinned staging");  // the staging buffer may still feed a copy
+  std::memcpy(c->ex->pin, T.pose.data(), T.pose.size() * sizeof(double));
+  CK(cudaMemcpyAsync(D.pose, c->ex->pin, T.pose.size() * sizeof(double), cudaMemcpyHostToDevice, c->ex->st),
      "upload poses");
-  if (T.n_prob) CK(cudaMemsetAsync(D.pflags, 0, T.n_prob * sizeof(int), c->st), "pflags");
-  CK(cudaMemsetAsync(D.derr, 0, sizeof(int), c->st), "dense status");
+  if (T.n_prob) CK(cudaMemsetAsync(D.pflags, 0, T.n_prob * sizeof(int), c->ex->st), "pflags");
+  CK(cudaMemsetAsync(D.derr, 0, sizeof(int), c->ex->st), "dense status");
   return BF_OK;
 }
 
@@ -1007,21 +1090,21 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
   Gates g;
   g.tau_d2 = (float)(prm.tau_dist * prm.tau_dist);
   g.tau_n = (float)prm.tau_normal;
-  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->st); });
+  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
   run_k(c, BF_K_DENSE, [&] {
     if (t.n_wi > 0)
       return launch_dense_staged<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
-                                      (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, c->st);
+                                      (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, c->ex->st);
     return launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
-                             (float)(wd * prm.w_photo), (Acc *)D.dpart, nullptr, c->st);
+                             (float)(wd * prm.w_photo), (Acc *)D.dpart, nullptr, c->ex->st);
   });
   run_k(c, BF_K_SPARSE, [&] {
     return launch_sparse<Acc>(mode, t, c->cP, c->cQ, D.pairM, (float)prm.w_sparse, (Acc *)D.spart, D.srmax,
-                              D.srarg, c->st);
+                              D.srarg, c->ex->st);
   });
   run_k(c, BF_K_MERGE, [&] {
     return launch_pair_merge<Acc, Acc>(t, D.pose, (const Acc *)D.dpart, (const Acc *)D.spart, (Acc *)D.pairblk,
-                                       (Acc *)D.pairen, D.pairoff, c->st);
+                                       (Acc *)D.pairen, D.pairoff, c->ex->st);
   });
 }
 
@@ -1036,34 +1119,34 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
     const double wd = wdense_at(prm, k);
     linearise<Acc>(c, D, prm, wd, MODE_ACCUM);
     run_k(c, BF_K_ENERGY, [&] {
-      return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)k * T.n_prob * PAIREN, c->st);
+      return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)k * T.n_prob * PAIREN, c->ex->st);
     });
     run_k(c, BF_K_ASSEMBLE, [&] {
       return launch_assemble<Acc>(t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv,
-                                  D.vflags, c->st);
+                                  D.vflags, c->ex->st);
     });
     int pcg_rc = 0;
     run_k(c, BF_K_PCG, [&] {
       if (D.cluster > 0) {
         pcg_rc = launch_pcg_cluster<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, prm.n_pcg, D.pflags,
-                                         D.cluster, T.inc_off.data(), c->st);
+                                         D.cluster, T.inc_off.data(), c->ex->st);
         return pcg_rc < 0 ? 0 : pcg_rc;
       }
       if (D.coop_grid > 0) {
         pcg_rc = launch_pcg_coop<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.p1, D.q,
-                                      prm.n_pcg, D.pflags, D.coop, D.coop_grid, c->st);
+                                      prm.n_pcg, D.pflags, D.coop, D.coop_grid, c->ex->st);
         return pcg_rc < 0 ? 0 : pcg_rc;
       }
       return launch_pcg<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.q, prm.n_pcg,
-                             D.pflags, c->st);
+                             D.pflags, c->ex->st);
     });
     if (pcg_rc < 0) return cuda_fail(c, cudaGetLastError(), "PCG launch");
-    run_k(c, BF_K_UPDATE, [&] { return launch_update(t, D.x, D.pose, c->st); });
+    run_k(c, BF_K_UPDATE, [&] { return launch_update(t, D.x, D.pose, c->ex->st); });
   }
   const double wd = prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense;
   linearise<Acc>(c, D, prm, wd, MODE_ENERGY);
   run_k(c, BF_K_ENERGY, [&] {
-    return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)prm.n_gn * T.n_prob * PAIREN, c->st);
+    return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)prm.n_gn * T.n_prob * PAIREN, c->ex->st);
   });
   CK(cudaGetLastError(), "solve launches");
   return BF_OK;
@@ -1082,23 +1165,23 @@ bf_status run_gn_graph(bf_ctx *c, const HostTables &T, const bf_solve_params &pr
   const int dims[8] = {T.n_frames, T.n_pairs, T.n_dp, T.n_tiles, T.n_segs, T.n_vars, T.n_prob, mixed ? 1 : 0};
   std::memcpy(kp, dims, sizeof(dims));
   kp += sizeof(dims);
-  const void *ptrs[9] = {c->ws, c->A, c->B, c->cP, c->cQ, c->kx, c->ky, (void *)c->st, (void *)c->ws_bytes};
+  const void *ptrs[9] = {c->ex->ws, c->A, c->B, c->cP, c->cQ, c->kx, c->ky, (void *)c->ex->st, (void *)c->ex->ws_bytes};
   std::memcpy(kp, ptrs, sizeof(ptrs));
-  const bool tables_same = c->last_ws == (const void *)c->ws && c->last_ints == pack_ints(T);
-  if (c->gexec && tables_same && c->gkey == key) {
-    CK(cudaGraphLaunch(c->gexec, c->st), "graph launch");
-    c->launches += c->gkernels;
+  const bool tables_same = c->ex->last_ws == (const void *)c->ex->ws && c->ex->last_ints == pack_ints(T);
+  if (c->ex->gexec && tables_same && c->ex->gkey == key) {
+    CK(cudaGraphLaunch(c->ex->gexec, c->ex->st), "graph launch");
+    c->launches += c->ex->gkernels;
     return BF_OK;
   }
-  if (c->gexec) {
-    cudaGraphExecDestroy(c->gexec);
-    c->gexec = nullptr;
+  if (c->ex->gexec) {
+    cudaGraphExecDestroy(c->ex->gexec);
+    c->ex->gexec = nullptr;
   }
-  CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal), "begin capture");
+  CK(cudaStreamBeginCapture(c->ex->st, cudaStreamCaptureModeThreadLocal), "begin capture");
   const long long before = c->launches;
   bf_status s = mixed ? run_gn<double>(c, T, prm, D) : run_gn<float>(c, T, prm, D);
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(c->st, &g);
+  cudaError_t e = cudaStreamEndCapture(c->ex->st, &g);
   if (s) {
     if (g) cudaGraphDestroy(g);
     return s;
@@ -1108,10 +1191,10 @@ bf_status run_gn_graph(bf_ctx *c, const HostTables &T, const bf_solve_params &pr
   e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-  c->gexec = ge;
-  c->gkey = key;
-  c->gkernels = (int)(c->launches - before);
-  CK(cudaGraphLaunch(c->gexec, c->st), "graph launch");
+  c->ex->gexec = ge;
+  c->ex->gkey = key;
+  c->ex->gkernels = (int)(c->launches - before);
+  CK(cudaGraphLaunch(c->ex->gexec, c->ex->st), "graph launch");
   return BF_OK;
 }
 
@@ -1132,15 +1215,29 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
 }
 
 // Solve a set of problems; writes final poses per problem and stats.
-bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm,
-                         std::vector<std::vector<Pose12>> &out, bf_solve_stats *stats) {
-  const auto t0 = std::chrono::steady_clock::now();
+// A solve whose device work has been enqueued on an executor's stream.
+struct SolveJob {
   HostTables T;
+  DevSolve D;
+  bf_solve_params prm;
+  std::vector<int> sizes;  // frames per problem
+  size_t n_pose = 0, n_en = 0, o_en = 0, o_vf = 0, o_pf = 0, o_sm = 0, o_sa = 0, o_ce = 0;
+  std::chrono::steady_clock::time_point t0;
+};
+
+// Phase 1 (context lock held): build the tables, upload, enqueue the Gauss-Newton loop and the
+// asynchronous result copies into the executor's pinned staging.
+bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm, SolveJob &J) {
+  J.t0 = std::chrono::steady_clock::now();
+  J.prm = prm;
+  J.sizes.clear();
+  for (const Problem &P : probs) J.sizes.push_back((int)P.ids.size());
+  HostTables &T = J.T;
+  DevSolve &D = J.D;
   bf_status s = build_tables(c, probs, prm, T);
   if (s) return s;
   const bool mixed = prm.precision == BF_PREC_MIXED;
   const size_t acc_size = mixed ? sizeof(double) : sizeof(float);
-  DevSolve D;
   s = prepare(c, T, prm.n_gn, acc_size, false, D, prm.pcg_variant);
   if (s) return s;
   if (prm.use_graph && !c->prof) {
@@ -1149,49 +1246,59 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
     s = mixed ? run_gn<double>(c, T, prm, D) : run_gn<float>(c, T, prm, D);
   }
   if (s) return s;
-  // results into pinned staging with asynchronous copies, then one synchronisation
-  const size_t n_pose = T.pose.size(), n_en = (size_t)(prm.n_gn + 1) * T.n_prob * PAIREN;
-  const size_t o_en = n_pose * 8, o_vf = o_en + n_en * 8, o_pf = o_vf + 4 * (size_t)T.n_vars,
-               o_sm = o_pf + 4 * (size_t)T.n_prob, o_sa = o_sm + 4 * (size_t)T.n_segs, o_ce = o_sa + 4 * (size_t)T.n_segs,
-               n_all = o_ce + 16;
-  s = ensure_pinned(c, n_all);
+  J.n_pose = T.pose.size();
+  J.n_en = (size_t)(prm.n_gn + 1) * T.n_prob * PAIREN;
+  J.o_en = J.n_pose * 8;
+  J.o_vf = J.o_en + J.n_en * 8;
+  J.o_pf = J.o_vf + 4 * (size_t)T.n_vars;
+  J.o_sm = J.o_pf + 4 * (size_t)T.n_prob;
+  J.o_sa = J.o_sm + 4 * (size_t)T.n_segs;
+  J.o_ce = J.o_sa + 4 * (size_t)T.n_segs;
+  s = ensure_pinned(c, J.o_ce + 16);
   if (s) return s;
-  unsigned char *pb = c->pin;
-  CK(cudaMemcpyAsync(pb, D.pose, n_pose * 8, cudaMemcpyDeviceToHost, c->st), "poses");
-  CK(cudaMemcpyAsync(pb + o_en, D.energy, n_en * 8, cudaMemcpyDeviceToHost, c->st), "energy");
-  if (T.n_vars) CK(cudaMemcpyAsync(pb + o_vf, D.vflags, 4 * (size_t)T.n_vars, cudaMemcpyDeviceToHost, c->st), "flags");
-  CK(cudaMemcpyAsync(pb + o_pf, D.pflags, 4 * (size_t)T.n_prob, cudaMemcpyDeviceToHost, c->st), "flags");
+  unsigned char *pb = c->ex->pin;
+  cudaStream_t st = c->ex->st;
+  CK(cudaMemcpyAsync(pb, D.pose, J.n_pose * 8, cudaMemcpyDeviceToHost, st), "poses");
+  CK(cudaMemcpyAsync(pb + J.o_en, D.energy, J.n_en * 8, cudaMemcpyDeviceToHost, st), "energy");
+  if (T.n_vars) CK(cudaMemcpyAsync(pb + J.o_vf, D.vflags, 4 * (size_t)T.n_vars, cudaMemcpyDeviceToHost, st), "flags");
+  CK(cudaMemcpyAsync(pb + J.o_pf, D.pflags, 4 * (size_t)T.n_prob, cudaMemcpyDeviceToHost, st), "flags");
   if (T.n_segs) {
-    CK(cudaMemcpyAsync(pb + o_sm, D.srmax, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, c->st), "rmax");
-    CK(cudaMemcpyAsync(pb + o_sa, D.srarg, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, c->st), "rmax");
+    CK(cudaMemcpyAsync(pb + J.o_sm, D.srmax, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, st), "rmax");
+    CK(cudaMemcpyAsync(pb + J.o_sa, D.srarg, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, st), "rmax");
   }
-  std::memset(pb + o_ce, 0, 8);
+  std::memset(pb + J.o_ce, 0, 8);
   if (D.coop_grid > 0)
-    CK(cudaMemcpyAsync(pb + o_ce, (char *)D.coop + 8, sizeof(int), cudaMemcpyDeviceToHost, c->st), "pcg status");
-  CK(cudaMemcpyAsync(pb + o_ce + 4, D.derr, sizeof(int), cudaMemcpyDeviceToHost, c->st), "dense status");
-  CK(cudaStreamSynchronize(c->st), "solve");
-  std::vector<double> pose(n_pose), energy(n_en);
+    CK(cudaMemcpyAsync(pb + J.o_ce, (char *)D.coop + 8, sizeof(int), cudaMemcpyDeviceToHost, st), "pcg status");
+  CK(cudaMemcpyAsync(pb + J.o_ce + 4, D.derr, sizeof(int), cudaMemcpyDeviceToHost, st), "dense status");
+  return BF_OK;
+}
+
+// Phase 3 (after the executor's stream is synchronised, context lock held): unpack the results.
+bf_status finish_solve(bf_ctx *c, SolveJob &J, std::vector<std::vector<Pose12>> &out, bf_solve_stats *stats) {
+  const HostTables &T = J.T;
+  const bf_solve_params &prm = J.prm;
+  const unsigned char *pb = c->ex->pin;
+  std::vector<double> pose(J.n_pose), energy(J.n_en);
   std::vector<int> vflags(T.n_vars), pflags(T.n_prob), srarg(T.n_segs);
   std::vector<float> srmax(T.n_segs);
-  std::memcpy(pose.data(), pb, n_pose * 8);
-  std::memcpy(energy.data(), pb + o_en, n_en * 8);
-  if (T.n_vars) std::memcpy(vflags.data(), pb + o_vf, 4 * (size_t)T.n_vars);
-  std::memcpy(pflags.data(), pb + o_pf, 4 * (size_t)T.n_prob);
+  std::memcpy(pose.data(), pb, J.n_pose * 8);
+  std::memcpy(energy.data(), pb + J.o_en, J.n_en * 8);
+  if (T.n_vars) std::memcpy(vflags.data(), pb + J.o_vf, 4 * (size_t)T.n_vars);
+  std::memcpy(pflags.data(), pb + J.o_pf, 4 * (size_t)T.n_prob);
   if (T.n_segs) {
-    std::memcpy(srmax.data(), pb + o_sm, 4 * (size_t)T.n_segs);
-    std::memcpy(srarg.data(), pb + o_sa, 4 * (size_t)T.n_segs);
+    std::memcpy(srmax.data(), pb + J.o_sm, 4 * (size_t)T.n_segs);
+    std::memcpy(srarg.data(), pb + J.o_sa, 4 * (size_t)T.n_segs);
   }
   int coop_err = 0, dense_err = 0;
-  std::memcpy(&coop_err, pb + o_ce, 4);
-  std::memcpy(&dense_err, pb + o_ce + 4, 4);
+  std::memcpy(&coop_err, pb + J.o_ce, 4);
+  std::memcpy(&dense_err, pb + J.o_ce + 4, 4);
   if (coop_err) return fail(c, BF_ERR_TIMEOUT, "PCG grid barrier timed out");
   if (dense_err) return fail(c, BF_ERR_TIMEOUT, "dense kernel: frame copy into shared memory timed out");
-  const double ms =
-      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - J.t0).count();
   out.assign(T.n_prob, {});
   for (int pi = 0; pi < T.n_prob; ++pi) {
     const int F0 = T.prob_frame0[pi];
-    const int n = (int)probs[pi].ids.size();
+    const int n = J.sizes[pi];
     for (int k = 0; k < n; ++k) {
       Pose12 p;
       for (int q = 0; q < 12; ++q) p[q] = pose[(size_t)(F0 + k) * 12 + q];
@@ -1231,6 +1338,15 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
   return BF_OK;
 }
 
+bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm,
+                         std::vector<std::vector<Pose12>> &out, bf_solve_stats *stats) {
+  SolveJob J;
+  bf_status s = enqueue_solve(c, probs, prm, J);
+  if (s) return s;
+  CK(cudaStreamSynchronize(c->ex->st), "solve");
+  return finish_solve(c, J, out, stats);
+}
+
 Pose12 world_of(bf_ctx *c, int id) {
   auto it = c->frames.find(id);
   if (it == c->frames.end()) return ident12();
@@ -1258,9 +1374,9 @@ Pose12 world_of(bf_ctx *c, int id) {
 }  // namespace
 
 // ---------------------------------------------------------------------------- local solves
-static bf_status local_batch(bf_ctx *c, int n_chunks, const int *chunk_ids, const int *frame_ids, const int *offsets,
-                             const bf_solve_params *params, bf_solve_stats *stats) {
-  std::vector<Problem> probs(n_chunks);
+static bf_status make_local_problems(bf_ctx *c, int n_chunks, const int *chunk_ids, const int *frame_ids,
+                                     const int *offsets, const bf_solve_params *params, std::vector<Problem> &probs) {
+  probs.assign(n_chunks, Problem());
   for (int k = 0; k < n_chunks; ++k) {
     const int n = offsets[k + 1] - offsets[k];
     if (n < 1) return fail(c, BF_ERR_INVALID_ARG, "local solve: a chunk needs at least one frame");
@@ -1275,9 +1391,11 @@ static bf_status local_batch(bf_ctx *c, int n_chunks, const int *chunk_ids, cons
             if (ch->second.frames[b] == P.ids[a]) P.init[a] = ch->second.local[b];
     }
   }
-  std::vector<std::vector<Pose12>> out;
-  bf_status s = solve_problems(c, probs, *params, out, stats);
-  if (s) return s;
+  return BF_OK;
+}
+
+static void commit_local(bf_ctx *c, int n_chunks, const int *chunk_ids, const std::vector<Problem> &probs,
+                         const std::vector<std::vector<Pose12>> &out) {
   for (int k = 0; k < n_chunks; ++k) {
     Chunk &C = c->chunks[chunk_ids[k]];
     C.frames = probs[k].ids;
@@ -1285,12 +1403,24 @@ static bf_status local_batch(bf_ctx *c, int n_chunks, const int *chunk_ids, cons
     c->frames[C.frames[0]].keyframe_of = chunk_ids[k];
     for (size_t a = 1; a < C.frames.size(); ++a) c->frames[C.frames[a]].member_of = chunk_ids[k];
   }
+}
+
+static bf_status local_batch(bf_ctx *c, int n_chunks, const int *chunk_ids, const int *frame_ids, const int *offsets,
+                             const bf_solve_params *params, bf_solve_stats *stats) {
+  std::vector<Problem> probs;
+  bf_status s = make_local_problems(c, n_chunks, chunk_ids, frame_ids, offsets, params, probs);
+  if (s) return s;
+  std::vector<std::vector<Pose12>> out;
+  s = solve_problems(c, probs, *params, out, stats);
+  if (s) return s;
+  commit_local(c, n_chunks, chunk_ids, probs, out);
   return BF_OK;
 }
 
 extern "C" bf_status bf_solve_local(bf_ctx *c, int chunk_id, const int *frame_ids, int n,
                                     const bf_solve_params *params, bf_solve_stats *stats) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (!frame_ids || n < 1) return fail(c, BF_ERR_INVALID_ARG, "bf_solve_local: bad frame list");
   bf_status s = check_params(c, params);
   if (s) return s;
@@ -1301,6 +1431,7 @@ extern "C" bf_status bf_solve_local(bf_ctx *c, int chunk_id, const int *frame_id
 extern "C" bf_status bf_solve_local_batch(bf_ctx *c, int n_chunks, const int *chunk_ids, const int *frame_ids,
                                           const int *offsets, const bf_solve_params *params, bf_solve_stats *stats) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (n_chunks < 0 || (n_chunks > 0 && (!chunk_ids || !frame_ids || !offsets)))
     return fail(c, BF_ERR_INVALID_ARG, "bf_solve_local_batch: bad arguments");
   if (n_chunks == 0) return BF_OK;
@@ -1311,14 +1442,9 @@ extern "C" bf_status bf_solve_local_batch(bf_ctx *c, int n_chunks, const int *ch
 }
 
 // --------------------------------------------------------------------------- global solve
-extern "C" bf_status bf_solve_global(bf_ctx *c, const int *keyframe_ids, int n, const bf_solve_params *params,
-                                     bf_solve_stats *stats) {
-  if (!c) return BF_ERR_INVALID_ARG;
-  if (!keyframe_ids || n < 1) return fail(c, BF_ERR_INVALID_ARG, "bf_solve_global: bad keyframe list");
-  bf_status s = check_params(c, params);
-  if (s) return s;
-  Problem P;
+static bf_status make_global_problem(bf_ctx *c, const int *keyframe_ids, int n, Problem &P) {
   P.ids.assign(keyframe_ids, keyframe_ids + n);
+  P.init.clear();
   for (int k = 0; k < n; ++k) {
     auto it = c->frames.find(P.ids[k]);
     if (it == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_solve_global: unknown keyframe id");
@@ -1340,20 +1466,38 @@ extern "C" bf_status bf_solve_global(bf_ctx *c, const int *keyframe_ids, int n, 
     }
     P.init.push_back(init);
   }
+  return BF_OK;
+}
+
+static void commit_global(bf_ctx *c, const Problem &P, const std::vector<Pose12> &out) {
+  for (size_t k = 0; k < P.ids.size(); ++k) {
+    FrameInfo &f = c->frames[P.ids[k]];
+    std::memcpy(f.world, out[k].data(), sizeof(f.world));
+    f.has_world = true;
+  }
+}
+
+extern "C" bf_status bf_solve_global(bf_ctx *c, const int *keyframe_ids, int n, const bf_solve_params *params,
+                                     bf_solve_stats *stats) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (!keyframe_ids || n < 1) return fail(c, BF_ERR_INVALID_ARG, "bf_solve_global: bad keyframe list");
+  bf_status s = check_params(c, params);
+  if (s) return s;
+  Problem P;
+  s = make_global_problem(c, keyframe_ids, n, P);
+  if (s) return s;
   std::vector<Problem> probs{P};
   std::vector<std::vector<Pose12>> out;
   s = solve_problems(c, probs, *params, out, stats);
   if (s) return s;
-  for (int k = 0; k < n; ++k) {
-    FrameInfo &f = c->frames[P.ids[k]];
-    std::memcpy(f.world, out[0][k].data(), sizeof(f.world));
-    f.has_world = true;
-  }
+  commit_global(c, P, out[0]);
   return BF_OK;
 }
 
 extern "C" bf_status bf_get_poses(bf_ctx *c, const int *frame_ids, int n, double *out) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (n < 0 || (n > 0 && (!frame_ids || !out))) return fail(c, BF_ERR_INVALID_ARG, "bf_get_poses: bad arguments");
   for (int k = 0; k < n; ++k) {
     if (!c->frames.count(frame_ids[k])) return fail(c, BF_ERR_NOT_FOUND, "bf_get_poses: unknown frame id");
@@ -1367,21 +1511,21 @@ template <typename Acc>
 static bf_status build_system_t(bf_ctx *c, const HostTables &T, DevSolve &D, const bf_solve_params &prm, double *A,
                                 double *b, double *energy4, long long *n_dense) {
   linearise<Acc>(c, D, prm, prm.w_dense, MODE_ACCUM);
-  run_k(c, BF_K_ENERGY, [&] { return launch_energy_reduce<Acc>(D.t, (const Acc *)D.pairen, D.energy, c->st); });
+  run_k(c, BF_K_ENERGY, [&] { return launch_energy_reduce<Acc>(D.t, (const Acc *)D.pairen, D.energy, c->ex->st); });
   run_k(c, BF_K_ASSEMBLE, [&] {
     return launch_assemble<Acc>(D.t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv,
-                                D.vflags, c->st);
+                                D.vflags, c->ex->st);
   });
   CK(cudaGetLastError(), "build system launches");
   std::vector<Acc> Dd((size_t)T.n_vars * 36), rhs((size_t)T.n_vars * 6), pb((size_t)T.n_pairs * PAIRBLK);
   double en[PAIREN];
   if (T.n_vars) {
-    CK(cudaMemcpyAsync(Dd.data(), D.Dd, Dd.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->st), "Dd");
-    CK(cudaMemcpyAsync(rhs.data(), D.rhs, rhs.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->st), "rhs");
+    CK(cudaMemcpyAsync(Dd.data(), D.Dd, Dd.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->ex->st), "Dd");
+    CK(cudaMemcpyAsync(rhs.data(), D.rhs, rhs.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->ex->st), "rhs");
   }
-  if (T.n_pairs) CK(cudaMemcpyAsync(pb.data(), D.pairblk, pb.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->st), "pb");
-  CK(cudaMemcpyAsync(en, D.energy, sizeof(en), cudaMemcpyDeviceToHost, c->st), "energy");
-  CK(cudaStreamSynchronize(c->st), "build system");
+  if (T.n_pairs) CK(cudaMemcpyAsync(pb.data(), D.pairblk, pb.size() * sizeof(Acc), cudaMemcpyDeviceToHost, c->ex->st), "pb");
+  CK(cudaMemcpyAsync(en, D.energy, sizeof(en), cudaMemcpyDeviceToHost, c->ex->st), "energy");
+  CK(cudaStreamSynchronize(c->ex->st), "build system");
   const int m = 6 * T.n_vars;
   std::fill(A, A + (size_t)m * m, 0.0);
   for (int v = 0; v < T.n_vars; ++v) {
@@ -1412,6 +1556,7 @@ extern "C" bf_status bf_build_system(bf_ctx *c, const int *frame_ids, int n, con
                                      const bf_solve_params *params, double *A, double *b, double *energy4,
                                      long long *n_dense) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (!frame_ids || n < 1 || !poses || !A || !b || !energy4)
     return fail(c, BF_ERR_INVALID_ARG, "bf_build_system: bad arguments");
   bf_status s = check_params(c, params);
@@ -1433,6 +1578,7 @@ extern "C" bf_status bf_build_system(bf_ctx *c, const int *frame_ids, int n, con
 extern "C" bf_status bf_debug_association(bf_ctx *c, int frame_i, int frame_j, const double *pose_i,
                                           const double *pose_j, const bf_solve_params *params, int32_t *out_target) {
   if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
   if (!pose_i || !pose_j || !out_target || frame_i == frame_j)
     return fail(c, BF_ERR_INVALID_ARG, "bf_debug_association: bad arguments");
   bf_status s = check_params(c, params);
@@ -1480,13 +1626,244 @@ extern "C" bf_status bf_debug_association(bf_ctx *c, int frame_i, int frame_j, c
   Gates g;
   g.tau_d2 = (float)(params->tau_dist * params->tau_dist);
   g.tau_n = (float)params->tau_normal;
-  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(D.t, D.pose, D.pairM, c->st); });
+  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(D.t, D.pose, D.pairM, c->ex->st); });
   run_k(c, BF_K_DENSE, [&] {
     return launch_dense<float>(MODE_ASSOC, D.t, frame_store(c), c->intr, D.pairM, g, 0.f, 0.f, nullptr, D.assoc,
-                               c->st);
+                               c->ex->st);
   });
   CK(cudaGetLastError(), "association launch");
-  CK(cudaMemcpyAsync(out_target, D.assoc, HW * sizeof(int), cudaMemcpyDeviceToHost, c->st), "association");
-  CK(cudaStreamSynchronize(c->st), "association");
+  CK(cudaMemcpyAsync(out_target, D.assoc, HW * sizeof(int), cudaMemcpyDeviceToHost, c->ex->st), "association");
+  CK(cudaStreamSynchronize(c->ex->st), "association");
   return BF_OK;
+}
+
+// ------------------------------------------------------------------------------- serving
+// Continuous batching on a persistent context.  A worker slot takes the request at the head of
+// the queue and, for local solves, every following local request with identical parameters (up
+// to max_batch): the batch is one bf_solve_local_batch problem set.  It enqueues the batch on
+// its own stream under the context lock, waits for the GPU without the lock (other slots form
+// and launch their batches meanwhile, so batches overlap on the device), then unpacks results
+// under the lock.  Admission: a batch whose solve workspace would exceed the context's HBM budget
+// is halved and the rest returned to the queue head; a single request that cannot fit fails with
+// BF_ERR_OUT_OF_MEMORY.
+static void complete_requests(Server &S, const std::vector<uint64_t> &batch, bf_status st,
+                              const std::vector<bf_solve_stats> *stats) {
+  std::lock_guard<std::mutex> q(S.qm);
+  const auto now = std::chrono::steady_clock::now();
+  for (size_t k = 0; k < batch.size(); ++k) {
+    auto it = S.reqs.find(batch[k]);
+    if (it == S.reqs.end()) continue;
+    ServeReq &r = it->second;
+    r.done = true;
+    r.status = st;
+    if (stats && k < stats->size()) r.stats = (*stats)[k];
+    r.stats.ms = std::chrono::duration<double, std::milli>(now - r.t_submit).count();
+  }
+  S.dcv.notify_all();
+}
+
+static void run_batch(bf_ctx *c, Exec &ex, std::vector<uint64_t> batch) {
+  Server &S = *c->srv;
+  while (!batch.empty()) {
+    std::vector<Problem> probs;
+    std::vector<int> chunk_ids;
+    bf_solve_params prm{};
+    int kind = 0;
+    {
+      std::lock_guard<std::mutex> q(S.qm);
+      const ServeReq &h = S.reqs[batch[0]];
+      kind = h.kind;
+      prm = h.prm;
+    }
+    std::unique_lock<std::mutex> lk(c->mu);
+    c->ex = &ex;
+    bf_status st = check_params(c, &prm);
+    if (!st) {
+      if (cudaStreamWaitEvent(ex.st, c->data_ev, 0) != cudaSuccess) {
+        cudaGetLastError();
+        st = BF_ERR_CUDA;
+      }
+    }
+    if (!st) {
+      std::lock_guard<std::mutex> q(S.qm);
+      if (kind == BF_REQ_GLOBAL) {
+        const ServeReq &r = S.reqs[batch[0]];
+        Problem P;
+        st = make_global_problem(c, r.ids.data(), (int)r.ids.size(), P);
+        probs.push_back(P);
+      } else {
+        std::vector<int> flat, offs{0};
+        for (uint64_t t : batch) {
+          const ServeReq &r = S.reqs[t];
+          flat.insert(flat.end(), r.ids.begin(), r.ids.end());
+          offs.push_back((int)flat.size());
+          chunk_ids.push_back(r.chunk_id);
+        }
+        st = make_local_problems(c, (int)batch.size(), chunk_ids.data(), flat.data(), offs.data(), &prm, probs);
+      }
+    }
+    SolveJob J;
+    if (!st) st = enqueue_solve(c, probs, prm, J);
+    if (st == BF_ERR_OUT_OF_MEMORY && batch.size() > 1) {
+      // admission: return the second half to the head of the queue and retry with the first
+      c->ex = &c->main;
+      lk.unlock();
+      const size_t half = batch.size() / 2;
+      {
+        std::lock_guard<std::mutex> q(S.qm);
+        for (size_t k = batch.size(); k-- > half;) S.pending.push_front(batch[k]);
+        S.qcv.notify_one();
+      }
+      batch.resize(half);
+      continue;
+    }
+    if (st) {
+      c->ex = &c->main;
+      lk.unlock();
+      complete_requests(S, batch, st, nullptr);
+      return;
+    }
+    ++c->in_flight;
+    c->ex = &c->main;
+    lk.unlock();
+    const cudaError_t e = cudaStreamSynchronize(ex.st);
+    lk.lock();
+    c->ex = &ex;
+    std::vector<bf_solve_stats> stats(probs.size());
+    std::vector<std::vector<Pose12>> out;
+    st = e != cudaSuccess ? cuda_fail(c, e, "serving batch") : finish_solve(c, J, out, stats.data());
+    if (!st) {
+      if (kind == BF_REQ_GLOBAL)
+        commit_global(c, probs[0], out[0]);
+      else
+        commit_local(c, (int)probs.size(), chunk_ids.data(), probs, out);
+    }
+    --c->in_flight;
+    c->ex = &c->main;
+    c->busy_cv.notify_all();
+    lk.unlock();
+    complete_requests(S, batch, st, &stats);
+    return;
+  }
+}
+
+static void serve_worker(bf_ctx *c, int slot) {
+  cudaSetDevice(c->cfg.device);
+  Server &S = *c->srv;
+  Exec &ex = *S.slots[slot];
+  for (;;) {
+    std::vector<uint64_t> batch;
+    {
+      std::unique_lock<std::mutex> q(S.qm);
+      S.qcv.wait(q, [&] { return S.stop || !S.pending.empty(); });
+      if (S.stop) return;
+      const uint64_t h = S.pending.front();
+      S.pending.pop_front();
+      batch.push_back(h);
+      const ServeReq &hr = S.reqs[h];
+      if (hr.kind == BF_REQ_LOCAL) {
+        while (!S.pending.empty() && (int)batch.size() < S.max_batch) {
+          const ServeReq &nr = S.reqs[S.pending.front()];
+          if (nr.kind != BF_REQ_LOCAL || std::memcmp(&nr.prm, &hr.prm, sizeof(bf_solve_params)) != 0) break;
+          batch.push_back(S.pending.front());
+          S.pending.pop_front();
+        }
+      }
+    }
+    run_batch(c, ex, batch);
+  }
+}
+
+extern "C" bf_status bf_serve_start(bf_ctx *c, int n_slots, int max_batch, int max_queue) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (c->srv) return fail(c, BF_ERR_INVALID_ARG, "bf_serve_start: already serving");
+  if (n_slots < 1 || n_slots > 8 || max_batch < 1 || max_queue < 1)
+    return fail(c, BF_ERR_INVALID_ARG, "bf_serve_start: need 1 <= n_slots <= 8, max_batch >= 1, max_queue >= 1");
+  std::unique_ptr<Server> S(new Server());
+  S->max_batch = max_batch;
+  S->max_queue = max_queue;
+  for (int k = 0; k < n_slots; ++k) {
+    std::unique_ptr<Exec> e(new Exec());
+    if (cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto &x : S->slots) cudaStreamDestroy(x->st);
+      return fail(c, BF_ERR_CUDA, "bf_serve_start: stream creation failed");
+    }
+    S->slots.push_back(std::move(e));
+  }
+  c->srv = std::move(S);
+  for (int k = 0; k < n_slots; ++k) c->srv->workers.emplace_back(serve_worker, c, k);
+  return BF_OK;
+}
+
+extern "C" bf_status bf_serve_stop(bf_ctx *c) {
+  if (!c || !c->srv) return BF_OK;
+  Server &S = *c->srv;
+  {
+    std::lock_guard<std::mutex> q(S.qm);
+    S.stop = true;
+    S.qcv.notify_all();
+  }
+  for (auto &t : S.workers) t.join();
+  std::vector<uint64_t> cancelled;
+  {
+    std::lock_guard<std::mutex> q(S.qm);
+    cancelled.assign(S.pending.begin(), S.pending.end());
+    S.pending.clear();
+  }
+  complete_requests(S, cancelled, BF_ERR_BUSY, nullptr);
+  std::unique_lock<std::mutex> lk(c->mu);
+  for (auto &e : S.slots) {
+    cudaStreamSynchronize(e->st);
+    free_exec(c, *e);
+    cudaStreamDestroy(e->st);
+  }
+  cudaGetLastError();
+  c->srv.reset();
+  return BF_OK;
+}
+
+extern "C" bf_status bf_submit(bf_ctx *c, const bf_request *req, uint64_t *ticket) {
+  if (!c || !req || !ticket) return BF_ERR_INVALID_ARG;
+  if (!c->srv) return BF_ERR_INVALID_ARG;
+  if ((req->kind != BF_REQ_LOCAL && req->kind != BF_REQ_GLOBAL) || !req->frame_ids || req->n < 1)
+    return BF_ERR_INVALID_ARG;
+  Server &S = *c->srv;
+  std::lock_guard<std::mutex> q(S.qm);
+  if ((int)S.pending.size() >= S.max_queue) return BF_ERR_BUSY;
+  const uint64_t t = S.next_ticket++;
+  ServeReq &r = S.reqs[t];
+  r.kind = req->kind;
+  r.chunk_id = req->chunk_id;
+  r.ids.assign(req->frame_ids, req->frame_ids + req->n);
+  r.prm = req->params;
+  r.prm.use_graph = 0;  // batches differ from one another: no graph reuse
+  r.t_submit = std::chrono::steady_clock::now();
+  S.pending.push_back(t);
+  S.qcv.notify_one();
+  *ticket = t;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_wait(bf_ctx *c, uint64_t ticket, int timeout_ms, bf_solve_stats *stats) {
+  if (!c || !c->srv) return BF_ERR_INVALID_ARG;
+  Server &S = *c->srv;
+  std::unique_lock<std::mutex> q(S.qm);
+  auto it = S.reqs.find(ticket);
+  if (it == S.reqs.end()) return BF_ERR_NOT_FOUND;
+  auto ready = [&] {
+    auto jt = S.reqs.find(ticket);
+    return jt == S.reqs.end() || jt->second.done;
+  };
+  if (timeout_ms < 0)
+    S.dcv.wait(q, ready);
+  else if (!S.dcv.wait_for(q, std::chrono::milliseconds(timeout_ms), ready))
+    return BF_ERR_TIMEOUT;
+  it = S.reqs.find(ticket);
+  if (it == S.reqs.end()) return BF_ERR_NOT_FOUND;
+  const bf_status st = it->second.status;
+  if (stats) *stats = it->second.stats;
+  S.reqs.erase(it);
+  return st;
 }
