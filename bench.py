@@ -369,7 +369,10 @@ def run_ours(args, rank, world, local_rank):
                               "ms_per_step": statistics.mean(tp), "final_energy": stp["energy"][-1]}
 
         line["chunk_latency"] = chunk_latency(bf, torch, dev)
-        line["chunk_batch"] = chunk_batch_leg(bf, torch, dev, stream)
+        import synth
+        cprob = synth.cfg3()
+        line["chunk_batch"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob)
+        line["serving"] = serving_leg(bf, torch, dev, cprob, prob)
 
         v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
@@ -378,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
-def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256):
+def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None):
     """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.
 
     batched: all chunks in one launch sequence (one problem per chunk), mixed precision, replayed
@@ -386,7 +389,7 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256):
     re-runs frame preprocessing from device-resident raw frames.  Chunk-solve latency: call ->
     poses on the host; in the batched mode every chunk completes with its batch."""
     import synth
-    prob = synth.cfg3(n_chunks=n_chunks)
+    prob = prob or synth.cfg3(n_chunks=n_chunks)
     intr = prob.intr
     prm = prob.solve
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], stream=stream.cuda_stream,
@@ -466,6 +469,63 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256):
                             "algorithmic_GBps": alg_bytes / (dense_ms / 1000.0) / 1e9,
                             "unique_frame_bytes": int(prob.n_frames * HW * 32)}}
     ctx.close()
+    return out
+
+
+def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0, seed=1604):
+    """Serving: Poisson arrivals of chunk requests (320x240, 3-11 frames, 6 GN x 10 PCG) at `rate`
+    per second for `seconds`, and after every 10th chunk a global request over the first k
+    keyframes of the 300-keyframe 80x60 corridor (k grows from 100 to 300; 8 GN x 20 PCG).
+    served: continuous batching (2 slots, batches of up to 16, mixed precision); plain: the same
+    arrivals served one request at a time by the plain FP32 path (1 slot, batch 1).  Latency =
+    submit -> completion; p50 / p99 per request kind."""
+    rng = np.random.default_rng(seed)
+    n_req = int(seconds * rate)
+    gaps = rng.exponential(1.0 / rate, size=n_req)
+    ci, gi = chunk_prob.intr, global_prob.intr
+    lists = [c.tolist() for c in chunk_prob.chunks]
+    pc = {k: chunk_prob.solve[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
+    pg = {k: global_prob.solve[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
+    out = {"arrival_rate_per_s": rate, "seconds": seconds, "chunk_requests": n_req,
+           "global_requests": n_req // 10, "chunk_workload": chunk_prob.name, "global_workload": global_prob.name}
+    for name, slots, batch, prec in (("served", 2, 16, bf.BF_PREC_MIXED), ("plain_fp32", 1, 1, bf.BF_PREC_FP32)):
+        cctx = bf.Context(ci["W"], ci["H"], ci["fx"], ci["fy"], ci["cx"], ci["cy"], max_frames_hint=chunk_prob.n_frames)
+        cctx.add_frames(0, torch.from_numpy(chunk_prob.depth).to(dev), torch.from_numpy(chunk_prob.lum).to(dev))
+        cctx.add_correspondences_batch(chunk_prob.pairs, chunk_prob.corr_off, torch.from_numpy(chunk_prob.p_i).to(dev),
+                                       torch.from_numpy(chunk_prob.p_j).to(dev))
+        gctx = bf.Context(gi["W"], gi["H"], gi["fx"], gi["fy"], gi["cx"], gi["cy"], max_frames_hint=global_prob.n_frames)
+        gctx.add_frames(0, global_prob.depth, global_prob.lum, init_pose=global_prob.init)
+        gctx.add_correspondences_batch(global_prob.pairs, global_prob.corr_off, global_prob.p_i, global_prob.p_j)
+        torch.cuda.synchronize(dev)
+        cctx.serve_start(n_slots=slots, max_batch=batch, max_queue=4096)
+        gctx.serve_start(n_slots=1, max_batch=1, max_queue=4096)
+        cparams = bf.default_params(precision=prec, **pc)
+        gparams = bf.default_params(precision=prec, **pg)
+        ct, gt = [], []
+        t0 = time.perf_counter()
+        t_next = t0
+        for r in range(n_req):
+            t_next += gaps[r]
+            while time.perf_counter() < t_next:
+                time.sleep(0.0002)
+            ct.append(cctx.submit(lists[r % len(lists)], chunk_id=r, params=cparams))
+            if r % 10 == 9:
+                k = int(100 + 200 * r / max(1, n_req - 1))
+                gt.append(gctx.submit(list(range(k)), kind=bf._lib.BF_REQ_GLOBAL, params=gparams))
+        clat = [cctx.wait(t)[1]["ms"] for t in ct]
+        glat = [gctx.wait(t)[1]["ms"] for t in gt]
+        wall = time.perf_counter() - t0
+        cctx.serve_stop()
+        gctx.serve_stop()
+        cctx.close()
+        gctx.close()
+        clat.sort()
+        glat.sort()
+        q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))] if v else None  # noqa: E731
+        out[name] = {"chunk_p50_ms": q(clat, 0.5), "chunk_p99_ms": q(clat, 0.99), "global_p50_ms": q(glat, 0.5),
+                     "global_p99_ms": q(glat, 0.99), "solves_per_s": (len(clat) + len(glat)) / wall,
+                     "wall_s": wall, "slots": slots, "max_batch": batch,
+                     "precision": "mixed" if prec == bf.BF_PREC_MIXED else "fp32"}
     return out
 
 

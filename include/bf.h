@@ -233,7 +233,11 @@ bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const doub
 /*
  * Kernel accounting.  Every kernel the context launches is counted; with profiling enabled the
  * context also records a CUDA event pair around each launch on its stream and sums the device
- * time per kernel class.  bf_get_profile synchronises the stream.
+ * time per kernel class.  bf_get_profile synchronises the stream.  The pose update and the
+ * per-iteration energy record run inside the PCG kernel, so BF_K_UPDATE keeps its slot but counts
+ * no launches and BF_K_ENERGY counts only a solve's final energy evaluation.  BF_K_XFORM counts
+ * the pair-transform launches: one per solve when every problem is solved by the per-problem PCG
+ * kernel (which refreshes its pairs' transforms itself), one more per GN iteration otherwise.
  */
 enum {
   BF_K_PREPROCESS = 0, BF_K_XFORM, BF_K_DENSE, BF_K_SPARSE, BF_K_MERGE, BF_K_ASSEMBLE, BF_K_PCG, BF_K_UPDATE,

@@ -878,7 +878,7 @@ struct Arena {
 struct DevSolve {
   Tables t;
   double *pose;
-  float *pairM;
+  float *pairM;  // [n_pairs][2][12] pair transforms at the current poses
   void *dpart, *spart;
   float *srmax;
   int *srarg;
@@ -1083,14 +1083,14 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
   return BF_OK;
 }
 
-// One Gauss-Newton iteration's linearisation: pair transforms, dense + sparse partials, merge.
+// One Gauss-Newton iteration's linearisation at the pair transforms in D.pairM: dense + sparse
+// partials, merge.
 template <typename Acc>
 void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, int mode) {
   const Tables &t = D.t;
   Gates g;
   g.tau_d2 = (float)(prm.tau_dist * prm.tau_dist);
   g.tau_n = (float)prm.tau_normal;
-  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
   run_k(c, BF_K_DENSE, [&] {
     if (t.n_wi > 0)
       return launch_dense_staged<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
@@ -1115,33 +1115,39 @@ double wdense_at(const bf_solve_params &prm, int k) {
 template <typename Acc>
 bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, DevSolve &D) {
   const Tables &t = D.t;
+  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
   for (int k = 0; k < prm.n_gn; ++k) {
     const double wd = wdense_at(prm, k);
     linearise<Acc>(c, D, prm, wd, MODE_ACCUM);
-    run_k(c, BF_K_ENERGY, [&] {
-      return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)k * T.n_prob * PAIREN, c->ex->st);
-    });
     run_k(c, BF_K_ASSEMBLE, [&] {
       return launch_assemble<Acc>(t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv,
                                   D.vflags, c->ex->st);
     });
+    // the PCG kernel also records this linearisation's energy and applies the pose update; the
+    // per-problem kernel also refreshes the pair transforms, the multi-CTA ones leave that to
+    // k_pair_xform
+    PcgOut po;
+    po.energy = D.energy + (size_t)k * T.n_prob * PAIREN;
+    po.pose = D.pose;
+    po.pairM = (D.cluster > 0 || D.coop_grid > 0) ? nullptr : D.pairM;
+    const Acc *pen = (const Acc *)D.pairen;
     int pcg_rc = 0;
     run_k(c, BF_K_PCG, [&] {
       if (D.cluster > 0) {
         pcg_rc = launch_pcg_cluster<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, prm.n_pcg, D.pflags,
-                                         D.cluster, T.inc_off.data(), c->ex->st);
+                                         D.cluster, T.inc_off.data(), pen, po, c->ex->st);
         return pcg_rc < 0 ? 0 : pcg_rc;
       }
       if (D.coop_grid > 0) {
         pcg_rc = launch_pcg_coop<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.p1, D.q,
-                                      prm.n_pcg, D.pflags, D.coop, D.coop_grid, c->ex->st);
+                                      prm.n_pcg, D.pflags, D.coop, D.coop_grid, pen, po, c->ex->st);
         return pcg_rc < 0 ? 0 : pcg_rc;
       }
       return launch_pcg<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.q, prm.n_pcg,
-                             D.pflags, c->ex->st);
+                             D.pflags, pen, po, c->ex->st);
     });
     if (pcg_rc < 0) return cuda_fail(c, cudaGetLastError(), "PCG launch");
-    run_k(c, BF_K_UPDATE, [&] { return launch_update(t, D.x, D.pose, c->ex->st); });
+    if (!po.pairM) run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
   }
   const double wd = prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense;
   linearise<Acc>(c, D, prm, wd, MODE_ENERGY);
@@ -1510,6 +1516,7 @@ extern "C" bf_status bf_get_poses(bf_ctx *c, const int *frame_ids, int n, double
 template <typename Acc>
 static bf_status build_system_t(bf_ctx *c, const HostTables &T, DevSolve &D, const bf_solve_params &prm, double *A,
                                 double *b, double *energy4, long long *n_dense) {
+  run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(D.t, D.pose, D.pairM, c->ex->st); });
   linearise<Acc>(c, D, prm, prm.w_dense, MODE_ACCUM);
   run_k(c, BF_K_ENERGY, [&] { return launch_energy_reduce<Acc>(D.t, (const Acc *)D.pairen, D.energy, c->ex->st); });
   run_k(c, BF_K_ASSEMBLE, [&] {

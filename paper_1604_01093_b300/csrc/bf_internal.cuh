@@ -104,11 +104,95 @@ struct Gates {
 
 enum { MODE_ACCUM = 0, MODE_ENERGY = 1, MODE_ASSOC = 2 };
 
+// M = T_j^-1 T_i (source i, target j) from FP64 poses (R row-major, t), each entry summed left to
+// right with explicit FP64 rounding and rounded once to FP32 (the association decisions depend on
+// these exact values).  Entry e < 9 is R[e / 3][e % 3] = sum_k Rj[k][a] Ri[k][b]; entry 9 + a is
+// t[a] = sum_k Rj[k][a] (t_i - t_j)[k].
+__device__ __forceinline__ float pair_xform_entry(const double *Ti, const double *Tj, int e) {
+  if (e < 9) {
+    const int a = e / 3, b = e % 3;
+    return (float)__dadd_rn(__dadd_rn(__dmul_rn(Tj[a], Ti[b]), __dmul_rn(Tj[3 + a], Ti[3 + b])),
+                            __dmul_rn(Tj[6 + a], Ti[6 + b]));
+  }
+  const int a = e - 9;
+  const double d0 = __dsub_rn(Ti[9], Tj[9]), d1 = __dsub_rn(Ti[10], Tj[10]), d2 = __dsub_rn(Ti[11], Tj[11]);
+  return (float)__dadd_rn(__dadd_rn(__dmul_rn(Tj[a], d0), __dmul_rn(Tj[3 + a], d1)), __dmul_rn(Tj[6 + a], d2));
+}
+
+__device__ __forceinline__ void pair_xform32(const double *Ti, const double *Tj, float *M) {
+#pragma unroll
+  for (int e = 0; e < 12; ++e) M[e] = pair_xform_entry(Ti, Tj, e);
+}
+
+// Exp-map pose update R <- Exp(dw) R, t <- t + dt in FP64 (Rodrigues: Exp(dw) = I + A K + B K^2,
+// K = [dw]x, K^2 = dw dw^T - th^2 I, A = sin(th) / th, B = (1 - cos(th)) / th^2).  For th <= 1/2
+// (every step but a gross first one) A and B come from their Taylor series in th^2, eight terms
+// each, the first omitted term below 1e-17 relative: FP64 runs at 1/64 of the FP32 rate on B300
+// and the series needs 16 FMAs where sin, cos and two divisions need several times that.
+__device__ __forceinline__ void update_pose(double *T, const float *x) {
+  const double w0 = x[0], w1 = x[1], w2 = x[2];
+  const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
+  double A, B;
+  if (th2 <= 0.25) {
+    // A = sum_k (-1)^k th^2k / (2k+1)!,  B = sum_k (-1)^k th^2k / (2k+2)!,  k = 0..7
+    A = -1.0 / 1307674368000.0;
+    A = fma(A, th2, 1.0 / 6227020800.0);
+    A = fma(A, th2, -1.0 / 39916800.0);
+    A = fma(A, th2, 1.0 / 362880.0);
+    A = fma(A, th2, -1.0 / 5040.0);
+    A = fma(A, th2, 1.0 / 120.0);
+    A = fma(A, th2, -1.0 / 6.0);
+    A = fma(A, th2, 1.0);
+    B = -1.0 / 20922789888000.0;
+    B = fma(B, th2, 1.0 / 87178291200.0);
+    B = fma(B, th2, -1.0 / 479001600.0);
+    B = fma(B, th2, 1.0 / 3628800.0);
+    B = fma(B, th2, -1.0 / 40320.0);
+    B = fma(B, th2, 1.0 / 720.0);
+    B = fma(B, th2, -1.0 / 24.0);
+    B = fma(B, th2, 0.5);
+  } else {
+    const double th = sqrt(th2);
+    A = sin(th) / th;
+    B = (1.0 - cos(th)) / th2;
+  }
+  const double w[3] = {w0, w1, w2};
+  const double K[3][3] = {{0.0, -w2, w1}, {w2, 0.0, -w0}, {-w1, w0, 0.0}};
+  double E[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const double K2 = w[i] * w[j] - (i == j ? th2 : 0.0);
+      E[i][j] = (i == j ? 1.0 : 0.0) + A * K[i][j] + B * K2;
+    }
+  double R[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) R[3 * i + j] = E[i][0] * T[j] + E[i][1] * T[3 + j] + E[i][2] * T[6 + j];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) T[k] = R[k];
+  T[9] += (double)x[3];
+  T[10] += (double)x[4];
+  T[11] += (double)x[5];
+}
+
+// Per-GN-iteration outputs the PCG kernels write besides the step: the problem's energy record
+// (sum of its pairs' records, fixed order), the updated poses and (per-problem kernel only) the
+// pair transforms of the updated poses for the next linearisation.
+struct PcgOut {
+  double *energy;  // [n_prob][PAIREN], nullable
+  double *pose;    // poses updated in place with the step, nullable
+  float *pairM;    // [n_pairs][2][12] transforms at the updated poses, nullable
+};
+
 // ------------------------------------------------------------------ launch wrappers (host side)
 int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
                        float4 *A, float4 *B, uint4 *P16, float dmin, float dmax, cudaStream_t st);
 int launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, int swap, float4 *P, float4 *Q,
                       cudaStream_t st);
+int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st);
 int launch_pack_corr_batch(const float *p_i, const float *p_j, const float *w, int n_total, const int *off,
                            const int *swap, int n_pairs, float4 *P, float4 *Q, cudaStream_t st);
 // Target-staged dense kernel (whole target frame in shared memory, loaded by TMA bulk copies).
@@ -118,7 +202,6 @@ bool dense_staged_fits(int W, int H);
 template <typename Part>
 int launch_dense_staged(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                         float w_geo, float w_photo, Part *part, int *err, cudaStream_t st);
-int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st);
 template <typename Part>
 int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                   float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st);
@@ -133,24 +216,25 @@ int launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, A
                      int *vflags, cudaStream_t st);
 template <typename Acc>
 int launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
-                float *r, float *z, float *p, float *q, int n_pcg, int *pflags, cudaStream_t st);
+                float *r, float *z, float *p, float *q, int n_pcg, int *pflags, const Acc *pairen, PcgOut po,
+                cudaStream_t st);
 // One large problem over many CTAs (cooperative launch).  coop_mem: coop_mem_bytes(grid) bytes
 // of device memory (barrier state + per-CTA partials); its first 16 bytes are reset here.
 // Returns -1 if the cooperative launch was refused.
 template <typename Acc>
 int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
                     float *x, float *r, float *z, float *p0, float *p1, float *q, int n_pcg, int *pflags,
-                    void *coop_mem, int grid, cudaStream_t st);
+                    void *coop_mem, int grid, const Acc *pairen, PcgOut po, cudaStream_t st);
 int coop_grid_size(int n_vars);
 // One large problem on one thread-block cluster of cl CTAs (vectors replicated in shared memory).
 // Returns -1 if the launch was refused.
 template <typename Acc>
 int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
-                       float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, cudaStream_t st);
+                       float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, const Acc *pairen, PcgOut po,
+                       cudaStream_t st);
 size_t cluster_smem_bytes(int n_vars, int cl);
 int cluster_size_max();
 size_t coop_mem_bytes(int grid);
-int launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st);
 template <typename Acc>
 int launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st);
 

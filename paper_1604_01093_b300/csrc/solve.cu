@@ -8,10 +8,16 @@
 //                  fixed order) and the preconditioner: 6x6 Cholesky inverse (block-Jacobi) or the
 //                  inverse diagonal (Jacobi, the paper's choice)
 //   k_pcg          one CTA per problem (batches of small problems): exactly n_pcg PCG
-//                  iterations from x = 0, stopping early only if p.Ap <= 0 or r.z == 0
+//                  iterations from x = 0, stopping early only if p.Ap <= 0 or r.z == 0; a problem
+//                  with at most 16 free frames keeps its whole system in shared memory
 //   k_pcg_coop     one large problem over many CTAs (cooperative launch, all CTAs resident):
 //                  warp per frame, two grid barriers per iteration, deterministic dot products
-//   k_update       per free frame: R <- Exp(dw) R, t <- t + dt (FP64)
+//   k_pcg_cluster  one large problem on a thread-block cluster (distributed shared memory)
+// Each PCG kernel also writes the problem's energy record of the linearisation it solves (the
+// pairs' records summed in a fixed order) and, once the step is final, applies the exp-map pose
+// update R <- Exp(dw) R, t <- t + dt (FP64) to its free frames; k_pcg then forms its pairs'
+// transforms for the next linearisation.  A GN iteration of a batch of chunks is five launches:
+// dense, sparse, merge, assemble, PCG.
 //
 // The paper's solver (Sec. 4.4) sums the PCG scalars with warp shuffles plus global atomics in a
 // single kernel; here every dot product is reduced in a fixed order (warp tree, then CTA
@@ -31,31 +37,17 @@ namespace cgx = cooperative_groups;
 namespace bf {
 
 // ------------------------------------------------------------------------------- pair xform
+// Both transforms of every pair, one thread per pair: M_ab = T_b^-1 T_a (source a) then M_ba.
+// The per-problem PCG kernel refreshes its own pairs' transforms after the pose update; this
+// kernel serves the first linearisation of a solve and the multi-CTA PCG variants.
 __global__ void k_pair_xform(int n_pairs, const int *__restrict__ pa, const int *__restrict__ pb,
                              const double *__restrict__ pose, float *__restrict__ pairM) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n_pairs) return;
   const double *Ta = pose + 12 * pa[p];
   const double *Tb = pose + 12 * pb[p];
-#pragma unroll
-  for (int dir = 0; dir < 2; ++dir) {
-    const double *Ti = dir == 0 ? Ta : Tb;  // source
-    const double *Tj = dir == 0 ? Tb : Ta;  // target
-    float *M = pairM + p * 24 + dir * 12;
-    const double d0 = __dsub_rn(Ti[9], Tj[9]), d1 = __dsub_rn(Ti[10], Tj[10]), d2 = __dsub_rn(Ti[11], Tj[11]);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        // R[a][b] = (Rj[0][a] Ri[0][b] + Rj[1][a] Ri[1][b]) + Rj[2][a] Ri[2][b]
-        const double v = __dadd_rn(__dadd_rn(__dmul_rn(Tj[a], Ti[b]), __dmul_rn(Tj[3 + a], Ti[3 + b])),
-                                   __dmul_rn(Tj[6 + a], Ti[6 + b]));
-        M[3 * a + b] = (float)v;
-      }
-      const double tv = __dadd_rn(__dadd_rn(__dmul_rn(Tj[a], d0), __dmul_rn(Tj[3 + a], d1)), __dmul_rn(Tj[6 + a], d2));
-      M[9 + a] = (float)tv;
-    }
-  }
+  pair_xform32(Ta, Tb, pairM + 24 * p);
+  pair_xform32(Tb, Ta, pairM + 24 * p + 12);
 }
 
 int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st) {
@@ -137,7 +129,7 @@ __device__ __forceinline__ void slot_source(int s, bool src_is_a, int &idx, int 
   }
 }
 
-constexpr int MERGE_WARPS = 4;
+constexpr int MERGE_WARPS = 1;  // one warp per CTA spreads the pairs over the SMs
 
 template <typename Acc, typename Part>
 __global__ void __launch_bounds__(32 * MERGE_WARPS)
@@ -313,49 +305,76 @@ template int launch_pair_merge<float, float>(const Tables &, const double *, con
                                              float *, float *, cudaStream_t);
 
 // --------------------------------------------------------------------------------- assemble
-// 6x6 SPD inverse by Cholesky (FP64).  Returns false if the block is not positive definite.
-__device__ bool chol_inverse6(const double *D, double *Mi) {
-  double L[36];
-  for (int k = 0; k < 36; ++k) L[k] = 0.0;
-  for (int j = 0; j < 6; ++j) {
-    double s = D[6 * j + j];
-    for (int k = 0; k < j; ++k) s -= L[6 * j + k] * L[6 * j + k];
-    if (!(s > 0.0)) return false;
-    const double ljj = sqrt(s);
-    L[6 * j + j] = ljj;
-    for (int i = j + 1; i < 6; ++i) {
-      double u = D[6 * i + j];
-      for (int k = 0; k < j; ++k) u -= L[6 * i + k] * L[6 * j + k];
-      L[6 * i + j] = u / ljj;
-    }
-  }
-  double Li[36];
-  for (int k = 0; k < 36; ++k) Li[k] = 0.0;
+// Block-Jacobi preconditioner block: the inverse of the 6x6 diagonal block D (FP64 sums) formed
+// in FP32.  D is first scaled symmetrically to unit diagonal (Dh = S D S, S = diag(D_ii^-1/2)),
+// then Dh = L L^T (Cholesky), Dh^-1 = L^-T L^-1 and D^-1 = S Dh^-1 S.  The preconditioner only
+// steers the PCG iterates, and B300 issues FP64 at 1/64 of the FP32 rate: one FP64 Cholesky
+// inverse in a single lane costs tens of microseconds there.  Returns false if the block is not
+// positive definite.
+__device__ bool chol_inverse6(const double *D, float *Mi) {
+  float sc[6];
+#pragma unroll
   for (int i = 0; i < 6; ++i) {
-    Li[6 * i + i] = 1.0 / L[6 * i + i];
-    for (int j = 0; j < i; ++j) {
-      double s = 0.0;
-      for (int k = j; k < i; ++k) s -= L[6 * i + k] * Li[6 * k + j];
-      Li[6 * i + j] = s / L[6 * i + i];
+    const float d = (float)D[7 * i];
+    if (!(d > 0.f)) return false;
+    sc[i] = 1.f / sqrtf(d);
+  }
+  float L[36];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) L[6 * i + j] = j <= i ? (float)D[6 * i + j] * sc[i] * sc[j] : 0.f;
+#pragma unroll
+  for (int j = 0; j < 6; ++j) {
+    float d = L[7 * j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= L[6 * j + k] * L[6 * j + k];
+    if (!(d > 0.f)) return false;
+    const float ljj = sqrtf(d), inv = 1.f / ljj;
+    L[7 * j] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < 6; ++i) {
+      float u = L[6 * i + j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) u -= L[6 * i + k] * L[6 * j + k];
+      L[6 * i + j] = u * inv;
     }
   }
+  float Li[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) Li[k] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float inv = 1.f / L[7 * i];
+    Li[7 * i] = inv;
+#pragma unroll
+    for (int j = 0; j < i; ++j) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = j; k < i; ++k) s -= L[6 * i + k] * Li[6 * k + j];
+      Li[6 * i + j] = s * inv;
+    }
+  }
+#pragma unroll
   for (int i = 0; i < 6; ++i)
+#pragma unroll
     for (int j = 0; j < 6; ++j) {
-      double s = 0.0;
+      float s = 0.f;
+#pragma unroll
       for (int k = (i > j ? i : j); k < 6; ++k) s += Li[6 * k + i] * Li[6 * k + j];
-      Mi[6 * i + j] = s;
+      Mi[6 * i + j] = sc[i] * s * sc[j];
     }
   return true;
 }
 
-constexpr int ASM_WARPS = 4;
+constexpr int ASM_WARPS = 1;  // one warp per CTA spreads the frames over the SMs
 
 template <typename Acc>
 __global__ void __launch_bounds__(32 * ASM_WARPS)
     k_assemble(Tables t, const Acc *__restrict__ pairblk, int precond, Acc *__restrict__ Dd, Acc *__restrict__ rhs,
                float *__restrict__ Df, float *__restrict__ Minv, int *__restrict__ vflags) {
   __shared__ double Dsh[ASM_WARPS][36];
-  __shared__ double Msh[ASM_WARPS][36];
+  __shared__ float Msh[ASM_WARPS][36];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int v = blockIdx.x * ASM_WARPS + w;
   if (v >= t.n_vars) return;
@@ -381,8 +400,9 @@ __global__ void __launch_bounds__(32 * ASM_WARPS)
   if (lane == 0) {
     int flag = 0;
     bool empty = true;
-    for (int k = 0; k < 36; ++k) empty = empty && (Dsh[w][k] == 0.0);
-    for (int k = 0; k < 36; ++k) Msh[w][k] = 0.0;
+    // integer test for +-0 (an FP64 compare would occupy the slow FP64 pipe 36 times)
+    for (int k = 0; k < 36; ++k) empty = empty && ((__double_as_longlong(Dsh[w][k]) << 1) == 0);
+    for (int k = 0; k < 36; ++k) Msh[w][k] = 0.f;
     if (empty) {
       flag = 2;  // BF_FLAG_EMPTY_FRAME: zero inverse, the frame's update stays 0
     } else {
@@ -392,17 +412,17 @@ __global__ void __launch_bounds__(32 * ASM_WARPS)
         if (!ok) flag = 1;  // BF_FLAG_SINGULAR_BLOCK: fall back to the diagonal
       }
       if (!ok) {
-        for (int k = 0; k < 36; ++k) Msh[w][k] = 0.0;
+        for (int k = 0; k < 36; ++k) Msh[w][k] = 0.f;
         for (int k = 0; k < 6; ++k) {
-          const double d = Dsh[w][7 * k];
-          Msh[w][7 * k] = d > 0.0 ? 1.0 / d : 0.0;
+          const float d = (float)Dsh[w][7 * k];
+          Msh[w][7 * k] = d > 0.f ? 1.f / d : 0.f;
         }
       }
     }
     vflags[v] = flag;
   }
   __syncwarp();
-  for (int k = lane; k < 36; k += 32) Minv[(long long)v * 36 + k] = (float)Msh[w][k];
+  for (int k = lane; k < 36; k += 32) Minv[(long long)v * 36 + k] = Msh[w][k];
 }
 
 template <typename Acc>
@@ -418,23 +438,87 @@ template int launch_assemble<double>(const Tables &, const double *, int, double
 template int launch_assemble<float>(const Tables &, const float *, int, float *, float *, float *, float *, int *,
                                     cudaStream_t);
 
+// ------------------------------------------------------------------------- energy reduce
+constexpr int EN_BS = 256;
+
+// Energy record of problem `prob`: the sum of its pairs' records, formed by the first EN_BS threads
+// of the calling block in a fixed order (strided partial sums, warp butterflies, warps in order),
+// so every kernel that calls it produces the same bits.  Every thread of the block must call it.
+template <typename Acc>
+__device__ void problem_energy(const Tables &t, const Acc *__restrict__ pairen, int prob, double *__restrict__ out,
+                               Acc (*sh)[PAIREN]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // warps past the problem's pair count hold zeros: left out (same result, less FP64 work)
+  const int np = t.prob_pair1[prob] - t.prob_pair0[prob];
+  const int nw = min(EN_BS / 32, (np + 31) / 32);
+  if (warp < nw) {
+    Acc s[PAIREN] = {0, 0, 0, 0};
+    for (int p = t.prob_pair0[prob] + threadIdx.x; p < t.prob_pair1[prob]; p += EN_BS)
+#pragma unroll
+      for (int k = 0; k < PAIREN; ++k) s[k] += pairen[(long long)p * PAIREN + k];
+#pragma unroll
+    for (int k = 0; k < PAIREN; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+      if (lane == 0) sh[warp][k] = s[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < PAIREN) {
+    Acc v = 0;
+    for (int w = 0; w < nw; ++w) v += sh[w][threadIdx.x];
+    out[prob * PAIREN + threadIdx.x] = (double)v;
+  }
+  __syncthreads();
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(EN_BS) k_energy_reduce(Tables t, const Acc *__restrict__ pairen,
+                                                         double *__restrict__ out) {
+  __shared__ Acc sh[EN_BS / 32][PAIREN];
+  problem_energy<Acc>(t, pairen, blockIdx.x, out, sh);
+}
+
+template <typename Acc>
+int launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st) {
+  if (t.n_prob == 0) return 0;
+  k_energy_reduce<Acc><<<t.n_prob, EN_BS, 0, st>>>(t, pairen, out);
+  return 1;
+}
+template int launch_energy_reduce<double>(const Tables &, const double *, double *, cudaStream_t);
+template int launch_energy_reduce<float>(const Tables &, const float *, double *, cudaStream_t);
+
 // ------------------------------------------------------------------------ PCG, one CTA/problem
 constexpr int PCG_BS = 256;
 
-// Block sum: FP32 warp tree, then the warps' sums in Acc, fixed order; same value in every thread.
-template <typename Acc>
-__device__ __forceinline__ Acc cta_sum(float v, Acc *sh) {
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();  // protect sh from a previous use
-  if (lane == 0) sh[warp] = (Acc)v;
+  return v;
+}
+
+// Fixed-order block sum, valid in thread 0 only: FP32 warp trees, then the warps' sums in Acc in
+// warp order.  The scalar recurrences (alpha, beta, the stop test) run in thread 0 alone and reach
+// the block through shared memory: B300 issues FP64 at 1/64 of the FP32 rate, so FP64 work
+// repeated by every thread would dominate the iteration.  The caller synchronises before wsum is
+// written again.
+// Warps at or beyond nw hold only zeros and are left out of the sum (the result is the same).
+template <typename Acc, int BS>
+__device__ __forceinline__ Acc block_sum0(float v, float *wsum, int nw = BS / 32) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
   __syncthreads();
   Acc s = 0;
-#pragma unroll
-  for (int w = 0; w < PCG_BS / 32; ++w) s += sh[w];
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nw; ++w) s += (Acc)wsum[w];
   return s;
 }
+
+// Scalars thread 0 hands to the block each half-iteration.
+struct PcgScal {
+  float fa, fb;
+  int stop;
+};
 
 // z_v = Minv_v r_v for the row u = 6 v + c
 __device__ __forceinline__ float precond_row(const float *__restrict__ Minv, const float *__restrict__ r, int v,
@@ -444,15 +528,154 @@ __device__ __forceinline__ float precond_row(const float *__restrict__ Minv, con
   return Mr[0] * rv[0] + Mr[1] * rv[1] + Mr[2] * rv[2] + Mr[3] * rv[3] + Mr[4] * rv[4] + Mr[5] * rv[5];
 }
 
+// Thread 0, after p.Ap: stop on breakdown, else alpha = rz / pq.  Returns the flag bits to add.
+// alpha and beta feed FP32 vector updates, so they are FP32 quotients of the rounded sums (within
+// 1.5 ulp of the rounded FP64 quotient; an FP64 division is a long FP64 instruction sequence).
+template <typename Acc>
+__device__ __forceinline__ int pcg_alpha(Acc rz, Acc pq, PcgScal &S) {
+  if (!(pq > (Acc)0)) {
+    S.stop = 1;
+    return 4;  // BF_FLAG_PCG_BREAKDOWN
+  }
+  S.fa = __fdiv_rn((float)rz, (float)pq);
+  return 0;
+}
+
+// Thread 0, after r.z: beta = rz_new / rz, stop once r.z reaches zero.
+template <typename Acc>
+__device__ __forceinline__ void pcg_beta(Acc &rz, Acc rz_new, PcgScal &S) {
+  S.fb = __fdiv_rn((float)rz_new, (float)rz);
+  rz = rz_new;
+  S.stop = rz == (Acc)0;
+}
+
+// Problems with at most PCG_SMALL_N unknowns (16 free frames) are solved from a dense copy of
+// their system in shared memory, one thread per unknown with its x, r, z, p in registers: no
+// global-memory round trip inside the iteration.  The choice depends on the problem alone, so a
+// problem solved in a batch gives the same bits as solved alone.
+constexpr int PCG_SMALL_N = 96;
+
+template <typename Acc>
+__device__ int pcg_small(const Tables &t, const float *__restrict__ Df, const float *__restrict__ pairoff,
+                         const float *__restrict__ Minv, const Acc *__restrict__ rhs, float *__restrict__ x,
+                         int n_pcg, int v0, int v1, float *wsum, PcgScal &S) {
+  __shared__ float AT[PCG_SMALL_N * PCG_SMALL_N];  // column-major: AT[k * n + u] = A[u][k]
+  __shared__ float sp[PCG_SMALL_N], sr[PCG_SMALL_N];
+  const int n = 6 * (v1 - v0);
+  const int u = threadIdx.x;
+  const bool own = u < n;
+  for (int k = u; k < n * n; k += PCG_BS) AT[k] = 0.f;
+  __syncthreads();
+  float Mr[6] = {0, 0, 0, 0, 0, 0};
+  float xu = 0.f, ru = 0.f, zu = 0.f, pu = 0.f;
+  const int lv = u / 6, c = u % 6;
+  if (own) {
+    const int v = v0 + lv;
+    const float *Dr = Df + (long long)v * 36 + 6 * c;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) AT[(6 * lv + j) * n + u] = Dr[j];
+    for (int e = t.inc_off[v]; e < t.inc_off[v + 1]; ++e) {
+      const int ov = t.inc_ov[e];
+      if (ov < 0) continue;
+      const int ent = t.inc[e];
+      const float *O = pairoff + (long long)(ent >> 1) * 36;
+      float *col = AT + 6 * (ov - v0) * n + u;
+      if ((ent & 1) == 0) {  // row c of A_ab
+#pragma unroll
+        for (int j = 0; j < 6; ++j) col[j * n] += O[6 * c + j];
+      } else {  // row c of A_ba = A_ab^T
+#pragma unroll
+        for (int j = 0; j < 6; ++j) col[j * n] += O[6 * j + c];
+      }
+    }
+    const float *M = Minv + (long long)v * 36 + 6 * c;
+#pragma unroll
+    for (int j = 0; j < 6; ++j) Mr[j] = M[j];
+    ru = (float)rhs[6 * v0 + u];
+    sr[u] = ru;
+  }
+  __syncthreads();
+  if (own) {
+    const float *rv = sr + 6 * lv;
+    zu = Mr[0] * rv[0] + Mr[1] * rv[1] + Mr[2] * rv[2] + Mr[3] * rv[3] + Mr[4] * rv[4] + Mr[5] * rv[5];
+    pu = zu;
+    sp[u] = pu;
+  }
+  const int nw = (n + 31) / 32;  // warps holding unknowns
+  Acc rz = block_sum0<Acc, PCG_BS>(own ? ru * zu : 0.f, wsum, nw);
+  if (u == 0) S.stop = rz == (Acc)0;
+  int flag = 0;
+  __syncthreads();
+  for (int it = 0; it < n_pcg; ++it) {
+    if (S.stop) break;
+    float qu = 0.f;
+    if (own)
+      for (int k = 0; k < n; ++k) qu += AT[k * n + u] * sp[k];
+    const Acc pq = block_sum0<Acc, PCG_BS>(own ? pu * qu : 0.f, wsum, nw);
+    if (u == 0) flag |= pcg_alpha(rz, pq, S);
+    __syncthreads();
+    if (S.stop) break;
+    const float fa = S.fa;
+    if (own) {
+      xu += fa * pu;
+      ru -= fa * qu;
+      sr[u] = ru;
+    }
+    __syncthreads();
+    if (own) {
+      const float *rv = sr + 6 * lv;
+      zu = Mr[0] * rv[0] + Mr[1] * rv[1] + Mr[2] * rv[2] + Mr[3] * rv[3] + Mr[4] * rv[4] + Mr[5] * rv[5];
+    }
+    const Acc rz_new = block_sum0<Acc, PCG_BS>(own ? ru * zu : 0.f, wsum, nw);
+    if (u == 0) pcg_beta(rz, rz_new, S);
+    __syncthreads();
+    if (own) {
+      pu = zu + S.fb * pu;
+      sp[u] = pu;
+    }
+    __syncthreads();
+  }
+  if (own) x[6 * v0 + u] = xu;
+  return flag;
+}
+
+// After the solve: pose update of the problem's free frames, then its pairs' transforms at the
+// new poses (both need the whole block's x, respectively poses, written first).
+__device__ void pcg_finish(const Tables &t, const float *x, int prob, int v0, int v1, const PcgOut &po) {
+  __syncthreads();
+  if (!po.pose) return;
+  for (int v = v0 + threadIdx.x; v < v1; v += PCG_BS) update_pose(po.pose + 12 * t.var_frame[v], x + 6 * v);
+  if (!po.pairM) return;
+  __syncthreads();
+  // one thread per transform entry (24 per pair): the FP64 work spreads over all warps
+  const int p0 = t.prob_pair0[prob], n = 24 * (t.prob_pair1[prob] - p0);
+  for (int k = threadIdx.x; k < n; k += PCG_BS) {
+    const int p = p0 + k / 24, e = k % 24;
+    const double *Ta = po.pose + 12 * t.pair_a[p];
+    const double *Tb = po.pose + 12 * t.pair_b[p];
+    po.pairM[24 * p + e] = e < 12 ? pair_xform_entry(Ta, Tb, e) : pair_xform_entry(Tb, Ta, e - 12);
+  }
+}
+
 template <typename Acc>
 __global__ void __launch_bounds__(PCG_BS)
     k_pcg(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff, const float *__restrict__ Minv,
           const Acc *__restrict__ rhs, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
-          float *__restrict__ p, float *__restrict__ q, int n_pcg, int *__restrict__ pflags) {
-  __shared__ Acc sh[PCG_BS / 32];
+          float *__restrict__ p, float *__restrict__ q, int n_pcg, int *__restrict__ pflags,
+          const Acc *__restrict__ pairen, PcgOut po) {
+  __shared__ float wsum[PCG_BS / 32];
+  __shared__ PcgScal S;
+  __shared__ Acc esh[EN_BS / 32][PAIREN];
   const int prob = blockIdx.x;
+  if (po.energy) problem_energy<Acc>(t, pairen, prob, po.energy, esh);
   const int v0 = t.prob_var0[prob], v1 = t.prob_var1[prob];
   const int u0 = 6 * v0, u1 = 6 * v1;
+  if (u1 - u0 <= PCG_SMALL_N) {
+    const int flag = pcg_small<Acc>(t, Df, pairoff, Minv, rhs, x, n_pcg, v0, v1, wsum, S);
+    if (threadIdx.x == 0 && pflags) pflags[prob] |= flag;
+    pcg_finish(t, x, prob, v0, v1, po);
+    return;
+  }
   for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
     x[u] = 0.f;
     r[u] = (float)rhs[u];
@@ -465,10 +688,12 @@ __global__ void __launch_bounds__(PCG_BS)
     p[u] = zu;
     loc += r[u] * zu;
   }
-  Acc rz = cta_sum(loc, sh);
+  Acc rz = block_sum0<Acc, PCG_BS>(loc, wsum);
+  if (threadIdx.x == 0) S.stop = rz == (Acc)0;
   int flag = 0;
+  __syncthreads();
   for (int it = 0; it < n_pcg; ++it) {
-    if (rz == (Acc)0) break;
+    if (S.stop) break;
     loc = 0.f;
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
       const int v = u / 6, c = u % 6;
@@ -482,24 +707,23 @@ __global__ void __launch_bounds__(PCG_BS)
         const int ent = t.inc[e];
         const int pr = ent >> 1, side = ent & 1;
         const float *O = pairoff + (long long)pr * 36;
-        const float *po = p + 6LL * ov;
+        const float *pw = p + 6LL * ov;
         if (side == 0) {  // row of A_ab
-          s += O[6 * c] * po[0] + O[6 * c + 1] * po[1] + O[6 * c + 2] * po[2] + O[6 * c + 3] * po[3] +
-               O[6 * c + 4] * po[4] + O[6 * c + 5] * po[5];
+          s += O[6 * c] * pw[0] + O[6 * c + 1] * pw[1] + O[6 * c + 2] * pw[2] + O[6 * c + 3] * pw[3] +
+               O[6 * c + 4] * pw[4] + O[6 * c + 5] * pw[5];
         } else {  // row of A_ba = A_ab^T
-          s += O[c] * po[0] + O[6 + c] * po[1] + O[12 + c] * po[2] + O[18 + c] * po[3] + O[24 + c] * po[4] +
-               O[30 + c] * po[5];
+          s += O[c] * pw[0] + O[6 + c] * pw[1] + O[12 + c] * pw[2] + O[18 + c] * pw[3] + O[24 + c] * pw[4] +
+               O[30 + c] * pw[5];
         }
       }
       q[u] = s;
       loc += p[u] * s;
     }
-    const Acc pq = cta_sum(loc, sh);
-    if (!(pq > (Acc)0)) {
-      flag |= 4;  // BF_FLAG_PCG_BREAKDOWN
-      break;
-    }
-    const float fa = (float)(rz / pq);
+    const Acc pq = block_sum0<Acc, PCG_BS>(loc, wsum);
+    if (threadIdx.x == 0) flag |= pcg_alpha(rz, pq, S);
+    __syncthreads();
+    if (S.stop) break;
+    const float fa = S.fa;
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
       x[u] += fa * p[u];
       r[u] -= fa * q[u];
@@ -511,26 +735,29 @@ __global__ void __launch_bounds__(PCG_BS)
       z[u] = zu;
       loc += r[u] * zu;
     }
-    const Acc rz_new = cta_sum(loc, sh);
-    const float fb = (float)(rz_new / rz);
-    rz = rz_new;
+    const Acc rz_new = block_sum0<Acc, PCG_BS>(loc, wsum);
+    if (threadIdx.x == 0) pcg_beta(rz, rz_new, S);
+    __syncthreads();
+    const float fb = S.fb;
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) p[u] = z[u] + fb * p[u];
     __syncthreads();
   }
   if (threadIdx.x == 0 && pflags) pflags[prob] |= flag;
+  pcg_finish(t, x, prob, v0, v1, po);
 }
 
 template <typename Acc>
 int launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
-               float *r, float *z, float *p, float *q, int n_pcg, int *pflags, cudaStream_t st) {
+               float *r, float *z, float *p, float *q, int n_pcg, int *pflags, const Acc *pairen, PcgOut po,
+               cudaStream_t st) {
   if (t.n_prob == 0) return 0;
-  k_pcg<Acc><<<t.n_prob, PCG_BS, 0, st>>>(t, Df, pairoff, Minv, rhs, x, r, z, p, q, n_pcg, pflags);
+  k_pcg<Acc><<<t.n_prob, PCG_BS, 0, st>>>(t, Df, pairoff, Minv, rhs, x, r, z, p, q, n_pcg, pflags, pairen, po);
   return 1;
 }
 template int launch_pcg<double>(const Tables &, const float *, const float *, const float *, const double *, float *,
-                                float *, float *, float *, float *, int, int *, cudaStream_t);
+                                float *, float *, float *, float *, int, int *, const double *, PcgOut, cudaStream_t);
 template int launch_pcg<float>(const Tables &, const float *, const float *, const float *, const float *, float *,
-                               float *, float *, float *, float *, int, int *, cudaStream_t);
+                               float *, float *, float *, float *, int, int *, const float *, PcgOut, cudaStream_t);
 
 // ------------------------------------------------------------- PCG, one problem over the grid
 constexpr int COOP_BS = 256;
@@ -585,7 +812,7 @@ struct CoopState {
 };
 
 // Sum of the per-CTA partials in a fixed order: lane l sums entries l, l+32, ... then a
-// butterfly over the warp; every warp of every CTA computes the identical value.
+// butterfly over the warp; called by warp 0 of each CTA, every such warp gets the same value.
 template <typename Acc>
 __device__ __forceinline__ Acc grid_total(const Acc *part, int n) {
   const int lane = threadIdx.x & 31;
@@ -596,33 +823,31 @@ __device__ __forceinline__ Acc grid_total(const Acc *part, int n) {
   return s;
 }
 
+// This CTA's partial of a dot product into part[blockIdx.x]: FP32 warp trees, the warps' sums in
+// Acc in warp order (thread 0).
 template <typename Acc>
-__device__ __forceinline__ void cta_partial(Acc v, Acc *sh, Acc *part) {
-  // fixed-order CTA reduction of per-warp values (lane 0 of each warp holds its warp's value)
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();  // sh may still be read by a previous call
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    Acc s = 0;
-    for (int w = 0; w < COOP_WARPS; ++w) s += sh[w];
-    part[blockIdx.x] = s;
-  }
+__device__ __forceinline__ void cta_partial(float v, float *wsum, Acc *part) {
+  const Acc s = block_sum0<Acc, COOP_BS>(v, wsum);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 template <typename Acc>
 __global__ void __launch_bounds__(COOP_BS)
     k_pcg_coop(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff,
                const float *__restrict__ Minv, const Acc *__restrict__ rhs, float *x, float *r, float *z, float *p0,
-               float *p1, float *q, int n_pcg, int *__restrict__ pflags, CoopState cs) {
-  __shared__ Acc sh[COOP_WARPS];
+               float *p1, float *q, int n_pcg, int *__restrict__ pflags, CoopState cs,
+               const Acc *__restrict__ pairen, PcgOut po) {
+  __shared__ float wsum[COOP_WARPS];
+  __shared__ PcgScal S;
+  __shared__ Acc esh[EN_BS / 32][PAIREN];
+  if (blockIdx.x == 0 && po.energy) problem_energy<Acc>(t, pairen, 0, po.energy, esh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = blockIdx.x * COOP_WARPS + warp, nw = gridDim.x * COOP_WARPS;
   const int v0 = t.prob_var0[0], v1 = t.prob_var1[0];
   Acc *ppq = (Acc *)cs.part_pq, *prz = (Acc *)cs.part_rz;
   volatile int *err = cs.err;
   // init: x = 0, r = b, z = M^-1 r, p_old = 0 (the first direction is z)
-  Acc loc = 0;
+  float loc = 0.f;
   for (int v = v0 + gw; v < v1; v += nw) {
     if (lane < 6) {
       float rr[6];
@@ -634,23 +859,29 @@ __global__ void __launch_bounds__(COOP_BS)
       r[6 * v + lane] = rr[lane];
       z[6 * v + lane] = zl;
       p0[6 * v + lane] = 0.f;
-      loc += (Acc)rr[lane] * (Acc)zl;
+      loc += rr[lane] * zl;
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
-  cta_partial(loc, sh, prz);
+  cta_partial<Acc>(loc, wsum, prz);
   if (!grid_barrier(cs.count, cs.gen, gridDim.x, err)) return;
-  Acc rz = grid_total(prz, gridDim.x);
-  Acc beta = 0;
+  Acc rz = 0;  // meaningful in thread 0
+  if (warp == 0) {
+    const Acc tot = grid_total(prz, gridDim.x);
+    if (lane == 0) {
+      rz = tot;
+      S.stop = rz == (Acc)0;
+      S.fb = 0.f;
+    }
+  }
+  __syncthreads();
   int flag = 0;
   float *pold = p0, *pnew = p1;
   for (int it = 0; it < n_pcg; ++it) {
-    if (rz == (Acc)0) break;
+    if (S.stop) break;
     // Phase A: p_new = z + beta p_old (own frames); q = A p_new with the neighbours' p_new formed
     // on the fly from z and p_old (both final since the last barrier)
-    const float fb = (float)beta;
-    Acc lpq = 0;
+    const float fb = S.fb;
+    float lpq = 0.f;
     for (int v = v0 + gw; v < v1; v += nw) {
       float pn[6];
 #pragma unroll
@@ -661,74 +892,83 @@ __global__ void __launch_bounds__(COOP_BS)
         if (ov < 0) continue;
         const int ent = t.inc[e];
         const int pr = ent >> 1, side = ent & 1;
-        float po[6];
+        float pw[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) po[k] = __ldcg(z + 6 * ov + k) + fb * __ldcg(pold + 6 * ov + k);
+        for (int k = 0; k < 6; ++k) pw[k] = __ldcg(z + 6 * ov + k) + fb * __ldcg(pold + 6 * ov + k);
         const float *O = pairoff + (long long)pr * 36;
         if (side == 0) {
 #pragma unroll
           for (int c = 0; c < 6; ++c)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[c] += O[6 * c + k] * po[k];
+            for (int k = 0; k < 6; ++k) acc[c] += O[6 * c + k] * pw[k];
         } else {
 #pragma unroll
           for (int c = 0; c < 6; ++c)
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[c] += O[6 * k + c] * po[k];
+            for (int k = 0; k < 6; ++k) acc[c] += O[6 * k + c] * pw[k];
         }
       }
 #pragma unroll
-      for (int c = 0; c < 6; ++c)
+      for (int c = 0; c < 6; ++c) acc[c] = warp_sum(acc[c]);
+      float qmine = 0.f, pmine = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+      for (int c = 0; c < 6; ++c) {
+        const float *Drow = Df + (long long)v * 36 + 6 * c;
+        if (lane == c) {
+          qmine = acc[c] + Drow[0] * pn[0] + Drow[1] * pn[1] + Drow[2] * pn[2] + Drow[3] * pn[3] +
+                  Drow[4] * pn[4] + Drow[5] * pn[5];
+          pmine = pn[c];
+        }
+      }
       if (lane < 6) {
-        const float *Drow = Df + (long long)v * 36 + 6 * lane;
-        const float qc = acc[lane] + Drow[0] * pn[0] + Drow[1] * pn[1] + Drow[2] * pn[2] + Drow[3] * pn[3] +
-                         Drow[4] * pn[4] + Drow[5] * pn[5];
-        q[6 * v + lane] = qc;
-        pnew[6 * v + lane] = pn[lane];
-        lpq += (Acc)pn[lane] * (Acc)qc;
+        q[6 * v + lane] = qmine;
+        pnew[6 * v + lane] = pmine;
+        lpq += pmine * qmine;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lpq += __shfl_xor_sync(0xffffffffu, lpq, o);
-    cta_partial(lpq, sh, ppq);
+    cta_partial<Acc>(lpq, wsum, ppq);
     if (!grid_barrier(cs.count, cs.gen, gridDim.x, err)) return;
-    const Acc pq = grid_total(ppq, gridDim.x);
-    if (!(pq > (Acc)0)) {
-      flag |= 4;  // BF_FLAG_PCG_BREAKDOWN
-      break;
+    if (warp == 0) {
+      const Acc pq = grid_total(ppq, gridDim.x);
+      if (lane == 0) flag |= pcg_alpha(rz, pq, S);
     }
-    const Acc alpha = rz / pq;
+    __syncthreads();
+    if (S.stop) break;
+    const float fa = S.fa;
     // Phase B: x += alpha p_new, r -= alpha q, z = M^-1 r (own frames only, written by this warp)
-    Acc lrz = 0;
+    float lrz = 0.f;
     for (int v = v0 + gw; v < v1; v += nw) {
+      const float rn_own = lane < 6 ? r[6 * v + lane] - fa * q[6 * v + lane] : 0.f;
       float rn[6];
 #pragma unroll
-      for (int k = 0; k < 6; ++k) rn[k] = (float)((Acc)r[6 * v + k] - alpha * (Acc)q[6 * v + k]);
-      __syncwarp();
+      for (int k = 0; k < 6; ++k) rn[k] = __shfl_sync(0xffffffffu, rn_own, k);
       if (lane < 6) {
         const float *M = Minv + (long long)v * 36 + 6 * lane;
         const float zl = M[0] * rn[0] + M[1] * rn[1] + M[2] * rn[2] + M[3] * rn[3] + M[4] * rn[4] + M[5] * rn[5];
-        x[6 * v + lane] = (float)((Acc)x[6 * v + lane] + alpha * (Acc)pnew[6 * v + lane]);
-        r[6 * v + lane] = rn[lane];
+        x[6 * v + lane] += fa * pnew[6 * v + lane];
+        r[6 * v + lane] = rn_own;
         z[6 * v + lane] = zl;
-        lrz += (Acc)rn[lane] * (Acc)zl;
+        lrz += rn_own * zl;
       }
-      __syncwarp();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lrz += __shfl_xor_sync(0xffffffffu, lrz, o);
-    cta_partial(lrz, sh, prz);
+    cta_partial<Acc>(lrz, wsum, prz);
     if (!grid_barrier(cs.count, cs.gen, gridDim.x, err)) return;
-    const Acc rz_new = grid_total(prz, gridDim.x);
-    beta = rz_new / rz;
-    rz = rz_new;
+    if (warp == 0) {
+      const Acc rz_new = grid_total(prz, gridDim.x);
+      if (lane == 0) pcg_beta(rz, rz_new, S);
+    }
+    __syncthreads();
     float *tmp = pold;
     pold = pnew;
     pnew = tmp;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && pflags) pflags[0] |= flag;
+  // a frame's step was written by lanes 0..5 of the warp that owns it
+  if (po.pose)
+    for (int v = v0 + gw; v < v1; v += nw) {
+      __syncwarp();
+      if (lane == 0) update_pose(po.pose + 12 * t.var_frame[v], x + 6 * v);
+    }
 }
 
 int coop_max_grid() {
@@ -757,7 +997,7 @@ size_t coop_mem_bytes(int grid) { return 256 + 2 * 8 * (size_t)grid; }
 template <typename Acc>
 int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
                     float *x, float *r, float *z, float *p0, float *p1, float *q, int n_pcg, int *pflags,
-                    void *coop_mem, int grid, cudaStream_t st) {
+                    void *coop_mem, int grid, const Acc *pairen, PcgOut po, cudaStream_t st) {
   if (t.n_vars == 0) return 0;
   CoopState cs;
   char *m = (char *)coop_mem;
@@ -768,7 +1008,7 @@ int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, cons
   cs.part_rz = m + 256 + 8 * (size_t)grid;
   if (cudaMemsetAsync(m, 0, 16, st) != cudaSuccess) return -1;
   Tables tt = t;
-  void *args[] = {&tt, &Df, &pairoff, &Minv, &rhs, &x, &r, &z, &p0, &p1, &q, &n_pcg, &pflags, &cs};
+  void *args[] = {&tt, &Df, &pairoff, &Minv, &rhs, &x, &r, &z, &p0, &p1, &q, &n_pcg, &pflags, &cs, &pairen, &po};
   if (cudaLaunchCooperativeKernel((const void *)k_pcg_coop<Acc>, dim3(grid), dim3(COOP_BS), args, 0, st) !=
       cudaSuccess)
     return -1;
@@ -776,85 +1016,10 @@ int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, cons
 }
 template int launch_pcg_coop<double>(const Tables &, const float *, const float *, const float *, const double *,
                                      float *, float *, float *, float *, float *, float *, int, int *, void *, int,
-                                     cudaStream_t);
+                                     const double *, PcgOut, cudaStream_t);
 template int launch_pcg_coop<float>(const Tables &, const float *, const float *, const float *, const float *,
                                     float *, float *, float *, float *, float *, float *, int, int *, void *, int,
-                                    cudaStream_t);
-
-// ----------------------------------------------------------------------------- pose update
-__global__ void k_update(int n_vars, const int *__restrict__ var_frame, const float *__restrict__ x,
-                         double *__restrict__ pose) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n_vars) return;
-  double *T = pose + 12 * var_frame[v];
-  const double w0 = x[6 * v], w1 = x[6 * v + 1], w2 = x[6 * v + 2];
-  const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
-  const double th = sqrt(th2);
-  double A, B;  // Exp(w) = I + A K + B K^2 (Rodrigues)
-  if (th < 1e-8) {
-    A = 1.0;
-    B = 0.5;
-  } else {
-    A = sin(th) / th;
-    B = (1.0 - cos(th)) / th2;
-  }
-  const double K[3][3] = {{0.0, -w2, w1}, {w2, 0.0, -w0}, {-w1, w0, 0.0}};
-  double E[3][3];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      const double K2 = K[i][0] * K[0][j] + K[i][1] * K[1][j] + K[i][2] * K[2][j];
-      E[i][j] = (i == j ? 1.0 : 0.0) + A * K[i][j] + B * K2;
-    }
-  double R[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) R[3 * i + j] = E[i][0] * T[j] + E[i][1] * T[3 + j] + E[i][2] * T[6 + j];
-  for (int k = 0; k < 9; ++k) T[k] = R[k];
-  T[9] += (double)x[6 * v + 3];
-  T[10] += (double)x[6 * v + 4];
-  T[11] += (double)x[6 * v + 5];
-}
-
-int launch_update(const Tables &t, const float *x, double *pose, cudaStream_t st) {
-  if (t.n_vars == 0) return 0;
-  k_update<<<(t.n_vars + 127) / 128, 128, 0, st>>>(t.n_vars, t.var_frame, x, pose);
-  return 1;
-}
-
-// ------------------------------------------------------------------------- energy reduce
-constexpr int EN_BS = 256;
-
-template <typename Acc>
-__global__ void __launch_bounds__(EN_BS) k_energy_reduce(Tables t, const Acc *__restrict__ pairen,
-                                                         double *__restrict__ out) {
-  __shared__ Acc sh[EN_BS / 32][PAIREN];
-  const int prob = blockIdx.x;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Acc s[PAIREN] = {0, 0, 0, 0};
-  for (int p = t.prob_pair0[prob] + threadIdx.x; p < t.prob_pair1[prob]; p += EN_BS)
-#pragma unroll
-    for (int k = 0; k < PAIREN; ++k) s[k] += pairen[(long long)p * PAIREN + k];
-#pragma unroll
-  for (int k = 0; k < PAIREN; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
-    if (lane == 0) sh[warp][k] = s[k];
-  }
-  __syncthreads();
-  if (threadIdx.x < PAIREN) {
-    Acc v = 0;
-    for (int w = 0; w < EN_BS / 32; ++w) v += sh[w][threadIdx.x];
-    out[prob * PAIREN + threadIdx.x] = (double)v;
-  }
-}
-
-template <typename Acc>
-int launch_energy_reduce(const Tables &t, const Acc *pairen, double *out, cudaStream_t st) {
-  if (t.n_prob == 0) return 0;
-  k_energy_reduce<Acc><<<t.n_prob, EN_BS, 0, st>>>(t, pairen, out);
-  return 1;
-}
-template int launch_energy_reduce<double>(const Tables &, const double *, double *, cudaStream_t);
-template int launch_energy_reduce<float>(const Tables &, const float *, double *, cudaStream_t);
+                                    const float *, PcgOut, cudaStream_t);
 
 // ------------------------------------------------------ PCG, one problem on a thread-block cluster
 // One cluster of CL CTAs (up to 16, one per SM) solves one problem.  Every CTA keeps replicas of
@@ -915,11 +1080,13 @@ template <typename Acc>
 __global__ void __launch_bounds__(CL_BS, 1)
     k_pcg_cluster(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff,
                   const float *__restrict__ Minv, const Acc *__restrict__ rhs, float *__restrict__ xg, int n_pcg,
-                  int *__restrict__ pflags, ClusterLayout L) {
+                  int *__restrict__ pflags, ClusterLayout L, const Acc *__restrict__ pairen, PcgOut po) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ const float4 *zp_rank[16];
+  __shared__ Acc esh[EN_BS / 32][PAIREN];
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
+  if (rank == 0 && po.energy) problem_energy<Acc>(t, pairen, 0, po.energy, esh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int v0 = t.prob_var0[0], v1 = t.prob_var1[0];
   const int nv = v1 - v0;
@@ -985,12 +1152,21 @@ __global__ void __launch_bounds__(CL_BS, 1)
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
   cluster_partial((Acc)loc, wsum, part, 1);
   cluster.sync();  // all CTAs running, owned z / p initialised
-  Acc rz = cluster_total(cluster, part, 1, CL);
-  Acc beta = 0;
+  __shared__ PcgScal S;
+  Acc rz = 0;  // meaningful in thread 0, which runs the scalar recurrences
+  if (warp == 0) {
+    const Acc tot = cluster_total(cluster, part, 1, CL);
+    if (lane == 0) {
+      rz = tot;
+      S.stop = rz == (Acc)0;
+      S.fb = 0.f;
+    }
+  }
+  __syncthreads();
   int flag = 0;
   for (int it = 0; it < n_pcg; ++it) {
-    if (rz == (Acc)0) break;
-    const float fb = (float)beta;
+    if (S.stop) break;
+    const float fb = S.fb;
     // Phase A: p_new = z + beta p (owned, kept in opn); q = A p_new, neighbours read remotely
     float lpq = 0.f;
     for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
@@ -1070,13 +1246,13 @@ __global__ void __launch_bounds__(CL_BS, 1)
     for (int o = 16; o > 0; o >>= 1) lpq += __shfl_xor_sync(0xffffffffu, lpq, o);
     cluster_partial((Acc)lpq, wsum, part, 0);
     cluster.sync();  // every CTA has finished reading the old z / p
-    const Acc pq = cluster_total(cluster, part, 0, CL);
-    if (!(pq > (Acc)0)) {
-      flag |= 4;  // BF_FLAG_PCG_BREAKDOWN
-      break;
+    if (warp == 0) {
+      const Acc pq = cluster_total(cluster, part, 0, CL);
+      if (lane == 0) flag |= pcg_alpha(rz, pq, S);
     }
-    const Acc alpha = rz / pq;
-    const float fa = (float)alpha;
+    __syncthreads();
+    if (S.stop) break;
+    const float fa = S.fa;
     // Phase B (local): x += alpha p_new, r -= alpha q, z = M^-1 r, p = p_new
     float lrz = 0.f;
     for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
@@ -1102,13 +1278,17 @@ __global__ void __launch_bounds__(CL_BS, 1)
     for (int o = 16; o > 0; o >>= 1) lrz += __shfl_xor_sync(0xffffffffu, lrz, o);
     cluster_partial((Acc)lrz, wsum, part, 1);
     cluster.sync();  // the new z / p are visible cluster-wide
-    const Acc rz_new = cluster_total(cluster, part, 1, CL);
-    beta = rz_new / rz;
-    rz = rz_new;
+    if (warp == 0) {
+      const Acc rz_new = cluster_total(cluster, part, 1, CL);
+      if (lane == 0) pcg_beta(rz, rz_new, S);
+    }
+    __syncthreads();
   }
   // write the owned part of the solution
   __syncthreads();
   for (int u = threadIdx.x; u < 6 * no; u += CL_BS) xg[6 * (v0 + o0) + u] = ox[u];
+  if (po.pose)
+    for (int k = threadIdx.x; k < no; k += CL_BS) update_pose(po.pose + 12 * t.var_frame[v0 + o0 + k], ox + 6 * k);
   if (rank == 0 && threadIdx.x == 0 && pflags) pflags[0] |= flag;
   cluster.sync();  // keep every CTA's shared memory alive until remote reads are done
 }
@@ -1160,7 +1340,8 @@ size_t cluster_smem_bytes(int n_vars, int cl) {
 
 template <typename Acc>
 int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
-                       float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, cudaStream_t st) {
+                       float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, const Acc *pairen,
+                       PcgOut po, cudaStream_t st) {
   if (t.n_vars == 0) return 0;
   size_t smem = 0;
   const ClusterLayout L = cluster_layout(t.n_vars, cl, inc_off_host, &smem);
@@ -1184,18 +1365,19 @@ int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, c
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_pcg_cluster<Acc>, t, Df, pairoff, Minv, rhs, x, n_pcg, pflags, L) != cudaSuccess) {
+  if (cudaLaunchKernelEx(&cfg, k_pcg_cluster<Acc>, t, Df, pairoff, Minv, rhs, x, n_pcg, pflags, L, pairen, po) !=
+      cudaSuccess) {
     cudaGetLastError();
     if (cl <= 8) return -1;
     // the device refused the non-portable size: use the portable maximum from now on
     cluster_size_override(8);
-    return launch_pcg_cluster<Acc>(t, Df, pairoff, Minv, rhs, x, n_pcg, pflags, 8, inc_off_host, st);
+    return launch_pcg_cluster<Acc>(t, Df, pairoff, Minv, rhs, x, n_pcg, pflags, 8, inc_off_host, pairen, po, st);
   }
   return 1;
 }
 template int launch_pcg_cluster<double>(const Tables &, const float *, const float *, const float *, const double *,
-                                        float *, int, int *, int, const int *, cudaStream_t);
+                                        float *, int, int *, int, const int *, const double *, PcgOut, cudaStream_t);
 template int launch_pcg_cluster<float>(const Tables &, const float *, const float *, const float *, const float *,
-                                       float *, int, int *, int, const int *, cudaStream_t);
+                                       float *, int, int *, int, const int *, const float *, PcgOut, cudaStream_t);
 
 }  // namespace bf
