@@ -14,8 +14,36 @@ cx, cy):
 * I = ||grad L||_2 with central differences (f(x+1) - f(x-1)) / 2, defined on the
   1-pixel interior (0 elsewhere);
 * grad I by central differences of I, defined on the 2-pixel interior (0 elsewhere).
+
+16-bit frame storage (a B300 memory-layout option; the paper keeps its cached frames in
+FP32): normals, I and grad I are rounded to BF16 or FP16 (round to nearest, ties to even)
+and depth stays FP32.  The oracle rounds its own FP64 values, so it sees the same stored
+images as the device up to the rare value whose FP32 and FP64 results straddle a 16-bit
+rounding boundary.
 """
 import numpy as np
+
+# 16-bit storage formats: (significant bits incl. the implicit one, exponent of the smallest
+# subnormal spacing, largest finite value)
+STORAGE_FORMATS = {
+    "bf16": (8, -133, float.fromhex("0x1.fep127")),
+    "fp16": (11, -24, 65504.0),
+}
+
+
+def round_to_storage(x, kind):
+    """Round FP64 values to the nearest BF16 / FP16 value, ties to even (IEEE 754 rounding).
+
+    x = m 2^e with 0.5 <= |m| < 1 keeps p significant bits: the quantum is 2^(e - p), floored at
+    the format's subnormal spacing; values past the largest finite one become +-inf."""
+    if kind in (None, "fp32"):
+        return np.asarray(x, dtype=np.float64)
+    p, s_min, vmax = STORAGE_FORMATS[kind]
+    x = np.asarray(x, dtype=np.float64)
+    _, e = np.frexp(x)
+    qexp = np.maximum(e - p, s_min)
+    q = np.ldexp(np.round(np.ldexp(x, -qexp)), qexp)  # np.round: half to even
+    return np.where(np.abs(q) > vmax, np.copysign(np.inf, x), q)
 
 
 def valid_depth(D, depth_min, depth_max):
@@ -67,9 +95,12 @@ def intensity_gradient(L):
 
 
 class Frame:
-    """A preprocessed frame: depth, validity, normals, I and grad I (all FP64)."""
+    """A preprocessed frame: depth, validity, normals, I and grad I (all FP64).
 
-    def __init__(self, depth, lum, intr, depth_min=0.1, depth_max=10.0):
+    storage "bf16" / "fp16" rounds N, I and grad I to that format after computing them in
+    FP64 (depth stays exact); None or "fp32" keeps them as computed."""
+
+    def __init__(self, depth, lum, intr, depth_min=0.1, depth_max=10.0, storage=None):
         self.W, self.H = intr["W"], intr["H"]
         self.fx, self.fy, self.cx, self.cy = intr["fx"], intr["fy"], intr["cx"], intr["cy"]
         D = np.asarray(depth, dtype=np.float64)
@@ -77,10 +108,14 @@ class Frame:
         self.D = np.where(self.valid, D, 0.0)
         self.N, self.nvalid = normals(self.D, self.valid, self.fx, self.fy, self.cx, self.cy)
         self.I, self.Ix, self.Iy = intensity_gradient(lum)
+        self.storage = storage
+        if storage not in (None, "fp32"):
+            self.N = round_to_storage(self.N, storage)
+            self.I, self.Ix, self.Iy = (round_to_storage(v, storage) for v in (self.I, self.Ix, self.Iy))
         # FP32 copies for the association decisions (see association.py)
         self.D32 = self.D.astype(np.float32)
         self.N32 = self.N.astype(np.float32)
 
 
-def preprocess(problem_depth, problem_lum, intr, depth_min=0.1, depth_max=10.0):
-    return [Frame(d, l, intr, depth_min, depth_max) for d, l in zip(problem_depth, problem_lum)]
+def preprocess(problem_depth, problem_lum, intr, depth_min=0.1, depth_max=10.0, storage=None):
+    return [Frame(d, l, intr, depth_min, depth_max, storage) for d, l in zip(problem_depth, problem_lum)]

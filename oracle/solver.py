@@ -171,10 +171,12 @@ def sparse_pairs_for(problem, frame_ids):
 
 
 def solve_frames(problem, frame_ids, init_poses, params: SolveParams, depth_min=0.1, depth_max=10.0,
-                 frames_cache=None, direct=False):
-    """Gauss-Newton over the given frames (first one fixed) starting from init_poses (n,4,4)."""
+                 frames_cache=None, direct=False, storage=None):
+    """Gauss-Newton over the given frames (first one fixed) starting from init_poses (n,4,4);
+    storage "bf16" / "fp16" evaluates the dense term on 16-bit stored frames."""
     if frames_cache is None:
-        frames = [Frame(problem.depth[f], problem.lum[f], problem.intr, depth_min, depth_max) for f in frame_ids]
+        frames = [Frame(problem.depth[f], problem.lum[f], problem.intr, depth_min, depth_max, storage)
+                  for f in frame_ids]
     else:
         frames = [frames_cache[f] for f in frame_ids]
     sp = sparse_pairs_for(problem, frame_ids)

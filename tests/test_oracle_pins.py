@@ -502,3 +502,65 @@ def test_r_max_finds_the_worst_pair():
     assert pair == (sp[2].a, sp[2].b)
     # the moved point is now 0.5 m away in camera b coordinates -> 0.5 m in world
     assert abs(val - 0.5) < 1e-12
+
+
+# ------------------------------------------------------------------ 16-bit frame storage
+def _fp16_grid_values(rng, n):
+    """FP64 values around FP16 numbers: exact grid points, midpoints (ties), near-midpoints,
+    subnormals and values past the largest finite one."""
+    bits = rng.integers(0, 0x7C00, size=n, dtype=np.uint16)  # finite, non-negative halves
+    h = bits.view(np.float16).astype(np.float64)
+    nxt = (bits + 1).view(np.float16).astype(np.float64)
+    mid = 0.5 * (h + nxt)
+    eps = np.abs(mid) * 2.0 ** -30
+    x = np.concatenate([h, mid, mid + eps, mid - eps, rng.uniform(-70000, 70000, n)])
+    return np.concatenate([x, -x])
+
+
+def test_fp16_rounding_matches_ieee_half_conversion():
+    """round_to_storage('fp16') is IEEE round-to-nearest-even: NumPy's double -> half cast."""
+    x = _fp16_grid_values(np.random.default_rng(5), 4000)
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float16).astype(np.float64)
+    got = frames.round_to_storage(x, "fp16")
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_bf16_rounding_is_nearest_with_ties_to_even():
+    """Brute force: among the numbers with 8 significant bits around x, the result is a nearest
+    one, and on a tie the one with an even last bit."""
+    rng = np.random.default_rng(6)
+    x = np.concatenate([rng.normal(size=3000) * 10.0 ** rng.integers(-30, 30, 3000),
+                        1.0 + np.array([2.0 ** -8, 3 * 2.0 ** -8, 2.0 ** -9, 5 * 2.0 ** -9])])
+    got = frames.round_to_storage(x, "bf16")
+    for v, q in zip(x, got):
+        e = math.frexp(v)[1]
+        quantum = 2.0 ** (e - 8)
+        k0 = math.floor(v / quantum)
+        cands = [k * quantum for k in (k0 - 1, k0, k0 + 1, k0 + 2)]
+        dist = [abs(c - v) for c in cands]
+        best = min(dist)
+        near = [k for k, dd in zip((k0 - 1, k0, k0 + 1, k0 + 2), dist) if dd == best]
+        k = near[0] if len(near) == 1 else [k for k in near if k % 2 == 0][0]
+        assert q == k * quantum, (v, q, k * quantum)
+    # the closed-form ties above
+    assert list(got[-4:]) == [1.0, 1.0 + 2.0 ** -6, 1.0, 1.0 + 2.0 ** -7]
+
+
+def test_storage_rounding_of_a_frame():
+    """16-bit storage rounds normals, I and grad I only; depth and validity are untouched, and
+    every stored value is representable in the format (rounding it again changes nothing)."""
+    prob = synth.cfg1()
+    intr = prob.intr
+    f64 = frames.Frame(prob.depth[0], prob.lum[0], intr)
+    for kind in ("bf16", "fp16"):
+        f = frames.Frame(prob.depth[0], prob.lum[0], intr, storage=kind)
+        np.testing.assert_array_equal(f.D, f64.D)
+        np.testing.assert_array_equal(f.nvalid, f64.nvalid)
+        for a, b in ((f.N, f64.N), (f.I, f64.I), (f.Ix, f64.Ix), (f.Iy, f64.Iy)):
+            np.testing.assert_array_equal(frames.round_to_storage(a, kind), a)
+            bits = 8 if kind == "bf16" else 11
+            np.testing.assert_array_less(np.abs(a - b), np.abs(b) * 2.0 ** -bits + 2.0 ** -24 + 1e-300)
+        assert np.any(f.N != f64.N)
+    f32 = frames.Frame(prob.depth[0], prob.lum[0], intr, storage="fp32")
+    np.testing.assert_array_equal(f32.N, f64.N)
