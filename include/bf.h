@@ -56,15 +56,22 @@ typedef enum {
 
 enum { BF_PTR_HOST = 0, BF_PTR_DEVICE = 1 };
 
-/* Frame storage type of the preprocessed planes (depth, normal, I, grad I). */
+/* Frame storage type of the preprocessed planes (depth, normal, I, grad I).
+ *   BF_STORE_FP32: two float4 planes, 32 bytes per pixel.
+ *   BF_STORE_BF16 / BF_STORE_FP16: one 16-byte record per pixel; depth stays FP32 (the dense
+ *   association decisions read it), normal, I and grad I are rounded to nearest-even 16-bit
+ *   values after being computed in FP32.  Halves the frame footprint and the dense term's
+ *   frame traffic.  The paper keeps FP32 frames; this is a memory-layout option. */
 enum { BF_STORE_FP32 = 0, BF_STORE_BF16 = 1, BF_STORE_FP16 = 2 };
 
 /* PCG preconditioner: 6x6 block-Jacobi (default) or the paper's scalar Jacobi (Sec. 4.4). */
 enum { BF_PRECOND_BLOCK_JACOBI = 0, BF_PRECOND_JACOBI = 1 };
 
 /* Solver arithmetic.  Both evaluate residuals and Jacobians in FP32.
- *   BF_PREC_MIXED: per-tile FP32 tree sums merged in FP64; 6x6 blocks, PCG dot products and
- *                  the alpha/beta scalars in FP64; pose composition in FP64.
+ *   BF_PREC_MIXED: per-tile FP32 tree sums merged in FP64; 6x6 blocks and the sums of the PCG
+ *                  dot products above the warp in FP64; pose composition in FP64.  PCG vectors,
+ *                  their element updates, alpha and beta (quotients of the FP64 sums) and the
+ *                  block-Jacobi inverse are FP32.
  *   BF_PREC_FP32:  the plain path, FP32 throughout except the FP64 pose composition. */
 enum { BF_PREC_MIXED = 0, BF_PREC_FP32 = 1 };
 

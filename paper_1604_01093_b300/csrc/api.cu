@@ -226,34 +226,40 @@ static FrameStore frame_store(const bf_ctx *c) {
   fs.storage = c->cfg.storage;
   fs.W = c->cfg.width;
   fs.H = c->cfg.height;
-  fs.A = c->A;
-  fs.B = c->B;
-  fs.P16 = nullptr;
+  const bool f32 = c->cfg.storage == BF_STORE_FP32;
+  fs.A = f32 ? c->A : nullptr;
+  fs.B = f32 ? c->B : nullptr;
+  fs.P16 = f32 ? nullptr : (const uint4 *)c->A;  // 16-bit storage keeps its records in the A buffer
   fs.kx = c->kx;
   fs.ky = c->ky;
   return fs;
 }
 
-// grow the frame store to hold at least n slots
+// grow the frame store to hold at least n slots: FP32 storage keeps two 16-byte planes per
+// pixel (A = depth + normal, B = I + grad I), 16-bit storage one 16-byte record plane (in A)
 static bf_status ensure_frames(bf_ctx *c, int n) {
   if (n <= c->cap) return BF_OK;
   int ncap = std::max(n, std::max(2 * c->cap, c->cfg.max_frames_hint));
   const size_t HW = (size_t)c->cfg.width * c->cfg.height;
+  const bool two = c->cfg.storage == BF_STORE_FP32;
   float4 *nA = nullptr, *nB = nullptr;
   bf_status s = dalloc(c, (void **)&nA, ncap * HW * sizeof(float4), "frame store");
   if (s) return s;
-  s = dalloc(c, (void **)&nB, ncap * HW * sizeof(float4), "frame store");
-  if (s) {
-    dfree(c, nA, ncap * HW * sizeof(float4));
-    return s;
+  if (two) {
+    s = dalloc(c, (void **)&nB, ncap * HW * sizeof(float4), "frame store");
+    if (s) {
+      dfree(c, nA, ncap * HW * sizeof(float4));
+      return s;
+    }
   }
   if (c->cap) {
     CK(cudaMemcpyAsync(nA, c->A, c->cap * HW * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow frames");
-    CK(cudaMemcpyAsync(nB, c->B, c->cap * HW * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow frames");
+    if (two)
+      CK(cudaMemcpyAsync(nB, c->B, c->cap * HW * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow frames");
     CK(cudaStreamSynchronize(c->st), "grow frames");
   }
   dfree(c, c->A, c->cap * HW * sizeof(float4));
-  dfree(c, c->B, c->cap * HW * sizeof(float4));
+  if (two) dfree(c, c->B, c->cap * HW * sizeof(float4));
   c->A = nA;
   c->B = nB;
   c->cap = ncap;
@@ -351,7 +357,8 @@ extern "C" bf_status bf_create(const bf_config *cfg, bf_ctx **out) {
   *out = nullptr;
   if (cfg->width < 8 || cfg->height < 8 || cfg->width > 8192 || cfg->height > 8192) return BF_ERR_INVALID_ARG;
   if (!(cfg->fx > 0) || !(cfg->fy > 0)) return BF_ERR_INVALID_ARG;
-  if (cfg->storage != BF_STORE_FP32) return BF_ERR_INVALID_ARG;
+  if (cfg->storage != BF_STORE_FP32 && cfg->storage != BF_STORE_BF16 && cfg->storage != BF_STORE_FP16)
+    return BF_ERR_INVALID_ARG;
   bf_ctx *c = new bf_ctx();
   c->cfg = *cfg;
   if (c->cfg.max_frames_hint <= 0) c->cfg.max_frames_hint = 64;
@@ -511,8 +518,8 @@ extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *
     lptr = c->stage + n * HW;
   }
   run_k(c, BF_K_PREPROCESS, [&] {
-    return launch_preprocess(dptr, lptr, n, c->slot_dev, frame_store(c), c->A, c->B, nullptr, c->cfg.depth_min,
-                             c->cfg.depth_max, c->st);
+    return launch_preprocess(dptr, lptr, n, c->slot_dev, frame_store(c), c->A, c->B, (uint4 *)c->A,
+                             c->cfg.depth_min, c->cfg.depth_max, c->st);
   });
   CK(cudaGetLastError(), "preprocess launch");
   CK(cudaEventRecord(c->data_ev, c->st), "data event");
@@ -529,9 +536,33 @@ extern "C" bf_status bf_get_frame_planes(bf_ctx *c, int frame_id, float *out) {
   std::vector<float4> a(HW), b(HW);
   CK(cudaMemcpyAsync(a.data(), c->A + it->second.slot * HW, HW * sizeof(float4), cudaMemcpyDeviceToHost, c->st),
      "planes");
-  CK(cudaMemcpyAsync(b.data(), c->B + it->second.slot * HW, HW * sizeof(float4), cudaMemcpyDeviceToHost, c->st),
-     "planes");
+  if (c->cfg.storage == BF_STORE_FP32)
+    CK(cudaMemcpyAsync(b.data(), c->B + it->second.slot * HW, HW * sizeof(float4), cudaMemcpyDeviceToHost, c->st),
+       "planes");
   CK(cudaStreamSynchronize(c->st), "planes");
+  if (c->cfg.storage != BF_STORE_FP32) {
+    // unpack the 16-bit records: {D bits, nx | ny, nz | I, Ix | Iy}
+    const bool bf = c->cfg.storage == BF_STORE_BF16;
+    auto h2f = [bf](uint32_t h) {
+      if (bf) {
+        const uint32_t u = h << 16;
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+      }
+      __half_raw r;
+      r.x = (unsigned short)h;
+      return __half2float(__half(r));
+    };
+    for (size_t k = 0; k < HW; ++k) {
+      uint32_t w[4];
+      std::memcpy(w, &a[k], 16);
+      float d;
+      std::memcpy(&d, &w[0], 4);
+      a[k] = make_float4(d, h2f(w[1] & 0xffffu), h2f(w[1] >> 16), h2f(w[2] & 0xffffu));
+      b[k] = make_float4(h2f(w[2] >> 16), h2f(w[3] & 0xffffu), h2f(w[3] >> 16), 0.f);
+    }
+  }
   for (size_t k = 0; k < HW; ++k) {
     out[k] = a[k].x;
     out[HW + k] = a[k].y;
@@ -724,7 +755,7 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
   // dense work decomposition: explicit tile_px -> tiles of that many pixels; automatic -> the
   // target frame staged in shared memory when it fits (one partial per directed pair), else
   // 4800-pixel tiles
-  const bool staged = prm.tile_px == 0 && dense_staged_fits(c->cfg.width, c->cfg.height);
+  const bool staged = prm.tile_px == 0 && dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage);
   int tile_px = prm.tile_px > 0 ? prm.tile_px : (staged ? HW : std::min(HW, 4800));
   T.n_prob = (int)probs.size();
   std::vector<std::vector<std::pair<int, int>>> var_inc;  // per var: (pair, side)

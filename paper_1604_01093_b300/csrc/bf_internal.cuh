@@ -15,6 +15,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "bf.h"
+
 namespace bf {
 
 // ---------------------------------------------------------------------------------------------
@@ -71,9 +73,43 @@ struct FrameStore {
   int W, H;
   const float4 *A;        // FP32: [slot][HW] (D, n)
   const float4 *B;        // FP32: [slot][HW] (I, Ix, Iy, 0)
-  const uint4 *P16;       // BF16/FP16: [slot][HW] 8 halves: D(hi,lo as fp32 split), n xyz, I, Ix, Iy
+  const uint4 *P16;       // BF16/FP16: [slot][HW] records {D (FP32 bits), nx | ny, nz | I, Ix | Iy}
   const float *kx, *ky;   // kx[x] = fl32((x - cx)/fx), ky[y] = fl32((y - cy)/fy)
 };
+
+// 16-bit storage record of one pixel (16 bytes): word 0 the FP32 depth bits, words 1-3 the pairs
+// (nx, ny), (nz, I), (Ix, Iy) as BF16 or FP16, low half first.  Rounding is to nearest, ties to
+// even, from the FP32 values.
+template <int KIND>
+__device__ __forceinline__ unsigned short f32_to16(float v) {
+  if (KIND == BF_STORE_BF16) return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  return __half_as_ushort(__float2half_rn(v));
+}
+template <int KIND>
+__device__ __forceinline__ float f16_to32(unsigned h) {
+  if (KIND == BF_STORE_BF16) return __uint_as_float(h << 16);  // BF16 = the top half of an FP32
+  return __half2float(__ushort_as_half((unsigned short)h));
+}
+template <int KIND>
+__device__ __forceinline__ uint4 pack16(float4 a, float I, float Ix, float Iy) {
+  uint4 r;
+  r.x = __float_as_uint(a.x);
+  r.y = (unsigned)f32_to16<KIND>(a.y) | ((unsigned)f32_to16<KIND>(a.z) << 16);
+  r.z = (unsigned)f32_to16<KIND>(a.w) | ((unsigned)f32_to16<KIND>(I) << 16);
+  r.w = (unsigned)f32_to16<KIND>(Ix) | ((unsigned)f32_to16<KIND>(Iy) << 16);
+  return r;
+}
+// (D, nx, ny, nz) of a record
+template <int KIND>
+__device__ __forceinline__ float4 unpack16_dn(uint4 r) {
+  return make_float4(__uint_as_float(r.x), f16_to32<KIND>(r.y & 0xffffu), f16_to32<KIND>(r.y >> 16),
+                     f16_to32<KIND>(r.z & 0xffffu));
+}
+// (I, Ix, Iy, 0) of a record
+template <int KIND>
+__device__ __forceinline__ float4 unpack16_i(uint4 r) {
+  return make_float4(f16_to32<KIND>(r.z >> 16), f16_to32<KIND>(r.w & 0xffffu), f16_to32<KIND>(r.w >> 16), 0.f);
+}
 
 // Flattened tables of one (batched) solve, all int32 device pointers.
 struct Tables {
@@ -198,7 +234,8 @@ int launch_pack_corr_batch(const float *p_i, const float *p_j, const float *w, i
 // Target-staged dense kernel (whole target frame in shared memory, loaded by TMA bulk copies).
 // Usable when dense_staged_fits(W, H); writes one partial per directed pair.  err: device int
 // set to 1 if a bulk copy did not complete within the wait limit.
-bool dense_staged_fits(int W, int H);
+bool dense_staged_fits(int W, int H, int storage);
+int dense_staged_smem(int W, int H, int storage);
 template <typename Part>
 int launch_dense_staged(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                         float w_geo, float w_photo, Part *part, int *err, cudaStream_t st);

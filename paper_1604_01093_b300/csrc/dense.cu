@@ -82,13 +82,13 @@ __device__ __forceinline__ PairXf load_xf(const float *M) {
 }
 
 // Evaluate source pixel (x, y) of a directed pair: association, gates and (MODE_ACCUM) the
-// residual rows' contributions to acc.  a = source (D, n); loadA / loadB read the target
-// planes; Bs is the source I plane.  Returns the associated target pixel or -1.
-template <int MODE, typename LA, typename LB>
-__device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, int px, const PairXf &X, const Intr &in,
+// residual rows' contributions to acc.  a = source (D, n); loadA / loadB read the target's
+// (D, n) and (I, Ix, Iy); srcI() gives the source pixel's I.  Returns the associated target
+// pixel or -1.
+template <int MODE, typename LA, typename LB, typename LI>
+__device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const PairXf &X, const Intr &in,
                                           const float *kx, const float *ky, const Gates &g, LA loadA, LB loadB,
-                                          const float4 *__restrict__ Bs, float w_geo, float w_photo,
-                                          float (&acc)[NPD]) {
+                                          LI srcI, float w_geo, float w_photo, float (&acc)[NPD]) {
   const bool nvalid = (a.y != 0.f) || (a.z != 0.f) || (a.w != 0.f);
   if (!(a.x > 0.f && nvalid)) return -1;
   const int W = in.W, H = in.H;
@@ -138,7 +138,7 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, int px, 
   const float Ij = w00 * c00.x + w01 * c01.x + w10 * c10.x + w11 * c11.x;
   const float gxI = w00 * c00.y + w01 * c01.y + w10 * c10.y + w11 * c11.y;
   const float gyI = w00 * c00.z + w01 * c01.z + w10 * c10.z + w11 * c11.z;
-  const float r_p = Bs[px].x - Ij;
+  const float r_p = srcI() - Ij;
   acc[D_E0] += r_g * r_g;
   acc[D_E1] += r_p * r_p;
   acc[D_CNT] += 1.f;
@@ -176,7 +176,7 @@ struct PixWalk {
 
 constexpr int DENSE_BS = 256;
 
-template <int MODE, typename Part>
+template <int MODE, int KIND, typename Part>
 __global__ void __launch_bounds__(DENSE_BS, 4)
     k_dense(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo, float w_photo,
             Part *__restrict__ part, int *__restrict__ assoc) {
@@ -187,10 +187,6 @@ __global__ void __launch_bounds__(DENSE_BS, 4)
   const int W = in.W, H = in.H;
   const long long HW = (long long)W * H;
   const int ss = t.frame_slot[t.dp_src[d]], ts = t.frame_slot[t.dp_dst[d]];
-  const float4 *__restrict__ As = fs.A + (long long)ss * HW;
-  const float4 *__restrict__ Bs = fs.B + (long long)ss * HW;
-  const float4 *__restrict__ At = fs.A + (long long)ts * HW;
-  const float4 *__restrict__ Bt = fs.B + (long long)ts * HW;
   const PairXf X = load_xf(pairM + (t.dp_pair[d] * 2 + t.dp_dir[d]) * 12);
   float *kx = ktab, *ky = ktab + W;
   for (int k = threadIdx.x; k < W + H; k += DENSE_BS) ktab[k] = k < W ? fs.kx[k] : fs.ky[k - W];
@@ -198,17 +194,51 @@ __global__ void __launch_bounds__(DENSE_BS, 4)
   float acc[NPD];
 #pragma unroll
   for (int k = 0; k < NPD; ++k) acc[k] = 0.f;
-  auto loadA = [&](int i) { return At[i]; };
-  auto loadB = [&](int i) { return Bt[i]; };
-  float4 a_next = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (px0 + (int)threadIdx.x < px1) a_next = As[px0 + threadIdx.x];
-  for (PixWalk w(px0 + threadIdx.x, DENSE_BS, W); w.px < px1; w.next(DENSE_BS)) {
-    const float4 a = a_next;  // prefetched one iteration ahead
-    if (w.px + DENSE_BS < px1) a_next = As[w.px + DENSE_BS];
-    const int tgt = eval_pixel<MODE>(a, w.x, w.y, w.px, X, in, kx, ky, g, loadA, loadB, Bs, w_geo, w_photo, acc);
-    if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
+  if (KIND == BF_STORE_FP32) {
+    const float4 *__restrict__ As = fs.A + (long long)ss * HW;
+    const float4 *__restrict__ Bs = fs.B + (long long)ss * HW;
+    const float4 *__restrict__ At = fs.A + (long long)ts * HW;
+    const float4 *__restrict__ Bt = fs.B + (long long)ts * HW;
+    auto loadA = [&](int i) { return At[i]; };
+    auto loadB = [&](int i) { return Bt[i]; };
+    float4 a_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (px0 + (int)threadIdx.x < px1) a_next = As[px0 + threadIdx.x];
+    for (PixWalk w(px0 + threadIdx.x, DENSE_BS, W); w.px < px1; w.next(DENSE_BS)) {
+      const float4 a = a_next;  // prefetched one iteration ahead
+      if (w.px + DENSE_BS < px1) a_next = As[w.px + DENSE_BS];
+      const int px = w.px;
+      auto srcI = [&]() { return Bs[px].x; };
+      const int tgt = eval_pixel<MODE>(a, w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
+      if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
+    }
+  } else {
+    const uint4 *__restrict__ Ps = fs.P16 + (long long)ss * HW;
+    const uint4 *__restrict__ Pt = fs.P16 + (long long)ts * HW;
+    auto loadA = [&](int i) { return unpack16_dn<KIND>(Pt[i]); };
+    auto loadB = [&](int i) { return unpack16_i<KIND>(Pt[i]); };
+    uint4 r_next = make_uint4(0u, 0u, 0u, 0u);
+    if (px0 + (int)threadIdx.x < px1) r_next = Ps[px0 + threadIdx.x];
+    for (PixWalk w(px0 + threadIdx.x, DENSE_BS, W); w.px < px1; w.next(DENSE_BS)) {
+      const uint4 r = r_next;
+      if (w.px + DENSE_BS < px1) r_next = Ps[w.px + DENSE_BS];
+      auto srcI = [&]() { return unpack16_i<KIND>(r).x; };
+      const int tgt = eval_pixel<MODE>(unpack16_dn<KIND>(r), w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo,
+                                       w_photo, acc);
+      if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
+    }
   }
   if (MODE != MODE_ASSOC) cta_reduce_store<DENSE_BS, NPD, Part>(acc, part + (long long)tile * NPD);
+}
+
+template <int MODE, typename Part>
+static void dense_go(int kind, int n, size_t ks, cudaStream_t st, const Tables &t, const FrameStore &fs,
+                     const Intr &in, const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *assoc) {
+  if (kind == BF_STORE_BF16)
+    k_dense<MODE, BF_STORE_BF16, Part><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+  else if (kind == BF_STORE_FP16)
+    k_dense<MODE, BF_STORE_FP16, Part><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+  else
+    k_dense<MODE, BF_STORE_FP32, Part><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
 }
 
 template <typename Part>
@@ -217,18 +247,18 @@ int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in
   if (t.n_tiles == 0) return 0;
   const size_t ks = (size_t)(in.W + in.H) * sizeof(float);
   if (mode == MODE_ACCUM)
-    k_dense<MODE_ACCUM, Part><<<t.n_tiles, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    dense_go<MODE_ACCUM>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else if (mode == MODE_ENERGY)
-    k_dense<MODE_ENERGY, Part><<<t.n_tiles, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    dense_go<MODE_ENERGY>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else
-    k_dense<MODE_ASSOC, Part><<<t.n_tiles, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    dense_go<MODE_ASSOC>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   return 1;
 }
 
 // ---------------------------------------------------------------------------------------------
 // Target-staged variant.  At the paper's dense resolution (80x60) a frame's two planes take
-// 2 x 76.8 KB, so one CTA holds its target frame in shared memory: a single thread issues two
-// cp.async.bulk copies completing on an mbarrier, every thread waits (bounded), and all target
+// 2 x 76.8 KB (FP32; one 76.8 KB record plane with 16-bit storage), so one CTA holds its target
+// frame in shared memory: a single thread issues the cp.async.bulk copies completing on an mbarrier, every thread waits (bounded), and all target
 // reads of the CTA's source frames then hit shared memory instead of L1/L2.  Work item = one
 // target frame with a few of its source frames (the host uses 4, one per quad, so that the
 // one-CTA-per-SM grid stays balanced); the CTA's 16 warps form 4 quads and each quad
@@ -239,7 +269,13 @@ constexpr int STG_QUADS = STG_BS / 128;
 constexpr int STG_MAX_SMEM = 200 * 1024;
 constexpr long long STG_WAIT_LIMIT = 1LL << 22;
 
-bool dense_staged_fits(int W, int H) { return (long long)W * H * 32 + (W + H) * 4 + 4096 <= STG_MAX_SMEM; }
+// Dynamic shared memory of the staged kernel: the target frame (32 B/px FP32 planes, 16 B/px
+// packed records) plus the ray tables.
+int dense_staged_smem(int W, int H, int storage) {
+  const long long b = (long long)W * H * (storage == BF_STORE_FP32 ? 32 : 16) + (W + H) * 4;
+  return b > (1LL << 30) ? (1 << 30) : (int)b;
+}
+bool dense_staged_fits(int W, int H, int storage) { return dense_staged_smem(W, H, storage) + 4096 <= STG_MAX_SMEM; }
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -288,17 +324,20 @@ __device__ __forceinline__ void quad_reduce_store(float (&acc)[N], float (*red)[
   asm volatile("bar.sync %0, 128;" ::"r"(1 + quad) : "memory");  // red reused by the next pair
 }
 
-template <int MODE, typename Part>
+template <int MODE, int KIND, typename Part>
 __global__ void __launch_bounds__(STG_BS, 1)
     k_dense_staged(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo,
                    float w_photo, Part *__restrict__ part, int *__restrict__ err) {
   extern __shared__ __align__(128) float4 stg[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ float red[STG_QUADS][4][NPD];
+  constexpr bool F32 = KIND == BF_STORE_FP32;
   const int W = in.W, H = in.H, HW = W * H;
   const int k0 = t.wi_off[blockIdx.x], k1 = t.wi_off[blockIdx.x + 1];
   const int tslot = t.frame_slot[t.dp_dst[t.sw_dp[k0]]];
+  // FP32: the target's (D, n) and (I, Ix, Iy) planes; 16-bit: its packed records
   float4 *sA = stg, *sB = stg + HW;
+  const uint4 *sP = (const uint4 *)stg;
   const unsigned barp = smem_u32(&bar);
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barp) : "memory");
@@ -307,15 +346,18 @@ __global__ void __launch_bounds__(STG_BS, 1)
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned bytes = (unsigned)HW * 16u;
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(barp), "r"(2u * bytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(barp), "r"((F32 ? 2u : 1u) * bytes)
+                 : "memory");
+    const void *src0 = F32 ? (const void *)(fs.A + (long long)tslot * HW) : (const void *)(fs.P16 + (long long)tslot * HW);
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_u32(sA)),
-                 "l"(fs.A + (long long)tslot * HW), "r"(bytes), "r"(barp)
+                 "l"(src0), "r"(bytes), "r"(barp)
                  : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(sB)),
-                 "l"(fs.B + (long long)tslot * HW), "r"(bytes), "r"(barp)
-                 : "memory");
+    if (F32)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(sB)),
+                   "l"(fs.B + (long long)tslot * HW), "r"(bytes), "r"(barp)
+                   : "memory");
   }
   if (!mbar_wait0(barp)) {
     // the copies did not land within the limit: report, wait once more for them, then leave
@@ -324,49 +366,78 @@ __global__ void __launch_bounds__(STG_BS, 1)
     return;
   }
   const int quad = threadIdx.x >> 7, tq = threadIdx.x & 127;
-  float *kx = (float *)(stg + 2 * HW), *ky = kx + W;
+  float *kx = (float *)(stg + (F32 ? 2 : 1) * HW), *ky = kx + W;
   for (int k = threadIdx.x; k < W + H; k += STG_BS) kx[k] = k < W ? fs.kx[k] : fs.ky[k - W];
   __syncthreads();
-  auto loadA = [&](int i) { return sA[i]; };
-  auto loadB = [&](int i) { return sB[i]; };
   for (int k = k0 + quad; k < k1; k += STG_QUADS) {
     const int d = t.sw_dp[k];
-    const float4 *__restrict__ As = fs.A + (long long)t.frame_slot[t.dp_src[d]] * HW;
-    const float4 *__restrict__ Bs = fs.B + (long long)t.frame_slot[t.dp_src[d]] * HW;
+    const long long so = (long long)t.frame_slot[t.dp_src[d]] * HW;
     const PairXf X = load_xf(pairM + (t.dp_pair[d] * 2 + t.dp_dir[d]) * 12);
     float acc[NPD];
 #pragma unroll
     for (int q = 0; q < NPD; ++q) acc[q] = 0.f;
-    float4 a_next = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (tq < HW) a_next = As[tq];
-    for (PixWalk w(tq, 128, W); w.px < HW; w.next(128)) {
-      const float4 a = a_next;
-      if (w.px + 128 < HW) a_next = As[w.px + 128];
-      eval_pixel<MODE>(a, w.x, w.y, w.px, X, in, kx, ky, g, loadA, loadB, Bs, w_geo, w_photo, acc);
+    if (F32) {
+      const float4 *__restrict__ As = fs.A + so;
+      const float4 *__restrict__ Bs = fs.B + so;
+      auto loadA = [&](int i) { return sA[i]; };
+      auto loadB = [&](int i) { return sB[i]; };
+      float4 a_next = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (tq < HW) a_next = As[tq];
+      for (PixWalk w(tq, 128, W); w.px < HW; w.next(128)) {
+        const float4 a = a_next;
+        if (w.px + 128 < HW) a_next = As[w.px + 128];
+        const int px = w.px;
+        auto srcI = [&]() { return Bs[px].x; };
+        eval_pixel<MODE>(a, w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
+      }
+    } else {
+      const uint4 *__restrict__ Ps = fs.P16 + so;
+      auto loadA = [&](int i) { return unpack16_dn<KIND>(sP[i]); };
+      auto loadB = [&](int i) { return unpack16_i<KIND>(sP[i]); };
+      uint4 r_next = make_uint4(0u, 0u, 0u, 0u);
+      if (tq < HW) r_next = Ps[tq];
+      for (PixWalk w(tq, 128, W); w.px < HW; w.next(128)) {
+        const uint4 r = r_next;
+        if (w.px + 128 < HW) r_next = Ps[w.px + 128];
+        auto srcI = [&]() { return unpack16_i<KIND>(r).x; };
+        eval_pixel<MODE>(unpack16_dn<KIND>(r), w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
+      }
     }
     quad_reduce_store<NPD, Part>(acc, red[quad], quad, part + (long long)d * NPD);
   }
+}
+
+template <int MODE, int KIND, typename Part>
+static void staged_go(int n, int smem, cudaStream_t st, const Tables &t, const FrameStore &fs, const Intr &in,
+                      const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *err) {
+  static bool attr_set = false;  // one flag per instantiation
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_dense_staged<MODE, KIND, Part>, cudaFuncAttributeMaxDynamicSharedMemorySize, STG_MAX_SMEM);
+    attr_set = true;
+  }
+  k_dense_staged<MODE, KIND, Part><<<n, STG_BS, smem, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, err);
+}
+
+template <int MODE, typename Part>
+static void staged_kind(int kind, int n, int smem, cudaStream_t st, const Tables &t, const FrameStore &fs,
+                        const Intr &in, const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *err) {
+  if (kind == BF_STORE_BF16)
+    staged_go<MODE, BF_STORE_BF16, Part>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
+  else if (kind == BF_STORE_FP16)
+    staged_go<MODE, BF_STORE_FP16, Part>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
+  else
+    staged_go<MODE, BF_STORE_FP32, Part>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
 }
 
 template <typename Part>
 int launch_dense_staged(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                         float w_geo, float w_photo, Part *part, int *err, cudaStream_t st) {
   if (t.n_wi == 0) return 0;
-  const int smem = in.W * in.H * 32 + (in.W + in.H) * 4;
-  static int set[2][2] = {{0, 0}, {0, 0}};
-  int &cur = set[sizeof(Part) == 8 ? 1 : 0][mode == MODE_ACCUM ? 0 : 1];
-  if (smem > cur) {
-    if (mode == MODE_ACCUM)
-      cudaFuncSetAttribute(k_dense_staged<MODE_ACCUM, Part>, cudaFuncAttributeMaxDynamicSharedMemorySize, STG_MAX_SMEM);
-    else
-      cudaFuncSetAttribute(k_dense_staged<MODE_ENERGY, Part>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           STG_MAX_SMEM);
-    cur = STG_MAX_SMEM;
-  }
+  const int smem = dense_staged_smem(in.W, in.H, fs.storage);
   if (mode == MODE_ACCUM)
-    k_dense_staged<MODE_ACCUM, Part><<<t.n_wi, STG_BS, smem, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, err);
+    staged_kind<MODE_ACCUM, Part>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
   else
-    k_dense_staged<MODE_ENERGY, Part><<<t.n_wi, STG_BS, smem, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, err);
+    staged_kind<MODE_ENERGY, Part>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
   return 1;
 }
 template int launch_dense_staged<float>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates,

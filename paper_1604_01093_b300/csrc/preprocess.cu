@@ -15,26 +15,23 @@ __device__ __forceinline__ bool depth_ok(float z, float dmin, float dmax) {
   return isfinite(z) && z > dmin && z < dmax;
 }
 
-// Pass 1: validity, normals, I.  One thread per pixel of n frames.
-__global__ void k_pre1(const float *__restrict__ depth, const float *__restrict__ lum, int n,
-                       const int *__restrict__ slots, FrameStore fs, float4 *__restrict__ A,
-                       float4 *__restrict__ B, float dmin, float dmax) {
+// |grad L| at interior pixel pix (central differences).
+__device__ __forceinline__ float lum_grad_mag(const float *__restrict__ Lf, int pix, int W) {
+  const float gx = 0.5f * (Lf[pix + 1] - Lf[pix - 1]);
+  const float gy = 0.5f * (Lf[pix + W] - Lf[pix - W]);
+  return sqrtf(gx * gx + gy * gy);
+}
+
+// Depth (0 if invalid) and unit normal (0 if invalid) of pixel (x, y).
+__device__ __forceinline__ float4 depth_normal(const float *__restrict__ Df, int pix, int x, int y,
+                                               const FrameStore &fs, float dmin, float dmax) {
   const int W = fs.W, H = fs.H;
-  const long long HW = (long long)W * H;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * HW) return;
-  const int f = (int)(idx / HW);
-  const int pix = (int)(idx - (long long)f * HW);
-  const int y = pix / W, x = pix - y * W;
-  const float *Df = depth + (long long)f * HW;
-  const float *Lf = lum + (long long)f * HW;
   const float z = Df[pix];
   const bool ok = depth_ok(z, dmin, dmax);
   float4 a = make_float4(ok ? z : 0.f, 0.f, 0.f, 0.f);
-  float I = 0.f;
-  if (x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2) {
+  if (ok && x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2) {
     const float zl = Df[pix - 1], zr = Df[pix + 1], zu = Df[pix - W], zd = Df[pix + W];
-    if (ok && depth_ok(zl, dmin, dmax) && depth_ok(zr, dmin, dmax) && depth_ok(zu, dmin, dmax) &&
+    if (depth_ok(zl, dmin, dmax) && depth_ok(zr, dmin, dmax) && depth_ok(zu, dmin, dmax) &&
         depth_ok(zd, dmin, dmax)) {
       const float kxl = fs.kx[x - 1], kxr = fs.kx[x + 1], kxc = fs.kx[x];
       const float kyu = fs.ky[y - 1], kyd = fs.ky[y + 1], kyc = fs.ky[y];
@@ -51,10 +48,25 @@ __global__ void k_pre1(const float *__restrict__ depth, const float *__restrict_
         a.w = cz / nrm;
       }
     }
-    const float gx = 0.5f * (Lf[pix + 1] - Lf[pix - 1]);
-    const float gy = 0.5f * (Lf[pix + W] - Lf[pix - W]);
-    I = sqrtf(gx * gx + gy * gy);
   }
+  return a;
+}
+
+// Pass 1: validity, normals, I.  One thread per pixel of n frames.
+__global__ void k_pre1(const float *__restrict__ depth, const float *__restrict__ lum, int n,
+                       const int *__restrict__ slots, FrameStore fs, float4 *__restrict__ A,
+                       float4 *__restrict__ B, float dmin, float dmax) {
+  const int W = fs.W, H = fs.H;
+  const long long HW = (long long)W * H;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * HW) return;
+  const int f = (int)(idx / HW);
+  const int pix = (int)(idx - (long long)f * HW);
+  const int y = pix / W, x = pix - y * W;
+  const float *Df = depth + (long long)f * HW;
+  const float *Lf = lum + (long long)f * HW;
+  const float4 a = depth_normal(Df, pix, x, y, fs, dmin, dmax);
+  const float I = (x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2) ? lum_grad_mag(Lf, pix, W) : 0.f;
   const long long o = (long long)slots[f] * HW + pix;
   A[o] = a;
   B[o] = make_float4(I, 0.f, 0.f, 0.f);
@@ -76,13 +88,46 @@ __global__ void k_pre2(int n, const int *__restrict__ slots, int W, int H, float
   Bf[pix] = b;
 }
 
+// 16-bit storage: one pass writes the packed record (depth FP32, normal, I, grad I rounded to
+// BF16 / FP16); the neighbours' I for grad I is recomputed from the luminance in FP32, so grad I
+// is formed from unrounded I exactly as in the FP32 path and rounded once.
+template <int KIND>
+__global__ void k_pre16(const float *__restrict__ depth, const float *__restrict__ lum, int n,
+                        const int *__restrict__ slots, FrameStore fs, uint4 *__restrict__ P, float dmin,
+                        float dmax) {
+  const int W = fs.W, H = fs.H;
+  const long long HW = (long long)W * H;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * HW) return;
+  const int f = (int)(idx / HW);
+  const int pix = (int)(idx - (long long)f * HW);
+  const int y = pix / W, x = pix - y * W;
+  const float *Df = depth + (long long)f * HW;
+  const float *Lf = lum + (long long)f * HW;
+  const float4 a = depth_normal(Df, pix, x, y, fs, dmin, dmax);
+  float I = 0.f, Ix = 0.f, Iy = 0.f;
+  if (x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2) I = lum_grad_mag(Lf, pix, W);
+  if (x >= 2 && x <= W - 3 && y >= 2 && y <= H - 3) {
+    Ix = 0.5f * (lum_grad_mag(Lf, pix + 1, W) - lum_grad_mag(Lf, pix - 1, W));
+    Iy = 0.5f * (lum_grad_mag(Lf, pix + W, W) - lum_grad_mag(Lf, pix - W, W));
+  }
+  P[(long long)slots[f] * HW + pix] = pack16<KIND>(a, I, Ix, Iy);
+}
+
 int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
                        float4 *A, float4 *B, uint4 *P16, float dmin, float dmax, cudaStream_t st) {
-  (void)P16;
   const long long total = (long long)n * fs.W * fs.H;
   if (total == 0) return 0;
   const int bs = 256;
   const unsigned grid = (unsigned)((total + bs - 1) / bs);
+  if (fs.storage == BF_STORE_BF16) {
+    k_pre16<BF_STORE_BF16><<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, P16, dmin, dmax);
+    return 1;
+  }
+  if (fs.storage == BF_STORE_FP16) {
+    k_pre16<BF_STORE_FP16><<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, P16, dmin, dmax);
+    return 1;
+  }
   k_pre1<<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, A, B, dmin, dmax);
   k_pre2<<<grid, bs, 0, st>>>(n, slots_dev, fs.W, fs.H, B);
   return 2;

@@ -37,22 +37,24 @@ namespace cgx = cooperative_groups;
 namespace bf {
 
 // ------------------------------------------------------------------------------- pair xform
-// Both transforms of every pair, one thread per pair: M_ab = T_b^-1 T_a (source a) then M_ba.
-// The per-problem PCG kernel refreshes its own pairs' transforms after the pose update; this
-// kernel serves the first linearisation of a solve and the multi-CTA PCG variants.
+// Both transforms of every pair, M_ab = T_b^-1 T_a (source a) then M_ba, one thread per entry
+// (24 per pair): each entry is a handful of FP64 operations, and spreading them over many warps
+// keeps the slow FP64 pipe of each SM sub-partition short.  The per-problem PCG kernel refreshes
+// its own pairs' transforms after the pose update; this kernel serves the first linearisation of
+// a solve and the multi-CTA PCG variants.
 __global__ void k_pair_xform(int n_pairs, const int *__restrict__ pa, const int *__restrict__ pb,
                              const double *__restrict__ pose, float *__restrict__ pairM) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n_pairs) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= 24 * n_pairs) return;
+  const int p = k / 24, e = k % 24;
   const double *Ta = pose + 12 * pa[p];
   const double *Tb = pose + 12 * pb[p];
-  pair_xform32(Ta, Tb, pairM + 24 * p);
-  pair_xform32(Tb, Ta, pairM + 24 * p + 12);
+  pairM[k] = e < 12 ? pair_xform_entry(Ta, Tb, e) : pair_xform_entry(Tb, Ta, e - 12);
 }
 
 int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st) {
   if (t.n_pairs == 0) return 0;
-  k_pair_xform<<<(t.n_pairs + 127) / 128, 128, 0, st>>>(t.n_pairs, t.pair_a, t.pair_b, pose, pairM);
+  k_pair_xform<<<(24 * t.n_pairs + 127) / 128, 128, 0, st>>>(t.n_pairs, t.pair_a, t.pair_b, pose, pairM);
   return 1;
 }
 
