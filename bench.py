@@ -41,12 +41,21 @@ import numpy as np  # noqa: E402
 METRIC = "GN iterations/sec + chunk-solve p50/p99 latency vs plain GPU path; HBM GB/s frac"
 UNIT = "GN iterations/s"
 DENSE_BYTES_PER_PX = 48  # FP32: source D, n, I (20 B) + target D, n nearest (16 B) + I, grad I bilinear (12 B)
+# 16-bit storage: D stays FP32, n, I, grad I take 2 B each: source 4 + 8, target 4 + 6 + 6
+DENSE_BYTES_PER_PX_16 = 28
+STORAGE_CODES = {"fp32": lambda bf: bf.BF_STORE_FP32, "bf16": lambda bf: bf.BF_STORE_BF16,
+                 "fp16": lambda bf: bf.BF_STORE_FP16}
+
+
+def dense_bytes_per_px(storage):
+    return DENSE_BYTES_PER_PX if storage == "fp32" else DENSE_BYTES_PER_PX_16
+
 # FP32 flops of the dense kernel per directed source pixel on this workload: ncu FFMA x 2 + FADD + FMUL
-# of one ACCUM launch divided by its 21.84 M directed source pixels (profiles/k_dense_global300_80x60.md)
+# of one ACCUM launch divided by its 21.84 M directed source pixels (profiles/k_dense_staged_global300_80x60.md)
 DENSE_FLOPS_PER_PX = 139.0
 # DRAM bytes (read + write) of one dense ACCUM launch from the same ncu capture (cold cache); set to
 # None whenever k_dense changes until it is captured again
-DENSE_TRAFFIC_BYTES = 41.39e6 + 0.05e6
+DENSE_TRAFFIC_BYTES = 46.44e6 + 0.09e6
 # B300 FP32 peak: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
@@ -63,6 +72,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--tile-px", type=int, default=0,
                     help="dense work item size in source pixels; 0 = automatic (target frame staged in shared memory)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
+                    help="frame storage of the timed workload (16-bit: normals, I, grad I)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="PCG kernel: 0 auto, 1 one CTA per problem, 2 grid-cooperative, 3 cluster")
     return ap.parse_args()
@@ -221,8 +232,9 @@ def run_ours(args, rank, world, local_rank):
                                     tile_px=args.tile_px)
     stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
     torch.cuda.set_stream(stream)
+    storage = STORAGE_CODES[args.storage](bf)
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
-                     stream=stream.cuda_stream, max_frames_hint=n)
+                     stream=stream.cuda_stream, max_frames_hint=n, storage=storage)
     depth_d = torch.from_numpy(prob.depth).to(dev)
     lum_d = torch.from_numpy(prob.lum).to(dev)
     pi_d = torch.from_numpy(prob.p_i).to(dev)
@@ -295,13 +307,15 @@ def run_ours(args, rank, world, local_rank):
     dense_ms = dense["ms"] / max(dense["count"], 1)
     units = n_dp * HW
     flops = DENSE_FLOPS_PER_PX * units
-    alg_bytes = DENSE_BYTES_PER_PX * units
+    alg_bytes = dense_bytes_per_px(args.storage) * units
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     achieved_tf = flops / (dense_ms / 1000.0) / 1e12
     achieved_gbs = alg_bytes / (dense_ms / 1000.0) / 1e9
     gpu_launches = launches
+    # the captured DRAM traffic belongs to the default configuration's dense kernel only
+    traffic = DENSE_TRAFFIC_BYTES if (args.storage == "fp32" and args.tile_px == 0) else None
     kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in prof["kernels"].values()), 1e-9), 4)
                     for k, v in prof["kernels"].items() if v["count"]}
 
@@ -312,21 +326,22 @@ def run_ours(args, rank, world, local_rank):
                        "cuda_graph": not args.no_graph, "tile_px": args.tile_px,
                        "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"],
                        "directed_dense_pairs": n_dp, "correspondences": prob.n_corr, "n_gn": n_gn,
-                       "n_pcg": prm["n_pcg"], "precision": args.precision,
+                       "n_pcg": prm["n_pcg"], "precision": args.precision, "storage": args.storage,
                        "l2": "256 MB buffer written between timed steps (inputs < L2)",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": gpu_launches,
             "roofline": {"bound": "alu", "kernel": "k_dense", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                         "traffic": DENSE_TRAFFIC_BYTES, "avg_launch_ms": dense_ms,
+                         "traffic": traffic, "avg_launch_ms": dense_ms,
                          "flops_per_launch": flops, "flops_per_directed_px": DENSE_FLOPS_PER_PX,
                          "directed_px_per_launch": units,
                          "peak_source": "derived FP32 peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz"},
             "roofline_hbm_view": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                                  "frac": achieved_gbs / hbm_peak, "traffic": DENSE_TRAFFIC_BYTES,
+                                  "frac": achieved_gbs / hbm_peak, "traffic": traffic,
                                   "algorithmic_bytes_per_launch": alg_bytes,
-                                  "note": "48 B per directed source pixel; the 40 MB of frames stay in L2, "
-                                          "so DRAM traffic is the unique frame bytes (of measured)"},
+                                  "note": f"{dense_bytes_per_px(args.storage)} B per directed source pixel; "
+                                          "the frames stay in L2, so DRAM traffic is the unique frame bytes "
+                                          "(of measured)"},
             "kernel_time_share": kernel_share,
             "final_energy": st["energy"][-1], "initial_energy": st["energy"][0]}
     if clk:
@@ -368,10 +383,15 @@ def run_ours(args, rank, world, local_rank):
         line["plain_fp32"] = {"value": n_gn / (statistics.mean(tp) / 1000.0), "unit": UNIT,
                               "ms_per_step": statistics.mean(tp), "final_energy": stp["energy"][-1]}
 
+        # the same global solve on 16-bit frame storage
+        if args.storage == "fp32":
+            line["bf16_storage"] = storage_leg(bf, torch, dev, stream, prob, params, prof_params, "bf16")
+
         line["chunk_latency"] = chunk_latency(bf, torch, dev)
         import synth
         cprob = synth.cfg3()
         line["chunk_batch"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob)
+        line["chunk_batch_bf16"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob, storage="bf16")
         line["serving"] = serving_leg(bf, torch, dev, cprob, prob)
 
         v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=15.0)
@@ -381,19 +401,64 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
 
-def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None):
+def storage_leg(bf, torch, dev, stream, prob, params, prof_params, kind, steps=5):
+    """The timed global solve with frames held in 16-bit storage (same poses, pairs, parameters)."""
+    intr = prob.intr
+    n = prob.n_frames
+    ids = list(range(n))
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], stream=stream.cuda_stream,
+                     max_frames_hint=n, storage=STORAGE_CODES[kind](bf))
+    depth_d = torch.from_numpy(prob.depth).to(dev)
+    lum_d = torch.from_numpy(prob.lum).to(dev)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                  torch.from_numpy(prob.p_j).to(dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(p):
+        ctx.add_frames(0, depth_d, lum_d, init_pose=prob.init)
+        return ctx.solve_global(ids, p)
+
+    for _ in range(3):
+        step(params)
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step(params)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    step(prof_params)
+    dense = ctx.profile()["kernels"]["dense"]
+    ctx.set_profiling(False)
+    ctx.close()
+    n_gn = params.n_gn
+    dense_ms = dense["ms"] / max(dense["count"], 1)
+    units = 2 * st["n_dense_pairs"] * intr["W"] * intr["H"]
+    return {"storage": kind, "value": n_gn / (statistics.mean(ts) / 1000.0), "unit": UNIT,
+            "ms_per_step": statistics.mean(ts), "final_energy": st["energy"][-1],
+            "dense_avg_launch_ms": dense_ms,
+            "dense_algorithmic_GBps": dense_bytes_per_px(kind) * units / (dense_ms / 1000.0) / 1e9,
+            "frame_bytes": int(n * intr["W"] * intr["H"] * 16)}
+
+
+def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None, storage="fp32"):
     """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.
 
     batched: all chunks in one launch sequence (one problem per chunk), mixed precision, replayed
-    as a CUDA graph; plain: one FP32 solve per chunk, kernel by kernel, no graph.  Each step
-    re-runs frame preprocessing from device-resident raw frames.  Chunk-solve latency: call ->
-    poses on the host; in the batched mode every chunk completes with its batch."""
+    as a CUDA graph; plain: one FP32 solve per chunk, kernel by kernel, no graph (FP32 storage
+    only).  Each step re-runs frame preprocessing from device-resident raw frames.  Chunk-solve
+    latency: call -> poses on the host; in the batched mode every chunk completes with its batch."""
     import synth
     prob = prob or synth.cfg3(n_chunks=n_chunks)
     intr = prob.intr
     prm = prob.solve
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], stream=stream.cuda_stream,
-                     max_frames_hint=prob.n_frames)
+                     max_frames_hint=prob.n_frames, storage=STORAGE_CODES[storage](bf))
     depth_d = torch.from_numpy(prob.depth).to(dev)
     lum_d = torch.from_numpy(prob.lum).to(dev)
     ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
@@ -443,31 +508,35 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
     ctx.solve_local_batch(ids, lists, bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=0, **common))
     prof = ctx.profile()
     ctx.set_profiling(False)
-    run(plain, 1)
-    lat.clear()
-    tp, _ = run(plain, max(1, steps - 1))
-    lat.sort()
+    tp = None
+    if storage == "fp32":
+        run(plain, 1)
+        lat.clear()
+        tp, _ = run(plain, max(1, steps - 1))
+        lat.sort()
     HW = intr["W"] * intr["H"]
     n_dp = 2 * sum(s["n_dense_pairs"] for s in sb)
     dense = prof["kernels"]["dense"]
     dense_ms = dense["ms"] / max(dense["count"], 1)
-    alg_bytes = DENSE_BYTES_PER_PX * n_dp * HW
-    out = {"workload": prob.name, "chunks": len(lists), "frames": prob.n_frames, "pairs": int(len(prob.pairs)),
+    alg_bytes = dense_bytes_per_px(storage) * n_dp * HW
+    out = {"workload": prob.name, "storage": storage, "chunks": len(lists), "frames": prob.n_frames,
+           "pairs": int(len(prob.pairs)),
            "directed_dense_pairs": n_dp, "correspondences": prob.n_corr, "n_gn": prm["n_gn"], "n_pcg": prm["n_pcg"],
            "batched": {"value": gn_per_step / (statistics.mean(tb) / 1000.0), "unit": UNIT,
                        "ms_per_step": statistics.mean(tb),
                        "solves_per_s": len(lists) / (statistics.mean(tb) / 1000.0),
                        "chunk_latency_p50_ms": statistics.mean(tb), "chunk_latency_p99_ms": max(tb),
                        "precision": "mixed", "cuda_graph": True},
-           "plain_fp32": {"value": gn_per_step / (statistics.mean(tp) / 1000.0), "unit": UNIT,
-                          "ms_per_step": statistics.mean(tp),
-                          "solves_per_s": len(lists) / (statistics.mean(tp) / 1000.0),
-                          "chunk_latency_p50_ms": lat[len(lat) // 2],
-                          "chunk_latency_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
            "dense_kernel": {"avg_launch_ms": dense_ms, "launches": dense["count"],
                             "algorithmic_bytes_per_launch": alg_bytes,
                             "algorithmic_GBps": alg_bytes / (dense_ms / 1000.0) / 1e9,
-                            "unique_frame_bytes": int(prob.n_frames * HW * 32)}}
+                            "unique_frame_bytes": int(prob.n_frames * HW * (32 if storage == "fp32" else 16))}}
+    if tp:
+        out["plain_fp32"] = {"value": gn_per_step / (statistics.mean(tp) / 1000.0), "unit": UNIT,
+                             "ms_per_step": statistics.mean(tp),
+                             "solves_per_s": len(lists) / (statistics.mean(tp) / 1000.0),
+                             "chunk_latency_p50_ms": lat[len(lat) // 2],
+                             "chunk_latency_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
     ctx.close()
     return out
 
