@@ -181,3 +181,40 @@ def solve_frames(problem, frame_ids, init_poses, params: SolveParams, depth_min=
         frames = [frames_cache[f] for f in frame_ids]
     sp = sparse_pairs_for(problem, frame_ids)
     return gauss_newton(frames, problem.intr, init_poses, sp, params, direct=direct)
+
+
+@dataclasses.dataclass
+class PrunedResult:
+    result: GNResult           # the last solve
+    pruned: list               # (a, b) local pair indices removed, in order
+    invalid: list              # local frame indices (not the fixed frame 0) left without any pair
+    rounds: int                # solves run
+
+
+def gauss_newton_pruned(frames, intr, poses0, sparse_pairs, params: SolveParams, prune_rmax, max_rounds=8):
+    """Sec. 4.4.1 correspondence pruning around the solve.
+
+    After a solve, r_max is the largest sparse correspondence distance ||T_a p - T_b q||.  If it
+    exceeds prune_rmax, every correspondence of the pair (a, b) holding it is removed and the
+    problem is solved again; at most max_rounds re-solves.  Reading (the paper does not say from
+    where the next solve starts): each re-solve starts from the same initial poses, so the result
+    is the solve of the pruned problem.  The dense pair set follows the remaining sparse pairs.
+    A frame left with no pair is marked invalid (it keeps its initial pose: no constraint moves it).
+    """
+    sp = list(sparse_pairs)
+    pruned = []
+    rounds = 0
+    while True:
+        res = gauss_newton(frames, intr, poses0, sp, params)
+        rounds += 1
+        if not (res.r_max > prune_rmax) or rounds > max_rounds:
+            break
+        a, b = res.r_max_pair
+        pruned.append((a, b))
+        sp = [p for p in sp if not (p.a == a and p.b == b)]
+    linked = set()
+    for p in sp:
+        if p.p.shape[0] > 0:
+            linked.update((p.a, p.b))
+    invalid = [k for k in range(1, len(frames)) if k not in linked]
+    return PrunedResult(res, pruned, invalid, rounds)

@@ -504,6 +504,64 @@ def test_r_max_finds_the_worst_pair():
     assert abs(val - 0.5) < 1e-12
 
 
+
+# ------------------------------------------------------------------ Sec. 4.4.1 pruning
+def false_loop_problem(rng, n=4, bad=(1, 3), offset=(0.0, 0.25, 0.2)):
+    """Noise-free correspondences on every pair except `bad`, whose points in frame b are all
+    shifted by one rigid offset (a false loop closure consistent with a wrong transform)."""
+    gt, sp = sparse_problem(rng, n, sigma=0.0)
+    for k, p in enumerate(sp):
+        if (p.a, p.b) == bad:
+            sp[k] = SparsePair(p.a, p.b, p.p, p.q + np.array(offset))
+    return gt, sp
+
+
+def test_pruning_removes_the_false_pair_and_equals_the_clean_solve():
+    rng = np.random.default_rng(41)
+    gt, sp = false_loop_problem(rng)
+    X0 = perturbed(gt, rng, 0.02, 0.03)
+    prm = SolveParams(n_gn=6, n_pcg=30, dense_on=False)
+    first = solver.gauss_newton([None] * 4, None, X0, sp, prm)
+    assert first.r_max > 0.05 and first.r_max_pair == (1, 3)
+    out = solver.gauss_newton_pruned([None] * 4, None, X0, sp, prm, prune_rmax=0.05)
+    assert out.pruned == [(1, 3)] and out.rounds == 2 and out.invalid == []
+    clean = solver.gauss_newton([None] * 4, None, X0, [p for p in sp if (p.a, p.b) != (1, 3)], prm)
+    np.testing.assert_array_equal(out.result.poses, clean.poses)  # re-solve restarts from X0
+    assert out.result.r_max < 1e-6
+    P = out.result.poses
+    for k in range(4):  # noise-free remaining pairs: the ground truth up to the gauge (frame 0 fixed)
+        np.testing.assert_allclose(np.linalg.inv(P[0]) @ P[k], np.linalg.inv(gt[0]) @ gt[k], atol=1e-8)
+
+
+def test_pruning_marks_a_frame_without_pairs_invalid():
+    """Frame 3 is tied to the others only through the false pair: once it is pruned the frame
+    has no constraint left, is reported invalid and keeps its initial pose."""
+    rng = np.random.default_rng(42)
+    gt, sp = sparse_problem(rng, 4, sigma=0.0)
+    sp = [p for p in sp if p.b != 3 or p.a == 2]
+    k = next(i for i, p in enumerate(sp) if (p.a, p.b) == (2, 3))
+    q = sp[k].q.copy()
+    q[::2] += np.array([0.0, 0.3, 0.0])  # half the matches wrong: no rigid motion explains the pair
+    sp[k] = SparsePair(2, 3, sp[k].p, q)
+    X0 = perturbed(gt, rng, 0.02, 0.03)
+    prm = SolveParams(n_gn=6, n_pcg=30, dense_on=False)
+    out = solver.gauss_newton_pruned([None] * 4, None, X0, sp, prm, prune_rmax=0.05)
+    assert out.pruned == [(2, 3)] and out.invalid == [3]
+    np.testing.assert_array_equal(out.result.poses[3], X0[3])
+
+
+def test_no_pruning_below_the_threshold():
+    rng = np.random.default_rng(43)
+    gt, sp = false_loop_problem(rng)
+    X0 = perturbed(gt, rng, 0.02, 0.03)
+    prm = SolveParams(n_gn=4, n_pcg=20, dense_on=False)
+    plain = solver.gauss_newton([None] * 4, None, X0, sp, prm)
+    out = solver.gauss_newton_pruned([None] * 4, None, X0, sp, prm, prune_rmax=plain.r_max + 1.0)
+    assert out.pruned == [] and out.rounds == 1
+    np.testing.assert_array_equal(out.result.poses, plain.poses)
+    capped = solver.gauss_newton_pruned([None] * 4, None, X0, sp, prm, prune_rmax=1e-300, max_rounds=2)
+    assert len(capped.pruned) == 2 and capped.rounds == 3
+
 # ------------------------------------------------------------------ 16-bit frame storage
 def _fp16_grid_values(rng, n):
     """FP64 values around FP16 numbers: exact grid points, midpoints (ties), near-midpoints,
