@@ -110,12 +110,21 @@ typedef struct {
   int use_graph;            /* replay the Gauss-Newton loop as a captured CUDA graph   */
   int tile_px;              /* source pixels per dense work item, 0 = autotuned        */
   int pcg_variant;          /* BF_PCG_*: which PCG kernel runs (results agree to rounding) */
+  /* Sec. 4.4.1 correspondence pruning.  prune_rmax > 0: after a solve whose r_max (largest
+   * ||T_i p - T_j q|| over its sparse correspondences) exceeds prune_rmax, every
+   * correspondence of the pair holding it is removed from the context and the problem is
+   * solved again from the same initial poses; at most prune_rounds re-solves.  Frames left
+   * without any pair are reported invalid (they keep their initial pose).  In a batch only the
+   * chunks that need it are re-solved.  0 = off (the paper uses 0.05 m; 0.16 m for Kinect). */
+  double prune_rmax;
+  int prune_rounds;
 } bf_solve_params;
 
 /* PCG kernels: AUTO picks CLUSTER for one large problem, else one CTA per problem. */
 enum { BF_PCG_AUTO = 0, BF_PCG_CTA = 1, BF_PCG_GRID = 2, BF_PCG_CLUSTER = 3 };
 
 #define BF_MAX_GN 64
+#define BF_MAX_PRUNE 32
 
 typedef struct {
   int n_gn_done;
@@ -129,7 +138,12 @@ typedef struct {
   int n_frames, n_pairs, n_dense_pairs;
   long long n_corr;
   int flags;                        /* BF_FLAG_*                                         */
-  double ms;                        /* wall time of the solve on the host               */
+  double ms;                        /* wall time of the solve on the host (all rounds)  */
+  int solves;                       /* solves run (1 + re-solves after pruning)         */
+  int n_pruned;                     /* pairs removed by pruning, in order ...           */
+  int pruned_pairs[2 * BF_MAX_PRUNE]; /* ... their frame ids (first BF_MAX_PRUNE pairs)  */
+  int n_invalid;                    /* frames other than the first left without a pair  */
+  int invalid_frames[BF_MAX_PRUNE]; /* their ids (first BF_MAX_PRUNE)                   */
 } bf_solve_stats;
 
 /* Fill defaults: 640x480 Kinect-like intrinsics scaled to 80x60, depth 0.1..10 m, FP32. */
@@ -303,7 +317,8 @@ typedef struct {
   int chunk_id;             /* local requests: chunk id the local poses are stored under   */
   const int *frame_ids;     /* host, copied by bf_submit; [0] is the fixed frame           */
   int n;
-  bf_solve_params params;   /* use_graph is ignored (batches differ from one another)      */
+  bf_solve_params params;   /* use_graph is ignored (batches differ from one another);
+                               prune_rmax must be 0 (pruning is in the synchronous calls)  */
 } bf_request;
 /* Start n_slots (1..8) worker slots; max_batch local requests per batch; max_queue pending. */
 bf_status bf_serve_start(bf_ctx *ctx, int n_slots, int max_batch, int max_queue);

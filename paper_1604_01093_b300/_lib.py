@@ -22,6 +22,7 @@ BF_PREC_MIXED, BF_PREC_FP32 = 0, 1
 BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
 BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER = 0, 1, 2, 3
 BF_MAX_GN = 64
+BF_MAX_PRUNE = 32
 BF_NPROF = 10
 KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack"]
 
@@ -43,7 +44,8 @@ class SolveParams(ctypes.Structure):
                 ("w_geo", ctypes.c_double), ("dense_ramp", ctypes.c_int), ("tau_dist", ctypes.c_double),
                 ("tau_normal", ctypes.c_double), ("max_angle_deg", ctypes.c_double), ("precond", ctypes.c_int),
                 ("dense_on", ctypes.c_int), ("warm_start", ctypes.c_int), ("precision", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int), ("pcg_variant", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int), ("pcg_variant", ctypes.c_int),
+                ("prune_rmax", ctypes.c_double), ("prune_rounds", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -53,15 +55,23 @@ class SolveStats(ctypes.Structure):
                 ("n_dense_valid", ctypes.c_longlong * (BF_MAX_GN + 1)),
                 ("r_max", ctypes.c_double), ("r_max_pair", ctypes.c_int * 2),
                 ("n_frames", ctypes.c_int), ("n_pairs", ctypes.c_int), ("n_dense_pairs", ctypes.c_int),
-                ("n_corr", ctypes.c_longlong), ("flags", ctypes.c_int), ("ms", ctypes.c_double)]
+                ("n_corr", ctypes.c_longlong), ("flags", ctypes.c_int), ("ms", ctypes.c_double),
+                ("solves", ctypes.c_int), ("n_pruned", ctypes.c_int),
+                ("pruned_pairs", ctypes.c_int * (2 * BF_MAX_PRUNE)), ("n_invalid", ctypes.c_int),
+                ("invalid_frames", ctypes.c_int * BF_MAX_PRUNE)]
 
     def to_dict(self):
         k = self.n_gn_done + 1
+        npr = min(self.n_pruned, BF_MAX_PRUNE)
         return dict(n_gn=self.n_gn_done, energy=list(self.energy[:k]), e_sparse=list(self.e_sparse[:k]),
                     e_photo=list(self.e_photo[:k]), e_geo=list(self.e_geo[:k]),
                     n_dense=list(self.n_dense_valid[:k]), r_max=self.r_max, r_max_pair=tuple(self.r_max_pair),
                     n_frames=self.n_frames, n_pairs=self.n_pairs, n_dense_pairs=self.n_dense_pairs,
-                    n_corr=self.n_corr, flags=self.flags, ms=self.ms)
+                    n_corr=self.n_corr, flags=self.flags, ms=self.ms, solves=self.solves,
+                    n_pruned=self.n_pruned,
+                    pruned=[(self.pruned_pairs[2 * i], self.pruned_pairs[2 * i + 1]) for i in range(npr)],
+                    n_invalid=self.n_invalid,
+                    invalid=list(self.invalid_frames[:min(self.n_invalid, BF_MAX_PRUNE)]))
 
 
 BF_REQ_LOCAL, BF_REQ_GLOBAL = 0, 1

@@ -328,6 +328,8 @@ extern "C" void bf_default_params(bf_solve_params *p) {
   p->precision = BF_PREC_MIXED;
   p->use_graph = 0;
   p->tile_px = 0;
+  p->prune_rmax = 0.0;
+  p->prune_rounds = 8;
 }
 
 extern "C" const char *bf_status_string(bf_status s) {
@@ -1248,6 +1250,8 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
   if (p->tile_px < 0) return fail(c, BF_ERR_INVALID_ARG, "tile_px must be >= 0");
   if (p->pcg_variant < BF_PCG_AUTO || p->pcg_variant > BF_PCG_CLUSTER)
     return fail(c, BF_ERR_INVALID_ARG, "unknown pcg_variant");
+  if (!(p->prune_rmax >= 0) || !std::isfinite(p->prune_rmax) || p->prune_rounds < 0 || p->prune_rounds > 100000)
+    return fail(c, BF_ERR_INVALID_ARG, "prune_rmax must be finite and >= 0, prune_rounds >= 0");
   return BF_OK;
 }
 
@@ -1375,13 +1379,86 @@ bf_status finish_solve(bf_ctx *c, SolveJob &J, std::vector<std::vector<Pose12>> 
   return BF_OK;
 }
 
-bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm,
-                         std::vector<std::vector<Pose12>> &out, bf_solve_stats *stats) {
+bf_status solve_once(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm,
+                     std::vector<std::vector<Pose12>> &out, bf_solve_stats *stats) {
   SolveJob J;
   bf_status s = enqueue_solve(c, probs, prm, J);
   if (s) return s;
   CK(cudaStreamSynchronize(c->ex->st), "solve");
   return finish_solve(c, J, out, stats);
+}
+
+// Sec. 4.4.1 pruning around the solve: problems whose r_max exceeds prm.prune_rmax lose every
+// correspondence of the pair holding it (removed from the context) and are solved again from
+// their initial poses, the others keep their result; at most prm.prune_rounds re-solves.
+// Afterwards every frame of a problem (but its first) that no remaining pair touches is
+// reported invalid.  Without pruning this is one solve.
+bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm,
+                         std::vector<std::vector<Pose12>> &out, bf_solve_stats *stats) {
+  if (!(prm.prune_rmax > 0)) {
+    bf_status s = solve_once(c, probs, prm, out, stats);
+    if (s == BF_OK && stats)
+      for (size_t k = 0; k < probs.size(); ++k) stats[k].solves = 1;
+    return s;
+  }
+  const size_t n = probs.size();
+  out.assign(n, {});
+  std::vector<bf_solve_stats> st(n);
+  std::vector<std::vector<std::pair<int, int>>> pruned(n);
+  std::vector<int> solves(n, 0);
+  std::vector<size_t> active(n);
+  for (size_t k = 0; k < n; ++k) active[k] = k;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (int round = 0; !active.empty(); ++round) {
+    std::vector<Problem> sub;
+    for (size_t k : active) sub.push_back(probs[k]);
+    std::vector<std::vector<Pose12>> sub_out;
+    std::vector<bf_solve_stats> sub_st(sub.size());
+    bf_status s = solve_once(c, sub, prm, sub_out, sub_st.data());
+    if (s) return s;
+    std::vector<size_t> next;
+    for (size_t q = 0; q < active.size(); ++q) {
+      const size_t k = active[q];
+      out[k] = sub_out[q];
+      st[k] = sub_st[q];
+      ++solves[k];
+      const bf_solve_stats &S = sub_st[q];
+      if (S.r_max > prm.prune_rmax && round < prm.prune_rounds && S.r_max_pair[0] >= 0) {
+        c->corr.erase(pair_key(S.r_max_pair[0], S.r_max_pair[1]));
+        pruned[k].push_back({S.r_max_pair[0], S.r_max_pair[1]});
+        next.push_back(k);
+      }
+    }
+    active.swap(next);
+  }
+  const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (size_t k = 0; k < n; ++k) {
+    bf_solve_stats &S = st[k];
+    S.ms = ms;
+    S.solves = solves[k];
+    S.n_pruned = (int)pruned[k].size();
+    for (int a = 0; a < S.n_pruned && a < BF_MAX_PRUNE; ++a) {
+      S.pruned_pairs[2 * a] = pruned[k][a].first;
+      S.pruned_pairs[2 * a + 1] = pruned[k][a].second;
+    }
+    // frames (but the first) without any remaining pair inside the problem
+    const std::vector<int> &ids = probs[k].ids;
+    S.n_invalid = 0;
+    for (size_t a = 1; a < ids.size(); ++a) {
+      bool linked = false;
+      for (size_t b = 0; b < ids.size() && !linked; ++b) {
+        if (b == a) continue;
+        auto it = c->corr.find(pair_key(ids[a], ids[b]));
+        linked = it != c->corr.end() && !it->second.empty();
+      }
+      if (!linked) {
+        if (S.n_invalid < BF_MAX_PRUNE) S.invalid_frames[S.n_invalid] = ids[a];
+        ++S.n_invalid;
+      }
+    }
+    if (stats) stats[k] = S;
+  }
+  return BF_OK;
 }
 
 Pose12 world_of(bf_ctx *c, int id) {
@@ -1867,6 +1944,7 @@ extern "C" bf_status bf_submit(bf_ctx *c, const bf_request *req, uint64_t *ticke
   if (!c->srv) return BF_ERR_INVALID_ARG;
   if ((req->kind != BF_REQ_LOCAL && req->kind != BF_REQ_GLOBAL) || !req->frame_ids || req->n < 1)
     return BF_ERR_INVALID_ARG;
+  if (req->params.prune_rmax != 0.0) return BF_ERR_INVALID_ARG;  // pruning re-solves: synchronous API only
   Server &S = *c->srv;
   std::lock_guard<std::mutex> q(S.qm);
   if ((int)S.pending.size() >= S.max_queue) return BF_ERR_BUSY;
