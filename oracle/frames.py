@@ -108,13 +108,17 @@ class Frame:
         self.D = np.where(self.valid, D, 0.0)
         self.N, self.nvalid = normals(self.D, self.valid, self.fx, self.fy, self.cx, self.cy)
         self.I, self.Ix, self.Iy = intensity_gradient(lum)
+        # the intensity itself, for the dense verification's photoconsistency test (Sec. 4.1.1)
+        self.C = np.asarray(lum, dtype=np.float64)
         self.storage = storage
         if storage not in (None, "fp32"):
             self.N = round_to_storage(self.N, storage)
             self.I, self.Ix, self.Iy = (round_to_storage(v, storage) for v in (self.I, self.Ix, self.Iy))
+            self.C = round_to_storage(self.C, storage)
         # FP32 copies for the association decisions (see association.py)
         self.D32 = self.D.astype(np.float32)
         self.N32 = self.N.astype(np.float32)
+        self.C32 = self.C.astype(np.float32)
 
 
 def preprocess(problem_depth, problem_lum, intr, depth_min=0.1, depth_max=10.0, storage=None):

@@ -16,7 +16,7 @@ from scipy.spatial.transform import Rotation
 
 import synth
 from synth import scene as sc
-from oracle import association, frames, lie, residuals, solver, system
+from oracle import association, frames, lie, residuals, solver, system, verification
 from oracle.system import SolveParams, SparsePair
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
@@ -561,6 +561,96 @@ def test_no_pruning_below_the_threshold():
     np.testing.assert_array_equal(out.result.poses, plain.poses)
     capped = solver.gauss_newton_pruned([None] * 4, None, X0, sp, prm, prune_rmax=1e-300, max_rounds=2)
     assert len(capped.pruned) == 2 and capped.rounds == 3
+
+
+# ------------------------------------------------------------- Sec. 4.1.1 dense verification
+def test_verification_of_a_frame_with_itself(room_frames):
+    """Identity transform, the same frame on both sides: every pixel with valid depth and normal
+    re-projects onto itself with distance exactly 0, in both directions."""
+    intr, poses, fr, depth, lum = room_frames
+    chk = verification.verify_pair(fr[0], fr[0], np.eye(4), intr)
+    n_valid = int((fr[0].valid & fr[0].nvalid).sum())
+    assert chk.n_ij == chk.n_ji == n_valid and chk.e_ij == 0.0 and chk.e_ji == 0.0
+    assert verification.pair_valid(chk, intr)
+
+
+def test_verification_gates(room_frames):
+    """Each gate alone rejects everything when violated by construction."""
+    intr, poses, fr, depth, lum = room_frames
+    n_valid = int((fr[0].valid & fr[0].nvalid).sum())
+    brighter = frames.Frame(depth[0], lum[0] + 0.2, intr)  # tau_c = 0.1
+    assert verification.verify_pair(fr[0], brighter, np.eye(4), intr).n_ij == 0
+    slightly = frames.Frame(depth[0], lum[0] + 0.05, intr)
+    assert verification.verify_pair(fr[0], slightly, np.eye(4), intr).n_ij == n_valid
+    deeper = frames.Frame(depth[0] + np.float32(0.2), lum[0], intr)  # 0.2 m along z: > tau_d = 0.15
+    chk = verification.verify_pair(fr[0], deeper, np.eye(4), intr)
+    assert chk.n_ij == 0 and chk.n_ji == 0
+    assert verification.verify_pair(fr[0], fr[0], np.eye(4), intr, tau_n=1.01).n_ij == 0
+    assert not verification.pair_valid(chk, intr)
+
+
+def test_verification_matches_a_per_pixel_loop():
+    """Brute force on a small frame: a pure-Python loop over pixels (FP32 decisions written out
+    per pixel, FP64 distances) gives the same count and error sum as the vectorised oracle."""
+    rng = np.random.default_rng(51)
+    intr = sc.intrinsics(32, 24)
+    start = lie.to44(sc.yaw_pitch_roll(0.2, 0.05, 0.0), np.array([0.0, 0.0, -0.5]))
+    room = sc.box_room(rng, (6.0, 2.8, 6.0), (20, 30), keep_clear=start[None, :3, 3], clear_radius=1.0)
+    poses = sc.smooth_walk(rng, 2, start, scene=room)
+    depth, lum = render_pair(rng, intr, room, poses)
+    fi, fj = (frames.Frame(depth[k], lum[k], intr) for k in range(2))
+    T = np.linalg.inv(poses[1]) @ poses[0]
+    R32, t32 = T[:3, :3].astype(np.float32), T[:3, 3].astype(np.float32)
+    n, e, _ = verification.reproject(fi, fj, (R32, t32), intr)
+    kx, ky = association.ray_tables(intr)
+    f = np.float32
+    W, H = intr["W"], intr["H"]
+    cnt, tot = 0, 0.0
+    for y in range(H):
+        for x in range(W):
+            if not (fi.valid[y, x] and fi.nvalid[y, x]):
+                continue
+            z = fi.D32[y, x]
+            d = [kx[x] * z, ky[y] * z, z]
+            Y = [f(f(f(R32[a, 0] * d[0]) + f(R32[a, 1] * d[1])) + f(R32[a, 2] * d[2])) + t32[a] for a in range(3)]
+            Y = [f(v) for v in Y]
+            if not Y[2] > 0:
+                continue
+            iz = f(f(1) / Y[2])
+            ux = f(f(f(intr["fx"]) * f(Y[0] * iz)) + f(intr["cx"]))
+            uy = f(f(f(intr["fy"]) * f(Y[1] * iz)) + f(intr["cy"]))
+            tx, ty = int(np.floor(f(ux + f(0.5)))), int(np.floor(f(uy + f(0.5))))
+            if not (0 <= tx < W and 0 <= ty < H) or not (fj.valid[ty, tx] and fj.nvalid[ty, tx]):
+                continue
+            q = [f(kx[tx] * fj.D32[ty, tx]), f(ky[ty] * fj.D32[ty, tx]), fj.D32[ty, tx]]
+            ex = [f(Y[a] - q[a]) for a in range(3)]
+            if not f(f(f(ex[0] * ex[0]) + f(ex[1] * ex[1])) + f(ex[2] * ex[2])) < f(0.15 * 0.15):
+                continue
+            m = [f(f(f(R32[a, 0] * fi.N32[y, x, 0]) + f(R32[a, 1] * fi.N32[y, x, 1])) + f(R32[a, 2] * fi.N32[y, x, 2]))
+                 for a in range(3)]
+            if not f(f(f(m[0] * fj.N32[ty, tx, 0]) + f(m[1] * fj.N32[ty, tx, 1])) + f(m[2] * fj.N32[ty, tx, 2])) > f(0.9):
+                continue
+            if not abs(f(fi.C32[y, x] - fj.C32[ty, tx])) < f(0.1):
+                continue
+            cnt += 1
+            tot += math.sqrt(sum((float(Y[a]) - float(q[a])) ** 2 for a in range(3)))
+    assert cnt > 100 and n == cnt
+    assert abs(e - tot) <= 1e-12 * tot
+
+
+def test_chunk_validation_flags_a_misaligned_frame(room_frames):
+    """At the ground-truth poses every pair is consistent (mean error below 0.05 m); moving one
+    frame's pose by 0.2 m makes its pairs fail and the chunk invalid.  (The tau_d gate keeps only
+    correspondences closer than 0.15 m, so the mean error of a misaligned pair grows slowly: at
+    0.1 m it is still below the 0.05 m threshold.)"""
+    intr, poses, fr, depth, lum = room_frames
+    local = np.einsum("ab,kbc->kac", np.linalg.inv(poses[0]), poses)
+    ok, worst, arg, checks = verification.validate_chunk(fr, local, intr)
+    assert ok and worst < 0.03  # nearest-pixel sampling at 80x60 leaves about 2 cm
+    bad = local.copy()
+    bad[2][:3, 3] += np.array([0.2, 0.0, 0.0])
+    ok2, worst2, arg2, _ = verification.validate_chunk(fr, bad, intr)
+    assert not ok2 and worst2 > 0.05 and 2 in arg2
 
 # ------------------------------------------------------------------ 16-bit frame storage
 def _fp16_grid_values(rng, n):
