@@ -262,7 +262,7 @@ bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const doub
  */
 enum {
   BF_K_PREPROCESS = 0, BF_K_XFORM, BF_K_DENSE, BF_K_SPARSE, BF_K_MERGE, BF_K_ASSEMBLE, BF_K_PCG, BF_K_UPDATE,
-  BF_K_ENERGY, BF_K_PACK, BF_NPROF
+  BF_K_ENERGY, BF_K_PACK, BF_K_VERIFY, BF_NPROF
 };
 typedef struct {
   long long launches;          /* kernels launched since the last reset (always counted)  */
@@ -331,6 +331,45 @@ bf_status bf_submit(bf_ctx *ctx, const bf_request *req, uint64_t *ticket);
  * BF_ERR_TIMEOUT if it has not completed (the ticket stays valid), BF_ERR_NOT_FOUND for an
  * unknown or already collected ticket.  stats: nullable. */
 bf_status bf_wait(bf_ctx *ctx, uint64_t ticket, int timeout_ms, bf_solve_stats *stats);
+
+/*
+ * Dense verification of frame pairs (Sec. 4.1.1) and chunk validation (Sec. 4.2).
+ * Both directions of a pair are checked: every pixel with valid depth and normal is projected
+ * into the other frame, matched to the nearest pixel, and kept when
+ *   ||T p - q|| < tau_dist,  (R n_src) . n_dst > tau_normal,  |C_src - C_dst| < tau_color
+ * (C = the luminance given to bf_add_frames).  One CTA per pair.
+ */
+typedef struct {
+  double tau_dist;        /* metres (default 0.15)                                      */
+  double tau_normal;      /* cosine (default 0.9)                                       */
+  double tau_color;       /* intensity difference (default 0.1)                         */
+  double max_err;         /* pair valid iff mean re-projection error <= max_err (0.075 m) */
+  double min_valid_frac;  /* ... and n_ij + n_ji >= min_valid_frac * W * H (0.02)        */
+} bf_verify_params;
+void bf_default_verify_params(bf_verify_params *p);
+
+typedef struct {
+  int n_ij, n_ji;         /* kept correspondences per direction                         */
+  double err_ij, err_ji;  /* sums of their distances ||T p - q|| (metres)               */
+  double mean_err;        /* (err_ij + err_ji) / (n_ij + n_ji), +inf if none            */
+  int valid;              /* the Sec. 4.1.1 decision with the given thresholds          */
+} bf_verify_result;
+
+/*
+ * Verify n frame pairs.  frame_pairs: 2n frame ids (i, j); rel: n x 16 doubles, row-major
+ * T_ij mapping camera-i points into camera j (e.g. from a key-point filter's Kabsch fit);
+ * T_ji is its inverse.  out: n results (host).  Synchronous.
+ */
+bf_status bf_verify_pairs(bf_ctx *ctx, int n, const int *frame_pairs, const double *rel,
+                          const bf_verify_params *params, bf_verify_result *out);
+
+/*
+ * Chunk validation (Sec. 4.2): verify every pair of a solved chunk's frames at its local poses;
+ * *valid = 0 if a pair with kept correspondences has a mean error above max_err (0.05 m).
+ * worst_err / worst_pair (2 frame ids): nullable.  BF_ERR_NOT_FOUND for an unsolved chunk.
+ */
+bf_status bf_validate_chunk(bf_ctx *ctx, int chunk_id, double max_err, const bf_verify_params *params,
+                            int *valid, double *worst_err, int *worst_pair);
 
 /* Device bytes currently held by the context. */
 size_t bf_device_bytes(bf_ctx *ctx);

@@ -23,8 +23,9 @@ BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
 BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER = 0, 1, 2, 3
 BF_MAX_GN = 64
 BF_MAX_PRUNE = 32
-BF_NPROF = 10
-KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack"]
+BF_NPROF = 11
+KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack",
+                  "verify"]
 
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_OUT_OF_MEMORY", 3: "BF_ERR_CUDA",
           4: "BF_ERR_NOT_FOUND", 5: "BF_ERR_SINGULAR", 6: "BF_ERR_TIMEOUT", 7: "BF_ERR_BUSY"}
@@ -72,6 +73,20 @@ class SolveStats(ctypes.Structure):
                     pruned=[(self.pruned_pairs[2 * i], self.pruned_pairs[2 * i + 1]) for i in range(npr)],
                     n_invalid=self.n_invalid,
                     invalid=list(self.invalid_frames[:min(self.n_invalid, BF_MAX_PRUNE)]))
+
+
+class VerifyParams(ctypes.Structure):
+    _fields_ = [("tau_dist", ctypes.c_double), ("tau_normal", ctypes.c_double), ("tau_color", ctypes.c_double),
+                ("max_err", ctypes.c_double), ("min_valid_frac", ctypes.c_double)]
+
+
+class VerifyResult(ctypes.Structure):
+    _fields_ = [("n_ij", ctypes.c_int), ("n_ji", ctypes.c_int), ("err_ij", ctypes.c_double),
+                ("err_ji", ctypes.c_double), ("mean_err", ctypes.c_double), ("valid", ctypes.c_int)]
+
+    def to_dict(self):
+        return dict(n_ij=self.n_ij, n_ji=self.n_ji, err_ij=self.err_ij, err_ji=self.err_ji, mean_err=self.mean_err,
+                    valid=bool(self.valid))
 
 
 BF_REQ_LOCAL, BF_REQ_GLOBAL = 0, 1
@@ -132,6 +147,9 @@ def lib():
         "bf_wait": (I, [P, ctypes.c_uint64, I, P]),
         "bf_dense_pair_noalloc": (I, [I, I, D, D, D, D, ctypes.c_float, ctypes.c_float, P, P, P, P, P, P,
                                       ctypes.POINTER(SolveParams), P, P]),
+        "bf_default_verify_params": (None, [ctypes.POINTER(VerifyParams)]),
+        "bf_verify_pairs": (I, [P, I, P, P, ctypes.POINTER(VerifyParams), P]),
+        "bf_validate_chunk": (I, [P, I, D, ctypes.POINTER(VerifyParams), P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -147,7 +165,8 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_remove_pair", "bf_set_profiling", "bf_get_profile", "bf_reset_profile",
            "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
            "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes",
-           "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait"]
+           "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait",
+           "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk"]
 
 
 class BFError(RuntimeError):
@@ -182,6 +201,16 @@ def default_params(**kw) -> SolveParams:
     for k, v in kw.items():
         if not hasattr(p, k):
             raise AttributeError(f"unknown solve parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def verify_params(**kw) -> VerifyParams:
+    p = VerifyParams()
+    lib().bf_default_verify_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"unknown verification parameter {k}")
         setattr(p, k, v)
     return p
 
@@ -299,6 +328,27 @@ class Context:
         out = np.zeros((len(ids), 4, 4), dtype=np.float64)
         self._check(lib().bf_get_poses(self.h, _ptr(ids), len(ids), _ptr(out)))
         return out
+
+    # ---------------------------------------------------- dense verification
+    def verify_pairs(self, frame_pairs, rel, **kw):
+        """Sec. 4.1.1 two-sided check of frame pairs (k, 2) under relative transforms (k, 4, 4)."""
+        vp = verify_params(**kw)
+        fp = np.ascontiguousarray(frame_pairs, dtype=np.int32).reshape(-1, 2)
+        T = np.ascontiguousarray(rel, dtype=np.float64).reshape(len(fp), 16)
+        out = (VerifyResult * max(len(fp), 1))()
+        self._check(lib().bf_verify_pairs(self.h, len(fp), _ptr(fp), _ptr(T), ctypes.byref(vp),
+                                          ctypes.cast(out, ctypes.c_void_p)))
+        return [out[k].to_dict() for k in range(len(fp))]
+
+    def validate_chunk(self, chunk_id, max_err=0.05, **kw):
+        """Sec. 4.2 chunk validation at the chunk's solved local poses."""
+        vp = verify_params(**kw)
+        valid = ctypes.c_int(0)
+        worst = ctypes.c_double(0.0)
+        pair = (ctypes.c_int * 2)()
+        self._check(lib().bf_validate_chunk(self.h, chunk_id, max_err, ctypes.byref(vp), ctypes.byref(valid),
+                                            ctypes.byref(worst), ctypes.cast(pair, ctypes.c_void_p)))
+        return dict(valid=bool(valid.value), worst_err=worst.value, worst_pair=(pair[0], pair[1]))
 
     # ------------------------------------------------------------ inspection
     def build_system(self, frame_ids, poses, params=None, **kw):

@@ -12,7 +12,8 @@ LIB = PKG / "libbf.so"
 BUILD = PKG / "_build"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", str(INCLUDE), "-I", str(CSRC)]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", str(INCLUDE),
+         "-I", str(CSRC)]
 
 
 def _nvcc():

@@ -120,6 +120,10 @@ struct bf_ctx {
   // frame store
   int cap = 0;
   float4 *A = nullptr, *B = nullptr;
+  unsigned short *C16 = nullptr;  // 16-bit storage: intensity plane (dense verification)
+  VerifyPair *vrec = nullptr;     // dense verification: pair records and results
+  double *vout = nullptr;
+  int vcap = 0;
   float *kx = nullptr, *ky = nullptr;
   std::unordered_map<int, FrameInfo> frames;
   std::vector<int> free_slots;
@@ -230,6 +234,7 @@ static FrameStore frame_store(const bf_ctx *c) {
   fs.A = f32 ? c->A : nullptr;
   fs.B = f32 ? c->B : nullptr;
   fs.P16 = f32 ? nullptr : (const uint4 *)c->A;  // 16-bit storage keeps its records in the A buffer
+  fs.C16 = f32 ? nullptr : c->C16;
   fs.kx = c->kx;
   fs.ky = c->ky;
   return fs;
@@ -243,25 +248,30 @@ static bf_status ensure_frames(bf_ctx *c, int n) {
   const size_t HW = (size_t)c->cfg.width * c->cfg.height;
   const bool two = c->cfg.storage == BF_STORE_FP32;
   float4 *nA = nullptr, *nB = nullptr;
+  unsigned short *nC = nullptr;
   bf_status s = dalloc(c, (void **)&nA, ncap * HW * sizeof(float4), "frame store");
   if (s) return s;
-  if (two) {
-    s = dalloc(c, (void **)&nB, ncap * HW * sizeof(float4), "frame store");
-    if (s) {
-      dfree(c, nA, ncap * HW * sizeof(float4));
-      return s;
-    }
+  s = two ? dalloc(c, (void **)&nB, ncap * HW * sizeof(float4), "frame store")
+          : dalloc(c, (void **)&nC, ncap * HW * sizeof(unsigned short), "frame store");
+  if (s) {
+    dfree(c, nA, ncap * HW * sizeof(float4));
+    return s;
   }
   if (c->cap) {
     CK(cudaMemcpyAsync(nA, c->A, c->cap * HW * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow frames");
     if (two)
       CK(cudaMemcpyAsync(nB, c->B, c->cap * HW * sizeof(float4), cudaMemcpyDeviceToDevice, c->st), "grow frames");
+    else
+      CK(cudaMemcpyAsync(nC, c->C16, c->cap * HW * sizeof(unsigned short), cudaMemcpyDeviceToDevice, c->st),
+         "grow frames");
     CK(cudaStreamSynchronize(c->st), "grow frames");
   }
   dfree(c, c->A, c->cap * HW * sizeof(float4));
   if (two) dfree(c, c->B, c->cap * HW * sizeof(float4));
+  else dfree(c, c->C16, c->cap * HW * sizeof(unsigned short));
   c->A = nA;
   c->B = nB;
+  c->C16 = nC;
   c->cap = ncap;
   return BF_OK;
 }
@@ -435,6 +445,9 @@ extern "C" bf_status bf_destroy(bf_ctx *c) {
   if (c->st) cudaStreamSynchronize(c->st);
   cudaFree(c->A);
   cudaFree(c->B);
+  cudaFree(c->C16);
+  cudaFree(c->vrec);
+  cudaFree(c->vout);
   cudaFree(c->kx);
   cudaFree(c->ky);
   cudaFree(c->stage);
@@ -520,7 +533,7 @@ extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *
     lptr = c->stage + n * HW;
   }
   run_k(c, BF_K_PREPROCESS, [&] {
-    return launch_preprocess(dptr, lptr, n, c->slot_dev, frame_store(c), c->A, c->B, (uint4 *)c->A,
+    return launch_preprocess(dptr, lptr, n, c->slot_dev, frame_store(c), c->A, c->B, (uint4 *)c->A, c->C16,
                              c->cfg.depth_min, c->cfg.depth_max, c->st);
   });
   CK(cudaGetLastError(), "preprocess launch");
@@ -1616,6 +1629,164 @@ extern "C" bf_status bf_get_poses(bf_ctx *c, const int *frame_ids, int n, double
   for (int k = 0; k < n; ++k) {
     if (!c->frames.count(frame_ids[k])) return fail(c, BF_ERR_NOT_FOUND, "bf_get_poses: unknown frame id");
     to16(world_of(c, frame_ids[k]), out + 16 * k);
+  }
+  return BF_OK;
+}
+
+
+// ----------------------------------------------------------------- dense verification
+extern "C" void bf_default_verify_params(bf_verify_params *p) {
+  if (!p) return;
+  p->tau_dist = 0.15;
+  p->tau_normal = 0.9;
+  p->tau_color = 0.1;
+  p->max_err = 0.075;
+  p->min_valid_frac = 0.02;
+}
+
+namespace {
+
+// fl32 of a relative transform (R row-major, t) and of its inverse (R^T, -R^T t with the sums
+// taken left to right in FP64, then rounded)
+void verify_record(const double *R, const double *t, VerifyPair &v) {
+  for (int k = 0; k < 9; ++k) v.M[0][k] = (float)R[k];
+  for (int a = 0; a < 3; ++a) v.M[0][9 + a] = (float)t[a];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) v.M[1][3 * a + b] = (float)R[3 * b + a];
+  for (int a = 0; a < 3; ++a) {
+    const double s = (R[a] * t[0] + R[3 + a] * t[1]) + R[6 + a] * t[2];
+    v.M[1][9 + a] = (float)(-s);
+  }
+}
+
+bool check_verify_params(const bf_verify_params *vp) {
+  return vp && vp->tau_dist > 0 && std::isfinite(vp->tau_dist) && std::isfinite(vp->tau_normal) &&
+         vp->tau_color > 0 && std::isfinite(vp->tau_color) && std::isfinite(vp->max_err) &&
+         std::isfinite(vp->min_valid_frac);
+}
+
+// Run the verification kernel over recs; res gets {n_ij, n_ji, e_ij, e_ji} per pair.
+bf_status run_verify(bf_ctx *c, const std::vector<VerifyPair> &recs, const bf_verify_params &vp,
+                     std::vector<double> &res) {
+  const int n = (int)recs.size();
+  res.assign(4 * (size_t)n, 0.0);
+  if (n == 0) return BF_OK;
+  if (n > c->vcap) {
+    const int nc = std::max(n, 2 * c->vcap);
+    CK(cudaStreamSynchronize(c->ex->st), "verify buffers");
+    dfree(c, c->vrec, (size_t)c->vcap * sizeof(VerifyPair));
+    dfree(c, c->vout, (size_t)c->vcap * 4 * sizeof(double));
+    c->vrec = nullptr;
+    c->vout = nullptr;
+    c->vcap = 0;
+    bf_status s = dalloc(c, (void **)&c->vrec, (size_t)nc * sizeof(VerifyPair), "verification records");
+    if (s) return s;
+    s = dalloc(c, (void **)&c->vout, (size_t)nc * 4 * sizeof(double), "verification results");
+    if (s) return s;
+    c->vcap = nc;
+  }
+  cudaStream_t st = c->ex->st;
+  CK(cudaMemcpyAsync(c->vrec, recs.data(), (size_t)n * sizeof(VerifyPair), cudaMemcpyHostToDevice, st),
+     "verification records");
+  run_k(c, BF_K_VERIFY, [&] {
+    return launch_verify(n, c->vrec, frame_store(c), c->intr, (float)(vp.tau_dist * vp.tau_dist),
+                         (float)vp.tau_normal, (float)vp.tau_color, c->vout, st);
+  });
+  CK(cudaGetLastError(), "verification launch");
+  CK(cudaMemcpyAsync(res.data(), c->vout, (size_t)n * 4 * sizeof(double), cudaMemcpyDeviceToHost, st),
+     "verification results");
+  CK(cudaStreamSynchronize(st), "verification");
+  return BF_OK;
+}
+
+double mean_err(const double *r) {
+  const double n = r[0] + r[1];
+  return n > 0 ? (r[2] + r[3]) / n : INFINITY;
+}
+
+}  // namespace
+
+extern "C" bf_status bf_verify_pairs(bf_ctx *c, int n, const int *frame_pairs, const double *rel,
+                                     const bf_verify_params *vp, bf_verify_result *out) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (n < 0 || (n > 0 && (!frame_pairs || !rel || !out)) || !check_verify_params(vp))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_verify_pairs: bad arguments");
+  std::vector<VerifyPair> recs(n);
+  for (int k = 0; k < n; ++k) {
+    auto fi = c->frames.find(frame_pairs[2 * k]), fj = c->frames.find(frame_pairs[2 * k + 1]);
+    if (fi == c->frames.end() || fj == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_verify_pairs: unknown frame");
+    recs[k].slot_i = fi->second.slot;
+    recs[k].slot_j = fj->second.slot;
+    const double *m = rel + 16 * k;
+    const double R[9] = {m[0], m[1], m[2], m[4], m[5], m[6], m[8], m[9], m[10]};
+    const double t[3] = {m[3], m[7], m[11]};
+    verify_record(R, t, recs[k]);
+  }
+  std::vector<double> res;
+  bf_status s = run_verify(c, recs, *vp, res);
+  if (s) return s;
+  const double need = vp->min_valid_frac * c->cfg.width * c->cfg.height;
+  for (int k = 0; k < n; ++k) {
+    const double *r = &res[4 * (size_t)k];
+    bf_verify_result &o = out[k];
+    o.n_ij = (int)r[0];
+    o.n_ji = (int)r[1];
+    o.err_ij = r[2];
+    o.err_ji = r[3];
+    o.mean_err = mean_err(r);
+    o.valid = (r[0] + r[1] >= need && o.mean_err <= vp->max_err) ? 1 : 0;
+  }
+  return BF_OK;
+}
+
+extern "C" bf_status bf_validate_chunk(bf_ctx *c, int chunk_id, double max_err, const bf_verify_params *vp,
+                                       int *valid, double *worst_err, int *worst_pair) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (!valid || !check_verify_params(vp) || !std::isfinite(max_err))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_validate_chunk: bad arguments");
+  auto ch = c->chunks.find(chunk_id);
+  if (ch == c->chunks.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_validate_chunk: unknown chunk (not solved yet)");
+  const Chunk &C = ch->second;
+  const int n = (int)C.frames.size();
+  std::vector<VerifyPair> recs;
+  std::vector<std::pair<int, int>> ids;
+  for (int a = 0; a < n; ++a)
+    for (int b = a + 1; b < n; ++b) {
+      // T_b^-1 T_a of the local poses, entries summed left to right in FP64
+      const Pose12 &Ti = C.local[a], &Tj = C.local[b];
+      double R[9], t[3];
+      const double d[3] = {Ti[9] - Tj[9], Ti[10] - Tj[10], Ti[11] - Tj[11]};
+      for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) R[3 * r + q] = (Tj[r] * Ti[q] + Tj[3 + r] * Ti[3 + q]) + Tj[6 + r] * Ti[6 + q];
+        t[r] = (Tj[r] * d[0] + Tj[3 + r] * d[1]) + Tj[6 + r] * d[2];
+      }
+      VerifyPair v;
+      v.slot_i = c->frames[C.frames[a]].slot;
+      v.slot_j = c->frames[C.frames[b]].slot;
+      verify_record(R, t, v);
+      recs.push_back(v);
+      ids.push_back({C.frames[a], C.frames[b]});
+    }
+  std::vector<double> res;
+  bf_status s = run_verify(c, recs, *vp, res);
+  if (s) return s;
+  double worst = 0.0;
+  int wa = -1, wb = -1;
+  for (size_t k = 0; k < recs.size(); ++k) {
+    const double *r = &res[4 * k];
+    if (r[0] + r[1] > 0 && mean_err(r) > worst) {
+      worst = mean_err(r);
+      wa = ids[k].first;
+      wb = ids[k].second;
+    }
+  }
+  *valid = worst <= max_err ? 1 : 0;
+  if (worst_err) *worst_err = worst;
+  if (worst_pair) {
+    worst_pair[0] = wa;
+    worst_pair[1] = wb;
   }
   return BF_OK;
 }

@@ -74,6 +74,7 @@ struct FrameStore {
   const float4 *A;        // FP32: [slot][HW] (D, n)
   const float4 *B;        // FP32: [slot][HW] (I, Ix, Iy, 0)
   const uint4 *P16;       // BF16/FP16: [slot][HW] records {D (FP32 bits), nx | ny, nz | I, Ix | Iy}
+  const unsigned short *C16;  // BF16/FP16: [slot][HW] intensity C (FP32 storage keeps it in B.w)
   const float *kx, *ky;   // kx[x] = fl32((x - cx)/fx), ky[y] = fl32((y - cy)/fy)
 };
 
@@ -224,8 +225,17 @@ struct PcgOut {
 };
 
 // ------------------------------------------------------------------ launch wrappers (host side)
+// Dense verification (Sec. 4.1.1): one CTA per frame pair, both directions.  rec[p]: slots of
+// the two frames, then fl32(T_ij) and fl32(T_ji) (R row-major, t); out[p] = {n_ij, n_ji, e_ij, e_ji}.
+struct VerifyPair {
+  int slot_i, slot_j;
+  float M[2][12];
+};
+int launch_verify(int n_pairs, const VerifyPair *rec, const FrameStore &fs, const Intr &in, float tau_d2,
+                  float tau_n, float tau_c, double *out, cudaStream_t st);
 int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
-                       float4 *A, float4 *B, uint4 *P16, float dmin, float dmax, cudaStream_t st);
+                       float4 *A, float4 *B, uint4 *P16, unsigned short *C16, float dmin, float dmax,
+                       cudaStream_t st);
 int launch_pack_corr(const float *p_i, const float *p_j, const float *w, int n, int swap, float4 *P, float4 *Q,
                       cudaStream_t st);
 int launch_pair_xform(const Tables &t, const double *pose, float *pairM, cudaStream_t st);

@@ -149,12 +149,13 @@ extern "C" bf_status bf_dense_pair_noalloc(int width, int height, double fx, dou
   fs.A = (const float4 *)(base + NA_OFF_A);
   fs.B = (const float4 *)(base + NA_OFF_B);
   fs.P16 = nullptr;
+  fs.C16 = nullptr;
   fs.kx = (const float *)(base + NA_OFF_K);
   fs.ky = fs.kx + 256;
   float4 *A = (float4 *)(base + NA_OFF_A), *B = (float4 *)(base + NA_OFF_B);
   // planes of frame i into slot 0, of frame j into slot 1 (slot tables: frame_slot = {0, 1})
-  launch_preprocess(depth_i, lum_i, 1, I + I_SLOT, fs, A, B, nullptr, depth_min, depth_max, st);
-  launch_preprocess(depth_j, lum_j, 1, I + I_SLOT + 1, fs, A, B, nullptr, depth_min, depth_max, st);
+  launch_preprocess(depth_i, lum_i, 1, I + I_SLOT, fs, A, B, nullptr, nullptr, depth_min, depth_max, st);
+  launch_preprocess(depth_j, lum_j, 1, I + I_SLOT + 1, fs, A, B, nullptr, nullptr, depth_min, depth_max, st);
 
   Tables t = {};
   t.n_frames = 2;

@@ -69,7 +69,7 @@ __global__ void k_pre1(const float *__restrict__ depth, const float *__restrict_
   const float I = (x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2) ? lum_grad_mag(Lf, pix, W) : 0.f;
   const long long o = (long long)slots[f] * HW + pix;
   A[o] = a;
-  B[o] = make_float4(I, 0.f, 0.f, 0.f);
+  B[o] = make_float4(I, 0.f, 0.f, Lf[pix]);  // w: the intensity itself (dense verification)
 }
 
 // Pass 2: grad I on the 2-pixel interior.
@@ -93,8 +93,8 @@ __global__ void k_pre2(int n, const int *__restrict__ slots, int W, int H, float
 // is formed from unrounded I exactly as in the FP32 path and rounded once.
 template <int KIND>
 __global__ void k_pre16(const float *__restrict__ depth, const float *__restrict__ lum, int n,
-                        const int *__restrict__ slots, FrameStore fs, uint4 *__restrict__ P, float dmin,
-                        float dmax) {
+                        const int *__restrict__ slots, FrameStore fs, uint4 *__restrict__ P,
+                        unsigned short *__restrict__ C16, float dmin, float dmax) {
   const int W = fs.W, H = fs.H;
   const long long HW = (long long)W * H;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -111,21 +111,24 @@ __global__ void k_pre16(const float *__restrict__ depth, const float *__restrict
     Ix = 0.5f * (lum_grad_mag(Lf, pix + 1, W) - lum_grad_mag(Lf, pix - 1, W));
     Iy = 0.5f * (lum_grad_mag(Lf, pix + W, W) - lum_grad_mag(Lf, pix - W, W));
   }
-  P[(long long)slots[f] * HW + pix] = pack16<KIND>(a, I, Ix, Iy);
+  const long long o = (long long)slots[f] * HW + pix;
+  P[o] = pack16<KIND>(a, I, Ix, Iy);
+  C16[o] = f32_to16<KIND>(Lf[pix]);
 }
 
 int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
-                       float4 *A, float4 *B, uint4 *P16, float dmin, float dmax, cudaStream_t st) {
+                       float4 *A, float4 *B, uint4 *P16, unsigned short *C16, float dmin, float dmax,
+                       cudaStream_t st) {
   const long long total = (long long)n * fs.W * fs.H;
   if (total == 0) return 0;
   const int bs = 256;
   const unsigned grid = (unsigned)((total + bs - 1) / bs);
   if (fs.storage == BF_STORE_BF16) {
-    k_pre16<BF_STORE_BF16><<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, P16, dmin, dmax);
+    k_pre16<BF_STORE_BF16><<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, P16, C16, dmin, dmax);
     return 1;
   }
   if (fs.storage == BF_STORE_FP16) {
-    k_pre16<BF_STORE_FP16><<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, P16, dmin, dmax);
+    k_pre16<BF_STORE_FP16><<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, P16, C16, dmin, dmax);
     return 1;
   }
   k_pre1<<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, A, B, dmin, dmax);

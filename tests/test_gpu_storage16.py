@@ -130,9 +130,10 @@ def test_local_solve_bf16_matches_oracle(bf, cfg1, tile_px):
 
 
 def test_16bit_store_halves_frame_memory(bf, cfg1):
-    """FP32 storage holds two 16-byte planes per pixel, 16-bit storage one."""
+    """FP32 storage holds two 16-byte planes per pixel (the intensity rides in the second), 16-bit
+    storage one 16-byte record plane plus a 2-byte intensity plane."""
     ctxs = {kind: make_ctx(bf, cfg1, kind) for kind in ("fp32", "bf16", "fp16")}
     intr = cfg1.intr
-    plane = 64 * intr["W"] * intr["H"] * 16  # default capacity: 64 frames
+    px = 64 * intr["W"] * intr["H"]  # default capacity: 64 frames
     for kind in ("bf16", "fp16"):
-        assert ctxs["fp32"].device_bytes() - ctxs[kind].device_bytes() == plane
+        assert ctxs["fp32"].device_bytes() - ctxs[kind].device_bytes() == px * (16 - 2)
