@@ -16,7 +16,7 @@ from scipy.spatial.transform import Rotation
 
 import synth
 from synth import scene as sc
-from oracle import association, frames, lie, residuals, solver, system, verification
+from oracle import association, frames, keypoints, lie, residuals, solver, system, verification
 from oracle.system import SolveParams, SparsePair
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
@@ -651,6 +651,74 @@ def test_chunk_validation_flags_a_misaligned_frame(room_frames):
     bad[2][:3, 3] += np.array([0.2, 0.0, 0.0])
     ok2, worst2, arg2, _ = verification.validate_chunk(fr, bad, intr)
     assert not ok2 and worst2 > 0.05 and 2 in arg2
+
+
+# ------------------------------------------------------- Sec. 4.1.1 key-point filters
+def spread_points(rng, n, scale=(1.0, 0.8, 0.5), centre=(0.0, 0.0, 2.0)):
+    return rng.uniform(-1, 1, (n, 3)) * np.array(scale) + np.array(centre)
+
+
+def test_kabsch_matches_an_independent_wahba_solver():
+    """scipy's Rotation.align_vectors (Wahba's problem, a different algorithm) on the centred
+    point sets gives the same rotation."""
+    rng = np.random.default_rng(61)
+    P = spread_points(rng, 40)
+    R0 = Rotation.from_rotvec([0.2, -0.4, 0.3]).as_matrix()
+    Q = P @ R0.T + np.array([0.3, -0.1, 0.5]) + rng.normal(0, 0.01, (40, 3))
+    R, t = keypoints.kabsch(P, Q)
+    Ra, _ = Rotation.align_vectors(Q - Q.mean(0), P - P.mean(0))
+    np.testing.assert_allclose(R, Ra.as_matrix(), atol=1e-12)
+    np.testing.assert_allclose(t, Q.mean(0) - R @ P.mean(0), atol=1e-12)
+
+
+def test_keypoint_filter_drops_exactly_the_outliers():
+    rng = np.random.default_rng(62)
+    P = spread_points(rng, 30)
+    R0 = Rotation.from_rotvec([0.1, 0.3, -0.2]).as_matrix()
+    t0 = np.array([0.2, 0.0, -0.3])
+    Q = P @ R0.T + t0
+    bad = [4, 11, 12, 25]
+    Q[bad] += rng.normal(0, 0.3, (len(bad), 3))  # gross mismatches, anywhere in the match order
+    out = keypoints.filter_pair(P, Q)
+    assert out.status == 0 and sorted(out.keep) == [k for k in range(30) if k not in bad]
+    np.testing.assert_allclose(out.R, R0, atol=1e-10)
+    np.testing.assert_allclose(out.t, t0, atol=1e-10)
+
+
+def test_keypoint_filter_residual_threshold():
+    """One correspondence off by 5 cm is removed, one off by 1 cm stays (its residual under the
+    refit is below the 2 cm threshold)."""
+    rng = np.random.default_rng(63)
+    P = spread_points(rng, 20)
+    Q = P.copy()
+    Q[7] += np.array([0.05, 0.0, 0.0])
+    assert 7 not in keypoints.filter_pair(P, Q).keep
+    Q = P.copy()
+    Q[7] += np.array([0.01, 0.0, 0.0])
+    assert 7 in keypoints.filter_pair(P, Q).keep
+
+
+def test_keypoint_filter_rejects_collinear_and_too_few():
+    rng = np.random.default_rng(64)
+    s = rng.uniform(-1, 1, 20)
+    P = np.stack([s, 2 * s, 0.5 * s + 2], axis=1) + rng.normal(0, 1e-4, (20, 3))  # nearly a line
+    assert keypoints.filter_pair(P, P + 0.1).status == 1
+    P4 = spread_points(rng, 4)
+    assert keypoints.filter_pair(P4, P4).status == 1  # fewer than N_min = 5
+
+
+def test_surface_area_of_a_rectangle():
+    """Points filling a 0.3 x 0.2 m rectangle (any rigid placement): area 0.06 m^2; 0.1 x 0.2: 0.02."""
+    rng = np.random.default_rng(65)
+    for a, b in ((0.3, 0.2), (0.1, 0.2)):
+        grid = np.array([[x, y, 0.0] for x in np.linspace(0, a, 7) for y in np.linspace(0, b, 5)])
+        R = Rotation.from_rotvec(rng.normal(size=3)).as_matrix()
+        X = grid @ R.T + rng.normal(size=3)
+        assert abs(keypoints.surface_area(X) - a * b) < 1e-12
+    grid = np.array([[x, y, 0.0] for x in np.linspace(0, 0.1, 7) for y in np.linspace(0, 0.2, 5)]) + [0, 0, 2.0]
+    assert keypoints.filter_pair(grid, grid).status == 2
+    big = grid * np.array([3.0, 1.0, 1.0])
+    assert keypoints.filter_pair(big, big).status == 0
 
 # ------------------------------------------------------------------ 16-bit frame storage
 def _fp16_grid_values(rng, n):
