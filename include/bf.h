@@ -262,7 +262,7 @@ bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const doub
  */
 enum {
   BF_K_PREPROCESS = 0, BF_K_XFORM, BF_K_DENSE, BF_K_SPARSE, BF_K_MERGE, BF_K_ASSEMBLE, BF_K_PCG, BF_K_UPDATE,
-  BF_K_ENERGY, BF_K_PACK, BF_K_VERIFY, BF_NPROF
+  BF_K_ENERGY, BF_K_PACK, BF_K_VERIFY, BF_K_KEYPOINT, BF_NPROF
 };
 typedef struct {
   long long launches;          /* kernels launched since the last reset (always counted)  */
@@ -331,6 +331,35 @@ bf_status bf_submit(bf_ctx *ctx, const bf_request *req, uint64_t *ticket);
  * BF_ERR_TIMEOUT if it has not completed (the ticket stays valid), BF_ERR_NOT_FOUND for an
  * unknown or already collected ticket.  stats: nullable. */
 bf_status bf_wait(bf_ctx *ctx, uint64_t ticket, int timeout_ms, bf_solve_stats *stats);
+
+/*
+ * Key-point correspondence filter and surface-area filter (Sec. 4.1.1), batched over pairs.
+ * Per pair the matches (p in camera i, q in camera j) come in order of match distance; the set
+ * grows one match at a time and, while the Kabsch fit q ~ R p + t over it has a residual above
+ * max_residual or a condition number sigma_1/sigma_2 above max_cond (covariance of the p points,
+ * of the q points, their cross-covariance), the match with the largest residual leaves the set.
+ * A pair keeps its surviving matches if at least min_matches survive and the kept p points and
+ * the kept q points each span at least min_area (bounding rectangle in the plane of their two
+ * principal axes).  Arithmetic in FP64, one warp per pair, at most 1024 matches per pair.
+ */
+typedef struct {
+  double max_residual;  /* metres (default 0.02)                                        */
+  double max_cond;      /* default 100                                                  */
+  double min_area;      /* m^2 (default 0.032)                                          */
+  int min_matches;      /* N_min (default 5)                                            */
+} bf_keypoint_params;
+void bf_default_keypoint_params(bf_keypoint_params *p);
+
+/*
+ *   offsets: n_pairs + 1 host ints (offsets[0] = 0); p_i, p_j: offsets[n_pairs] x 3 host floats.
+ *   keep: offsets[n_pairs] host bytes (out): 1 = the match survives in a kept pair.
+ *   transforms: n_pairs x 16 host doubles (out, nullable): row-major T_ij of kept pairs (else 0).
+ *   status: n_pairs host ints (out, nullable): 0 kept, 1 too few matches survive, 2 area too small.
+ * Synchronous; needs a context only for its device and stream.
+ */
+bf_status bf_filter_keypoints(bf_ctx *ctx, int n_pairs, const int *offsets, const float *p_i, const float *p_j,
+                              const bf_keypoint_params *params, unsigned char *keep, double *transforms,
+                              int *status);
 
 /*
  * Dense verification of frame pairs (Sec. 4.1.1) and chunk validation (Sec. 4.2).

@@ -23,9 +23,9 @@ BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
 BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER = 0, 1, 2, 3
 BF_MAX_GN = 64
 BF_MAX_PRUNE = 32
-BF_NPROF = 11
+BF_NPROF = 12
 KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack",
-                  "verify"]
+                  "verify", "keypoint"]
 
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_OUT_OF_MEMORY", 3: "BF_ERR_CUDA",
           4: "BF_ERR_NOT_FOUND", 5: "BF_ERR_SINGULAR", 6: "BF_ERR_TIMEOUT", 7: "BF_ERR_BUSY"}
@@ -89,6 +89,11 @@ class VerifyResult(ctypes.Structure):
                     valid=bool(self.valid))
 
 
+class KeypointParams(ctypes.Structure):
+    _fields_ = [("max_residual", ctypes.c_double), ("max_cond", ctypes.c_double), ("min_area", ctypes.c_double),
+                ("min_matches", ctypes.c_int)]
+
+
 BF_REQ_LOCAL, BF_REQ_GLOBAL = 0, 1
 
 
@@ -148,6 +153,8 @@ def lib():
         "bf_dense_pair_noalloc": (I, [I, I, D, D, D, D, ctypes.c_float, ctypes.c_float, P, P, P, P, P, P,
                                       ctypes.POINTER(SolveParams), P, P]),
         "bf_default_verify_params": (None, [ctypes.POINTER(VerifyParams)]),
+        "bf_default_keypoint_params": (None, [ctypes.POINTER(KeypointParams)]),
+        "bf_filter_keypoints": (I, [P, I, P, P, P, ctypes.POINTER(KeypointParams), P, P, P]),
         "bf_verify_pairs": (I, [P, I, P, P, ctypes.POINTER(VerifyParams), P]),
         "bf_validate_chunk": (I, [P, I, D, ctypes.POINTER(VerifyParams), P, P, P]),
     }
@@ -166,7 +173,8 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
            "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes",
            "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait",
-           "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk"]
+           "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk", "bf_default_keypoint_params",
+           "bf_filter_keypoints"]
 
 
 class BFError(RuntimeError):
@@ -328,6 +336,27 @@ class Context:
         out = np.zeros((len(ids), 4, 4), dtype=np.float64)
         self._check(lib().bf_get_poses(self.h, _ptr(ids), len(ids), _ptr(out)))
         return out
+
+    # ------------------------------------------------------ key-point filter
+    def filter_keypoints(self, offsets, p_i, p_j, **kw):
+        """Sec. 4.1.1 key-point and surface-area filters for a batch of pairs.  Returns
+        (keep mask over all matches, per-pair 4x4 transforms, per-pair status)."""
+        kp = KeypointParams()
+        lib().bf_default_keypoint_params(ctypes.byref(kp))
+        for k, v in kw.items():
+            if not hasattr(kp, k):
+                raise AttributeError(f"unknown key-point parameter {k}")
+            setattr(kp, k, v)
+        off = np.ascontiguousarray(offsets, dtype=np.int32)
+        n_pairs = len(off) - 1
+        P = np.ascontiguousarray(p_i, dtype=np.float32).reshape(-1, 3)
+        Q = np.ascontiguousarray(p_j, dtype=np.float32).reshape(-1, 3)
+        keep = np.zeros(max(int(off[-1]), 1), dtype=np.uint8)
+        T = np.zeros((max(n_pairs, 1), 4, 4))
+        status = np.zeros(max(n_pairs, 1), dtype=np.int32)
+        self._check(lib().bf_filter_keypoints(self.h, n_pairs, _ptr(off), _ptr(P), _ptr(Q), ctypes.byref(kp),
+                                              _ptr(keep), _ptr(T), _ptr(status)))
+        return keep[:int(off[-1])].astype(bool), T[:n_pairs], status[:n_pairs]
 
     # ---------------------------------------------------- dense verification
     def verify_pairs(self, frame_pairs, rel, **kw):

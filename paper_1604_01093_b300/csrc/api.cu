@@ -121,6 +121,8 @@ struct bf_ctx {
   int cap = 0;
   float4 *A = nullptr, *B = nullptr;
   unsigned short *C16 = nullptr;  // 16-bit storage: intensity plane (dense verification)
+  void *kp_buf = nullptr;         // key-point filter: inputs and results
+  size_t kp_cap = 0;
   VerifyPair *vrec = nullptr;     // dense verification: pair records and results
   double *vout = nullptr;
   int vcap = 0;
@@ -447,6 +449,7 @@ extern "C" bf_status bf_destroy(bf_ctx *c) {
   cudaFree(c->B);
   cudaFree(c->C16);
   cudaFree(c->vrec);
+  cudaFree(c->kp_buf);
   cudaFree(c->vout);
   cudaFree(c->kx);
   cudaFree(c->ky);
@@ -1633,6 +1636,85 @@ extern "C" bf_status bf_get_poses(bf_ctx *c, const int *frame_ids, int n, double
   return BF_OK;
 }
 
+
+
+// ------------------------------------------------------------------- key-point filter
+extern "C" void bf_default_keypoint_params(bf_keypoint_params *p) {
+  if (!p) return;
+  p->max_residual = 0.02;
+  p->max_cond = 100.0;
+  p->min_area = 0.032;
+  p->min_matches = 5;
+}
+
+extern "C" bf_status bf_filter_keypoints(bf_ctx *c, int n_pairs, const int *offsets, const float *p_i,
+                                         const float *p_j, const bf_keypoint_params *kp, unsigned char *keep,
+                                         double *transforms, int *status) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (n_pairs < 0 || (n_pairs > 0 && (!offsets || !keep)) || !kp || !(kp->max_residual >= 0) ||
+      !(kp->max_cond >= 1) || !std::isfinite(kp->min_area) || kp->min_matches < 0)
+    return fail(c, BF_ERR_INVALID_ARG, "bf_filter_keypoints: bad arguments");
+  if (n_pairs == 0) return BF_OK;
+  if (offsets[0] != 0) return fail(c, BF_ERR_INVALID_ARG, "bf_filter_keypoints: offsets[0] must be 0");
+  for (int k = 0; k < n_pairs; ++k) {
+    const int n = offsets[k + 1] - offsets[k];
+    if (n < 0 || n > keypoint_nmax())
+      return fail(c, BF_ERR_INVALID_ARG, "bf_filter_keypoints: a pair has more than 1024 matches (or a negative count)");
+  }
+  const long long total = offsets[n_pairs];
+  if (total > 0 && (!p_i || !p_j)) return fail(c, BF_ERR_INVALID_ARG, "bf_filter_keypoints: null points");
+  // device layout: offsets | p_i | p_j | keep | results
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_off = al(sizeof(int) * (n_pairs + 1)), b_pts = al(12 * (size_t)total),
+               b_keep = al((size_t)total), b_res = al(keypoint_result_bytes() * n_pairs);
+  const size_t need = b_off + 2 * b_pts + b_keep + b_res;
+  cudaStream_t st = c->ex->st;
+  if (need > c->kp_cap) {
+    CK(cudaStreamSynchronize(st), "key-point buffers");
+    dfree(c, c->kp_buf, c->kp_cap);
+    c->kp_buf = nullptr;
+    c->kp_cap = 0;
+    bf_status s = dalloc(c, &c->kp_buf, need, "key-point filter");
+    if (s) return s;
+    c->kp_cap = need;
+  }
+  char *base = (char *)c->kp_buf;
+  int *d_off = (int *)base;
+  float *d_p = (float *)(base + b_off), *d_q = (float *)(base + b_off + b_pts);
+  unsigned char *d_keep = (unsigned char *)(base + b_off + 2 * b_pts);
+  char *d_res = base + b_off + 2 * b_pts + b_keep;
+  CK(cudaMemcpyAsync(d_off, offsets, sizeof(int) * (n_pairs + 1), cudaMemcpyHostToDevice, st), "key-point input");
+  if (total > 0) {
+    CK(cudaMemcpyAsync(d_p, p_i, 12 * (size_t)total, cudaMemcpyHostToDevice, st), "key-point input");
+    CK(cudaMemcpyAsync(d_q, p_j, 12 * (size_t)total, cudaMemcpyHostToDevice, st), "key-point input");
+  }
+  run_k(c, BF_K_KEYPOINT, [&] {
+    return launch_keypoints(n_pairs, d_off, d_p, d_q, kp->max_residual, kp->max_cond, kp->min_matches, kp->min_area,
+                            d_keep, d_res, st);
+  });
+  CK(cudaGetLastError(), "key-point launch");
+  std::vector<char> res(keypoint_result_bytes() * n_pairs);
+  if (total > 0) CK(cudaMemcpyAsync(keep, d_keep, (size_t)total, cudaMemcpyDeviceToHost, st), "key-point output");
+  CK(cudaMemcpyAsync(res.data(), d_res, res.size(), cudaMemcpyDeviceToHost, st), "key-point output");
+  CK(cudaStreamSynchronize(st), "key-point filter");
+  for (int k = 0; k < n_pairs; ++k) {
+    const char *r = res.data() + keypoint_result_bytes() * k;
+    double R[9], t[3];
+    int stt;
+    std::memcpy(R, r, sizeof(R));
+    std::memcpy(t, r + sizeof(R), sizeof(t));
+    std::memcpy(&stt, r + sizeof(R) + sizeof(t), sizeof(int));
+    if (status) status[k] = stt;
+    if (transforms) {
+      double *m = transforms + 16 * k;
+      const double M[16] = {R[0], R[1], R[2], t[0], R[3], R[4], R[5], t[1], R[6], R[7], R[8], t[2], 0, 0, 0, 1};
+      if (stt == 0) std::memcpy(m, M, sizeof(M));
+      else std::memset(m, 0, sizeof(M));
+    }
+  }
+  return BF_OK;
+}
 
 // ----------------------------------------------------------------- dense verification
 extern "C" void bf_default_verify_params(bf_verify_params *p) {

@@ -233,6 +233,12 @@ struct VerifyPair {
 };
 int launch_verify(int n_pairs, const VerifyPair *rec, const FrameStore &fs, const Intr &in, float tau_d2,
                   float tau_n, float tau_c, double *out, cudaStream_t st);
+// Key-point filter (Sec. 4.1.1), one warp per pair; res: keypoint_result_bytes() per pair
+// {R (9 doubles), t (3 doubles), status, pad}.  Pairs must have at most keypoint_nmax() matches.
+int keypoint_nmax();
+size_t keypoint_result_bytes();
+int launch_keypoints(int n_pairs, const int *off, const float *P, const float *Q, double max_res, double max_cond,
+                     int min_matches, double min_area, unsigned char *keep, void *res, cudaStream_t st);
 int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
                        float4 *A, float4 *B, uint4 *P16, unsigned short *C16, float dmin, float dmax,
                        cudaStream_t st);
