@@ -197,6 +197,7 @@ bf_status bf_clear_correspondences(bf_ctx *ctx);
  * the other frames start at identity (or, with warm_start, at the chunk's previous local
  * poses, Sec. 4.4).  Every correspondence pair within the chunk is used; the dense set E is
  * the pairs within max_angle_deg at the initial poses.  Local poses are stored under chunk_id.
+ * A pair with fewer than 3 correspondences makes the call fail with BF_ERR_INVALID_ARG.
  * stats: nullable.
  */
 bf_status bf_solve_local(bf_ctx *ctx, int chunk_id, const int *frame_ids, int n,
@@ -399,6 +400,16 @@ bf_status bf_verify_pairs(bf_ctx *ctx, int n, const int *frame_pairs, const doub
  */
 bf_status bf_validate_chunk(bf_ctx *ctx, int chunk_id, double max_err, const bf_verify_params *params,
                             int *valid, double *worst_err, int *worst_pair);
+
+/*
+ * Failure-detection self-test.  The library's device waits (the cooperative PCG's grid barrier,
+ * the staged dense kernel's wait for its bulk copies) give up after a bounded number of polls
+ * and the call that launched them returns BF_ERR_TIMEOUT.  This call makes one such wait run out
+ * on purpose with `limit` polls (1 .. 2^24): which = 0 polls a device word that nothing
+ * changes, which = 1 waits on an mbarrier that nothing arrives on.  *gave_up = 1 and
+ * BF_ERR_TIMEOUT when the wait ended as designed; the context stays usable.
+ */
+bf_status bf_selftest_wait_timeout(bf_ctx *ctx, int which, long long limit, int *gave_up);
 
 /* Device bytes currently held by the context. */
 size_t bf_device_bytes(bf_ctx *ctx);

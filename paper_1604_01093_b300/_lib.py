@@ -153,6 +153,7 @@ def lib():
         "bf_dense_pair_noalloc": (I, [I, I, D, D, D, D, ctypes.c_float, ctypes.c_float, P, P, P, P, P, P,
                                       ctypes.POINTER(SolveParams), P, P]),
         "bf_default_verify_params": (None, [ctypes.POINTER(VerifyParams)]),
+        "bf_selftest_wait_timeout": (I, [P, I, ctypes.c_longlong, P]),
         "bf_default_keypoint_params": (None, [ctypes.POINTER(KeypointParams)]),
         "bf_filter_keypoints": (I, [P, I, P, P, P, ctypes.POINTER(KeypointParams), P, P, P]),
         "bf_verify_pairs": (I, [P, I, P, P, ctypes.POINTER(VerifyParams), P]),
@@ -174,7 +175,7 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes",
            "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait",
            "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk", "bf_default_keypoint_params",
-           "bf_filter_keypoints"]
+           "bf_filter_keypoints", "bf_selftest_wait_timeout"]
 
 
 class BFError(RuntimeError):
@@ -336,6 +337,14 @@ class Context:
         out = np.zeros((len(ids), 4, 4), dtype=np.float64)
         self._check(lib().bf_get_poses(self.h, _ptr(ids), len(ids), _ptr(out)))
         return out
+
+    # ------------------------------------------------------ failure detection
+    def selftest_wait_timeout(self, which, limit=1 << 16):
+        """Make one bounded device wait run out (0: a word nothing changes, 1: an mbarrier nothing
+        arrives on); returns (status, gave_up)."""
+        flag = ctypes.c_int(0)
+        st = lib().bf_selftest_wait_timeout(self.h, which, limit, ctypes.byref(flag))
+        return st, flag.value
 
     # ------------------------------------------------------ key-point filter
     def filter_keypoints(self, offsets, p_i, p_j, **kw):

@@ -830,6 +830,10 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
       T.pair_ida.push_back(P.ids[a]);
       T.pair_idb.push_back(P.ids[b]);
       const auto &segs = c->corr[pair_key(P.ids[a], P.ids[b])];
+      long long pair_n = 0;
+      for (const Seg &sg : segs) pair_n += sg.cnt;
+      if (pair_n < 3)  // fewer than 3 matches determine no rigid transform (Sec. 4.1.1)
+        return fail(c, BF_ERR_INVALID_ARG, "a frame pair of the solve has fewer than 3 correspondences");
       T.pair_seg0.push_back(T.n_segs);
       const int swap = P.ids[a] > P.ids[b] ? 1 : 0;  // pool stores the smaller id's point first
       for (const Seg &sg : segs) {
@@ -1637,6 +1641,31 @@ extern "C" bf_status bf_get_poses(bf_ctx *c, const int *frame_ids, int n, double
 }
 
 
+
+
+// ------------------------------------------------------------ failure-detection self-test
+extern "C" bf_status bf_selftest_wait_timeout(bf_ctx *c, int which, long long limit, int *gave_up) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if ((which != 0 && which != 1) || limit < 1 || limit > (1LL << 24) || !gave_up)
+    return fail(c, BF_ERR_INVALID_ARG, "bf_selftest_wait_timeout: bad arguments");
+  cudaStream_t st = c->ex->st;
+  int *buf = nullptr;  // [0] the word nothing changes, [1] the kernel's error flag
+  bf_status s = dalloc(c, (void **)&buf, 2 * sizeof(int), "self-test");
+  if (s) return s;
+  cudaError_t e = cudaMemsetAsync(buf, 0, 2 * sizeof(int), st);
+  int flag = 0;
+  if (e == cudaSuccess) {
+    launch_selftest_wait(which, (const unsigned *)buf, buf + 1, limit, st);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, buf + 1, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  dfree(c, buf, 2 * sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(c, e, "self-test");
+  *gave_up = flag;
+  return flag ? fail(c, BF_ERR_TIMEOUT, "self-test: the bounded wait gave up as intended") : BF_OK;
+}
 
 // ------------------------------------------------------------------- key-point filter
 extern "C" void bf_default_keypoint_params(bf_keypoint_params *p) {

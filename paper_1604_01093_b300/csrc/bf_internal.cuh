@@ -215,6 +215,44 @@ __device__ __forceinline__ void update_pose(double *T, const float *x) {
   T[11] += (double)x[5];
 }
 
+// ------------------------------------------------------------------------- bounded waits
+// Every wait of this library on another thread's or the copy engine's progress gives up after a
+// bounded number of polls and reports an error instead of hanging the GPU.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_try_wait_parity(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the given phase parity of an mbarrier; false if `limit` polls ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, long long limit) {
+  for (long long k = 0; k < limit; ++k) {
+    if (mbar_try_wait_parity(bar, parity)) return true;
+    if (k > 64) __nanosleep(128);
+  }
+  return false;
+}
+
+// Spin until *word != old: the first `fast` polls back to back, then with a 64 ns back-off.
+// Gives up (false) after `limit` polls, or as soon as *abort is set by another waiter.
+__device__ __forceinline__ bool wait_change(const volatile unsigned *word, unsigned old, const volatile int *abort,
+                                            long long limit, long long fast) {
+  long long spins = 0;
+  while (*word == old) {
+    if (*abort) return false;
+    if (++spins > limit) return false;
+    if (spins > fast) __nanosleep(64);
+  }
+  return true;
+}
+
 // Per-GN-iteration outputs the PCG kernels write besides the step: the problem's energy record
 // (sum of its pairs' records, fixed order), the updated poses and (per-problem kernel only) the
 // pair transforms of the updated poses for the next linearisation.
@@ -239,6 +277,9 @@ int keypoint_nmax();
 size_t keypoint_result_bytes();
 int launch_keypoints(int n_pairs, const int *off, const float *P, const float *Q, double max_res, double max_cond,
                      int min_matches, double min_area, unsigned char *keep, void *res, cudaStream_t st);
+// Bounded-wait self-test: which = 0 polls *word (which stays 0), 1 waits on an mbarrier nothing
+// arrives on; *err = 1 when the wait gave up after `limit` polls.
+int launch_selftest_wait(int which, const unsigned *word, int *err, long long limit, cudaStream_t st);
 int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
                        float4 *A, float4 *B, uint4 *P16, unsigned short *C16, float dmin, float dmax,
                        cudaStream_t st);

@@ -277,27 +277,6 @@ int dense_staged_smem(int W, int H, int storage) {
 }
 bool dense_staged_fits(int W, int H, int storage) { return dense_staged_smem(W, H, storage) + 4096 <= STG_MAX_SMEM; }
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_try_wait_parity(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait for phase 0 of the barrier; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait0(unsigned bar) {
-  for (long long k = 0; k < STG_WAIT_LIMIT; ++k) {
-    if (mbar_try_wait_parity(bar, 0)) return true;
-    if (k > 64) __nanosleep(128);
-  }
-  return false;
-}
-
 // Sum of N per-thread values over a quad (4 warps, 128 threads): warp trees, then the 4 warp
 // results in order by thread k < N, which writes out[k].
 template <int N, typename Part>
@@ -359,10 +338,10 @@ __global__ void __launch_bounds__(STG_BS, 1)
                    "l"(fs.B + (long long)tslot * HW), "r"(bytes), "r"(barp)
                    : "memory");
   }
-  if (!mbar_wait0(barp)) {
+  if (!mbar_wait(barp, 0, STG_WAIT_LIMIT)) {
     // the copies did not land within the limit: report, wait once more for them, then leave
     if (threadIdx.x == 0) atomicExch(err, 1);
-    mbar_wait0(barp);
+    mbar_wait(barp, 0, STG_WAIT_LIMIT);
     return;
   }
   const int quad = threadIdx.x >> 7, tq = threadIdx.x & 127;

@@ -784,20 +784,9 @@ __device__ bool grid_barrier(unsigned *count, volatile unsigned *gen, unsigned n
       atomicExch(count, 0u);
       __threadfence();
       atomicAdd((unsigned *)gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (*err) {
-          ok = 0;
-          break;
-        }
-        if (++spins > BARRIER_SPIN_LIMIT) {
-          *err = 1;
-          ok = 0;
-          break;
-        }
-        if (spins > BARRIER_SPIN_FAST) __nanosleep(64);
-      }
+    } else if (!wait_change(gen, g, err, BARRIER_SPIN_LIMIT, BARRIER_SPIN_FAST)) {
+      *err = 1;  // timed out here, or another CTA already gave up
+      ok = 0;
     }
     __threadfence();
   }

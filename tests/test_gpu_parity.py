@@ -264,6 +264,15 @@ def test_invalid_arguments(bf, cfg1):
     with pytest.raises(bf.BFError) as e:
         ctx.solve_local(0, [0, 1], n_gn=bf._lib.BF_MAX_GN + 1)
     assert e.value.status == 1
+    # a pair with fewer than 3 correspondences cannot take part in a solve
+    n = cfg1.n_frames
+    ctx.add_frames(n, cfg1.depth[:2], cfg1.lum[:2])
+    ctx.add_correspondences(n, n + 1, np.ones((2, 3), np.float32), np.ones((2, 3), np.float32))
+    with pytest.raises(bf.BFError) as e:
+        ctx.solve_local(1, [n, n + 1], n_gn=1)
+    assert e.value.status == 1
+    ctx.add_correspondences(n, n + 1, np.ones((1, 3), np.float32), np.ones((1, 3), np.float32))
+    ctx.solve_local(1, [n, n + 1], n_gn=1)  # three now
 
 
 def test_single_frame_and_empty_solves(bf, cfg1):
@@ -398,3 +407,14 @@ def test_batched_chunks_320x240_match_oracle(bf, batch320):
         fr = [ofr.Frame(prob.depth[f], prob.lum[f], prob.intr) for f in ids]
         ref = solver.gauss_newton(fr, prob.intr, prob.init[ids], solver.sparse_pairs_for(prob, ids), prm)
         compare_solve(stats[k], ctx.get_poses(ids), ref, f"chunk {k} at 320x240")
+
+
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_waits_give_up_and_the_context_survives(bf, cfg1, which):
+    """Failure detection without a fault: a wait on a flag nothing sets (0) or an mbarrier nothing
+    arrives on (1) ends after its poll limit with BF_ERR_TIMEOUT; the same context then solves."""
+    ctx = make_ctx(bf, cfg1)
+    status, gave_up = ctx.selftest_wait_timeout(which, 1 << 14)
+    assert status == 6 and gave_up == 1  # BF_ERR_TIMEOUT
+    st = ctx.solve_local(0, list(range(11)), n_gn=1, n_pcg=4)
+    assert st["n_gn"] == 1 and np.isfinite(st["energy"]).all()
