@@ -16,7 +16,7 @@ from scipy.spatial.transform import Rotation
 
 import synth
 from synth import scene as sc
-from oracle import association, frames, keypoints, lie, residuals, solver, system, verification
+from oracle import association, frames, keypoints, lie, residuals, solver, system, tsdf, verification
 from oracle.system import SolveParams, SparsePair
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
@@ -719,6 +719,95 @@ def test_surface_area_of_a_rectangle():
     assert keypoints.filter_pair(grid, grid).status == 2
     big = grid * np.array([3.0, 1.0, 1.0])
     assert keypoints.filter_pair(big, big).status == 0
+
+
+# ------------------------------------------------------------- Sec. 5 TSDF integration
+def plane_depth(intr, Z):
+    return np.full((intr["H"], intr["W"]), Z, dtype=np.float32)
+
+
+def test_tsdf_plane_closed_form():
+    """A fronto-parallel plane at depth Z seen from the identity pose: every touched voxel in
+    front of it within the truncation band holds Z - z, further in front mu, and nothing behind
+    Z + mu is touched."""
+    intr = sc.intrinsics(80, 60)
+    prm = tsdf.Params()
+    Z = 1.3
+    vol = tsdf.integrate({}, plane_depth(intr, Z), np.full((60, 80), 0.25, np.float32), intr, np.eye(4), prm)
+    assert len(vol) > 50
+    mu = float(prm.mu)
+    n_band = 0
+    for key, blk in vol.items():
+        D, Wt = tsdf.tsdf_value(blk)
+        z = (8 * key[2] + np.arange(512) // 64 + 0.5) * 0.004
+        hit = Wt > 0
+        assert np.all(z[hit] <= Z + mu + 1e-6)  # nothing behind the band
+        near = hit & (np.abs(Z - z) < mu - 1e-5)
+        np.testing.assert_allclose(D[near], Z - z[near], atol=2e-6)
+        np.testing.assert_allclose(D[hit & (Z - z > mu + 1e-5)], mu, atol=1e-6)
+        assert np.all(blk[2][hit] == round(0.25 * 65535))  # one sample: the quantised intensity
+        n_band += near.sum()
+    assert n_band > 1000
+
+
+def test_tsdf_running_average_and_exact_inverse():
+    """Two planes (Z1, Z2) give the paper's running average D = (d1 + d2) / 2 with W = 2;
+    removing one with the inverse update leaves exactly the other; the order of integration
+    does not matter and integrate + de-integrate restores every sum to zero."""
+    intr = sc.intrinsics(80, 60)
+    prm = tsdf.Params()
+    c = np.full((60, 80), 0.5, np.float32)
+    d1, d2 = plane_depth(intr, 1.30), plane_depth(intr, 1.31)
+    both = tsdf.integrate(tsdf.integrate({}, d1, c, intr, np.eye(4), prm), d2, c, intr, np.eye(4), prm)
+    rev = tsdf.integrate(tsdf.integrate({}, d2, c, intr, np.eye(4), prm), d1, c, intr, np.eye(4), prm)
+    assert both.keys() == rev.keys() and all(np.array_equal(both[k], rev[k]) for k in both)
+    one = tsdf.integrate({}, d1, c, intr, np.eye(4), prm)
+    for k, blk in both.items():
+        D, Wt = tsdf.tsdf_value(blk)
+        z = (8 * k[2] + np.arange(512) // 64 + 0.5) * 0.004
+        two = Wt == 2
+        sdf = lambda Z: np.minimum(Z - z, float(prm.mu))
+        np.testing.assert_allclose(D[two], 0.5 * (sdf(1.30) + sdf(1.31))[two], atol=2e-6)
+    back = tsdf.integrate({k: v.copy() for k, v in both.items()}, d2, c, intr, np.eye(4), prm, sign=-1)
+    for k, blk in back.items():
+        np.testing.assert_array_equal(blk, one.get(k, np.zeros((3, 512), np.int64)))
+    zero = tsdf.integrate(back, d1, c, intr, np.eye(4), prm, sign=-1)
+    assert all(not blk.any() for blk in zero.values())
+
+
+def test_tsdf_pose_moves_the_surface():
+    """Integrating the plane from a camera moved by +0.1 m along z at a pose that says so puts
+    the same world surface in the same voxels as the original view."""
+    intr = sc.intrinsics(80, 60)
+    prm = tsdf.Params()
+    c = np.full((60, 80), 0.5, np.float32)
+    T = np.eye(4)
+    T[2, 3] = 0.1  # camera 0.1 m further along +z: the plane at 1.3 is at depth 1.2
+    a = tsdf.integrate({}, plane_depth(intr, 1.3), c, intr, np.eye(4), prm)
+    b = tsdf.integrate({}, plane_depth(intr, 1.2), c, intr, T, prm)
+    common = set(a) & set(b)
+    assert len(common) > 20
+    for k in common:
+        Da, Wa = tsdf.tsdf_value(a[k])
+        Db, Wb = tsdf.tsdf_value(b[k])
+        both = (Wa > 0) & (Wb > 0)
+        np.testing.assert_allclose(Da[both], Db[both], atol=1e-5)
+
+
+def test_euler_angles_and_pose_distance():
+    rng = np.random.default_rng(66)
+    for _ in range(5):
+        al, be, ga = rng.uniform(-1, 1, 3)
+        R = Rotation.from_euler("ZYX", [ga, be, al]).as_matrix()  # Rz(ga) Ry(be) Rx(al)
+        np.testing.assert_allclose(tsdf.euler(R), [al, be, ga], atol=1e-12)
+    Ta, Tb = np.eye(4), np.eye(4)
+    Tb[:3, :3] = Rotation.from_euler("ZYX", [0.0, 0.0, 0.1]).as_matrix()
+    Tb[:3, 3] = [0.3, 0.0, 0.4]
+    assert abs(tsdf.pose_distance(Ta, Tb) - math.sqrt(0.2 ** 2 + 0.3 ** 2 + 0.4 ** 2)) < 1e-12
+    integ = {5: Ta, 7: Ta, 9: Ta}
+    opt = {5: Tb, 7: Ta, 9: Tb}
+    assert tsdf.reintegration_order(integ, opt, n_fix=10) == [5, 9]
+    assert tsdf.reintegration_order(integ, opt, n_fix=1) == [5]
 
 # ------------------------------------------------------------------ 16-bit frame storage
 def _fp16_grid_values(rng, n):
