@@ -263,7 +263,7 @@ bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const doub
  */
 enum {
   BF_K_PREPROCESS = 0, BF_K_XFORM, BF_K_DENSE, BF_K_SPARSE, BF_K_MERGE, BF_K_ASSEMBLE, BF_K_PCG, BF_K_UPDATE,
-  BF_K_ENERGY, BF_K_PACK, BF_K_VERIFY, BF_K_KEYPOINT, BF_NPROF
+  BF_K_ENERGY, BF_K_PACK, BF_K_VERIFY, BF_K_KEYPOINT, BF_K_TSDF, BF_NPROF
 };
 typedef struct {
   long long launches;          /* kernels launched since the last reset (always counted)  */
@@ -400,6 +400,48 @@ bf_status bf_verify_pairs(bf_ctx *ctx, int n, const int *frame_pairs, const doub
  */
 bf_status bf_validate_chunk(bf_ctx *ctx, int chunk_id, double max_err, const bf_verify_params *params,
                             int *valid, double *worst_err, int *worst_pair);
+
+/*
+ * TSDF reconstruction with integration and de-integration (Sec. 5), one volume per context.
+ * Voxels of 8x8x8 blocks (Sec. 5.1) found through a hash table of block coordinates keep the
+ * integer sums S = sum w d_q (truncated signed distance in units of 2^-20 m), W = sum w and
+ * SC = sum w c_q (intensity in units of 1/65535), w = 1 per sample; the paper's running average
+ * D = (D W + w d) / (W + w) (Sec. 5.2) is S 2^-20 / W, and de-integration subtracts exactly
+ * what integration added.  A frame touches the blocks containing its band samples (every valid
+ * pixel's ray at depths D + k voxel/2, |k voxel/2| <= mu) and updates their voxels: projective
+ * distance d = D(u) - z to the nearest pixel u of the voxel centre's projection, voxels with
+ * d < -mu left alone, sdf = min(d, mu), mu = trunc_voxels * voxel_size.  Depth and intensity
+ * are the frame's stored planes.  Synchronous calls.
+ */
+typedef struct {
+  double voxel_size;   /* metres (default 0.004, the paper's default)                     */
+  int trunc_voxels;    /* mu in voxels (default 5)                                        */
+  int table_log2;      /* hash table of 2^table_log2 slots (default 20)                    */
+  int max_blocks;      /* block pool capacity (default 65536; 6 KB per block)              */
+} bf_tsdf_config;
+void bf_default_tsdf_config(bf_tsdf_config *p);
+/* (Re)create the context's volume, empty.  BF_ERR_OUT_OF_MEMORY beyond the HBM budget. */
+bf_status bf_tsdf_init(bf_ctx *ctx, const bf_tsdf_config *cfg);
+/* Integrate a frame at pose (16 doubles, camera -> world; NULL = the frame's current world
+ * pose) and remember that pose as its integrated pose.  A full table or pool returns
+ * BF_ERR_OUT_OF_MEMORY. */
+bf_status bf_tsdf_integrate(bf_ctx *ctx, int frame_id, const double *pose);
+/* Remove a frame at its integrated pose (the exact inverse of its integration). */
+bf_status bf_tsdf_deintegrate(bf_ctx *ctx, int frame_id);
+/*
+ * Sec. 5.3 update: order the integrated frames by the distance between integrated and current
+ * (optimised) world pose, ||s (e_int, t_int) - s (e_opt, t_opt)||, s = (2, 2, 2, 1, 1, 1), e the
+ * Euler angles of R = Rz(g) Ry(b) Rx(a); de-integrate and re-integrate the first n_fix (the paper
+ * uses 10) with a non-zero distance.  frame_ids (nullable, n_fix ints) gets them in order.
+ */
+bf_status bf_tsdf_reintegrate(bf_ctx *ctx, int n_fix, int *frame_ids, int *n_done);
+/*
+ * Copy out the allocated blocks sorted by coordinate: block_coords capacity x 3 ints (bx, by,
+ * bz; voxel (ix, iy, iz) of a block has centre ((8 bx + ix + 1/2) voxel_size, ...)), sums
+ * capacity x 3 x 512 ints (S, W, SC per voxel, voxel index ix + 8 iy + 64 iz).  *n = the number
+ * of allocated blocks (also when it exceeds capacity; capacity 0 only counts).
+ */
+bf_status bf_tsdf_export(bf_ctx *ctx, long long capacity, int *block_coords, int *sums, long long *n);
 
 /*
  * Failure-detection self-test.  The library's device waits (the cooperative PCG's grid barrier,

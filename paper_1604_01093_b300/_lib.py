@@ -23,9 +23,9 @@ BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
 BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER = 0, 1, 2, 3
 BF_MAX_GN = 64
 BF_MAX_PRUNE = 32
-BF_NPROF = 12
+BF_NPROF = 13
 KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack",
-                  "verify", "keypoint"]
+                  "verify", "keypoint", "tsdf"]
 
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_OUT_OF_MEMORY", 3: "BF_ERR_CUDA",
           4: "BF_ERR_NOT_FOUND", 5: "BF_ERR_SINGULAR", 6: "BF_ERR_TIMEOUT", 7: "BF_ERR_BUSY"}
@@ -94,6 +94,11 @@ class KeypointParams(ctypes.Structure):
                 ("min_matches", ctypes.c_int)]
 
 
+class TsdfConfig(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_double), ("trunc_voxels", ctypes.c_int), ("table_log2", ctypes.c_int),
+                ("max_blocks", ctypes.c_int)]
+
+
 BF_REQ_LOCAL, BF_REQ_GLOBAL = 0, 1
 
 
@@ -154,6 +159,12 @@ def lib():
                                       ctypes.POINTER(SolveParams), P, P]),
         "bf_default_verify_params": (None, [ctypes.POINTER(VerifyParams)]),
         "bf_selftest_wait_timeout": (I, [P, I, ctypes.c_longlong, P]),
+        "bf_default_tsdf_config": (None, [ctypes.POINTER(TsdfConfig)]),
+        "bf_tsdf_init": (I, [P, ctypes.POINTER(TsdfConfig)]),
+        "bf_tsdf_integrate": (I, [P, I, P]),
+        "bf_tsdf_deintegrate": (I, [P, I]),
+        "bf_tsdf_reintegrate": (I, [P, I, P, P]),
+        "bf_tsdf_export": (I, [P, ctypes.c_longlong, P, P, P]),
         "bf_default_keypoint_params": (None, [ctypes.POINTER(KeypointParams)]),
         "bf_filter_keypoints": (I, [P, I, P, P, P, ctypes.POINTER(KeypointParams), P, P, P]),
         "bf_verify_pairs": (I, [P, I, P, P, ctypes.POINTER(VerifyParams), P]),
@@ -175,7 +186,8 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes",
            "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait",
            "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk", "bf_default_keypoint_params",
-           "bf_filter_keypoints", "bf_selftest_wait_timeout"]
+           "bf_filter_keypoints", "bf_selftest_wait_timeout", "bf_default_tsdf_config", "bf_tsdf_init",
+           "bf_tsdf_integrate", "bf_tsdf_deintegrate", "bf_tsdf_reintegrate", "bf_tsdf_export"]
 
 
 class BFError(RuntimeError):
@@ -337,6 +349,39 @@ class Context:
         out = np.zeros((len(ids), 4, 4), dtype=np.float64)
         self._check(lib().bf_get_poses(self.h, _ptr(ids), len(ids), _ptr(out)))
         return out
+
+    # ------------------------------------------------------------------ TSDF
+    def tsdf_init(self, **kw):
+        cfg = TsdfConfig()
+        lib().bf_default_tsdf_config(ctypes.byref(cfg))
+        for k, v in kw.items():
+            if not hasattr(cfg, k):
+                raise AttributeError(f"unknown TSDF setting {k}")
+            setattr(cfg, k, v)
+        self._check(lib().bf_tsdf_init(self.h, ctypes.byref(cfg)))
+
+    def tsdf_integrate(self, frame_id, pose=None):
+        T = None if pose is None else np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+        self._check(lib().bf_tsdf_integrate(self.h, frame_id, None if T is None else _ptr(T)))
+
+    def tsdf_deintegrate(self, frame_id):
+        self._check(lib().bf_tsdf_deintegrate(self.h, frame_id))
+
+    def tsdf_reintegrate(self, n_fix=10):
+        ids = np.zeros(max(n_fix, 1), dtype=np.int32)
+        n = ctypes.c_int(0)
+        self._check(lib().bf_tsdf_reintegrate(self.h, n_fix, _ptr(ids), ctypes.byref(n)))
+        return ids[:n.value].tolist()
+
+    def tsdf_export(self):
+        """{(bx, by, bz): int64 array (3, 512) of S, W, SC}."""
+        n = ctypes.c_longlong(0)
+        self._check(lib().bf_tsdf_export(self.h, 0, None, None, ctypes.byref(n)))
+        cap = n.value
+        coords = np.zeros((max(cap, 1), 3), dtype=np.int32)
+        sums = np.zeros((max(cap, 1), 3, 512), dtype=np.int32)
+        self._check(lib().bf_tsdf_export(self.h, cap, _ptr(coords), _ptr(sums), ctypes.byref(n)))
+        return {tuple(map(int, coords[k])): sums[k].astype(np.int64) for k in range(cap)}
 
     # ------------------------------------------------------ failure detection
     def selftest_wait_timeout(self, which, limit=1 << 16):

@@ -13,6 +13,7 @@
 #include <condition_variable>
 #include <deque>
 #include <memory>
+#include <map>
 #include <mutex>
 #include <thread>
 #include <cstdio>
@@ -121,6 +122,13 @@ struct bf_ctx {
   int cap = 0;
   float4 *A = nullptr, *B = nullptr;
   unsigned short *C16 = nullptr;  // 16-bit storage: intensity plane (dense verification)
+  // TSDF volume (Sec. 5): device arrays, the frames integrated and the pose each used
+  bool tsdf_on = false;
+  bf_tsdf_config tsdf_cfg{};
+  TsdfDev tsdf{};
+  std::vector<std::pair<void *, size_t>> tsdf_allocs;
+  std::map<int, Pose12> tsdf_integrated;
+  int tsdf_call = 0;
   void *kp_buf = nullptr;         // key-point filter: inputs and results
   size_t kp_cap = 0;
   VerifyPair *vrec = nullptr;     // dense verification: pair records and results
@@ -448,6 +456,7 @@ extern "C" bf_status bf_destroy(bf_ctx *c) {
   cudaFree(c->A);
   cudaFree(c->B);
   cudaFree(c->C16);
+  for (auto &a : c->tsdf_allocs) cudaFree(a.first);
   cudaFree(c->vrec);
   cudaFree(c->kp_buf);
   cudaFree(c->vout);
@@ -1665,6 +1674,209 @@ extern "C" bf_status bf_selftest_wait_timeout(bf_ctx *c, int which, long long li
   if (e != cudaSuccess) return cuda_fail(c, e, "self-test");
   *gave_up = flag;
   return flag ? fail(c, BF_ERR_TIMEOUT, "self-test: the bounded wait gave up as intended") : BF_OK;
+}
+
+
+// -------------------------------------------------------------------------------- TSDF
+extern "C" void bf_default_tsdf_config(bf_tsdf_config *p) {
+  if (!p) return;
+  p->voxel_size = 0.004;
+  p->trunc_voxels = 5;
+  p->table_log2 = 20;
+  p->max_blocks = 1 << 16;
+}
+
+namespace {
+
+void tsdf_release(bf_ctx *c) {
+  for (auto &a : c->tsdf_allocs) dfree(c, a.first, a.second);
+  c->tsdf_allocs.clear();
+  c->tsdf = TsdfDev{};
+  c->tsdf_on = false;
+  c->tsdf_integrated.clear();
+}
+
+TsdfPose tsdf_pose(const Pose12 &T) {
+  TsdfPose P;
+  for (int k = 0; k < 9; ++k) P.R[k] = (float)T[k];
+  for (int k = 0; k < 3; ++k) P.t[k] = (float)T[9 + k];
+  return P;
+}
+
+// One integrate (+1) or de-integrate (-1) of frame f at pose T; checks the device error bits.
+bf_status tsdf_apply(bf_ctx *c, int frame_id, const Pose12 &T, int sign) {
+  auto it = c->frames.find(frame_id);
+  if (it == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "TSDF: unknown frame id");
+  cudaStream_t st = c->ex->st;
+  CK(cudaMemsetAsync(c->tsdf.err, 0, sizeof(int), st), "TSDF");
+  const int call = ++c->tsdf_call;
+  run_k(c, BF_K_TSDF, [&] {
+    return launch_tsdf(c->tsdf, frame_store(c), c->intr, it->second.slot, tsdf_pose(T), sign, call, st);
+  });
+  CK(cudaGetLastError(), "TSDF launch");
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, c->tsdf.err, sizeof(int), cudaMemcpyDeviceToHost, st), "TSDF status");
+  CK(cudaStreamSynchronize(st), "TSDF");
+  if (err & 8) return fail(c, BF_ERR_INVALID_ARG, "TSDF: a point lies outside the addressable block range");
+  if (err) return fail(c, BF_ERR_OUT_OF_MEMORY, "TSDF: hash table or block pool full (raise table_log2 / max_blocks)");
+  return BF_OK;
+}
+
+// Sec. 5.3 distance: Euler angles R = Rz(g) Ry(b) Rx(a) and translation, weights (2,2,2,1,1,1)
+double tsdf_pose_distance(const Pose12 &A, const Pose12 &B) {
+  auto eul = [](const Pose12 &T, double *e) {
+    e[0] = std::atan2(T[7], T[8]);
+    e[1] = std::asin(std::max(-1.0, std::min(1.0, -T[6])));
+    e[2] = std::atan2(T[3], T[0]);
+  };
+  double ea[3], eb[3];
+  eul(A, ea);
+  eul(B, eb);
+  double s = 0.0;
+  for (int k = 0; k < 3; ++k) s += (2.0 * ea[k] - 2.0 * eb[k]) * (2.0 * ea[k] - 2.0 * eb[k]);
+  for (int k = 0; k < 3; ++k) s += (A[9 + k] - B[9 + k]) * (A[9 + k] - B[9 + k]);
+  return std::sqrt(s);
+}
+
+}  // namespace
+
+extern "C" bf_status bf_tsdf_init(bf_ctx *c, const bf_tsdf_config *cfg) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (!cfg || !(cfg->voxel_size > 0) || !std::isfinite(cfg->voxel_size) || cfg->trunc_voxels < 1 ||
+      cfg->trunc_voxels > 64 || cfg->table_log2 < 8 || cfg->table_log2 > 30 || cfg->max_blocks < 1 ||
+      cfg->max_blocks > (1 << 29))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_tsdf_init: bad configuration");
+  CK(cudaStreamSynchronize(c->ex->st), "TSDF init");
+  tsdf_release(c);
+  const size_t slots = (size_t)1 << cfg->table_log2, nb = (size_t)cfg->max_blocks;
+  TsdfDev &v = c->tsdf;
+  auto take = [&](void **p, size_t bytes) -> bf_status {
+    bf_status s = dalloc(c, p, bytes, "TSDF volume");
+    if (!s) c->tsdf_allocs.push_back({*p, bytes});
+    return s;
+  };
+  bf_status s;
+  if ((s = take((void **)&v.keys, slots * 8)) || (s = take((void **)&v.vals, slots * 4)) ||
+      (s = take((void **)&v.stamp, slots * 4)) || (s = take((void **)&v.touched, nb * 4)) ||
+      (s = take((void **)&v.n_touched, 16)) || (s = take((void **)&v.S, nb * 512 * 4)) ||
+      (s = take((void **)&v.W, nb * 512 * 4)) || (s = take((void **)&v.SC, nb * 512 * 4))) {
+    tsdf_release(c);
+    return s;
+  }
+  v.n_blocks = v.n_touched + 1;
+  v.err = v.n_touched + 2;
+  cudaStream_t st = c->ex->st;
+  CK(cudaMemsetAsync(v.keys, 0xff, slots * 8, st), "TSDF init");
+  CK(cudaMemsetAsync(v.vals, 0xff, slots * 4, st), "TSDF init");
+  CK(cudaMemsetAsync(v.stamp, 0, slots * 4, st), "TSDF init");
+  CK(cudaMemsetAsync(v.n_touched, 0, 16, st), "TSDF init");
+  CK(cudaStreamSynchronize(st), "TSDF init");
+  v.mask = (unsigned)(slots - 1);
+  v.max_blocks = cfg->max_blocks;
+  v.K = 2 * cfg->trunc_voxels;  // band samples every half voxel out to mu
+  v.h = (float)(0.5 * cfg->voxel_size);
+  v.mu = (float)(cfg->trunc_voxels * cfg->voxel_size);
+  v.inv_block = (float)(1.0 / (8.0 * cfg->voxel_size));
+  v.vs = (float)cfg->voxel_size;
+  v.inv_q = (float)1048576.0;
+  c->tsdf_cfg = *cfg;
+  c->tsdf_on = true;
+  c->tsdf_call = 0;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_tsdf_integrate(bf_ctx *c, int frame_id, const double *pose) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (!c->tsdf_on) return fail(c, BF_ERR_INVALID_ARG, "bf_tsdf_integrate: call bf_tsdf_init first");
+  if (c->tsdf_integrated.count(frame_id)) return fail(c, BF_ERR_INVALID_ARG, "bf_tsdf_integrate: frame already integrated");
+  if (!c->frames.count(frame_id)) return fail(c, BF_ERR_NOT_FOUND, "bf_tsdf_integrate: unknown frame id");
+  const Pose12 T = pose ? from16(pose) : world_of(c, frame_id);
+  bf_status s = tsdf_apply(c, frame_id, T, +1);
+  if (s) return s;
+  c->tsdf_integrated[frame_id] = T;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_tsdf_deintegrate(bf_ctx *c, int frame_id) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  auto it = c->tsdf_integrated.find(frame_id);
+  if (!c->tsdf_on || it == c->tsdf_integrated.end())
+    return fail(c, BF_ERR_NOT_FOUND, "bf_tsdf_deintegrate: frame not integrated");
+  bf_status s = tsdf_apply(c, frame_id, it->second, -1);
+  if (s) return s;
+  c->tsdf_integrated.erase(it);
+  return BF_OK;
+}
+
+extern "C" bf_status bf_tsdf_reintegrate(bf_ctx *c, int n_fix, int *frame_ids, int *n_done) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (!c->tsdf_on || n_fix < 0) return fail(c, BF_ERR_INVALID_ARG, "bf_tsdf_reintegrate: bad arguments");
+  std::vector<std::pair<double, int>> order;  // (-distance, id): descending distance, ties by id
+  for (auto &kv : c->tsdf_integrated) {
+    const double d = tsdf_pose_distance(kv.second, world_of(c, kv.first));
+    if (d > 0) order.push_back({-d, kv.first});
+  }
+  std::sort(order.begin(), order.end());
+  int done = 0;
+  for (const auto &o : order) {
+    if (done >= n_fix) break;
+    const int f = o.second;
+    const Pose12 opt = world_of(c, f);
+    bf_status s = tsdf_apply(c, f, c->tsdf_integrated[f], -1);
+    if (s) return s;
+    s = tsdf_apply(c, f, opt, +1);
+    if (s) return s;
+    c->tsdf_integrated[f] = opt;
+    if (frame_ids) frame_ids[done] = f;
+    ++done;
+  }
+  if (n_done) *n_done = done;
+  return BF_OK;
+}
+
+extern "C" bf_status bf_tsdf_export(bf_ctx *c, long long capacity, int *block_coords, int *sums, long long *n) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  if (!c->tsdf_on || !n || capacity < 0 || (capacity > 0 && (!block_coords || !sums)))
+    return fail(c, BF_ERR_INVALID_ARG, "bf_tsdf_export: bad arguments");
+  const TsdfDev &v = c->tsdf;
+  const size_t slots = (size_t)v.mask + 1;
+  cudaStream_t st = c->ex->st;
+  std::vector<unsigned long long> keys(slots);
+  std::vector<int> vals(slots);
+  int nb = 0;
+  CK(cudaMemcpyAsync(keys.data(), v.keys, slots * 8, cudaMemcpyDeviceToHost, st), "TSDF export");
+  CK(cudaMemcpyAsync(vals.data(), v.vals, slots * 4, cudaMemcpyDeviceToHost, st), "TSDF export");
+  CK(cudaMemcpyAsync(&nb, v.n_blocks, sizeof(int), cudaMemcpyDeviceToHost, st), "TSDF export");
+  CK(cudaStreamSynchronize(st), "TSDF export");
+  std::vector<std::pair<unsigned long long, int>> blocks;
+  for (size_t h = 0; h < slots; ++h)
+    if (keys[h] != ~0ull && vals[h] >= 0) blocks.push_back({keys[h], vals[h] & ((1 << 30) - 1)});
+  std::sort(blocks.begin(), blocks.end());
+  *n = (long long)blocks.size();
+  const long long m = std::min<long long>(capacity, (long long)blocks.size());
+  if (m == 0) return BF_OK;
+  nb = std::min(nb, v.max_blocks);
+  std::vector<int> S((size_t)nb * 512), W((size_t)nb * 512), SC((size_t)nb * 512);
+  CK(cudaMemcpyAsync(S.data(), v.S, S.size() * 4, cudaMemcpyDeviceToHost, st), "TSDF export");
+  CK(cudaMemcpyAsync(W.data(), v.W, W.size() * 4, cudaMemcpyDeviceToHost, st), "TSDF export");
+  CK(cudaMemcpyAsync(SC.data(), v.SC, SC.size() * 4, cudaMemcpyDeviceToHost, st), "TSDF export");
+  CK(cudaStreamSynchronize(st), "TSDF export");
+  for (long long k = 0; k < m; ++k) {
+    const unsigned long long key = blocks[k].first;
+    block_coords[3 * k] = (int)((key >> 42) & 0x1fffff) - (1 << 20);
+    block_coords[3 * k + 1] = (int)((key >> 21) & 0x1fffff) - (1 << 20);
+    block_coords[3 * k + 2] = (int)(key & 0x1fffff) - (1 << 20);
+    const size_t b = (size_t)blocks[k].second * 512;
+    std::memcpy(sums + (size_t)k * 1536, S.data() + b, 512 * 4);
+    std::memcpy(sums + (size_t)k * 1536 + 512, W.data() + b, 512 * 4);
+    std::memcpy(sums + (size_t)k * 1536 + 1024, SC.data() + b, 512 * 4);
+  }
+  return BF_OK;
 }
 
 // ------------------------------------------------------------------- key-point filter

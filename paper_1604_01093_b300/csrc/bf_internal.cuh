@@ -280,6 +280,25 @@ int launch_keypoints(int n_pairs, const int *off, const float *P, const float *Q
 // Bounded-wait self-test: which = 0 polls *word (which stays 0), 1 waits on an mbarrier nothing
 // arrives on; *err = 1 when the wait gave up after `limit` polls.
 int launch_selftest_wait(int which, const unsigned *word, int *err, long long limit, cudaStream_t st);
+// TSDF volume on the device (Sec. 5): hash table of packed block coordinates, block pool of
+// integer sums, the touched list of the current call, counters and the error bits
+// (1 probe limit, 2 pool full, 4 touched list full, 8 block coordinate out of range).
+struct TsdfDev {
+  unsigned long long *keys;  // [mask + 1], ~0 = empty
+  int *vals;                 // [mask + 1], pool record (bit 30: fresh), -1 = none
+  int *stamp;                // [mask + 1], id of the last call that touched the slot
+  int *touched;              // [max_blocks] slots touched by the current call
+  int *n_touched, *n_blocks, *err;
+  int *S, *W, *SC;           // [max_blocks][512]
+  unsigned mask;
+  int max_blocks, K;
+  float h, mu, inv_block, vs, inv_q;
+};
+struct TsdfPose {
+  float R[9], t[3];  // camera -> world, rounded to FP32
+};
+int launch_tsdf(const TsdfDev &v, const FrameStore &fs, const Intr &in, int slot, const TsdfPose &P, int sign,
+                int call_id, cudaStream_t st);
 int launch_preprocess(const float *depth, const float *lum, int n, const int *slots_dev, FrameStore fs,
                        float4 *A, float4 *B, uint4 *P16, unsigned short *C16, float dmin, float dmax,
                        cudaStream_t st);
