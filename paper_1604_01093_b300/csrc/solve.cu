@@ -133,48 +133,48 @@ __device__ __forceinline__ void slot_source(int s, bool src_is_a, int &idx, int 
 
 constexpr int MERGE_WARPS = 1;  // one warp per CTA spreads the pairs over the SMs
 
+// One warp per pair.  The pair's record combines up to three sources: the dense direction a -> b
+// and the sparse segments (both evaluated in camera-b coordinates, source a), and the dense
+// direction b -> a (camera a, source b).  Sources that share a target camera are summed in the
+// NPART layout first and rotated to world coordinates once, R X R^T in two 3-FMA stages
+// (X R^T, then R (X R^T)); B300 issues FP64 at 1/64 of the FP32 rate, so the merge is bound by
+// its FP64 instruction count.
 template <typename Acc, typename Part>
 __global__ void __launch_bounds__(32 * MERGE_WARPS)
     k_pair_merge(Tables t, const double *__restrict__ pose, const Part *__restrict__ dpart,
                  const Part *__restrict__ spart, Acc *__restrict__ pairblk, Acc *__restrict__ pairen,
                  float *__restrict__ pairoff) {
   __shared__ Acc S_sh[MERGE_WARPS][NPART + 7];
+  __shared__ Acc T_sh[MERGE_WARPS][54];
   __shared__ Acc rot_sh[MERGE_WARPS][NROT + 1];
   __shared__ Acc R_sh[MERGE_WARPS][9];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int p = blockIdx.x * MERGE_WARPS + w;
   if (p >= t.n_pairs) return;  // whole warp exits together
   Acc *S = S_sh[w];
+  Acc *T = T_sh[w];
   Acc *rot = rot_sh[w];
   Acc *R = R_sh[w];
   Acc out[4] = {0, 0, 0, 0};  // slots lane, lane+32, lane+64, lane+96
   Acc en[4] = {0, 0, 0, 0};   // kept by lane 0: e_sparse, e_photo, e_geo, n_dense
-  for (int src = 0; src < 3; ++src) {
-    // src 0: dense a->b (target b), 1: dense b->a (target a), 2: sparse (target b, source a)
-    int k0, k1;
-    const Part *base;
-    if (src < 2) {
-      const int d = t.pair_dp[2 * p + src];
-      if (d < 0) continue;
-      k0 = t.dp_tile0[d];
-      k1 = t.dp_tile1[d];
-      base = dpart;
-    } else {
-      k0 = t.pair_seg0[p];
-      k1 = t.pair_seg1[p];
-      base = spart;
-      if (k1 <= k0) continue;
-    }
-    const int tgt = (src == 1) ? t.pair_a[p] : t.pair_b[p];
-    const int srcf = (src == 1) ? t.pair_b[p] : t.pair_a[p];
+  for (int half = 0; half < 2; ++half) {
+    // half 0: target b (dense a -> b and the sparse segments); half 1: target a (dense b -> a)
+    const int d = t.pair_dp[2 * p + half];
+    const bool has_sparse = half == 0 && t.pair_seg1[p] > t.pair_seg0[p];
+    if (d < 0 && !has_sparse) continue;
+    const int tgt = half == 1 ? t.pair_a[p] : t.pair_b[p];
+    const int srcf = half == 1 ? t.pair_b[p] : t.pair_a[p];
     if (lane < 9) R[lane] = (Acc)pose[12 * tgt + lane];
-    if (src < 2) {
+    for (int k = lane; k < NPART; k += 32) S[k] = 0;
+    __syncwarp();
+    if (d >= 0) {
       // dense: sum the tiles' v / c sums (fixed order), then rebuild the a-sums with
       // a = T v - c, T v = v x t, t = t_ji = R_j^T (t_i - t_j)
+      const int k0 = t.dp_tile0[d], k1 = t.dp_tile1[d];
       Acc *Sd = rot;  // scratch for the NPD sums
       for (int k = lane; k < NPD; k += 32) {
         Acc s = 0;
-        for (int it = k0; it < k1; ++it) s += (Acc)base[(long long)it * NPD + k];
+        for (int it = k0; it < k1; ++it) s += (Acc)dpart[(long long)it * NPD + k];
         Sd[k] = s;
       }
       __syncwarp();
@@ -186,7 +186,6 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
         for (int m = 0; m < 3; ++m) tt[m] = (Acc)(Tj[m] * d0 + Tj[3 + m] * d1 + Tj[6 + m] * d2);
       }
       const Acc T3[3][3] = {{0, tt[2], -tt[1]}, {-tt[2], 0, tt[0]}, {tt[1], -tt[0], 0}};
-      // copy the v / c sums into the NPART layout
       for (int k = lane; k < 6; k += 32) {
         S[P_VV + k] = Sd[D_VV + k];
         S[P_CC + k] = Sd[D_CC + k];
@@ -197,9 +196,9 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
         S[P_GC + lane] = Sd[D_GC + lane];
       }
       if (lane == 0) {
-        S[P_E0] = Sd[D_E0];
-        S[P_E1] = Sd[D_E1];
-        S[P_CNT] = Sd[D_CNT];
+        en[2] += Sd[D_E0];
+        en[1] += Sd[D_E1];
+        en[3] += Sd[D_CNT];
       }
       __syncwarp();
       // S_av = T S_vv - S_vc^T ; S_ac = T S_vc - S_cc ; g_a = T g_v - g_c
@@ -227,27 +226,32 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
         for (int k = 0; k < 3; ++k) aa += S[P_AV + 3 * i + k] * T3[j][k];
         S[P_AA + lane] = aa;
       }
-    } else {
-      // sparse: full NPART sums per segment (fixed order)
+      __syncwarp();
+    }
+    if (has_sparse) {
+      // sparse: full NPART sums per segment (fixed order), added to the dense ones
+      const int k0 = t.pair_seg0[p], k1 = t.pair_seg1[p];
       for (int k = lane; k < NPART; k += 32) {
         Acc s = 0;
-        for (int it = k0; it < k1; ++it) s += (Acc)base[(long long)it * NPART + k];
-        S[k] = s;
+        for (int it = k0; it < k1; ++it) s += (Acc)spart[(long long)it * NPART + k];
+        if (k == P_E0) S[NPART] = s;  // the sparse energy, read by lane 0 below
+        S[k] += s;
       }
+      __syncwarp();
+      if (lane == 0) en[0] += S[NPART];
+    }
+    // rotate to world: T_blk = X_blk R^T, then R T_blk; vectors R g
+    for (int e = lane; e < 54; e += 32) {
+      const int blk = e / 9, m = (e % 9) / 3, j = e % 3;
+      T[e] = S[part_index(blk, m, 0)] * R[3 * j] + S[part_index(blk, m, 1)] * R[3 * j + 1] +
+             S[part_index(blk, m, 2)] * R[3 * j + 2];
     }
     __syncwarp();
-    // rotate to world: blocks R X R^T, vectors R g
     for (int e = lane; e < NROT; e += 32) {
-      Acc v = 0;
+      Acc v;
       if (e < 54) {
         const int blk = e / 9, i = (e % 9) / 3, j = e % 3;
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          Acc tm = 0;
-#pragma unroll
-          for (int n = 0; n < 3; ++n) tm += S[part_index(blk, m, n)] * R[3 * j + n];
-          v += R[3 * i + m] * tm;
-        }
+        v = R[3 * i] * T[9 * blk + j] + R[3 * i + 1] * T[9 * blk + 3 + j] + R[3 * i + 2] * T[9 * blk + 6 + j];
       } else {
         const int vec = (e - 54) / 3, i = (e - 54) % 3;
         const int off = vec == 0 ? P_GA : (vec == 1 ? P_GV : P_GC);
@@ -256,24 +260,15 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
       rot[e] = v;
     }
     __syncwarp();
-    const bool src_is_a = (src != 1);
+    const bool src_is_a = half == 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int s = lane + 32 * q;
-      if (s < PAIRBLK) {
+      const int sl = lane + 32 * q;
+      if (sl < PAIRBLK) {
         int idx, sign;
-        slot_source(s, src_is_a, idx, sign);
+        slot_source(sl, src_is_a, idx, sign);
         if (sign > 0) out[q] += rot[idx];
         else if (sign < 0) out[q] -= rot[idx];
-      }
-    }
-    if (lane == 0) {
-      if (src < 2) {
-        en[2] += S[P_E0];
-        en[1] += S[P_E1];
-        en[3] += S[P_CNT];
-      } else {
-        en[0] += S[P_E0];
       }
     }
     __syncwarp();
@@ -281,10 +276,10 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
   Acc *o = pairblk + (long long)p * PAIRBLK;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const int s = lane + 32 * q;
-    if (s < PAIRBLK) {
-      o[s] = out[q];
-      if (s >= PB_AB && s < PB_AB + 36) pairoff[(long long)p * 36 + s - PB_AB] = (float)out[q];
+    const int sl = lane + 32 * q;
+    if (sl < PAIRBLK) {
+      o[sl] = out[q];
+      if (sl >= PB_AB && sl < PB_AB + 36) pairoff[(long long)p * 36 + sl - PB_AB] = (float)out[q];
     }
   }
   if (lane == 0) {
@@ -381,14 +376,25 @@ __global__ void __launch_bounds__(32 * ASM_WARPS)
   const int v = blockIdx.x * ASM_WARPS + w;
   if (v >= t.n_vars) return;
   const int e0 = t.inc_off[v], e1 = t.inc_off[v + 1];
-  // lane handles entries lane and lane + 32 of [D (36) | rhs (6)]
+  // lane handles entries lane and lane + 32 of [D (36) | rhs (6)]; the incidences are read 8 at
+  // a time (all loads in flight together) and summed in incidence order
   for (int k = lane; k < 42; k += 32) {
     Acc s = 0;
-    for (int e = e0; e < e1; ++e) {
-      const int ent = t.inc[e];
-      const int p = ent >> 1, side = ent & 1;
-      const Acc *b = pairblk + (long long)p * PAIRBLK;
-      s += k < 36 ? b[(side == 0 ? PB_AA : PB_BB) + k] : b[(side == 0 ? PB_RA : PB_RB) + k - 36];
+    for (int e = e0; e < e1; e += 8) {
+      Acc v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        v[u] = 0;
+        if (e + u < e1) {
+          const int ent = t.inc[e + u];
+          const int p = ent >> 1, side = ent & 1;
+          const Acc *b = pairblk + (long long)p * PAIRBLK;
+          v[u] = k < 36 ? b[(side == 0 ? PB_AA : PB_BB) + k] : b[(side == 0 ? PB_RA : PB_RB) + k - 36];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e + u < e1) s += v[u];
     }
     if (k < 36) {
       Dd[(long long)v * 36 + k] = s;
@@ -1032,17 +1038,20 @@ __device__ __forceinline__ Acc cluster_total(cgx::cluster_group &cluster, Acc *p
   return s;
 }
 
-// Fixed-order CTA sum of one value per warp (lane 0 holds it) into part[k].
+// Fixed-order CTA sum of one FP32 value per warp (lane 0 holds it) into part[k]: a butterfly
+// over the CL_WARPS values in warp 0 (FP32), then one conversion; FP64 starts at the sum over
+// the cluster's CTAs.
 template <typename Acc>
-__device__ __forceinline__ void cluster_partial(Acc v, Acc *wsum, Acc *part, int k) {
+__device__ __forceinline__ void cluster_partial(float v, float *wsum, Acc *part, int k) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) wsum[warp] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    Acc s = 0;
-    for (int w = 0; w < CL_WARPS; ++w) s += wsum[w];
-    part[k] = s;
+  if (warp == 0) {
+    float s = lane < CL_WARPS ? wsum[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) part[k] = (Acc)s;
   }
 }
 
@@ -1094,7 +1103,7 @@ __global__ void __launch_bounds__(CL_BS, 1)
   float *sM = sD + 36 * per;
   float *sB = sM + 36 * per;
   int *sov = (int *)(sB + 36 * (size_t)L.max_inc);
-  __shared__ Acc wsum[CL_WARPS];
+  __shared__ float wsum[CL_WARPS];
   const int e_base = t.inc_off[v0 + o0];
   if (threadIdx.x < CL) zp_rank[threadIdx.x] = (const float4 *)cluster.map_shared_rank(zp, (int)threadIdx.x);
   if (L.cache) {
@@ -1141,7 +1150,7 @@ __global__ void __launch_bounds__(CL_BS, 1)
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
-  cluster_partial((Acc)loc, wsum, part, 1);
+  cluster_partial<Acc>(loc, wsum, part, 1);
   cluster.sync();  // all CTAs running, owned z / p initialised
   __shared__ PcgScal S;
   Acc rz = 0;  // meaningful in thread 0, which runs the scalar recurrences
@@ -1235,7 +1244,7 @@ __global__ void __launch_bounds__(CL_BS, 1)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lpq += __shfl_xor_sync(0xffffffffu, lpq, o);
-    cluster_partial((Acc)lpq, wsum, part, 0);
+    cluster_partial<Acc>(lpq, wsum, part, 0);
     cluster.sync();  // every CTA has finished reading the old z / p
     if (warp == 0) {
       const Acc pq = cluster_total(cluster, part, 0, CL);
@@ -1267,7 +1276,7 @@ __global__ void __launch_bounds__(CL_BS, 1)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lrz += __shfl_xor_sync(0xffffffffu, lrz, o);
-    cluster_partial((Acc)lrz, wsum, part, 1);
+    cluster_partial<Acc>(lrz, wsum, part, 1);
     cluster.sync();  // the new z / p are visible cluster-wide
     if (warp == 0) {
       const Acc rz_new = cluster_total(cluster, part, 1, CL);
