@@ -773,7 +773,7 @@ struct HostTables {
   std::vector<long long> prob_ncorr;
 };
 
-constexpr int STAGED_PAIRS_PER_ITEM = 4;
+constexpr int STAGED_PAIRS_PER_ITEM = 6;
 
 // Build the flattened tables of a set of problems.  force_dense: every pair gets both dense
 // directions (debug), else the Sec. 4.3 angle test on the initial poses selects E.
@@ -1121,6 +1121,10 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
     dfree(c, c->ex->ws, c->ex->ws_bytes);
     c->ex->ws = nullptr;
     c->ex->ws_bytes = 0;
+    // the new allocation may come back at the old address with other contents: forget what the
+    // old workspace held so the tables are uploaded again
+    c->ex->last_ws = nullptr;
+    c->ex->last_ints.clear();
     bf_status s = dalloc(c, (void **)&c->ex->ws, nb, "solve workspace");
     if (s) return s;
     c->ex->ws_bytes = nb;

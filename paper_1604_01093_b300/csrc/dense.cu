@@ -264,7 +264,7 @@ int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in
 // one-CTA-per-SM grid stays balanced); the CTA's 16 warps form 4 quads and each quad
 // evaluates one directed pair at a time (fixed lane-strided pixel order, quad tree reduction,
 // one partial per directed pair).
-constexpr int STG_BS = 512;
+constexpr int STG_BS = 768;
 constexpr int STG_QUADS = STG_BS / 128;
 constexpr int STG_MAX_SMEM = 200 * 1024;
 constexpr long long STG_WAIT_LIMIT = 1LL << 22;

@@ -418,3 +418,28 @@ def test_bounded_waits_give_up_and_the_context_survives(bf, cfg1, which):
     assert status == 6 and gave_up == 1  # BF_ERR_TIMEOUT
     st = ctx.solve_local(0, list(range(11)), n_gn=1, n_pcg=4)
     assert st["n_gn"] == 1 and np.isfinite(st["energy"]).all()
+
+
+def test_workspace_growth_reuploads_tables(bf):
+    """A solve that needs a larger workspace than the previous one (here: the grid-cooperative PCG
+    after the cluster PCG) gets its tables uploaded again even if the new allocation lands at the
+    old address; its result equals the same solve on a fresh context."""
+    prob = synth.cfg2()
+    n = prob.n_frames
+
+    def ctx_for():
+        intr = prob.intr
+        c = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], max_frames_hint=n)
+        c.add_frames(0, prob.depth, prob.lum, init_pose=prob.init)
+        c.add_correspondences_batch(prob.pairs, prob.corr_off, prob.p_i, prob.p_j)
+        return c
+
+    kw = dict(n_gn=2, n_pcg=5, w_dense=0.5)
+    ref = ctx_for().solve_global(list(range(n)), pcg_variant=2, **kw)
+    ctx = ctx_for()
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    ctx.solve_global(list(range(n)), pcg_variant=3, **kw)
+    ctx.add_frames(0, prob.depth, prob.lum, init_pose=prob.init)
+    st = ctx.solve_global(list(range(n)), pcg_variant=2, **kw)
+    assert st["energy"] == ref["energy"] and st["flags"] == 0
