@@ -1026,6 +1026,7 @@ template int launch_pcg_coop<float>(const Tables &, const float *, const float *
 // partials are read from the other CTAs' shared memory and summed in rank order.
 constexpr int CL_BS = 512;
 constexpr int CL_WARPS = CL_BS / 32;
+constexpr int CL_G = 16;  // lanes per frame in the matvec
 
 // Sum of the CL per-CTA partials (slot k of each CTA's part array), read lane-parallel from the
 // cluster's shared memory and combined by a butterfly: identical in every lane of every CTA.
@@ -1083,11 +1084,33 @@ __global__ void __launch_bounds__(CL_BS, 1)
                   int *__restrict__ pflags, ClusterLayout L, const Acc *__restrict__ pairen, PcgOut po) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ const float4 *zp_rank[16];
-  __shared__ Acc esh[EN_BS / 32][PAIREN];
+  __shared__ Acc esh[CL_WARPS][PAIREN];
+  __shared__ Acc eslice[PAIREN];
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
-  if (rank == 0 && po.energy) problem_energy<Acc>(t, pairen, 0, po.energy, esh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (po.energy) {
+    // this CTA's slice of the energy record: its share of the pairs, strided over threads, warp
+    // trees, warps in order; rank 0 adds the slices in rank order after the first barrier
+    const int p0 = t.prob_pair0[0], np = t.prob_pair1[0] - p0, chunk = (np + CL - 1) / CL;
+    const int pa = p0 + min(np, rank * chunk), pb = p0 + min(np, (rank + 1) * chunk);
+    Acc es[PAIREN] = {0, 0, 0, 0};
+    for (int q = pa + threadIdx.x; q < pb; q += CL_BS)
+#pragma unroll
+      for (int c = 0; c < PAIREN; ++c) es[c] += pairen[(long long)q * PAIREN + c];
+#pragma unroll
+    for (int c = 0; c < PAIREN; ++c) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) es[c] += __shfl_xor_sync(0xffffffffu, es[c], o);
+      if (lane == 0) esh[warp][c] = es[c];
+    }
+    __syncthreads();
+    if (threadIdx.x < PAIREN) {
+      Acc v = 0;
+      for (int w = 0; w < CL_WARPS; ++w) v += esh[w][threadIdx.x];
+      eslice[threadIdx.x] = v;
+    }
+  }
   const int v0 = t.prob_var0[0], v1 = t.prob_var1[0];
   const int nv = v1 - v0;
   const int per = L.per;
@@ -1111,33 +1134,50 @@ __global__ void __launch_bounds__(CL_BS, 1)
       sD[u] = Df[(long long)(v0 + o0) * 36 + u];
       sM[u] = Minv[(long long)(v0 + o0) * 36 + u];
     }
+    // one thread per incidence: its block as 9 independent 16-byte loads, stored pre-transposed
     const int n_inc = t.inc_off[v0 + o1] - e_base;
-    for (int u = threadIdx.x; u < 36 * n_inc; u += CL_BS) {
-      const int e = u / 36, k = u % 36;
-      const int ent = t.inc[e_base + e];
-      const int pr = ent >> 1, side = ent & 1;
-      const int c = k / 6, j = k % 6;
-      sB[u] = side == 0 ? pairoff[(long long)pr * 36 + 6 * c + j] : pairoff[(long long)pr * 36 + 6 * j + c];
-    }
     for (int e = threadIdx.x; e < n_inc; e += CL_BS) {
+      const int ent = t.inc[e_base + e];
       const int ov = t.inc_ov[e_base + e];
+      const float4 *O4 = (const float4 *)(pairoff + (long long)(ent >> 1) * 36);
+      float o[36];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const float4 v4 = O4[q];
+        o[4 * q] = v4.x;
+        o[4 * q + 1] = v4.y;
+        o[4 * q + 2] = v4.z;
+        o[4 * q + 3] = v4.w;
+      }
+      float *dst = sB + 36 * e;
+      if ((ent & 1) == 0) {
+#pragma unroll
+        for (int q = 0; q < 36; ++q) dst[q] = o[q];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+          for (int j = 0; j < 6; ++j) dst[6 * c + j] = o[6 * j + c];
+      }
       const int lo = ov - v0;
       sov[e] = ov < 0 ? -1 : (((lo / per) << 16) | (lo % per));
     }
   }
-  // Frames are processed by 8-lane groups: group g of a warp owns frame base + g; within a group
-  // lane gl walks the frame's incidences gl, gl+8, ... and lanes gl < 6 own the frame's 6 rows.
-  const int g = lane >> 3, gl = lane & 7;
+  // Frames are processed by CL_G-lane groups: group g of a warp owns frame base + g; within a
+  // group lane gl walks the frame's incidences gl, gl + CL_G, ... and lanes gl < 6 own the
+  // frame's 6 rows.
+  constexpr int GPW = 32 / CL_G;  // groups per warp
+  const int g = lane / CL_G, gl = lane % CL_G, gbase = lane & ~(CL_G - 1);
   // init: x = 0, r = b, z = M^-1 r, p = 0 for owned frames
   float loc = 0.f;
-  for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
+  for (int base = o0 + GPW * warp; base < o1; base += GPW * CL_WARPS) {
     const int lv = base + g;
     const bool valid = lv < o1;
     const int v = v0 + lv, k = lv - o0;
     const float rown = (valid && gl < 6) ? (float)rhs[6 * v + gl] : 0.f;
     float rr[6];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) rr[c] = __shfl_sync(0xffffffffu, rown, (lane & ~7) + c);
+    for (int c = 0; c < 6; ++c) rr[c] = __shfl_sync(0xffffffffu, rown, gbase + c);
     if (valid && gl < 6) {
       const float *M = L.cache ? sM + 36 * k + 6 * gl : Minv + (long long)v * 36 + 6 * gl;
       const float zl = M[0] * rr[0] + M[1] * rr[1] + M[2] * rr[2] + M[3] * rr[3] + M[4] * rr[4] + M[5] * rr[5];
@@ -1151,7 +1191,12 @@ __global__ void __launch_bounds__(CL_BS, 1)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
   cluster_partial<Acc>(loc, wsum, part, 1);
-  cluster.sync();  // all CTAs running, owned z / p initialised
+  cluster.sync();  // all CTAs running, owned z / p initialised, energy slices ready
+  if (po.energy && rank == 0 && threadIdx.x < PAIREN) {
+    Acc v = 0;
+    for (int r = 0; r < CL; ++r) v += cluster.map_shared_rank(eslice, r)[threadIdx.x];
+    po.energy[threadIdx.x] = (double)v;
+  }
   __shared__ PcgScal S;
   Acc rz = 0;  // meaningful in thread 0, which runs the scalar recurrences
   if (warp == 0) {
@@ -1169,14 +1214,14 @@ __global__ void __launch_bounds__(CL_BS, 1)
     const float fb = S.fb;
     // Phase A: p_new = z + beta p (owned, kept in opn); q = A p_new, neighbours read remotely
     float lpq = 0.f;
-    for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
+    for (int base = o0 + GPW * warp; base < o1; base += GPW * CL_WARPS) {
       const int lv = base + g;
       const bool valid = lv < o1;
       const int v = v0 + lv, k = lv - o0;
       float acc[6] = {0, 0, 0, 0, 0, 0};
       if (valid) {
         const int e0 = t.inc_off[v], e1 = t.inc_off[v + 1];
-        for (int e = e0 + gl; e < e1; e += 8) {
+        for (int e = e0 + gl; e < e1; e += CL_G) {
           int owner, idx;
           const float *B;
           bool trans = false;
@@ -1220,9 +1265,8 @@ __global__ void __launch_bounds__(CL_BS, 1)
       }
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
-        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 4);
-        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
-        acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+#pragma unroll
+        for (int o = CL_G / 2; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
       }
       if (valid && gl < 6) {
         float mine = acc[0];
@@ -1255,14 +1299,14 @@ __global__ void __launch_bounds__(CL_BS, 1)
     const float fa = S.fa;
     // Phase B (local): x += alpha p_new, r -= alpha q, z = M^-1 r, p = p_new
     float lrz = 0.f;
-    for (int base = o0 + 4 * warp; base < o1; base += 4 * CL_WARPS) {
+    for (int base = o0 + GPW * warp; base < o1; base += GPW * CL_WARPS) {
       const int lv = base + g;
       const bool valid = lv < o1;
       const int v = v0 + lv, k = lv - o0;
       const float rn_own = (valid && gl < 6) ? orr[6 * k + gl] - fa * oq[6 * k + gl] : 0.f;
       float rn[6];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) rn[c] = __shfl_sync(0xffffffffu, rn_own, (lane & ~7) + c);
+      for (int c = 0; c < 6; ++c) rn[c] = __shfl_sync(0xffffffffu, rn_own, gbase + c);
       if (valid && gl < 6) {
         const float *M = L.cache ? sM + 36 * k + 6 * gl : Minv + (long long)v * 36 + 6 * gl;
         const float zl = M[0] * rn[0] + M[1] * rn[1] + M[2] * rn[2] + M[3] * rn[3] + M[4] * rn[4] + M[5] * rn[5];
