@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--tile-px", type=int, default=0,
                     help="dense work item size in source pixels; 0 = automatic (target frame staged in shared memory)")
+    ap.add_argument("--next-rows-only", action="store_true",
+                    help="run only the pruning / verification / key-point / TSDF legs (one JSON line)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
                     help="frame storage of the timed workload (16-bit: normals, I, grad I)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1, 2, 3],
@@ -221,6 +223,12 @@ def run_ours(args, rank, world, local_rank):
     intr = prob.intr
     n = prob.n_frames
     ids = list(range(n))
+    if args.next_rows_only:
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(stream)
+        if rank == 0:
+            print(json.dumps({"next_rows": next_rows_leg(bf, torch, dev, stream, prob, prm)}), flush=True)
+        return
     precision = bf.BF_PREC_MIXED if args.precision == "mixed" else bf.BF_PREC_FP32
     params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
                                w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
@@ -394,6 +402,8 @@ def run_ours(args, rank, world, local_rank):
         line["chunk_batch_bf16"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob, storage="bf16")
         line["serving"] = serving_leg(bf, torch, dev, cprob, prob)
 
+        line["next_rows"] = next_rows_leg(bf, torch, dev, stream, prob, prm)
+
         v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
@@ -445,6 +455,80 @@ def storage_leg(bf, torch, dev, stream, prob, params, prof_params, kind, steps=5
             "dense_algorithmic_GBps": dense_bytes_per_px(kind) * units / (dense_ms / 1000.0) / 1e9,
             "frame_bytes": int(n * intr["W"] * intr["H"] * 16)}
 
+
+
+def next_rows_leg(bf, torch, dev, stream, prob, prm):
+    """The steps around the solver on the 300-keyframe workload (Sec. 4.1.1, 4.4.1, 5).
+
+    verify: every pair, both directions, at the ground-truth relative poses (one launch);
+    keypoints: every pair's matches through the key-point and surface-area filters (one launch);
+    pruning: the global solve with r_max pruning at 0.05 m (the workload has 5 % random outliers,
+    so pairs are pruned until the round cap); tsdf: the 300 frames integrated then de-integrated
+    (1 cm voxels)."""
+    import numpy as np
+    intr = prob.intr
+    n = prob.n_frames
+    ids = list(range(n))
+    out = {}
+
+    def ctx_new():
+        c = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], stream=stream.cuda_stream,
+                       max_frames_hint=n)
+        c.add_frames(0, torch.from_numpy(prob.depth).to(dev), torch.from_numpy(prob.lum).to(dev),
+                     init_pose=prob.gt)
+        return c
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) / reps, r
+
+    ctx = ctx_new()
+    pairs = np.asarray(prob.pairs, dtype=np.int32)
+    rel = np.stack([np.linalg.inv(prob.gt[j]) @ prob.gt[i] for i, j in pairs])
+    HW = intr["W"] * intr["H"]
+    t, res = timed(lambda: ctx.verify_pairs(pairs, rel), 5)
+    out["verify"] = {"pairs": len(pairs), "ms_per_call": 1e3 * t, "pairs_per_s": len(pairs) / t,
+                     "valid_pairs": int(sum(r["valid"] for r in res)),
+                     "algorithmic_GBps": 2 * len(pairs) * HW * 36 / t / 1e9,
+                     "note": "host call incl. record upload and result read-back; 36 B per directed pixel"}
+    t, (keep, T, status) = timed(lambda: ctx.filter_keypoints(prob.corr_off.astype(np.int32), prob.p_i, prob.p_j),
+                                 3)
+    out["keypoints"] = {"pairs": len(pairs), "matches": int(prob.corr_off[-1]), "ms_per_call": 1e3 * t,
+                        "pairs_per_s": len(pairs) / t, "kept_pairs": int((status == 0).sum()),
+                        "kept_matches": int(keep.sum()), "arithmetic": "FP64, one warp per pair"}
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, prob.p_i, prob.p_j)
+    ctx.add_frames(0, torch.from_numpy(prob.depth).to(dev), torch.from_numpy(prob.lum).to(dev), init_pose=prob.init)
+    pp = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"], w_dense=prm["w_dense"],
+                           w_photo=prm["w_photo"], w_geo=prm["w_geo"], prune_rmax=0.05, prune_rounds=8)
+    t0 = time.perf_counter()
+    st = ctx.solve_global(ids, pp)
+    t = time.perf_counter() - t0
+    out["pruning"] = {"solves": st["solves"], "pruned_pairs": st["n_pruned"], "invalid_frames": st["n_invalid"],
+                      "ms_total": 1e3 * t, "final_r_max": st["r_max"], "gn_iterations_per_s": st["solves"] * prm["n_gn"] / t}
+    ctx.close()
+    ctx = ctx_new()
+    ctx.tsdf_init(voxel_size=0.01, table_log2=21, max_blocks=1 << 17)
+
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(n):
+        ctx.tsdf_integrate(k)  # at the frame's world pose
+    t_in = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for k in range(n):
+        ctx.tsdf_deintegrate(k)
+    t_de = time.perf_counter() - t0
+    blocks = len(ctx.tsdf_export())
+    out["tsdf"] = {"frames": n, "voxel_m": 0.01, "blocks": blocks, "integrate_ms_per_frame": 1e3 * t_in / n,
+                   "deintegrate_ms_per_frame": 1e3 * t_de / n, "frames_per_s": n / t_in,
+                   "note": "synchronous calls (status read back per frame)"}
+    ctx.close()
+    return out
 
 def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None, storage="fp32"):
     """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.
