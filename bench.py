@@ -533,9 +533,9 @@ def next_rows_leg(bf, torch, dev, stream, prob, prm):
 def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None, storage="fp32"):
     """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.
 
-    batched: all chunks in one launch sequence (one problem per chunk), mixed precision, replayed
-    as a CUDA graph; plain: one FP32 solve per chunk, kernel by kernel, no graph (FP32 storage
-    only).  Each step re-runs frame preprocessing from device-resident raw frames.  Chunk-solve
+    batched: all chunks in one launch sequence (one problem per chunk), replayed as a CUDA graph;
+    plain: one solve per chunk, kernel by kernel, no graph (FP32 storage only); FP32 arithmetic
+    with pairwise sums in both.  Each step re-runs frame preprocessing from device-resident raw frames.  Chunk-solve
     latency: call -> poses on the host; in the batched mode every chunk completes with its batch."""
     import synth
     prob = prob or synth.cfg3(n_chunks=n_chunks)
@@ -550,7 +550,10 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
     ids = list(range(len(prob.chunks)))
     lists = [c.tolist() for c in prob.chunks]
     common = {k: prm[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
-    pb = bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=1, **common)
+    # chunk solves in FP32 arithmetic with pairwise (tree) sums in both modes: on these problems it
+    # meets the oracle tolerances as well as the FP64-merged mode, so the comparison is at equal
+    # accuracy and isolates batching + graph replay
+    pb = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, **common)
     pp = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, **common)
     gn_per_step = prm["n_gn"] * len(lists)
 
@@ -589,7 +592,7 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
     ctx.reset_profile()
     ctx.set_profiling(True)
     ctx.add_frames(0, depth_d, lum_d)
-    ctx.solve_local_batch(ids, lists, bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=0, **common))
+    ctx.solve_local_batch(ids, lists, bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, **common))
     prof = ctx.profile()
     ctx.set_profiling(False)
     tp = None
@@ -610,7 +613,7 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
                        "ms_per_step": statistics.mean(tb),
                        "solves_per_s": len(lists) / (statistics.mean(tb) / 1000.0),
                        "chunk_latency_p50_ms": statistics.mean(tb), "chunk_latency_p99_ms": max(tb),
-                       "precision": "mixed", "cuda_graph": True},
+                       "precision": "fp32", "cuda_graph": True},
            "dense_kernel": {"avg_launch_ms": dense_ms, "launches": dense["count"],
                             "algorithmic_bytes_per_launch": alg_bytes,
                             "algorithmic_GBps": alg_bytes / (dense_ms / 1000.0) / 1e9,
@@ -629,9 +632,10 @@ def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0,
     """Serving: Poisson arrivals of chunk requests (320x240, 3-11 frames, 6 GN x 10 PCG) at `rate`
     per second for `seconds`, and after every 10th chunk a global request over the first k
     keyframes of the 300-keyframe 80x60 corridor (k grows from 100 to 300; 8 GN x 20 PCG).
-    served: continuous batching (2 slots, batches of up to 16, mixed precision); plain: the same
-    arrivals served one request at a time by the plain FP32 path (1 slot, batch 1).  Latency =
-    submit -> completion; p50 / p99 per request kind."""
+    served: continuous batching (2 slots, batches of up to 16, chunk solves on high-priority
+    streams, FP32 chunk arithmetic, FP64-merged global solves); plain: the same arrivals served one
+    request at a time by the plain FP32 path (1 slot, batch 1).  Latency = submit -> completion;
+    p50 / p99 per request kind."""
     rng = np.random.default_rng(seed)
     n_req = int(seconds * rate)
     gaps = rng.exponential(1.0 / rate, size=n_req)
@@ -641,7 +645,8 @@ def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0,
     pg = {k: global_prob.solve[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
     out = {"arrival_rate_per_s": rate, "seconds": seconds, "chunk_requests": n_req,
            "global_requests": n_req // 10, "chunk_workload": chunk_prob.name, "global_workload": global_prob.name}
-    for name, slots, batch, prec in (("served", 2, 16, bf.BF_PREC_MIXED), ("plain_fp32", 1, 1, bf.BF_PREC_FP32)):
+    for name, slots, batch, cprec, gprec in (("served", 2, 16, bf.BF_PREC_FP32, bf.BF_PREC_MIXED),
+                                             ("plain_fp32", 1, 1, bf.BF_PREC_FP32, bf.BF_PREC_FP32)):
         cctx = bf.Context(ci["W"], ci["H"], ci["fx"], ci["fy"], ci["cx"], ci["cy"], max_frames_hint=chunk_prob.n_frames)
         cctx.add_frames(0, torch.from_numpy(chunk_prob.depth).to(dev), torch.from_numpy(chunk_prob.lum).to(dev))
         cctx.add_correspondences_batch(chunk_prob.pairs, chunk_prob.corr_off, torch.from_numpy(chunk_prob.p_i).to(dev),
@@ -652,8 +657,14 @@ def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0,
         torch.cuda.synchronize(dev)
         cctx.serve_start(n_slots=slots, max_batch=batch, max_queue=4096)
         gctx.serve_start(n_slots=1, max_batch=1, max_queue=4096)
-        cparams = bf.default_params(precision=prec, **pc)
-        gparams = bf.default_params(precision=prec, **pg)
+        cparams = bf.default_params(precision=cprec, **pc)
+        gparams = bf.default_params(precision=gprec, **pg)
+        # warm-up (not timed): every slot allocates its workspace and pinned staging on first use
+        warm = [cctx.submit(lists[k % len(lists)], chunk_id=100000 + k, params=cparams) for k in range(4 * slots)]
+        warm.append(gctx.submit(list(range(100)), kind=bf._lib.BF_REQ_GLOBAL, params=gparams))
+        for t in warm[:-1]:
+            cctx.wait(t)
+        gctx.wait(warm[-1])
         ct, gt = [], []
         t0 = time.perf_counter()
         t_next = t0
@@ -670,15 +681,34 @@ def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0,
         wall = time.perf_counter() - t0
         cctx.serve_stop()
         gctx.serve_stop()
-        cctx.close()
         gctx.close()
+        # a heavier chunk-only stream, where requests overlap and batching pays
+        hi_rate, hi_n = 600.0, 1200
+        hgaps = rng.exponential(1.0 / hi_rate, size=hi_n)
+        cctx.serve_start(n_slots=slots, max_batch=batch, max_queue=100000)
+        for t in [cctx.submit(lists[k % len(lists)], chunk_id=200000 + k, params=cparams) for k in range(4 * slots)]:
+            cctx.wait(t)
+        ht = []
+        th0 = time.perf_counter()
+        t_next = th0
+        for r in range(hi_n):
+            t_next += hgaps[r]
+            while time.perf_counter() < t_next:
+                time.sleep(0.0001)
+            ht.append(cctx.submit(lists[r % len(lists)], chunk_id=300000 + r, params=cparams))
+        hlat = sorted(cctx.wait(t)[1]["ms"] for t in ht)
+        hwall = time.perf_counter() - th0
+        cctx.serve_stop()
+        cctx.close()
         clat.sort()
         glat.sort()
         q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))] if v else None  # noqa: E731
         out[name] = {"chunk_p50_ms": q(clat, 0.5), "chunk_p99_ms": q(clat, 0.99), "global_p50_ms": q(glat, 0.5),
                      "global_p99_ms": q(glat, 0.99), "solves_per_s": (len(clat) + len(glat)) / wall,
                      "wall_s": wall, "slots": slots, "max_batch": batch,
-                     "precision": "mixed" if prec == bf.BF_PREC_MIXED else "fp32"}
+                     "chunk_only_600_per_s": {"p50_ms": q(hlat, 0.5), "p99_ms": q(hlat, 0.99),
+                                              "solves_per_s": len(hlat) / hwall, "requests": len(hlat)},
+                     "precision": {"chunk": "fp32", "global": "mixed" if gprec == bf.BF_PREC_MIXED else "fp32"}}
     return out
 
 

@@ -321,7 +321,9 @@ typedef struct {
   bf_solve_params params;   /* use_graph is ignored (batches differ from one another);
                                prune_rmax must be 0 (pruning is in the synchronous calls)  */
 } bf_request;
-/* Start n_slots (1..8) worker slots; max_batch local requests per batch; max_queue pending. */
+/* Start n_slots (1..8) worker slots; max_batch local requests per batch; max_queue pending.
+ * Each slot runs local (chunk) batches on a high-priority stream and global solves on a
+ * low-priority one, so when both are on the device the short chunk kernels are scheduled first. */
 bf_status bf_serve_start(bf_ctx *ctx, int n_slots, int max_batch, int max_queue);
 /* Stop the workers after their current batch; pending requests complete with BF_ERR_BUSY.
  * bf_destroy stops serving too. */

@@ -77,6 +77,7 @@ inline uint64_t pair_key(int a, int b) {
 // a stream, the workspace arena, pinned staging and the cached Gauss-Newton graph.
 struct Exec {
   cudaStream_t st = nullptr;
+  cudaStream_t st_hi = nullptr, st_lo = nullptr;  // serving slots: local / global request streams
   char *ws = nullptr;
   size_t ws_bytes = 0;
   unsigned char *pin = nullptr;
@@ -2289,6 +2290,9 @@ static void run_batch(bf_ctx *c, Exec &ex, std::vector<uint64_t> batch) {
       prm = h.prm;
     }
     std::unique_lock<std::mutex> lk(c->mu);
+    // chunk solves run on the slot's high-priority stream, global solves on its low-priority one:
+    // when both kinds are resident the scheduler dispatches the short chunk kernels first
+    ex.st = kind == BF_REQ_GLOBAL ? ex.st_lo : ex.st_hi;
     c->ex = &ex;
     bf_status st = check_params(c, &prm);
     if (!st) {
@@ -2396,13 +2400,24 @@ extern "C" bf_status bf_serve_start(bf_ctx *c, int n_slots, int max_batch, int m
   std::unique_ptr<Server> S(new Server());
   S->max_batch = max_batch;
   S->max_queue = max_queue;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaGetLastError();
+    least = greatest = 0;
+  }
   for (int k = 0; k < n_slots; ++k) {
     std::unique_ptr<Exec> e(new Exec());
-    if (cudaStreamCreateWithFlags(&e->st, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithPriority(&e->st_hi, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&e->st_lo, cudaStreamNonBlocking, least) != cudaSuccess) {
       cudaGetLastError();
-      for (auto &x : S->slots) cudaStreamDestroy(x->st);
+      if (e->st_hi) cudaStreamDestroy(e->st_hi);
+      for (auto &x : S->slots) {
+        cudaStreamDestroy(x->st_hi);
+        cudaStreamDestroy(x->st_lo);
+      }
       return fail(c, BF_ERR_CUDA, "bf_serve_start: stream creation failed");
     }
+    e->st = e->st_hi;
     S->slots.push_back(std::move(e));
   }
   c->srv = std::move(S);
@@ -2428,9 +2443,11 @@ extern "C" bf_status bf_serve_stop(bf_ctx *c) {
   complete_requests(S, cancelled, BF_ERR_BUSY, nullptr);
   std::unique_lock<std::mutex> lk(c->mu);
   for (auto &e : S.slots) {
-    cudaStreamSynchronize(e->st);
+    cudaStreamSynchronize(e->st_hi);
+    cudaStreamSynchronize(e->st_lo);
     free_exec(c, *e);
-    cudaStreamDestroy(e->st);
+    cudaStreamDestroy(e->st_hi);
+    cudaStreamDestroy(e->st_lo);
   }
   cudaGetLastError();
   c->srv.reset();
