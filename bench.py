@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
     ap.add_argument("--tile-px", type=int, default=0,
                     help="dense work item size in source pixels; 0 = automatic (target frame staged in shared memory)")
+    ap.add_argument("--large-only", action="store_true",
+                    help="run only the 2000-keyframe 160x120 BF16 global solve leg (one JSON line)")
     ap.add_argument("--next-rows-only", action="store_true",
                     help="run only the pruning / verification / key-point / TSDF legs (one JSON line)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
@@ -223,6 +225,12 @@ def run_ours(args, rank, world, local_rank):
     intr = prob.intr
     n = prob.n_frames
     ids = list(range(n))
+    if args.large_only:
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(stream)
+        if rank == 0:
+            print(json.dumps({"large_global": large_global_leg(bf, torch, dev, stream)}), flush=True)
+        return
     if args.next_rows_only:
         stream = torch.cuda.Stream(dev)
         torch.cuda.set_stream(stream)
@@ -403,6 +411,7 @@ def run_ours(args, rank, world, local_rank):
         line["serving"] = serving_leg(bf, torch, dev, cprob, prob)
 
         line["next_rows"] = next_rows_leg(bf, torch, dev, stream, prob, prm)
+        line["large_global"] = large_global_leg(bf, torch, dev, stream)
 
         v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
@@ -529,6 +538,65 @@ def next_rows_leg(bf, torch, dev, stream, prob, prm):
                    "note": "synchronous calls (status read back per frame)"}
     ctx.close()
     return out
+
+
+def large_global_leg(bf, torch, dev, stream, steps=3, warmup=1):
+    """Large global mixed-precision solve: 2000 keyframes at 160x120 in BF16 frame storage, 25k
+    pairs, 2.5M correspondences (10 % outliers), 10 GN x 30 PCG, CUDA graph.  The frames
+    (2000 x 19200 px x 18 B = 0.69 GB) exceed L2, so the dense kernel streams them from HBM."""
+    import synth
+    t_gen = time.perf_counter()
+    prob = synth.cfg5()
+    t_gen = time.perf_counter() - t_gen
+    intr = prob.intr
+    n = prob.n_frames
+    ids = list(range(n))
+    prm = prob.solve
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], stream=stream.cuda_stream,
+                     max_frames_hint=n, storage=bf.BF_STORE_BF16)
+    depth_d = torch.from_numpy(prob.depth).to(dev)
+    lum_d = torch.from_numpy(prob.lum).to(dev)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                  torch.from_numpy(prob.p_j).to(dev))
+    common = {k: prm[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
+    p = bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=1, **common)
+
+    def step(pp=p):
+        ctx.add_frames(0, depth_d, lum_d, init_pose=prob.init)
+        return ctx.solve_global(ids, pp)
+
+    for _ in range(warmup):
+        step()
+    ts = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    step(bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=0, **common))
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    ctx.close()
+    dense = prof["kernels"]["dense"]
+    dense_ms = dense["ms"] / max(dense["count"], 1)
+    HW = intr["W"] * intr["H"]
+    units = 2 * st["n_dense_pairs"] * HW
+    tot = sum(v["ms"] for v in prof["kernels"].values())
+    return {"workload": prob.name, "keyframes": n, "resolution": f"{intr['W']}x{intr['H']}", "storage": "bf16",
+            "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"], "correspondences": prob.n_corr,
+            "n_gn": prm["n_gn"], "n_pcg": prm["n_pcg"], "precision": "mixed", "generation_s": t_gen,
+            "value": prm["n_gn"] / (statistics.mean(ts) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(ts),
+            "initial_energy": st["energy"][0], "final_energy": st["energy"][-1],
+            "dense_kernel": {"avg_launch_ms": dense_ms, "directed_px_per_launch": units,
+                             "algorithmic_GBps": DENSE_BYTES_PER_PX_16 * units / (dense_ms / 1000.0) / 1e9,
+                             "frame_bytes": n * HW * 18},
+            "kernel_time_share": {k: round(v["ms"] / max(tot, 1e-9), 4) for k, v in prof["kernels"].items()
+                                  if v["count"]}}
 
 def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None, storage="fp32"):
     """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.

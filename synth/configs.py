@@ -149,6 +149,49 @@ def global_problem(seed, n_kf=300, W=80, H=60, n_corr=(64, 256), sigma=0.01, out
                      solve=dict(n_gn=8, n_pcg=20, w_sparse=1.0, w_dense=0.5, w_photo=0.1, w_geo=1.0))
 
 
+def large_global_problem(seed, n_kf=2000, W=160, H=120, n_corr=(64, 136), sigma=0.01, outlier_frac=0.10,
+                         overlap_min=0.30, max_pairs=25000, outer=(60.0, 2.8, 40.0), inner=(50.0, 30.0),
+                         name="global2000_160x120"):
+    """Large global solve: keyframes along one loop of a large ring corridor (about 180 m), cameras
+    facing the outer wall; candidate pairs within 3 m, kept when their GT overlap exceeds
+    overlap_min (stride-4 test), then subsampled to max_pairs; 10 % outliers."""
+    rng = np.random.default_rng(seed)
+    intr = sc.intrinsics(W, H)
+    wob = np.stack([rng.normal(0, 0.05, n_kf), rng.normal(0, 0.04, n_kf), rng.normal(0, 0.02, n_kf)], 1)
+    gt, L = sc.ring_loop(n_kf, (outer[0], outer[2]), inner, 90.0, wob)
+    gt[:, 1, 3] = rng.normal(0, 0.1, n_kf)
+    centres = gt[:, :3, 3]
+    room = sc.ring_corridor(rng, outer, inner, n_boxes=(300, 400), keep_clear=centres, clear_radius=0.5)
+    depth_gt, lum = sc.render_culled(room, gt, intr)
+    depth, _ = sc.sensor_depth(rng, depth_gt)
+    pair_list = []
+    for i in range(n_kf):
+        near = np.flatnonzero(np.linalg.norm(centres[i + 1:] - centres[i], axis=1) < 3.0) + i + 1
+        for j in near:
+            if sc.overlap(intr, depth_gt, gt, i, int(j), stride=4) > overlap_min:
+                pair_list.append((i, int(j)))
+    if len(pair_list) > max_pairs:
+        keep = np.sort(rng.choice(len(pair_list), max_pairs, replace=False))
+        pair_list = [pair_list[k] for k in keep]
+    corr, kept = [], []
+    for (i, j) in pair_list:
+        n = int(rng.integers(n_corr[0], n_corr[1] + 1))
+        c = sc.sample_correspondences(rng, intr, depth_gt, depth, gt, i, j, n, sigma, outlier_frac)
+        if c is None:
+            continue
+        kept.append((i, j))
+        corr.append(c)
+    init = sc.drift(rng, gt)
+    return _assemble(name, intr, depth, lum, gt, init, kept, corr, depth_gt=depth_gt,
+                     solve=dict(n_gn=10, n_pcg=30, w_sparse=1.0, w_dense=0.5, w_photo=0.1, w_geo=1.0))
+
+
+def cfg5():
+    """Large global mixed-precision solve: 2000 keyframes at 160x120, ~25k pairs, ~2.5M
+    correspondences with 10 % outliers, 10 GN x 30 PCG (BF16 frame storage in the benchmark)."""
+    return large_global_problem(seed_for(5))
+
+
 def cfg2():
     """Global solve: 300 keyframes at 80x60 along a ~60 m loop, overlap > 30 %, 8 GN x 20 PCG."""
     return global_problem(seed_for(2), 300, 80, 60, name="global300_80x60")

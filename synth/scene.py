@@ -240,6 +240,24 @@ def render(scene: Scene, poses, intr):
     return depth, lum
 
 
+def render_culled(scene: Scene, poses, intr, max_range=4.5):
+    """render(), one frame at a time with only the boxes whose bounds come within max_range of the
+    camera centre (plus the room shell): depths below max_range are the same as with every box,
+    and the per-frame work no longer grows with the size of the scene."""
+    poses = np.asarray(poses, dtype=np.float64)
+    n = poses.shape[0]
+    depth = np.zeros((n, intr["H"], intr["W"]), dtype=np.float32)
+    lum = np.zeros((n, intr["H"], intr["W"]), dtype=np.float32)
+    for k in range(n):
+        c = poses[k, :3, 3]
+        gap = np.maximum(0.0, np.maximum(scene.lo - c, c - scene.hi))
+        near = (np.linalg.norm(gap, axis=1) < max_range) | (scene.kind == 0)
+        sub = Scene(scene.lo[near], scene.hi[near], scene.kind[near], scene.tex[near])
+        d, l = render(sub, poses[k:k + 1], intr)
+        depth[k], lum[k] = d[0], l[0]
+    return depth, lum
+
+
 def sensor_depth(rng, depth_gt, sigma=0.002, dmin=0.5, dmax=4.0):
     """Clip to [dmin, dmax] (outside -> 0 = invalid) and add N(0, sigma^2) noise to valid pixels."""
     d = depth_gt.astype(np.float64)
@@ -368,7 +386,7 @@ def sample_correspondences(rng, intr, depth_gt, depth_noisy, poses, i, j, n, sig
     A fraction outlier_frac of p_j is replaced by the back-projection of a random valid pixel of j.
     Returns (p_i, p_j, is_outlier) as float32 / bool arrays, or None if nothing of i is visible in j.
     """
-    stride = 1 if intr["W"] <= 160 else 2  # candidates from every second pixel on large frames
+    stride = 1 if intr["W"] < 160 else 2  # candidates from every second pixel on large frames
     ok, _, xs, ys = visible_mask(intr, depth_gt[i], depth_gt[j], poses[i], poses[j], stride=stride)
     ok &= depth_noisy[i][ys, xs] > 0
     cand = np.flatnonzero(ok.ravel())
