@@ -1,0 +1,118 @@
+"""Sizes beyond the chunk and 300-keyframe workloads.
+
+* 160x120 frames in BF16 storage (the large global workload's frame format) through the tiled
+  dense kernel, against the oracle on the same BF16-rounded planes;
+* a 2000-frame sparse-only global solve, where the cluster PCG's per-CTA share of the pair blocks
+  no longer fits in shared memory (the kernel reads them from global memory): its result agrees
+  with the per-problem and grid-cooperative PCG kernels, and a 300-frame slice with the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import frames as ofr, lie, solver
+from oracle.system import SolveParams, SparsePair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_1604_01093_b300 as bf
+    return bf
+
+
+def test_bf16_160x120_chunk_matches_oracle(bf):
+    prob = synth.chunk_problem(95, 5, 160, 120, (80, 160), name="chunk5_160x120")
+    n = prob.n_frames
+    fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr, storage="bf16") for k in range(n)]
+    prm = SolveParams(n_gn=3, n_pcg=10, w_dense=0.5)
+    ref = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm)
+    intr = prob.intr
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], storage=bf.BF_STORE_BF16)
+    ctx.add_frames(0, prob.depth, prob.lum)
+    for k, (i, j) in enumerate(prob.pairs):
+        p, q = prob.pair_corr(k)
+        ctx.add_correspondences(int(i), int(j), p, q)
+    st = ctx.solve_local(0, list(range(n)), n_gn=3, n_pcg=10, w_dense=0.5)
+    rel = np.abs(np.array(st["energy"]) - ref.energy) / np.abs(ref.energy)
+    assert rel.max() <= 1e-5, rel
+    P = ctx.get_poses(list(range(n)))
+    for k in range(n):
+        rot, tr = lie.pose_error(P[k], ref.poses[k])
+        assert rot <= 1e-4 and tr <= 1e-5, (k, rot, tr)
+
+
+def sparse_chain(n, seed, neighbours=12, n_corr=24, sigma=0.005):
+    """n frames along a wavy path; every frame matched with its next `neighbours` frames."""
+    rng = np.random.default_rng(seed)
+    gt = np.zeros((n, 4, 4))
+    for k in range(n):
+        gt[k] = lie.to44(lie.exp_so3(np.array([0.0, 0.01 * k, 0.02 * np.sin(0.05 * k)])),
+                         np.array([0.05 * k, 0.1 * np.sin(0.03 * k), 0.0]))
+    init = gt.copy()
+    for k in range(1, n):
+        init[k][:3, :3] = lie.exp_so3(rng.normal(0, 0.002, 3)) @ gt[k][:3, :3]
+        init[k][:3, 3] += rng.normal(0, 0.005, 3)
+    pairs, P, Q = [], [], []
+    for i in range(n):
+        for j in range(i + 1, min(n, i + 1 + neighbours)):
+            p = rng.uniform([-1, -1, 1], [1, 1, 3], (n_corr, 3))
+            Tji = np.linalg.inv(gt[j]) @ gt[i]
+            q = p @ Tji[:3, :3].T + Tji[:3, 3] + rng.normal(0, sigma, (n_corr, 3))
+            pairs.append((i, j))
+            P.append(p)
+            Q.append(q)
+    return gt, init, pairs, P, Q
+
+
+def sparse_ctx(bf, init, pairs, P, Q):
+    n = len(init)
+    ctx = bf.Context(8, 8, 6.5625, 6.5625, 3.5, 3.5, max_frames_hint=n)
+    z = np.zeros((n, 8, 8), np.float32)
+    ctx.add_frames(0, z, z, init_pose=init)
+    off = np.concatenate([[0], np.cumsum([len(p) for p in P])]).astype(np.int32)
+    ctx.add_correspondences_batch(np.asarray(pairs, np.int32), off, np.concatenate(P).astype(np.float32),
+                                  np.concatenate(Q).astype(np.float32))
+    return ctx
+
+
+def test_large_sparse_solve_variants_agree(bf):
+    gt, init, pairs, P, Q = sparse_chain(2000, 96)
+    n = len(gt)
+    kw = dict(n_gn=3, n_pcg=30, dense_on=0)
+    res = {}
+    for v in (1, 2, 3):
+        ctx = sparse_ctx(bf, init, pairs, P, Q)
+        st = ctx.solve_global(list(range(n)), pcg_variant=v, **kw)
+        res[v] = (st, ctx.get_poses(list(range(n))))
+        assert st["flags"] == 0
+    for v in (2, 3):
+        rot = max(lie.pose_error(res[v][1][k], res[1][1][k])[0] for k in range(n))
+        tr = max(lie.pose_error(res[v][1][k], res[1][1][k])[1] for k in range(n))
+        assert rot < 2e-5 and tr < 2e-5, (v, rot, tr)
+        np.testing.assert_allclose(res[v][0]["energy"], res[1][0]["energy"], rtol=1e-5)
+    # converged to the noise floor (5 mm noise: about 2000 x 12 x 24 x 3 x 2.5e-5 = 43)
+    e = res[3][0]["energy"]
+    assert e[-1] < 0.3 * e[0] and e[-1] < 50.0
+
+
+def test_large_sparse_slice_matches_oracle(bf):
+    gt, init, pairs, P, Q = sparse_chain(300, 97)
+    n = len(gt)
+    prm = SolveParams(n_gn=3, n_pcg=30, dense_on=False)
+    sp = [SparsePair(i, j, p, q) for (i, j), p, q in zip(pairs, P, Q)]
+    # the oracle sees the FP32 points the device got
+    sp = [SparsePair(s.a, s.b, s.p.astype(np.float32).astype(np.float64), s.q.astype(np.float32).astype(np.float64))
+          for s in sp]
+    ref = solver.gauss_newton([None] * n, None, init, sp, prm)
+    ctx = sparse_ctx(bf, init, pairs, P, Q)
+    st = ctx.solve_global(list(range(n)), n_gn=3, n_pcg=30, dense_on=0)
+    rel = np.abs(np.array(st["energy"]) - ref.energy) / np.abs(ref.energy)
+    assert rel.max() <= 1e-5, rel
+    Pg = ctx.get_poses(list(range(n)))
+    for k in range(n):
+        rot, tr = lie.pose_error(Pg[k], ref.poses[k])
+        assert rot <= 1e-4 and tr <= 1e-5, (k, rot, tr)
