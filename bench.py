@@ -621,7 +621,7 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
     # chunk solves in FP32 arithmetic with pairwise (tree) sums in both modes: on these problems it
     # meets the oracle tolerances as well as the FP64-merged mode, so the comparison is at equal
     # accuracy and isolates batching + graph replay
-    pb = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, **common)
+    pb = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, tile_px=bf._lib.BF_TILE_AUTOTUNE, **common)
     pp = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, **common)
     gn_per_step = prm["n_gn"] * len(lists)
 
@@ -660,7 +660,9 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
     ctx.reset_profile()
     ctx.set_profiling(True)
     ctx.add_frames(0, depth_d, lum_d)
-    ctx.solve_local_batch(ids, lists, bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, **common))
+    ctx.solve_local_batch(ids, lists, bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0,
+                                                        tile_px=bf._lib.BF_TILE_AUTOTUNE, **common))
+    tuned = ctx.tuned_tile_px()
     prof = ctx.profile()
     ctx.set_profiling(False)
     tp = None
@@ -681,7 +683,8 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
                        "ms_per_step": statistics.mean(tb),
                        "solves_per_s": len(lists) / (statistics.mean(tb) / 1000.0),
                        "chunk_latency_p50_ms": statistics.mean(tb), "chunk_latency_p99_ms": max(tb),
-                       "precision": "fp32", "cuda_graph": True},
+                       "precision": "fp32", "cuda_graph": True,
+                       "tile_px": {"autotuned": tuned, "meaning": "0 = target frame staged in shared memory"}},
            "dense_kernel": {"avg_launch_ms": dense_ms, "launches": dense["count"],
                             "algorithmic_bytes_per_launch": alg_bytes,
                             "algorithmic_GBps": alg_bytes / (dense_ms / 1000.0) / 1e9,

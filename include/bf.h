@@ -108,7 +108,9 @@ typedef struct {
   int warm_start;           /* local solves: start from the chunk's previous local poses */
   int precision;            /* BF_PREC_*                                               */
   int use_graph;            /* replay the Gauss-Newton loop as a captured CUDA graph   */
-  int tile_px;              /* source pixels per dense work item, 0 = autotuned        */
+  int tile_px;              /* source pixels per dense work item; 0 = the fixed rule (target
+                               frame staged in shared memory when it fits, else 4800-pixel
+                               tiles); BF_TILE_AUTOTUNE = timed choice, see bf_tuned_tile_px */
   int pcg_variant;          /* BF_PCG_*: which PCG kernel runs (results agree to rounding) */
   /* Sec. 4.4.1 correspondence pruning.  prune_rmax > 0: after a solve whose r_max (largest
    * ||T_i p - T_j q|| over its sparse correspondences) exceeds prune_rmax, every
@@ -119,6 +121,10 @@ typedef struct {
   double prune_rmax;
   int prune_rounds;
 } bf_solve_params;
+
+/* tile_px value asking the library to time the candidate dense work decompositions on the
+ * first solve of the context (per frame size and storage) and keep the fastest. */
+#define BF_TILE_AUTOTUNE (-1)
 
 /* PCG kernels: AUTO picks CLUSTER for one large problem, else one CTA per problem. */
 enum { BF_PCG_AUTO = 0, BF_PCG_CTA = 1, BF_PCG_GRID = 2, BF_PCG_CLUSTER = 3 };
@@ -444,6 +450,12 @@ bf_status bf_tsdf_reintegrate(bf_ctx *ctx, int n_fix, int *frame_ids, int *n_don
  * of allocated blocks (also when it exceeds capacity; capacity 0 only counts).
  */
 bf_status bf_tsdf_export(bf_ctx *ctx, long long capacity, int *block_coords, int *sums, long long *n);
+
+/* The decomposition the autotuner chose for this context's frame size and storage: 0 = target
+ * frame staged in shared memory, else the tile size in pixels.  BF_ERR_NOT_FOUND before the
+ * first autotuned solve.  The choice depends on timing, so two contexts may choose differently
+ * (their results then differ in the last bits); within a context it is fixed. */
+bf_status bf_tuned_tile_px(bf_ctx *ctx, int *tile_px);
 
 /*
  * Failure-detection self-test.  The library's device waits (the cooperative PCG's grid barrier,

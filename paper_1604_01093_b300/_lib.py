@@ -23,6 +23,7 @@ BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
 BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER = 0, 1, 2, 3
 BF_MAX_GN = 64
 BF_MAX_PRUNE = 32
+BF_TILE_AUTOTUNE = -1
 BF_NPROF = 13
 KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack",
                   "verify", "keypoint", "tsdf"]
@@ -159,6 +160,7 @@ def lib():
                                       ctypes.POINTER(SolveParams), P, P]),
         "bf_default_verify_params": (None, [ctypes.POINTER(VerifyParams)]),
         "bf_selftest_wait_timeout": (I, [P, I, ctypes.c_longlong, P]),
+        "bf_tuned_tile_px": (I, [P, P]),
         "bf_default_tsdf_config": (None, [ctypes.POINTER(TsdfConfig)]),
         "bf_tsdf_init": (I, [P, ctypes.POINTER(TsdfConfig)]),
         "bf_tsdf_integrate": (I, [P, I, P]),
@@ -187,7 +189,7 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait",
            "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk", "bf_default_keypoint_params",
            "bf_filter_keypoints", "bf_selftest_wait_timeout", "bf_default_tsdf_config", "bf_tsdf_init",
-           "bf_tsdf_integrate", "bf_tsdf_deintegrate", "bf_tsdf_reintegrate", "bf_tsdf_export"]
+           "bf_tsdf_integrate", "bf_tsdf_deintegrate", "bf_tsdf_reintegrate", "bf_tsdf_export", "bf_tuned_tile_px"]
 
 
 class BFError(RuntimeError):
@@ -382,6 +384,12 @@ class Context:
         sums = np.zeros((max(cap, 1), 3, 512), dtype=np.int32)
         self._check(lib().bf_tsdf_export(self.h, cap, _ptr(coords), _ptr(sums), ctypes.byref(n)))
         return {tuple(map(int, coords[k])): sums[k].astype(np.int64) for k in range(cap)}
+
+    def tuned_tile_px(self):
+        """The autotuner's choice for this context (0 = staged target frame), or None."""
+        v = ctypes.c_int(0)
+        st = lib().bf_tuned_tile_px(self.h, ctypes.byref(v))
+        return v.value if st == 0 else None
 
     # ------------------------------------------------------ failure detection
     def selftest_wait_timeout(self, which, limit=1 << 16):

@@ -130,6 +130,7 @@ struct bf_ctx {
   std::vector<std::pair<void *, size_t>> tsdf_allocs;
   std::map<int, Pose12> tsdf_integrated;
   int tsdf_call = 0;
+  std::map<long long, int> tuned_tile;  // dense decomposition chosen by the autotuner, per frame size/storage
   void *kp_buf = nullptr;         // key-point filter: inputs and results
   size_t kp_cap = 0;
   VerifyPair *vrec = nullptr;     // dense verification: pair records and results
@@ -1281,7 +1282,8 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
     return fail(c, BF_ERR_INVALID_ARG, "unknown preconditioner");
   if (!(p->tau_dist > 0) || !std::isfinite(p->tau_normal) || !std::isfinite(p->max_angle_deg))
     return fail(c, BF_ERR_INVALID_ARG, "bad gates");
-  if (p->tile_px < 0) return fail(c, BF_ERR_INVALID_ARG, "tile_px must be >= 0");
+  if (p->tile_px < 0 && p->tile_px != BF_TILE_AUTOTUNE)
+    return fail(c, BF_ERR_INVALID_ARG, "tile_px must be >= 0 or BF_TILE_AUTOTUNE");
   if (p->pcg_variant < BF_PCG_AUTO || p->pcg_variant > BF_PCG_CLUSTER)
     return fail(c, BF_ERR_INVALID_ARG, "unknown pcg_variant");
   if (!(p->prune_rmax >= 0) || !std::isfinite(p->prune_rmax) || p->prune_rounds < 0 || p->prune_rounds > 100000)
@@ -1302,8 +1304,80 @@ struct SolveJob {
 
 // Phase 1 (context lock held): build the tables, upload, enqueue the Gauss-Newton loop and the
 // asynchronous result copies into the executor's pinned staging.
-bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm, SolveJob &J) {
+// ---------------------------------------------------------------- dense work autotuner
+// tile_px = BF_TILE_AUTOTUNE: the first solve of a context (per frame size and storage) times the
+// dense kernel on its own tables for each candidate decomposition — the target frame staged in
+// shared memory when it fits, else whole-frame, half-frame and quarter-frame tiles — takes the
+// fastest (median of 3 launches, CUDA events on the solve's stream) and keeps it for the
+// context's later solves.  The choice depends on the frame size and storage only, so a problem
+// gets the same decomposition alone and inside a batch.
+static int tune_tile(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm) {
+  const int HW = c->cfg.width * c->cfg.height;
+  const long long key = ((long long)c->cfg.width << 32) | ((long long)c->cfg.height << 8) | c->cfg.storage;
+  auto it = c->tuned_tile.find(key);
+  if (it != c->tuned_tile.end()) return it->second;
+  std::vector<int> cand;
+  if (dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage)) cand.push_back(0);
+  for (int d : {1, 2, 4}) {
+    const int t = std::max(256, (HW + d - 1) / d);
+    if (std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
+  }
+  int best = cand[0];
+  float best_ms = INFINITY;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return best;
+  }
+  const bool mixed = prm.precision == BF_PREC_MIXED;
+  for (int tp : cand) {
+    bf_solve_params q = prm;
+    q.tile_px = tp;
+    HostTables T;
+    DevSolve D;
+    if (build_tables(c, probs, q, T) || prepare(c, T, 1, mixed ? 8 : 4, false, D, q.pcg_variant)) continue;
+    if (T.n_dp == 0) break;  // no dense pairs: nothing to choose
+    launch_pair_xform(D.t, D.pose, D.pairM, c->ex->st);
+    Gates g;
+    g.tau_d2 = (float)(prm.tau_dist * prm.tau_dist);
+    g.tau_n = (float)prm.tau_normal;
+    std::vector<float> ms;
+    for (int r = 0; r < 4; ++r) {
+      cudaEventRecord(e0, c->ex->st);
+      if (D.t.n_wi > 0) {
+        if (mixed) launch_dense_staged<double>(MODE_ACCUM, D.t, frame_store(c), c->intr, D.pairM, g, 1.f, 0.1f,
+                                               (double *)D.dpart, D.derr, c->ex->st);
+        else launch_dense_staged<float>(MODE_ACCUM, D.t, frame_store(c), c->intr, D.pairM, g, 1.f, 0.1f,
+                                        (float *)D.dpart, D.derr, c->ex->st);
+      } else {
+        if (mixed) launch_dense<double>(MODE_ACCUM, D.t, frame_store(c), c->intr, D.pairM, g, 1.f, 0.1f,
+                                        (double *)D.dpart, nullptr, c->ex->st);
+        else launch_dense<float>(MODE_ACCUM, D.t, frame_store(c), c->intr, D.pairM, g, 1.f, 0.1f,
+                                 (float *)D.dpart, nullptr, c->ex->st);
+      }
+      cudaEventRecord(e1, c->ex->st);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) ms.push_back(t);  // the first launch warms up
+    }
+    std::sort(ms.begin(), ms.end());
+    if (!ms.empty() && ms[ms.size() / 2] < best_ms) {
+      best_ms = ms[ms.size() / 2];
+      best = tp;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  c->tuned_tile[key] = best;
+  return best;
+}
+
+bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm_in, SolveJob &J) {
   J.t0 = std::chrono::steady_clock::now();
+  bf_solve_params prm = prm_in;
+  if (prm.tile_px == BF_TILE_AUTOTUNE) prm.tile_px = tune_tile(c, probs, prm);
   J.prm = prm;
   J.sizes.clear();
   for (const Problem &P : probs) J.sizes.push_back((int)P.ids.size());
@@ -1656,6 +1730,17 @@ extern "C" bf_status bf_get_poses(bf_ctx *c, const int *frame_ids, int n, double
 
 
 
+
+
+extern "C" bf_status bf_tuned_tile_px(bf_ctx *c, int *tile_px) {
+  if (!c || !tile_px) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  const long long key = ((long long)c->cfg.width << 32) | ((long long)c->cfg.height << 8) | c->cfg.storage;
+  auto it = c->tuned_tile.find(key);
+  if (it == c->tuned_tile.end()) return fail(c, BF_ERR_NOT_FOUND, "no autotuned decomposition yet");
+  *tile_px = it->second;
+  return BF_OK;
+}
 
 // ------------------------------------------------------------ failure-detection self-test
 extern "C" bf_status bf_selftest_wait_timeout(bf_ctx *c, int which, long long limit, int *gave_up) {

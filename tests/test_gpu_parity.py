@@ -443,3 +443,17 @@ def test_workspace_growth_reuploads_tables(bf):
     ctx.add_frames(0, prob.depth, prob.lum, init_pose=prob.init)
     st = ctx.solve_global(list(range(n)), pcg_variant=2, **kw)
     assert st["energy"] == ref["energy"] and st["flags"] == 0
+
+
+def test_autotuned_decomposition(bf, cfg1, cfg1_oracle):
+    """tile_px = BF_TILE_AUTOTUNE times the candidate decompositions once, keeps the fastest, and
+    then gives the same result as asking for that decomposition explicitly; the solve matches the
+    oracle like any other."""
+    ctx = make_ctx(bf, cfg1)
+    assert ctx.tuned_tile_px() is None
+    st = ctx.solve_local(0, list(range(11)), tile_px=bf._lib.BF_TILE_AUTOTUNE, **dict(cfg1.solve))
+    chosen = ctx.tuned_tile_px()
+    assert chosen == 0 or 256 <= chosen <= 4800
+    compare_solve(st, ctx.get_poses(list(range(11))), cfg1_oracle, "autotuned")
+    again = make_ctx(bf, cfg1).solve_local(0, list(range(11)), tile_px=chosen, **dict(cfg1.solve))
+    assert again["energy"] == st["energy"]
