@@ -399,6 +399,10 @@ def run_ours(args, rank, world, local_rank):
         line["plain_fp32"] = {"value": n_gn / (statistics.mean(tp) / 1000.0), "unit": UNIT,
                               "ms_per_step": statistics.mean(tp), "final_energy": stp["energy"][-1]}
 
+        # Sec. 4.4's matrix-free sparse term (J p, then J^T (J p) every PCG iteration) against the
+        # sparse 6x6 blocks assembled once per GN iteration, both on the grid-cooperative PCG kernel
+        line["sparse_term"] = sparse_term_leg(bf, step, timed, prm, precision, max(3, args.steps // 2))
+
         # the same global solve on 16-bit frame storage
         if args.storage == "fp32":
             line["bf16_storage"] = storage_leg(bf, torch, dev, stream, prob, params, prof_params, "bf16")
@@ -418,6 +422,29 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
+
+
+def sparse_term_leg(bf, step, timed, prm, precision, steps):
+    """Global solve with the sparse term as assembled blocks vs matrix-free, grid-cooperative PCG."""
+    out = {"pcg_kernel": "k_pcg_coop (grid-cooperative)", "n_pcg": prm["n_pcg"]}
+    for name, mode in (("blocks", bf.BF_SPARSE_BLOCKS), ("matfree", bf.BF_SPARSE_MATFREE)):
+        kw = dict(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"], w_dense=prm["w_dense"],
+                  w_photo=prm["w_photo"], w_geo=prm["w_geo"], precision=precision, pcg_variant=bf.BF_PCG_GRID,
+                  sparse_mode=mode)
+        pg = bf.default_params(use_graph=1, **kw)
+        pp = bf.default_params(use_graph=0, **kw)
+        for _ in range(2):
+            step(pg)
+        tt, st, _ = timed(lambda: step(pg), steps)
+        _, _, prof = timed(lambda: step(pp), 2, profile=True)
+        k = prof["kernels"]
+        per_solve = {n: round(v["ms"] / 2, 4) for n, v in k.items() if v["count"]}
+        out[name] = {"value": prm["n_gn"] / (statistics.mean(tt) / 1000.0), "unit": UNIT,
+                     "ms_per_step": statistics.mean(tt), "final_energy": st["energy"][-1],
+                     "pcg_ms_per_launch": k["pcg"]["ms"] / max(k["pcg"]["count"], 1),
+                     "kernel_ms_per_solve": per_solve}
+    out["pcg_iteration_us"] = {n: 1000.0 * out[n]["pcg_ms_per_launch"] / prm["n_pcg"] for n in ("blocks", "matfree")}
+    return out
 
 
 def storage_leg(bf, torch, dev, stream, prob, params, prof_params, kind, steps=5):

@@ -120,7 +120,17 @@ typedef struct {
    * chunks that need it are re-solved.  0 = off (the paper uses 0.05 m; 0.16 m for Kinect). */
   double prune_rmax;
   int prune_rounds;
+  /* BF_SPARSE_*: how PCG applies the sparse term.  BLOCKS (default): its 6x6 pair blocks are
+   * formed once per Gauss-Newton iteration and assembled with the dense ones.  MATFREE: Sec. 4.4's
+   * own scheme, J p then J^T (J p) over the correspondences in every PCG iteration; the assembled
+   * blocks hold the dense term alone (the preconditioner and right-hand side still include the
+   * sparse term).  MATFREE runs on the grid-cooperative kernel for one problem with at least 32
+   * free frames (AUTO or GRID) and on the per-problem kernel otherwise; the cluster kernel does
+   * not offer it.  Both give the same step up to FP32 rounding. */
+  int sparse_mode;
 } bf_solve_params;
+
+enum { BF_SPARSE_BLOCKS = 0, BF_SPARSE_MATFREE = 1 };
 
 /* tile_px value asking the library to time the candidate dense work decompositions on the
  * first solve of the context (per frame size and storage) and keep the fastest. */

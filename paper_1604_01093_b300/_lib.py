@@ -21,6 +21,7 @@ BF_PRECOND_BLOCK_JACOBI, BF_PRECOND_JACOBI = 0, 1
 BF_PREC_MIXED, BF_PREC_FP32 = 0, 1
 BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN = 1, 2, 4
 BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER = 0, 1, 2, 3
+BF_SPARSE_BLOCKS, BF_SPARSE_MATFREE = 0, 1
 BF_MAX_GN = 64
 BF_MAX_PRUNE = 32
 BF_TILE_AUTOTUNE = -1
@@ -47,7 +48,8 @@ class SolveParams(ctypes.Structure):
                 ("tau_normal", ctypes.c_double), ("max_angle_deg", ctypes.c_double), ("precond", ctypes.c_int),
                 ("dense_on", ctypes.c_int), ("warm_start", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int), ("pcg_variant", ctypes.c_int),
-                ("prune_rmax", ctypes.c_double), ("prune_rounds", ctypes.c_int)]
+                ("prune_rmax", ctypes.c_double), ("prune_rounds", ctypes.c_int),
+                ("sparse_mode", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):

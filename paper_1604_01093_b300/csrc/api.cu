@@ -352,6 +352,7 @@ extern "C" void bf_default_params(bf_solve_params *p) {
   p->tile_px = 0;
   p->prune_rmax = 0.0;
   p->prune_rounds = 8;
+  p->sparse_mode = BF_SPARSE_BLOCKS;
 }
 
 extern "C" const char *bf_status_string(bf_status s) {
@@ -954,6 +955,11 @@ struct DevSolve {
   float *x, *r, *z, *p, *q, *p1;
   double *energy;  // (n_gn + 1) x n_prob x 4
   int *assoc;
+  // matrix-free sparse term: dense-only pair blocks / diagonal blocks and the per-pair products
+  void *pairblk2, *pairen2, *Dd2, *rhs2;
+  float *Minv2, *mfy;
+  int *vflags2;
+  bool matfree;
   void *coop;      // cooperative PCG state (barrier, error flag, partials)
   int *derr;       // set by the staged dense kernel if its bulk copies did not land
   int coop_grid;   // > 0: one large problem solved by the cooperative PCG
@@ -966,23 +972,24 @@ constexpr int COOP_MIN_VARS = 32;
 // Cluster PCG (vectors replicated in shared memory) while the replicas fit.
 constexpr size_t CLUSTER_SMEM_MAX = 200 * 1024;
 
-int cluster_for(const HostTables &T, int variant) {
-  if (T.n_prob != 1 || T.n_vars == 0) return 0;
+int cluster_for(const HostTables &T, int variant, bool matfree) {
+  if (T.n_prob != 1 || T.n_vars == 0 || matfree) return 0;
   if (variant == BF_PCG_CTA || variant == BF_PCG_GRID) return 0;
   if (variant == BF_PCG_AUTO && T.n_vars < COOP_MIN_VARS) return 0;
   const int cl = cluster_size_max();
   return cluster_smem_bytes(T.n_vars, cl) <= CLUSTER_SMEM_MAX ? cl : 0;
 }
 
-int coop_grid_for(const HostTables &T, int variant) {
+// The matrix-free sparse term is offered by the grid-cooperative and per-problem kernels only.
+int coop_grid_for(const HostTables &T, int variant, bool matfree) {
   if (T.n_prob != 1 || T.n_vars == 0 || variant == BF_PCG_CTA) return 0;
   if (variant == BF_PCG_GRID) return coop_grid_size(T.n_vars);
   if (variant == BF_PCG_AUTO && T.n_vars < COOP_MIN_VARS) return 0;
-  return cluster_for(T, variant) == 0 ? coop_grid_size(T.n_vars) : 0;
+  return cluster_for(T, variant, matfree) == 0 ? coop_grid_size(T.n_vars) : 0;
 }
 
 size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D, size_t acc_size, int HW,
-              bool want_assoc, int variant) {
+              bool want_assoc, int variant, bool matfree) {
   Arena a{base};
   int *ib = a.take<int>(n_int);
   double *pose = a.take<double>(T.n_frames * 12);
@@ -1006,7 +1013,15 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
   float *p = a.take<float>((size_t)T.n_vars * 6);
   float *q = a.take<float>((size_t)T.n_vars * 6);
   float *p1 = a.take<float>((size_t)T.n_vars * 6);
-  const int cg = coop_grid_for(T, variant);
+  const size_t nm = matfree ? 1 : 0;
+  char *pairblk2 = a.take<char>(nm * T.n_pairs * PAIRBLK * acc_size);
+  char *pairen2 = a.take<char>(nm * T.n_pairs * PAIREN * acc_size);
+  char *Dd2 = a.take<char>(nm * T.n_vars * 36 * acc_size);
+  char *rhs2 = a.take<char>(nm * T.n_vars * 6 * acc_size);
+  float *Minv2 = a.take<float>(nm * T.n_vars * 36);
+  float *mfy = a.take<float>(nm * T.n_pairs * 12);
+  int *vflags2 = a.take<int>(nm * T.n_vars);
+  const int cg = coop_grid_for(T, variant, matfree);
   void *coop = a.take<char>(cg > 0 ? coop_mem_bytes(cg) : 256);
   double *energy = a.take<double>((size_t)(n_gn + 1) * T.n_prob * PAIREN);
   int *derr = a.take<int>(1);
@@ -1033,9 +1048,17 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     D->p = p;
     D->q = q;
     D->p1 = p1;
+    D->pairblk2 = pairblk2;
+    D->pairen2 = pairen2;
+    D->Dd2 = Dd2;
+    D->rhs2 = rhs2;
+    D->Minv2 = Minv2;
+    D->mfy = mfy;
+    D->vflags2 = vflags2;
+    D->matfree = matfree;
     D->coop = coop;
     D->coop_grid = cg;
-    D->cluster = cluster_for(T, variant);
+    D->cluster = cluster_for(T, variant, matfree);
     D->energy = energy;
     D->derr = derr;
     D->assoc = assoc;
@@ -1113,10 +1136,11 @@ bf_status ensure_pinned(bf_ctx *c, size_t n) {
 }
 
 bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, bool want_assoc, DevSolve &D,
-                  int variant = BF_PCG_AUTO) {
+                  int variant = BF_PCG_AUTO, bool matfree = false) {
   const std::vector<int> ints = pack_ints(T);
   const int HW = c->cfg.width * c->cfg.height;
-  const size_t need = layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc, variant) + 256;
+  const size_t need =
+      layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc, variant, matfree) + 256;
   if (need > c->ex->ws_bytes) {
     const size_t nb = std::max(need, c->ex->ws_bytes * 3 / 2);
     CK(cudaStreamSynchronize(c->ex->st), "workspace");
@@ -1131,7 +1155,7 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
     if (s) return s;
     c->ex->ws_bytes = nb;
   }
-  layout(T, n_gn, ints.size(), c->ex->ws, &D, acc_size, HW, want_assoc, variant);
+  layout(T, n_gn, ints.size(), c->ex->ws, &D, acc_size, HW, want_assoc, variant, matfree);
   const bool same_tables = c->ex->last_ws == (const void *)c->ex->ws && c->ex->last_ints == ints;
   if (!ints.empty() && !same_tables) {
     CK(cudaMemcpyAsync((void *)D.t.frame_slot, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, c->ex->st),
@@ -1191,6 +1215,25 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
       return launch_assemble<Acc>(t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv,
                                   D.vflags, c->ex->st);
     });
+    MatFree mf{};
+    if (D.matfree) {
+      // the matvec's blocks hold the dense term alone: merge and assemble again without the
+      // sparse segments (pair blocks, off-diagonal FP32 copies and diagonal blocks; the
+      // preconditioner and right-hand side above keep the sparse term)
+      run_k(c, BF_K_MERGE, [&] {
+        return launch_pair_merge<Acc, Acc>(t, D.pose, (const Acc *)D.dpart, (const Acc *)nullptr,
+                                           (Acc *)D.pairblk2, (Acc *)D.pairen2, D.pairoff, c->ex->st);
+      });
+      run_k(c, BF_K_ASSEMBLE, [&] {
+        return launch_assemble<Acc>(t, (const Acc *)D.pairblk2, prm.precond, (Acc *)D.Dd2, (Acc *)D.rhs2, D.Df,
+                                    D.Minv2, D.vflags2, c->ex->st);
+      });
+      mf.P = c->cP;
+      mf.Q = c->cQ;
+      mf.pose = D.pose;
+      mf.w_sparse = (float)prm.w_sparse;
+      mf.mfy = D.mfy;
+    }
     // the PCG kernel also records this linearisation's energy and applies the pose update; the
     // per-problem kernel also refreshes the pair transforms, the multi-CTA ones leave that to
     // k_pair_xform
@@ -1208,11 +1251,11 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
       }
       if (D.coop_grid > 0) {
         pcg_rc = launch_pcg_coop<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.p1, D.q,
-                                      prm.n_pcg, D.pflags, D.coop, D.coop_grid, pen, po, c->ex->st);
+                                      prm.n_pcg, D.pflags, D.coop, D.coop_grid, pen, po, mf, c->ex->st);
         return pcg_rc < 0 ? 0 : pcg_rc;
       }
       return launch_pcg<Acc>(t, D.Df, D.pairoff, D.Minv, (const Acc *)D.rhs, D.x, D.r, D.z, D.p, D.q, prm.n_pcg,
-                             D.pflags, pen, po, c->ex->st);
+                             D.pflags, pen, po, mf, c->ex->st);
     });
     if (pcg_rc < 0) return cuda_fail(c, cudaGetLastError(), "PCG launch");
     if (!po.pairM) run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
@@ -1288,6 +1331,10 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
     return fail(c, BF_ERR_INVALID_ARG, "unknown pcg_variant");
   if (!(p->prune_rmax >= 0) || !std::isfinite(p->prune_rmax) || p->prune_rounds < 0 || p->prune_rounds > 100000)
     return fail(c, BF_ERR_INVALID_ARG, "prune_rmax must be finite and >= 0, prune_rounds >= 0");
+  if (p->sparse_mode != BF_SPARSE_BLOCKS && p->sparse_mode != BF_SPARSE_MATFREE)
+    return fail(c, BF_ERR_INVALID_ARG, "unknown sparse_mode");
+  if (p->sparse_mode == BF_SPARSE_MATFREE && p->pcg_variant == BF_PCG_CLUSTER)
+    return fail(c, BF_ERR_INVALID_ARG, "the cluster PCG kernel has no matrix-free sparse term");
   return BF_OK;
 }
 
@@ -1387,7 +1434,7 @@ bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_s
   if (s) return s;
   const bool mixed = prm.precision == BF_PREC_MIXED;
   const size_t acc_size = mixed ? sizeof(double) : sizeof(float);
-  s = prepare(c, T, prm.n_gn, acc_size, false, D, prm.pcg_variant);
+  s = prepare(c, T, prm.n_gn, acc_size, false, D, prm.pcg_variant, prm.sparse_mode == BF_SPARSE_MATFREE);
   if (s) return s;
   if (prm.use_graph && !c->prof) {
     s = run_gn_graph(c, T, prm, D, mixed);

@@ -262,6 +262,18 @@ struct PcgOut {
   float *pairM;    // [n_pairs][2][12] transforms at the updated poses, nullable
 };
 
+// Matrix-free sparse term inside PCG (Sec. 4.4: the sparse residuals are not assembled; every
+// PCG iteration evaluates J p, then J^T (J p)).  With P == nullptr the sparse 6x6 blocks are part
+// of the assembled system (the default); otherwise the assembled off-diagonal and diagonal blocks
+// the matvec reads hold the dense term alone and the sparse term is applied from the
+// correspondence pool at the linearisation poses.
+struct MatFree {
+  const float4 *P, *Q;  // correspondence pool (p, w) / (q, 0); nullptr = off
+  const double *pose;   // [n_frames][12] poses of the linearisation
+  float w_sparse;
+  float *mfy;           // [n_pairs][12] scratch: the pair's J^T W J d, frame a then frame b
+};
+
 // ------------------------------------------------------------------ launch wrappers (host side)
 // Dense verification (Sec. 4.1.1): one CTA per frame pair, both directions.  rec[p]: slots of
 // the two frames, then fl32(T_ij) and fl32(T_ji) (R row-major, t); out[p] = {n_ij, n_ji, e_ij, e_ji}.
@@ -330,14 +342,14 @@ int launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, A
 template <typename Acc>
 int launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
                 float *r, float *z, float *p, float *q, int n_pcg, int *pflags, const Acc *pairen, PcgOut po,
-                cudaStream_t st);
+                const MatFree &mf, cudaStream_t st);
 // One large problem over many CTAs (cooperative launch).  coop_mem: coop_mem_bytes(grid) bytes
 // of device memory (barrier state + per-CTA partials); its first 16 bytes are reset here.
 // Returns -1 if the cooperative launch was refused.
 template <typename Acc>
 int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
                     float *x, float *r, float *z, float *p0, float *p1, float *q, int n_pcg, int *pflags,
-                    void *coop_mem, int grid, const Acc *pairen, PcgOut po, cudaStream_t st);
+                    void *coop_mem, int grid, const Acc *pairen, PcgOut po, const MatFree &mf, cudaStream_t st);
 int coop_grid_size(int n_vars);
 // One large problem on one thread-block cluster of cl CTAs (vectors replicated in shared memory).
 // Returns -1 if the launch was refused.

@@ -13,6 +13,9 @@
 //   k_pcg_coop     one large problem over many CTAs (cooperative launch, all CTAs resident):
 //                  warp per frame, two grid barriers per iteration, deterministic dot products
 //   k_pcg_cluster  one large problem on a thread-block cluster (distributed shared memory)
+// With the matrix-free sparse term (MatFree, Sec. 4.4's own scheme) k_pcg (general path) and
+// k_pcg_coop evaluate J p and J^T (J p) over the correspondences in every iteration and read the
+// dense term alone from the assembled blocks.
 // Each PCG kernel also writes the problem's energy record of the linearisation it solves (the
 // pairs' records summed in a fixed order) and, once the step is final, applies the exp-map pose
 // update R <- Exp(dw) R, t <- t + dt (FP64) to its free frames; k_pcg then forms its pairs'
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
   for (int half = 0; half < 2; ++half) {
     // half 0: target b (dense a -> b and the sparse segments); half 1: target a (dense b -> a)
     const int d = t.pair_dp[2 * p + half];
-    const bool has_sparse = half == 0 && t.pair_seg1[p] > t.pair_seg0[p];
+    const bool has_sparse = spart != nullptr && half == 0 && t.pair_seg1[p] > t.pair_seg0[p];
     if (d < 0 && !has_sparse) continue;
     const int tgt = half == 1 ? t.pair_a[p] : t.pair_b[p];
     const int srcf = half == 1 ? t.pair_b[p] : t.pair_a[p];
@@ -557,6 +560,62 @@ __device__ __forceinline__ void pcg_beta(Acc &rz, Acc rz_new, PcgScal &S) {
   S.stop = rz == (Acc)0;
 }
 
+// Matrix-free sparse product of one pair (Sec. 4.4: J p, then J^T (J p), the sparse residuals
+// never assembled).  Correspondence k of the pair (a, b) has the world-frame residual
+// r_k = T_a p_k - T_b q_k with Jacobian [-[P]x, I, [Q]x, -I] over (dw_a, dt_a, dw_b, dt_b),
+// P = R_a p_k, Q = R_b q_k (rotations of the linearisation point).  For the direction d:
+//   y_k = w_sparse w_k (dw_a x P + dt_a - dw_b x Q - dt_b)          (J p, three rows)
+//   J^T y_k = (P x y_k, y_k) for frame a, (-(Q x y_k), -y_k) for frame b.
+// The calling warp walks the pair's segments with lane-strided correspondences; the 12 sums
+// (frame a's six, then frame b's) reach every lane through a butterfly.  da / db are the two
+// frames' direction blocks (zero for a gauge frame).
+__device__ void mf_pair(const Tables &t, const MatFree &mf, int pr, const float (&da)[6], const float (&db)[6],
+                        float (&out)[12]) {
+  const int lane = threadIdx.x & 31;
+  const double *Ta = mf.pose + 12 * t.pair_a[pr], *Tb = mf.pose + 12 * t.pair_b[pr];
+  float Ra[9], Rb[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    Ra[k] = (float)Ta[k];
+    Rb[k] = (float)Tb[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) out[k] = 0.f;
+  for (int s = t.pair_seg0[pr]; s < t.pair_seg1[pr]; ++s) {
+    const int off = t.seg_off[s], cnt = t.seg_cnt[s];
+    const bool swap = t.seg_swap[s] != 0;
+    for (int k = lane; k < cnt; k += 32) {
+      const float4 u = mf.P[off + k], v = mf.Q[off + k];
+      const float px = swap ? v.x : u.x, py = swap ? v.y : u.y, pz = swap ? v.z : u.z;
+      const float qx = swap ? u.x : v.x, qy = swap ? u.y : v.y, qz = swap ? u.z : v.z;
+      const float w = mf.w_sparse * u.w;
+      const float P0 = Ra[0] * px + Ra[1] * py + Ra[2] * pz;
+      const float P1 = Ra[3] * px + Ra[4] * py + Ra[5] * pz;
+      const float P2 = Ra[6] * px + Ra[7] * py + Ra[8] * pz;
+      const float Q0 = Rb[0] * qx + Rb[1] * qy + Rb[2] * qz;
+      const float Q1 = Rb[3] * qx + Rb[4] * qy + Rb[5] * qz;
+      const float Q2 = Rb[6] * qx + Rb[7] * qy + Rb[8] * qz;
+      const float y0 = w * ((da[1] * P2 - da[2] * P1) + da[3] - (db[1] * Q2 - db[2] * Q1) - db[3]);
+      const float y1 = w * ((da[2] * P0 - da[0] * P2) + da[4] - (db[2] * Q0 - db[0] * Q2) - db[4]);
+      const float y2 = w * ((da[0] * P1 - da[1] * P0) + da[5] - (db[0] * Q1 - db[1] * Q0) - db[5]);
+      out[0] += P1 * y2 - P2 * y1;
+      out[1] += P2 * y0 - P0 * y2;
+      out[2] += P0 * y1 - P1 * y0;
+      out[3] += y0;
+      out[4] += y1;
+      out[5] += y2;
+      out[6] -= Q1 * y2 - Q2 * y1;
+      out[7] -= Q2 * y0 - Q0 * y2;
+      out[8] -= Q0 * y1 - Q1 * y0;
+      out[9] -= y0;
+      out[10] -= y1;
+      out[11] -= y2;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 12; ++k) out[k] = warp_sum(out[k]);
+}
+
 // Problems with at most PCG_SMALL_N unknowns (16 free frames) are solved from a dense copy of
 // their system in shared memory, one thread per unknown with its x, r, z, p in registers: no
 // global-memory round trip inside the iteration.  The choice depends on the problem alone, so a
@@ -670,7 +729,7 @@ __global__ void __launch_bounds__(PCG_BS)
     k_pcg(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff, const float *__restrict__ Minv,
           const Acc *__restrict__ rhs, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
           float *__restrict__ p, float *__restrict__ q, int n_pcg, int *__restrict__ pflags,
-          const Acc *__restrict__ pairen, PcgOut po) {
+          const Acc *__restrict__ pairen, PcgOut po, MatFree mf) {
   __shared__ float wsum[PCG_BS / 32];
   __shared__ PcgScal S;
   __shared__ Acc esh[EN_BS / 32][PAIREN];
@@ -678,7 +737,7 @@ __global__ void __launch_bounds__(PCG_BS)
   if (po.energy) problem_energy<Acc>(t, pairen, prob, po.energy, esh);
   const int v0 = t.prob_var0[prob], v1 = t.prob_var1[prob];
   const int u0 = 6 * v0, u1 = 6 * v1;
-  if (u1 - u0 <= PCG_SMALL_N) {
+  if (u1 - u0 <= PCG_SMALL_N && !mf.P) {
     const int flag = pcg_small<Acc>(t, Df, pairoff, Minv, rhs, x, n_pcg, v0, v1, wsum, S);
     if (threadIdx.x == 0 && pflags) pflags[prob] |= flag;
     pcg_finish(t, x, prob, v0, v1, po);
@@ -702,6 +761,25 @@ __global__ void __launch_bounds__(PCG_BS)
   __syncthreads();
   for (int it = 0; it < n_pcg; ++it) {
     if (S.stop) break;
+    if (mf.P) {
+      // matrix-free sparse term: every pair's J^T W J p (warps over the problem's pairs), added
+      // below by the pair's two frames
+      const int lane = threadIdx.x & 31;
+      for (int pr = t.prob_pair0[prob] + (threadIdx.x >> 5); pr < t.prob_pair1[prob]; pr += PCG_BS / 32) {
+        float da[6], db[6], y[12];
+        const int va = t.frame_var[t.pair_a[pr]], vb = t.frame_var[t.pair_b[pr]];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          da[k] = va >= 0 ? p[6 * va + k] : 0.f;
+          db[k] = vb >= 0 ? p[6 * vb + k] : 0.f;
+        }
+        mf_pair(t, mf, pr, da, db, y);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          if (lane == k) mf.mfy[12 * pr + k] = y[k];
+      }
+      __syncthreads();
+    }
     loc = 0.f;
     for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
       const int v = u / 6, c = u % 6;
@@ -711,6 +789,7 @@ __global__ void __launch_bounds__(PCG_BS)
                 Drow[5] * pv[5];
       for (int e = t.inc_off[v]; e < t.inc_off[v + 1]; ++e) {
         const int ov = t.inc_ov[e];
+        if (mf.P) s += mf.mfy[12 * (t.inc[e] >> 1) + 6 * (t.inc[e] & 1) + c];
         if (ov < 0) continue;
         const int ent = t.inc[e];
         const int pr = ent >> 1, side = ent & 1;
@@ -757,15 +836,17 @@ __global__ void __launch_bounds__(PCG_BS)
 template <typename Acc>
 int launch_pcg(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs, float *x,
                float *r, float *z, float *p, float *q, int n_pcg, int *pflags, const Acc *pairen, PcgOut po,
-               cudaStream_t st) {
+               const MatFree &mf, cudaStream_t st) {
   if (t.n_prob == 0) return 0;
-  k_pcg<Acc><<<t.n_prob, PCG_BS, 0, st>>>(t, Df, pairoff, Minv, rhs, x, r, z, p, q, n_pcg, pflags, pairen, po);
+  k_pcg<Acc><<<t.n_prob, PCG_BS, 0, st>>>(t, Df, pairoff, Minv, rhs, x, r, z, p, q, n_pcg, pflags, pairen, po, mf);
   return 1;
 }
 template int launch_pcg<double>(const Tables &, const float *, const float *, const float *, const double *, float *,
-                                float *, float *, float *, float *, int, int *, const double *, PcgOut, cudaStream_t);
+                                float *, float *, float *, float *, int, int *, const double *, PcgOut,
+                                const MatFree &, cudaStream_t);
 template int launch_pcg<float>(const Tables &, const float *, const float *, const float *, const float *, float *,
-                               float *, float *, float *, float *, int, int *, const float *, PcgOut, cudaStream_t);
+                               float *, float *, float *, float *, int, int *, const float *, PcgOut, const MatFree &,
+                               cudaStream_t);
 
 // ------------------------------------------------------------- PCG, one problem over the grid
 constexpr int COOP_BS = 256;
@@ -833,7 +914,7 @@ __global__ void __launch_bounds__(COOP_BS)
     k_pcg_coop(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff,
                const float *__restrict__ Minv, const Acc *__restrict__ rhs, float *x, float *r, float *z, float *p0,
                float *p1, float *q, int n_pcg, int *__restrict__ pflags, CoopState cs,
-               const Acc *__restrict__ pairen, PcgOut po) {
+               const Acc *__restrict__ pairen, PcgOut po, MatFree mf) {
   __shared__ float wsum[COOP_WARPS];
   __shared__ PcgScal S;
   __shared__ Acc esh[EN_BS / 32][PAIREN];
@@ -878,6 +959,24 @@ __global__ void __launch_bounds__(COOP_BS)
     // Phase A: p_new = z + beta p_old (own frames); q = A p_new with the neighbours' p_new formed
     // on the fly from z and p_old (both final since the last barrier)
     const float fb = S.fb;
+    if (mf.P) {
+      // Phase A0 (matrix-free sparse term): every pair's J^T W J p_new, p_new of both frames formed
+      // on the fly like the neighbours' below; the frames add their pairs' shares in phase A
+      for (int pr = gw; pr < t.n_pairs; pr += nw) {
+        float da[6], db[6], y[12];
+        const int va = t.frame_var[t.pair_a[pr]], vb = t.frame_var[t.pair_b[pr]];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          da[k] = va >= 0 ? __ldcg(z + 6 * va + k) + fb * __ldcg(pold + 6 * va + k) : 0.f;
+          db[k] = vb >= 0 ? __ldcg(z + 6 * vb + k) + fb * __ldcg(pold + 6 * vb + k) : 0.f;
+        }
+        mf_pair(t, mf, pr, da, db, y);
+#pragma unroll
+        for (int k = 0; k < 12; ++k)
+          if (lane == k) mf.mfy[12 * pr + k] = y[k];
+      }
+      if (!grid_barrier(cs.count, cs.gen, gridDim.x, err)) return;
+    }
     float lpq = 0.f;
     for (int v = v0 + gw; v < v1; v += nw) {
       float pn[6];
@@ -886,6 +985,11 @@ __global__ void __launch_bounds__(COOP_BS)
       float acc[6] = {0, 0, 0, 0, 0, 0};
       for (int e = t.inc_off[v] + lane; e < t.inc_off[v + 1]; e += 32) {
         const int ov = t.inc_ov[e];
+        if (mf.P) {
+          const float *y = mf.mfy + 12 * (t.inc[e] >> 1) + 6 * (t.inc[e] & 1);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) acc[c] += __ldcg(y + c);
+        }
         if (ov < 0) continue;
         const int ent = t.inc[e];
         const int pr = ent >> 1, side = ent & 1;
@@ -994,7 +1098,8 @@ size_t coop_mem_bytes(int grid) { return 256 + 2 * 8 * (size_t)grid; }
 template <typename Acc>
 int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
                     float *x, float *r, float *z, float *p0, float *p1, float *q, int n_pcg, int *pflags,
-                    void *coop_mem, int grid, const Acc *pairen, PcgOut po, cudaStream_t st) {
+                    void *coop_mem, int grid, const Acc *pairen, PcgOut po, const MatFree &mf,
+                    cudaStream_t st) {
   if (t.n_vars == 0) return 0;
   CoopState cs;
   char *m = (char *)coop_mem;
@@ -1005,7 +1110,8 @@ int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, cons
   cs.part_rz = m + 256 + 8 * (size_t)grid;
   if (cudaMemsetAsync(m, 0, 16, st) != cudaSuccess) return -1;
   Tables tt = t;
-  void *args[] = {&tt, &Df, &pairoff, &Minv, &rhs, &x, &r, &z, &p0, &p1, &q, &n_pcg, &pflags, &cs, &pairen, &po};
+  MatFree mff = mf;
+  void *args[] = {&tt, &Df, &pairoff, &Minv, &rhs, &x, &r, &z, &p0, &p1, &q, &n_pcg, &pflags, &cs, &pairen, &po, &mff};
   if (cudaLaunchCooperativeKernel((const void *)k_pcg_coop<Acc>, dim3(grid), dim3(COOP_BS), args, 0, st) !=
       cudaSuccess)
     return -1;
@@ -1013,10 +1119,10 @@ int launch_pcg_coop(const Tables &t, const float *Df, const float *pairoff, cons
 }
 template int launch_pcg_coop<double>(const Tables &, const float *, const float *, const float *, const double *,
                                      float *, float *, float *, float *, float *, float *, int, int *, void *, int,
-                                     const double *, PcgOut, cudaStream_t);
+                                     const double *, PcgOut, const MatFree &, cudaStream_t);
 template int launch_pcg_coop<float>(const Tables &, const float *, const float *, const float *, const float *,
                                     float *, float *, float *, float *, float *, float *, int, int *, void *, int,
-                                    const float *, PcgOut, cudaStream_t);
+                                    const float *, PcgOut, const MatFree &, cudaStream_t);
 
 // ------------------------------------------------------ PCG, one problem on a thread-block cluster
 // One cluster of CL CTAs (up to 16, one per SM) solves one problem.  Every CTA keeps replicas of
@@ -1162,6 +1268,7 @@ __global__ void __launch_bounds__(CL_BS, 1)
       const int lo = ov - v0;
       sov[e] = ov < 0 ? -1 : (((lo / per) << 16) | (lo % per));
     }
+    __syncthreads();  // the init below reads sM rows that other threads of the CTA filled
   }
   // Frames are processed by CL_G-lane groups: group g of a warp owns frame base + g; within a
   // group lane gl walks the frame's incidences gl, gl + CL_G, ... and lanes gl < 6 own the

@@ -9,10 +9,12 @@
 // world-frame Jacobian -[R_a p]_x, I, [R_b q]_x, -I.)  The per-segment sums are reduced by the
 // same fixed-order tree as the dense tiles.
 //
-// The paper applies the sparse term matrix-free inside PCG (J p, then J^T (J p)); here its
-// 6x6 pair blocks are formed once per Gauss-Newton iteration, like the dense term, because a
-// pair's block costs 72 values while its correspondences are re-read every PCG iteration
-// otherwise.
+// The paper applies the sparse term matrix-free inside PCG (J p, then J^T (J p)); by default
+// its 6x6 pair blocks are formed here once per Gauss-Newton iteration, like the dense term,
+// because a pair's block costs 72 values while its correspondences are re-read every PCG
+// iteration otherwise.  The matrix-free scheme is the BF_SPARSE_MATFREE option (mf_pair in
+// solve.cu); these sums then still give the right-hand side, the preconditioner's diagonal
+// blocks and the energy.
 #include "bf_internal.cuh"
 
 namespace bf {

@@ -116,3 +116,20 @@ def test_large_sparse_slice_matches_oracle(bf):
     for k in range(n):
         rot, tr = lie.pose_error(Pg[k], ref.poses[k])
         assert rot <= 1e-4 and tr <= 1e-5, (k, rot, tr)
+
+
+def test_cluster_pcg_with_block_cache_is_repeatable(bf):
+    """The 300-frame slice runs the cluster PCG with its shared-memory block cache; repeated solves
+    must give the same bits and never report a PCG breakdown (the cache is filled by all threads of
+    a CTA and read by others, so a missing barrier there shows up as an occasional wrong first z)."""
+    gt, init, pairs, P, Q = sparse_chain(300, 97)
+    n = len(gt)
+    first = None
+    for _ in range(8):
+        ctx = sparse_ctx(bf, init, pairs, P, Q)
+        st = ctx.solve_global(list(range(n)), n_gn=3, n_pcg=30, dense_on=0, pcg_variant=3)
+        assert st["flags"] == 0
+        if first is None:
+            first = st["energy"]
+        assert st["energy"] == first
+        ctx.close()
