@@ -767,6 +767,7 @@ struct HostTables {
   std::vector<int> dp_src, dp_dst, dp_pair, dp_dir, dp_tile0, dp_tile1, tile_dp, tile_px0, tile_px1;
   std::vector<int> seg_pair, seg_off, seg_cnt, seg_swap, inc_off, inc, inc_ov, var_frame;
   std::vector<int> prob_var0, prob_var1, prob_pair0, prob_pair1, prob_frame0;
+  std::vector<int> prob_tile0, prob_tile1, prob_seg0, prob_seg1;
   int n_wi = 0;                        // target-staged dense work items (0: tiled kernel)
   std::vector<int> wi_off, sw_dp, dp_dst_host;
   std::vector<int> pair_ida, pair_idb;  // frame ids of the pair (for stats)
@@ -832,6 +833,8 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
       std::sort(plist.begin(), plist.end());
     }
     T.prob_pair0.push_back(T.n_pairs);
+    T.prob_tile0.push_back(T.n_tiles);
+    T.prob_seg0.push_back(T.n_segs);
     int ndense = 0;
     long long ncorr = 0;
     for (auto &ab : plist) {
@@ -890,6 +893,8 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
       if (b != 0) var_inc[T.frame_var[F0 + b]].push_back({p, 1});
     }
     T.prob_pair1.push_back(T.n_pairs);
+    T.prob_tile1.push_back(T.n_tiles);
+    T.prob_seg1.push_back(T.n_segs);
     T.prob_npairs.push_back((int)plist.size());
     T.prob_ndense.push_back(ndense);
     T.prob_ncorr.push_back(ncorr);
@@ -1105,6 +1110,10 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     t.prob_var1 = nxt(T.prob_var1.size());
     t.prob_pair0 = nxt(T.prob_pair0.size());
     t.prob_pair1 = nxt(T.prob_pair1.size());
+    t.prob_tile0 = nxt(T.prob_tile0.size());
+    t.prob_tile1 = nxt(T.prob_tile1.size());
+    t.prob_seg0 = nxt(T.prob_seg0.size());
+    t.prob_seg1 = nxt(T.prob_seg1.size());
     t.n_wi = T.n_wi;
     t.wi_off = nxt(T.wi_off.size());
     t.sw_dp = nxt(T.sw_dp.size());
@@ -1118,7 +1127,8 @@ std::vector<int> pack_ints(const HostTables &T) {
        {&T.frame_slot, &T.frame_var, &T.pair_a, &T.pair_b, &T.pair_dp, &T.pair_seg0, &T.pair_seg1, &T.dp_src,
         &T.dp_dst, &T.dp_pair, &T.dp_dir, &T.dp_tile0, &T.dp_tile1, &T.tile_dp, &T.tile_px0, &T.tile_px1,
         &T.seg_pair, &T.seg_off, &T.seg_cnt, &T.seg_swap, &T.inc_off, &T.inc, &T.inc_ov, &T.var_frame, &T.prob_var0,
-        &T.prob_var1, &T.prob_pair0, &T.prob_pair1, &T.wi_off, &T.sw_dp})
+        &T.prob_var1, &T.prob_pair0, &T.prob_pair1, &T.prob_tile0, &T.prob_tile1, &T.prob_seg0, &T.prob_seg1,
+        &T.wi_off, &T.sw_dp})
     v.insert(v.end(), x->begin(), x->end());
   return v;
 }
@@ -2363,6 +2373,10 @@ extern "C" bf_status bf_debug_association(bf_ctx *c, int frame_i, int frame_j, c
   T.prob_var1 = {0};
   T.prob_pair0 = {0};
   T.prob_pair1 = {1};
+  T.prob_tile0 = {0};
+  T.prob_tile1 = {T.n_tiles};
+  T.prob_seg0 = {0};
+  T.prob_seg1 = {0};
   const Pose12 a = from16(pose_i), b = from16(pose_j);
   T.pose.assign(a.begin(), a.end());
   T.pose.insert(T.pose.end(), b.begin(), b.end());

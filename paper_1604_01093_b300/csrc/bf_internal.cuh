@@ -128,6 +128,7 @@ struct Tables {
   const int *inc_ov;                // [n_inc] var block of the pair's other frame, -1 for a gauge frame
   const int *var_frame;             // [n_vars]
   const int *prob_var0, *prob_var1, *prob_pair0, *prob_pair1;  // [n_prob]
+  const int *prob_tile0, *prob_tile1, *prob_seg0, *prob_seg1;  // [n_prob] the problem's tiles / segments
   // target-staged dense work items (small frames): item w covers sw_dp[wi_off[w] .. wi_off[w+1]),
   // directed pairs that share one target frame
   int n_wi;
@@ -161,11 +162,21 @@ __device__ __forceinline__ void pair_xform32(const double *Ti, const double *Tj,
   for (int e = 0; e < 12; ++e) M[e] = pair_xform_entry(Ti, Tj, e);
 }
 
+// Load through L2 when CG (data written by another CTA of the same persistent launch, which the
+// SM's L1 may hold an older copy of), a plain load otherwise.
+template <bool CG, typename X>
+__device__ __forceinline__ X ldx(const X *p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+
 // Exp-map pose update R <- Exp(dw) R, t <- t + dt in FP64 (Rodrigues: Exp(dw) = I + A K + B K^2,
 // K = [dw]x, K^2 = dw dw^T - th^2 I, A = sin(th) / th, B = (1 - cos(th)) / th^2).  For th <= 1/2
 // (every step but a gross first one) A and B come from their Taylor series in th^2, eight terms
 // each, the first omitted term below 1e-17 relative: FP64 runs at 1/64 of the FP32 rate on B300
 // and the series needs 16 FMAs where sin, cos and two divisions need several times that.
+// CG: the current pose is read through L2 (see ldx).
+template <bool CG = false>
 __device__ __forceinline__ void update_pose(double *T, const float *x) {
   const double w0 = x[0], w1 = x[1], w2 = x[2];
   const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
@@ -203,16 +214,19 @@ __device__ __forceinline__ void update_pose(double *T, const float *x) {
       const double K2 = w[i] * w[j] - (i == j ? th2 : 0.0);
       E[i][j] = (i == j ? 1.0 : 0.0) + A * K[i][j] + B * K2;
     }
+  double T0[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) T0[k] = ldx<CG>(T + k);
   double R[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) R[3 * i + j] = E[i][0] * T[j] + E[i][1] * T[3 + j] + E[i][2] * T[6 + j];
+    for (int j = 0; j < 3; ++j) R[3 * i + j] = E[i][0] * T0[j] + E[i][1] * T0[3 + j] + E[i][2] * T0[6 + j];
 #pragma unroll
   for (int k = 0; k < 9; ++k) T[k] = R[k];
-  T[9] += (double)x[3];
-  T[10] += (double)x[4];
-  T[11] += (double)x[5];
+  T[9] = T0[9] + (double)x[3];
+  T[10] = T0[10] + (double)x[4];
+  T[11] = T0[11] + (double)x[5];
 }
 
 // ------------------------------------------------------------------------- bounded waits

@@ -1,0 +1,229 @@
+// Dense photometric + geometric term evaluation shared by the dense kernels of dense.cu and the
+// persistent batched solve of solve.cu (per-pixel association, residuals, Jacobians and the
+// per-tile reduction; the design notes are at the top of dense.cu).
+#pragma once
+#include "bf_internal.cuh"
+
+namespace bf {
+
+
+#define FM __fmul_rn
+#define FA __fadd_rn
+#define FS __fsub_rn
+
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 cross3(V3 a, V3 b) {
+  return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// Accumulate one dense residual row (weight w, residual r, Jacobian [v x t - c, v, c, -v]).
+__device__ __forceinline__ void accum_vc(float (&acc)[NPD], float w, float r, V3 v, V3 c) {
+  const float wv0 = w * v.x, wv1 = w * v.y, wv2 = w * v.z;
+  const float wc0 = w * c.x, wc1 = w * c.y, wc2 = w * c.z;
+  acc[D_VV + 0] += wv0 * v.x; acc[D_VV + 1] += wv0 * v.y; acc[D_VV + 2] += wv0 * v.z;
+  acc[D_VV + 3] += wv1 * v.y; acc[D_VV + 4] += wv1 * v.z; acc[D_VV + 5] += wv2 * v.z;
+  acc[D_VC + 0] += wv0 * c.x; acc[D_VC + 1] += wv0 * c.y; acc[D_VC + 2] += wv0 * c.z;
+  acc[D_VC + 3] += wv1 * c.x; acc[D_VC + 4] += wv1 * c.y; acc[D_VC + 5] += wv1 * c.z;
+  acc[D_VC + 6] += wv2 * c.x; acc[D_VC + 7] += wv2 * c.y; acc[D_VC + 8] += wv2 * c.z;
+  acc[D_CC + 0] += wc0 * c.x; acc[D_CC + 1] += wc0 * c.y; acc[D_CC + 2] += wc0 * c.z;
+  acc[D_CC + 3] += wc1 * c.y; acc[D_CC + 4] += wc1 * c.z; acc[D_CC + 5] += wc2 * c.z;
+  acc[D_GV + 0] += r * wv0; acc[D_GV + 1] += r * wv1; acc[D_GV + 2] += r * wv2;
+  acc[D_GC + 0] += r * wc0; acc[D_GC + 1] += r * wc1; acc[D_GC + 2] += r * wc2;
+}
+
+// Fixed-order CTA reduction of N values; thread k < N writes out[k].
+// red: shared memory of BS / 32 rows of N floats.
+template <int BS, int N, typename Part>
+__device__ __forceinline__ void cta_reduce_store(float (&acc)[N], Part *__restrict__ out, float (*red)[N]) {
+  constexpr int NW = BS / 32;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float v = acc[k];
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if (lane == 0) red[warp][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < N) {
+    Part s = (Part)red[0][threadIdx.x];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) s += (Part)red[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+// Relative pose of a directed pair (FP32): y = R d + t maps source-camera to target-camera points.
+struct PairXf {
+  float R00, R01, R02, R10, R11, R12, R20, R21, R22, t0, t1, t2;
+};
+
+// CG: read through L2 (the transforms were written by another CTA of a persistent launch).
+template <bool CG = false>
+__device__ __forceinline__ PairXf load_xf(const float *M) {
+  if (CG)
+    return PairXf{__ldcg(M), __ldcg(M + 1), __ldcg(M + 2), __ldcg(M + 3), __ldcg(M + 4),  __ldcg(M + 5),
+                  __ldcg(M + 6), __ldcg(M + 7), __ldcg(M + 8), __ldcg(M + 9), __ldcg(M + 10), __ldcg(M + 11)};
+  return PairXf{M[0], M[1], M[2], M[3], M[4], M[5], M[6], M[7], M[8], M[9], M[10], M[11]};
+}
+
+// Evaluate source pixel (x, y) of a directed pair: association, gates and (MODE_ACCUM) the
+// residual rows' contributions to acc.  a = source (D, n); loadA / loadB read the target's
+// (D, n) and (I, Ix, Iy); srcI() gives the source pixel's I.  Returns the associated target
+// pixel or -1.
+template <int MODE, typename LA, typename LB, typename LI>
+__device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const PairXf &X, const Intr &in,
+                                          const float *kx, const float *ky, const Gates &g, LA loadA, LB loadB,
+                                          LI srcI, float w_geo, float w_photo, float (&acc)[NPD]) {
+  const bool nvalid = (a.y != 0.f) || (a.z != 0.f) || (a.w != 0.f);
+  if (!(a.x > 0.f && nvalid)) return -1;
+  const int W = in.W, H = in.H;
+  const float z = a.x;
+  // ---- association decisions, explicitly rounded FP32 in a fixed order ----
+  const float dx = FM(kx[x], z), dy = FM(ky[y], z), dz = z;
+  const float Y0 = FA(FA(FA(FM(X.R00, dx), FM(X.R01, dy)), FM(X.R02, dz)), X.t0);
+  const float Y1 = FA(FA(FA(FM(X.R10, dx), FM(X.R11, dy)), FM(X.R12, dz)), X.t1);
+  const float Y2 = FA(FA(FA(FM(X.R20, dx), FM(X.R21, dy)), FM(X.R22, dz)), X.t2);
+  if (!(Y2 > 0.f)) return -1;
+  const float iz = __frcp_rn(Y2);
+  const float ux = FA(FM(in.fx, FM(Y0, iz)), in.cx);
+  const float uy = FA(FM(in.fy, FM(Y1, iz)), in.cy);
+  const float nxf = floorf(FA(ux, 0.5f)), nyf = floorf(FA(uy, 0.5f));
+  const float bxf = floorf(ux), byf = floorf(uy);
+  if (!(nxf >= 0.f && nxf <= (float)(W - 1) && nyf >= 0.f && nyf <= (float)(H - 1) && bxf >= 2.f &&
+        FA(bxf, 1.f) <= (float)(W - 3) && byf >= 2.f && FA(byf, 1.f) <= (float)(H - 3)))
+    return -1;
+  const int tx = (int)nxf, ty = (int)nyf;
+  const int bx = (int)bxf, by = (int)byf;
+  const int tpx = ty * W + tx, b0 = by * W + bx;
+  // issue the target reads together: nearest (D, n) and the four (I, Ix, Iy) taps
+  const float4 b = loadA(tpx);
+  float4 c00, c01, c10, c11;
+  if (MODE != MODE_ASSOC) {
+    c00 = loadB(b0);
+    c01 = loadB(b0 + 1);
+    c10 = loadB(b0 + W);
+    c11 = loadB(b0 + W + 1);
+  }
+  const bool tnvalid = (b.y != 0.f) || (b.z != 0.f) || (b.w != 0.f);
+  if (!(b.x > 0.f && tnvalid)) return -1;
+  const float qx = FM(kx[tx], b.x), qy = FM(ky[ty], b.x), qz = b.x;
+  const float ex = FS(Y0, qx), ey = FS(Y1, qy), ez = FS(Y2, qz);
+  const float dist2 = FA(FA(FM(ex, ex), FM(ey, ey)), FM(ez, ez));
+  const float m0 = FA(FA(FM(X.R00, a.y), FM(X.R01, a.z)), FM(X.R02, a.w));
+  const float m1 = FA(FA(FM(X.R10, a.y), FM(X.R11, a.z)), FM(X.R12, a.w));
+  const float m2 = FA(FA(FM(X.R20, a.y), FM(X.R21, a.z)), FM(X.R22, a.w));
+  const float ndot = FA(FA(FM(m0, b.y), FM(m1, b.z)), FM(m2, b.w));
+  if (!(dist2 < g.tau_d2 && ndot > g.tau_n)) return -1;
+  if (MODE == MODE_ASSOC) return tpx;
+  // ---- residuals and Jacobians (free FP32) in camera-j coordinates ----
+  const float r_g = m0 * ex + m1 * ey + m2 * ez;
+  const float wx = ux - bxf, wy = uy - byf;
+  const float w00 = (1.f - wx) * (1.f - wy), w01 = wx * (1.f - wy);
+  const float w10 = (1.f - wx) * wy, w11 = wx * wy;
+  const float Ij = w00 * c00.x + w01 * c01.x + w10 * c10.x + w11 * c11.x;
+  const float gxI = w00 * c00.y + w01 * c01.y + w10 * c10.y + w11 * c11.y;
+  const float gyI = w00 * c00.z + w01 * c01.z + w10 * c10.z + w11 * c11.z;
+  const float r_p = srcI() - Ij;
+  acc[D_E0] += r_g * r_g;
+  acc[D_E1] += r_p * r_p;
+  acc[D_CNT] += 1.f;
+  if (MODE == MODE_ACCUM) {
+    // geometric: v = m, c = m x q
+    const V3 m{m0, m1, m2}, q{qx, qy, qz};
+    accum_vc(acc, w_geo, r_g, m, cross3(m, q));
+    // photometric: v = g = d r_p / d y = -grad I^T Jpi(y), c = g x y
+    const float gfx = gxI * in.fx * iz, gfy = gyI * in.fy * iz;
+    const V3 gv{-gfx, -gfy, (gfx * Y0 + gfy * Y1) * iz};
+    accum_vc(acc, w_photo, r_p, gv, cross3(gv, V3{Y0, Y1, Y2}));
+  }
+  return tpx;
+}
+
+// Pixel walk of one thread: px = start, start + stride, ... with (x, y) advanced incrementally.
+struct PixWalk {
+  int px, x, y, sx, sy, W;
+  __device__ __forceinline__ PixWalk(int start, int stride, int W_) : px(start), W(W_) {
+    y = start / W_;
+    x = start - y * W_;
+    sy = stride / W_;
+    sx = stride - sy * W_;
+  }
+  __device__ __forceinline__ void next(int stride) {
+    px += stride;
+    x += sx;
+    y += sy;
+    if (x >= W) {
+      x -= W;
+      ++y;
+    }
+  }
+};
+
+constexpr int DENSE_BS = 256;
+
+// One dense tile (work item = consecutive source pixels of one directed pair), evaluated by a
+// CTA of DENSE_BS threads.  ktab holds kx[W] then ky[H] (loaded by the caller); red is the
+// reduction's shared memory.  Ends with the CTA's partial record written by threads < NPD.
+template <int MODE, int KIND, typename Part, bool CG = false>
+__device__ __forceinline__ void dense_tile(int tile, const Tables &t, const FrameStore &fs, const Intr &in,
+                                           const float *__restrict__ pairM, const Gates &g, float w_geo,
+                                           float w_photo, Part *__restrict__ part, int *__restrict__ assoc,
+                                           const float *ktab, float (*red)[NPD]) {
+  const int d = t.tile_dp[tile];
+  const int px0 = t.tile_px0[tile], px1 = t.tile_px1[tile];
+  const int W = in.W, H = in.H;
+  const long long HW = (long long)W * H;
+  const int ss = t.frame_slot[t.dp_src[d]], ts = t.frame_slot[t.dp_dst[d]];
+  const PairXf X = load_xf<CG>(pairM + (t.dp_pair[d] * 2 + t.dp_dir[d]) * 12);
+  const float *kx = ktab, *ky = ktab + W;
+  float acc[NPD];
+#pragma unroll
+  for (int k = 0; k < NPD; ++k) acc[k] = 0.f;
+  if (KIND == BF_STORE_FP32) {
+    const float4 *__restrict__ As = fs.A + (long long)ss * HW;
+    const float4 *__restrict__ Bs = fs.B + (long long)ss * HW;
+    const float4 *__restrict__ At = fs.A + (long long)ts * HW;
+    const float4 *__restrict__ Bt = fs.B + (long long)ts * HW;
+    auto loadA = [&](int i) { return At[i]; };
+    auto loadB = [&](int i) { return Bt[i]; };
+    float4 a_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (px0 + (int)threadIdx.x < px1) a_next = As[px0 + threadIdx.x];
+    for (PixWalk w(px0 + threadIdx.x, DENSE_BS, W); w.px < px1; w.next(DENSE_BS)) {
+      const float4 a = a_next;  // prefetched one iteration ahead
+      if (w.px + DENSE_BS < px1) a_next = As[w.px + DENSE_BS];
+      const int px = w.px;
+      auto srcI = [&]() { return Bs[px].x; };
+      const int tgt = eval_pixel<MODE>(a, w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
+      if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
+    }
+  } else {
+    const uint4 *__restrict__ Ps = fs.P16 + (long long)ss * HW;
+    const uint4 *__restrict__ Pt = fs.P16 + (long long)ts * HW;
+    auto loadA = [&](int i) { return unpack16_dn<KIND>(Pt[i]); };
+    auto loadB = [&](int i) { return unpack16_i<KIND>(Pt[i]); };
+    uint4 r_next = make_uint4(0u, 0u, 0u, 0u);
+    if (px0 + (int)threadIdx.x < px1) r_next = Ps[px0 + threadIdx.x];
+    for (PixWalk w(px0 + threadIdx.x, DENSE_BS, W); w.px < px1; w.next(DENSE_BS)) {
+      const uint4 r = r_next;
+      if (w.px + DENSE_BS < px1) r_next = Ps[w.px + DENSE_BS];
+      auto srcI = [&]() { return unpack16_i<KIND>(r).x; };
+      const int tgt = eval_pixel<MODE>(unpack16_dn<KIND>(r), w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo,
+                                       w_photo, acc);
+      if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
+    }
+  }
+  if (MODE != MODE_ASSOC) cta_reduce_store<DENSE_BS, NPD, Part>(acc, part + (long long)tile * NPD, red);
+}
+
+
+#undef FM
+#undef FA
+#undef FS
+
+}  // namespace bf

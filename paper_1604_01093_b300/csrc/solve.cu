@@ -142,22 +142,27 @@ constexpr int MERGE_WARPS = 1;  // one warp per CTA spreads the pairs over the S
 // NPART layout first and rotated to world coordinates once, R X R^T in two 3-FMA stages
 // (X R^T, then R (X R^T)); B300 issues FP64 at 1/64 of the FP32 rate, so the merge is bound by
 // its FP64 instruction count.
-template <typename Acc, typename Part>
-__global__ void __launch_bounds__(32 * MERGE_WARPS)
-    k_pair_merge(Tables t, const double *__restrict__ pose, const Part *__restrict__ dpart,
-                 const Part *__restrict__ spart, Acc *__restrict__ pairblk, Acc *__restrict__ pairen,
-                 float *__restrict__ pairoff) {
-  __shared__ Acc S_sh[MERGE_WARPS][NPART + 7];
-  __shared__ Acc T_sh[MERGE_WARPS][54];
-  __shared__ Acc rot_sh[MERGE_WARPS][NROT + 1];
-  __shared__ Acc R_sh[MERGE_WARPS][9];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int p = blockIdx.x * MERGE_WARPS + w;
-  if (p >= t.n_pairs) return;  // whole warp exits together
-  Acc *S = S_sh[w];
-  Acc *T = T_sh[w];
-  Acc *rot = rot_sh[w];
-  Acc *R = R_sh[w];
+// Shared memory of one merging warp.
+template <typename Acc>
+struct MergeSmem {
+  Acc S[NPART + 7];
+  Acc T[54];
+  Acc rot[NROT + 1];
+  Acc R[9];
+};
+
+// Merge of pair p by the calling warp (all 32 lanes).  CG: partials and poses are read through
+// L2 (written by other CTAs of a persistent launch).
+template <typename Acc, typename Part, bool CG = false>
+__device__ __forceinline__ void merge_pair(int p, const Tables &t, const double *__restrict__ pose,
+                                           const Part *__restrict__ dpart, const Part *__restrict__ spart,
+                                           Acc *__restrict__ pairblk, Acc *__restrict__ pairen,
+                                           float *__restrict__ pairoff, MergeSmem<Acc> &sm) {
+  const int lane = threadIdx.x & 31;
+  Acc *S = sm.S;
+  Acc *T = sm.T;
+  Acc *rot = sm.rot;
+  Acc *R = sm.R;
   Acc out[4] = {0, 0, 0, 0};  // slots lane, lane+32, lane+64, lane+96
   Acc en[4] = {0, 0, 0, 0};   // kept by lane 0: e_sparse, e_photo, e_geo, n_dense
   for (int half = 0; half < 2; ++half) {
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
     if (d < 0 && !has_sparse) continue;
     const int tgt = half == 1 ? t.pair_a[p] : t.pair_b[p];
     const int srcf = half == 1 ? t.pair_b[p] : t.pair_a[p];
-    if (lane < 9) R[lane] = (Acc)pose[12 * tgt + lane];
+    if (lane < 9) R[lane] = (Acc)ldx<CG>(pose + 12 * tgt + lane);
     for (int k = lane; k < NPART; k += 32) S[k] = 0;
     __syncwarp();
     if (d >= 0) {
@@ -177,16 +182,18 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
       Acc *Sd = rot;  // scratch for the NPD sums
       for (int k = lane; k < NPD; k += 32) {
         Acc s = 0;
-        for (int it = k0; it < k1; ++it) s += (Acc)dpart[(long long)it * NPD + k];
+        for (int it = k0; it < k1; ++it) s += (Acc)ldx<CG>(dpart + (long long)it * NPD + k);
         Sd[k] = s;
       }
       __syncwarp();
       Acc tt[3];
       {
         const double *Ti = pose + 12 * srcf, *Tj = pose + 12 * tgt;
-        const double d0 = Ti[9] - Tj[9], d1 = Ti[10] - Tj[10], d2 = Ti[11] - Tj[11];
+        const double d0 = ldx<CG>(Ti + 9) - ldx<CG>(Tj + 9), d1 = ldx<CG>(Ti + 10) - ldx<CG>(Tj + 10),
+                     d2 = ldx<CG>(Ti + 11) - ldx<CG>(Tj + 11);
 #pragma unroll
-        for (int m = 0; m < 3; ++m) tt[m] = (Acc)(Tj[m] * d0 + Tj[3 + m] * d1 + Tj[6 + m] * d2);
+        for (int m = 0; m < 3; ++m)
+          tt[m] = (Acc)(ldx<CG>(Tj + m) * d0 + ldx<CG>(Tj + 3 + m) * d1 + ldx<CG>(Tj + 6 + m) * d2);
       }
       const Acc T3[3][3] = {{0, tt[2], -tt[1]}, {-tt[2], 0, tt[0]}, {tt[1], -tt[0], 0}};
       for (int k = lane; k < 6; k += 32) {
@@ -236,7 +243,7 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
       const int k0 = t.pair_seg0[p], k1 = t.pair_seg1[p];
       for (int k = lane; k < NPART; k += 32) {
         Acc s = 0;
-        for (int it = k0; it < k1; ++it) s += (Acc)spart[(long long)it * NPART + k];
+        for (int it = k0; it < k1; ++it) s += (Acc)ldx<CG>(spart + (long long)it * NPART + k);
         if (k == P_E0) S[NPART] = s;  // the sparse energy, read by lane 0 below
         S[k] += s;
       }
@@ -289,6 +296,18 @@ __global__ void __launch_bounds__(32 * MERGE_WARPS)
 #pragma unroll
     for (int k = 0; k < PAIREN; ++k) pairen[(long long)p * PAIREN + k] = en[k];
   }
+}
+
+template <typename Acc, typename Part>
+__global__ void __launch_bounds__(32 * MERGE_WARPS)
+    k_pair_merge(Tables t, const double *__restrict__ pose, const Part *__restrict__ dpart,
+                 const Part *__restrict__ spart, Acc *__restrict__ pairblk, Acc *__restrict__ pairen,
+                 float *__restrict__ pairoff) {
+  __shared__ MergeSmem<Acc> sm[MERGE_WARPS];
+  const int w = threadIdx.x >> 5;
+  const int p = blockIdx.x * MERGE_WARPS + w;
+  if (p >= t.n_pairs) return;  // whole warp exits together
+  merge_pair<Acc, Part>(p, t, pose, dpart, spart, pairblk, pairen, pairoff, sm[w]);
 }
 
 template <typename Acc, typename Part>
@@ -369,15 +388,20 @@ __device__ bool chol_inverse6(const double *D, float *Mi) {
 
 constexpr int ASM_WARPS = 1;  // one warp per CTA spreads the frames over the SMs
 
+// Shared memory of one assembling warp.
+struct AsmSmem {
+  double D[36];
+  float M[36];
+};
+
+// Diagonal block, rhs and preconditioner block of free frame v, by the calling warp.
 template <typename Acc>
-__global__ void __launch_bounds__(32 * ASM_WARPS)
-    k_assemble(Tables t, const Acc *__restrict__ pairblk, int precond, Acc *__restrict__ Dd, Acc *__restrict__ rhs,
-               float *__restrict__ Df, float *__restrict__ Minv, int *__restrict__ vflags) {
-  __shared__ double Dsh[ASM_WARPS][36];
-  __shared__ float Msh[ASM_WARPS][36];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int v = blockIdx.x * ASM_WARPS + w;
-  if (v >= t.n_vars) return;
+__device__ __forceinline__ void assemble_var(int v, const Tables &t, const Acc *__restrict__ pairblk, int precond,
+                                             Acc *__restrict__ Dd, Acc *__restrict__ rhs, float *__restrict__ Df,
+                                             float *__restrict__ Minv, int *__restrict__ vflags, AsmSmem &sm) {
+  const int lane = threadIdx.x & 31;
+  double *Dshw = sm.D;
+  float *Mshw = sm.M;
   const int e0 = t.inc_off[v], e1 = t.inc_off[v + 1];
   // lane handles entries lane and lane + 32 of [D (36) | rhs (6)]; the incidences are read 8 at
   // a time (all loads in flight together) and summed in incidence order
@@ -402,7 +426,7 @@ __global__ void __launch_bounds__(32 * ASM_WARPS)
     if (k < 36) {
       Dd[(long long)v * 36 + k] = s;
       Df[(long long)v * 36 + k] = (float)s;
-      Dsh[w][k] = (double)s;
+      Dshw[k] = (double)s;
     } else {
       rhs[(long long)v * 6 + k - 36] = s;
     }
@@ -412,28 +436,39 @@ __global__ void __launch_bounds__(32 * ASM_WARPS)
     int flag = 0;
     bool empty = true;
     // integer test for +-0 (an FP64 compare would occupy the slow FP64 pipe 36 times)
-    for (int k = 0; k < 36; ++k) empty = empty && ((__double_as_longlong(Dsh[w][k]) << 1) == 0);
-    for (int k = 0; k < 36; ++k) Msh[w][k] = 0.f;
+    for (int k = 0; k < 36; ++k) empty = empty && ((__double_as_longlong(Dshw[k]) << 1) == 0);
+    for (int k = 0; k < 36; ++k) Mshw[k] = 0.f;
     if (empty) {
       flag = 2;  // BF_FLAG_EMPTY_FRAME: zero inverse, the frame's update stays 0
     } else {
       bool ok = false;
       if (precond == 0) {
-        ok = chol_inverse6(Dsh[w], Msh[w]);
+        ok = chol_inverse6(Dshw, Mshw);
         if (!ok) flag = 1;  // BF_FLAG_SINGULAR_BLOCK: fall back to the diagonal
       }
       if (!ok) {
-        for (int k = 0; k < 36; ++k) Msh[w][k] = 0.f;
+        for (int k = 0; k < 36; ++k) Mshw[k] = 0.f;
         for (int k = 0; k < 6; ++k) {
-          const float d = (float)Dsh[w][7 * k];
-          Msh[w][7 * k] = d > 0.f ? 1.f / d : 0.f;
+          const float d = (float)Dshw[7 * k];
+          Mshw[7 * k] = d > 0.f ? 1.f / d : 0.f;
         }
       }
     }
     vflags[v] = flag;
   }
   __syncwarp();
-  for (int k = lane; k < 36; k += 32) Minv[(long long)v * 36 + k] = Msh[w][k];
+  for (int k = lane; k < 36; k += 32) Minv[(long long)v * 36 + k] = Mshw[k];
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(32 * ASM_WARPS)
+    k_assemble(Tables t, const Acc *__restrict__ pairblk, int precond, Acc *__restrict__ Dd, Acc *__restrict__ rhs,
+               float *__restrict__ Df, float *__restrict__ Minv, int *__restrict__ vflags) {
+  __shared__ AsmSmem sm[ASM_WARPS];
+  const int w = threadIdx.x >> 5;
+  const int v = blockIdx.x * ASM_WARPS + w;
+  if (v >= t.n_vars) return;
+  assemble_var<Acc>(v, t, pairblk, precond, Dd, rhs, Df, Minv, vflags, sm[w]);
 }
 
 template <typename Acc>
@@ -625,9 +660,8 @@ constexpr int PCG_SMALL_N = 96;
 template <typename Acc>
 __device__ int pcg_small(const Tables &t, const float *__restrict__ Df, const float *__restrict__ pairoff,
                          const float *__restrict__ Minv, const Acc *__restrict__ rhs, float *__restrict__ x,
-                         int n_pcg, int v0, int v1, float *wsum, PcgScal &S) {
-  __shared__ float AT[PCG_SMALL_N * PCG_SMALL_N];  // column-major: AT[k * n + u] = A[u][k]
-  __shared__ float sp[PCG_SMALL_N], sr[PCG_SMALL_N];
+                         int n_pcg, int v0, int v1, float *wsum, PcgScal &S, float *AT, float *sp, float *sr) {
+  // AT: column-major dense system, AT[k * n + u] = A[u][k]; sp, sr: p and r of the iteration
   const int n = 6 * (v1 - v0);
   const int u = threadIdx.x;
   const bool own = u < n;
@@ -708,10 +742,11 @@ __device__ int pcg_small(const Tables &t, const float *__restrict__ Df, const fl
 
 // After the solve: pose update of the problem's free frames, then its pairs' transforms at the
 // new poses (both need the whole block's x, respectively poses, written first).
+template <bool CG = false>
 __device__ void pcg_finish(const Tables &t, const float *x, int prob, int v0, int v1, const PcgOut &po) {
   __syncthreads();
   if (!po.pose) return;
-  for (int v = v0 + threadIdx.x; v < v1; v += PCG_BS) update_pose(po.pose + 12 * t.var_frame[v], x + 6 * v);
+  for (int v = v0 + threadIdx.x; v < v1; v += PCG_BS) update_pose<CG>(po.pose + 12 * t.var_frame[v], x + 6 * v);
   if (!po.pairM) return;
   __syncthreads();
   // one thread per transform entry (24 per pair): the FP64 work spreads over all warps
@@ -724,23 +759,35 @@ __device__ void pcg_finish(const Tables &t, const float *x, int prob, int v0, in
   }
 }
 
+// Shared memory of one problem's PCG.
 template <typename Acc>
-__global__ void __launch_bounds__(PCG_BS)
-    k_pcg(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff, const float *__restrict__ Minv,
-          const Acc *__restrict__ rhs, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
-          float *__restrict__ p, float *__restrict__ q, int n_pcg, int *__restrict__ pflags,
-          const Acc *__restrict__ pairen, PcgOut po, MatFree mf) {
-  __shared__ float wsum[PCG_BS / 32];
-  __shared__ PcgScal S;
-  __shared__ Acc esh[EN_BS / 32][PAIREN];
-  const int prob = blockIdx.x;
-  if (po.energy) problem_energy<Acc>(t, pairen, prob, po.energy, esh);
+struct PcgSmem {
+  float AT[PCG_SMALL_N * PCG_SMALL_N];
+  float sp[PCG_SMALL_N], sr[PCG_SMALL_N];
+  float wsum[PCG_BS / 32];
+  PcgScal S;
+  Acc esh[EN_BS / 32][PAIREN];
+};
+
+// The PCG of problem `prob` by a CTA of PCG_BS threads: energy record, exactly n_pcg iterations
+// (shared-memory dense path for small problems), pose update and pair transforms.  CG: the poses
+// are read through L2 (written by other CTAs of a persistent launch).
+template <typename Acc, bool CG = false>
+__device__ void pcg_problem(int prob, const Tables &t, const float *__restrict__ Df,
+                            const float *__restrict__ pairoff, const float *__restrict__ Minv,
+                            const Acc *__restrict__ rhs, float *__restrict__ x, float *__restrict__ r,
+                            float *__restrict__ z, float *__restrict__ p, float *__restrict__ q, int n_pcg,
+                            int *__restrict__ pflags, const Acc *__restrict__ pairen, const PcgOut &po,
+                            const MatFree &mf, PcgSmem<Acc> &sm) {
+  float *wsum = sm.wsum;
+  PcgScal &S = sm.S;
+  if (po.energy) problem_energy<Acc>(t, pairen, prob, po.energy, sm.esh);
   const int v0 = t.prob_var0[prob], v1 = t.prob_var1[prob];
   const int u0 = 6 * v0, u1 = 6 * v1;
   if (u1 - u0 <= PCG_SMALL_N && !mf.P) {
-    const int flag = pcg_small<Acc>(t, Df, pairoff, Minv, rhs, x, n_pcg, v0, v1, wsum, S);
+    const int flag = pcg_small<Acc>(t, Df, pairoff, Minv, rhs, x, n_pcg, v0, v1, wsum, S, sm.AT, sm.sp, sm.sr);
     if (threadIdx.x == 0 && pflags) pflags[prob] |= flag;
-    pcg_finish(t, x, prob, v0, v1, po);
+    pcg_finish<CG>(t, x, prob, v0, v1, po);
     return;
   }
   for (int u = u0 + threadIdx.x; u < u1; u += PCG_BS) {
@@ -830,7 +877,17 @@ __global__ void __launch_bounds__(PCG_BS)
     __syncthreads();
   }
   if (threadIdx.x == 0 && pflags) pflags[prob] |= flag;
-  pcg_finish(t, x, prob, v0, v1, po);
+  pcg_finish<CG>(t, x, prob, v0, v1, po);
+}
+
+template <typename Acc>
+__global__ void __launch_bounds__(PCG_BS)
+    k_pcg(Tables t, const float *__restrict__ Df, const float *__restrict__ pairoff, const float *__restrict__ Minv,
+          const Acc *__restrict__ rhs, float *__restrict__ x, float *__restrict__ r, float *__restrict__ z,
+          float *__restrict__ p, float *__restrict__ q, int n_pcg, int *__restrict__ pflags,
+          const Acc *__restrict__ pairen, PcgOut po, MatFree mf) {
+  __shared__ PcgSmem<Acc> sm;
+  pcg_problem<Acc>(blockIdx.x, t, Df, pairoff, Minv, rhs, x, r, z, p, q, n_pcg, pflags, pairen, po, mf, sm);
 }
 
 template <typename Acc>
