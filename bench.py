@@ -74,6 +74,7 @@ def parse():
                     help="dense work item size in source pixels; 0 = automatic (target frame staged in shared memory)")
     ap.add_argument("--large-only", action="store_true",
                     help="run only the 2000-keyframe 160x120 BF16 global solve leg (one JSON line)")
+    ap.add_argument("--batch-only", action="store_true", help="only the 256-chunk batch legs (FP32 and BF16 storage)")
     ap.add_argument("--next-rows-only", action="store_true",
                     help="run only the pruning / verification / key-point / TSDF legs (one JSON line)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
@@ -230,6 +231,16 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.set_stream(stream)
         if rank == 0:
             print(json.dumps({"large_global": large_global_leg(bf, torch, dev, stream)}), flush=True)
+        return
+    if args.batch_only:
+        stream = torch.cuda.Stream(dev)
+        torch.cuda.set_stream(stream)
+        if rank == 0:
+            import synth
+            cprob = synth.cfg3()
+            print(json.dumps({"chunk_batch": chunk_batch_leg(bf, torch, dev, stream, prob=cprob),
+                              "chunk_batch_bf16": chunk_batch_leg(bf, torch, dev, stream, prob=cprob,
+                                                                  storage="bf16")}), flush=True)
         return
     if args.next_rows_only:
         stream = torch.cuda.Stream(dev)
@@ -625,6 +636,10 @@ def large_global_leg(bf, torch, dev, stream, steps=3, warmup=1):
             "kernel_time_share": {k: round(v["ms"] / max(tot, 1e-9), 4) for k, v in prof["kernels"].items()
                                   if v["count"]}}
 
+# tiles of half a 320x240 frame for the persistent launch (the fastest of 19200 / 38400 / 76800 there)
+PERSISTENT_TILE_PX = 38400
+
+
 def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None, storage="fp32"):
     """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.
 
@@ -683,6 +698,26 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
 
     run(batched, warmup)
     tb, sb = run(batched, steps)
+
+    # the same batch as ONE persistent launch (device work queue over tiles, segments and solves)
+    pk = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, tile_px=PERSISTENT_TILE_PX, persistent=1, **common)
+
+    def persistent():
+        ctx.add_frames(0, depth_d, lum_d)
+        return ctx.solve_local_batch(ids, lists, pk)
+
+    run(persistent, warmup)
+    tk, sk = run(persistent, steps)
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    persistent_kernel = None
+    ctx.add_frames(0, depth_d, lum_d)
+    ctx.solve_local_batch(ids, lists, bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, persistent=1,
+                                                        tile_px=PERSISTENT_TILE_PX, **common))
+    kp = ctx.profile()["kernels"]
+    if kp["batch"]["count"]:
+        persistent_kernel = {"launches": kp["batch"]["count"], "ms": kp["batch"]["ms"] / kp["batch"]["count"]}
+    ctx.set_profiling(False)
     # dense kernel time in this workload (kernel by kernel, CUDA events around each launch)
     ctx.reset_profile()
     ctx.set_profiling(True)
@@ -712,6 +747,14 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
                        "chunk_latency_p50_ms": statistics.mean(tb), "chunk_latency_p99_ms": max(tb),
                        "precision": "fp32", "cuda_graph": True,
                        "tile_px": {"autotuned": tuned, "meaning": "0 = target frame staged in shared memory"}},
+           "persistent": {"value": gn_per_step / (statistics.mean(tk) / 1000.0), "unit": UNIT,
+                          "ms_per_step": statistics.mean(tk), "solves_per_s": len(lists) / (statistics.mean(tk) / 1000.0),
+                          "launches_per_solve": 1, "kernel": persistent_kernel, "cuda_graph": True,
+                          "tile_px": PERSISTENT_TILE_PX,
+                          "final_energy_max_rel_diff_vs_launch_sequence": max(
+                              abs(a["energy"][-1] - b["energy"][-1]) / abs(b["energy"][-1]) for a, b in zip(sk, sb)),
+                          "note": "tiles of tile_px pixels here, the autotuned size in the launch sequence; at equal "
+                                  "tiles the two are bitwise equal (tests/test_gpu_persistent.py)"},
            "dense_kernel": {"avg_launch_ms": dense_ms, "launches": dense["count"],
                             "algorithmic_bytes_per_launch": alg_bytes,
                             "algorithmic_GBps": alg_bytes / (dense_ms / 1000.0) / 1e9,

@@ -128,6 +128,15 @@ typedef struct {
    * free frames (AUTO or GRID) and on the per-problem kernel otherwise; the cluster kernel does
    * not offer it.  Both give the same step up to FP32 rounding. */
   int sparse_mode;
+  /* 1: run the whole Gauss-Newton loop (all iterations, the final energy) as ONE persistent
+   * kernel launch whose CTAs take tiles, segments and per-problem solves from a device work
+   * queue, so independent problems (chunks, Sec. 4.2) advance at their own pace; results are
+   * bitwise those of the launch sequence.  Applies to the tiled dense decomposition (tile_px > 0
+   * or BF_TILE_AUTOTUNE choosing tiles, or frames too large to stage in shared memory), the
+   * per-problem PCG kernel (every problem of a batch, or pcg_variant BF_PCG_CTA) and assembled
+   * sparse blocks; otherwise the launch sequence runs.  A wait inside it that runs out ends
+   * the solve with BF_ERR_TIMEOUT. */
+  int persistent;
 } bf_solve_params;
 
 enum { BF_SPARSE_BLOCKS = 0, BF_SPARSE_MATFREE = 1 };
@@ -276,10 +285,11 @@ bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const doub
  * no launches and BF_K_ENERGY counts only a solve's final energy evaluation.  BF_K_XFORM counts
  * the pair-transform launches: one per solve when every problem is solved by the per-problem PCG
  * kernel (which refreshes its pairs' transforms itself), one more per GN iteration otherwise.
+ * BF_K_BATCH counts the persistent batched-solve launches (one per solve, see `persistent`).
  */
 enum {
   BF_K_PREPROCESS = 0, BF_K_XFORM, BF_K_DENSE, BF_K_SPARSE, BF_K_MERGE, BF_K_ASSEMBLE, BF_K_PCG, BF_K_UPDATE,
-  BF_K_ENERGY, BF_K_PACK, BF_K_VERIFY, BF_K_KEYPOINT, BF_K_TSDF, BF_NPROF
+  BF_K_ENERGY, BF_K_PACK, BF_K_VERIFY, BF_K_KEYPOINT, BF_K_TSDF, BF_K_BATCH, BF_NPROF
 };
 typedef struct {
   long long launches;          /* kernels launched since the last reset (always counted)  */

@@ -25,9 +25,9 @@ BF_SPARSE_BLOCKS, BF_SPARSE_MATFREE = 0, 1
 BF_MAX_GN = 64
 BF_MAX_PRUNE = 32
 BF_TILE_AUTOTUNE = -1
-BF_NPROF = 13
+BF_NPROF = 14
 KERNEL_CLASSES = ["preprocess", "xform", "dense", "sparse", "merge", "assemble", "pcg", "update", "energy", "pack",
-                  "verify", "keypoint", "tsdf"]
+                  "verify", "keypoint", "tsdf", "batch"]
 
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_OUT_OF_MEMORY", 3: "BF_ERR_CUDA",
           4: "BF_ERR_NOT_FOUND", 5: "BF_ERR_SINGULAR", 6: "BF_ERR_TIMEOUT", 7: "BF_ERR_BUSY"}
@@ -49,7 +49,7 @@ class SolveParams(ctypes.Structure):
                 ("dense_on", ctypes.c_int), ("warm_start", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int), ("pcg_variant", ctypes.c_int),
                 ("prune_rmax", ctypes.c_double), ("prune_rounds", ctypes.c_int),
-                ("sparse_mode", ctypes.c_int)]
+                ("sparse_mode", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):

@@ -965,6 +965,10 @@ struct DevSolve {
   float *Minv2, *mfy;
   int *vflags2;
   bool matfree;
+  // persistent batched solve: its work queue (batch_queue_bytes) and item count
+  void *bq;
+  long long bq_total;
+  bool persistent;
   void *coop;      // cooperative PCG state (barrier, error flag, partials)
   int *derr;       // set by the staged dense kernel if its bulk copies did not land
   int coop_grid;   // > 0: one large problem solved by the cooperative PCG
@@ -993,8 +997,21 @@ int coop_grid_for(const HostTables &T, int variant, bool matfree) {
   return cluster_for(T, variant, matfree) == 0 ? coop_grid_size(T.n_vars) : 0;
 }
 
+// The persistent batched solve serves tiled dense work, the per-problem PCG kernel and assembled
+// sparse blocks.
+bool persistent_for(const HostTables &T, int variant, bool matfree) {
+  return T.n_wi == 0 && !matfree && cluster_for(T, variant, matfree) == 0 && coop_grid_for(T, variant, matfree) == 0;
+}
+
+long long batch_items(const HostTables &T, int n_gn) {
+  std::vector<int> L(T.n_prob);
+  for (int p = 0; p < T.n_prob; ++p)
+    L[p] = (T.prob_tile1[p] - T.prob_tile0[p]) + (T.prob_seg1[p] - T.prob_seg0[p]);
+  return batch_total_items(L.data(), T.n_prob, n_gn);
+}
+
 size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D, size_t acc_size, int HW,
-              bool want_assoc, int variant, bool matfree) {
+              bool want_assoc, int variant, bool matfree, bool persistent) {
   Arena a{base};
   int *ib = a.take<int>(n_int);
   double *pose = a.take<double>(T.n_frames * 12);
@@ -1028,6 +1045,9 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
   int *vflags2 = a.take<int>(nm * T.n_vars);
   const int cg = coop_grid_for(T, variant, matfree);
   void *coop = a.take<char>(cg > 0 ? coop_mem_bytes(cg) : 256);
+  const bool pers = persistent && persistent_for(T, variant, matfree);
+  const long long bq_total = pers ? batch_items(T, n_gn) : 0;
+  void *bq = a.take<char>(pers ? batch_queue_bytes(T.n_prob, bq_total) : 0);
   double *energy = a.take<double>((size_t)(n_gn + 1) * T.n_prob * PAIREN);
   int *derr = a.take<int>(1);
   int *assoc = want_assoc ? a.take<int>(HW) : nullptr;
@@ -1061,6 +1081,9 @@ size_t layout(const HostTables &T, int n_gn, int n_int, char *base, DevSolve *D,
     D->mfy = mfy;
     D->vflags2 = vflags2;
     D->matfree = matfree;
+    D->bq = bq;
+    D->bq_total = bq_total;
+    D->persistent = pers;
     D->coop = coop;
     D->coop_grid = cg;
     D->cluster = cluster_for(T, variant, matfree);
@@ -1146,11 +1169,11 @@ bf_status ensure_pinned(bf_ctx *c, size_t n) {
 }
 
 bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, bool want_assoc, DevSolve &D,
-                  int variant = BF_PCG_AUTO, bool matfree = false) {
+                  int variant = BF_PCG_AUTO, bool matfree = false, bool persistent = false) {
   const std::vector<int> ints = pack_ints(T);
   const int HW = c->cfg.width * c->cfg.height;
   const size_t need =
-      layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc, variant, matfree) + 256;
+      layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc, variant, matfree, persistent) + 256;
   if (need > c->ex->ws_bytes) {
     const size_t nb = std::max(need, c->ex->ws_bytes * 3 / 2);
     CK(cudaStreamSynchronize(c->ex->st), "workspace");
@@ -1165,7 +1188,7 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
     if (s) return s;
     c->ex->ws_bytes = nb;
   }
-  layout(T, n_gn, ints.size(), c->ex->ws, &D, acc_size, HW, want_assoc, variant, matfree);
+  layout(T, n_gn, ints.size(), c->ex->ws, &D, acc_size, HW, want_assoc, variant, matfree, persistent);
   const bool same_tables = c->ex->last_ws == (const void *)c->ex->ws && c->ex->last_ints == ints;
   if (!ints.empty() && !same_tables) {
     CK(cudaMemcpyAsync((void *)D.t.frame_slot, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, c->ex->st),
@@ -1214,8 +1237,62 @@ double wdense_at(const bf_solve_params &prm, int k) {
   return prm.dense_ramp ? prm.w_dense * (k + 1) / prm.n_gn : prm.w_dense;
 }
 
+// The whole Gauss-Newton loop as one persistent launch (batch.cu): same weights, gates and
+// buffers as the launch sequence below.
+template <typename Acc>
+bf_status run_gn_batch(bf_ctx *c, const bf_solve_params &prm, DevSolve &D) {
+  BatchArgs a;
+  a.t = D.t;
+  a.fs = frame_store(c);
+  a.in = c->intr;
+  a.gates.tau_d2 = (float)(prm.tau_dist * prm.tau_dist);
+  a.gates.tau_n = (float)prm.tau_normal;
+  a.P = c->cP;
+  a.Q = c->cQ;
+  a.w_sparse = (float)prm.w_sparse;
+  for (int k = 0; k <= prm.n_gn; ++k) {
+    // iteration k's dense weight; the final energy uses the last iteration's
+    const double wd = k < prm.n_gn ? wdense_at(prm, k) : (prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense);
+    a.wg[k] = (float)(wd * prm.w_geo);
+    a.wp[k] = (float)(wd * prm.w_photo);
+  }
+  a.n_gn = prm.n_gn;
+  a.n_pcg = prm.n_pcg;
+  a.precond = prm.precond;
+  a.pose = D.pose;
+  a.pairM = D.pairM;
+  a.dpart = D.dpart;
+  a.spart = D.spart;
+  a.srmax = D.srmax;
+  a.srarg = D.srarg;
+  a.pairblk = D.pairblk;
+  a.pairen = D.pairen;
+  a.pairoff = D.pairoff;
+  a.Dd = D.Dd;
+  a.rhs = D.rhs;
+  a.Df = D.Df;
+  a.Minv = D.Minv;
+  a.vflags = D.vflags;
+  a.pflags = D.pflags;
+  a.x = D.x;
+  a.r = D.r;
+  a.z = D.z;
+  a.p = D.p;
+  a.q = D.q;
+  a.energy = D.energy;
+  int rc = 0;
+  run_k(c, BF_K_BATCH, [&] {
+    rc = launch_batch<Acc>(a, D.bq, D.bq_total, c->ex->st);
+    return rc < 0 ? 0 : rc;
+  });
+  if (rc < 0) return cuda_fail(c, cudaGetLastError(), "persistent batch launch");
+  CK(cudaGetLastError(), "persistent batch");
+  return BF_OK;
+}
+
 template <typename Acc>
 bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, DevSolve &D) {
+  if (D.persistent) return run_gn_batch<Acc>(c, prm, D);
   const Tables &t = D.t;
   run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
   for (int k = 0; k < prm.n_gn; ++k) {
@@ -1341,6 +1418,7 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
     return fail(c, BF_ERR_INVALID_ARG, "unknown pcg_variant");
   if (!(p->prune_rmax >= 0) || !std::isfinite(p->prune_rmax) || p->prune_rounds < 0 || p->prune_rounds > 100000)
     return fail(c, BF_ERR_INVALID_ARG, "prune_rmax must be finite and >= 0, prune_rounds >= 0");
+  if (p->persistent != 0 && p->persistent != 1) return fail(c, BF_ERR_INVALID_ARG, "persistent must be 0 or 1");
   if (p->sparse_mode != BF_SPARSE_BLOCKS && p->sparse_mode != BF_SPARSE_MATFREE)
     return fail(c, BF_ERR_INVALID_ARG, "unknown sparse_mode");
   if (p->sparse_mode == BF_SPARSE_MATFREE && p->pcg_variant == BF_PCG_CLUSTER)
@@ -1444,7 +1522,8 @@ bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_s
   if (s) return s;
   const bool mixed = prm.precision == BF_PREC_MIXED;
   const size_t acc_size = mixed ? sizeof(double) : sizeof(float);
-  s = prepare(c, T, prm.n_gn, acc_size, false, D, prm.pcg_variant, prm.sparse_mode == BF_SPARSE_MATFREE);
+  s = prepare(c, T, prm.n_gn, acc_size, false, D, prm.pcg_variant, prm.sparse_mode == BF_SPARSE_MATFREE,
+              prm.persistent != 0);
   if (s) return s;
   if (prm.use_graph && !c->prof) {
     s = run_gn_graph(c, T, prm, D, mixed);
@@ -1472,10 +1551,12 @@ bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_s
     CK(cudaMemcpyAsync(pb + J.o_sm, D.srmax, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, st), "rmax");
     CK(cudaMemcpyAsync(pb + J.o_sa, D.srarg, 4 * (size_t)T.n_segs, cudaMemcpyDeviceToHost, st), "rmax");
   }
-  std::memset(pb + J.o_ce, 0, 8);
+  std::memset(pb + J.o_ce, 0, 12);
   if (D.coop_grid > 0)
     CK(cudaMemcpyAsync(pb + J.o_ce, (char *)D.coop + 8, sizeof(int), cudaMemcpyDeviceToHost, st), "pcg status");
   CK(cudaMemcpyAsync(pb + J.o_ce + 4, D.derr, sizeof(int), cudaMemcpyDeviceToHost, st), "dense status");
+  if (D.persistent)
+    CK(cudaMemcpyAsync(pb + J.o_ce + 8, (char *)D.bq + 8, sizeof(int), cudaMemcpyDeviceToHost, st), "batch status");
   return BF_OK;
 }
 
@@ -1495,10 +1576,12 @@ bf_status finish_solve(bf_ctx *c, SolveJob &J, std::vector<std::vector<Pose12>> 
     std::memcpy(srmax.data(), pb + J.o_sm, 4 * (size_t)T.n_segs);
     std::memcpy(srarg.data(), pb + J.o_sa, 4 * (size_t)T.n_segs);
   }
-  int coop_err = 0, dense_err = 0;
+  int coop_err = 0, dense_err = 0, batch_err = 0;
   std::memcpy(&coop_err, pb + J.o_ce, 4);
   std::memcpy(&dense_err, pb + J.o_ce + 4, 4);
+  std::memcpy(&batch_err, pb + J.o_ce + 8, 4);
   if (coop_err) return fail(c, BF_ERR_TIMEOUT, "PCG grid barrier timed out");
+  if (batch_err) return fail(c, BF_ERR_TIMEOUT, "persistent batch: a work-queue wait gave up");
   if (dense_err) return fail(c, BF_ERR_TIMEOUT, "dense kernel: frame copy into shared memory timed out");
   const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - J.t0).count();
   out.assign(T.n_prob, {});

@@ -288,6 +288,56 @@ struct MatFree {
   float *mfy;           // [n_pairs][12] scratch: the pair's J^T W J d, frame a then frame b
 };
 
+// Arguments of the persistent batched solve (batch.cu): the solve's tables and workspace.
+struct BatchArgs {
+  Tables t;
+  FrameStore fs;
+  Intr in;
+  Gates gates;
+  const float4 *P, *Q;
+  float w_sparse;
+  float wg[BF_MAX_GN + 1], wp[BF_MAX_GN + 1];  // dense weights of each GN iteration; [n_gn]: final energy
+  int n_gn, n_pcg, precond;
+  double *pose;
+  float *pairM;
+  void *dpart, *spart;
+  float *srmax;
+  int *srarg;
+  void *pairblk, *pairen;
+  float *pairoff;
+  void *Dd, *rhs;
+  float *Df, *Minv;
+  int *vflags, *pflags;
+  float *x, *r, *z, *p, *q;
+  double *energy;
+};
+// Work queue of the persistent batched solve (device memory of batch_queue_bytes()).
+struct BatchQueue {
+  int *head, *tail, *err;  // claim and publication counters; err: 1 a wait ran out, 2 queue overflow
+  int *done;               // [n_prob] completed tiles / segments of each problem's current stage
+  int *flags;              // [total] 1 once the slot's item is published
+  int4 *items;             // [total] {type, problem, GN iteration, tile / segment}
+  int n_prob, total;
+  long long wait_limit;
+};
+// Items a persistent solve of problems with L_p tiles + segments publishes: per problem one
+// transform item, n_gn x (L_p + 1) for the iterations, L_p + 1 for the final energy.
+inline long long batch_total_items(const int *L, int n_prob, int n_gn) {
+  long long total = 0;
+  for (int p = 0; p < n_prob; ++p) total += 1 + (long long)n_gn * (L[p] + 1) + L[p] + 1;
+  return total;
+}
+inline size_t batch_zero_bytes(int n_prob, long long total) {
+  return ((256 + 4 * (size_t)n_prob + 4 * (size_t)total) + 255) & ~(size_t)255;
+}
+inline size_t batch_queue_bytes(int n_prob, long long total) {
+  return batch_zero_bytes(n_prob, total) + 16 * (size_t)total;
+}
+// One cooperative launch (after resetting the queue's counters and flags); -1 if refused.  The
+// error word (offset 8 of qmem) is nonzero after the launch if a wait gave up.
+template <typename Acc>
+int launch_batch(const BatchArgs &a, void *qmem, long long total, cudaStream_t st);
+
 // ------------------------------------------------------------------ launch wrappers (host side)
 // Dense verification (Sec. 4.1.1): one CTA per frame pair, both directions.  rec[p]: slots of
 // the two frames, then fl32(T_ij) and fl32(T_ji) (R row-major, t); out[p] = {n_ij, n_ji, e_ij, e_ji}.

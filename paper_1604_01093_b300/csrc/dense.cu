@@ -27,8 +27,6 @@ __global__ void __launch_bounds__(DENSE_BS, 4)
             Part *__restrict__ part, int *__restrict__ assoc) {
   extern __shared__ float ktab[];  // kx[W], ky[H]
   __shared__ float red[DENSE_BS / 32][NPD];
-  for (int k = threadIdx.x; k < in.W + in.H; k += DENSE_BS) ktab[k] = k < in.W ? fs.kx[k] : fs.ky[k - in.W];
-  __syncthreads();
   dense_tile<MODE, KIND, Part>(blockIdx.x, t, fs, in, pairM, g, w_geo, w_photo, part, assoc, ktab, red);
 }
 

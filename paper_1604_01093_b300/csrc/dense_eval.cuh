@@ -168,20 +168,23 @@ struct PixWalk {
 constexpr int DENSE_BS = 256;
 
 // One dense tile (work item = consecutive source pixels of one directed pair), evaluated by a
-// CTA of DENSE_BS threads.  ktab holds kx[W] then ky[H] (loaded by the caller); red is the
-// reduction's shared memory.  Ends with the CTA's partial record written by threads < NPD.
+// CTA of DENSE_BS threads.  ktab: shared memory for kx[W] then ky[H]; red: the reduction's shared
+// memory.  Ends with the CTA's partial record written by threads < NPD.
 template <int MODE, int KIND, typename Part, bool CG = false>
 __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const FrameStore &fs, const Intr &in,
                                            const float *__restrict__ pairM, const Gates &g, float w_geo,
                                            float w_photo, Part *__restrict__ part, int *__restrict__ assoc,
-                                           const float *ktab, float (*red)[NPD]) {
+                                           float *ktab, float (*red)[NPD]) {
   const int d = t.tile_dp[tile];
   const int px0 = t.tile_px0[tile], px1 = t.tile_px1[tile];
   const int W = in.W, H = in.H;
   const long long HW = (long long)W * H;
   const int ss = t.frame_slot[t.dp_src[d]], ts = t.frame_slot[t.dp_dst[d]];
   const PairXf X = load_xf<CG>(pairM + (t.dp_pair[d] * 2 + t.dp_dir[d]) * 12);
-  const float *kx = ktab, *ky = ktab + W;
+  // the ray tables, loaded here (after X: that order keeps the register allocation of the pixel loop)
+  float *kx = ktab, *ky = ktab + W;
+  for (int k = threadIdx.x; k < W + H; k += DENSE_BS) ktab[k] = k < W ? fs.kx[k] : fs.ky[k - W];
+  __syncthreads();
   float acc[NPD];
 #pragma unroll
   for (int k = 0; k < NPD; ++k) acc[k] = 0.f;
