@@ -17,11 +17,11 @@ Readings used (the paper gives no numbers for this pruning):
 * the source pixel needs valid depth and a valid normal.
 
 Every one of these decisions turns a floating-point value into an integer or a
-boolean.  They are taken in IEEE FP32 with one rounding per operation, in the fixed
-order written below (the projection uses one correctly rounded reciprocal 1/y_z), the same
-precision and order as the GPU kernel, so that both sides take identical decisions on
-identical inputs.  The residual values
-themselves (residuals.py) are FP64.
+boolean.  They are taken in IEEE FP32 in the fixed order written below: products, sums and
+fused multiply-adds (one rounding of a*b + c, see fma32), and one correctly rounded
+reciprocal 1/y_z for the projection; the same precision and order as the GPU kernel, so that
+both sides take identical decisions on identical inputs.  The residual values themselves
+(residuals.py) are FP64.
 
 Per directed pair the relative transform M = T_j^-1 T_i is formed in FP64 with
 explicit sums (R = R_j^T R_i, t = R_j^T (t_i - t_j)) and rounded once to FP32.
@@ -29,6 +29,30 @@ explicit sums (R = R_j^T R_i, t = R_j^T (t_i - t_j)) and rounded once to FP32.
 import numpy as np
 
 f32 = np.float32
+
+
+def fma32(a, b, c):
+    """IEEE FP32 fused multiply-add: a*b + c rounded once to nearest (ties to even).
+
+    a, b, c are FP32.  In FP64 the product p = a*b is exact (24 + 24 significant bits);
+    TwoSum gives p + c = s + e exactly with s = fl64(p + c).  Rounding s + e to FP64 "to odd"
+    (s itself if e == 0 or s's last significand bit is odd, else the FP64 neighbour of s in
+    the direction of e) and then to FP32 to nearest is the correctly rounded FP32 result,
+    because FP64 carries at least two bits more than FP32 (Boldo and Melquiond, "Emulation of
+    FMA and correctly rounded sums: proved algorithms using rounding to odd", IEEE TC 2008).
+    """
+    a64 = np.asarray(a, dtype=f32).astype(np.float64)
+    b64 = np.asarray(b, dtype=f32).astype(np.float64)
+    c64 = np.asarray(c, dtype=f32).astype(np.float64)
+    p = a64 * b64
+    s = p + c64
+    bb = s - p
+    e = (p - (s - bb)) + (c64 - bb)
+    even = (np.asarray(s).view(np.int64) & 1) == 0
+    with np.errstate(invalid="ignore"):
+        toward = np.where(e > 0, np.inf, -np.inf)
+        s_odd = np.where((e != 0) & even & np.isfinite(s), np.nextafter(s, toward), s)
+    return s_odd.astype(f32)
 
 
 def pair_transform32(Ri, ti, Rj, tj):
@@ -65,16 +89,17 @@ def associate(fi, fj, M32, intr, tau_d=0.15, tau_n=0.9):
     z = fi.D32.ravel()
     n_i = fi.N32.reshape(-1, 3)
     ok = fi.valid.ravel() & fi.nvalid.ravel()
-    # camera-space source point, one rounding per product
+    # camera-space source point (rounded products), then y = R d + t as fused multiply-adds
+    # accumulated from t: y_a = fma(R_a2, d_z, fma(R_a1, d_y, fma(R_a0, d_x, t_a)))
     dx = kx[xs] * z
     dy = ky[ys] * z
     dz = z
-    Y = [((R[a, 0] * dx + R[a, 1] * dy) + R[a, 2] * dz) + t[a] for a in range(3)]
+    Y = [fma32(R[a, 2], dz, fma32(R[a, 1], dy, fma32(R[a, 0], dx, t[a]))) for a in range(3)]
     ok &= Y[2] > f32(0)
     with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         iz = f32(1) / np.where(ok, Y[2], f32(1))
-        ux = fx * (Y[0] * iz) + cx
-        uy = fy * (Y[1] * iz) + cy
+        ux = fma32(fx, Y[0] * iz, cx)
+        uy = fma32(fy, Y[1] * iz, cy)
     ux = np.where(ok, ux, f32(-100))
     uy = np.where(ok, uy, f32(-100))
     nxf = np.floor(ux + f32(0.5))
@@ -94,10 +119,10 @@ def associate(fi, fj, M32, intr, tau_d=0.15, tau_n=0.9):
     qy = ky[ny] * Dj
     qz = Dj
     ex, ey, ez = Y[0] - qx, Y[1] - qy, Y[2] - qz
-    dist2 = (ex * ex + ey * ey) + ez * ez
+    dist2 = fma32(ez, ez, fma32(ey, ey, ex * ex))
     ok &= dist2 < f32(tau_d * tau_d)
-    m = [(R[a, 0] * n_i[:, 0] + R[a, 1] * n_i[:, 1]) + R[a, 2] * n_i[:, 2] for a in range(3)]
+    m = [fma32(R[a, 2], n_i[:, 2], fma32(R[a, 1], n_i[:, 1], R[a, 0] * n_i[:, 0])) for a in range(3)]
     n_j = fj.N32.reshape(-1, 3)[tgt]
-    dot = (m[0] * n_j[:, 0] + m[1] * n_j[:, 1]) + m[2] * n_j[:, 2]
+    dot = fma32(m[2], n_j[:, 2], fma32(m[1], n_j[:, 1], m[0] * n_j[:, 0]))
     ok &= dot > f32(tau_n)
     return dict(valid=ok, nx=nx, ny=ny, bx=bx, by=by)

@@ -12,8 +12,9 @@
 // long; everything above a tile is summed in FP64 (mixed precision) by the pair merge.
 //
 // The association decisions (target pixel, bilinear taps, validity, gates) are computed with
-// explicitly rounded FP32 operations in a fixed order (no contraction), so a CPU restatement in
-// IEEE FP32 takes the same decisions.  Residuals and Jacobians are free FP32 arithmetic.
+// explicitly rounded FP32 operations in a fixed order (products, sums and fused multiply-adds,
+// no other contraction), so a CPU restatement in IEEE FP32 (with an exact FP32 fused
+// multiply-add) takes the same decisions.  Residuals and Jacobians are free FP32 arithmetic.
 //
 // Everything is evaluated in the coordinates of the target camera j with the pair transform
 // M = T_j^-1 T_i (y = R d + t); the merge rotates the sums to world coordinates with R_j.

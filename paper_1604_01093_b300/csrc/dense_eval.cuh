@@ -10,6 +10,7 @@ namespace bf {
 #define FM __fmul_rn
 #define FA __fadd_rn
 #define FS __fsub_rn
+#define FMA __fmaf_rn
 
 struct V3 {
   float x, y, z;
@@ -84,15 +85,16 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
   if (!(a.x > 0.f && nvalid)) return -1;
   const int W = in.W, H = in.H;
   const float z = a.x;
-  // ---- association decisions, explicitly rounded FP32 in a fixed order ----
+  // ---- association decisions, explicitly rounded FP32 in a fixed order: products, sums and
+  // fused multiply-adds (one rounding of a*b + c), y = R d + t accumulated from t ----
   const float dx = FM(kx[x], z), dy = FM(ky[y], z), dz = z;
-  const float Y0 = FA(FA(FA(FM(X.R00, dx), FM(X.R01, dy)), FM(X.R02, dz)), X.t0);
-  const float Y1 = FA(FA(FA(FM(X.R10, dx), FM(X.R11, dy)), FM(X.R12, dz)), X.t1);
-  const float Y2 = FA(FA(FA(FM(X.R20, dx), FM(X.R21, dy)), FM(X.R22, dz)), X.t2);
+  const float Y0 = FMA(X.R02, dz, FMA(X.R01, dy, FMA(X.R00, dx, X.t0)));
+  const float Y1 = FMA(X.R12, dz, FMA(X.R11, dy, FMA(X.R10, dx, X.t1)));
+  const float Y2 = FMA(X.R22, dz, FMA(X.R21, dy, FMA(X.R20, dx, X.t2)));
   if (!(Y2 > 0.f)) return -1;
   const float iz = __frcp_rn(Y2);
-  const float ux = FA(FM(in.fx, FM(Y0, iz)), in.cx);
-  const float uy = FA(FM(in.fy, FM(Y1, iz)), in.cy);
+  const float ux = FMA(in.fx, FM(Y0, iz), in.cx);
+  const float uy = FMA(in.fy, FM(Y1, iz), in.cy);
   const float nxf = floorf(FA(ux, 0.5f)), nyf = floorf(FA(uy, 0.5f));
   const float bxf = floorf(ux), byf = floorf(uy);
   if (!(nxf >= 0.f && nxf <= (float)(W - 1) && nyf >= 0.f && nyf <= (float)(H - 1) && bxf >= 2.f &&
@@ -114,11 +116,11 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
   if (!(b.x > 0.f && tnvalid)) return -1;
   const float qx = FM(kx[tx], b.x), qy = FM(ky[ty], b.x), qz = b.x;
   const float ex = FS(Y0, qx), ey = FS(Y1, qy), ez = FS(Y2, qz);
-  const float dist2 = FA(FA(FM(ex, ex), FM(ey, ey)), FM(ez, ez));
-  const float m0 = FA(FA(FM(X.R00, a.y), FM(X.R01, a.z)), FM(X.R02, a.w));
-  const float m1 = FA(FA(FM(X.R10, a.y), FM(X.R11, a.z)), FM(X.R12, a.w));
-  const float m2 = FA(FA(FM(X.R20, a.y), FM(X.R21, a.z)), FM(X.R22, a.w));
-  const float ndot = FA(FA(FM(m0, b.y), FM(m1, b.z)), FM(m2, b.w));
+  const float dist2 = FMA(ez, ez, FMA(ey, ey, FM(ex, ex)));
+  const float m0 = FMA(X.R02, a.w, FMA(X.R01, a.z, FM(X.R00, a.y)));
+  const float m1 = FMA(X.R12, a.w, FMA(X.R11, a.z, FM(X.R10, a.y)));
+  const float m2 = FMA(X.R22, a.w, FMA(X.R21, a.z, FM(X.R20, a.y)));
+  const float ndot = FMA(m2, b.w, FMA(m1, b.z, FM(m0, b.y)));
   if (!(dist2 < g.tau_d2 && ndot > g.tau_n)) return -1;
   if (MODE == MODE_ASSOC) return tpx;
   // ---- residuals and Jacobians (free FP32) in camera-j coordinates ----
@@ -228,5 +230,6 @@ __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const Fram
 #undef FM
 #undef FA
 #undef FS
+#undef FMA
 
 }  // namespace bf

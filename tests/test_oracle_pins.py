@@ -146,6 +146,38 @@ def test_depth_validity_range():
 
 # ----------------------------------------------------------- sparse residuals
 
+def _round_f32_exact(q):
+    """Correctly rounded FP32 (to nearest, ties to even) of an exact rational, by brute force
+    over the FP32 neighbours of its FP64 approximation."""
+    from fractions import Fraction
+    x = np.float32(float(q))
+    cands = [np.nextafter(x, np.float32(-np.inf)), x, np.nextafter(x, np.float32(np.inf))]
+    return min(cands, key=lambda c: (abs(Fraction(float(c)) - q), int(np.array(c).view(np.int32)) & 1))
+
+
+def test_fma32_is_the_correctly_rounded_fused_multiply_add():
+    """The association's FP32 fused multiply-add equals exact rational arithmetic rounded once:
+    random operands over many scales, near-cancelling sums, and a constructed case where the
+    naive route (FP64 sum, then FP32) double-rounds to the wrong neighbour."""
+    from fractions import Fraction
+    rng = np.random.default_rng(7)
+    a = (rng.normal(size=3000) * np.exp(rng.normal(size=3000) * 4)).astype(np.float32)
+    b = (rng.normal(size=3000) * np.exp(rng.normal(size=3000) * 4)).astype(np.float32)
+    c = (rng.normal(size=3000) * np.exp(rng.normal(size=3000) * 4)).astype(np.float32)
+    c[::3] = (-(a[::3].astype(np.float64) * b[::3])).astype(np.float32)  # near-cancellation
+    got = association.fma32(a, b, c)
+    for k in range(len(a)):
+        exact = Fraction(float(a[k])) * Fraction(float(b[k])) + Fraction(float(c[k]))
+        assert got[k] == (_round_f32_exact(exact) if exact != 0 else np.float32(0)), k
+    # (1 + 2^-12)^2 = 1 + 2^-11 + 2^-24 is an FP32 midpoint; + 2^-60 lies above it, which FP64
+    # cannot hold next to 1: naive rounding goes down (ties to even), the correct result is up
+    x = np.float32(1 + 2.0 ** -12)
+    tiny = np.float32(2.0 ** -60)
+    assert np.float32(np.float64(x) * np.float64(x) + np.float64(tiny)) == np.float32(1 + 2.0 ** -11)
+    assert association.fma32(x, x, tiny) == np.float32(1 + 2.0 ** -11 + 2.0 ** -23)
+    assert association.fma32(x, x, -tiny) == np.float32(1 + 2.0 ** -11)
+
+
 def test_sparse_zero_at_ground_truth():
     rng = np.random.default_rng(3)
     Ti, Tj = rand_pose(rng), rand_pose(rng)
