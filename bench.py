@@ -51,11 +51,12 @@ def dense_bytes_per_px(storage):
     return DENSE_BYTES_PER_PX if storage == "fp32" else DENSE_BYTES_PER_PX_16
 
 # FP32 flops of the dense kernel per directed source pixel on this workload: ncu FFMA x 2 + FADD + FMUL
-# of one ACCUM launch divided by its 21.84 M directed source pixels (profiles/k_dense_staged_global300_80x60.md)
-DENSE_FLOPS_PER_PX = 139.0
+# thread counts of one ACCUM launch divided by its 21.84 M directed source pixels
+# (profiles/k_dense_staged_global300_80x60.md)
+DENSE_FLOPS_PER_PX = 122.8
 # DRAM bytes (read + write) of one dense ACCUM launch from the same ncu capture (cold cache); set to
-# None whenever k_dense changes until it is captured again
-DENSE_TRAFFIC_BYTES = 46.44e6 + 0.09e6
+# None whenever the dense kernel changes until it is captured again
+DENSE_TRAFFIC_BYTES = 46.44e6 + 0.354e6
 # B300 FP32 peak: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
