@@ -61,6 +61,24 @@ DENSE_TRAFFIC_BYTES = 46.44e6 + 0.354e6
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
 
+def max_over_ranks(x, dist=None):
+    """The largest x over all ranks of the process group (x itself without one): the job's time is
+    its slowest rank's.  NCCL reduces on the rank's GPU, gloo on the host."""
+    if dist is None or not dist.is_initialized():
+        return float(x)
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" else torch.device("cpu")
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_step, steps, world, total_ms):
+    """Whole-job throughput: the units every rank processed in `steps` steps over the (max-over-ranks)
+    time; each rank runs its own replica (weak scaling)."""
+    return units_per_step * steps * world / (total_ms / 1000.0)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,13 +331,9 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop() if clocks else None
-    total_ms = sum(times)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(times), dist)
     n_gn = prm["n_gn"]
-    value = n_gn * args.steps * world / (total_ms / 1000.0)
+    value = job_rate(n_gn, args.steps, world, total_ms)
     if args.profile_run:
         if rank == 0:
             print(json.dumps({"profile_run": True, "value": value, "ms_per_step": total_ms / args.steps}))
