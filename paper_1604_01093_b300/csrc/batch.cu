@@ -47,7 +47,6 @@ template <typename Acc>
 struct BatchSmem {
   union {
     float dred[DENSE_BS / 32][NPD];
-    SparseSmem sp;
     struct {
       MergeSmem<Acc> m[BATCH_BS / 32];
       AsmSmem a[BATCH_BS / 32];
@@ -154,12 +153,12 @@ __device__ __forceinline__ void item_dense(const BatchArgs &a, const BatchQueue 
 template <typename Acc>
 __device__ __noinline__ void item_sparse(const BatchArgs &a, const BatchQueue &q, int4 it, BatchSmem<Acc> &sm) {
   const bool fin = it.x == IT_ESPARSE;
-  if (fin)
-    sparse_seg<MODE_ENERGY, Acc, true>(it.w, a.t, a.P, a.Q, a.pairM, a.w_sparse, (Acc *)a.spart, a.srmax, a.srarg,
-                                       sm.u.sp);
-  else
-    sparse_seg<MODE_ACCUM, Acc, true>(it.w, a.t, a.P, a.Q, a.pairM, a.w_sparse, (Acc *)a.spart, a.srmax, a.srarg,
-                                      sm.u.sp);
+  if (threadIdx.x < 32) {  // one warp per segment, as k_sparse
+    if (fin)
+      sparse_seg<MODE_ENERGY, Acc, true>(it.w, a.t, a.P, a.Q, a.pairM, a.w_sparse, (Acc *)a.spart, a.srmax, a.srarg);
+    else
+      sparse_seg<MODE_ACCUM, Acc, true>(it.w, a.t, a.P, a.Q, a.pairM, a.w_sparse, (Acc *)a.spart, a.srmax, a.srarg);
+  }
   finish_part<Acc>(a, q, it.y, it.z, fin, sm);
 }
 

@@ -162,6 +162,27 @@ __device__ __forceinline__ void pair_xform32(const double *Ti, const double *Tj,
   for (int e = 0; e < 12; ++e) M[e] = pair_xform_entry(Ti, Tj, e);
 }
 
+// Warp reduce-scatter of M per-lane values (M a power of two, 32 <= M <= 64): five exchange steps
+// (lane offsets 16, 8, 4, 2, 1), each sending one half of the values still held to the partner
+// lane and adding the half received, so a step costs one shuffle per value kept instead of a full
+// butterfly per value.  Afterwards lane l holds the warp totals of indices (M / 32) l + j in
+// acc[j], j < M / 32.  The order of the additions is fixed, so the result is deterministic.
+template <int M>
+__device__ __forceinline__ void warp_reduce_scatter(float (&acc)[M]) {
+  static_assert(M == 32 || M == 64, "32 or 64 values");
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16, h = M / 2; o >= 1; o >>= 1, h >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const float send = upper ? acc[k] : acc[k + h];
+      const float keep = upper ? acc[k + h] : acc[k];
+      acc[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+}
+
 // Load through L2 when CG (data written by another CTA of the same persistent launch, which the
 // SM's L1 may hold an older copy of), a plain load otherwise.
 template <bool CG, typename X>

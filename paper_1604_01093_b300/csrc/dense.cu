@@ -78,21 +78,18 @@ int dense_staged_smem(int W, int H, int storage) {
 }
 bool dense_staged_fits(int W, int H, int storage) { return dense_staged_smem(W, H, storage) + 4096 <= STG_MAX_SMEM; }
 
-// Sum of N per-thread values over a quad (4 warps, 128 threads): warp trees, then the 4 warp
-// results in order by thread k < N, which writes out[k].
+// Sum of N <= 32 per-thread values over a quad (4 warps, 128 threads): a reduce-scatter per warp
+// (lane l ends with value l), then the 4 warp results in order by thread k < N, which writes
+// out[k].
 template <int N, typename Part>
 __device__ __forceinline__ void quad_reduce_store(float (&acc)[N], float (*red)[N], int quad, Part *__restrict__ out) {
+  static_assert(N <= 32, "at most 32 values");
   const int lane = threadIdx.x & 31, wq = (threadIdx.x >> 5) & 3;
+  float v[32];
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    float v = acc[k];
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (lane == 0) red[wq][k] = v;
-  }
+  for (int k = 0; k < 32; ++k) v[k] = k < N ? acc[k] : 0.f;
+  warp_reduce_scatter<32>(v);
+  if (lane < N) red[wq][lane] = v[0];
   asm volatile("bar.sync %0, 128;" ::"r"(1 + quad) : "memory");
   const int tq = threadIdx.x & 127;
   if (tq < N) {

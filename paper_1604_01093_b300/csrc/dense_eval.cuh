@@ -35,21 +35,19 @@ __device__ __forceinline__ void accum_vc(float (&acc)[NPD], float w, float r, V3
 }
 
 // Fixed-order CTA reduction of N values; thread k < N writes out[k].
-// red: shared memory of BS / 32 rows of N floats.
+// Fixed-order CTA reduction of N <= 32 values; thread k < N writes out[k].  red: shared memory
+// of BS / 32 rows of N floats.  Per warp a reduce-scatter (lane l ends with value l), then the
+// warps' totals in warp order.
 template <int BS, int N, typename Part>
 __device__ __forceinline__ void cta_reduce_store(float (&acc)[N], Part *__restrict__ out, float (*red)[N]) {
+  static_assert(N <= 32, "at most 32 values");
   constexpr int NW = BS / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float v[32];
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    float v = acc[k];
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (lane == 0) red[warp][k] = v;
-  }
+  for (int k = 0; k < 32; ++k) v[k] = k < N ? acc[k] : 0.f;
+  warp_reduce_scatter<32>(v);
+  if (lane < N) red[warp][lane] = v[0];
   __syncthreads();
   if (threadIdx.x < N) {
     Part s = (Part)red[0][threadIdx.x];

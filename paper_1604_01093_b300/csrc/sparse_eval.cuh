@@ -7,50 +7,21 @@
 namespace bf {
 
 
-constexpr int SPARSE_BS = 128;
+constexpr int SPARSE_BS = 128;  // threads of k_sparse: 4 warps, one segment each
 
-// red: shared memory of BS / 32 rows of NPART floats.  Threads at or beyond BS take part in the
-// barrier only.
-template <int BS, typename Part>
-__device__ __forceinline__ void cta_reduce_store_s(float (&acc)[NPART], Part *__restrict__ out, float (*red)[NPART]) {
-  constexpr int NW = BS / 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NPART; ++k) {
-    float v = acc[k];
-    v += __shfl_xor_sync(0xffffffffu, v, 16);
-    v += __shfl_xor_sync(0xffffffffu, v, 8);
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    if (lane == 0 && warp < NW) red[warp][k] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < NPART) {
-    Part s = (Part)red[0][threadIdx.x];
-#pragma unroll
-    for (int w = 1; w < NW; ++w) s += (Part)red[w][threadIdx.x];
-    out[threadIdx.x] = s;
-  }
-}
-
-// Shared memory of one segment evaluation.
-struct SparseSmem {
-  float red[SPARSE_BS / 32][NPART];
-  float bm[SPARSE_BS / 32];
-  int ba[SPARSE_BS / 32];
-};
-
-// One correspondence segment s, evaluated by the first SPARSE_BS threads of the calling CTA (the
-// others only join its barriers).  CG: the pair transform is read through L2 (written by another
-// CTA of a persistent launch).
+// One correspondence segment s, evaluated by the calling warp: lanes stride the
+// correspondences, a warp reduce-scatter sums the 57 partial sums (lane l writes sums 2l and
+// 2l + 1), and in ENERGY mode a butterfly finds the largest distance (first index on ties).  No
+// barrier.  CG: the pair transform is read through L2 (written by another CTA of a persistent
+// launch).
 template <int MODE, typename Part, bool CG = false>
 __device__ __forceinline__ void sparse_seg(int s, const Tables &t, const float4 *__restrict__ P,
                                            const float4 *__restrict__ Q, const float *__restrict__ pairM,
                                            float w_sparse, Part *__restrict__ part, float *__restrict__ seg_rmax,
-                                           int *__restrict__ seg_rarg, SparseSmem &sm) {
+                                           int *__restrict__ seg_rarg) {
+  const int lane = threadIdx.x & 31;
   const int pr = t.seg_pair[s];
-  const int off = t.seg_off[s], cnt = threadIdx.x < SPARSE_BS ? t.seg_cnt[s] : 0;
+  const int off = t.seg_off[s], cnt = t.seg_cnt[s];
   const bool swap = t.seg_swap[s] != 0;
   const float *M = pairM + pr * 24;  // T_b^-1 T_a
   float Mv[12];
@@ -63,7 +34,7 @@ __device__ __forceinline__ void sparse_seg(int s, const Tables &t, const float4 
   for (int k = 0; k < NPART; ++k) acc[k] = 0.f;
   float best = -1.f;
   int barg = 0x7fffffff;
-  for (int k = threadIdx.x; k < cnt; k += SPARSE_BS) {
+  for (int k = lane; k < cnt; k += 32) {
     const float4 u = P[off + k], v = Q[off + k];
     // p in camera a, q in camera b (the pool stores the smaller frame id first)
     const float px = swap ? v.x : u.x, py = swap ? v.y : u.y, pz = swap ? v.z : u.z;
@@ -132,11 +103,16 @@ __device__ __forceinline__ void sparse_seg(int s, const Tables &t, const float4 
       }
     }
   }
-  cta_reduce_store_s<SPARSE_BS, Part>(acc, part + (long long)s * NPART, sm.red);
+  float v[64];
+#pragma unroll
+  for (int k = 0; k < 64; ++k) v[k] = k < NPART ? acc[k] : 0.f;
+  warp_reduce_scatter<64>(v);
+  Part *out = part + (long long)s * NPART;
+  if (2 * lane < NPART) out[2 * lane] = (Part)v[0];
+  if (2 * lane + 1 < NPART) out[2 * lane + 1] = (Part)v[1];
   if (MODE == MODE_ENERGY) {
     // max and its first index over the segment (ties -> smallest index)
-    float *bm = sm.bm;
-    int *ba = sm.ba;
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int oa = __shfl_xor_sync(0xffffffffu, barg, o);
@@ -145,22 +121,9 @@ __device__ __forceinline__ void sparse_seg(int s, const Tables &t, const float4 
         barg = oa;
       }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0 && warp < SPARSE_BS / 32) {
-      bm[warp] = best;
-      ba[warp] = barg;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float b = bm[0];
-      int a = ba[0];
-      for (int w = 1; w < SPARSE_BS / 32; ++w)
-        if (bm[w] > b || (bm[w] == b && ba[w] < a)) {
-          b = bm[w];
-          a = ba[w];
-        }
-      seg_rmax[s] = b;
-      seg_rarg[s] = a;
+    if (lane == 0) {
+      seg_rmax[s] = best;
+      seg_rarg[s] = barg;
     }
   }
 }
