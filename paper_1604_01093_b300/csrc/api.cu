@@ -661,20 +661,28 @@ extern "C" bf_status bf_add_correspondences_batch(bf_ctx *c, int n_pairs, const 
   bf_status s = ensure_corr(c, c->cused + total);
   if (s) return s;
   if (ptr_kind == BF_PTR_HOST) {
-    std::vector<float4> P(total), Q(total);
-    for (int k = 0; k < n_pairs; ++k) {
-      const bool swap = pair_ids[2 * k] > pair_ids[2 * k + 1];
-      const float *a = swap ? p_j : p_i;
-      const float *b = swap ? p_i : p_j;
-      for (int m = offsets[k]; m < offsets[k + 1]; ++m) {
-        P[m] = make_float4(a[3 * m], a[3 * m + 1], a[3 * m + 2], weight ? weight[m] : 1.f);
-        Q[m] = make_float4(b[3 * m], b[3 * m + 1], b[3 * m + 2], 0.f);
-      }
+    // the caller's arrays go to the device as they are (one copy each, straight from pinned
+    // memory when the caller's is pinned) into the upload staging buffer; the packing kernel below
+    // then builds the pool records on the device
+    const size_t need_b = (size_t)total * (weight ? 7 : 6) * sizeof(float);
+    if (need_b > c->stage_bytes) {
+      CK(cudaStreamSynchronize(c->st), "staging");
+      dfree(c, c->stage, c->stage_bytes);
+      c->stage = nullptr;
+      c->stage_bytes = 0;
+      s = dalloc(c, (void **)&c->stage, need_b, "upload staging");
+      if (s) return s;
+      c->stage_bytes = need_b;
     }
-    CK(cudaMemcpyAsync(c->cP + c->cused, P.data(), total * sizeof(float4), cudaMemcpyHostToDevice, c->st), "corr");
-    CK(cudaMemcpyAsync(c->cQ + c->cused, Q.data(), total * sizeof(float4), cudaMemcpyHostToDevice, c->st), "corr");
-    CK(cudaStreamSynchronize(c->st), "corr");
-  } else {
+    float *sp = c->stage, *sq = c->stage + 3 * total, *sw = weight ? c->stage + 6 * total : nullptr;
+    CK(cudaMemcpyAsync(sp, p_i, total * 3 * sizeof(float), cudaMemcpyHostToDevice, c->st), "upload p_i");
+    CK(cudaMemcpyAsync(sq, p_j, total * 3 * sizeof(float), cudaMemcpyHostToDevice, c->st), "upload p_j");
+    if (weight) CK(cudaMemcpyAsync(sw, weight, total * sizeof(float), cudaMemcpyHostToDevice, c->st), "upload w");
+    p_i = sp;
+    p_j = sq;
+    weight = sw;
+  }
+  {
     // offsets and swap flags to the device (scratch), then one packing kernel
     std::vector<int> meta(2 * (size_t)n_pairs + 1);
     for (int k = 0; k <= n_pairs; ++k) meta[k] = offsets[k];
