@@ -841,6 +841,9 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
     return out
 
 
+SERVING_HBM_BUDGET = 40 * 1024 ** 3
+
+
 def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0, seed=1604):
     """Serving: Poisson arrivals of chunk requests (320x240, 3-11 frames, 6 GN x 10 PCG) at `rate`
     per second for `seconds`, and after every 10th chunk a global request over the first k
@@ -857,14 +860,18 @@ def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0,
     pc = {k: chunk_prob.solve[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
     pg = {k: global_prob.solve[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
     out = {"arrival_rate_per_s": rate, "seconds": seconds, "chunk_requests": n_req,
-           "global_requests": n_req // 10, "chunk_workload": chunk_prob.name, "global_workload": global_prob.name}
+           "global_requests": n_req // 10, "chunk_workload": chunk_prob.name, "global_workload": global_prob.name,
+           "hbm_budget_bytes_per_context": SERVING_HBM_BUDGET}
     for name, slots, batch, cprec, gprec in (("served", 2, 16, bf.BF_PREC_FP32, bf.BF_PREC_MIXED),
                                              ("plain_fp32", 1, 1, bf.BF_PREC_FP32, bf.BF_PREC_FP32)):
-        cctx = bf.Context(ci["W"], ci["H"], ci["fx"], ci["fy"], ci["cx"], ci["cy"], max_frames_hint=chunk_prob.n_frames)
+        # admission by a 40 GB HBM budget (each context; batches that would exceed it are split)
+        cctx = bf.Context(ci["W"], ci["H"], ci["fx"], ci["fy"], ci["cx"], ci["cy"], max_frames_hint=chunk_prob.n_frames,
+                          hbm_budget_bytes=SERVING_HBM_BUDGET)
         cctx.add_frames(0, torch.from_numpy(chunk_prob.depth).to(dev), torch.from_numpy(chunk_prob.lum).to(dev))
         cctx.add_correspondences_batch(chunk_prob.pairs, chunk_prob.corr_off, torch.from_numpy(chunk_prob.p_i).to(dev),
                                        torch.from_numpy(chunk_prob.p_j).to(dev))
-        gctx = bf.Context(gi["W"], gi["H"], gi["fx"], gi["fy"], gi["cx"], gi["cy"], max_frames_hint=global_prob.n_frames)
+        gctx = bf.Context(gi["W"], gi["H"], gi["fx"], gi["fy"], gi["cx"], gi["cy"], max_frames_hint=global_prob.n_frames,
+                          hbm_budget_bytes=SERVING_HBM_BUDGET)
         gctx.add_frames(0, global_prob.depth, global_prob.lum, init_pose=global_prob.init)
         gctx.add_correspondences_batch(global_prob.pairs, global_prob.corr_off, global_prob.p_i, global_prob.p_j)
         torch.cuda.synchronize(dev)
