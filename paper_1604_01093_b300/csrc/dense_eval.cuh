@@ -15,6 +15,11 @@ namespace bf {
 struct V3 {
   float x, y, z;
 };
+
+// A stored normal (y, z, w of the record) is valid unless all three components are +-0.
+__device__ __forceinline__ bool normal_valid(const float4 &a) {
+  return ((__float_as_uint(a.y) | __float_as_uint(a.z) | __float_as_uint(a.w)) << 1) != 0u;
+}
 __device__ __forceinline__ V3 cross3(V3 a, V3 b) {
   return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
@@ -79,8 +84,7 @@ template <int MODE, typename LA, typename LB, typename LI>
 __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const PairXf &X, const Intr &in,
                                           const float *kx, const float *ky, const Gates &g, LA loadA, LB loadB,
                                           LI srcI, float w_geo, float w_photo, float (&acc)[NPD]) {
-  const bool nvalid = (a.y != 0.f) || (a.z != 0.f) || (a.w != 0.f);
-  if (!(a.x > 0.f && nvalid)) return -1;
+  if (!(a.x > 0.f && normal_valid(a))) return -1;
   const int W = in.W, H = in.H;
   const float z = a.x;
   // ---- association decisions, explicitly rounded FP32 in a fixed order: products, sums and
@@ -93,11 +97,12 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
   const float iz = __frcp_rn(Y2);
   const float ux = FMA(in.fx, FM(Y0, iz), in.cx);
   const float uy = FMA(in.fy, FM(Y1, iz), in.cy);
-  const float nxf = floorf(FA(ux, 0.5f)), nyf = floorf(FA(uy, 0.5f));
+  // bilinear taps on the 2-pixel interior: 2 <= bx and bx + 1 <= W - 3 (bx integer-valued).  That
+  // bounds u to [2, W - 3), so the nearest pixel floor(u + 0.5) (FP32 rounding is monotonic and
+  // 2.5, W - 2.5 are representable) lies in [2, W - 3]: inside the image without a test of its own
   const float bxf = floorf(ux), byf = floorf(uy);
-  if (!(nxf >= 0.f && nxf <= (float)(W - 1) && nyf >= 0.f && nyf <= (float)(H - 1) && bxf >= 2.f &&
-        FA(bxf, 1.f) <= (float)(W - 3) && byf >= 2.f && FA(byf, 1.f) <= (float)(H - 3)))
-    return -1;
+  if (!(bxf >= 2.f && bxf <= (float)(W - 4) && byf >= 2.f && byf <= (float)(H - 4))) return -1;
+  const float nxf = floorf(FA(ux, 0.5f)), nyf = floorf(FA(uy, 0.5f));
   const int tx = (int)nxf, ty = (int)nyf;
   const int bx = (int)bxf, by = (int)byf;
   const int tpx = ty * W + tx, b0 = by * W + bx;
@@ -110,8 +115,7 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
     c10 = loadB(b0 + W);
     c11 = loadB(b0 + W + 1);
   }
-  const bool tnvalid = (b.y != 0.f) || (b.z != 0.f) || (b.w != 0.f);
-  if (!(b.x > 0.f && tnvalid)) return -1;
+  if (!(b.x > 0.f && normal_valid(b))) return -1;
   const float qx = FM(kx[tx], b.x), qy = FM(ky[ty], b.x), qz = b.x;
   const float ex = FS(Y0, qx), ey = FS(Y1, qy), ez = FS(Y2, qz);
   const float dist2 = FMA(ez, ez, FMA(ey, ey, FM(ex, ex)));

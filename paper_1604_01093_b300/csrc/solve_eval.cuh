@@ -134,12 +134,16 @@ __device__ __forceinline__ void merge_pair(int p, const Tables &t, const double 
       __syncwarp();
       Acc tt[3];
       {
+        // lanes 0-2 form one component each (B300 runs FP64 at 1/64 rate: a warp FP64
+        // instruction costs the same with 3 lanes active as with 32), then broadcast
         const double *Ti = pose + 12 * srcf, *Tj = pose + 12 * tgt;
-        const double d0 = ldx<CG>(Ti + 9) - ldx<CG>(Tj + 9), d1 = ldx<CG>(Ti + 10) - ldx<CG>(Tj + 10),
-                     d2 = ldx<CG>(Ti + 11) - ldx<CG>(Tj + 11);
+        const int m = lane < 3 ? lane : 0;
+        const double dm = ldx<CG>(Ti + 9 + m) - ldx<CG>(Tj + 9 + m);
+        const double d0 = __shfl_sync(0xffffffffu, dm, 0), d1 = __shfl_sync(0xffffffffu, dm, 1),
+                     d2 = __shfl_sync(0xffffffffu, dm, 2);
+        const Acc tm = (Acc)(ldx<CG>(Tj + m) * d0 + ldx<CG>(Tj + 3 + m) * d1 + ldx<CG>(Tj + 6 + m) * d2);
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-          tt[m] = (Acc)(ldx<CG>(Tj + m) * d0 + ldx<CG>(Tj + 3 + m) * d1 + ldx<CG>(Tj + 6 + m) * d2);
+        for (int k = 0; k < 3; ++k) tt[k] = __shfl_sync(0xffffffffu, tm, k);
       }
       const Acc T3[3][3] = {{0, tt[2], -tt[1]}, {-tt[2], 0, tt[0]}, {tt[1], -tt[0], 0}};
       for (int k = lane; k < 6; k += 32) {
