@@ -87,6 +87,9 @@ struct Exec {
   int gkernels = 0;
   std::vector<int> last_ints;  // tables last uploaded into ws (skipped when unchanged)
   const void *last_ws = nullptr;
+  // second stream for work independent of the main stream's (a parallel branch of the graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Serving: queued requests and the worker slots that run them.
@@ -439,6 +442,11 @@ extern "C" bf_status bf_create(const bf_config *cfg, bf_ctx **out) {
 }
 
 static void free_exec(bf_ctx *c, Exec &e) {
+  if (e.side) cudaStreamDestroy(e.side);
+  if (e.ev_fork) cudaEventDestroy(e.ev_fork);
+  if (e.ev_join) cudaEventDestroy(e.ev_join);
+  e.side = nullptr;
+  e.ev_fork = e.ev_join = nullptr;
   if (e.ws) cudaFree(e.ws);
   if (e.gexec) cudaGraphExecDestroy(e.gexec);
   if (e.pin) cudaFreeHost(e.pin);
@@ -1216,11 +1224,38 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
   return BF_OK;
 }
 
+// The executor's second stream (created on first use), or nullptr when kernels are timed one
+// by one (profiling) or it cannot be created: the caller then stays on the main stream.
+static cudaStream_t side_stream(bf_ctx *c) {
+  Exec &e = *c->ex;
+  if (c->prof) return nullptr;
+  if (!e.side) {
+    if (cudaStreamCreateWithFlags(&e.side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      if (e.side) cudaStreamDestroy(e.side);
+      if (e.ev_fork) cudaEventDestroy(e.ev_fork);
+      e.side = nullptr;
+      e.ev_fork = e.ev_join = nullptr;
+      return nullptr;
+    }
+  }
+  return e.side;
+}
+
 // One Gauss-Newton iteration's linearisation at the pair transforms in D.pairM: dense + sparse
-// partials, merge.
+// partials, merge.  The sparse kernel does not depend on the dense one: it runs on the second
+// stream (a parallel branch of the captured graph), where it fills the SMs the dense launch's
+// last wave leaves idle, and the merge waits for both.
 template <typename Acc>
 void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, int mode) {
   const Tables &t = D.t;
+  cudaStream_t side = t.n_segs > 0 ? side_stream(c) : nullptr;
+  if (side) {
+    cudaEventRecord(c->ex->ev_fork, c->ex->st);
+    cudaStreamWaitEvent(side, c->ex->ev_fork, 0);
+  }
   Gates g;
   g.tau_d2 = (float)(prm.tau_dist * prm.tau_dist);
   g.tau_n = (float)prm.tau_normal;
@@ -1233,8 +1268,12 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
   });
   run_k(c, BF_K_SPARSE, [&] {
     return launch_sparse<Acc>(mode, t, c->cP, c->cQ, D.pairM, (float)prm.w_sparse, (Acc *)D.spart, D.srmax,
-                              D.srarg, c->ex->st);
+                              D.srarg, side ? side : c->ex->st);
   });
+  if (side) {
+    cudaEventRecord(c->ex->ev_join, side);
+    cudaStreamWaitEvent(c->ex->st, c->ex->ev_join, 0);
+  }
   run_k(c, BF_K_MERGE, [&] {
     return launch_pair_merge<Acc, Acc>(t, D.pose, (const Acc *)D.dpart, (const Acc *)D.spart, (Acc *)D.pairblk,
                                        (Acc *)D.pairen, D.pairoff, c->ex->st);
@@ -1389,6 +1428,7 @@ bf_status run_gn_graph(bf_ctx *c, const HostTables &T, const bf_solve_params &pr
     cudaGraphExecDestroy(c->ex->gexec);
     c->ex->gexec = nullptr;
   }
+  side_stream(c);  // create the second stream and its events before the capture, not during it
   CK(cudaStreamBeginCapture(c->ex->st, cudaStreamCaptureModeThreadLocal), "begin capture");
   const long long before = c->launches;
   bf_status s = mixed ? run_gn<double>(c, T, prm, D) : run_gn<float>(c, T, prm, D);
