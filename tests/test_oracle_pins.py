@@ -901,3 +901,20 @@ def test_storage_rounding_of_a_frame():
         assert np.any(f.N != f64.N)
     f32 = frames.Frame(prob.depth[0], prob.lum[0], intr, storage="fp32")
     np.testing.assert_array_equal(f32.N, f64.N)
+
+
+def test_global300_golden_is_the_oracles_output():
+    """tests/golden/global300_oracle.json (the full-size reference of the GPU tests) is what the
+    oracle computes today on the seeded workload: regenerate the first Gauss-Newton step and compare."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "global300_oracle.json")
+    with open(path) as f:
+        gold = json.load(f)
+    prob = synth.cfg2()
+    d = prob.solve
+    fr = [frames.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in range(prob.n_frames)]
+    prm = SolveParams(n_gn=1, n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"], w_photo=d["w_photo"],
+                      w_geo=d["w_geo"])
+    res = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(prob.n_frames)), prm)
+    np.testing.assert_allclose(res.energy, gold["energy"], rtol=1e-12)
+    np.testing.assert_allclose(np.stack([P[:3, :].ravel() for P in res.poses]), np.array(gold["poses"]),
+                               rtol=0, atol=1e-12)
