@@ -1,10 +1,14 @@
-"""Full-size parity: the 300-keyframe global solve in the launch configuration bench.py times
-(mixed precision, target frames staged in shared memory, cluster PCG, the Gauss-Newton loop
-replayed as a CUDA graph) against the FP64 oracle's first Gauss-Newton step on the same workload.
+"""Full-size parity in the launch configurations bench.py times, against stored oracle results:
 
-The oracle's step takes about a minute at this size, so its result is stored in
-tests/golden/global300_oracle.json, written by tests/golden/make_global300_oracle.py from the
-oracle and the seeded scene generator alone.  Tolerances are the spec ones.
+* the 300-keyframe global solve (mixed precision, target frames staged in shared memory, cluster
+  PCG, the Gauss-Newton loop replayed as a CUDA graph) against the FP64 oracle's first
+  Gauss-Newton step (tests/golden/global300_oracle.json);
+* the whole 256-chunk 320x240 batch (FP32 arithmetic, graph; launch sequence and persistent
+  launch), sampled on a 3-frame and an 11-frame chunk (tests/golden/chunks256_oracle.json).
+
+The oracle needs one to two minutes for these, so its results are stored, written by the
+make_*_oracle.py scripts beside them from the oracle and the seeded scene generator alone.
+Tolerances are the spec ones.
 """
 import json
 import os
@@ -88,3 +92,48 @@ def test_global300_bench_solve_starts_at_the_oracle_energy(bf, global300, golden
     assert abs(st["energy"][0] - golden["energy"][0]) <= ENERGY_RTOL * golden["energy"][0]
     assert abs(st["energy"][1] - golden["energy"][1]) <= ENERGY_RTOL * golden["energy"][1]
     assert st["energy"][-1] < 0.8 * st["energy"][0]
+
+
+@pytest.fixture(scope="module")
+def chunks256():
+    return synth.cfg3()
+
+
+@pytest.fixture(scope="module")
+def golden_chunks():
+    with open(os.path.join(HERE, "golden", "chunks256_oracle.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("persistent,tile", [(0, -1), (1, 38400)])
+def test_chunks256_batch_matches_oracle_on_sampled_chunks(bf, chunks256, golden_chunks, persistent, tile):
+    """The whole 256-chunk 320x240 batch in bench.py's configuration (FP32 arithmetic, CUDA graph;
+    autotuned tiles for the launch sequence, half-frame tiles for the persistent launch); a 3-frame
+    and an 11-frame chunk against the oracle's solves."""
+    import torch
+    prob = chunks256
+    assert golden_chunks["workload"] == prob.name and golden_chunks["chunks"] == len(prob.chunks)
+    intr = prob.intr
+    dev = torch.device("cuda", 0)
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"],
+                     max_frames_hint=prob.n_frames)
+    ctx.add_frames(0, torch.from_numpy(prob.depth).to(dev), torch.from_numpy(prob.lum).to(dev))
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                  torch.from_numpy(prob.p_j).to(dev))
+    d = prob.solve
+    lists = [c.tolist() for c in prob.chunks]
+    stats = ctx.solve_local_batch(list(range(len(lists))), lists, n_gn=d["n_gn"], n_pcg=d["n_pcg"],
+                                  w_sparse=d["w_sparse"], w_dense=d["w_dense"], w_photo=d["w_photo"],
+                                  w_geo=d["w_geo"], precision=bf.BF_PREC_FP32, use_graph=1, tile_px=tile,
+                                  persistent=persistent)
+    for s in golden_chunks["samples"]:
+        k = s["chunk"]
+        assert lists[k] == s["frames"]
+        rel = np.abs(np.array(stats[k]["energy"]) - np.array(s["energy"])) / np.array(s["energy"])
+        assert rel.max() <= ENERGY_RTOL, (k, rel)
+        P = ctx.get_poses(lists[k])
+        for f in range(len(lists[k])):
+            ref = np.eye(4)
+            ref[:3, :] = np.array(s["poses"][f]).reshape(3, 4)
+            rot, tr = lie.pose_error(P[f], ref)
+            assert rot <= ROT_TOL and tr <= TRANS_TOL, (k, f, rot, tr)
