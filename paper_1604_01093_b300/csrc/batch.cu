@@ -39,7 +39,8 @@ enum : int { IT_XFORM = 0, IT_DENSE = 1, IT_SPARSE = 2, IT_SOLVE = 3, IT_EDENSE 
 constexpr int BATCH_BS = 256;  // = DENSE_BS = PCG_BS
 static_assert(BATCH_BS == DENSE_BS && BATCH_BS == PCG_BS && BATCH_BS >= SPARSE_BS, "one CTA shape for all items");
 // Polls of a slot's flag before a CTA gives up: the first 2^10 back to back, then with a 256 ns
-// back-off, about 4 s in all (a legitimate wait is at most one item's duration).
+// back-off, about 4 s in all (a legitimate wait ends when an item in progress on another CTA
+// finishes and publishes its followers: milliseconds at most).
 constexpr long long BATCH_WAIT_LIMIT = 1LL << 24;
 
 // Shared memory of one CTA: the item functions' scratch, one at a time.
