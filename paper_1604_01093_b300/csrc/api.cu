@@ -1490,7 +1490,7 @@ struct SolveJob {
 // ---------------------------------------------------------------- dense work autotuner
 // tile_px = BF_TILE_AUTOTUNE: the first solve of a context (per frame size and storage) times the
 // dense kernel on its own tables for each candidate decomposition — the target frame staged in
-// shared memory when it fits, else whole-frame, half-frame and quarter-frame tiles — takes the
+// shared memory when it fits, and tiles of 1, 1/2, 1/4, 1/8 and 1/16 of a frame — takes the
 // fastest (median of 3 launches, CUDA events on the solve's stream) and keeps it for the
 // context's later solves.  The choice depends on the frame size and storage only, so a problem
 // gets the same decomposition alone and inside a batch.
@@ -1501,7 +1501,7 @@ static int tune_tile(bf_ctx *c, const std::vector<Problem> &probs, const bf_solv
   if (it != c->tuned_tile.end()) return it->second;
   std::vector<int> cand;
   if (dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage)) cand.push_back(0);
-  for (int d : {1, 2, 4}) {
+  for (int d : {1, 2, 4, 8, 16}) {
     const int t = std::max(256, (HW + d - 1) / d);
     if (std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
   }
