@@ -479,11 +479,12 @@ bf_status bf_tuned_tile_px(bf_ctx *ctx, int *tile_px);
 
 /*
  * Failure-detection self-test.  The library's device waits (the cooperative PCG's grid barrier,
- * the staged dense kernel's wait for its bulk copies) give up after a bounded number of polls
- * and the call that launched them returns BF_ERR_TIMEOUT.  This call makes one such wait run out
- * on purpose with `limit` polls (1 .. 2^24): which = 0 polls a device word that nothing
- * changes, which = 1 waits on an mbarrier that nothing arrives on.  *gave_up = 1 and
- * BF_ERR_TIMEOUT when the wait ended as designed; the context stays usable.
+ * the staged dense kernel's wait for its bulk copies, the persistent batched solve's wait for a
+ * work-queue slot) give up after a bounded number of polls and the call that launched them
+ * returns BF_ERR_TIMEOUT.  This call makes one such wait run out on purpose with `limit` polls
+ * (1 .. 2^24): which = 0 polls a device word that nothing changes, which = 1 waits on an mbarrier
+ * that nothing arrives on, which = 2 waits for a queue slot that nothing publishes.  *gave_up = 1
+ * and BF_ERR_TIMEOUT when the wait ended as designed; the context stays usable.
  */
 bf_status bf_selftest_wait_timeout(bf_ctx *ctx, int which, long long limit, int *gave_up);
 

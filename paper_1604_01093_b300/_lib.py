@@ -396,7 +396,7 @@ class Context:
     # ------------------------------------------------------ failure detection
     def selftest_wait_timeout(self, which, limit=1 << 16):
         """Make one bounded device wait run out (0: a word nothing changes, 1: an mbarrier nothing
-        arrives on); returns (status, gave_up)."""
+        arrives on, 2: a work-queue slot nothing publishes); returns (status, gave_up)."""
         flag = ctypes.c_int(0)
         st = lib().bf_selftest_wait_timeout(self.h, which, limit, ctypes.byref(flag))
         return st, flag.value

@@ -1934,7 +1934,7 @@ extern "C" bf_status bf_tuned_tile_px(bf_ctx *c, int *tile_px) {
 extern "C" bf_status bf_selftest_wait_timeout(bf_ctx *c, int which, long long limit, int *gave_up) {
   if (!c) return BF_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(c->mu);
-  if ((which != 0 && which != 1) || limit < 1 || limit > (1LL << 24) || !gave_up)
+  if (which < 0 || which > 2 || limit < 1 || limit > (1LL << 24) || !gave_up)
     return fail(c, BF_ERR_INVALID_ARG, "bf_selftest_wait_timeout: bad arguments");
   cudaStream_t st = c->ex->st;
   int *buf = nullptr;  // [0] the word nothing changes, [1] the kernel's error flag

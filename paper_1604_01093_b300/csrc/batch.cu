@@ -60,16 +60,6 @@ struct BatchSmem {
   BatchQueue queue;
 };
 
-__device__ __forceinline__ bool wait_slot(const int *flag, const volatile int *err, long long limit) {
-  const volatile int *f = flag;
-  for (long long k = 0; k < limit; ++k) {
-    if (*f != 0) return true;
-    if (*err) return false;
-    if (k > 1024) __nanosleep(256);
-  }
-  return false;
-}
-
 // Publish the items of problem p's stage g (g < n_gn: its tiles and segments of iteration g;
 // g == n_gn: the final energy's); a problem without any goes straight to SOLVE / FINAL.  Called
 // by every thread of the CTA.
@@ -232,7 +222,7 @@ __global__ void __launch_bounds__(BATCH_BS, 3) k_batch(BatchArgs a, BatchQueue q
         stop = 1;
       } else if (h < q.n_prob) {
         it = make_int4(IT_XFORM, h, 0, 0);  // the first n_prob slots are implicit
-      } else if (!wait_slot(q.flags + h, q.err, q.wait_limit)) {
+      } else if (!wait_published(q.flags + h, q.err, q.wait_limit)) {
         atomicCAS(q.err, 0, 1);
         stop = 1;
       } else {

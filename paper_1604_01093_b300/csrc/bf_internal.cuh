@@ -288,6 +288,18 @@ __device__ __forceinline__ bool wait_change(const volatile unsigned *word, unsig
   return true;
 }
 
+// Spin until a work-queue slot's flag is set (published): the first 1024 polls back to back, then
+// with a 256 ns back-off.  Gives up (false) after `limit` polls, or as soon as *abort is set.
+__device__ __forceinline__ bool wait_published(const int *flag, const volatile int *abort, long long limit) {
+  const volatile int *f = flag;
+  for (long long k = 0; k < limit; ++k) {
+    if (*f != 0) return true;
+    if (*abort) return false;
+    if (k > 1024) __nanosleep(256);
+  }
+  return false;
+}
+
 // Per-GN-iteration outputs the PCG kernels write besides the step: the problem's energy record
 // (sum of its pairs' records, fixed order), the updated poses and (per-problem kernel only) the
 // pair transforms of the updated poses for the next linearisation.
@@ -375,7 +387,8 @@ size_t keypoint_result_bytes();
 int launch_keypoints(int n_pairs, const int *off, const float *P, const float *Q, double max_res, double max_cond,
                      int min_matches, double min_area, unsigned char *keep, void *res, cudaStream_t st);
 // Bounded-wait self-test: which = 0 polls *word (which stays 0), 1 waits on an mbarrier nothing
-// arrives on; *err = 1 when the wait gave up after `limit` polls.
+// arrives on, 2 waits for a work-queue slot nothing publishes (*word as its flag); *err = 1 when
+// the wait gave up after `limit` polls.
 int launch_selftest_wait(int which, const unsigned *word, int *err, long long limit, cudaStream_t st);
 // TSDF volume on the device (Sec. 5): hash table of packed block coordinates, block pool of
 // integer sums, the touched list of the current call, counters and the error bits

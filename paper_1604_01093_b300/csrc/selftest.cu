@@ -1,11 +1,13 @@
 // Failure-detection self-test of the bounded device waits.
 //
 // The library's device waits (the cooperative PCG's grid barrier polling a generation word, the
-// staged dense kernel waiting on an mbarrier for its bulk copies) give up after a bounded number
-// of polls and report an error the host turns into BF_ERR_TIMEOUT, so a lost participant cannot
-// hang the GPU.  These kernels make each kind of wait run out on purpose, with the same helpers
-// and a short limit: a generation word that nothing advances, an mbarrier that nothing arrives
-// on.  Nothing faults and nothing is left in flight: no copy was issued, the wait just ends.
+// staged dense kernel waiting on an mbarrier for its bulk copies, the persistent batched solve
+// waiting for a work-queue slot to be published) give up after a bounded number of polls and
+// report an error the host turns into BF_ERR_TIMEOUT, so a lost participant cannot hang the GPU.
+// These kernels make each kind of wait run out on purpose, with the same helpers and a short
+// limit: a generation word that nothing advances, an mbarrier that nothing arrives on, a slot
+// flag that nothing sets.  Nothing faults and nothing is left in flight: no copy was issued, the
+// wait just ends.
 #include "bf_internal.cuh"
 
 namespace bf {
@@ -34,11 +36,23 @@ __global__ void k_selftest_mbarrier(int *err, long long limit) {
   if (threadIdx.x == 0) *err = done ? 0 : 1;
 }
 
+// One thread waits for a work-queue slot flag (the word) nothing publishes; err = 1 when the wait
+// gave up.
+__global__ void k_selftest_slot(const unsigned *word, int *err, long long limit) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  __shared__ int abort_flag;
+  abort_flag = 0;
+  const bool published = wait_published((const int *)word, (const volatile int *)&abort_flag, limit);
+  *err = published ? 0 : 1;
+}
+
 int launch_selftest_wait(int which, const unsigned *word, int *err, long long limit, cudaStream_t st) {
   if (which == 0)
     k_selftest_word<<<1, 32, 0, st>>>(word, err, limit);
-  else
+  else if (which == 1)
     k_selftest_mbarrier<<<1, 128, 0, st>>>(err, limit);
+  else
+    k_selftest_slot<<<1, 32, 0, st>>>(word, err, limit);
   return 1;
 }
 

@@ -83,6 +83,36 @@ def test_preprocess_matches_oracle(bf, cfg1, cfg1_frames):
         np.testing.assert_allclose(P[6], f.Iy, atol=2e-6)
 
 
+def test_malformed_depth_is_invalid_and_the_solve_stays_finite(bf, cfg1):
+    """Host-side fault injection: NaN, +-inf, negative and out-of-range depths in the input frames
+    are invalid pixels exactly as the oracle marks them (and so are their normals' neighbours), and
+    a solve over the corrupted frames stays finite."""
+    depth = cfg1.depth.copy()
+    rng = np.random.default_rng(3)
+    for k in range(cfg1.n_frames):
+        idx = rng.choice(depth[k].size, 60, replace=False)
+        flat = depth[k].reshape(-1)
+        flat[idx[:15]] = np.nan
+        flat[idx[15:30]] = np.inf
+        flat[idx[30:45]] = -np.inf
+        flat[idx[45:52]] = -1.0
+        flat[idx[52:]] = 1e6
+    intr = cfg1.intr
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"])
+    ctx.add_frames(0, depth, cfg1.lum)
+    for k, (i, j) in enumerate(cfg1.pairs):
+        p, q = cfg1.pair_corr(k)
+        ctx.add_correspondences(int(i), int(j), p, q)
+    for k in (0, 7):
+        P = ctx.frame_planes(k)
+        f = ofr.Frame(depth[k], cfg1.lum[k], intr)
+        np.testing.assert_array_equal(P[0] > 0, f.valid)
+        np.testing.assert_array_equal(np.any(P[1:4] != 0, axis=0), f.nvalid)
+        assert np.isfinite(P).all()
+    st = ctx.solve_local(0, list(range(cfg1.n_frames)), **dict(cfg1.solve))
+    assert np.isfinite(st["energy"]).all() and np.isfinite(ctx.get_poses(list(range(cfg1.n_frames)))).all()
+
+
 # ------------------------------------------------------------------------------- association
 
 @pytest.mark.parametrize("pair", [(0, 1), (3, 0), (2, 9), (10, 4)])
@@ -409,10 +439,11 @@ def test_batched_chunks_320x240_match_oracle(bf, batch320):
         compare_solve(stats[k], ctx.get_poses(ids), ref, f"chunk {k} at 320x240")
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_waits_give_up_and_the_context_survives(bf, cfg1, which):
-    """Failure detection without a fault: a wait on a flag nothing sets (0) or an mbarrier nothing
-    arrives on (1) ends after its poll limit with BF_ERR_TIMEOUT; the same context then solves."""
+    """Failure detection without a fault: a wait on a flag nothing sets (0), an mbarrier nothing
+    arrives on (1) or a work-queue slot nothing publishes (2) ends after its poll limit with
+    BF_ERR_TIMEOUT; the same context then solves."""
     ctx = make_ctx(bf, cfg1)
     status, gave_up = ctx.selftest_wait_timeout(which, 1 << 14)
     assert status == 6 and gave_up == 1  # BF_ERR_TIMEOUT
