@@ -328,41 +328,52 @@ __device__ __forceinline__ void assemble_var(int v, const Tables &t, const Acc *
   double *Dshw = sm.D;
   float *Mshw = sm.M;
   const int e0 = t.inc_off[v], e1 = t.inc_off[v + 1];
-  // lane handles entries lane and lane + 32 of [D (36) | rhs (6)]; the incidences are read 8 at
-  // a time (all loads in flight together) and summed in incidence order
-  for (int k = lane; k < 42; k += 32) {
-    Acc s = 0;
-    for (int e = e0; e < e1; e += 8) {
-      Acc v[8];
+  // lane handles entries lane and lane + 32 of [D (36) | rhs (6)] in one pass over the incidences,
+  // read 8 at a time (all loads in flight together) and summed in incidence order
+  const int k2 = lane + 32;
+  const bool has2 = k2 < 42;
+  Acc s1 = 0, s2 = 0;
+  for (int e = e0; e < e1; e += 8) {
+    Acc v1[8], v2[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        v[u] = 0;
-        if (e + u < e1) {
-          const int ent = t.inc[e + u];
-          const int p = ent >> 1, side = ent & 1;
-          const Acc *b = pairblk + (long long)p * PAIRBLK;
-          v[u] = k < 36 ? b[(side == 0 ? PB_AA : PB_BB) + k] : b[(side == 0 ? PB_RA : PB_RB) + k - 36];
-        }
+    for (int u = 0; u < 8; ++u) {
+      v1[u] = 0;
+      v2[u] = 0;
+      if (e + u < e1) {
+        const int ent = t.inc[e + u];
+        const int p = ent >> 1, side = ent & 1;
+        const Acc *b = pairblk + (long long)p * PAIRBLK;
+        v1[u] = b[(side == 0 ? PB_AA : PB_BB) + lane];
+        if (has2) v2[u] = k2 < 36 ? b[(side == 0 ? PB_AA : PB_BB) + k2] : b[(side == 0 ? PB_RA : PB_RB) + k2 - 36];
       }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (e + u < e1) s += v[u];
     }
-    if (k < 36) {
-      Dd[(long long)v * 36 + k] = s;
-      Df[(long long)v * 36 + k] = (float)s;
-      Dshw[k] = (double)s;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (e + u < e1) {
+        s1 += v1[u];
+        s2 += v2[u];
+      }
+  }
+  Dd[(long long)v * 36 + lane] = s1;
+  Df[(long long)v * 36 + lane] = (float)s1;
+  Dshw[lane] = (double)s1;
+  if (has2) {
+    if (k2 < 36) {
+      Dd[(long long)v * 36 + k2] = s2;
+      Df[(long long)v * 36 + k2] = (float)s2;
+      Dshw[k2] = (double)s2;
     } else {
-      rhs[(long long)v * 6 + k - 36] = s;
+      rhs[(long long)v * 6 + k2 - 36] = s2;
     }
   }
+  // an all-zero block (integer test for +-0: an FP64 compare would occupy the slow FP64 pipe)
+  const bool nz = ((__double_as_longlong((double)s1) << 1) != 0) ||
+                  (k2 < 36 && ((__double_as_longlong((double)s2) << 1) != 0));
+  const bool empty = __ballot_sync(0xffffffffu, nz) == 0u;
+  for (int k = lane; k < 36; k += 32) Mshw[k] = 0.f;
   __syncwarp();
   if (lane == 0) {
     int flag = 0;
-    bool empty = true;
-    // integer test for +-0 (an FP64 compare would occupy the slow FP64 pipe 36 times)
-    for (int k = 0; k < 36; ++k) empty = empty && ((__double_as_longlong(Dshw[k]) << 1) == 0);
-    for (int k = 0; k < 36; ++k) Mshw[k] = 0.f;
     if (empty) {
       flag = 2;  // BF_FLAG_EMPTY_FRAME: zero inverse, the frame's update stays 0
     } else {

@@ -137,3 +137,52 @@ def test_chunks256_batch_matches_oracle_on_sampled_chunks(bf, chunks256, golden_
             ref[:3, :] = np.array(s["poses"][f]).reshape(3, 4)
             rot, tr = lie.pose_error(P[f], ref)
             assert rot <= ROT_TOL and tr <= TRANS_TOL, (k, f, rot, tr)
+
+
+@pytest.fixture(scope="module")
+def global2000():
+    return synth.cfg5()
+
+
+@pytest.fixture(scope="module")
+def golden2000():
+    with open(os.path.join(HERE, "golden", "global2000_oracle.json")) as f:
+        return json.load(f)
+
+
+def test_global2000_first_step_matches_oracle(bf, global2000, golden2000):
+    """The 2000-keyframe 160x120 solve in bench.py's configuration (BF16 frame storage, mixed
+    precision, tiled dense kernel, cluster PCG with its blocks in global memory, CUDA graph): its
+    first Gauss-Newton step against the oracle's on the same BF16-rounded planes (energies, and the
+    poses of every 32nd keyframe); the bench's own 10-step solve starts at the same two energies."""
+    import torch
+    prob = global2000
+    assert golden2000["workload"] == prob.name and golden2000["n_frames"] == prob.n_frames
+    intr = prob.intr
+    dev = torch.device("cuda", 0)
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"],
+                     max_frames_hint=prob.n_frames, storage=bf.BF_STORE_BF16)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                  torch.from_numpy(prob.p_j).to(dev))
+    depth, lum = torch.from_numpy(prob.depth).to(dev), torch.from_numpy(prob.lum).to(dev)
+    d = prob.solve
+    common = dict(n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"], w_photo=d["w_photo"],
+                  w_geo=d["w_geo"], use_graph=1)
+    ids = list(range(prob.n_frames))
+    ctx.add_frames(0, depth, lum, init_pose=prob.init)
+    st = ctx.solve_global(ids, n_gn=1, **common)
+    assert st["flags"] == 0
+    gold_e = np.array(golden2000["energy"])
+    rel = np.abs(np.array(st["energy"]) - gold_e) / gold_e
+    assert rel.max() <= ENERGY_RTOL, rel
+    P = ctx.get_poses(golden2000["frames_kept"])
+    for k, f in enumerate(golden2000["frames_kept"]):
+        ref = np.eye(4)
+        ref[:3, :] = np.array(golden2000["poses"][k]).reshape(3, 4)
+        rot, tr = lie.pose_error(P[k], ref)
+        assert rot <= ROT_TOL and tr <= TRANS_TOL, (f, rot, tr)
+    ctx.add_frames(0, depth, lum, init_pose=prob.init)
+    full = ctx.solve_global(ids, n_gn=d["n_gn"], **common)
+    assert abs(full["energy"][0] - gold_e[0]) <= ENERGY_RTOL * gold_e[0]
+    assert abs(full["energy"][1] - gold_e[1]) <= ENERGY_RTOL * gold_e[1]
+    assert full["energy"][-1] < full["energy"][0]
