@@ -75,6 +75,10 @@ inline uint64_t pair_key(int a, int b) {
 
 // Everything one solve in flight needs besides the shared frame store and correspondence pool:
 // a stream, the workspace arena, pinned staging and the cached Gauss-Newton graph.
+namespace {
+struct TableCache;  // defined with the solve tables below
+}
+
 struct Exec {
   cudaStream_t st = nullptr;
   cudaStream_t st_hi = nullptr, st_lo = nullptr;  // serving slots: local / global request streams
@@ -85,8 +89,15 @@ struct Exec {
   cudaGraphExec_t gexec = nullptr;
   std::vector<unsigned char> gkey;
   int gkernels = 0;
-  std::vector<int> last_ints;  // tables last uploaded into ws (skipped when unchanged)
+  // tables are identified by a generation number (one per distinct build, 0 = unnamed): the one
+  // whose contents ws holds (re-uploaded only when it changes) and the one the graph was
+  // captured with (its launch parameters and table pointers depend on them)
+  uint64_t ws_gen = 0, graph_gen = 0;
   const void *last_ws = nullptr;
+  std::shared_ptr<TableCache> tcache;  // the last tables built on this executor
+  // recorded after the last copy into or out of the pinned buffer
+  cudaEvent_t pin_ev = nullptr;
+  bool pin_ev_live = false;
   // second stream for work independent of the main stream's (a parallel branch of the graph)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -153,6 +164,9 @@ struct bf_ctx {
   long long ccap = 0, cused = 0;
   std::unordered_map<uint64_t, std::vector<Seg>> corr;
   std::unordered_map<int, Chunk> chunks;
+  // bumped whenever the pair map changes / a frame id gets a slot; with the problem list and the
+  // table parameters they decide whether a solve can reuse the last tables it built
+  uint64_t corr_ver = 0, frames_ver = 0, tables_gen = 0;
   // solve executor in use (main, or a serving slot while it holds the context lock)
   Exec main;
   Exec *ex = &main;
@@ -450,6 +464,12 @@ static void free_exec(bf_ctx *c, Exec &e) {
   if (e.ws) cudaFree(e.ws);
   if (e.gexec) cudaGraphExecDestroy(e.gexec);
   if (e.pin) cudaFreeHost(e.pin);
+  if (e.pin_ev) cudaEventDestroy(e.pin_ev);
+  e.pin_ev = nullptr;
+  e.pin_ev_live = false;
+  e.tcache.reset();
+  e.ws_gen = e.graph_gen = 0;
+  e.last_ws = nullptr;
   c->bytes -= e.ws_bytes;
   e.ws = nullptr;
   e.ws_bytes = 0;
@@ -515,6 +535,7 @@ extern "C" bf_status bf_add_frames(bf_ctx *c, int first_id, int n, const float *
   for (int k = 0; k < n; ++k) {
     FrameInfo &fi = c->frames[first_id + k];
     if (fi.slot < 0) {
+      ++c->frames_ver;
       if (!c->free_slots.empty()) {
         fi.slot = c->free_slots.back();
         c->free_slots.pop_back();
@@ -643,6 +664,7 @@ extern "C" bf_status bf_add_correspondences(bf_ctx *c, int frame_i, int frame_j,
     CK(cudaGetLastError(), "pack corr");
   }
   c->corr[pair_key(frame_i, frame_j)].push_back(Seg{(int)c->cused, n});
+  ++c->corr_ver;
   c->cused += n;
   CK(cudaEventRecord(c->data_ev, c->st), "data event");
   return BF_OK;
@@ -716,6 +738,7 @@ extern "C" bf_status bf_add_correspondences_batch(bf_ctx *c, int n_pairs, const 
     if (n == 0) continue;
     c->corr[pair_key(pair_ids[2 * k], pair_ids[2 * k + 1])].push_back(Seg{(int)(c->cused + offsets[k]), n});
   }
+  ++c->corr_ver;
   c->cused += total;
   CK(cudaEventRecord(c->data_ev, c->st), "data event");
   return BF_OK;
@@ -757,6 +780,7 @@ extern "C" bf_status bf_remove_pair(bf_ctx *c, int frame_i, int frame_j) {
   auto it = c->corr.find(pair_key(frame_i, frame_j));
   if (it == c->corr.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_remove_pair: no such pair");
   c->corr.erase(it);
+  ++c->corr_ver;
   return BF_OK;
 }
 
@@ -766,6 +790,7 @@ extern "C" bf_status bf_clear_correspondences(bf_ctx *c) {
   c->busy_cv.wait(lk, [&] { return c->in_flight == 0; });  // batches in flight still read the pool
   c->corr.clear();
   c->cused = 0;
+  ++c->corr_ver;
   return BF_OK;
 }
 
@@ -791,19 +816,46 @@ struct HostTables {
   long long n_corr = 0;
   std::vector<int> prob_npairs, prob_ndense;
   std::vector<long long> prob_ncorr;
+  uint64_t gen = 0;                              // build generation (0: assembled by hand)
+  std::shared_ptr<const std::vector<int>> ints;  // the device tables, packed (see pack_ints)
+};
+
+// The last tables an executor built, with what they were built from.
+struct TableCache {
+  std::vector<std::vector<int>> ids;  // frame ids per problem
+  uint64_t corr_ver = 0, frames_ver = 0;
+  int tile_px = 0, dense_on = 0;
+  bool staged = false;
+  double max_angle_deg = 0;
+  HostTables T;
 };
 
 constexpr int STAGED_PAIRS_PER_ITEM = 6;
 
 // Build the flattened tables of a set of problems.  force_dense: every pair gets both dense
 // directions (debug), else the Sec. 4.3 angle test on the initial poses selects E.
-bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm, HostTables &T) {
+// Sec. 4.3's dense set E: the optical axes (third rotation columns) of the pair's initial poses
+// within the maximum angle, tested in FP64.
+static inline bool axes_within(const Pose12 &Pa, const Pose12 &Pb, double cos_max) {
+  const double dot = (Pa[2] * Pb[2] + Pa[5] * Pb[5]) + Pa[8] * Pb[8];
+  return dot > cos_max;
+}
+
+// dense work decomposition: explicit tile_px -> tiles of that many pixels; automatic -> the
+// target frame staged in shared memory when it fits (one partial per directed pair), else
+// 4800-pixel tiles
+static void dense_decomposition(const bf_ctx *c, const bf_solve_params &prm, bool &staged, int &tile_px) {
   const int HW = c->cfg.width * c->cfg.height;
-  // dense work decomposition: explicit tile_px -> tiles of that many pixels; automatic -> the
-  // target frame staged in shared memory when it fits (one partial per directed pair), else
-  // 4800-pixel tiles
-  const bool staged = prm.tile_px == 0 && dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage);
-  int tile_px = prm.tile_px > 0 ? prm.tile_px : (staged ? HW : std::min(HW, 4800));
+  staged = prm.tile_px == 0 && dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage);
+  tile_px = prm.tile_px > 0 ? prm.tile_px : (staged ? HW : std::min(HW, 4800));
+}
+
+bf_status build_tables_fresh(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm,
+                             HostTables &T) {
+  const int HW = c->cfg.width * c->cfg.height;
+  bool staged;
+  int tile_px;
+  dense_decomposition(c, prm, staged, tile_px);
   T.n_prob = (int)probs.size();
   std::vector<std::vector<std::pair<int, int>>> var_inc;  // per var: (pair, side)
   const double cos_max = std::cos(prm.max_angle_deg * M_PI / 180.0);
@@ -877,12 +929,7 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
       }
       T.pair_seg1.push_back(T.n_segs);
       // dense set E: optical axes within max_angle at the initial poses (FP64)
-      bool dense = false;
-      if (prm.dense_on) {
-        const Pose12 &Pa = P.init[a], &Pb = P.init[b];
-        const double dot = (Pa[2] * Pb[2] + Pa[5] * Pb[5]) + Pa[8] * Pb[8];
-        dense = dot > cos_max;
-      }
+      const bool dense = prm.dense_on && axes_within(P.init[a], P.init[b], cos_max);
       for (int dir = 0; dir < 2; ++dir) {
         if (!dense) {
           T.pair_dp.push_back(-1);
@@ -1172,6 +1219,69 @@ std::vector<int> pack_ints(const HostTables &T) {
   return v;
 }
 
+// Tables of a set of problems.  The executor keeps the last tables it built: a solve over the
+// same problems with the same pairs, frame slots, dense decomposition and dense set (the angle
+// test at the new initial poses gives the same E) takes a copy of them with the new initial
+// poses instead of rebuilding them (the steady state of repeated global solves).
+bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm, HostTables &T) {
+  bool staged;
+  int tile_px;
+  dense_decomposition(c, prm, staged, tile_px);
+  const double cos_max = std::cos(prm.max_angle_deg * M_PI / 180.0);
+  Exec &ex = *c->ex;
+  if (ex.tcache) {
+    const TableCache &tc = *ex.tcache;
+    bool hit = tc.corr_ver == c->corr_ver && tc.frames_ver == c->frames_ver && tc.tile_px == tile_px &&
+               tc.staged == staged && tc.dense_on == prm.dense_on && tc.max_angle_deg == prm.max_angle_deg &&
+               tc.ids.size() == probs.size();
+    for (size_t q = 0; hit && q < probs.size(); ++q) hit = tc.ids[q] == probs[q].ids;
+    const HostTables &C = tc.T;
+    for (int q = 0; hit && q < C.n_prob; ++q) {
+      const int F0 = C.prob_frame0[q];
+      const Problem &P = probs[q];
+      for (int p = C.prob_pair0[q]; hit && p < C.prob_pair1[q]; ++p) {
+        const bool dense =
+            prm.dense_on && axes_within(P.init[C.pair_a[p] - F0], P.init[C.pair_b[p] - F0], cos_max);
+        hit = dense == (C.pair_dp[2 * p] >= 0);
+      }
+    }
+    if (hit) {
+      T = C;
+      T.pose.clear();
+      for (const Problem &P : probs)
+        for (const Pose12 &x : P.init) T.pose.insert(T.pose.end(), x.begin(), x.end());
+      return BF_OK;
+    }
+  }
+  ex.tcache.reset();
+  T = HostTables{};
+  bf_status s = build_tables_fresh(c, probs, prm, T);
+  if (s) return s;
+  T.ints = std::make_shared<const std::vector<int>>(pack_ints(T));
+  T.gen = ++c->tables_gen;
+  auto tc = std::make_shared<TableCache>();
+  tc->ids.reserve(probs.size());
+  for (const Problem &P : probs) tc->ids.push_back(P.ids);
+  tc->corr_ver = c->corr_ver;
+  tc->frames_ver = c->frames_ver;
+  tc->tile_px = tile_px;
+  tc->staged = staged;
+  tc->dense_on = prm.dense_on;
+  tc->max_angle_deg = prm.max_angle_deg;
+  tc->T = T;
+  ex.tcache = std::move(tc);
+  return BF_OK;
+}
+
+// Marks the end of the copies queued so far into or out of the executor's pinned buffer.
+bf_status pin_used(bf_ctx *c) {
+  Exec &e = *c->ex;
+  if (!e.pin_ev) CK(cudaEventCreateWithFlags(&e.pin_ev, cudaEventDisableTiming), "pinned staging event");
+  CK(cudaEventRecord(e.pin_ev, e.st), "pinned staging event");
+  e.pin_ev_live = true;
+  return BF_OK;
+}
+
 bf_status ensure_pinned(bf_ctx *c, size_t n) {
   if (n <= c->ex->pin_bytes) return BF_OK;
   CK(cudaStreamSynchronize(c->ex->st), "pinned staging");
@@ -1186,7 +1296,9 @@ bf_status ensure_pinned(bf_ctx *c, size_t n) {
 
 bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, bool want_assoc, DevSolve &D,
                   int variant = BF_PCG_AUTO, bool matfree = false, bool persistent = false) {
-  const std::vector<int> ints = pack_ints(T);
+  std::shared_ptr<const std::vector<int>> ints_p = T.ints;
+  if (!ints_p) ints_p = std::make_shared<const std::vector<int>>(pack_ints(T));
+  const std::vector<int> &ints = *ints_p;
   const int HW = c->cfg.width * c->cfg.height;
   const size_t need =
       layout(T, n_gn, ints.size(), nullptr, nullptr, acc_size, HW, want_assoc, variant, matfree, persistent) + 256;
@@ -1199,26 +1311,30 @@ bf_status prepare(bf_ctx *c, const HostTables &T, int n_gn, size_t acc_size, boo
     // the new allocation may come back at the old address with other contents: forget what the
     // old workspace held so the tables are uploaded again
     c->ex->last_ws = nullptr;
-    c->ex->last_ints.clear();
+    c->ex->ws_gen = 0;
     bf_status s = dalloc(c, (void **)&c->ex->ws, nb, "solve workspace");
     if (s) return s;
     c->ex->ws_bytes = nb;
   }
   layout(T, n_gn, ints.size(), c->ex->ws, &D, acc_size, HW, want_assoc, variant, matfree, persistent);
-  const bool same_tables = c->ex->last_ws == (const void *)c->ex->ws && c->ex->last_ints == ints;
+  const bool same_tables = c->ex->last_ws == (const void *)c->ex->ws && T.gen != 0 && c->ex->ws_gen == T.gen;
   if (!ints.empty() && !same_tables) {
     CK(cudaMemcpyAsync((void *)D.t.frame_slot, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, c->ex->st),
        "upload tables");
     CK(cudaStreamSynchronize(c->ex->st), "upload tables");
-    c->ex->last_ints = ints;
+    c->ex->ws_gen = T.gen;
     c->ex->last_ws = c->ex->ws;
   }
   bf_status s = ensure_pinned(c, T.pose.size() * sizeof(double));
   if (s) return s;
-  CK(cudaStreamSynchronize(c->ex->st), "pinned staging");  // the staging buffer may still feed a copy
+  // the pinned buffer may still feed or receive the previous solve's copies: wait for those
+  // alone, not for the kernels queued since (frame preprocessing runs on while the host prepares)
+  if (c->ex->pin_ev_live) CK(cudaEventSynchronize(c->ex->pin_ev), "pinned staging");
   std::memcpy(c->ex->pin, T.pose.data(), T.pose.size() * sizeof(double));
   CK(cudaMemcpyAsync(D.pose, c->ex->pin, T.pose.size() * sizeof(double), cudaMemcpyHostToDevice, c->ex->st),
      "upload poses");
+  s = pin_used(c);
+  if (s) return s;
   if (T.n_prob) CK(cudaMemsetAsync(D.pflags, 0, T.n_prob * sizeof(int), c->ex->st), "pflags");
   CK(cudaMemsetAsync(D.derr, 0, sizeof(int), c->ex->st), "dense status");
   return BF_OK;
@@ -1407,8 +1523,7 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
 // on (table contents, parameters, device buffers) is unchanged.  The tables and initial poses
 // have already been uploaded into the workspace by prepare(), which the graph reads.
 bf_status run_gn_graph(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, DevSolve &D, bool mixed) {
-  // key = parameters, sizes and device buffers, plus the tables (compared through last_ints,
-  // which prepare() keeps equal to what the workspace holds)
+  // key = parameters, sizes and device buffers, plus the tables (through their generation)
   std::vector<unsigned char> key(sizeof(prm) + 8 * sizeof(int) + 9 * sizeof(void *));
   unsigned char *kp = key.data();
   std::memcpy(kp, &prm, sizeof(prm));
@@ -1418,7 +1533,7 @@ bf_status run_gn_graph(bf_ctx *c, const HostTables &T, const bf_solve_params &pr
   kp += sizeof(dims);
   const void *ptrs[9] = {c->ex->ws, c->A, c->B, c->cP, c->cQ, c->kx, c->ky, (void *)c->ex->st, (void *)c->ex->ws_bytes};
   std::memcpy(kp, ptrs, sizeof(ptrs));
-  const bool tables_same = c->ex->last_ws == (const void *)c->ex->ws && c->ex->last_ints == pack_ints(T);
+  const bool tables_same = T.gen != 0 && c->ex->graph_gen == T.gen;
   if (c->ex->gexec && tables_same && c->ex->gkey == key) {
     CK(cudaGraphLaunch(c->ex->gexec, c->ex->st), "graph launch");
     c->launches += c->ex->gkernels;
@@ -1445,6 +1560,7 @@ bf_status run_gn_graph(bf_ctx *c, const HostTables &T, const bf_solve_params &pr
   if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
   c->ex->gexec = ge;
   c->ex->gkey = key;
+  c->ex->graph_gen = T.gen;
   c->ex->gkernels = (int)(c->launches - before);
   CK(cudaGraphLaunch(c->ex->gexec, c->ex->st), "graph launch");
   return BF_OK;
@@ -1605,7 +1721,7 @@ bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_s
   CK(cudaMemcpyAsync(pb + J.o_ce + 4, D.derr, sizeof(int), cudaMemcpyDeviceToHost, st), "dense status");
   if (D.persistent)
     CK(cudaMemcpyAsync(pb + J.o_ce + 8, (char *)D.bq + 8, sizeof(int), cudaMemcpyDeviceToHost, st), "batch status");
-  return BF_OK;
+  return pin_used(c);
 }
 
 // Phase 3 (after the executor's stream is synchronised, context lock held): unpack the results.
@@ -1721,6 +1837,7 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
       const bf_solve_stats &S = sub_st[q];
       if (S.r_max > prm.prune_rmax && round < prm.prune_rounds && S.r_max_pair[0] >= 0) {
         c->corr.erase(pair_key(S.r_max_pair[0], S.r_max_pair[1]));
+        ++c->corr_ver;
         pruned[k].push_back({S.r_max_pair[0], S.r_max_pair[1]});
         next.push_back(k);
       }
