@@ -112,18 +112,51 @@ def workload():
 
 # ------------------------------------------------------------------------------- clocks
 class Clocks:
-    """nvidia-smi sampler running during the timed region."""
+    """SM clock and clock-event-reason sampler running during the timed region.
 
+    NVML (read-only queries) every 5 ms from a thread, so that even a timed region of a few tens of
+    milliseconds gets samples; nvidia-smi at its 200 ms minimum period where NVML is missing."""
+
+    REASONS = (("hw_slowdown", "HwSlowdown", 0x8), ("hw_thermal_slowdown", "HwThermalSlowdown", 0x40),
+               ("sw_thermal_slowdown", "SwThermalSlowdown", 0x20), ("sw_power_cap", "SwPowerCap", 0x4))
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_s=0.005):
         self.index = index
+        self.period = period_s
+        self.rows = []
+        self.thread = None
+        self.stop_ev = threading.Event()
         self.proc = None
         self.file = None
 
+    def _nvml_loop(self, nv, h, bits):
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+        while not self.stop_ev.is_set():
+            try:
+                sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
+                r = int(get_reasons(h))
+                self.rows.append((sm, mx, [name for name, bit in bits if r & bit]))
+            except Exception:
+                pass
+            self.stop_ev.wait(self.period)
+
     def start(self):
+        try:
+            import pynvml as nv
+            nv.nvmlInit()
+            h = nv.nvmlDeviceGetHandleByIndex(self.index)
+            bits = [(name, getattr(nv, "nvmlClocksEventReason" + cname, None) or
+                     getattr(nv, "nvmlClocksThrottleReason" + cname, bit)) for name, cname, bit in self.REASONS]
+            self.thread = threading.Thread(target=self._nvml_loop, args=(nv, h, bits), daemon=True)
+            self.thread.start()
+            return
+        except Exception:
+            self.thread = None
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
@@ -133,30 +166,36 @@ class Clocks:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
+        if self.thread is not None:
+            self.stop_ev.set()
+            self.thread.join(timeout=5)
+            rows, source = self.rows, "nvml, 5 ms"
+        elif self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.file.flush()
+            rows = []
+            with open(self.file.name) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 8 and parts[0].replace(".", "").isdigit():
+                        rows.append((float(parts[0]), float(parts[1]) if parts[1].replace(".", "").isdigit() else 0.0,
+                                     [name for (name, _, _), v in zip(self.REASONS, parts[4:8]) if v.lower() == "active"]))
+            os.unlink(self.file.name)
+            source = "nvidia-smi, 200 ms"
+        else:
             return None
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.file.flush()
-        rows = []
-        with open(self.file.name) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 8:
-                    rows.append(parts)
-        os.unlink(self.file.name)
         if not rows:
             return None
-        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower() == "active"})
-        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
-        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        sm = [r[0] for r in rows]
+        mx = max(r[1] for r in rows)
+        load = [x for x in sm if mx and x > 0.5 * mx] or sm
+        reasons = sorted({n for r in rows for n in r[2]})
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "source": source}
 
 
 # ------------------------------------------------------------------------- CPU baseline

@@ -865,13 +865,29 @@ bf_status build_tables_fresh(bf_ctx *c, const std::vector<Problem> &probs, const
     const int F0 = T.n_frames;
     T.prob_frame0.push_back(F0);
     T.prob_var0.push_back(T.n_vars);
-    std::unordered_map<int, int> loc;
-    loc.reserve(n * 2);
+    // frame id -> local index: a direct table when the ids are small, else a hash map
+    int id_max = -1;
+    bool id_neg = false;
+    for (int id : P.ids) {
+      id_max = std::max(id_max, id);
+      id_neg |= id < 0;
+    }
+    const bool direct = !id_neg && (long long)id_max <= 8LL * n + 4096;
+    std::vector<int> dloc(direct ? id_max + 1 : 0, -1);
+    std::unordered_map<int, int> hloc;
+    if (!direct) hloc.reserve(n * 2);
+    auto local_of = [&](int id) -> int {
+      if (direct) return id >= 0 && id <= id_max ? dloc[id] : -1;
+      auto it = hloc.find(id);
+      return it == hloc.end() ? -1 : it->second;
+    };
     for (int k = 0; k < n; ++k) {
       auto it = c->frames.find(P.ids[k]);
       if (it == c->frames.end()) return fail(c, BF_ERR_NOT_FOUND, "solve: unknown frame id " + std::to_string(P.ids[k]));
-      if (!loc.emplace(P.ids[k], k).second)
+      if (local_of(P.ids[k]) >= 0)
         return fail(c, BF_ERR_INVALID_ARG, "solve: duplicate frame id " + std::to_string(P.ids[k]));
+      if (direct) dloc[P.ids[k]] = k;
+      else hloc.emplace(P.ids[k], k);
       T.frame_slot.push_back(it->second.slot);
       if (k == 0) {
         T.frame_var.push_back(-1);
@@ -885,34 +901,42 @@ bf_status build_tables_fresh(bf_ctx *c, const std::vector<Problem> &probs, const
     }
     T.n_frames += n;
     T.prob_var1.push_back(T.n_vars);
-    // pairs with correspondences among the problem's frames
-    std::vector<std::array<int, 2>> plist;
+    // pairs with correspondences among the problem's frames, in (a, b) order, each with its
+    // segment list (one map lookup per pair)
+    struct PEnt {
+      int a, b;
+      const std::vector<Seg> *segs;
+    };
+    std::vector<PEnt> plist;
     if ((long long)n * (n - 1) / 2 <= (long long)c->corr.size()) {
       for (int a = 0; a < n; ++a)
-        for (int b = a + 1; b < n; ++b)
-          if (c->corr.count(pair_key(P.ids[a], P.ids[b]))) plist.push_back({a, b});
+        for (int b = a + 1; b < n; ++b) {
+          auto it = c->corr.find(pair_key(P.ids[a], P.ids[b]));
+          if (it != c->corr.end()) plist.push_back({a, b, &it->second});
+        }
     } else {
+      plist.reserve(c->corr.size());
       for (auto &kv : c->corr) {
-        const int lo = (int)(kv.first >> 32), hi = (int)(kv.first & 0xffffffffu);
-        auto ia = loc.find(lo), ib = loc.find(hi);
-        if (ia == loc.end() || ib == loc.end()) continue;
-        plist.push_back({std::min(ia->second, ib->second), std::max(ia->second, ib->second)});
+        const int la = local_of((int)(kv.first >> 32)), lb = local_of((int)(kv.first & 0xffffffffu));
+        if (la < 0 || lb < 0) continue;
+        plist.push_back({std::min(la, lb), std::max(la, lb), &kv.second});
       }
-      std::sort(plist.begin(), plist.end());
+      std::sort(plist.begin(), plist.end(),
+                [](const PEnt &x, const PEnt &y) { return x.a != y.a ? x.a < y.a : x.b < y.b; });
     }
     T.prob_pair0.push_back(T.n_pairs);
     T.prob_tile0.push_back(T.n_tiles);
     T.prob_seg0.push_back(T.n_segs);
     int ndense = 0;
     long long ncorr = 0;
-    for (auto &ab : plist) {
-      const int a = ab[0], b = ab[1];
+    for (const PEnt &ab : plist) {
+      const int a = ab.a, b = ab.b;
       const int p = T.n_pairs++;
       T.pair_a.push_back(F0 + a);
       T.pair_b.push_back(F0 + b);
       T.pair_ida.push_back(P.ids[a]);
       T.pair_idb.push_back(P.ids[b]);
-      const auto &segs = c->corr[pair_key(P.ids[a], P.ids[b])];
+      const std::vector<Seg> &segs = *ab.segs;
       long long pair_n = 0;
       for (const Seg &sg : segs) pair_n += sg.cnt;
       if (pair_n < 3)  // fewer than 3 matches determine no rigid transform (Sec. 4.1.1)
@@ -966,10 +990,11 @@ bf_status build_tables_fresh(bf_ctx *c, const std::vector<Problem> &probs, const
   if (staged && T.n_dp > 0) {
     // group the directed pairs by target frame, at most STAGED_PAIRS_PER_ITEM per work item (one per
     // warp quad: many small items keep the one-CTA-per-SM grid balanced)
-    std::vector<int> order(T.n_dp);
-    for (int d = 0; d < T.n_dp; ++d) order[d] = d;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return T.dp_dst_host[x] < T.dp_dst_host[y]; });
+    // (a stable counting sort by target frame)
+    std::vector<int> order(T.n_dp), start(T.n_frames + 1, 0);
+    for (int d = 0; d < T.n_dp; ++d) ++start[T.dp_dst_host[d] + 1];
+    for (int f = 0; f < T.n_frames; ++f) start[f + 1] += start[f];
+    for (int d = 0; d < T.n_dp; ++d) order[start[T.dp_dst_host[d]]++] = d;
     T.wi_off.push_back(0);
     int run = 0;
     for (int k = 0; k < T.n_dp; ++k) {
