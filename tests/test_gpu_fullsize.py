@@ -5,8 +5,11 @@
   Gauss-Newton step (tests/golden/global300_oracle.json);
 * the whole 256-chunk 320x240 batch (FP32 arithmetic, graph; launch sequence and persistent
   launch), sampled on a 3-frame and an 11-frame chunk (tests/golden/chunks256_oracle.json).
+* the 2000-keyframe 160x120 solve (BF16 frame storage, tiled dense kernel, cluster PCG with its
+  blocks in global memory), first Gauss-Newton step against the oracle's on the same BF16-rounded
+  planes (tests/golden/global2000_oracle.json).
 
-The oracle needs one to two minutes for these, so its results are stored, written by the
+The oracle needs minutes (the 2000-keyframe step about forty) for these, so its results are stored, written by the
 make_*_oracle.py scripts beside them from the oracle and the seeded scene generator alone.
 Tolerances are the spec ones.
 """
