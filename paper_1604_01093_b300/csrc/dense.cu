@@ -150,9 +150,8 @@ __global__ void __launch_bounds__(STG_BS, 1)
     const int d = t.sw_dp[k];
     const long long so = (long long)t.frame_slot[t.dp_src[d]] * HW;
     const PairXf X = load_xf(pairM + (t.dp_pair[d] * 2 + t.dp_dir[d]) * 12);
-    float acc[NPD];
-#pragma unroll
-    for (int q = 0; q < NPD; ++q) acc[q] = 0.f;
+    DAcc acc;
+    acc.zero();
     if (F32) {
       const float4 *__restrict__ As = fs.A + so;
       const float4 *__restrict__ Bs = fs.B + so;
@@ -180,7 +179,9 @@ __global__ void __launch_bounds__(STG_BS, 1)
         eval_pixel<MODE>(unpack16_dn<KIND>(r), w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
       }
     }
-    quad_reduce_store<NPD, Part>(acc, red[quad], quad, part + (long long)d * NPD);
+    float sums[NPD];
+    acc.to_array(sums);
+    quad_reduce_store<NPD, Part>(sums, red[quad], quad, part + (long long)d * NPD);
   }
 }
 

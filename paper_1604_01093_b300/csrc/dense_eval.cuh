@@ -24,19 +24,63 @@ __device__ __forceinline__ V3 cross3(V3 a, V3 b) {
   return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
 }
 
+// Per-thread dense sums.  With u = (v, c) the six Jacobian components of a row, the 21 upper-
+// triangle products w u_i u_j (the VV, VC and CC sums) are kept in register pairs so that one
+// packed FP32 fused multiply-add (__ffma2_rn: per component exactly __fmaf_rn) updates two of
+// them: pair (i, j) with (i + 1, j + 1) for rows 0-1, 2-3 and 4-5, and the three left over
+// ((0,5), (2,5), (4,5)) alone.  Every sum sees the same operations in the same order as with one
+// scalar accumulator each: w u_i first, then fma(w u_i, u_j, sum).
+struct DAcc {
+  float2 p[9];  // (0,0)(1,1) (0,1)(1,2) (0,2)(1,3) (0,3)(1,4) (0,4)(1,5) (2,2)(3,3) (2,3)(3,4) (2,4)(3,5) (4,4)(5,5)
+  float s05, s25, s45;
+  float2 g[3];  // r w u: (0,1) (2,3) (4,5)
+  float e0, e1, cnt;
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) p[k] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = make_float2(0.f, 0.f);
+    s05 = s25 = s45 = e0 = e1 = cnt = 0.f;
+  }
+  // the NPD layout (D_VV, D_VC, D_CC, D_GV, D_GC, D_E0, D_E1, D_CNT)
+  __device__ __forceinline__ void to_array(float (&a)[NPD]) const {
+    a[D_VV + 0] = p[0].x; a[D_VV + 1] = p[1].x; a[D_VV + 2] = p[2].x;
+    a[D_VV + 3] = p[0].y; a[D_VV + 4] = p[1].y; a[D_VV + 5] = p[5].x;
+    a[D_VC + 0] = p[3].x; a[D_VC + 1] = p[4].x; a[D_VC + 2] = s05;
+    a[D_VC + 3] = p[2].y; a[D_VC + 4] = p[3].y; a[D_VC + 5] = p[4].y;
+    a[D_VC + 6] = p[6].x; a[D_VC + 7] = p[7].x; a[D_VC + 8] = s25;
+    a[D_CC + 0] = p[5].y; a[D_CC + 1] = p[6].y; a[D_CC + 2] = p[7].y;
+    a[D_CC + 3] = p[8].x; a[D_CC + 4] = s45; a[D_CC + 5] = p[8].y;
+    a[D_GV + 0] = g[0].x; a[D_GV + 1] = g[0].y; a[D_GV + 2] = g[1].x;
+    a[D_GC + 0] = g[1].y; a[D_GC + 1] = g[2].x; a[D_GC + 2] = g[2].y;
+    a[D_E0] = e0;
+    a[D_E1] = e1;
+    a[D_CNT] = cnt;
+  }
+};
+
 // Accumulate one dense residual row (weight w, residual r, Jacobian [v x t - c, v, c, -v]).
-__device__ __forceinline__ void accum_vc(float (&acc)[NPD], float w, float r, V3 v, V3 c) {
-  const float wv0 = w * v.x, wv1 = w * v.y, wv2 = w * v.z;
-  const float wc0 = w * c.x, wc1 = w * c.y, wc2 = w * c.z;
-  acc[D_VV + 0] += wv0 * v.x; acc[D_VV + 1] += wv0 * v.y; acc[D_VV + 2] += wv0 * v.z;
-  acc[D_VV + 3] += wv1 * v.y; acc[D_VV + 4] += wv1 * v.z; acc[D_VV + 5] += wv2 * v.z;
-  acc[D_VC + 0] += wv0 * c.x; acc[D_VC + 1] += wv0 * c.y; acc[D_VC + 2] += wv0 * c.z;
-  acc[D_VC + 3] += wv1 * c.x; acc[D_VC + 4] += wv1 * c.y; acc[D_VC + 5] += wv1 * c.z;
-  acc[D_VC + 6] += wv2 * c.x; acc[D_VC + 7] += wv2 * c.y; acc[D_VC + 8] += wv2 * c.z;
-  acc[D_CC + 0] += wc0 * c.x; acc[D_CC + 1] += wc0 * c.y; acc[D_CC + 2] += wc0 * c.z;
-  acc[D_CC + 3] += wc1 * c.y; acc[D_CC + 4] += wc1 * c.z; acc[D_CC + 5] += wc2 * c.z;
-  acc[D_GV + 0] += r * wv0; acc[D_GV + 1] += r * wv1; acc[D_GV + 2] += r * wv2;
-  acc[D_GC + 0] += r * wc0; acc[D_GC + 1] += r * wc1; acc[D_GC + 2] += r * wc2;
+__device__ __forceinline__ void accum_vc(DAcc &A, float w, float r, V3 v, V3 c) {
+  const float2 U01 = make_float2(v.x, v.y), U12 = make_float2(v.y, v.z), U23 = make_float2(v.z, c.x);
+  const float2 U34 = make_float2(c.x, c.y), U45 = make_float2(c.y, c.z);
+  const float2 W2 = make_float2(w, w);
+  const float2 WU01 = __fmul2_rn(W2, U01), WU23 = __fmul2_rn(W2, U23), WU45 = __fmul2_rn(W2, U45);
+  A.p[0] = __ffma2_rn(WU01, U01, A.p[0]);
+  A.p[1] = __ffma2_rn(WU01, U12, A.p[1]);
+  A.p[2] = __ffma2_rn(WU01, U23, A.p[2]);
+  A.p[3] = __ffma2_rn(WU01, U34, A.p[3]);
+  A.p[4] = __ffma2_rn(WU01, U45, A.p[4]);
+  A.p[5] = __ffma2_rn(WU23, U23, A.p[5]);
+  A.p[6] = __ffma2_rn(WU23, U34, A.p[6]);
+  A.p[7] = __ffma2_rn(WU23, U45, A.p[7]);
+  A.p[8] = __ffma2_rn(WU45, U45, A.p[8]);
+  A.s05 = __fmaf_rn(WU01.x, c.z, A.s05);
+  A.s25 = __fmaf_rn(WU23.x, c.z, A.s25);
+  A.s45 = __fmaf_rn(WU45.x, c.z, A.s45);
+  const float2 R2 = make_float2(r, r);
+  A.g[0] = __ffma2_rn(R2, WU01, A.g[0]);
+  A.g[1] = __ffma2_rn(R2, WU23, A.g[1]);
+  A.g[2] = __ffma2_rn(R2, WU45, A.g[2]);
 }
 
 // Fixed-order CTA reduction of N values; thread k < N writes out[k].
@@ -83,7 +127,7 @@ __device__ __forceinline__ PairXf load_xf(const float *M) {
 template <int MODE, typename LA, typename LB, typename LI>
 __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const PairXf &X, const Intr &in,
                                           const float *kx, const float *ky, const Gates &g, LA loadA, LB loadB,
-                                          LI srcI, float w_geo, float w_photo, float (&acc)[NPD]) {
+                                          LI srcI, float w_geo, float w_photo, DAcc &acc) {
   if (!(a.x > 0.f && normal_valid(a))) return -1;
   const int W = in.W, H = in.H;
   const float z = a.x;
@@ -134,9 +178,9 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
   const float gxI = w00 * c00.y + w01 * c01.y + w10 * c10.y + w11 * c11.y;
   const float gyI = w00 * c00.z + w01 * c01.z + w10 * c10.z + w11 * c11.z;
   const float r_p = srcI() - Ij;
-  acc[D_E0] += r_g * r_g;
-  acc[D_E1] += r_p * r_p;
-  acc[D_CNT] += 1.f;
+  acc.e0 = __fmaf_rn(r_g, r_g, acc.e0);
+  acc.e1 = __fmaf_rn(r_p, r_p, acc.e1);
+  acc.cnt += 1.f;
   if (MODE == MODE_ACCUM) {
     // geometric: v = m, c = m x q
     const V3 m{m0, m1, m2}, q{qx, qy, qz};
@@ -189,9 +233,8 @@ __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const Fram
   float *kx = ktab, *ky = ktab + W;
   for (int k = threadIdx.x; k < W + H; k += DENSE_BS) ktab[k] = k < W ? fs.kx[k] : fs.ky[k - W];
   __syncthreads();
-  float acc[NPD];
-#pragma unroll
-  for (int k = 0; k < NPD; ++k) acc[k] = 0.f;
+  DAcc acc;
+  acc.zero();
   if (KIND == BF_STORE_FP32) {
     const float4 *__restrict__ As = fs.A + (long long)ss * HW;
     const float4 *__restrict__ Bs = fs.B + (long long)ss * HW;
@@ -225,7 +268,11 @@ __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const Fram
       if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
     }
   }
-  if (MODE != MODE_ASSOC) cta_reduce_store<DENSE_BS, NPD, Part>(acc, part + (long long)tile * NPD, red);
+  if (MODE != MODE_ASSOC) {
+    float sums[NPD];
+    acc.to_array(sums);
+    cta_reduce_store<DENSE_BS, NPD, Part>(sums, part + (long long)tile * NPD, red);
+  }
 }
 
 
