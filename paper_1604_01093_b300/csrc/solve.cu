@@ -437,22 +437,43 @@ constexpr int CL_BS = 512;
 constexpr int CL_WARPS = CL_BS / 32;
 constexpr int CL_G = 16;  // lanes per frame in the matvec
 
-// Sum of the CL per-CTA partials (slot k of each CTA's part array), read lane-parallel from the
-// cluster's shared memory and combined by a butterfly: identical in every lane of every CTA.
+// Type of the cross-CTA sums: float-float in mixed precision (about 48 bits on the FP32 pipe,
+// see FF), FP32 in the plain path.
 template <typename Acc>
-__device__ __forceinline__ Acc cluster_total(cgx::cluster_group &cluster, Acc *part, int k, int CL) {
+struct ClusterRed {
+  using T = float;
+};
+template <>
+struct ClusterRed<double> {
+  using T = FF;
+};
+__device__ __forceinline__ float red_of(float x, float) { return x; }
+__device__ __forceinline__ FF red_of(float x, FF) { return ff_from(x); }
+__device__ __forceinline__ float red_add(float a, float b) { return a + b; }
+__device__ __forceinline__ FF red_add(FF a, FF b) { return ff_add(a, b); }
+__device__ __forceinline__ float red_shfl(float a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+__device__ __forceinline__ FF red_shfl(FF a, int o) { return ff_shfl_xor(a, o); }
+__device__ __forceinline__ bool red_zero(float a) { return a == 0.f; }
+__device__ __forceinline__ bool red_zero(FF a) { return a.hi == 0.f; }
+
+// Sum of the CL <= 16 per-CTA partials (slot k of each CTA's part array), read lane-parallel from
+// the cluster's shared memory and combined by a butterfly over lanes 0-15: lane 0 holds the total.
+template <typename R>
+__device__ __forceinline__ R cluster_total(cgx::cluster_group &cluster, R *part, int k, int CL) {
   const int lane = threadIdx.x & 31;
-  Acc s = lane < CL ? cluster.map_shared_rank(part, lane)[k] : (Acc)0;
+  R s = red_of(0.f, R{});
+  if (lane < CL) s = cluster.map_shared_rank(part, lane)[k];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  for (int o = 8; o > 0; o >>= 1) s = red_add(s, red_shfl(s, o));
   return s;
 }
 
 // Fixed-order CTA sum of one FP32 value per warp (lane 0 holds it) into part[k]: a butterfly
-// over the CL_WARPS values in warp 0 (FP32), then one conversion; FP64 starts at the sum over
-// the cluster's CTAs.
-template <typename Acc>
-__device__ __forceinline__ void cluster_partial(float v, float *wsum, Acc *part, int k) {
+// over the CL_WARPS = 16 values in warp 0 (FP32); the wider type starts at the sum over the
+// cluster's CTAs.
+template <typename R>
+__device__ __forceinline__ void cluster_partial(float v, float *wsum, R *part, int k) {
+  static_assert(CL_WARPS == 16, "the butterfly below sums 16 warp values");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) wsum[warp] = v;
@@ -460,8 +481,8 @@ __device__ __forceinline__ void cluster_partial(float v, float *wsum, Acc *part,
   if (warp == 0) {
     float s = lane < CL_WARPS ? wsum[lane] : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) part[k] = (Acc)s;
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) part[k] = red_of(s, R{});
   }
 }
 
@@ -530,7 +551,8 @@ __global__ void __launch_bounds__(CL_BS, 1)
   float *orr = ox + 6 * per;
   float *oq = orr + 6 * per;
   float *opn = oq + 6 * per;
-  Acc *part = (Acc *)(((uintptr_t)(opn + 6 * per) + 15) & ~(uintptr_t)15);
+  using R = typename ClusterRed<Acc>::T;
+  R *part = (R *)(((uintptr_t)(opn + 6 * per) + 15) & ~(uintptr_t)15);
   float *sD = (float *)(part + 2);
   float *sM = sD + 36 * per;
   float *sB = sM + 36 * per;
@@ -600,7 +622,7 @@ __global__ void __launch_bounds__(CL_BS, 1)
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) loc += __shfl_xor_sync(0xffffffffu, loc, o);
-  cluster_partial<Acc>(loc, wsum, part, 1);
+  cluster_partial<R>(loc, wsum, part, 1);
   cluster.sync();  // all CTAs running, owned z / p initialised, energy slices ready
   if (po.energy && rank == 0 && threadIdx.x < PAIREN) {
     Acc v = 0;
@@ -608,12 +630,12 @@ __global__ void __launch_bounds__(CL_BS, 1)
     po.energy[threadIdx.x] = (double)v;
   }
   __shared__ PcgScal S;
-  Acc rz = 0;  // meaningful in thread 0, which runs the scalar recurrences
+  R rz = red_of(0.f, R{});  // meaningful in thread 0, which runs the scalar recurrences
   if (warp == 0) {
-    const Acc tot = cluster_total(cluster, part, 1, CL);
+    const R tot = cluster_total(cluster, part, 1, CL);
     if (lane == 0) {
       rz = tot;
-      S.stop = rz == (Acc)0;
+      S.stop = red_zero(rz);
       S.fb = 0.f;
     }
   }
@@ -698,10 +720,10 @@ __global__ void __launch_bounds__(CL_BS, 1)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lpq += __shfl_xor_sync(0xffffffffu, lpq, o);
-    cluster_partial<Acc>(lpq, wsum, part, 0);
+    cluster_partial<R>(lpq, wsum, part, 0);
     cluster.sync();  // every CTA has finished reading the old z / p
     if (warp == 0) {
-      const Acc pq = cluster_total(cluster, part, 0, CL);
+      const R pq = cluster_total(cluster, part, 0, CL);
       if (lane == 0) flag |= pcg_alpha(rz, pq, S);
     }
     __syncthreads();
@@ -730,10 +752,10 @@ __global__ void __launch_bounds__(CL_BS, 1)
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) lrz += __shfl_xor_sync(0xffffffffu, lrz, o);
-    cluster_partial<Acc>(lrz, wsum, part, 1);
+    cluster_partial<R>(lrz, wsum, part, 1);
     cluster.sync();  // the new z / p are visible cluster-wide
     if (warp == 0) {
-      const Acc rz_new = cluster_total(cluster, part, 1, CL);
+      const R rz_new = cluster_total(cluster, part, 1, CL);
       if (lane == 0) pcg_beta(rz, rz_new, S);
     }
     __syncthreads();

@@ -462,6 +462,45 @@ struct PcgScal {
   int stop;
 };
 
+// Float-float sums for the cross-CTA reductions of the mixed-precision PCG.  B300 issues FP64 at
+// 1/64 of the FP32 rate, so every FP64 step of a reduction chain (convert, add, compare) holds
+// the chain for at least 64 cycles; an unevaluated sum hi + lo of two FP32 values, added with
+// Knuth's TwoSum and renormalised (Dekker's FastTwoSum), keeps about 48 significant bits on the
+// FP32 pipe.  ff_add is commutative (the low parts are added to each other first), so a butterfly
+// leaves every lane with the same value.
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ FF ff_from(float x) { return FF{x, 0.f}; }
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));  // a.hi + b.hi - s, exactly
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, e);
+  return FF{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int o) {
+  return FF{__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+// FP32 rounding of hi + lo (hi alone after renormalisation, but for the halfway cases)
+__device__ __forceinline__ float ff_f32(FF a) { return __fadd_rn(a.hi, a.lo); }
+
+// The PCG scalars from float-float sums (same decisions as the FP64 forms below).
+__device__ __forceinline__ int pcg_alpha(FF rz, FF pq, PcgScal &S) {
+  if (!(pq.hi > 0.f)) {
+    S.stop = 1;
+    return 4;  // BF_FLAG_PCG_BREAKDOWN
+  }
+  S.fa = __fdiv_rn(ff_f32(rz), ff_f32(pq));
+  return 0;
+}
+__device__ __forceinline__ void pcg_beta(FF &rz, FF rz_new, PcgScal &S) {
+  S.fb = __fdiv_rn(ff_f32(rz_new), ff_f32(rz));
+  rz = rz_new;
+  S.stop = rz.hi == 0.f;
+}
+
 // z_v = Minv_v r_v for the row u = 6 v + c
 __device__ __forceinline__ float precond_row(const float *__restrict__ Minv, const float *__restrict__ r, int v,
                                              int c) {
