@@ -514,32 +514,31 @@ __global__ void __launch_bounds__(CL_BS, 1)
                   int *__restrict__ pflags, ClusterLayout L, const Acc *__restrict__ pairen, PcgOut po) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ const float4 *zp_rank[16];
-  __shared__ Acc esh[CL_WARPS][PAIREN];
   __shared__ Acc eslice[PAIREN];
   cgx::cluster_group cluster = cgx::this_cluster();
   const int rank = (int)cluster.block_rank(), CL = (int)cluster.num_blocks();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (po.energy) {
-    // this CTA's slice of the energy record: its share of the pairs, strided over threads, warp
-    // trees, warps in order; rank 0 adds the slices in rank order after the first barrier
+  if (po.energy && warp == CL_WARPS - 1) {
+    // this CTA's slice of the energy record, by its last warp while the others fill the block
+    // cache: its share of the pairs strided over the lanes, then a reduce-scatter of the four
+    // FP64 sums (6 FP64 adds instead of a butterfly per sum); rank 0 adds the slices in rank order
+    // after the first barrier
     const int p0 = t.prob_pair0[0], np = t.prob_pair1[0] - p0, chunk = (np + CL - 1) / CL;
     const int pa = p0 + min(np, rank * chunk), pb = p0 + min(np, (rank + 1) * chunk);
     Acc es[PAIREN] = {0, 0, 0, 0};
-    for (int q = pa + threadIdx.x; q < pb; q += CL_BS)
+    for (int q = pa + lane; q < pb; q += 32)
 #pragma unroll
       for (int c = 0; c < PAIREN; ++c) es[c] += pairen[(long long)q * PAIREN + c];
+    static_assert(PAIREN == 4, "the reduce-scatter below splits four sums");
+    const bool hi16 = (lane & 16) != 0, hi8 = (lane & 8) != 0;
+    Acc k0 = hi16 ? es[2] : es[0], k1 = hi16 ? es[3] : es[1];
+    k0 += __shfl_xor_sync(0xffffffffu, hi16 ? es[0] : es[2], 16);
+    k1 += __shfl_xor_sync(0xffffffffu, hi16 ? es[1] : es[3], 16);
+    Acc v = hi8 ? k1 : k0;
+    v += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
 #pragma unroll
-    for (int c = 0; c < PAIREN; ++c) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) es[c] += __shfl_xor_sync(0xffffffffu, es[c], o);
-      if (lane == 0) esh[warp][c] = es[c];
-    }
-    __syncthreads();
-    if (threadIdx.x < PAIREN) {
-      Acc v = 0;
-      for (int w = 0; w < CL_WARPS; ++w) v += esh[w][threadIdx.x];
-      eslice[threadIdx.x] = v;
-    }
+    for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((lane & 7) == 0) eslice[lane >> 3] = v;  // lanes 0, 8, 16, 24: sums 0, 1, 2, 3
   }
   const int v0 = t.prob_var0[0], v1 = t.prob_var1[0];
   const int nv = v1 - v0;
