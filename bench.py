@@ -111,14 +111,59 @@ def workload():
 
 
 # ------------------------------------------------------------------------------- clocks
+class _Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml ships with the driver): the SM clock, its
+    maximum and the active clock-event-reason mask of the device torch calls `index`."""
+    CLOCK_SM = 1
+
+    def __init__(self, index):
+        import ctypes
+        self.c = ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.lib = lib
+        self.h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(index).uuid)
+        except Exception:
+            pass
+        ok = uuid and lib.nvmlDeviceGetHandleByUUID(("GPU-" + uuid).encode(), ctypes.byref(self.h)) == 0
+        if not ok and lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        self.reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+    def clock(self, fn):
+        v = self.c.c_uint()
+        if fn(self.h, self.c.c_int(self.CLOCK_SM), self.c.byref(v)) != 0:
+            raise RuntimeError("clock query failed")
+        return float(v.value)
+
+    def sm_mhz(self):
+        return self.clock(self.lib.nvmlDeviceGetClockInfo)
+
+    def sm_max_mhz(self):
+        return self.clock(self.lib.nvmlDeviceGetMaxClockInfo)
+
+    def reasons(self):
+        v = self.c.c_ulonglong()
+        if self.reasons_fn(self.h, self.c.byref(v)) != 0:
+            raise RuntimeError("reason query failed")
+        return int(v.value)
+
+
 class Clocks:
     """SM clock and clock-event-reason sampler running during the timed region.
 
     NVML (read-only queries) every 5 ms from a thread, so that even a timed region of a few tens of
-    milliseconds gets samples; nvidia-smi at its 200 ms minimum period where NVML is missing."""
+    milliseconds gets samples; nvidia-smi at its 200 ms minimum period where NVML cannot be loaded."""
 
-    REASONS = (("hw_slowdown", "HwSlowdown", 0x8), ("hw_thermal_slowdown", "HwThermalSlowdown", 0x40),
-               ("sw_thermal_slowdown", "SwThermalSlowdown", 0x20), ("sw_power_cap", "SwPowerCap", 0x4))
+    # (name, NVML clock-event-reason bit)
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4))
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -132,27 +177,20 @@ class Clocks:
         self.proc = None
         self.file = None
 
-    def _nvml_loop(self, nv, h, bits):
-        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            nv.nvmlDeviceGetCurrentClocksThrottleReasons
-        mx = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+    def _nvml_loop(self, nv):
+        mx = nv.sm_max_mhz()
         while not self.stop_ev.is_set():
             try:
-                sm = float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM))
-                r = int(get_reasons(h))
-                self.rows.append((sm, mx, [name for name, bit in bits if r & bit]))
+                sm, r = nv.sm_mhz(), nv.reasons()
+                self.rows.append((sm, mx, [name for name, bit in self.REASONS if r & bit]))
             except Exception:
                 pass
             self.stop_ev.wait(self.period)
 
     def start(self):
         try:
-            import pynvml as nv
-            nv.nvmlInit()
-            h = nv.nvmlDeviceGetHandleByIndex(self.index)
-            bits = [(name, getattr(nv, "nvmlClocksEventReason" + cname, None) or
-                     getattr(nv, "nvmlClocksThrottleReason" + cname, bit)) for name, cname, bit in self.REASONS]
-            self.thread = threading.Thread(target=self._nvml_loop, args=(nv, h, bits), daemon=True)
+            nv = _Nvml(self.index)
+            self.thread = threading.Thread(target=self._nvml_loop, args=(nv,), daemon=True)
             self.thread.start()
             return
         except Exception:
@@ -183,7 +221,7 @@ class Clocks:
                     parts = [p.strip() for p in line.split(",")]
                     if len(parts) >= 8 and parts[0].replace(".", "").isdigit():
                         rows.append((float(parts[0]), float(parts[1]) if parts[1].replace(".", "").isdigit() else 0.0,
-                                     [name for (name, _, _), v in zip(self.REASONS, parts[4:8]) if v.lower() == "active"]))
+                                     [name for (name, _), v in zip(self.REASONS, parts[4:8]) if v.lower() == "active"]))
             os.unlink(self.file.name)
             source = "nvidia-smi, 200 ms"
         else:
