@@ -26,9 +26,11 @@
 // single kernel; here every dot product is reduced in a fixed order (warp tree, then CTA
 // partials summed in index order by every CTA) so results do not depend on scheduling.
 // Precision (mixed mode): vectors and their element-wise updates are FP32; a dot product's
-// products are summed in FP32 within a warp (a 32-term tree) and everything above the warp,
-// plus alpha and beta, in FP64.  B300 issues FP64 at 1/64 of the FP32 rate, so per-element
-// FP64 arithmetic would dominate these latency-bound kernels.
+// products are summed in FP32 within a warp (a 32-term tree; in k_pcg_cluster within the CTA)
+// and everything above that in FP64, or in k_pcg_cluster as float-float sums (about 48 bits,
+// FP32 pipe: the cross-CTA reductions are on its critical path twice per iteration); alpha and
+// beta are FP32 quotients of the rounded sums.  B300 issues FP64 at 1/64 of the FP32 rate, so
+// per-element FP64 arithmetic would dominate these latency-bound kernels.
 #include <cooperative_groups.h>
 
 #include <algorithm>
