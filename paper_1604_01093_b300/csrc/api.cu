@@ -995,18 +995,29 @@ bf_status build_tables_fresh(bf_ctx *c, const std::vector<Problem> &probs, const
     for (int d = 0; d < T.n_dp; ++d) ++start[T.dp_dst_host[d] + 1];
     for (int f = 0; f < T.n_frames; ++f) start[f + 1] += start[f];
     for (int d = 0; d < T.n_dp; ++d) order[start[T.dp_dst_host[d]]++] = d;
-    T.wi_off.push_back(0);
-    int run = 0;
-    for (int k = 0; k < T.n_dp; ++k) {
-      if (k > 0 && (T.dp_dst_host[order[k]] != T.dp_dst_host[order[k - 1]] || run == STAGED_PAIRS_PER_ITEM)) {
-        T.wi_off.push_back(k);
-        run = 0;
+    // a target with n directed pairs gets ceil(n / 6) items of near-equal size (15 pairs: 5, 5, 5
+    // rather than 6, 6, 3), and the items are launched largest first, so the launch's last wave
+    // holds the short items (one CTA per SM: the tail is one item long)
+    std::vector<std::array<int, 2>> items;  // (first index into order, size)
+    for (int k = 0; k < T.n_dp;) {
+      int e = k;
+      while (e < T.n_dp && T.dp_dst_host[order[e]] == T.dp_dst_host[order[k]]) ++e;
+      const int n = e - k, m = (n + STAGED_PAIRS_PER_ITEM - 1) / STAGED_PAIRS_PER_ITEM;
+      for (int q = 0, at = k; q < m; ++q) {
+        const int sz = n / m + (q < n % m ? 1 : 0);
+        items.push_back({at, sz});
+        at += sz;
       }
-      T.sw_dp.push_back(order[k]);
-      ++run;
+      k = e;
     }
-    T.wi_off.push_back(T.n_dp);
-    T.n_wi = (int)T.wi_off.size() - 1;
+    std::stable_sort(items.begin(), items.end(),
+                     [](const std::array<int, 2> &x, const std::array<int, 2> &y) { return x[1] > y[1]; });
+    T.wi_off.push_back(0);
+    for (const auto &it : items) {
+      for (int q = 0; q < it[1]; ++q) T.sw_dp.push_back(order[it[0] + q]);
+      T.wi_off.push_back((int)T.sw_dp.size());
+    }
+    T.n_wi = (int)items.size();
   } else {
     T.wi_off.push_back(0);
   }
