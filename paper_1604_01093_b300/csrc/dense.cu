@@ -22,8 +22,16 @@
 
 namespace bf {
 
+// Residency: with FP32 frames the accumulating pixel loop needs about 80 registers, so 3 CTAs
+// per SM (24 warps, no spills; 4 CTAs at 64 registers spill and run about 9 % slower); the 16-bit
+// unpacking path runs faster at 4 CTAs per SM.
+template <int MODE, int KIND>
+struct DenseOcc {
+  static constexpr int value = (KIND == BF_STORE_FP32 && MODE == MODE_ACCUM) ? 3 : 4;
+};
+
 template <int MODE, int KIND, typename Part>
-__global__ void __launch_bounds__(DENSE_BS, 4)
+__global__ void __launch_bounds__(DENSE_BS, DenseOcc<MODE, KIND>::value)
     k_dense(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo, float w_photo,
             Part *__restrict__ part, int *__restrict__ assoc) {
   extern __shared__ float ktab[];  // kx[W], ky[H]
@@ -61,10 +69,10 @@ int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in
 // 2 x 76.8 KB (FP32; one 76.8 KB record plane with 16-bit storage), so one CTA holds its target
 // frame in shared memory: a single thread issues the cp.async.bulk copies completing on an mbarrier, every thread waits (bounded), and all target
 // reads of the CTA's source frames then hit shared memory instead of L1/L2.  Work item = one
-// target frame with a few of its source frames (the host uses 4, one per quad, so that the
-// one-CTA-per-SM grid stays balanced); the CTA's 16 warps form 4 quads and each quad
-// evaluates one directed pair at a time (fixed lane-strided pixel order, quad tree reduction,
-// one partial per directed pair).
+// target frame with up to 6 of its source frames (a target's pairs split into near-equal items,
+// launched largest first, so that the one-CTA-per-SM grid stays balanced); the CTA's 24 warps
+// form 6 quads and each quad evaluates one directed pair at a time (fixed lane-strided pixel
+// order, quad tree reduction, one partial per directed pair).
 constexpr int STG_BS = 768;
 constexpr int STG_QUADS = STG_BS / 128;
 constexpr int STG_MAX_SMEM = 200 * 1024;
