@@ -51,12 +51,13 @@ def dense_bytes_per_px(storage):
     return DENSE_BYTES_PER_PX if storage == "fp32" else DENSE_BYTES_PER_PX_16
 
 # FP32 flops of the dense kernel per directed source pixel on this workload: ncu FFMA x 2 + FADD + FMUL
-# thread counts of one ACCUM launch divided by its 21.84 M directed source pixels
-# (profiles/k_dense_staged_global300_80x60.md)
+# thread counts of one ACCUM launch divided by its 21.84 M directed source pixels, counted on the
+# scalar build (profiles/k_dense_staged_global300_80x60.md); the packed-FMA build performs the
+# same operations, two per instruction
 DENSE_FLOPS_PER_PX = 122.8
-# DRAM bytes (read + write) of one dense ACCUM launch from the same ncu capture (cold cache); set to
-# None whenever the dense kernel changes until it is captured again
-DENSE_TRAFFIC_BYTES = 46.44e6 + 0.354e6
+# DRAM bytes (read + write) of one dense ACCUM launch from an ncu capture of the current kernel
+# (cold cache); set to None whenever the dense kernel changes until it is captured again
+DENSE_TRAFFIC_BYTES = 46.43e6 + 0.314e6
 # B300 FP32 peak: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 
