@@ -8,4 +8,5 @@ from ._lib import (Context, BFError, default_params, verify_params, lib, LIB_PAT
                    BF_PTR_HOST, BF_PTR_DEVICE, BF_STORE_FP32, BF_STORE_BF16, BF_STORE_FP16,
                    BF_PRECOND_BLOCK_JACOBI, BF_PRECOND_JACOBI, BF_PREC_MIXED, BF_PREC_FP32,
                    BF_FLAG_SINGULAR_BLOCK, BF_FLAG_EMPTY_FRAME, BF_FLAG_PCG_BREAKDOWN,
-                   BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER, BF_SPARSE_BLOCKS, BF_SPARSE_MATFREE)
+                   BF_PCG_AUTO, BF_PCG_CTA, BF_PCG_GRID, BF_PCG_CLUSTER, BF_SPARSE_BLOCKS, BF_SPARSE_MATFREE,
+                   BF_TILE_AUTOTUNE)
