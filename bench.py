@@ -747,7 +747,8 @@ def large_global_leg(bf, torch, dev, stream, steps=3, warmup=1):
     ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
                                   torch.from_numpy(prob.p_j).to(dev))
     common = {k: prm[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
-    p = bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=1, **common)
+    # the dense work decomposition from the library's autotuner (timed once, in the warm-up)
+    p = bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=1, tile_px=bf.BF_TILE_AUTOTUNE, **common)
 
     def step(pp=p):
         ctx.add_frames(0, depth_d, lum_d, init_pose=prob.init)
@@ -766,8 +767,9 @@ def large_global_leg(bf, torch, dev, stream, steps=3, warmup=1):
         ts.append(e0.elapsed_time(e1))
     ctx.reset_profile()
     ctx.set_profiling(True)
-    step(bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=0, **common))
+    step(bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=0, tile_px=bf.BF_TILE_AUTOTUNE, **common))
     prof = ctx.profile()
+    tuned = ctx.tuned_tile_px()
     ctx.set_profiling(False)
     ctx.close()
     dense = prof["kernels"]["dense"]
@@ -779,7 +781,7 @@ def large_global_leg(bf, torch, dev, stream, steps=3, warmup=1):
             "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"], "correspondences": prob.n_corr,
             "n_gn": prm["n_gn"], "n_pcg": prm["n_pcg"], "precision": "mixed", "generation_s": t_gen,
             "value": prm["n_gn"] / (statistics.mean(ts) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(ts),
-            "initial_energy": st["energy"][0], "final_energy": st["energy"][-1],
+            "initial_energy": st["energy"][0], "final_energy": st["energy"][-1], "tile_px_autotuned": tuned,
             "dense_kernel": {"avg_launch_ms": dense_ms, "directed_px_per_launch": units,
                              "algorithmic_GBps": DENSE_BYTES_PER_PX_16 * units / (dense_ms / 1000.0) / 1e9,
                              "frame_bytes": n * HW * 18},

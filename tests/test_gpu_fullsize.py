@@ -155,7 +155,8 @@ def golden2000():
 
 def test_global2000_first_step_matches_oracle(bf, global2000, golden2000):
     """The 2000-keyframe 160x120 solve in bench.py's configuration (BF16 frame storage, mixed
-    precision, tiled dense kernel, cluster PCG with its blocks in global memory, CUDA graph): its
+    precision, tiled dense kernel with the autotuned decomposition, cluster PCG with its blocks in
+    global memory, CUDA graph): its
     first Gauss-Newton step against the oracle's on the same BF16-rounded planes (energies, and the
     poses of every 32nd keyframe); the bench's own 10-step solve starts at the same two energies."""
     import torch
@@ -170,7 +171,7 @@ def test_global2000_first_step_matches_oracle(bf, global2000, golden2000):
     depth, lum = torch.from_numpy(prob.depth).to(dev), torch.from_numpy(prob.lum).to(dev)
     d = prob.solve
     common = dict(n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"], w_photo=d["w_photo"],
-                  w_geo=d["w_geo"], use_graph=1)
+                  w_geo=d["w_geo"], use_graph=1, tile_px=bf.BF_TILE_AUTOTUNE)
     ids = list(range(prob.n_frames))
     ctx.add_frames(0, depth, lum, init_pose=prob.init)
     st = ctx.solve_global(ids, n_gn=1, **common)
