@@ -456,6 +456,9 @@ int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, c
                        float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, const Acc *pairen, PcgOut po,
                        cudaStream_t st);
 size_t cluster_smem_bytes(int n_vars, int cl);
+// Whether the cluster PCG's CTAs can keep their incidence blocks in shared memory (inc_off: the
+// host copy of the incidence offsets).
+bool cluster_cache_fits(int n_vars, int cl, const int *inc_off);
 int cluster_size_max();
 size_t coop_mem_bytes(int grid);
 template <typename Acc>

@@ -815,6 +815,11 @@ size_t cluster_smem_bytes(int n_vars, int cl) {
   return b;
 }
 
+bool cluster_cache_fits(int n_vars, int cl, const int *inc_off) {
+  size_t b;
+  return cluster_layout(n_vars, cl, inc_off, &b).cache;
+}
+
 template <typename Acc>
 int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, const float *Minv, const Acc *rhs,
                        float *x, int n_pcg, int *pflags, int cl, const int *inc_off_host, const Acc *pairen,
