@@ -164,9 +164,11 @@ struct bf_ctx {
   long long ccap = 0, cused = 0;
   std::unordered_map<uint64_t, std::vector<Seg>> corr;
   std::unordered_map<int, Chunk> chunks;
-  // bumped whenever the pair map changes / a frame id gets a slot; with the problem list and the
-  // table parameters they decide whether a solve can reuse the last tables it built
-  uint64_t corr_ver = 0, frames_ver = 0, tables_gen = 0;
+  // signature of the pair map's layout (an XOR of one hash per segment: pair, position within the
+  // pair, pool offset, count; points re-uploaded into the same layout keep it) and a counter bumped
+  // whenever a frame id gets a slot; with the problem list and the table parameters they decide
+  // whether a solve can reuse the last tables it built
+  uint64_t corr_sig = 0, frames_ver = 0, tables_gen = 0;
   // solve executor in use (main, or a serving slot while it holds the context lock)
   Exec main;
   Exec *ex = &main;
@@ -634,6 +636,30 @@ extern "C" bf_status bf_get_frame_planes(bf_ctx *c, int frame_id, float *out) {
   return BF_OK;
 }
 
+// ------------------------------------------------------------------ correspondence map
+static inline uint64_t mix64(uint64_t x) {  // SplitMix64's finaliser (Steele, Lea, Flood 2014)
+  x += 0x9e3779b97f4a7c15ULL;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+  return x ^ (x >> 31);
+}
+static inline uint64_t seg_sig(uint64_t key, size_t pos, const Seg &s) {
+  return mix64(key ^ mix64((uint64_t)pos ^ mix64(((uint64_t)(uint32_t)s.off << 32) | (uint32_t)s.cnt)));
+}
+// Appends a segment to a pair's list, keeping the map's layout signature.
+static void corr_push(bf_ctx *c, uint64_t key, const Seg &s) {
+  std::vector<Seg> &v = c->corr[key];
+  c->corr_sig ^= seg_sig(key, v.size(), s);
+  v.push_back(s);
+}
+// Removes a pair and its segments from the map and the signature.
+static void corr_erase(bf_ctx *c, uint64_t key) {
+  auto it = c->corr.find(key);
+  if (it == c->corr.end()) return;
+  for (size_t k = 0; k < it->second.size(); ++k) c->corr_sig ^= seg_sig(key, k, it->second[k]);
+  c->corr.erase(it);
+}
+
 // ---------------------------------------------------------------------- correspondences
 extern "C" bf_status bf_add_correspondences(bf_ctx *c, int frame_i, int frame_j, int n, const float *p_i,
                                             const float *p_j, const float *weight, int ptr_kind) {
@@ -663,8 +689,7 @@ extern "C" bf_status bf_add_correspondences(bf_ctx *c, int frame_i, int frame_j,
           [&] { return launch_pack_corr(p_i, p_j, weight, n, swap, c->cP + c->cused, c->cQ + c->cused, c->st); });
     CK(cudaGetLastError(), "pack corr");
   }
-  c->corr[pair_key(frame_i, frame_j)].push_back(Seg{(int)c->cused, n});
-  ++c->corr_ver;
+  corr_push(c, pair_key(frame_i, frame_j), Seg{(int)c->cused, n});
   c->cused += n;
   CK(cudaEventRecord(c->data_ev, c->st), "data event");
   return BF_OK;
@@ -736,9 +761,8 @@ extern "C" bf_status bf_add_correspondences_batch(bf_ctx *c, int n_pairs, const 
   for (int k = 0; k < n_pairs; ++k) {
     const int n = offsets[k + 1] - offsets[k];
     if (n == 0) continue;
-    c->corr[pair_key(pair_ids[2 * k], pair_ids[2 * k + 1])].push_back(Seg{(int)(c->cused + offsets[k]), n});
+    corr_push(c, pair_key(pair_ids[2 * k], pair_ids[2 * k + 1]), Seg{(int)(c->cused + offsets[k]), n});
   }
-  ++c->corr_ver;
   c->cused += total;
   CK(cudaEventRecord(c->data_ev, c->st), "data event");
   return BF_OK;
@@ -779,8 +803,7 @@ extern "C" bf_status bf_remove_pair(bf_ctx *c, int frame_i, int frame_j) {
   std::unique_lock<std::mutex> lk(c->mu);
   auto it = c->corr.find(pair_key(frame_i, frame_j));
   if (it == c->corr.end()) return fail(c, BF_ERR_NOT_FOUND, "bf_remove_pair: no such pair");
-  c->corr.erase(it);
-  ++c->corr_ver;
+  corr_erase(c, it->first);
   return BF_OK;
 }
 
@@ -790,7 +813,7 @@ extern "C" bf_status bf_clear_correspondences(bf_ctx *c) {
   c->busy_cv.wait(lk, [&] { return c->in_flight == 0; });  // batches in flight still read the pool
   c->corr.clear();
   c->cused = 0;
-  ++c->corr_ver;
+  c->corr_sig = 0;
   return BF_OK;
 }
 
@@ -823,7 +846,8 @@ struct HostTables {
 // The last tables an executor built, with what they were built from.
 struct TableCache {
   std::vector<std::vector<int>> ids;  // frame ids per problem
-  uint64_t corr_ver = 0, frames_ver = 0;
+  uint64_t corr_sig = 0, frames_ver = 0;
+  size_t corr_pairs = 0;
   int tile_px = 0, dense_on = 0;
   bool staged = false;
   double max_angle_deg = 0;
@@ -1272,7 +1296,8 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
   Exec &ex = *c->ex;
   if (ex.tcache) {
     const TableCache &tc = *ex.tcache;
-    bool hit = tc.corr_ver == c->corr_ver && tc.frames_ver == c->frames_ver && tc.tile_px == tile_px &&
+    bool hit = tc.corr_sig == c->corr_sig && tc.corr_pairs == c->corr.size() && tc.frames_ver == c->frames_ver &&
+               tc.tile_px == tile_px &&
                tc.staged == staged && tc.dense_on == prm.dense_on && tc.max_angle_deg == prm.max_angle_deg &&
                tc.ids.size() == probs.size();
     for (size_t q = 0; hit && q < probs.size(); ++q) hit = tc.ids[q] == probs[q].ids;
@@ -1303,7 +1328,8 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
   auto tc = std::make_shared<TableCache>();
   tc->ids.reserve(probs.size());
   for (const Problem &P : probs) tc->ids.push_back(P.ids);
-  tc->corr_ver = c->corr_ver;
+  tc->corr_sig = c->corr_sig;
+  tc->corr_pairs = c->corr.size();
   tc->frames_ver = c->frames_ver;
   tc->tile_px = tile_px;
   tc->staged = staged;
@@ -1877,8 +1903,7 @@ bf_status solve_problems(bf_ctx *c, const std::vector<Problem> &probs, const bf_
       ++solves[k];
       const bf_solve_stats &S = sub_st[q];
       if (S.r_max > prm.prune_rmax && round < prm.prune_rounds && S.r_max_pair[0] >= 0) {
-        c->corr.erase(pair_key(S.r_max_pair[0], S.r_max_pair[1]));
-        ++c->corr_ver;
+        corr_erase(c, pair_key(S.r_max_pair[0], S.r_max_pair[1]));
         pruned[k].push_back({S.r_max_pair[0], S.r_max_pair[1]});
         next.push_back(k);
       }

@@ -108,3 +108,48 @@ def test_alternating_problems_of_equal_size(bf, prob):
     for _ in range(2):
         assert_same(solve(ctx, prob, s1), r1)
         assert_same(solve(ctx, prob, s2), r2)
+
+
+def test_reuploaded_correspondences(bf, prob):
+    """Cleared and uploaded again: in the same layout (the tables may be reused, the points are
+    read afresh) and in reversed pair order (a different layout); both equal a fresh context
+    loaded the same way."""
+    ids = list(range(prob.n_frames))
+    ctx = make_ctx(bf, prob)
+    ref = solve(ctx, prob, ids)
+    order = list(range(len(prob.pairs)))
+    for rev in (False, True, False):
+        ks = order[::-1] if rev else order
+        ctx.clear_correspondences()
+        for k in ks:
+            i, j = (int(x) for x in prob.pairs[k])
+            p, q = prob.pair_corr(k)
+            ctx.add_correspondences(i, j, p, q)
+        got = solve(ctx, prob, ids)
+        if not rev:
+            assert_same(got, ref)
+        else:
+            fresh_ctx = make_ctx(bf, prob, skip={(int(i), int(j)) for i, j in prob.pairs})
+            for k in ks:
+                i, j = (int(x) for x in prob.pairs[k])
+                p, q = prob.pair_corr(k)
+                fresh_ctx.add_correspondences(i, j, p, q)
+            assert_same(got, solve(fresh_ctx, prob, ids))
+
+
+def test_new_points_in_the_same_layout_are_used(bf, prob):
+    """Points moved by 2 mm and uploaded into the same layout: the solve sees the new points (it
+    equals a fresh context loaded with them and differs from the solve on the old ones)."""
+    ids = list(range(prob.n_frames))
+    ctx = make_ctx(bf, prob)
+    old = solve(ctx, prob, ids)
+    ctx.clear_correspondences()
+    fresh_ctx = make_ctx(bf, prob, skip={(int(i), int(j)) for i, j in prob.pairs})
+    for k, (i, j) in enumerate(prob.pairs):
+        p, q = prob.pair_corr(k)
+        p = p + np.float32(0.002)
+        ctx.add_correspondences(int(i), int(j), p, q)
+        fresh_ctx.add_correspondences(int(i), int(j), p, q)
+    got = solve(ctx, prob, ids)
+    assert_same(got, solve(fresh_ctx, prob, ids))
+    assert got[0]["energy"] != old[0]["energy"]
