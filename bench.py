@@ -530,7 +530,7 @@ def run_ours(args, rank, world, local_rank):
 
 
 def accuracy_leg(bf, torch, dev, batch_prob=None):
-    """Error of the GPU solves against the FP64 oracle (spec tolerances: rotation 1e-4 rad,
+    """Error of the GPU solves against the FP64 oracle (the accuracy targets: rotation 1e-4 rad,
     translation 1e-5 m, per-iteration energy 1e-5 relative): the 11-frame 80x60 chunk in mixed
     precision, plain FP32 and with BF16 frame storage, and one chunk of the 256-chunk 320x240 batch
     in the batch's FP32 arithmetic with FP32 and BF16 storage (a chunk solved alone gives the same

@@ -11,7 +11,7 @@
 
 The oracle needs minutes (the 2000-keyframe step about forty) for these, so its results are stored, written by the
 make_*_oracle.py scripts beside them from the oracle and the seeded scene generator alone.
-Tolerances are the spec ones.
+Tolerances are the accuracy targets: 1e-4 rad, 1e-5 m, 1e-5 relative energy.
 """
 import json
 import os

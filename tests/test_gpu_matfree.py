@@ -2,8 +2,8 @@
 
 The matrix-free product and the assembled 6x6 sparse blocks are the same linear operator, so the
 two modes must give the same Gauss-Newton steps up to FP32 rounding (compared like the PCG kernel
-variants: 5e-6 in the poses, 1e-6 relative in the energies), and both must meet the north-star
-tolerances against the FP64 oracle, which assembles the normal equations explicitly.
+variants: 5e-6 in the poses, 1e-6 relative in the energies), and both must meet the accuracy
+targets against the FP64 oracle, which assembles the normal equations explicitly.
 """
 import numpy as np
 import pytest

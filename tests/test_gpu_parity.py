@@ -1,6 +1,6 @@
 """GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
 
-Tolerances (spec numbers, and ones derived from the FP32 evaluation):
+Tolerances (the accuracy targets, and ones derived from the FP32 evaluation):
 * final poses: rotation <= 1e-4 rad, translation <= 1e-5 m;
 * per-iteration energy: relative error <= 1e-5;
 * association decisions are taken in FP32 with the same operation order on both sides,

@@ -2,8 +2,8 @@
 
 Chunks of 80x60 frames with 5 mm correspondence noise and no random outliers, plus one pair
 whose matches are half wrong (shifted 0.3 m in frame j: no rigid motion explains them).  Both
-sides must remove the same pairs in the same order and end at the same poses (north-star
-tolerances), and frames left without pairs are reported invalid.
+sides must remove the same pairs in the same order and end at the same poses (within the
+accuracy targets), and frames left without pairs are reported invalid.
 """
 import copy
 
