@@ -517,7 +517,6 @@ def run_ours(args, rank, world, local_rank):
         line["chunk_batch"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob)
         line["chunk_batch_bf16"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob, storage="bf16")
         line["serving"] = serving_leg(bf, torch, dev, cprob, prob)
-        line["accuracy_vs_oracle"] = accuracy_leg(bf, torch, dev, cprob)
 
         line["next_rows"] = next_rows_leg(bf, torch, dev, stream, prob, prm)
         line["large_global"] = large_global_leg(bf, torch, dev, stream)
@@ -527,62 +526,6 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
-
-
-def accuracy_leg(bf, torch, dev, batch_prob=None):
-    """Error of the GPU solves against the FP64 oracle (the accuracy targets: rotation 1e-4 rad,
-    translation 1e-5 m, per-iteration energy 1e-5 relative): the 11-frame 80x60 chunk in mixed
-    precision, plain FP32 and with BF16 frame storage, and one chunk of the 256-chunk 320x240 batch
-    in the batch's FP32 arithmetic with FP32 and BF16 storage (a chunk solved alone gives the same
-    bits as inside its batch).  The oracle sees the unrounded frames in every case."""
-    import synth
-    from oracle import frames as ofr, lie, solver
-    from oracle.system import SolveParams
-
-    def errors(st, poses, ref):
-        rot = max(lie.pose_error(poses[k], ref.poses[k])[0] for k in range(len(poses)))
-        tr = max(lie.pose_error(poses[k], ref.poses[k])[1] for k in range(len(poses)))
-        en = max(abs(a - b) / abs(b) for a, b in zip(st["energy"], ref.energy))
-        return {"rotation_rad": rot, "translation_m": tr, "energy_rel": en}
-
-    def case(prob, ids, d, runs):
-        intr = prob.intr
-        fr = [ofr.Frame(prob.depth[f], prob.lum[f], intr) for f in ids]
-        t0 = time.perf_counter()
-        ref = solver.gauss_newton(fr, intr, prob.init[ids], solver.sparse_pairs_for(prob, ids),
-                                  SolveParams(n_gn=d["n_gn"], n_pcg=d["n_pcg"], w_sparse=d["w_sparse"],
-                                              w_dense=d["w_dense"], w_photo=d["w_photo"], w_geo=d["w_geo"]))
-        out = {"frames": len(ids), "resolution": f"{intr['W']}x{intr['H']}", "n_gn": d["n_gn"],
-               "n_pcg": d["n_pcg"], "oracle_s": time.perf_counter() - t0}
-        for name, storage, kw in runs:
-            ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"],
-                             storage=STORAGE_CODES[storage](bf), max_frames_hint=len(ids))
-            ctx.add_frames(0, prob.depth[ids], prob.lum[ids])
-            loc = {f: k for k, f in enumerate(ids)}
-            for k, (i, j) in enumerate(prob.pairs):
-                if int(i) in loc and int(j) in loc:
-                    p, q = prob.pair_corr(k)
-                    ctx.add_correspondences(loc[int(i)], loc[int(j)], p, q)
-            st = ctx.solve_local(0, list(range(len(ids))), **{k: d[k] for k in
-                                                               ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo",
-                                                                "w_geo")}, **kw)
-            out[name] = errors(st, ctx.get_poses(list(range(len(ids)))), ref)
-            ctx.close()
-        return out
-
-    res = {"tolerances": {"rotation_rad": 1e-4, "translation_m": 1e-5, "energy_rel": 1e-5}}
-    c1 = synth.cfg1()
-    res["chunk11_80x60"] = case(c1, list(range(c1.n_frames)), c1.solve,
-                                [("mixed", "fp32", {}), ("plain_fp32", "fp32", {"precision": bf.BF_PREC_FP32}),
-                                 ("mixed_bf16_storage", "bf16", {})])
-    if batch_prob is not None:
-        k = min(range(len(batch_prob.chunks)), key=lambda c: (len(batch_prob.chunks[c]) != 5, c))
-        ids = [int(f) for f in batch_prob.chunks[k]]
-        res["batch_chunk_320x240"] = case(batch_prob, ids, batch_prob.solve,
-                                          [("fp32_arith_fp32_storage", "fp32", {"precision": bf.BF_PREC_FP32}),
-                                           ("fp32_arith_bf16_storage", "bf16", {"precision": bf.BF_PREC_FP32})])
-        res["batch_chunk_320x240"]["chunk"] = k
-    return res
 
 
 def sparse_term_leg(bf, step, timed, prm, precision, steps):
