@@ -1458,6 +1458,8 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
     cudaStreamWaitEvent(c->ex->st, c->ex->ev_join, 0);
   }
   run_k(c, BF_K_MERGE, [&] {
+    if (mode == MODE_ENERGY)  // the energy record alone
+      return launch_pair_energy<Acc>(t, (const Acc *)D.dpart, (const Acc *)D.spart, (Acc *)D.pairen, c->ex->st);
     return launch_pair_merge<Acc, Acc>(t, D.pose, (const Acc *)D.dpart, (const Acc *)D.spart, (Acc *)D.pairblk,
                                        (Acc *)D.pairen, D.pairoff, c->ex->st);
   });

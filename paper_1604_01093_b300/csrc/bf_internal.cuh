@@ -435,6 +435,8 @@ template <typename Acc, typename Part>
 int launch_pair_merge(const Tables &t, const double *pose, const Part *dpart, const Part *spart, Acc *pairblk,
                        Acc *pairen, float *pairoff, cudaStream_t st);
 template <typename Acc>
+int launch_pair_energy(const Tables &t, const Acc *dpart, const Acc *spart, Acc *pairen, cudaStream_t st);
+template <typename Acc>
 int launch_assemble(const Tables &t, const Acc *pairblk, int precond, Acc *Dd, Acc *rhs, float *Df, float *Minv,
                      int *vflags, cudaStream_t st);
 template <typename Acc>

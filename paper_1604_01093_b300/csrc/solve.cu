@@ -88,6 +88,46 @@ template int launch_pair_merge<double, double>(const Tables &, const double *, c
 template int launch_pair_merge<float, float>(const Tables &, const double *, const float *, const float *, float *,
                                              float *, float *, cudaStream_t);
 
+// Energy record of every pair alone (the final energy evaluation needs no pair blocks): one
+// thread per pair, the same sums in the same order as merge_pair (dense a -> b, sparse segments,
+// dense b -> a), so the records equal the full merge's bit for bit.
+template <typename Acc>
+__global__ void k_pair_energy(Tables t, const Acc *__restrict__ dpart, const Acc *__restrict__ spart,
+                              Acc *__restrict__ pairen) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= t.n_pairs) return;
+  Acc en[4] = {0, 0, 0, 0};  // e_sparse, e_photo, e_geo, n_dense
+  for (int half = 0; half < 2; ++half) {
+    const int d = t.pair_dp[2 * p + half];
+    if (d >= 0) {
+      const int k0 = t.dp_tile0[d], k1 = t.dp_tile1[d];
+      Acc e0 = 0, e1 = 0, cn = 0;
+      for (int it = k0; it < k1; ++it) e0 += dpart[(long long)it * NPD + D_E0];
+      for (int it = k0; it < k1; ++it) e1 += dpart[(long long)it * NPD + D_E1];
+      for (int it = k0; it < k1; ++it) cn += dpart[(long long)it * NPD + D_CNT];
+      en[2] += e0;
+      en[1] += e1;
+      en[3] += cn;
+    }
+    if (spart != nullptr && half == 0 && t.pair_seg1[p] > t.pair_seg0[p]) {
+      Acc s = 0;
+      for (int it = t.pair_seg0[p]; it < t.pair_seg1[p]; ++it) s += spart[(long long)it * NPART + P_E0];
+      en[0] += s;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < PAIREN; ++k) pairen[(long long)p * PAIREN + k] = en[k];
+}
+
+template <typename Acc>
+int launch_pair_energy(const Tables &t, const Acc *dpart, const Acc *spart, Acc *pairen, cudaStream_t st) {
+  if (t.n_pairs == 0) return 0;
+  k_pair_energy<Acc><<<(t.n_pairs + 127) / 128, 128, 0, st>>>(t, dpart, spart, pairen);
+  return 1;
+}
+template int launch_pair_energy<double>(const Tables &, const double *, const double *, double *, cudaStream_t);
+template int launch_pair_energy<float>(const Tables &, const float *, const float *, float *, cudaStream_t);
+
 template <typename Acc>
 __global__ void __launch_bounds__(32 * ASM_WARPS)
     k_assemble(Tables t, const Acc *__restrict__ pairblk, int precond, Acc *__restrict__ Dd, Acc *__restrict__ rhs,
