@@ -852,6 +852,8 @@ struct TableCache {
   bool staged = false;
   double max_angle_deg = 0;
   HostTables T;
+  uint64_t gen = 0;   // T's generation
+  bool lent = false;  // T moved out to a solve in flight (given back by return_tables)
 };
 
 constexpr int STAGED_PAIRS_PER_ITEM = 6;
@@ -1295,8 +1297,8 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
   const double cos_max = std::cos(prm.max_angle_deg * M_PI / 180.0);
   Exec &ex = *c->ex;
   if (ex.tcache) {
-    const TableCache &tc = *ex.tcache;
-    bool hit = tc.corr_sig == c->corr_sig && tc.corr_pairs == c->corr.size() && tc.frames_ver == c->frames_ver &&
+    TableCache &tc = *ex.tcache;
+    bool hit = !tc.lent && tc.corr_sig == c->corr_sig && tc.corr_pairs == c->corr.size() && tc.frames_ver == c->frames_ver &&
                tc.tile_px == tile_px &&
                tc.staged == staged && tc.dense_on == prm.dense_on && tc.max_angle_deg == prm.max_angle_deg &&
                tc.ids.size() == probs.size();
@@ -1312,7 +1314,10 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
       }
     }
     if (hit) {
-      T = C;
+      // lent to this solve instead of copied (about 0.4 MB of tables for 300 keyframes); the
+      // solve gives them back when it finishes
+      T = std::move(tc.T);
+      tc.lent = true;
       T.pose.clear();
       for (const Problem &P : probs)
         for (const Pose12 &x : P.init) T.pose.insert(T.pose.end(), x.begin(), x.end());
@@ -1336,6 +1341,7 @@ bf_status build_tables(bf_ctx *c, const std::vector<Problem> &probs, const bf_so
   tc->dense_on = prm.dense_on;
   tc->max_angle_deg = prm.max_angle_deg;
   tc->T = T;
+  tc->gen = T.gen;
   ex.tcache = std::move(tc);
   return BF_OK;
 }
@@ -1663,6 +1669,7 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
 // A solve whose device work has been enqueued on an executor's stream.
 struct SolveJob {
   HostTables T;
+  Exec *ex = nullptr;  // the executor whose table cache T may have come from
   DevSolve D;
   bf_solve_params prm;
   std::vector<int> sizes;  // frames per problem
@@ -1744,6 +1751,7 @@ static int tune_tile(bf_ctx *c, const std::vector<Problem> &probs, const bf_solv
 
 bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_solve_params &prm_in, SolveJob &J) {
   J.t0 = std::chrono::steady_clock::now();
+  J.ex = c->ex;
   bf_solve_params prm = prm_in;
   if (prm.tile_px == BF_TILE_AUTOTUNE) prm.tile_px = tune_tile(c, probs, prm);
   J.prm = prm;
@@ -1791,6 +1799,16 @@ bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_s
   if (D.persistent)
     CK(cudaMemcpyAsync(pb + J.o_ce + 8, (char *)D.bq + 8, sizeof(int), cudaMemcpyDeviceToHost, st), "batch status");
   return pin_used(c);
+}
+
+// A solve that took its tables from the executor's cache gives them back when it has finished.
+static void return_tables(SolveJob &J) {
+  if (J.ex == nullptr || !J.ex->tcache) return;
+  TableCache &tc = *J.ex->tcache;
+  if (tc.lent && J.T.gen != 0 && J.T.gen == tc.gen) {
+    tc.T = std::move(J.T);
+    tc.lent = false;
+  }
 }
 
 // Phase 3 (after the executor's stream is synchronised, context lock held): unpack the results.
@@ -1857,6 +1875,7 @@ bf_status finish_solve(bf_ctx *c, SolveJob &J, std::vector<std::vector<Pose12>> 
     S.flags = fl;
     S.ms = ms;
   }
+  return_tables(J);
   return BF_OK;
 }
 
