@@ -153,3 +153,23 @@ def test_new_points_in_the_same_layout_are_used(bf, prob):
     got = solve(ctx, prob, ids)
     assert_same(got, solve(fresh_ctx, prob, ids))
     assert got[0]["energy"] != old[0]["energy"]
+
+
+def test_failed_solve_leaves_the_cache_usable(bf, prob):
+    """A solve that the table build rejects (a pair with 2 correspondences: Sec. 4.1.1 needs 3),
+    then the pair removed: the next solves equal a fresh context's."""
+    ids = list(range(prob.n_frames))
+    ref = fresh(bf, prob, ids)
+    ctx = make_ctx(bf, prob)
+    assert_same(solve(ctx, prob, ids), ref)
+    # the first pair keeps only 2 of its correspondences
+    i, j = (int(x) for x in prob.pairs[0])
+    ctx.remove_pair(i, j)
+    p, q = prob.pair_corr(0)
+    ctx.add_correspondences(i, j, p[:2], q[:2])
+    with pytest.raises(bf.BFError):
+        solve(ctx, prob, ids)
+    ctx.remove_pair(i, j)
+    ctx.add_correspondences(i, j, p, q)
+    assert_same(solve(ctx, prob, ids), ref)
+    assert_same(solve(ctx, prob, ids), ref)
