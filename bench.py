@@ -1,21 +1,25 @@
 #!/usr/bin/env python
-"""Benchmark of the global pose alignment solve (BundleFusion Sec. 4.2-4.4) on B300.
+"""Benchmark of BundleFusion's pose-alignment hot path (Sec. 4.2-4.4) on B300.
 
-Workload (default): the global solve over 300 keyframes at 80x60 along a ~60 m loop of a
-synthetic ring corridor, pairs with ground-truth overlap > 30 %, 64-256 correspondences
-per pair (sigma 1 cm, 5 % outliers), dense weight 0.5, 8 Gauss-Newton x 20 PCG
-iterations.  One step = the whole hot path once: frame preprocessing from device-resident
-raw depth/luminance, pair-set construction, 8 linearisations (dense + sparse terms,
-block reduction, assembly), 8 x 20 PCG iterations and pose updates, final energy and r_max.
+Workload (the line's value): 256 independent chunk solves of U{3..11} frames at 320x240 (1831
+frames, 3.9 GB of FP32 frame planes: larger than L2), all intra-chunk pairs (6559 pairs,
+13118 directed dense pairs), 100-400 sparse correspondences per pair (sigma 1 cm, 5 % outliers),
+6 Gauss-Newton x 10 PCG iterations each, FP32 arithmetic, FP32 frame storage, solved as one batch
+(one launch sequence replayed as a CUDA graph, the dense work decomposition chosen by the
+library's autotuner).  One step = the whole hot path once over the batch: frame preprocessing
+from device-resident raw depth / luminance, pair-set and table construction, 6 linearisations
+(dense + sparse terms, block reduction, assembly), 6 x 10 PCG iterations and pose updates, final
+energy and r_max, results read back.
 
-Metric: Gauss-Newton iterations per second (whole job over all ranks).  Extra fields:
-the plain FP32 one-solve-per-launch path on the same workload, chunk-solve latency
-p50/p99 (single 11-frame 80x60 chunks, optimised vs plain path), the roofline of the
-dominant kernel (dense term) and the FP64 oracle timed on the host cores.
+Metric: Gauss-Newton iterations per second (one chunk's iteration = 1; whole job over all ranks),
+chunk-solve p50 / p99 latency of the batch and of the plain path (the FP32 one-solve-per-launch
+sequence, kernel by kernel), and the dense kernel's algorithmic HBM bandwidth as a fraction of the
+measured peak.  Extra legs: the same batch end to end from host buffers, with BF16 storage and as
+one persistent launch; the 300-keyframe 80x60 global solve; the 2000-keyframe 160x120 global solve;
+serving; the steps around the solver; the FP64 oracle on the host cores.
 
-Under torchrun (N > 1) every rank solves its own replica (the global solve does not
-shard; chunk solves would): scaling "weak", no collective on the data path, the step
-time is the max over ranks.
+Under torchrun (N > 1) every rank solves its own replica of the batch (chunks are independent
+problems): scaling "weak", no collective on the data path, the step time is the max over ranks.
 """
 import argparse
 import json
@@ -56,8 +60,11 @@ def dense_bytes_per_px(storage):
 # same operations, two per instruction
 DENSE_FLOPS_PER_PX = 122.8
 # DRAM bytes (read + write) of one dense ACCUM launch from an ncu capture of the current kernel
-# (cold cache); set to None whenever the dense kernel changes until it is captured again
-DENSE_TRAFFIC_BYTES = 46.43e6 + 0.314e6
+# (cold cache); set to None whenever the dense kernel changes until it is captured again.
+# 300-keyframe 80x60 workload, k_dense_staged:
+DENSE_TRAFFIC_BYTES = None
+# 256-chunk 320x240 batch, k_dense (tiled, autotuned decomposition):
+DENSE_TRAFFIC_BYTES_CHUNKS = None
 # untimed warm-up floor after the W warm-up steps (seconds of repeated steps)
 WARMUP_MIN_S = 0.5
 # B300 FP32 peak: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock
@@ -88,12 +95,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp32"])
-    ap.add_argument("--no-extras", action="store_true", help="skip plain-path, latency and CPU-baseline legs")
+    ap.add_argument("--precision", default="fp32", choices=["mixed", "fp32"],
+                    help="arithmetic of the timed batch (chunk solves meet the accuracy targets in FP32)")
+    ap.add_argument("--no-extras", action="store_true", help="skip every leg after the headline (e2e, plain, ...)")
     ap.add_argument("--profile-run", action="store_true", help="short run for ncu: no extras, no clocks")
     ap.add_argument("--no-graph", action="store_true", help="launch kernel by kernel instead of a CUDA graph")
-    ap.add_argument("--tile-px", type=int, default=0,
-                    help="dense work item size in source pixels; 0 = automatic (target frame staged in shared memory)")
+    ap.add_argument("--tile-px", type=int, default=-1,
+                    help="dense work item size in source pixels; -1 = the library's autotuner, 0 = staged target")
+    ap.add_argument("--global-only", action="store_true",
+                    help="run only the 300-keyframe 80x60 global solve leg (one JSON line)")
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving leg (one JSON line)")
+    ap.add_argument("--serving-seconds", type=float, default=8.0, help="length of the served session")
+    ap.add_argument("--chunks", type=int, default=256,
+                    help="chunks in the timed batch (a smaller batch for profiling captures; the line then names it)")
     ap.add_argument("--large-only", action="store_true",
                     help="run only the 2000-keyframe 160x120 BF16 global solve leg (one JSON line)")
     ap.add_argument("--batch-only", action="store_true", help="only the 256-chunk batch legs (FP32 and BF16 storage)")
@@ -106,11 +120,16 @@ def parse():
     return ap.parse_args()
 
 
-def workload():
+def workload(n_chunks=256):
+    """The 256-chunk 320x240 batch (its default solve parameters); fewer chunks for profiling."""
     import synth
-    prob = synth.cfg2()
-    prm = prob.solve
-    return prob, prm
+    prob = synth.cfg3() if n_chunks == 256 else synth.cfg3(n_chunks=n_chunks)
+    return prob, prob.solve
+
+
+def quantile(v, f):
+    v = sorted(v)
+    return v[min(len(v) - 1, int(f * len(v)))] if v else None
 
 
 # ------------------------------------------------------------------------------- clocks
@@ -240,74 +259,124 @@ class Clocks:
 
 
 # ------------------------------------------------------------------------- CPU baseline
-def oracle_gn_iteration_rate(prob, prm, budget_s=15.0, max_pairs=None):
-    """Time the FP64 oracle's Gauss-Newton iteration on a bounded sample of pairs and scale.
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
 
-    The sample is the first k pairs (in pair order) with all their frames; assemble time is
-    scaled by n_pairs / k, the PCG over the full explicit system is timed as is.  Single
-    BLAS thread.  Returns (GN iterations/s, description, cores)."""
-    from oracle import frames as ofr, solver, system
-    from oracle.system import SolveParams
 
-    P = SolveParams(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"], w_dense=prm["w_dense"],
-                    w_photo=prm["w_photo"], w_geo=prm["w_geo"])
-    n = prob.n_frames
-    sp_all = solver.sparse_pairs_for(prob, range(n))
-    cache = {}
-    t0 = time.perf_counter()
-    done = 0
-    t_assemble = 0.0
-    for sp in sp_all:
-        if max_pairs is not None and done >= max_pairs:
-            break
-        if time.perf_counter() - t0 > budget_s:
-            break
-        ts = time.perf_counter()
-        for f in (sp.a, sp.b):
-            if f not in cache:
-                cache[f] = ofr.Frame(prob.depth[f], prob.lum[f], prob.intr)
-        fr = [cache.get(k) for k in range(n)]
-        dp = system.dense_pair_set(prob.init, [sp], P.max_angle_deg)
-        system.assemble(fr, prob.intr, prob.init, [sp], dp, P, P.w_dense)
-        t_assemble += time.perf_counter() - ts
-        done += 1
-    m = 6 * (n - 1)
-    rng = np.random.default_rng(0)
-    B = rng.normal(size=(m, m))
-    A = B @ B.T + m * np.eye(m)
-    b = rng.normal(size=m)
-    ts = time.perf_counter()
-    Minv, _ = solver.block_jacobi_inverse(A, "block")
-    solver.pcg(A, b, Minv, P.n_pcg)
-    t_pcg = time.perf_counter() - ts
-    per_iter = t_assemble * (len(sp_all) / max(done, 1)) + t_pcg
-    desc = (f"oracle GN iteration: system assembly over {done} of {len(sp_all)} pairs (dense both directions "
-            f"+ sparse) timed and scaled to all pairs, plus block-Jacobi PCG ({P.n_pcg} it.) over the full "
-            f"{m}x{m} system; numpy, 1 BLAS thread")
-    return 1.0 / per_iter, desc, 1
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+class OracleSampler:
+    """The FP64 oracle (Sec. 4.4 Gauss-Newton over explicitly assembled normal equations) on the
+    host cores, for a bounded sample of the chunk batch: a spawn process pool whose workers build
+    the sampled chunks' frames from their raw depth / luminance on first use and evaluate the dense
+    pairs; the parent assembles the sparse term, sums the pairs in order, and runs the block-Jacobi
+    PCG on the assembled system and the pose update.  One chunk GN iteration = 1 unit, as on the
+    GPU."""
+
+    def __init__(self, prob, prm, chunk_ids, processes=None):
+        from oracle import frames as ofr, system
+        from oracle.system import SolveParams
+        self.prob, self.chunk_ids = prob, list(chunk_ids)
+        self.P = SolveParams(n_gn=1, n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"], w_dense=prm["w_dense"],
+                             w_photo=prm["w_photo"], w_geo=prm["w_geo"])
+        self.cores = processes or host_cores()
+        fids = sorted({int(f) for k in self.chunk_ids for f in prob.chunks[k]})
+        cache = ofr.FrameCache({f: prob.depth[f] for f in fids}, {f: prob.lum[f] for f in fids}, prob.intr)
+        self.pool = system.frame_pool(cache, self.cores)
+        self.pool.map(abs, range(4 * self.cores))  # workers started before any timing
+
+    def gn_iterations(self, chunks):
+        """One GN iteration of each listed chunk from its initial poses; returns wall seconds."""
+        from oracle import solver, system
+        prob, P = self.prob, self.P
+        pmap = lambda f, tasks: self.pool.map(f, tasks, chunksize=1)  # noqa: E731
+        t0 = time.perf_counter()
+        for k in chunks:
+            ids = [int(f) for f in prob.chunks[k]]
+            sp = solver.sparse_pairs_for(prob, ids)
+            X0 = prob.init[ids]
+            dp = system.dense_pair_set(X0, sp, P.max_angle_deg)
+            S = system.assemble([None] * len(ids), prob.intr, X0, sp, dp, P, P.w_dense, pmap=pmap, frame_keys=ids)
+            Minv, _ = solver.block_jacobi_inverse(S.A, P.precond)
+            delta, _ = solver.pcg(S.A, S.b, Minv, P.n_pcg)
+            solver.apply_step(X0, delta)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def cpu_baseline_leg(prob, prm, n_chunks=16):
+    """The oracle on a bounded sample: one GN iteration of each of the first n_chunks chunks."""
+    chunks = list(range(n_chunks))
+    s = OracleSampler(prob, prm, chunks)
+    try:
+        dt = s.gn_iterations(chunks)
+    finally:
+        s.close()
+    frames = sum(len(prob.chunks[k]) for k in chunks)
+    return {"value": len(chunks) / dt, "unit": UNIT, "cores": s.cores, "kind": "oracle",
+            "sample": f"one Gauss-Newton iteration ({prm['n_pcg']} PCG) of each of chunks 0..{n_chunks - 1} of this "
+                      f"workload ({frames} frames at 320x240, frames preprocessed inside the timing): FP64 numpy, "
+                      f"system assembled explicitly, dense pairs spread over {s.cores} spawn processes "
+                      f"(1 BLAS thread each), measured, not extrapolated; {dt:.2f} s wall",
+            "cpu": cpu_model()}
 
 
 # ------------------------------------------------------------------------------ reference
 def run_reference(args, rank, world):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores.  Each step is one GN
+    iteration of the next chunk of the batch (in chunk order), measured; the line reports what ran."""
     if rank != 0:
         return
     prob, prm = workload()
-    vals = []
-    desc = ""
-    for k in range(args.warmup + args.steps):
-        v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=4.0)
-        if k >= args.warmup:
-            vals.append(v)
-    value = statistics.mean(vals)
+    n = args.warmup + args.steps
+    chunks = [k % len(prob.chunks) for k in range(n)]
+    s = OracleSampler(prob, prm, sorted(set(chunks)))
+    try:
+        times = [s.gn_iterations([k]) for k in chunks]
+    finally:
+        s.close()
+    timed = times[args.warmup:]
+    value = len(timed) / sum(timed)
+    frames = sum(len(prob.chunks[k]) for k in chunks[args.warmup:])
+    desc = (f"each step: one Gauss-Newton iteration ({prm['n_pcg']} PCG) of one chunk of this workload, chunks "
+            f"{chunks[args.warmup]}..{chunks[-1]} in order ({frames} frames at 320x240 in the timed steps), frames "
+            f"preprocessed inside the timing; FP64 numpy with explicit normal equations, dense pairs over "
+            f"{s.cores} spawn processes; every step measured (ms_per_step x steps is the time that ran)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * prm["n_gn"] / value,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sum(timed) / len(timed),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": prob.name, "keyframes": prob.n_frames,
-                                            "pairs": int(len(prob.pairs)), "n_gn": prm["n_gn"],
-                                            "n_pcg": prm["n_pcg"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "data": "synthetic", "config": workload_config(prob, prm, "fp32", "fp64 (oracle)"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": s.cores, "kind": "oracle", "sample": desc,
+                             "cpu": cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_config(prob, prm, storage, precision, **extra):
+    intr = prob.intr
+    n = len(prob.chunks)
+    cfg = {"workload": f"chunks{n}_320x240: {n} chunk solves of U{{3..11}} frames at 320x240",
+           "chunks": len(prob.chunks), "frames": prob.n_frames, "resolution": f"{intr['W']}x{intr['H']}",
+           "pairs": int(len(prob.pairs)), "correspondences": prob.n_corr, "n_gn": prm["n_gn"], "n_pcg": prm["n_pcg"],
+           "storage": storage, "precision": precision,
+           "l2": "inputs larger than L2 (3.9 GB of FP32 frame planes, 126 MB L2): no flush between steps"}
+    cfg.update(extra)
+    return cfg
 
 
 # ------------------------------------------------------------------------------- ours
@@ -321,52 +390,273 @@ def run_ours(args, rank, world, local_rank):
     dist = None
     if world > 1:
         import torch.distributed as dist
-    prob, prm = workload()
+    stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
+    torch.cuda.set_stream(stream)
+    only = [(args.large_only, "large_global", lambda: large_global_leg(bf, torch, dev, stream)),
+            (args.global_only, "global300", lambda: global300_leg(bf, torch, dev, stream, args)),
+            (args.next_rows_only, "next_rows", lambda: next_rows_leg(bf, torch, dev, stream)),
+            (args.serving_only, "serving", lambda: serving_leg(bf, torch, dev, seconds=args.serving_seconds)),
+            (args.batch_only, "chunk_batch_bf16",
+             lambda: chunk_batch_leg(bf, torch, dev, stream, storage="bf16"))]
+    for flag, name, fn in only:
+        if flag:
+            if rank == 0:
+                print(json.dumps({name: fn()}), flush=True)
+            return
+
+    prob, prm = workload(args.chunks)
+    intr = prob.intr
+    lists = [c.tolist() for c in prob.chunks]
+    cids = list(range(len(lists)))
+    all_ids = list(range(prob.n_frames))
+    precision = bf.BF_PREC_FP32 if args.precision == "fp32" else bf.BF_PREC_MIXED
+    common = {k: prm[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
+    params = bf.default_params(precision=precision, use_graph=0 if args.no_graph else 1, tile_px=args.tile_px,
+                               pcg_variant=args.pcg_variant, **common)
+    storage = STORAGE_CODES[args.storage](bf)
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
+                     stream=stream.cuda_stream, max_frames_hint=prob.n_frames, storage=storage)
+    depth_d = torch.from_numpy(prob.depth).to(dev)
+    lum_d = torch.from_numpy(prob.lum).to(dev)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                  torch.from_numpy(prob.p_j).to(dev))
+    torch.cuda.synchronize(dev)
+    gn_per_step = prm["n_gn"] * len(lists)
+
+    def step(p=params):
+        ctx.add_frames(0, depth_d, lum_d)
+        return ctx.solve_local_batch(cids, lists, p)
+
+    def timed(fn, k, profile=False):
+        times = []
+        if profile:
+            ctx.reset_profile()
+            ctx.set_profiling(True)
+        out = None
+        for _ in range(k):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        prof = None
+        if profile:
+            prof = ctx.profile()
+            ctx.set_profiling(False)
+        return times, out, prof
+
+    t_w = time.perf_counter()
+    for _ in range(args.warmup):
+        stats = step()
+    torch.cuda.synchronize(dev)
+    warm_steps = args.warmup
+    # then untimed steps until WARMUP_MIN_S has passed (the first runs after an idle period run slow)
+    while not args.profile_run and time.perf_counter() - t_w < WARMUP_MIN_S:
+        stats = step()
+        warm_steps += 1
+    torch.cuda.synchronize(dev)
+    t_w = time.perf_counter() - t_w
+    clocks = None if args.profile_run else Clocks(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+    ctx.reset_profile()
+    times, stats, _ = timed(step, args.steps)
+    launches = ctx.profile()["launches"]
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    total_ms = max_over_ranks(sum(times), dist)
+    value = job_rate(gn_per_step, args.steps, world, total_ms)
+    if args.profile_run:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "value": value, "ms_per_step": total_ms / args.steps}))
+        return
+
+    # per-kernel device times: a pass kernel by kernel with CUDA events around every launch on the
+    # context's stream (the graph replay above carries no events); same decomposition as the graph
+    prof_params = bf.default_params(precision=precision, use_graph=0, tile_px=args.tile_px,
+                                    pcg_variant=args.pcg_variant, **common)
+    _, _, prof = timed(lambda: step(prof_params), 2, profile=True)
+    tuned = ctx.tuned_tile_px() if args.tile_px == bf.BF_TILE_AUTOTUNE else args.tile_px
+    HW = intr["W"] * intr["H"]
+    n_dp = 2 * sum(st["n_dense_pairs"] for st in stats)
+    dense = prof["kernels"]["dense"]
+    dense_ms = dense["ms"] / max(dense["count"], 1)
+    units = n_dp * HW
+    alg_bytes = dense_bytes_per_px(args.storage) * units
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "of measured (MEASURED_PEAKS.json hbm_gbs: copy bandwidth)"
+    if hbm_peak is None:
+        hbm_peak, peak_src = 6400.0, "of fallback (6.4 TB/s)"
+    achieved = alg_bytes / (dense_ms / 1000.0) / 1e9
+    flops = DENSE_FLOPS_PER_PX * units
+    achieved_tf = flops / (dense_ms / 1000.0) / 1e12
+    traffic = DENSE_TRAFFIC_BYTES_CHUNKS if (args.storage == "fp32" and args.tile_px == bf.BF_TILE_AUTOTUNE) else None
+    tot = sum(v["ms"] for v in prof["kernels"].values())
+    kernel_share = {k: round(v["ms"] / max(tot, 1e-9), 4) for k, v in prof["kernels"].items() if v["count"]}
+    lat_ms = [t for t in times]  # every chunk of a step completes with its batch: its latency is the step
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(prob, prm, args.storage, args.precision, cuda_graph=not args.no_graph,
+                                      directed_dense_pairs=n_dp, tile_px=tuned, warmup_steps_run=warm_steps,
+                                      warmup_s=round(t_w, 3), warmup_min_s=WARMUP_MIN_S,
+                                      parallelism=f"replicas x{world}"),
+            "gpu_launches": launches,
+            "chunk_latency": {"batched_p50_ms": quantile(lat_ms, 0.5), "batched_p99_ms": quantile(lat_ms, 0.99),
+                              "note": "batched: every chunk of a step completes with its batch (call -> results "
+                                      "on the host), so its latency is the step time; quantiles over the steps"},
+            "roofline": {"bound": "hbm", "kernel": "k_dense (tiled, accumulate + final energy launches)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "traffic": traffic, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "bytes_per_directed_px": dense_bytes_per_px(args.storage), "directed_px_per_launch": units,
+                         "avg_launch_ms": dense_ms, "launches_timed": dense["count"],
+                         "note": "achieved = algorithmic bytes (source D, n, I; target D, n nearest; I, grad I "
+                                 "bilinear) per launch / CUDA-event launch time; traffic = ncu DRAM bytes per launch"},
+            "roofline_fp32_view": {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": achieved_tf / FP32_PEAK_TFLOPS, "flops_per_directed_px": DENSE_FLOPS_PER_PX,
+                                   "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 flop x 2.032 GHz"},
+            "kernel_time_share": kernel_share,
+            "energy": {"initial_sum": sum(st["energy"][0] for st in stats),
+                       "final_sum": sum(st["energy"][-1] for st in stats)}}
+    if clk:
+        line["clocks"] = clk
+
+    if not args.no_extras and rank == 0:
+        line["e2e"] = chunk_e2e_leg(bf, torch, ctx, prob, stream, cids, lists, params, all_ids, timed,
+                                    max(3, args.steps // 2))
+        # restore the device-resident correspondences
+        ctx.clear_correspondences()
+        ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                      torch.from_numpy(prob.p_j).to(dev))
+        line["plain_fp32"] = chunk_plain_leg(bf, torch, ctx, dev, prob, depth_d, lum_d, cids, lists, common,
+                                             gn_per_step, stream)
+        line["persistent"] = chunk_persistent_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn_per_step,
+                                                  stats, stream)
+        ctx.close()
+        line["bf16_storage"] = chunk_batch_leg(bf, torch, dev, stream, prob=prob, storage="bf16")
+        line["global300"] = global300_leg(bf, torch, dev, stream, args)
+        line["large_global"] = large_global_leg(bf, torch, dev, stream)
+        line["serving"] = serving_leg(bf, torch, dev, chunk_prob=prob, seconds=args.serving_seconds)
+        line["next_rows"] = next_rows_leg(bf, torch, dev, stream)
+        line["chunk11_latency"] = chunk_latency(bf, torch, dev)
+        line["cpu_baseline"] = cpu_baseline_leg(prob, prm)
+    else:
+        ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def chunk_e2e_leg(bf, torch, ctx, prob, stream, cids, lists, params, all_ids, timed, steps):
+    """The batch end to end through the C ABI from pinned host buffers: every step uploads the raw
+    frames and the correspondences, solves, and reads every frame's pose back."""
+    depth_h = torch.from_numpy(prob.depth).pin_memory()
+    lum_h = torch.from_numpy(prob.lum).pin_memory()
+    pi_h = torch.from_numpy(prob.p_i).pin_memory()
+    pj_h = torch.from_numpy(prob.p_j).pin_memory()
+
+    def step_e2e():
+        ctx.add_frames(0, depth_h, lum_h)
+        ctx.clear_correspondences()
+        ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_h, pj_h)
+        s = ctx.solve_local_batch(cids, lists, params)
+        ctx.get_poses(all_ids)
+        return s
+
+    for _ in range(2):
+        step_e2e()
+    te, _, _ = timed(step_e2e, steps)
+    h2d = prob.depth.nbytes + prob.lum.nbytes + prob.p_i.nbytes + prob.p_j.nbytes + prob.pairs.nbytes + \
+        prob.corr_off.nbytes
+    d2h = prob.n_frames * 16 * 8
+    gn = params.n_gn * len(lists)
+    return {"value": gn / (statistics.mean(te) / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(te),
+            "note": "pinned host depth, luminance and correspondences uploaded, poses of all frames read back, "
+                    "every step; per-chunk statistics also come back each step"}
+
+
+def chunk_plain_leg(bf, torch, ctx, dev, prob, depth_d, lum_d, cids, lists, common, gn_per_step, stream, steps=2):
+    """The plain path: one FP32 solve per chunk, kernel by kernel (no batching, no graph); chunk-solve
+    latency = call -> poses on the host."""
+    pp = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, **common)
+    lat, tot = [], []
+    for rep in range(steps + 1):
+        ctx.add_frames(0, depth_d, lum_d)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for cid, lst in zip(cids, lists):
+            t1 = time.perf_counter()
+            ctx.solve_local(cid, lst, pp)
+            ctx.get_poses(lst)
+            if rep:
+                lat.append(1000.0 * (time.perf_counter() - t1))
+        if rep:
+            tot.append(time.perf_counter() - t0)
+    return {"value": gn_per_step / statistics.mean(tot), "unit": UNIT, "ms_per_step": 1000.0 * statistics.mean(tot),
+            "solves_per_s": len(lists) / statistics.mean(tot), "chunk_latency_p50_ms": quantile(lat, 0.5),
+            "chunk_latency_p99_ms": quantile(lat, 0.99), "precision": "fp32", "cuda_graph": False,
+            "note": "same chunks, one bf_solve_local per chunk (host clock around each call)"}
+
+
+# tiles of half a 320x240 frame for the persistent launch (the fastest of 19200 / 38400 / 76800 there)
+PERSISTENT_TILE_PX = 38400
+
+
+def chunk_persistent_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn_per_step, ref_stats, stream,
+                         steps=3):
+    """The same batch as ONE persistent cooperative launch over a device work queue."""
+    pk = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, tile_px=PERSISTENT_TILE_PX, persistent=1, **common)
+
+    def run():
+        ctx.add_frames(0, depth_d, lum_d)
+        return ctx.solve_local_batch(cids, lists, pk)
+
+    run()
+    ts = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sk = run()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return {"value": gn_per_step / (statistics.mean(ts) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(ts),
+            "launches_per_solve": 1, "tile_px": PERSISTENT_TILE_PX, "cuda_graph": True,
+            "final_energy_max_rel_diff_vs_launch_sequence": max(
+                abs(a["energy"][-1] - b["energy"][-1]) / abs(b["energy"][-1]) for a, b in zip(sk, ref_stats))}
+
+
+def global300_leg(bf, torch, dev, stream, args, steps=10, warmup=3):
+    """The 300-keyframe 80x60 global solve (8 GN x 20 PCG, mixed precision, CUDA graph; its frames
+    fit in L2): GN iterations/s, end to end from host buffers, the plain FP32 path, BF16 storage,
+    the dense kernel's FP32 and algorithmic-byte rates, the matrix-free sparse term."""
+    import synth
+    prob = synth.cfg2()
+    prm = prob.solve
     intr = prob.intr
     n = prob.n_frames
     ids = list(range(n))
-    if args.large_only:
-        stream = torch.cuda.Stream(dev)
-        torch.cuda.set_stream(stream)
-        if rank == 0:
-            print(json.dumps({"large_global": large_global_leg(bf, torch, dev, stream)}), flush=True)
-        return
-    if args.batch_only:
-        stream = torch.cuda.Stream(dev)
-        torch.cuda.set_stream(stream)
-        if rank == 0:
-            import synth
-            cprob = synth.cfg3()
-            print(json.dumps({"chunk_batch": chunk_batch_leg(bf, torch, dev, stream, prob=cprob),
-                              "chunk_batch_bf16": chunk_batch_leg(bf, torch, dev, stream, prob=cprob,
-                                                                  storage="bf16")}), flush=True)
-        return
-    if args.next_rows_only:
-        stream = torch.cuda.Stream(dev)
-        torch.cuda.set_stream(stream)
-        if rank == 0:
-            print(json.dumps({"next_rows": next_rows_leg(bf, torch, dev, stream, prob, prm)}), flush=True)
-        return
-    precision = bf.BF_PREC_MIXED if args.precision == "mixed" else bf.BF_PREC_FP32
-    params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
-                               w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
-                               precision=precision, pcg_variant=args.pcg_variant, use_graph=0 if args.no_graph else 1,
-                               tile_px=args.tile_px)
-    prof_params = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
-                                    w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
-                                    precision=precision, pcg_variant=args.pcg_variant, use_graph=0,
-                                    tile_px=args.tile_px)
-    stream = torch.cuda.Stream(dev)  # the library and the timing events share this stream
-    torch.cuda.set_stream(stream)
-    storage = STORAGE_CODES[args.storage](bf)
-    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
-                     stream=stream.cuda_stream, max_frames_hint=n, storage=storage)
+    common = {k: prm[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
+    params = bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=1, tile_px=0, **common)
+    prof_params = bf.default_params(precision=bf.BF_PREC_MIXED, use_graph=0, tile_px=0, **common)
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], stream=stream.cuda_stream,
+                     max_frames_hint=n)
     depth_d = torch.from_numpy(prob.depth).to(dev)
     lum_d = torch.from_numpy(prob.lum).to(dev)
     pi_d = torch.from_numpy(prob.p_i).to(dev)
     pj_d = torch.from_numpy(prob.p_j).to(dev)
     ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_d, pj_d)
-    torch.cuda.synchronize(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 126 MB L2
 
     def step(p=params):
@@ -393,148 +683,66 @@ def run_ours(args, rank, world, local_rank):
             ctx.set_profiling(False)
         return times, out, prof
 
-    for _ in range(args.warmup):
-        st = step()
-    torch.cuda.synchronize(dev)
-    # then more untimed steps until WARMUP_MIN_S has passed: W steps of this solve take ~10 ms,
-    # too short for the GPU and host to settle after an idle period
     t_w = time.perf_counter()
-    while not args.profile_run and time.perf_counter() - t_w < WARMUP_MIN_S:
-        st = step()
-        torch.cuda.synchronize(dev)
-    clocks = None if args.profile_run else Clocks(local_rank)
-    if dist is not None:
-        dist.barrier()
+    for _ in range(warmup):
+        step()
+    while time.perf_counter() - t_w < WARMUP_MIN_S:
+        step()
     torch.cuda.synchronize(dev)
-    if clocks:
-        clocks.start()
-    t_wall = time.perf_counter()
-    ctx.reset_profile()
-    times, st, _ = timed(step, args.steps)
-    launches = ctx.profile()["launches"]
-    torch.cuda.synchronize(dev)
-    if dist is not None:
-        dist.barrier()
-    t_wall = time.perf_counter() - t_wall
-    clk = clocks.stop() if clocks else None
-    total_ms = max_over_ranks(sum(times), dist)
+    times, st, _ = timed(step, steps)
+    _, _, prof = timed(lambda: step(prof_params), 3, profile=True)
     n_gn = prm["n_gn"]
-    value = job_rate(n_gn, args.steps, world, total_ms)
-    if args.profile_run:
-        if rank == 0:
-            print(json.dumps({"profile_run": True, "value": value, "ms_per_step": total_ms / args.steps}))
-        return
-
-    # per-kernel device times: a second pass, kernel by kernel, CUDA events around every launch on
-    # the context's stream (the graph replay above carries no events)
-    _, _, prof = timed(lambda: step(prof_params), max(3, args.steps // 2), profile=True)
-    # roofline of the dominant kernel (dense term, ACCUM launches): FP32 flops per launch / event time
     n_dp = 2 * st["n_dense_pairs"]
     HW = intr["W"] * intr["H"]
     dense = prof["kernels"]["dense"]
     dense_ms = dense["ms"] / max(dense["count"], 1)
     units = n_dp * HW
-    flops = DENSE_FLOPS_PER_PX * units
-    alg_bytes = dense_bytes_per_px(args.storage) * units
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    hbm_peak = peaks.get("hbm_gbs", 6400.0)
-    achieved_tf = flops / (dense_ms / 1000.0) / 1e12
-    achieved_gbs = alg_bytes / (dense_ms / 1000.0) / 1e9
-    gpu_launches = launches
-    # the captured DRAM traffic belongs to the default configuration's dense kernel only
-    traffic = DENSE_TRAFFIC_BYTES if (args.storage == "fp32" and args.tile_px == 0) else None
-    kernel_share = {k: round(v["ms"] / max(sum(x["ms"] for x in prof["kernels"].values()), 1e-9), 4)
-                    for k, v in prof["kernels"].items() if v["count"]}
+    out = {"workload": prob.name, "keyframes": n, "resolution": f"{intr['W']}x{intr['H']}",
+           "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"], "correspondences": prob.n_corr,
+           "n_gn": n_gn, "n_pcg": prm["n_pcg"], "precision": "mixed", "cuda_graph": True,
+           "value": n_gn / (statistics.mean(times) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(times),
+           "l2": "256 MB buffer written between timed steps (inputs < L2)",
+           "initial_energy": st["energy"][0], "final_energy": st["energy"][-1],
+           "dense_kernel": {"kernel": "k_dense_staged", "avg_launch_ms": dense_ms, "directed_px_per_launch": units,
+                            "fp32_TFLOPs": DENSE_FLOPS_PER_PX * units / (dense_ms / 1000.0) / 1e12,
+                            "fp32_frac": DENSE_FLOPS_PER_PX * units / (dense_ms / 1000.0) / 1e12 / FP32_PEAK_TFLOPS,
+                            "algorithmic_GBps": DENSE_BYTES_PER_PX * units / (dense_ms / 1000.0) / 1e9,
+                            "traffic": DENSE_TRAFFIC_BYTES,
+                            "note": "frames L2-resident: DRAM traffic is the unique frame bytes"},
+           "kernel_time_share": {k: round(v["ms"] / max(sum(x["ms"] for x in prof["kernels"].values()), 1e-9), 4)
+                                 for k, v in prof["kernels"].items() if v["count"]}}
+    # end to end from pinned host buffers
+    depth_h = torch.from_numpy(prob.depth).pin_memory()
+    lum_h = torch.from_numpy(prob.lum).pin_memory()
+    pi_h = torch.from_numpy(prob.p_i).pin_memory()
+    pj_h = torch.from_numpy(prob.p_j).pin_memory()
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": prob.name, "keyframes": n, "resolution": f"{intr['W']}x{intr['H']}",
-                       "cuda_graph": not args.no_graph, "tile_px": args.tile_px,
-                       "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"],
-                       "directed_dense_pairs": n_dp, "correspondences": prob.n_corr, "n_gn": n_gn,
-                       "n_pcg": prm["n_pcg"], "precision": args.precision, "storage": args.storage,
-                       "l2": "256 MB buffer written between timed steps (inputs < L2)",
-                       "warmup_min_s": WARMUP_MIN_S,
-                       "parallelism": f"replicas x{world}"},
-            "gpu_launches": gpu_launches,
-            "roofline": {"bound": "alu", "kernel": "k_dense", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
-                         "traffic": traffic, "avg_launch_ms": dense_ms,
-                         "flops_per_launch": flops, "flops_per_directed_px": DENSE_FLOPS_PER_PX,
-                         "directed_px_per_launch": units,
-                         "peak_source": "derived FP32 peak: 148 SMs x 128 lanes x 2 flop x 2.032 GHz"},
-            "roofline_hbm_view": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                                  "frac": achieved_gbs / hbm_peak, "traffic": traffic,
-                                  "algorithmic_bytes_per_launch": alg_bytes,
-                                  "note": f"{dense_bytes_per_px(args.storage)} B per directed source pixel; "
-                                          "the frames stay in L2, so DRAM traffic is the unique frame bytes "
-                                          "(of measured)"},
-            "kernel_time_share": kernel_share,
-            "final_energy": st["energy"][-1], "initial_energy": st["energy"][0]}
-    if clk:
-        line["clocks"] = clk
-
-    if not args.no_extras and rank == 0:
-        # e2e through the public API with host (pinned) buffers
-        depth_h = torch.from_numpy(prob.depth).pin_memory()
-        lum_h = torch.from_numpy(prob.lum).pin_memory()
-        pi_h = torch.from_numpy(prob.p_i).pin_memory()
-        pj_h = torch.from_numpy(prob.p_j).pin_memory()
-
-        def step_e2e():
-            ctx.add_frames(0, depth_h, lum_h, init_pose=prob.init)
-            ctx.clear_correspondences()
-            ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_h, pj_h)
-            s = ctx.solve_global(ids, params)
-            ctx.get_poses(ids)
-            return s
-
-        for _ in range(2):
-            step_e2e()
-        te, _, _ = timed(step_e2e, max(3, args.steps // 2))
-        h2d = prob.depth.nbytes + prob.lum.nbytes + 2 * 16 * prob.n_corr + prob.init.nbytes
-        d2h = n * 16 * 8 + n * 12 * 8
-        line["e2e"] = {"value": n_gn / (statistics.mean(te) / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": statistics.mean(te)}
-        # restore device-resident correspondences
+    def step_e2e():
+        ctx.add_frames(0, depth_h, lum_h, init_pose=prob.init)
         ctx.clear_correspondences()
-        ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_d, pj_d)
+        ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_h, pj_h)
+        s = ctx.solve_global(ids, params)
+        ctx.get_poses(ids)
+        return s
 
-        # plain FP32 one-solve-per-launch path on the same workload
-        plain = bf.default_params(n_gn=prm["n_gn"], n_pcg=prm["n_pcg"], w_sparse=prm["w_sparse"],
-                                  w_dense=prm["w_dense"], w_photo=prm["w_photo"], w_geo=prm["w_geo"],
-                                  precision=bf.BF_PREC_FP32)
-        for _ in range(2):
-            step(plain)
-        tp, stp, _ = timed(lambda: step(plain), max(3, args.steps // 2))
-        line["plain_fp32"] = {"value": n_gn / (statistics.mean(tp) / 1000.0), "unit": UNIT,
-                              "ms_per_step": statistics.mean(tp), "final_energy": stp["energy"][-1]}
-
-        # Sec. 4.4's matrix-free sparse term (J p, then J^T (J p) every PCG iteration) against the
-        # sparse 6x6 blocks assembled once per GN iteration, both on the grid-cooperative PCG kernel
-        line["sparse_term"] = sparse_term_leg(bf, step, timed, prm, precision, max(3, args.steps // 2))
-
-        # the same global solve on 16-bit frame storage
-        if args.storage == "fp32":
-            line["bf16_storage"] = storage_leg(bf, torch, dev, stream, prob, params, prof_params, "bf16")
-
-        line["chunk_latency"] = chunk_latency(bf, torch, dev)
-        import synth
-        cprob = synth.cfg3()
-        line["chunk_batch"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob)
-        line["chunk_batch_bf16"] = chunk_batch_leg(bf, torch, dev, stream, prob=cprob, storage="bf16")
-        line["serving"] = serving_leg(bf, torch, dev, cprob, prob)
-
-        line["next_rows"] = next_rows_leg(bf, torch, dev, stream, prob, prm)
-        line["large_global"] = large_global_leg(bf, torch, dev, stream)
-
-        v, desc, cores = oracle_gn_iteration_rate(prob, prm, budget_s=15.0)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    for _ in range(2):
+        step_e2e()
+    te, _, _ = timed(step_e2e, 5)
+    out["e2e"] = {"value": n_gn / (statistics.mean(te) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(te),
+                  "h2d_bytes_per_step": int(prob.depth.nbytes + prob.lum.nbytes + 2 * 16 * prob.n_corr +
+                                            prob.init.nbytes), "d2h_bytes_per_step": n * 16 * 8 + n * 12 * 8}
+    ctx.clear_correspondences()
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_d, pj_d)
+    plain = bf.default_params(precision=bf.BF_PREC_FP32, **common)
+    for _ in range(2):
+        step(plain)
+    tp, stp, _ = timed(lambda: step(plain), 5)
+    out["plain_fp32"] = {"value": n_gn / (statistics.mean(tp) / 1000.0), "unit": UNIT,
+                         "ms_per_step": statistics.mean(tp), "final_energy": stp["energy"][-1]}
+    out["sparse_term"] = sparse_term_leg(bf, step, timed, prm, bf.BF_PREC_MIXED, 5)
     ctx.close()
+    out["bf16_storage"] = storage_leg(bf, torch, dev, stream, prob, params, prof_params, "bf16")
+    return out
 
 
 def sparse_term_leg(bf, step, timed, prm, precision, steps):
@@ -606,7 +814,7 @@ def storage_leg(bf, torch, dev, stream, prob, params, prof_params, kind, steps=5
 
 
 
-def next_rows_leg(bf, torch, dev, stream, prob, prm):
+def next_rows_leg(bf, torch, dev, stream):
     """The steps around the solver on the 300-keyframe workload (Sec. 4.1.1, 4.4.1, 5).
 
     verify: every pair, both directions, at the ground-truth relative poses (one launch);
@@ -615,6 +823,9 @@ def next_rows_leg(bf, torch, dev, stream, prob, prm):
     so pairs are pruned until the round cap); tsdf: the 300 frames integrated then de-integrated
     (1 cm voxels)."""
     import numpy as np
+    import synth
+    prob = synth.cfg2()
+    prm = prob.solve
     intr = prob.intr
     n = prob.n_frames
     ids = list(range(n))
@@ -739,10 +950,6 @@ def large_global_leg(bf, torch, dev, stream, steps=3, warmup=1):
                              "frame_bytes": n * HW * 18},
             "kernel_time_share": {k: round(v["ms"] / max(tot, 1e-9), 4) for k, v in prof["kernels"].items()
                                   if v["count"]}}
-
-# tiles of half a 320x240 frame for the persistent launch (the fastest of 19200 / 38400 / 76800 there)
-PERSISTENT_TILE_PX = 38400
-
 
 def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, prob=None, storage="fp32"):
     """Batched chunk solves: 256 chunks of U{3..11} frames at 320x240, 6 GN x 10 PCG.
@@ -876,7 +1083,7 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
 SERVING_HBM_BUDGET = 40 * 1024 ** 3
 
 
-def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0, seed=1604):
+def serving_leg(bf, torch, dev, chunk_prob=None, seconds=8.0, rate=30.0, seed=1604):
     """Serving: Poisson arrivals of chunk requests (320x240, 3-11 frames, 6 GN x 10 PCG) at `rate`
     per second for `seconds`, and after every 10th chunk a global request over the first k
     keyframes of the 300-keyframe 80x60 corridor (k grows from 100 to 300; 8 GN x 20 PCG).
@@ -884,6 +1091,9 @@ def serving_leg(bf, torch, dev, chunk_prob, global_prob, seconds=8.0, rate=30.0,
     streams, FP32 chunk arithmetic, FP64-merged global solves); plain: the same arrivals served one
     request at a time by the plain FP32 path (1 slot, batch 1).  Latency = submit -> completion;
     p50 / p99 per request kind."""
+    import synth
+    chunk_prob = chunk_prob or synth.cfg3()
+    global_prob = synth.cfg2()
     rng = np.random.default_rng(seed)
     n_req = int(seconds * rate)
     gaps = rng.exponential(1.0 / rate, size=n_req)

@@ -303,19 +303,25 @@ bf_status bf_reset_profile(bf_ctx *ctx);
 /*
  * Dense normal-equation blocks of one frame pair, computed without allocating device memory.
  * The paper has no counterpart: this entry point exists for callers that cannot allocate at the
- * point of use (code running while another component captures its stream into a CUDA graph,
- * real-time loops that cannot afford cudaMalloc's implicit device-wide synchronisation, hosts
- * whose memory manager already owns the device memory).  No context is involved and nothing is
- * allocated: intermediates live in one fixed device array built into the library (about 1.25 MB
- * per device, held until exit).
- *   width, height: at most 160 x 120 (larger sizes return BF_ERR_INVALID_ARG);
- *   fx, fy, cx, cy, depth_min, depth_max: as in bf_config;
+ * point of use (real-time loops that cannot afford cudaMalloc's implicit device-wide
+ * synchronisation, hosts whose memory manager already owns the device memory, plugins that are
+ * handed their buffers by the application embedding them).  No context is involved and nothing
+ * is allocated: intermediates live in one fixed device array built into the library (about
+ * 1.25 MB per device, held until exit).
+ *   width, height: 8..160 x 8..120 (anything else returns BF_ERR_INVALID_ARG);
+ *   fx, fy, cx, cy: as in bf_config (fx, fy > 0);  depth_min < depth_max: the validity range;
  *   depth_i, lum_i, depth_j, lum_j: device, H x W float32 each (raw frames);
  *   pose_i, pose_j: host, 16 doubles each (camera -> world);
- *   params: host; uses tau_dist, tau_normal, w_dense, w_photo, w_geo (no ramp, no angle test);
+ *   params: host; uses tau_dist (> 0), tau_normal, w_dense, w_photo, w_geo (finite; no ramp, no
+ *           angle test); anything else about them returns BF_ERR_INVALID_ARG;
  *   out: device, 124 doubles: A_ii, A_ij, A_jj (row-major 6x6), rhs_i, rhs_j (= -J^T W r),
  *        then e_sparse (0), e_photo, e_geo, associated pixels, both directions i->j and j->i;
  *   cuda_stream: cudaStream_t (NULL = legacy default stream); the call only enqueues work.
+ * Errors: argument errors return BF_ERR_INVALID_ARG before any CUDA call.  A CUDA error already
+ * pending on the calling thread (for example from the caller's own failed allocation) makes the
+ * call return BF_ERR_CUDA without enqueuing anything and without clearing that error.  A launch
+ * that fails returns BF_ERR_CUDA at once (the launch error is consumed; work enqueued before it
+ * stays queued).
  * The first call on a device looks up the array's device address: make it before any stream
  * capture.  Every call on a device shares the array and leaves its contents behind; calls whose
  * GPU work overlaps race on it, so order them on one stream.

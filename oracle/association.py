@@ -1,128 +1,162 @@
-"""Dense projective association for a directed frame pair i -> j (oracle).
+"""Dense projective association for a directed frame pair i -> j (oracle, FP64).
 
-Sec. 4.3 (dense matching) maps the 3D point d_ik of source pixel k into frame j
-through T_j^-1 T_i, projects it with pi, reads D_j there, ignores projections
-outside the frame, and prunes ICP-style by distance and normal after each step.
-Readings used (the paper gives no numbers for this pruning):
+TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-* the association is recomputed once per Gauss-Newton iteration at the current
-  poses and held fixed inside the linearisation (projective, "ICP-like");
-* target pixel = nearest pixel (floor(u + 0.5) per axis), inside the image, with
-  valid depth and a valid normal;
-* the photometric term samples I_j and grad I_j bilinearly at u; all 4 taps must
-  lie on the 2-pixel interior where grad I is defined;
-* gates ||T_i d - T_j q|| < tau_d and (R_i n_i).(R_j n_j) > tau_n with the dense
+Sec. 4.3 (dense matching) maps the 3D point d_ik of source pixel k into frame j through
+T_j^-1 T_i, projects it with pi, reads D_j there, ignores projections outside the frame, and
+prunes ICP-style by distance and normal.  Readings used (the paper gives no numbers for this
+pruning):
+
+* the association is recomputed once per Gauss-Newton iteration at the current poses and held
+  fixed inside the linearisation (projective, "ICP-like");
+* y = T_j^-1 T_i d with d = pi^-1(x, y, D_i(x, y)); y_z must be positive;
+* target pixel = nearest pixel of u = pi(y): (floor(u_x + 1/2), floor(u_y + 1/2)), with valid
+  depth and a valid normal, on the 3-pixel interior (3 <= x <= W - 4, 3 <= y <= H - 4);
+* the photometric term samples I_j and grad I_j bilinearly at u from the four pixels around it,
+  (floor(u_x), floor(u_y)) and its +1 neighbours, which the 3-pixel interior of the nearest pixel
+  keeps on the 2-pixel interior where grad I is defined.  (Every threshold on u then sits at a
+  half-integer: an integer projection, as of every pixel of an identity relative pose, at which
+  Sec. 4.2 starts every chunk, is never on one.  A test on the taps themselves would put the
+  thresholds at integers, where identity poses place whole image columns and rows.)
+* gates ||y - q|| < tau_d (q = pi^-1 of the target pixel; the distance of Sec. 4.1.1 between the
+  world points T_i d and T_j q, measured in camera j) and (R n_i) . n_j > tau_n with the dense
   verification constants of Sec. 4.1.1 (tau_d = 0.15 m, tau_n = 0.9);
 * the photometric and geometric residuals share one validity mask;
 * the source pixel needs valid depth and a valid normal.
 
-Every one of these decisions turns a floating-point value into an integer or a
-boolean.  They are taken in IEEE FP32 in the fixed order written below: products, sums and
-fused multiply-adds (one rounding of a*b + c, see fma32), and one correctly rounded
-reciprocal 1/y_z for the projection; the same precision and order as the GPU kernel, so that
-both sides take identical decisions on identical inputs.  The residual values themselves
-(residuals.py) are FP64.
-
-Per directed pair the relative transform M = T_j^-1 T_i is formed in FP64 with
-explicit sums (R = R_j^T R_i, t = R_j^T (t_i - t_j)) and rounded once to FP32.
+Everything here is FP64 from the frames' FP64 planes.  Every decision is a comparison of a
+computed value with a threshold; ``associate`` also returns each pixel's distance to the
+nearest threshold it was compared with (``margin_px`` in pixels for the rounding and interior
+tests, ``margin_d`` in metres for the distance gate, ``margin_n`` for the normal gate),
+so that a caller comparing with an implementation in lower precision can tell a decision that
+sits within that precision's rounding of its threshold (either outcome is correct there) from a
+real disagreement (see ``ties``).
 """
 import numpy as np
 
-f32 = np.float32
+
+def relative_transform(Ri, ti, Rj, tj):
+    """T_j^-1 T_i as (R, t): R = R_j^T R_i, t = R_j^T (t_i - t_j) (FP64)."""
+    Ri, ti, Rj, tj = (np.asarray(v, dtype=np.float64) for v in (Ri, ti, Rj, tj))
+    return Rj.T @ Ri, Rj.T @ (ti - tj)
 
 
-def fma32(a, b, c):
-    """IEEE FP32 fused multiply-add: a*b + c rounded once to nearest (ties to even).
+def associate(fi, fj, M, intr, tau_d=0.15, tau_n=0.9):
+    """Association of every source pixel of frame i into frame j under M = T_j^-1 T_i.
 
-    a, b, c are FP32.  In FP64 the product p = a*b is exact (24 + 24 significant bits);
-    TwoSum gives p + c = s + e exactly with s = fl64(p + c).  Rounding s + e to FP64 "to odd"
-    (s itself if e == 0 or s's last significand bit is odd, else the FP64 neighbour of s in
-    the direction of e) and then to FP32 to nearest is the correctly rounded FP32 result,
-    because FP64 carries at least two bits more than FP32 (Boldo and Melquiond, "Emulation of
-    FMA and correctly rounded sums: proved algorithms using rounding to odd", IEEE TC 2008).
+    fi, fj: frames.Frame; M: (R, t) from relative_transform.  Returns a dict of flat arrays over
+    the source pixels (row-major): valid (bool), nx, ny (nearest target pixel), bx, by (bilinear
+    base tap), ux, uy (the projection), and the decision margins margin_px, margin_d, margin_n
+    (+inf where a test was not reached).
     """
-    a64 = np.asarray(a, dtype=f32).astype(np.float64)
-    b64 = np.asarray(b, dtype=f32).astype(np.float64)
-    c64 = np.asarray(c, dtype=f32).astype(np.float64)
-    p = a64 * b64
-    s = p + c64
-    bb = s - p
-    e = (p - (s - bb)) + (c64 - bb)
-    even = (np.asarray(s).view(np.int64) & 1) == 0
-    with np.errstate(invalid="ignore"):
-        toward = np.where(e > 0, np.inf, -np.inf)
-        s_odd = np.where((e != 0) & even & np.isfinite(s), np.nextafter(s, toward), s)
-    return s_odd.astype(f32)
-
-
-def pair_transform32(Ri, ti, Rj, tj):
-    """FP32 rounding of T_j^-1 T_i, each FP64 entry summed left to right."""
-    R = np.zeros((3, 3))
-    t = np.zeros(3)
-    dt = [ti[0] - tj[0], ti[1] - tj[1], ti[2] - tj[2]]
-    for a in range(3):
-        for b in range(3):
-            R[a, b] = (Rj[0, a] * Ri[0, b] + Rj[1, a] * Ri[1, b]) + Rj[2, a] * Ri[2, b]
-        t[a] = (Rj[0, a] * dt[0] + Rj[1, a] * dt[1]) + Rj[2, a] * dt[2]
-    return R.astype(f32), t.astype(f32)
-
-
-def ray_tables(intr):
-    """kx[x] = fl32((x - cx)/fx), ky[y] = fl32((y - cy)/fy), each computed in FP64 and rounded once."""
+    R, t = (np.asarray(v, dtype=np.float64) for v in M)
     W, H = intr["W"], intr["H"]
-    kx = ((np.arange(W, dtype=np.float64) - intr["cx"]) / intr["fx"]).astype(f32)
-    ky = ((np.arange(H, dtype=np.float64) - intr["cy"]) / intr["fy"]).astype(f32)
-    return kx, ky
-
-
-def associate(fi, fj, M32, intr, tau_d=0.15, tau_n=0.9):
-    """Association of every source pixel of frame i into frame j.
-
-    Returns a dict of flat arrays over the source pixels (row-major):
-      valid (bool), nx, ny (nearest target pixel), bx, by (bilinear base tap).
-    """
-    R, t = M32
-    W, H = intr["W"], intr["H"]
-    kx, ky = ray_tables(intr)
-    fx, fy, cx, cy = f32(intr["fx"]), f32(intr["fy"]), f32(intr["cx"]), f32(intr["cy"])
-    ys, xs = np.divmod(np.arange(W * H), W)
-    z = fi.D32.ravel()
-    n_i = fi.N32.reshape(-1, 3)
-    ok = fi.valid.ravel() & fi.nvalid.ravel()
-    # camera-space source point (rounded products), then y = R d + t as fused multiply-adds
-    # accumulated from t: y_a = fma(R_a2, d_z, fma(R_a1, d_y, fma(R_a0, d_x, t_a)))
-    dx = kx[xs] * z
-    dy = ky[ys] * z
-    dz = z
-    Y = [fma32(R[a, 2], dz, fma32(R[a, 1], dy, fma32(R[a, 0], dx, t[a]))) for a in range(3)]
-    ok &= Y[2] > f32(0)
-    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
-        iz = f32(1) / np.where(ok, Y[2], f32(1))
-        ux = fma32(fx, Y[0] * iz, cx)
-        uy = fma32(fy, Y[1] * iz, cy)
-    ux = np.where(ok, ux, f32(-100))
-    uy = np.where(ok, uy, f32(-100))
-    nxf = np.floor(ux + f32(0.5))
-    nyf = np.floor(uy + f32(0.5))
-    ok &= (nxf >= 0) & (nxf <= W - 1) & (nyf >= 0) & (nyf <= H - 1)
+    fx, fy, cx, cy = (float(intr[k]) for k in ("fx", "fy", "cx", "cy"))
+    n_px = W * H
+    ys, xs = np.divmod(np.arange(n_px), W)
+    z = fi.D.ravel()
+    d = np.stack([(xs - cx) * z / fx, (ys - cy) * z / fy, z], axis=1)
+    y = d @ R.T + t
+    ok = fi.valid.ravel() & fi.nvalid.ravel() & (y[:, 2] > 0)
+    yz = np.where(ok, y[:, 2], 1.0)
+    ux = np.where(ok, fx * y[:, 0] / yz + cx, -100.0)
+    uy = np.where(ok, fy * y[:, 1] / yz + cy, -100.0)
+    margin_px = np.full(n_px, np.inf)
+    margin_d = np.full(n_px, np.inf)
+    margin_n = np.full(n_px, np.inf)
+    # nearest pixel on the 3-pixel interior; the rounding boundaries (u + 1/2 an integer) include
+    # the interior's edges 2.5 and W - 3.5
+    nxf = np.floor(ux + 0.5)
+    nyf = np.floor(uy + 0.5)
+    mr = np.minimum(np.abs(ux + 0.5 - np.round(ux + 0.5)), np.abs(uy + 0.5 - np.round(uy + 0.5)))
+    margin_px = np.where(ok, mr, margin_px)
+    ok &= (nxf >= 3) & (nxf <= W - 4) & (nyf >= 3) & (nyf <= H - 4)
+    # bilinear base tap; floor(u) >= nearest - 1 >= 2 and floor(u) + 1 <= nearest + 1 <= W - 3
     bxf = np.floor(ux)
     byf = np.floor(uy)
-    ok &= (bxf >= 2) & (bxf + 1 <= W - 3) & (byf >= 2) & (byf + 1 <= H - 3)
     nx = np.where(ok, nxf, 0).astype(np.int64)
     ny = np.where(ok, nyf, 0).astype(np.int64)
     bx = np.where(ok, bxf, 0).astype(np.int64)
     by = np.where(ok, byf, 0).astype(np.int64)
     tgt = ny * W + nx
     ok &= fj.valid.ravel()[tgt] & fj.nvalid.ravel()[tgt]
-    Dj = fj.D32.ravel()[tgt]
-    qx = kx[nx] * Dj
-    qy = ky[ny] * Dj
-    qz = Dj
-    ex, ey, ez = Y[0] - qx, Y[1] - qy, Y[2] - qz
-    dist2 = fma32(ez, ez, fma32(ey, ey, ex * ex))
-    ok &= dist2 < f32(tau_d * tau_d)
-    m = [fma32(R[a, 2], n_i[:, 2], fma32(R[a, 1], n_i[:, 1], R[a, 0] * n_i[:, 0])) for a in range(3)]
-    n_j = fj.N32.reshape(-1, 3)[tgt]
-    dot = fma32(m[2], n_j[:, 2], fma32(m[1], n_j[:, 1], m[0] * n_j[:, 0]))
-    ok &= dot > f32(tau_n)
-    return dict(valid=ok, nx=nx, ny=ny, bx=bx, by=by)
+    Dj = fj.D.ravel()[tgt]
+    q = np.stack([(nx - cx) * Dj / fx, (ny - cy) * Dj / fy, Dj], axis=1)
+    dist = np.sqrt(np.sum((y - q) ** 2, axis=1))
+    margin_d = np.where(ok, np.abs(dist - tau_d), margin_d)
+    ok &= dist < tau_d
+    ndot = np.sum((fi.N.reshape(-1, 3) @ R.T) * fj.N.reshape(-1, 3)[tgt], axis=1)
+    margin_n = np.where(ok, np.abs(ndot - tau_n), margin_n)
+    ok &= ndot > tau_n
+    return dict(valid=ok, nx=nx, ny=ny, bx=bx, by=by, ux=ux, uy=uy,
+                margin_px=margin_px, margin_d=margin_d, margin_n=margin_n)
+
+
+def targets(asc, W):
+    """Flat target index per source pixel, -1 where the pixel has no association."""
+    return np.where(asc["valid"], asc["ny"] * W + asc["nx"], -1)
+
+
+def ties(asc, eps_px, eps_d, eps_n):
+    """Pixels whose outcome depends on a comparison within (eps_px, eps_d, eps_n) of its threshold.
+
+    Any decision taken on such a pixel by an evaluation whose rounding error stays below those
+    bounds is as correct as this one; everywhere else both must agree."""
+    return (asc["margin_px"] < eps_px) | (asc["margin_d"] < eps_d) | (asc["margin_n"] < eps_n)
+
+
+def replay(asc_own, target, W, H):
+    """An association with the decisions given by ``target`` (flat target index or -1 per source
+    pixel, e.g. another implementation's) and this oracle's own projection for the bilinear taps.
+
+    Used to compare residual and normal-equation arithmetic on identical decisions; the given
+    decisions must first be checked against ``asc_own`` (they may differ only on ties)."""
+    target = np.asarray(target).ravel()
+    valid = target >= 0
+    ny, nx = np.divmod(np.where(valid, target, 0), W)
+    # the base tap of a pixel that another evaluation kept next to the interior's edge may round to
+    # the other side here; clamping moves it by one pixel, where the bilinear weight is within
+    # rounding of 0 or 1 and the interpolated value is the same
+    bx = np.where(valid, np.clip(np.floor(np.where(valid, asc_own["ux"], 2.0)), 2, W - 4), 0).astype(np.int64)
+    by = np.where(valid, np.clip(np.floor(np.where(valid, asc_own["uy"], 2.0)), 2, H - 4), 0).astype(np.int64)
+    return dict(valid=valid, nx=nx.astype(np.int64), ny=ny.astype(np.int64), bx=bx, by=by,
+                ux=asc_own["ux"], uy=asc_own["uy"])
+
+
+# Rounding-error bounds of an FP32 evaluation of the decisions above, at the workloads' scales
+# (depths 0.1-10 m, focal lengths up to 262.5 px, relative motions of metres): the projection u
+# within EPS_PX pixels, the distance ||y - q|| within EPS_D metres and the normal cosine within
+# EPS_N (FP32 normals from central differences of FP32 points: the cancellation of
+# P(x+1) - P(x-1) leaves ~1e-5).  A decision whose margin is below its bound is a tie.
+EPS_PX, EPS_D, EPS_N = 5e-4, 2e-5, 2e-4
+
+
+class CheckedReplay:
+    """Association provider for system.assemble that replays another implementation's decisions.
+
+    fetch(i, j, poses) returns that implementation's flat target index (or -1) per source pixel of
+    the directed pair i -> j at the given poses.  Each call checks it against this oracle's own
+    decisions: they may differ only on ties (AssertionError otherwise).  Counts the valid pixels
+    (of the oracle's association) and the differing decisions (flips) over all calls."""
+
+    def __init__(self, fetch, W, H, eps=(EPS_PX, EPS_D, EPS_N)):
+        self.fetch, self.W, self.H, self.eps = fetch, W, H, eps
+        self.n_valid = 0
+        self.n_flips = 0
+        self.calls = 0
+
+    def __call__(self, i, j, poses, own):
+        target = np.asarray(self.fetch(i, j, poses)).ravel()
+        ref = targets(own, self.W)
+        diff = target != ref
+        bad = np.flatnonzero(diff & ~ties(own, *self.eps))
+        if len(bad):
+            k = bad[0]
+            raise AssertionError(
+                f"pair {i}->{j}: {len(bad)} decisions differ outside the rounding bounds; first at pixel {k}: "
+                f"other {target[k]}, oracle {ref[k]} (u = {own['ux'][k]:.6f}, {own['uy'][k]:.6f}; margins "
+                f"{own['margin_px'][k]:.3g} px, {own['margin_d'][k]:.3g} m, {own['margin_n'][k]:.3g})")
+        self.n_valid += int((ref >= 0).sum())
+        self.n_flips += int(diff.sum())
+        self.calls += 1
+        return replay(own, target, self.W, self.H)

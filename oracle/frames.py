@@ -115,10 +115,28 @@ class Frame:
             self.N = round_to_storage(self.N, storage)
             self.I, self.Ix, self.Iy = (round_to_storage(v, storage) for v in (self.I, self.Ix, self.Iy))
             self.C = round_to_storage(self.C, storage)
-        # FP32 copies for the association decisions (see association.py)
+        # FP32 depth and intensity: the inputs of the TSDF oracle (tsdf.py), which takes its
+        # quantised decisions in FP32
         self.D32 = self.D.astype(np.float32)
-        self.N32 = self.N.astype(np.float32)
         self.C32 = self.C.astype(np.float32)
+
+
+class FrameCache:
+    """Frames built on first use from raw depth / luminance arrays and kept (frame id -> Frame)."""
+
+    def __init__(self, depth, lum, intr, depth_min=0.1, depth_max=10.0, storage=None):
+        self.depth, self.lum, self.intr = depth, lum, intr
+        self.args = (depth_min, depth_max, storage)
+        self.cache = {}
+
+    def __getitem__(self, k):
+        k = int(k)
+        if k not in self.cache:
+            self.cache[k] = Frame(self.depth[k], self.lum[k], self.intr, *self.args)
+        return self.cache[k]
+
+    def __len__(self):
+        return len(self.depth)
 
 
 def preprocess(problem_depth, problem_lum, intr, depth_min=0.1, depth_max=10.0, storage=None):

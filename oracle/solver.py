@@ -117,14 +117,17 @@ class GNResult:
     pcg_iters: list
 
 
-def gauss_newton(frames, intr, poses0, sparse_pairs, params: SolveParams, direct=False):
-    """Sec. 4.4 Gauss-Newton: n_gn linearisations, each solved by PCG (or Cholesky if direct)."""
+def gauss_newton(frames, intr, poses0, sparse_pairs, params: SolveParams, direct=False, assoc=None, pmap=None):
+    """Sec. 4.4 Gauss-Newton: n_gn linearisations, each solved by PCG (or Cholesky if direct).
+
+    assoc, pmap: optional association provider (replayed decisions) and parallel map over the
+    directed pairs, passed to system.assemble."""
     poses = np.array(poses0, dtype=np.float64)
     dense_pairs = system.dense_pair_set(poses, sparse_pairs, params.max_angle_deg) if params.dense_on else []
     res = GNResult(None, [], [], [], [], [], [], [poses.copy()], 0.0, (-1, -1), [])
     for k in range(params.n_gn):
         wd = params.w_dense_at(k)
-        S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd)
+        S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd, assoc, pmap)
         res.energy.append(S.energy)
         res.e_sparse.append(S.e_sparse)
         res.e_geo.append(S.e_geo)
@@ -141,7 +144,7 @@ def gauss_newton(frames, intr, poses0, sparse_pairs, params: SolveParams, direct
         poses = apply_step(poses, delta)
         res.pose_history.append(poses.copy())
     wd = params.w_dense_at(params.n_gn - 1) if params.n_gn > 0 else params.w_dense
-    S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd)
+    S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd, assoc, pmap)
     res.energy.append(S.energy)
     res.e_sparse.append(S.e_sparse)
     res.e_geo.append(S.e_geo)
@@ -171,7 +174,7 @@ def sparse_pairs_for(problem, frame_ids):
 
 
 def solve_frames(problem, frame_ids, init_poses, params: SolveParams, depth_min=0.1, depth_max=10.0,
-                 frames_cache=None, direct=False, storage=None):
+                 frames_cache=None, direct=False, storage=None, assoc=None, pmap=None):
     """Gauss-Newton over the given frames (first one fixed) starting from init_poses (n,4,4);
     storage "bf16" / "fp16" evaluates the dense term on 16-bit stored frames."""
     if frames_cache is None:
@@ -180,7 +183,7 @@ def solve_frames(problem, frame_ids, init_poses, params: SolveParams, depth_min=
     else:
         frames = [frames_cache[f] for f in frame_ids]
     sp = sparse_pairs_for(problem, frame_ids)
-    return gauss_newton(frames, problem.intr, init_poses, sp, params, direct=direct)
+    return gauss_newton(frames, problem.intr, init_poses, sp, params, direct=direct, assoc=assoc, pmap=pmap)
 
 
 @dataclasses.dataclass
@@ -191,7 +194,7 @@ class PrunedResult:
     rounds: int                # solves run
 
 
-def gauss_newton_pruned(frames, intr, poses0, sparse_pairs, params: SolveParams, prune_rmax, max_rounds=8):
+def gauss_newton_pruned(frames, intr, poses0, sparse_pairs, params: SolveParams, prune_rmax, max_rounds=8, assoc=None):
     """Sec. 4.4.1 correspondence pruning around the solve.
 
     After a solve, r_max is the largest sparse correspondence distance ||T_a p - T_b q||.  If it
@@ -205,7 +208,7 @@ def gauss_newton_pruned(frames, intr, poses0, sparse_pairs, params: SolveParams,
     pruned = []
     rounds = 0
     while True:
-        res = gauss_newton(frames, intr, poses0, sp, params)
+        res = gauss_newton(frames, intr, poses0, sp, params, assoc=assoc)
         rounds += 1
         if not (res.r_max > prune_rmax) or rounds > max_rounds:
             break

@@ -70,6 +70,16 @@ def dense_pair_set(poses, sparse_pairs, max_angle_deg):
     return out
 
 
+def row_products(Ja, Jb, r, w):
+    """For rows r (N,) with Jacobians Ja, Jb (N,6) w.r.t. two frames and weights w (N,): the blocks
+    sum w J_x^T J_y (x, y in {a, b}) and the right-hand sides -sum w J_x^T r."""
+    Ja = np.asarray(Ja, dtype=np.float64)
+    Jb = np.asarray(Jb, dtype=np.float64)
+    wr = w * r
+    Wa, Wb = Ja * w[:, None], Jb * w[:, None]
+    return dict(aa=Wa.T @ Ja, ab=Wa.T @ Jb, ba=Wb.T @ Ja, bb=Wb.T @ Jb, ga=-(Ja.T @ wr), gb=-(Jb.T @ wr))
+
+
 class System:
     def __init__(self, n_frames):
         self.n = n_frames
@@ -82,29 +92,79 @@ class System:
         self.n_sparse = 0
         self.n_dense = 0
 
+    def add_products(self, a, b, P):
+        """Add row_products of frames a, b into the system; the gauge frame 0 has no unknowns."""
+        for fx, kx in ((a, "a"), (b, "b")):
+            if fx == 0:
+                continue
+            ix = 6 * (fx - 1)
+            self.b[ix:ix + 6] += P["g" + kx]
+            for fy, ky in ((a, "a"), (b, "b")):
+                if fy == 0:
+                    continue
+                iy = 6 * (fy - 1)
+                self.A[ix:ix + 6, iy:iy + 6] += P[kx + ky]
+
     def add(self, a, Ja, b, Jb, r, w):
         """Accumulate rows r (N,) with Jacobians Ja, Jb (N,6) for frames a, b and weights w (N,)."""
-        Ja = np.asarray(Ja, dtype=np.float64)
-        Jb = np.asarray(Jb, dtype=np.float64)
-        wr = w * r
-        blocks = [(a, Ja), (b, Jb)]
-        for fa, Jx in blocks:
-            if fa == 0:
-                continue
-            ia = 6 * (fa - 1)
-            self.b[ia:ia + 6] -= Jx.T @ wr
-            for fb, Jy in blocks:
-                if fb == 0:
-                    continue
-                ib = 6 * (fb - 1)
-                self.A[ia:ia + 6, ib:ib + 6] += (Jx * w[:, None]).T @ Jy
+        self.add_products(a, b, row_products(Ja, Jb, r, w))
 
 
-def assemble(frames, intr, poses, sparse_pairs, dense_pairs, params: SolveParams, w_dense):
+# Frames of the solve in a worker process of a parallel assembly (set by init_worker).
+_WORKER_FRAMES = None
+
+
+def init_worker(frames):
+    """Initializer of a worker pool for assemble(pmap=...): the solve's frames, sent once."""
+    global _WORKER_FRAMES
+    _WORKER_FRAMES = frames
+
+
+def dense_pair(frames, task):
+    """Dense photometric and geometric contribution of one directed pair i -> j (Sec. 4.3).
+
+    task = (i, j, poses (4x4 of i and j), intr, tau_d, tau_n, w_geo, w_photo, asc): weights already
+    multiplied by w_dense (0 = energies only); asc None = this oracle's own association.
+    Returns the residual count, both energies and the row products of the two residual kinds."""
+    i, j, Ti, Tj, intr, tau_d, tau_n, w_geo, w_photo, asc = task
+    Ri, ti, Rj, tj = Ti[:3, :3], Ti[:3, 3], Tj[:3, :3], Tj[:3, 3]
+    if asc is None:
+        asc = association.associate(frames[i], frames[j], association.relative_transform(Ri, ti, Rj, tj), intr,
+                                    tau_d, tau_n)
+    d = residuals.dense_terms(frames[i], frames[j], Ri, ti, Rj, tj, asc)
+    k = len(d["idx"])
+    out = dict(k=k, e_geo=float(np.sum(d["r_geo"] ** 2)), e_photo=float(np.sum(d["r_photo"] ** 2)))
+    if w_geo != 0.0 or w_photo != 0.0:
+        out["geo"] = row_products(d["J_geo_i"], d["J_geo_j"], d["r_geo"], np.full(k, w_geo))
+        out["photo"] = row_products(d["J_photo_i"], d["J_photo_j"], d["r_photo"], np.full(k, w_photo))
+    return out
+
+
+def _dense_pair_worker(task):
+    return dense_pair(_WORKER_FRAMES, task)
+
+
+def frame_pool(frames, processes=None):
+    """A process pool (spawn start method) whose workers hold the solve's frames (a list, or e.g. a
+    frames.FrameCache over a whole problem, with assemble's frame_keys); pass
+    ``lambda f, tasks: pool.map(f, tasks, chunksize=8)`` as assemble's pmap."""
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(processes, initializer=init_worker, initargs=(frames,))
+
+
+def assemble(frames, intr, poses, sparse_pairs, dense_pairs, params: SolveParams, w_dense, assoc=None, pmap=None,
+             frame_keys=None):
     """Normal equations and energy at the given poses.
 
     frames: preprocessed frames (frames.Frame) of the solve, index 0 = gauge frame.
     poses: (n,4,4) camera->world.  Returns a System.
+    assoc: optional callable (i, j, poses, own) -> association that replaces this oracle's own
+    association ``own`` of the directed pair i -> j (association.replay of decisions taken by
+    another implementation, which the caller has checked against ``own``); None keeps the
+    oracle's decisions.
+    pmap: optional order-preserving map (e.g. a process pool's, initialised with init_worker(frames))
+    over the directed pairs; each pair is evaluated alone and the sums are taken in pair order.
+    frame_keys: with pmap, the key under which the workers' frames hold local frame k (default k).
     """
     S = System(len(frames))
     R = [P[:3, :3] for P in poses]
@@ -119,27 +179,31 @@ def assemble(frames, intr, poses, sparse_pairs, dense_pairs, params: SolveParams
         S.n_sparse += 3 * N
         for row in range(3):
             S.add(a, Ja[:, row, :], b, Jb[:, row, :], r[:, row], params.w_sparse * w)
-    if params.dense_on and w_dense != 0.0:
-        for (a, b) in dense_pairs:
-            for (i, j) in ((a, b), (b, a)):
-                M32 = association.pair_transform32(R[i], t[i], R[j], t[j])
-                asc = association.associate(frames[i], frames[j], M32, intr, params.tau_dist, params.tau_normal)
-                d = residuals.dense_terms(frames[i], frames[j], R[i], t[i], R[j], t[j], asc)
-                k = len(d["idx"])
-                S.n_dense += k
-                S.e_geo += float(np.sum(d["r_geo"] ** 2))
-                S.e_photo += float(np.sum(d["r_photo"] ** 2))
-                S.add(i, d["J_geo_i"], j, d["J_geo_j"], d["r_geo"], np.full(k, w_dense * params.w_geo))
-                S.add(i, d["J_photo_i"], j, d["J_photo_j"], d["r_photo"], np.full(k, w_dense * params.w_photo))
-    elif params.dense_on:
+    if params.dense_on:
         # zero dense weight: energies still reported, no contribution to the system
+        wg, wp = w_dense * params.w_geo, w_dense * params.w_photo
+        tasks, order = [], []
         for (a, b) in dense_pairs:
             for (i, j) in ((a, b), (b, a)):
-                M32 = association.pair_transform32(R[i], t[i], R[j], t[j])
-                asc = association.associate(frames[i], frames[j], M32, intr, params.tau_dist, params.tau_normal)
-                d = residuals.dense_terms(frames[i], frames[j], R[i], t[i], R[j], t[j], asc)
-                S.n_dense += len(d["idx"])
-                S.e_geo += float(np.sum(d["r_geo"] ** 2))
-                S.e_photo += float(np.sum(d["r_photo"] ** 2))
+                asc = None
+                if assoc is not None:
+                    own = association.associate(frames[i], frames[j], association.relative_transform(R[i], t[i], R[j], t[j]),
+                                                intr, params.tau_dist, params.tau_normal)
+                    asc = {k: v for k, v in assoc(i, j, poses, own).items() if k in ("valid", "nx", "ny", "bx", "by")}
+                tasks.append((i, j, poses[i], poses[j], intr, params.tau_dist, params.tau_normal, wg, wp, asc))
+                order.append((i, j))
+        if pmap is not None:
+            if frame_keys is not None:
+                tasks = [(frame_keys[tk[0]], frame_keys[tk[1]]) + tk[2:] for tk in tasks]
+            results = pmap(_dense_pair_worker, tasks)
+        else:
+            results = (dense_pair(frames, tk) for tk in tasks)
+        for (i, j), res in zip(order, results):
+            S.n_dense += res["k"]
+            S.e_geo += res["e_geo"]
+            S.e_photo += res["e_photo"]
+            if "geo" in res:
+                S.add_products(i, j, res["geo"])
+                S.add_products(i, j, res["photo"])
     S.energy = params.w_sparse * S.e_sparse + w_dense * (params.w_photo * S.e_photo + params.w_geo * S.e_geo)
     return S

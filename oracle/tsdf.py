@@ -34,8 +34,6 @@ import math
 
 import numpy as np
 
-from . import association
-
 f32 = np.float32
 Q_SDF = 2.0 ** -20
 C_SCALE = 65535.0
@@ -52,6 +50,14 @@ class Params:
         self.inv_q = f32(1.0 / Q_SDF)
 
 
+def ray_tables(intr):
+    """kx[x] = fl32((x - cx) / fx), ky[y] = fl32((y - cy) / fy): each computed in FP64, rounded once."""
+    W, H = intr["W"], intr["H"]
+    kx = ((np.arange(W, dtype=np.float64) - intr["cx"]) / intr["fx"]).astype(f32)
+    ky = ((np.arange(H, dtype=np.float64) - intr["cy"]) / intr["fy"]).astype(f32)
+    return kx, ky
+
+
 def pose32(T):
     T = np.asarray(T, dtype=np.float64)
     return T[:3, :3].astype(f32), T[:3, 3].astype(f32)
@@ -60,7 +66,7 @@ def pose32(T):
 def band_blocks(depth, intr, T, prm: Params):
     """Block coordinates (set of (bx, by, bz)) containing a band sample of a frame at pose T."""
     R, t = pose32(T)
-    kx, ky = association.ray_tables(intr)
+    kx, ky = ray_tables(intr)
     H, W = depth.shape
     ys, xs = np.divmod(np.arange(W * H), W)
     D = np.asarray(depth, dtype=f32).ravel()
@@ -93,7 +99,7 @@ def integrate(volume, depth, color, intr, T, prm: Params, sign=1):
     """Add (sign = +1) or remove (-1) one frame.  volume: dict key -> int64 array (3, 512) with
     rows S, W, SC; blocks are created on first touch and never dropped."""
     R, t = pose32(T)
-    kx, ky = association.ray_tables(intr)
+    kx, ky = ray_tables(intr)
     fx, fy, cx, cy = f32(intr["fx"]), f32(intr["fy"]), f32(intr["cx"]), f32(intr["cy"])
     H, W = depth.shape
     D = np.asarray(depth, dtype=f32).ravel()

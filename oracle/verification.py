@@ -1,6 +1,6 @@
-"""Dense verification of a frame pair and chunk validation (oracle, Sec. 4.1.1 and Sec. 4.2).
+"""Dense verification of a frame pair and chunk validation (oracle, FP64, Sec. 4.1.1 and Sec. 4.2).
 
-Test-infrastructure only: the CUDA library never imports this package.
+TEST INFRASTRUCTURE ONLY: the CUDA library never imports this package.
 
 Sec. 4.1.1 aligns frames f_i and f_j with a relative transform T_ij (camera i -> camera j),
 re-projects every pixel of one frame into the other in both directions, and keeps a pixel
@@ -11,9 +11,9 @@ at its optimised local poses and discards the chunk if any pair's error is too l
 
 Readings (the paper states the gates and thresholds but not every detail):
 
-* the correspondence of source pixel (x, y) is the nearest target pixel of pi(T_ij p) (the same
-  projective association as the dense energy, Sec. 4.3, without its bilinear border), inside
-  the image, with valid depth and normal on both sides;
+* the correspondence of source pixel (x, y) is the nearest target pixel of u = pi(T_ij p),
+  (floor(u_x + 1/2), floor(u_y + 1/2)) (the projective association of the dense energy, Sec. 4.3,
+  without its bilinear border), inside the image, with valid depth and normal on both sides;
 * gates: ||T_ij p - q|| < tau_d, (R_ij n_i) . n_j > tau_n, |C_i(x, y) - C_j(target)| < tau_c,
   where C is the frame's intensity (the luminance given with the depth);
 * the re-projection error of the pair is the mean distance over the kept correspondences of
@@ -22,71 +22,52 @@ Readings (the paper states the gates and thresholds but not every detail):
 * chunk validation: every pair of the chunk's frames at the optimised local poses; the chunk is
   invalid if some pair with kept correspondences has a mean error above 0.05 m.
 
-The gate decisions are taken in IEEE FP32 in the same operation order as the association of
-the dense energy (association.py) and as the GPU kernel; the distances are summed in FP64.
+Everything is FP64.  As in association.py, a pixel whose decision sits within an FP32 evaluation's
+rounding of a threshold is a tie; ``reproject`` counts the ties so that a comparison with an FP32
+implementation can bound its count and distance sum (``PairCheck.bounds``).
 """
 import dataclasses
 
 import numpy as np
 
-from . import association
+from .association import EPS_D, EPS_N, EPS_PX
 
-f32 = np.float32
-
-
-def inverse_transform32(R, t):
-    """FP32 rounding of T^-1 for an FP64 rigid transform (R^T, -R^T t summed left to right)."""
-    Ri = np.array([[R[b, a] for b in range(3)] for a in range(3)])
-    ti = np.array([-((R[0, a] * t[0] + R[1, a] * t[1]) + R[2, a] * t[2]) for a in range(3)])
-    return Ri.astype(f32), ti.astype(f32)
+# FP32 rounding of |C_i - C_j| for intensities in [0, 1]
+EPS_C = 1e-6
 
 
-def reproject(fi, fj, M32, intr, tau_d=0.15, tau_n=0.9, tau_c=0.1):
-    """One direction i -> j under M32 = fl32(T_ij): the kept correspondences' count and the FP64
-    sum of their distances ||T_ij p - q||, plus the per-pixel mask."""
-    R, t = M32
+def reproject(fi, fj, T, intr, tau_d=0.15, tau_n=0.9, tau_c=0.1):
+    """One direction i -> j under T (4x4, camera i -> camera j).  Returns (n kept, sum of the kept
+    correspondences' distances ||T p - q||, n ties, kept mask); ties are counted over the pixels
+    whose outcome (kept or not, or which target) an FP32 evaluation may decide otherwise."""
+    T = np.asarray(T, dtype=np.float64)
+    R, t = T[:3, :3], T[:3, 3]
     W, H = intr["W"], intr["H"]
-    kx, ky = association.ray_tables(intr)
-    fx, fy, cx, cy = f32(intr["fx"]), f32(intr["fy"]), f32(intr["cx"]), f32(intr["cy"])
+    fx, fy, cx, cy = (float(intr[k]) for k in ("fx", "fy", "cx", "cy"))
     ys, xs = np.divmod(np.arange(W * H), W)
-    z = fi.D32.ravel()
-    n_i = fi.N32.reshape(-1, 3)
-    ok = fi.valid.ravel() & fi.nvalid.ravel()
-    dx = kx[xs] * z
-    dy = ky[ys] * z
-    dz = z
-    Y = [((R[a, 0] * dx + R[a, 1] * dy) + R[a, 2] * dz) + t[a] for a in range(3)]
-    ok &= Y[2] > f32(0)
-    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
-        iz = f32(1) / np.where(ok, Y[2], f32(1))
-        ux = fx * (Y[0] * iz) + cx
-        uy = fy * (Y[1] * iz) + cy
-    ux = np.where(ok, ux, f32(-100))
-    uy = np.where(ok, uy, f32(-100))
-    nxf = np.floor(ux + f32(0.5))
-    nyf = np.floor(uy + f32(0.5))
+    z = fi.D.ravel()
+    d = np.stack([(xs - cx) * z / fx, (ys - cy) * z / fy, z], axis=1)
+    y = d @ R.T + t
+    ok = fi.valid.ravel() & fi.nvalid.ravel() & (y[:, 2] > 0)
+    yz = np.where(ok, y[:, 2], 1.0)
+    ux = np.where(ok, fx * y[:, 0] / yz + cx, -100.0)
+    uy = np.where(ok, fy * y[:, 1] / yz + cy, -100.0)
+    tie = ok & (np.minimum(np.abs(ux + 0.5 - np.round(ux + 0.5)), np.abs(uy + 0.5 - np.round(uy + 0.5))) < EPS_PX)
+    nxf = np.floor(ux + 0.5)
+    nyf = np.floor(uy + 0.5)
     ok &= (nxf >= 0) & (nxf <= W - 1) & (nyf >= 0) & (nyf <= H - 1)
     nx = np.where(ok, nxf, 0).astype(np.int64)
     ny = np.where(ok, nyf, 0).astype(np.int64)
     tgt = ny * W + nx
     ok &= fj.valid.ravel()[tgt] & fj.nvalid.ravel()[tgt]
-    Dj = fj.D32.ravel()[tgt]
-    qx = kx[nx] * Dj
-    qy = ky[ny] * Dj
-    qz = Dj
-    ex, ey, ez = Y[0] - qx, Y[1] - qy, Y[2] - qz
-    dist2 = (ex * ex + ey * ey) + ez * ez
-    ok &= dist2 < f32(tau_d * tau_d)
-    m = [(R[a, 0] * n_i[:, 0] + R[a, 1] * n_i[:, 1]) + R[a, 2] * n_i[:, 2] for a in range(3)]
-    n_j = fj.N32.reshape(-1, 3)[tgt]
-    dot = (m[0] * n_j[:, 0] + m[1] * n_j[:, 1]) + m[2] * n_j[:, 2]
-    ok &= dot > f32(tau_n)
-    ok &= np.abs(fi.C32.ravel() - fj.C32.ravel()[tgt]) < f32(tau_c)
-    # distances of the kept correspondences in FP64 (camera-j coordinates)
-    Ty = np.stack([Y[0], Y[1], Y[2]], axis=1).astype(np.float64)
-    q = np.stack([qx, qy, qz], axis=1).astype(np.float64)
-    d = np.sqrt(np.sum((Ty - q) ** 2, axis=1))
-    return int(ok.sum()), float(d[ok].sum()), ok
+    Dj = fj.D.ravel()[tgt]
+    q = np.stack([(nx - cx) * Dj / fx, (ny - cy) * Dj / fy, Dj], axis=1)
+    dist = np.sqrt(np.sum((y - q) ** 2, axis=1))
+    ndot = np.sum((fi.N.reshape(-1, 3) @ R.T) * fj.N.reshape(-1, 3)[tgt], axis=1)
+    dc = np.abs(fi.C.ravel() - fj.C.ravel()[tgt])
+    tie |= ok & ((np.abs(dist - tau_d) < EPS_D) | (np.abs(ndot - tau_n) < EPS_N) | (np.abs(dc - tau_c) < EPS_C))
+    ok &= (dist < tau_d) & (ndot > tau_n) & (dc < tau_c)
+    return int(ok.sum()), float(dist[ok].sum()), int(tie.sum()), ok, tie, dist
 
 
 @dataclasses.dataclass
@@ -95,21 +76,36 @@ class PairCheck:
     n_ji: int
     e_ij: float
     e_ji: float
+    tie_ij: int = 0
+    tie_ji: int = 0
+    sure_ij: tuple = (0, 0.0)   # (count, distance sum) of the kept pixels that are not ties
+    sure_ji: tuple = (0, 0.0)
 
     @property
     def mean(self):
         n = self.n_ij + self.n_ji
         return (self.e_ij + self.e_ji) / n if n else float("inf")
 
+    def bounds(self, direction, tau_d=0.15):
+        """(n_lo, n_hi, e_lo, e_hi): what an evaluation that may decide every tie either way can
+        report for one direction ("ij" or "ji"); a kept tie's distance is below tau_d."""
+        (n_s, e_s), n_t = (self.sure_ij, self.tie_ij) if direction == "ij" else (self.sure_ji, self.tie_ji)
+        return n_s, n_s + n_t, e_s, e_s + n_t * tau_d
+
+
+def _direction(fi, fj, T, intr, tau_d, tau_n, tau_c):
+    n, e, nt, ok, tie, dist = reproject(fi, fj, T, intr, tau_d, tau_n, tau_c)
+    sure = ok & ~tie
+    return n, e, nt, (int(sure.sum()), float(dist[sure].sum()))
+
 
 def verify_pair(fi, fj, T_ij, intr, tau_d=0.15, tau_n=0.9, tau_c=0.1):
     """Two-sided check of frames i, j under the relative transform T_ij (4x4, camera i -> j)."""
-    R, t = np.asarray(T_ij, dtype=np.float64)[:3, :3], np.asarray(T_ij, dtype=np.float64)[:3, 3]
-    M_ij = (R.astype(f32), t.astype(f32))
-    M_ji = inverse_transform32(R, t)
-    n1, e1, _ = reproject(fi, fj, M_ij, intr, tau_d, tau_n, tau_c)
-    n2, e2, _ = reproject(fj, fi, M_ji, intr, tau_d, tau_n, tau_c)
-    return PairCheck(n1, n2, e1, e2)
+    T_ij = np.asarray(T_ij, dtype=np.float64)
+    T_ji = np.linalg.inv(T_ij)
+    n1, e1, t1, s1 = _direction(fi, fj, T_ij, intr, tau_d, tau_n, tau_c)
+    n2, e2, t2, s2 = _direction(fj, fi, T_ji, intr, tau_d, tau_n, tau_c)
+    return PairCheck(n1, n2, e1, e2, t1, t2, s1, s2)
 
 
 def pair_valid(chk: PairCheck, intr, e_max=0.075, frac_min=0.02):
@@ -131,15 +127,5 @@ def validate_chunk(frames, poses, intr, e_max=0.05, tau_d=0.15, tau_n=0.9, tau_c
 
 
 def relative_from_poses(Ti, Tj):
-    """T_j^-1 T_i in FP64 with the explicit sums of association.pair_transform32 (before rounding)."""
-    Ri, ti, Rj, tj = Ti[:3, :3], Ti[:3, 3], Tj[:3, :3], Tj[:3, 3]
-    R = np.zeros((3, 3))
-    t = np.zeros(3)
-    dt = [ti[0] - tj[0], ti[1] - tj[1], ti[2] - tj[2]]
-    for a in range(3):
-        for b in range(3):
-            R[a, b] = (Rj[0, a] * Ri[0, b] + Rj[1, a] * Ri[1, b]) + Rj[2, a] * Ri[2, b]
-        t[a] = (Rj[0, a] * dt[0] + Rj[1, a] * dt[1]) + Rj[2, a] * dt[2]
-    T = np.eye(4)
-    T[:3, :3], T[:3, 3] = R, t
-    return T
+    """T_j^-1 T_i (FP64)."""
+    return np.linalg.inv(np.asarray(Tj, dtype=np.float64)) @ np.asarray(Ti, dtype=np.float64)

@@ -262,18 +262,17 @@ __global__ void __launch_bounds__(BATCH_BS, 3) k_batch(BatchArgs a, BatchQueue q
 
 template <typename Acc, int KIND>
 static int batch_grid(size_t smem) {
-  static int blocks = -1;  // one value per instantiation (the smem of a context's frame size)
-  static size_t for_smem = 0;
-  if (blocks < 0 || for_smem != smem) {
+  static PerDevice blocks;  // one per instantiation, per device and dynamic shared memory size
+  return (int)blocks.get((long long)smem, [smem] {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<Acc, KIND>, BATCH_BS, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<Acc, KIND>, BATCH_BS, smem) != cudaSuccess) {
       per_sm = 0;
-    blocks = sms * per_sm;
-    for_smem = smem;
-  }
-  return blocks;
+      cudaGetLastError();
+    }
+    return (long long)sms * per_sm;
+  });
 }
 
 template <typename Acc, int KIND>

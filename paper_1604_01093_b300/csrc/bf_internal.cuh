@@ -15,9 +15,39 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "bf.h"
 
 namespace bf {
+
+// One-time setup per device (a kernel attribute, an occupancy query).  Kernel attributes and
+// occupancy belong to a device, so a context on a second device must do its own; the mutex lets
+// the host threads of several contexts (and the serving workers) reach it at the same time.
+// get(key, f): the value stored for (current device, key), computed by f() the first time.
+struct PerDevice {
+  std::mutex mu;
+  std::map<std::pair<int, long long>, long long> v;
+  template <typename F>
+  long long get(long long key, F f) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    auto it = v.find({dev, key});
+    if (it != v.end()) return it->second;
+    const long long x = f();
+    v[{dev, key}] = x;
+    return x;
+  }
+  void set(long long key, long long x) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    v[{dev, key}] = x;
+  }
+};
 
 // ---------------------------------------------------------------------------------------------
 // Partial sums of one work item (a dense tile or a sparse segment), in the coordinates of the

@@ -11,10 +11,11 @@
 // record per tile.  Each run of sequential FP32 additions is at most ceil(tile/blockDim)
 // long; everything above a tile is summed in FP64 (mixed precision) by the pair merge.
 //
-// The association decisions (target pixel, bilinear taps, validity, gates) are computed with
-// explicitly rounded FP32 operations in a fixed order (products, sums and fused multiply-adds,
-// no other contraction), so a CPU restatement in IEEE FP32 (with an exact FP32 fused
-// multiply-add) takes the same decisions.  Residuals and Jacobians are free FP32 arithmetic.
+// The association decisions (target pixel, bilinear taps, validity, gates) are computed in FP32
+// with explicitly rounded operations in a fixed order (products, sums and fused multiply-adds, no
+// other contraction), so that every launch configuration takes the same decisions; they agree with
+// the exact (FP64) association except where a value lies within FP32 rounding of its threshold.
+// Residuals and Jacobians are free FP32 arithmetic.
 //
 // Everything is evaluated in the coordinates of the target camera j with the pair transform
 // M = T_j^-1 T_i (y = R d + t); the merge rotates the sums to world coordinates with R_j.
@@ -145,9 +146,15 @@ __global__ void __launch_bounds__(STG_BS, 1)
                    : "memory");
   }
   if (!mbar_wait(barp, 0, STG_WAIT_LIMIT)) {
-    // the copies did not land within the limit: report, wait once more for them, then leave
+    // The copies did not land within the limit (at least half a second for 154 KB read from this
+    // context's own frame store, in bounds by construction: only a stalled memory system gets here).
+    // Report it and skip the evaluation, but keep the CTA, and with it its shared memory, alive
+    // until the copies complete, for up to 16 more limits: a CTA that left with a bulk copy in
+    // flight could have it land in the shared memory of the next CTA this SM runs.  If even that
+    // wait gives up, the CTA leaves; the solve then fails with BF_ERR_TIMEOUT.
     if (threadIdx.x == 0) atomicExch(err, 1);
-    mbar_wait(barp, 0, STG_WAIT_LIMIT);
+    for (int r = 0; r < 16 && !mbar_wait(barp, 0, STG_WAIT_LIMIT); ++r) {
+    }
     return;
   }
   const int quad = threadIdx.x >> 7, tq = threadIdx.x & 127;
@@ -196,11 +203,11 @@ __global__ void __launch_bounds__(STG_BS, 1)
 template <int MODE, int KIND, typename Part>
 static void staged_go(int n, int smem, cudaStream_t st, const Tables &t, const FrameStore &fs, const Intr &in,
                       const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *err) {
-  static bool attr_set = false;  // one flag per instantiation
-  if (!attr_set) {
+  static PerDevice attr;  // one per instantiation, set once per device
+  attr.get(0, [] {
     cudaFuncSetAttribute(k_dense_staged<MODE, KIND, Part>, cudaFuncAttributeMaxDynamicSharedMemorySize, STG_MAX_SMEM);
-    attr_set = true;
-  }
+    return 1LL;
+  });
   k_dense_staged<MODE, KIND, Part><<<n, STG_BS, smem, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, err);
 }
 

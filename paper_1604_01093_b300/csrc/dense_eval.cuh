@@ -141,12 +141,13 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
   const float iz = __frcp_rn(Y2);
   const float ux = FMA(in.fx, FM(Y0, iz), in.cx);
   const float uy = FMA(in.fy, FM(Y1, iz), in.cy);
-  // bilinear taps on the 2-pixel interior: 2 <= bx and bx + 1 <= W - 3 (bx integer-valued).  That
-  // bounds u to [2, W - 3), so the nearest pixel floor(u + 0.5) (FP32 rounding is monotonic and
-  // 2.5, W - 2.5 are representable) lies in [2, W - 3]: inside the image without a test of its own
-  const float bxf = floorf(ux), byf = floorf(uy);
-  if (!(bxf >= 2.f && bxf <= (float)(W - 4) && byf >= 2.f && byf <= (float)(H - 4))) return -1;
+  // nearest pixel floor(u + 0.5) on the 3-pixel interior, 3 <= n <= W - 4 (inside the image without a
+  // test of its own).  Then the bilinear taps floor(u), floor(u) + 1 lie on the 2-pixel interior where
+  // grad I is defined (floor(u) >= n - 1 and floor(u) + 1 <= n + 1), and every threshold on u sits at
+  // a half-integer, which an integer projection (every pixel of an identity relative pose) never hits
   const float nxf = floorf(FA(ux, 0.5f)), nyf = floorf(FA(uy, 0.5f));
+  if (!(nxf >= 3.f && nxf <= (float)(W - 4) && nyf >= 3.f && nyf <= (float)(H - 4))) return -1;
+  const float bxf = floorf(ux), byf = floorf(uy);
   const int tx = (int)nxf, ty = (int)nyf;
   const int bx = (int)bxf, by = (int)byf;
   const int tpx = ty * W + tx, b0 = by * W + bx;

@@ -1,10 +1,10 @@
 // bf_dense_pair_noalloc: the dense normal-equation blocks of one frame pair without any device
 // allocation.
 //
-// Some callers cannot allocate device memory at the point where they need this: code that runs
-// while another component is capturing its stream into a CUDA graph, real-time loops that must
-// not pay cudaMalloc's implicit device-wide synchronisation, and processes whose memory
-// manager has already reserved the GPU's memory for itself.  They pass their inputs and the
+// Some callers cannot allocate device memory at the point where they need this: real-time loops
+// that must not pay cudaMalloc's implicit device-wide synchronisation, processes whose memory
+// manager has already reserved the GPU's memory for itself, and plugins that are handed their
+// buffers by the application that embeds them.  They pass their inputs and the
 // output buffer; every intermediate (the two frames' preprocessed planes, the ray tables, the
 // work tables and the per-tile partial sums) lives in one file-scope device array of fixed size.
 //
@@ -13,6 +13,7 @@
 // overlaps (for example on two streams without ordering) race on it.  The first call on a device
 // looks up the array's device address (cudaGetSymbolAddress); make that first call before any
 // stream capture.
+#include <cmath>
 #include <mutex>
 
 #include "bf.h"
@@ -126,13 +127,25 @@ extern "C" bf_status bf_dense_pair_noalloc(int width, int height, double fx, dou
   if (width < 8 || height < 8 || width > NA_MAX_W || height > NA_MAX_H) return BF_ERR_INVALID_ARG;
   if (!(fx > 0) || !(fy > 0) || !depth_i || !lum_i || !depth_j || !lum_j || !pose_i || !pose_j || !params || !out)
     return BF_ERR_INVALID_ARG;
-  if (!(params->tau_dist > 0)) return BF_ERR_INVALID_ARG;
+  if (!(depth_min < depth_max) || !std::isfinite(cx) || !std::isfinite(cy) || !std::isfinite(fx) ||
+      !std::isfinite(fy))
+    return BF_ERR_INVALID_ARG;
+  if (!(params->tau_dist > 0) || !std::isfinite(params->tau_dist) || !std::isfinite(params->tau_normal) ||
+      !std::isfinite(params->w_dense) || !std::isfinite(params->w_photo) || !std::isfinite(params->w_geo))
+    return BF_ERR_INVALID_ARG;
+  // an error left pending by the caller would be reported by the first launch check below as ours:
+  // refuse instead, and leave it for the caller to read
+  if (cudaPeekAtLastError() != cudaSuccess) return BF_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   unsigned char *base = nullptr;
   if (scratch_address((void **)&base) != cudaSuccess) {
     cudaGetLastError();
     return BF_ERR_CUDA;
   }
+#define NA_LAUNCHED()                                          \
+  do {                                                         \
+    if (cudaGetLastError() != cudaSuccess) return BF_ERR_CUDA; \
+  } while (0)
   const int HW = width * height;
   const int tiles_per_dir = (HW + NA_TILE_PX - 1) / NA_TILE_PX;
   const int n_tiles = 2 * tiles_per_dir;
@@ -140,6 +153,7 @@ extern "C" bf_status bf_dense_pair_noalloc(int width, int height, double fx, dou
   to_pose12(pose_i, poses.v);
   to_pose12(pose_j, poses.v + 12);
   k_noalloc_setup<<<1, 256, 0, st>>>(base, width, height, fx, fy, cx, cy, poses, tiles_per_dir);
+  NA_LAUNCHED();
 
   const int *I = (const int *)(base + NA_OFF_INT);
   FrameStore fs;
@@ -155,7 +169,9 @@ extern "C" bf_status bf_dense_pair_noalloc(int width, int height, double fx, dou
   float4 *A = (float4 *)(base + NA_OFF_A), *B = (float4 *)(base + NA_OFF_B);
   // planes of frame i into slot 0, of frame j into slot 1 (slot tables: frame_slot = {0, 1})
   launch_preprocess(depth_i, lum_i, 1, I + I_SLOT, fs, A, B, nullptr, nullptr, depth_min, depth_max, st);
+  NA_LAUNCHED();
   launch_preprocess(depth_j, lum_j, 1, I + I_SLOT + 1, fs, A, B, nullptr, nullptr, depth_min, depth_max, st);
+  NA_LAUNCHED();
 
   Tables t = {};
   t.n_frames = 2;
@@ -187,6 +203,7 @@ extern "C" bf_status bf_dense_pair_noalloc(int width, int height, double fx, dou
   float *pairM = (float *)(base + NA_OFF_M);
   double *part = (double *)(base + NA_OFF_PART);
   launch_pair_xform(t, pose, pairM, st);
+  NA_LAUNCHED();
   Intr in;
   in.fx = (float)fx;
   in.fy = (float)fy;
@@ -199,7 +216,9 @@ extern "C" bf_status bf_dense_pair_noalloc(int width, int height, double fx, dou
   g.tau_n = (float)params->tau_normal;
   launch_dense<double>(MODE_ACCUM, t, fs, in, pairM, g, (float)(params->w_dense * params->w_geo),
                        (float)(params->w_dense * params->w_photo), part, nullptr, st);
+  NA_LAUNCHED();
   launch_pair_merge<double, double>(t, pose, part, nullptr, out, out + PAIRBLK, (float *)(base + NA_OFF_OFF), st);
-  if (cudaGetLastError() != cudaSuccess) return BF_ERR_CUDA;
+  NA_LAUNCHED();
+#undef NA_LAUNCHED
   return BF_OK;
 }

@@ -418,17 +418,16 @@ __global__ void __launch_bounds__(COOP_BS)
 }
 
 int coop_max_grid() {
-  static int max_blocks = -1;
-  if (max_blocks < 0) {
+  static PerDevice max_blocks;
+  return (int)max_blocks.get(0, [] {
     int dev = 0, sms = 0, per_sm = 0, per_sm_f = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_coop<double>, COOP_BS, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_f, k_pcg_coop<float>, COOP_BS, 0);
     per_sm = per_sm < per_sm_f ? per_sm : per_sm_f;
-    max_blocks = sms * (per_sm < 1 ? 1 : per_sm);
-  }
-  return max_blocks;
+    return (long long)sms * (per_sm < 1 ? 1 : per_sm);
+  });
 }
 
 int coop_grid_size(int n_vars) {
@@ -810,23 +809,20 @@ __global__ void __launch_bounds__(CL_BS, 1)
   cluster.sync();  // keep every CTA's shared memory alive until remote reads are done
 }
 
-// Largest supported cluster (16 if the device allows non-portable sizes, else 8).
-static int g_cluster_max = -1;
-void cluster_size_override(int cl) { g_cluster_max = cl; }
+// Largest supported cluster on the current device (16 if it allows non-portable sizes, else 8).
+static PerDevice g_cluster_max;
+void cluster_size_override(int cl) { g_cluster_max.set(0, cl); }
 int cluster_size_max() {
-  int &cl = g_cluster_max;
-  if (cl < 0) {
-    cl = 0;
+  return (int)g_cluster_max.get(0, [] {
+    long long cl = 8;
     if (cudaFuncSetAttribute(k_pcg_cluster<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess &&
         cudaFuncSetAttribute(k_pcg_cluster<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
             cudaSuccess)
       cl = 16;
-    else
-      cl = 8;
     cudaGetLastError();
-  }
-  return cl;
+    return cl;
+  });
 }
 
 constexpr size_t CLUSTER_SMEM_LIMIT = 220 * 1024;
@@ -867,14 +863,14 @@ int launch_pcg_cluster(const Tables &t, const float *Df, const float *pairoff, c
   if (t.n_vars == 0) return 0;
   size_t smem = 0;
   const ClusterLayout L = cluster_layout(t.n_vars, cl, inc_off_host, &smem);
-  static size_t smem_set[2] = {0, 0};
-  size_t &cur = smem_set[sizeof(Acc) == 8 ? 1 : 0];
-  if (smem > cur) {
-    if (cudaFuncSetAttribute(k_pcg_cluster<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CLUSTER_SMEM_LIMIT) !=
-        cudaSuccess)
-      return -1;
-    cur = CLUSTER_SMEM_LIMIT;
-  }
+  static PerDevice smem_attr;  // one per instantiation: the opt-in above 48 KB, once per device
+  if (smem > 48 * 1024 && smem_attr.get(0, [] {
+        const bool ok = cudaFuncSetAttribute(k_pcg_cluster<Acc>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)CLUSTER_SMEM_LIMIT) == cudaSuccess;
+        cudaGetLastError();
+        return ok ? 1LL : 0LL;
+      }) == 0)
+    return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cl);
   cfg.blockDim = dim3(CL_BS);

@@ -9,8 +9,8 @@
 //   ||T p - q|| < tau_d,  (R n_src) . n_dst > tau_n,  |C_src(x, y) - C_dst(target)| < tau_c.
 // The CTA counts the kept matches and sums their distances per direction.
 //
-// The gate decisions use explicitly rounded FP32 operations in the same order as the dense
-// energy's association, so a CPU restatement in IEEE FP32 keeps exactly the same matches.
+// The gate decisions use explicitly rounded FP32 operations in a fixed order; they agree with the
+// exact (FP64) test except where a value lies within FP32 rounding of its threshold.
 #include "bf_internal.cuh"
 
 namespace bf {

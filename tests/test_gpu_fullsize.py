@@ -1,17 +1,25 @@
-"""Full-size parity in the launch configurations bench.py times, against stored oracle results:
+"""Full-size parity in the launch configurations bench.py times, against the FP64 oracle.
 
-* the 300-keyframe global solve (mixed precision, target frames staged in shared memory, cluster
-  PCG, the Gauss-Newton loop replayed as a CUDA graph) against the FP64 oracle's first
-  Gauss-Newton step (tests/golden/global300_oracle.json);
-* the whole 256-chunk 320x240 batch (FP32 arithmetic, graph; launch sequence and persistent
-  launch), sampled on a 3-frame and an 11-frame chunk (tests/golden/chunks256_oracle.json).
-* the 2000-keyframe 160x120 solve (BF16 frame storage, tiled dense kernel, cluster PCG with its
-  blocks in global memory), first Gauss-Newton step against the oracle's on the same BF16-rounded
-  planes (tests/golden/global2000_oracle.json).
+* The 300-keyframe global solve (mixed precision, target frames staged in shared memory, cluster
+  PCG, the Gauss-Newton loop replayed as a CUDA graph), 8 Gauss-Newton x 20 PCG:
+  - single steps: from the oracle's own iterates X_0, X_3 and X_7 (stored in
+    tests/golden/global300_oracle.json), the library's Gauss-Newton step against the oracle's step
+    from the same poses, run here on the library's checked association decisions (tests/replay.py):
+    1e-4 rad, 1e-5 m, 1e-5 relative energy;
+  - the whole solve against the stored oracle solve: all nine energies within 1e-5 relative.  The
+    poses after eight steps are not fixed to 1e-5 m by the arithmetic: the loop's weakly constrained
+    directions amplify any perturbation of a step (two oracle runs that decide a few tie pixels
+    differently end 9.6e-4 rad and 2.8e-4 m apart with energies equal to 1.4e-7), so the final
+    poses are held to 2e-3 rad and 2e-3 m and the deviation is printed.
+* The whole 256-chunk 320x240 batch (FP32 arithmetic, graph; launch sequence and persistent
+  launch; FP32 and BF16 frame storage): 18 chunks, two of every length 3..11, against the stored
+  oracle solves (tests/golden/chunks256_oracle.json) on the same planes: 1e-4 rad, 1e-5 m, 1e-5.
+* The 2000-keyframe 160x120 solve (BF16 frame storage, tiled dense kernel, its PCG): its first
+  Gauss-Newton step against the oracle's on the same BF16-rounded planes (energies, the poses of
+  every 32nd keyframe); its error against the oracle on the unrounded frames is printed.
 
-The oracle needs minutes (the 2000-keyframe step about forty) for these, so its results are stored, written by the
-make_*_oracle.py scripts beside them from the oracle and the seeded scene generator alone.
-Tolerances are the accuracy targets: 1e-4 rad, 1e-5 m, 1e-5 relative energy.
+The stored results are written by the make_*_oracle.py scripts beside them from the oracle and
+the seeded scene generator alone.
 """
 import json
 import os
@@ -19,13 +27,17 @@ import os
 import numpy as np
 import pytest
 
+import replay
 import synth
-from oracle import lie
+from oracle import frames as ofr, lie, solver, system
+from oracle.system import SolveParams
 
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROT_TOL, TRANS_TOL, ENERGY_RTOL = 1e-4, 1e-5, 1e-5
+# whole 8-step loop solve: see the module docstring
+LOOP_ROT_TOL, LOOP_TRANS_TOL = 2e-3, 2e-3
 
 
 @pytest.fixture(scope="module")
@@ -62,39 +74,72 @@ def params(prob, n_gn):
                 w_geo=d["w_geo"], use_graph=1)
 
 
+def poses44(rows):
+    out = np.tile(np.eye(4), (len(rows), 1, 1))
+    out[:, :3, :] = np.array(rows).reshape(-1, 3, 4)
+    return out
+
+
+def worst_pose_error(P, Q):
+    e = [lie.pose_error(P[k], Q[k]) for k in range(len(P))]
+    return max(x[0] for x in e), max(x[1] for x in e)
+
+
 def test_golden_matches_the_workload(global300, golden):
     assert golden["workload"] == global300.name and golden["n_frames"] == global300.n_frames
     assert golden["pairs"] == len(global300.pairs) and golden["n_pcg"] == global300.solve["n_pcg"]
+    assert golden["n_gn"] == global300.solve["n_gn"] and len(golden["energy"]) == golden["n_gn"] + 1
 
 
-def test_global300_first_step_matches_oracle(bf, global300, golden):
+def test_global300_single_steps_match_oracle(bf, global300, golden):
+    """Gauss-Newton steps k = 0, 3, 7 of the 8-step solve, each from the oracle's iterate X_k."""
+    prob = global300
+    n = prob.n_frames
+    ids = list(range(n))
+    frames = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in ids]
+    sp = solver.sparse_pairs_for(prob, ids)
+    d = prob.solve
+    prm = SolveParams(n_gn=1, n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"], w_photo=d["w_photo"],
+                      w_geo=d["w_geo"])
+    ctx = make_ctx(bf, prob)
+    rep = replay.from_ctx(ctx, ids, prob.intr["W"], prob.intr["H"])
+    hist = golden["iterates"]
+    with system.frame_pool(frames, min(16, os.cpu_count() or 1)) as pool:
+        pmap = lambda f, tasks: pool.map(f, tasks, chunksize=16)  # noqa: E731
+        for k in (0, 3, 7):
+            Xk = prob.init if k == 0 else poses44(hist[str(k)])
+            # the dense pair set is fixed at the solve's initial poses (Sec. 4.3): here X_k, on both sides
+            dp = system.dense_pair_set(Xk, sp, prm.max_angle_deg)
+            S = system.assemble(frames, prob.intr, Xk, sp, dp, prm, prm.w_dense, assoc=rep, pmap=pmap)
+            Minv, _ = solver.block_jacobi_inverse(S.A, prm.precond)
+            delta, _ = solver.pcg(S.A, S.b, Minv, prm.n_pcg)
+            Xn = solver.apply_step(Xk, delta)
+            ctx.add_frames(0, prob.depth, prob.lum, init_pose=Xk)
+            st = ctx.solve_global(ids, **params(prob, 1))
+            assert st["flags"] == 0
+            assert abs(st["energy"][0] - S.energy) <= ENERGY_RTOL * S.energy, (k, st["energy"][0], S.energy)
+            assert abs(st["energy"][0] - golden["energy"][k]) <= ENERGY_RTOL * golden["energy"][k]
+            rot, tr = worst_pose_error(ctx.get_poses(ids), Xn)
+            print(f"step {k}: energy rel {abs(st['energy'][0] - S.energy) / S.energy:.2e}, pose {rot:.2e} rad "
+                  f"{tr:.2e} m, association flips {rep.n_flips} of {rep.n_valid}")
+            assert rot <= ROT_TOL and tr <= TRANS_TOL, (k, rot, tr)
+    assert rep.n_flips <= 1e-4 * rep.n_valid
+
+
+def test_global300_whole_bench_solve_matches_oracle(bf, global300, golden):
+    """The bench's own solve (8 GN x 20 PCG, graph captured then replayed): all nine energies."""
     ctx = make_ctx(bf, global300)
     ids = list(range(global300.n_frames))
     for _ in range(2):  # capture, then replay the graph
         ctx.add_frames(0, global300.depth, global300.lum, init_pose=global300.init)
-        st = ctx.solve_global(ids, **params(global300, 1))
-        assert st["flags"] == 0
-        rel = np.abs(np.array(st["energy"]) - np.array(golden["energy"])) / np.array(golden["energy"])
+        st = ctx.solve_global(ids, **params(global300, global300.solve["n_gn"]))
+        assert st["flags"] == 0 and st["n_gn"] == global300.solve["n_gn"]
+        gold = np.array(golden["energy"])
+        rel = np.abs(np.array(st["energy"]) - gold) / gold
+        rot, tr = worst_pose_error(ctx.get_poses(ids), poses44(golden["poses"]))
+        print(f"whole solve: energy rel max {rel.max():.2e}, final poses {rot:.2e} rad {tr:.2e} m")
         assert rel.max() <= ENERGY_RTOL, rel
-        P = ctx.get_poses(ids)
-        worst_rot = worst_tr = 0.0
-        for k in range(len(ids)):
-            ref = np.eye(4)
-            ref[:3, :] = np.array(golden["poses"][k]).reshape(3, 4)
-            rot, tr = lie.pose_error(P[k], ref)
-            worst_rot, worst_tr = max(worst_rot, rot), max(worst_tr, tr)
-        assert worst_rot <= ROT_TOL and worst_tr <= TRANS_TOL, (worst_rot, worst_tr)
-
-
-def test_global300_bench_solve_starts_at_the_oracle_energy(bf, global300, golden):
-    """The bench's own solve (8 GN x 20 PCG): its first energy is the oracle's at the initial poses and
-    the energy falls from there."""
-    ctx = make_ctx(bf, global300)
-    st = ctx.solve_global(list(range(global300.n_frames)), **params(global300, global300.solve["n_gn"]))
-    assert st["flags"] == 0 and st["n_gn"] == global300.solve["n_gn"]
-    assert abs(st["energy"][0] - golden["energy"][0]) <= ENERGY_RTOL * golden["energy"][0]
-    assert abs(st["energy"][1] - golden["energy"][1]) <= ENERGY_RTOL * golden["energy"][1]
-    assert st["energy"][-1] < 0.8 * st["energy"][0]
+        assert rot <= LOOP_ROT_TOL and tr <= LOOP_TRANS_TOL, (rot, tr)
 
 
 @pytest.fixture(scope="module")
@@ -108,18 +153,19 @@ def golden_chunks():
         return json.load(f)
 
 
-@pytest.mark.parametrize("persistent,tile", [(0, -1), (1, 38400)])
-def test_chunks256_batch_matches_oracle_on_sampled_chunks(bf, chunks256, golden_chunks, persistent, tile):
+@pytest.mark.parametrize("storage,persistent,tile", [("fp32", 0, -1), ("fp32", 1, 38400), ("bf16", 0, -1)])
+def test_chunks256_batch_matches_oracle_on_sampled_chunks(bf, chunks256, golden_chunks, storage, persistent, tile):
     """The whole 256-chunk 320x240 batch in bench.py's configuration (FP32 arithmetic, CUDA graph;
-    autotuned tiles for the launch sequence, half-frame tiles for the persistent launch); a 3-frame
-    and an 11-frame chunk against the oracle's solves."""
+    autotuned tiles for the launch sequence, half-frame tiles for the persistent launch); two chunks
+    of every length 3..11 against the oracle's solves on the same planes."""
     import torch
     prob = chunks256
     assert golden_chunks["workload"] == prob.name and golden_chunks["chunks"] == len(prob.chunks)
     intr = prob.intr
     dev = torch.device("cuda", 0)
+    code = {"fp32": bf.BF_STORE_FP32, "bf16": bf.BF_STORE_BF16}[storage]
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"],
-                     max_frames_hint=prob.n_frames)
+                     max_frames_hint=prob.n_frames, storage=code)
     ctx.add_frames(0, torch.from_numpy(prob.depth).to(dev), torch.from_numpy(prob.lum).to(dev))
     ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
                                   torch.from_numpy(prob.p_j).to(dev))
@@ -129,17 +175,19 @@ def test_chunks256_batch_matches_oracle_on_sampled_chunks(bf, chunks256, golden_
                                   w_sparse=d["w_sparse"], w_dense=d["w_dense"], w_photo=d["w_photo"],
                                   w_geo=d["w_geo"], precision=bf.BF_PREC_FP32, use_graph=1, tile_px=tile,
                                   persistent=persistent)
-    for s in golden_chunks["samples"]:
+    samples = [s for s in golden_chunks["samples"] if s["storage"] == storage]
+    assert sorted({len(s["frames"]) for s in samples}) == list(range(3, 12)) and len(samples) >= 16
+    worst = [0.0, 0.0, 0.0]
+    for s in samples:
         k = s["chunk"]
         assert lists[k] == s["frames"]
         rel = np.abs(np.array(stats[k]["energy"]) - np.array(s["energy"])) / np.array(s["energy"])
+        rot, tr = worst_pose_error(ctx.get_poses(lists[k]), poses44(s["poses"]))
+        worst = [max(worst[0], rot), max(worst[1], tr), max(worst[2], rel.max())]
         assert rel.max() <= ENERGY_RTOL, (k, rel)
-        P = ctx.get_poses(lists[k])
-        for f in range(len(lists[k])):
-            ref = np.eye(4)
-            ref[:3, :] = np.array(s["poses"][f]).reshape(3, 4)
-            rot, tr = lie.pose_error(P[f], ref)
-            assert rot <= ROT_TOL and tr <= TRANS_TOL, (k, f, rot, tr)
+        assert rot <= ROT_TOL and tr <= TRANS_TOL, (k, rot, tr)
+    print(f"{storage} persistent={persistent}: worst {worst[0]:.2e} rad {worst[1]:.2e} m energy {worst[2]:.2e} "
+          f"over {len(samples)} chunks")
 
 
 @pytest.fixture(scope="module")
@@ -155,10 +203,10 @@ def golden2000():
 
 def test_global2000_first_step_matches_oracle(bf, global2000, golden2000):
     """The 2000-keyframe 160x120 solve in bench.py's configuration (BF16 frame storage, mixed
-    precision, tiled dense kernel with the autotuned decomposition, cluster PCG with its blocks in
-    global memory, CUDA graph): its
-    first Gauss-Newton step against the oracle's on the same BF16-rounded planes (energies, and the
-    poses of every 32nd keyframe); the bench's own 10-step solve starts at the same two energies."""
+    precision, tiled dense kernel with the autotuned decomposition, its PCG, CUDA graph): its first
+    Gauss-Newton step against the oracle's on the same BF16-rounded planes (energies, and the poses
+    of every 32nd keyframe); the bench's own 10-step solve starts at the same two energies.  The
+    step's error against the oracle on the unrounded frames (the cost of BF16 storage) is printed."""
     import torch
     prob = global2000
     assert golden2000["workload"] == prob.name and golden2000["n_frames"] == prob.n_frames
@@ -176,15 +224,18 @@ def test_global2000_first_step_matches_oracle(bf, global2000, golden2000):
     ctx.add_frames(0, depth, lum, init_pose=prob.init)
     st = ctx.solve_global(ids, n_gn=1, **common)
     assert st["flags"] == 0
-    gold_e = np.array(golden2000["energy"])
-    rel = np.abs(np.array(st["energy"]) - gold_e) / gold_e
-    assert rel.max() <= ENERGY_RTOL, rel
     P = ctx.get_poses(golden2000["frames_kept"])
-    for k, f in enumerate(golden2000["frames_kept"]):
-        ref = np.eye(4)
-        ref[:3, :] = np.array(golden2000["poses"][k]).reshape(3, 4)
-        rot, tr = lie.pose_error(P[k], ref)
-        assert rot <= ROT_TOL and tr <= TRANS_TOL, (f, rot, tr)
+    for ref_name in ("fp32", "bf16"):
+        g = golden2000[ref_name]
+        gold_e = np.array(g["energy"])
+        rel = np.abs(np.array(st["energy"]) - gold_e) / gold_e
+        rot, tr = worst_pose_error(P, poses44(g["poses"]))
+        print(f"2000 keyframes, BF16 storage vs oracle on {ref_name} planes: energy {rel.max():.2e}, "
+              f"poses {rot:.2e} rad {tr:.2e} m")
+        if ref_name == "bf16":
+            assert rel.max() <= ENERGY_RTOL, rel
+            assert rot <= ROT_TOL and tr <= TRANS_TOL, (rot, tr)
+    gold_e = np.array(golden2000["bf16"]["energy"])
     ctx.add_frames(0, depth, lum, init_pose=prob.init)
     full = ctx.solve_global(ids, n_gn=d["n_gn"], **common)
     assert abs(full["energy"][0] - gold_e[0]) <= ENERGY_RTOL * gold_e[0]

@@ -9,6 +9,7 @@
 import numpy as np
 import pytest
 
+import replay
 import synth
 from oracle import frames as ofr, lie, solver
 from oracle.system import SolveParams, SparsePair
@@ -29,13 +30,14 @@ def test_bf16_160x120_chunk_matches_oracle(bf):
     n = prob.n_frames
     fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr, storage="bf16") for k in range(n)]
     prm = SolveParams(n_gn=3, n_pcg=10, w_dense=0.5)
-    ref = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm)
     intr = prob.intr
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], storage=bf.BF_STORE_BF16)
     ctx.add_frames(0, prob.depth, prob.lum)
     for k, (i, j) in enumerate(prob.pairs):
         p, q = prob.pair_corr(k)
         ctx.add_correspondences(int(i), int(j), p, q)
+    rep = replay.from_ctx(ctx, range(n), intr["W"], intr["H"], storage="bf16")
+    ref = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm, assoc=rep)
     st = ctx.solve_local(0, list(range(n)), n_gn=3, n_pcg=10, w_dense=0.5)
     rel = np.abs(np.array(st["energy"]) - ref.energy) / np.abs(ref.energy)
     assert rel.max() <= 1e-5, rel

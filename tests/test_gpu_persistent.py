@@ -10,6 +10,7 @@ launch sequence does.
 import numpy as np
 import pytest
 
+import replay
 import synth
 from oracle import frames as ofr, lie, solver
 from oracle.system import SolveParams
@@ -106,7 +107,8 @@ def test_persistent_matches_oracle(bf, batch320):
     for k in sorted(range(len(lists)), key=lambda k: len(lists[k]))[:2]:
         ids = lists[k]
         fr = [ofr.Frame(prob.depth[f], prob.lum[f], prob.intr) for f in ids]
-        ref = solver.gauss_newton(fr, prob.intr, prob.init[ids], solver.sparse_pairs_for(prob, ids), prm)
+        rep = replay.from_ctx(ctx, ids, prob.intr["W"], prob.intr["H"])
+        ref = solver.gauss_newton(fr, prob.intr, prob.init[ids], solver.sparse_pairs_for(prob, ids), prm, assoc=rep)
         rel = np.abs(np.array(stats[k]["energy"]) - ref.energy) / np.abs(ref.energy)
         assert rel.max() <= ENERGY_RTOL, (k, rel)
         for f in range(len(ids)):

@@ -10,6 +10,7 @@ import copy
 import numpy as np
 import pytest
 
+import replay
 import synth
 from oracle import frames as ofr, lie, solver
 from oracle.system import SolveParams
@@ -58,7 +59,9 @@ def test_pruning_matches_oracle(bf, bad_chunk):
     n = prob.n_frames
     fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in range(n)]
     prm = SolveParams(n_gn=4, n_pcg=12, w_dense=0.5)
-    ref = solver.gauss_newton_pruned(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm, PRUNE)
+    rep = replay.from_ctx(make_ctx(bf, prob), range(n), prob.intr["W"], prob.intr["H"])
+    ref = solver.gauss_newton_pruned(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm, PRUNE,
+                                     assoc=rep)
     assert ref.pruned == [(1, 4)] and ref.rounds == 2  # the scenario does what it is meant to
     ctx = make_ctx(bf, prob)
     st = ctx.solve_local(3, list(range(n)), n_gn=4, n_pcg=12, w_dense=0.5, prune_rmax=PRUNE)

@@ -1,9 +1,11 @@
 """GPU parity of the dense verification (Sec. 4.1.1) and chunk validation (Sec. 4.2) kernels.
 
-The gate decisions are FP32 with the oracle's operation order, so kept-correspondence counts
-agree exactly except where the normal gate sits within FP32 rounding of tau_n (the two sides
-round their normals independently): at most max(2, 1e-3 n) differences.  Distance sums are
-FP32 per pixel and thread, FP64 across warps: relative 1e-5.
+The library decides the gates in FP32, the oracle in FP64; they agree except on ties (a value
+within FP32 rounding of its threshold, which either side may decide either way).  So the
+library's kept count must lie between the oracle's count of kept non-tie pixels and that plus
+the ties, and its distance sum between the non-tie sum and that plus tau_d per tie (a kept pixel is
+closer than tau_d), up to the FP32 summation's rounding (relative 1e-5).  With no tie the two must
+agree exactly in count.
 """
 import numpy as np
 import pytest
@@ -37,8 +39,18 @@ def make_ctx(bf, prob, storage=0):
     return ctx
 
 
-def close_counts(a, b):
-    return abs(a - b) <= max(2, int(1e-3 * max(a, b)))
+def mean_bounds(chk):
+    """Range of a pair's two-sided mean error over every way of deciding its ties."""
+    n_lo = chk.bounds("ij")[0] + chk.bounds("ji")[0]
+    n_hi = chk.bounds("ij")[1] + chk.bounds("ji")[1]
+    e_lo = chk.bounds("ij")[2] + chk.bounds("ji")[2]
+    e_hi = chk.bounds("ij")[3] + chk.bounds("ji")[3]
+    return e_lo / max(n_hi, 1), e_hi / max(n_lo, 1)
+
+
+def within_bounds(ref, direction, n, e, rtol=1e-5):
+    n_lo, n_hi, e_lo, e_hi = ref.bounds(direction)
+    return n_lo <= n <= n_hi and e_lo * (1 - rtol) - 1e-9 <= e <= e_hi * (1 + rtol) + 1e-9
 
 
 def perturbed_rel(T, seed, rot=0.02, trans=0.03):
@@ -62,17 +74,22 @@ def test_verify_pairs_matches_oracle(bf, cfg1, kind):
             pairs.append((i, j))
             rels.append(rel)
     got = ctx.verify_pairs(pairs, np.stack(rels))
-    n_checked = 0
+    n_decided = 0
     for (i, j), rel, g in zip(pairs, rels, got):
         ref = verification.verify_pair(fr[i], fr[j], rel, cfg1.intr)
-        assert close_counts(g["n_ij"], ref.n_ij) and close_counts(g["n_ji"], ref.n_ji), (i, j, g, ref)
-        for ge, re_, gn, rn in ((g["err_ij"], ref.e_ij, g["n_ij"], ref.n_ij), (g["err_ji"], ref.e_ji, g["n_ji"], ref.n_ji)):
-            if gn == rn:
-                assert abs(ge - re_) <= 1e-5 * max(re_, 1e-9), (ge, re_)
-        if g["n_ij"] == ref.n_ij and g["n_ji"] == ref.n_ji:
-            assert g["valid"] == verification.pair_valid(ref, cfg1.intr)
-            n_checked += 1
-    assert n_checked >= len(pairs) - 2
+        assert within_bounds(ref, "ij", g["n_ij"], g["err_ij"]), (i, j, g, ref)
+        assert within_bounds(ref, "ji", g["n_ji"], g["err_ji"]), (i, j, g, ref)
+        # the ties are few: the counts differ from the oracle's by at most the pair's ties
+        assert ref.tie_ij + ref.tie_ji <= 1e-3 * max(ref.n_ij + ref.n_ji, 1000)
+        # validity where no way of deciding the ties could change it
+        lo, hi = mean_bounds(ref)
+        n_lo = ref.bounds("ij")[0] + ref.bounds("ji")[0]
+        n_hi = ref.bounds("ij")[1] + ref.bounds("ji")[1]
+        min_n = 0.02 * cfg1.intr["W"] * cfg1.intr["H"]
+        if (hi <= 0.075 and n_lo >= min_n) or lo > 0.075 or n_hi < min_n:
+            assert g["valid"] == verification.pair_valid(ref, cfg1.intr), (i, j, g, ref)
+            n_decided += 1
+    assert n_decided >= len(pairs) - 2
     assert any(g["valid"] for g in got) and not all(g["valid"] for g in got)  # both outcomes exercised
 
 
@@ -93,15 +110,21 @@ def test_chunk_validation_matches_oracle(bf, cfg1):
     g = ctx.validate_chunk(0)
     local = ctx.get_poses(ids)
     local = np.einsum("ab,kbc->kac", np.linalg.inv(local[0]), local)
-    ok, worst, arg, _ = verification.validate_chunk(fr, local, cfg1.intr)
+    ok, worst, arg, checks = verification.validate_chunk(fr, local, cfg1.intr)
     assert g["valid"] == ok and ok
-    assert abs(g["worst_err"] - worst) <= 1e-4 * worst  # the poses went through the 4x4 round trip
+    # the worst pair's mean error within what the ties allow (the poses went through the 4x4 round trip)
+    bounds = [mean_bounds(c) for c in checks.values() if c.n_ij + c.n_ji > 0]
+    lo, hi = max(b[0] for b in bounds), max(b[1] for b in bounds)
+    assert lo * (1 - 1e-4) <= g["worst_err"] <= hi * (1 + 1e-4), (g["worst_err"], lo, hi, worst)
     # an unsolved chunk (no Gauss-Newton step: every frame at the identity) fails validation
     ctx.solve_local(1, ids, n_gn=0)
     bad = ctx.validate_chunk(1)
     ref_bad = verification.validate_chunk(fr, np.tile(np.eye(4), (11, 1, 1)), cfg1.intr)
     assert not bad["valid"] and not ref_bad[0]
-    assert abs(bad["worst_err"] - ref_bad[1]) <= 1e-5 * ref_bad[1] and bad["worst_pair"] == ref_bad[2]
+    bounds = [mean_bounds(c) for c in ref_bad[3].values() if c.n_ij + c.n_ji > 0]
+    lo, hi = max(b[0] for b in bounds), max(b[1] for b in bounds)
+    assert lo * (1 - 1e-5) <= bad["worst_err"] <= hi * (1 + 1e-5)
+    assert bad["worst_pair"] == ref_bad[2] or mean_bounds(ref_bad[3][tuple(bad["worst_pair"])])[1] >= lo
 
 
 def test_validate_unknown_chunk(bf, cfg1):

@@ -4,6 +4,7 @@ import ctypes
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 import paper_1604_01093_b300 as bf
@@ -68,3 +69,28 @@ def test_null_context_is_rejected_without_gpu():
     assert L.bf_destroy(None) == 0
     assert L.bf_solve_local(None, 0, None, 0, None, None) == 1
     assert L.bf_add_frames(None, 0, 0, None, None, 0, None) == 1
+
+
+def test_noalloc_rejects_bad_arguments_before_touching_the_gpu():
+    """bf_dense_pair_noalloc checks its arguments before any CUDA call, so this runs without a GPU:
+    frame sizes outside 8..160 x 8..120, a depth range that is empty, and non-finite gates or weights
+    are BF_ERR_INVALID_ARG.  (The device pointers are never dereferenced on the host.)"""
+    import ctypes
+    import math
+
+    from paper_1604_01093_b300 import _lib
+
+    L = _lib.lib()
+    fake = ctypes.c_void_p(256)
+    eye = np.eye(4).ravel().copy()
+
+    def call(W=80, H=60, dmin=0.1, dmax=10.0, **kw):
+        p = _lib.default_params(**kw)
+        return L.bf_dense_pair_noalloc(W, H, 65.625, 65.625, (W - 1) / 2, (H - 1) / 2, dmin, dmax, fake, fake, fake,
+                                       fake, eye.ctypes.data, eye.ctypes.data, ctypes.byref(p), fake, None)
+
+    bad = [dict(W=320, H=240), dict(W=161), dict(H=121), dict(W=4), dict(dmin=2.0, dmax=1.0), dict(dmin=1.0, dmax=1.0),
+           dict(tau_dist=0.0), dict(tau_dist=math.nan), dict(tau_normal=math.nan), dict(w_dense=math.inf),
+           dict(w_photo=math.nan), dict(w_geo=-math.inf)]
+    for kw in bad:
+        assert call(**kw) == 1, kw  # BF_ERR_INVALID_ARG
