@@ -278,6 +278,23 @@ bf_status bf_debug_association(bf_ctx *ctx, int frame_i, int frame_j, const doub
                                const double *pose_j, const bf_solve_params *params, int32_t *out_target);
 
 /*
+ * Association recording (debug; the parity protocol of the tests, Sec. 4.3 dense matching).
+ * While enabled, solves of a single problem (bf_solve_local, bf_solve_global; not batches, not
+ * serving) run kernel by kernel (no graph, no persistent launch) and record, for every dense
+ * evaluation e (e < n_gn: the linearisation of Gauss-Newton iteration e; e = n_gn: the final
+ * energy), the associated target pixel of every source pixel of every directed pair, and the poses
+ * the evaluation used.  The last such solve's record stays on the host until the next one.
+ * Device memory: (n_gn + 1) x directed pairs x H x W ints while a solve runs.  Disabling frees it.
+ */
+bf_status bf_debug_record_association(bf_ctx *ctx, int enable);
+/* The recorded association of directed pair frame_i -> frame_j (source i) at evaluation eval:
+ * out_target (host, H x W int32): target pixel index y W + x, or -1; pose_i, pose_j (host, 16
+ * doubles each, row-major camera -> world as the solve held them; nullable).  BF_ERR_NOT_FOUND if
+ * nothing was recorded or the pair was not a dense pair of the recorded solve. */
+bf_status bf_debug_recorded_association(bf_ctx *ctx, int eval, int frame_i, int frame_j, int32_t *out_target,
+                                        double *pose_i, double *pose_j);
+
+/*
  * Kernel accounting.  Every kernel the context launches is counted; with profiling enabled the
  * context also records a CUDA event pair around each launch on its stream and sums the device
  * time per kernel class.  bf_get_profile synchronises the stream.  The pose update and the

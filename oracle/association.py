@@ -131,32 +131,55 @@ def replay(asc_own, target, W, H):
 EPS_PX, EPS_D, EPS_N = 5e-4, 2e-5, 2e-4
 
 
+def check_replay(own, target, W, H, eps=(EPS_PX, EPS_D, EPS_N), own_replay=None):
+    """Check another implementation's decisions ``target`` (flat target index or -1 per source pixel)
+    against this oracle's association ``own`` (taken at the poses those decisions were taken at):
+    they may differ only on ties.  Returns the replayed association (with the bilinear taps of
+    ``own_replay``, this oracle's association at its own poses, default ``own``), the number of
+    valid pixels (of own), the number of differing decisions (flips), and None or the description
+    of the first disagreement outside the rounding bounds."""
+    target = np.asarray(target).ravel()
+    ref = targets(own, W)
+    diff = target != ref
+    bad = np.flatnonzero(diff & ~ties(own, *eps))
+    err = None
+    if len(bad):
+        k = bad[0]
+        err = (f"{len(bad)} decisions differ outside the rounding bounds; first at pixel {k}: other {target[k]}, "
+               f"oracle {ref[k]} (u = {own['ux'][k]:.6f}, {own['uy'][k]:.6f}; margins {own['margin_px'][k]:.3g} px, "
+               f"{own['margin_d'][k]:.3g} m, {own['margin_n'][k]:.3g})")
+    return replay(own if own_replay is None else own_replay, target, W, H), int((ref >= 0).sum()), int(diff.sum()), err
+
+
 class CheckedReplay:
     """Association provider for system.assemble that replays another implementation's decisions.
 
     fetch(i, j, poses) returns that implementation's flat target index (or -1) per source pixel of
-    the directed pair i -> j at the given poses.  Each call checks it against this oracle's own
-    decisions: they may differ only on ties (AssertionError otherwise).  Counts the valid pixels
-    (of the oracle's association) and the differing decisions (flips) over all calls."""
+    the directed pair i -> j; check_poses(i, j), if defined, the 4x4 poses of i and j at which it
+    took them (None: the poses the oracle passes).  The oracle checks them against its own
+    association at those poses with check_replay (AssertionError on a disagreement outside the
+    rounding bounds) and replays them at its own poses.  ``iteration`` is set by the Gauss-Newton
+    loop before each assembly (its linearisation index; n_gn for the final energy).  Counts the
+    valid pixels (of the oracle's association) and the differing decisions (flips)."""
 
     def __init__(self, fetch, W, H, eps=(EPS_PX, EPS_D, EPS_N)):
         self.fetch, self.W, self.H, self.eps = fetch, W, H, eps
         self.n_valid = 0
         self.n_flips = 0
         self.calls = 0
+        self.iteration = 0
+
+    def check_poses(self, i, j):
+        return None
+
+    def record(self, n_valid, n_flips, err, i, j):
+        if err:
+            raise AssertionError(f"evaluation {self.iteration}, pair {i}->{j}: {err}")
+        self.n_valid += n_valid
+        self.n_flips += n_flips
+        self.calls += 1
 
     def __call__(self, i, j, poses, own):
-        target = np.asarray(self.fetch(i, j, poses)).ravel()
-        ref = targets(own, self.W)
-        diff = target != ref
-        bad = np.flatnonzero(diff & ~ties(own, *self.eps))
-        if len(bad):
-            k = bad[0]
-            raise AssertionError(
-                f"pair {i}->{j}: {len(bad)} decisions differ outside the rounding bounds; first at pixel {k}: "
-                f"other {target[k]}, oracle {ref[k]} (u = {own['ux'][k]:.6f}, {own['uy'][k]:.6f}; margins "
-                f"{own['margin_px'][k]:.3g} px, {own['margin_d'][k]:.3g} m, {own['margin_n'][k]:.3g})")
-        self.n_valid += int((ref >= 0).sum())
-        self.n_flips += int(diff.sum())
-        self.calls += 1
-        return replay(own, target, self.W, self.H)
+        rep, nv, nf, err = check_replay(own, self.fetch(i, j, poses), self.W, self.H, self.eps)
+        self.record(nv, nf, err, i, j)
+        return rep

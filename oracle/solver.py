@@ -117,17 +117,20 @@ class GNResult:
     pcg_iters: list
 
 
-def gauss_newton(frames, intr, poses0, sparse_pairs, params: SolveParams, direct=False, assoc=None, pmap=None):
+def gauss_newton(frames, intr, poses0, sparse_pairs, params: SolveParams, direct=False, assoc=None, pmap=None,
+                 frame_keys=None):
     """Sec. 4.4 Gauss-Newton: n_gn linearisations, each solved by PCG (or Cholesky if direct).
 
-    assoc, pmap: optional association provider (replayed decisions) and parallel map over the
-    directed pairs, passed to system.assemble."""
+    assoc, pmap, frame_keys: optional association provider (replayed decisions), parallel map over
+    the directed pairs and the workers' frame keys, passed to system.assemble."""
     poses = np.array(poses0, dtype=np.float64)
     dense_pairs = system.dense_pair_set(poses, sparse_pairs, params.max_angle_deg) if params.dense_on else []
     res = GNResult(None, [], [], [], [], [], [], [poses.copy()], 0.0, (-1, -1), [])
     for k in range(params.n_gn):
         wd = params.w_dense_at(k)
-        S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd, assoc, pmap)
+        if assoc is not None:
+            assoc.iteration = k
+        S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd, assoc, pmap, frame_keys)
         res.energy.append(S.energy)
         res.e_sparse.append(S.e_sparse)
         res.e_geo.append(S.e_geo)
@@ -144,7 +147,9 @@ def gauss_newton(frames, intr, poses0, sparse_pairs, params: SolveParams, direct
         poses = apply_step(poses, delta)
         res.pose_history.append(poses.copy())
     wd = params.w_dense_at(params.n_gn - 1) if params.n_gn > 0 else params.w_dense
-    S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd, assoc, pmap)
+    if assoc is not None:
+        assoc.iteration = params.n_gn
+    S = system.assemble(frames, intr, poses, sparse_pairs, dense_pairs, params, wd, assoc, pmap, frame_keys)
     res.energy.append(S.energy)
     res.e_sparse.append(S.e_sparse)
     res.e_geo.append(S.e_geo)

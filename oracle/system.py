@@ -124,16 +124,32 @@ def dense_pair(frames, task):
     """Dense photometric and geometric contribution of one directed pair i -> j (Sec. 4.3).
 
     task = (i, j, poses (4x4 of i and j), intr, tau_d, tau_n, w_geo, w_photo, asc): weights already
-    multiplied by w_dense (0 = energies only); asc None = this oracle's own association.
+    multiplied by w_dense (0 = energies only); asc None = this oracle's own association, a dict = a
+    given association, ("replay", target, W, H, eps, check_poses) = another implementation's
+    decisions to check against this oracle's (at check_poses = (T_i, T_j), or at the task's poses
+    if None) and replay at the task's poses (association.check_replay; the result's "check" holds
+    the valid count, the flips and the first disagreement).
     Returns the residual count, both energies and the row products of the two residual kinds."""
     i, j, Ti, Tj, intr, tau_d, tau_n, w_geo, w_photo, asc = task
     Ri, ti, Rj, tj = Ti[:3, :3], Ti[:3, 3], Tj[:3, :3], Tj[:3, 3]
-    if asc is None:
-        asc = association.associate(frames[i], frames[j], association.relative_transform(Ri, ti, Rj, tj), intr,
+    check = None
+    if asc is None or (isinstance(asc, tuple) and asc[0] == "replay"):
+        own = association.associate(frames[i], frames[j], association.relative_transform(Ri, ti, Rj, tj), intr,
                                     tau_d, tau_n)
+        if asc is None:
+            asc = own
+        else:  # another implementation's decisions, checked here (association.check_replay)
+            _, target, W, H, eps, cp = asc
+            own_c = own
+            if cp is not None:  # checked at the poses they were taken at
+                Ci, Cj = cp
+                own_c = association.associate(frames[i], frames[j], association.relative_transform(
+                    Ci[:3, :3], Ci[:3, 3], Cj[:3, :3], Cj[:3, 3]), intr, tau_d, tau_n)
+            asc, nv, nf, err = association.check_replay(own_c, target, W, H, eps, own_replay=own)
+            check = (nv, nf, err)
     d = residuals.dense_terms(frames[i], frames[j], Ri, ti, Rj, tj, asc)
     k = len(d["idx"])
-    out = dict(k=k, e_geo=float(np.sum(d["r_geo"] ** 2)), e_photo=float(np.sum(d["r_photo"] ** 2)))
+    out = dict(k=k, e_geo=float(np.sum(d["r_geo"] ** 2)), e_photo=float(np.sum(d["r_photo"] ** 2)), check=check)
     if w_geo != 0.0 or w_photo != 0.0:
         out["geo"] = row_products(d["J_geo_i"], d["J_geo_j"], d["r_geo"], np.full(k, w_geo))
         out["photo"] = row_products(d["J_photo_i"], d["J_photo_j"], d["r_photo"], np.full(k, w_photo))
@@ -158,9 +174,8 @@ def assemble(frames, intr, poses, sparse_pairs, dense_pairs, params: SolveParams
 
     frames: preprocessed frames (frames.Frame) of the solve, index 0 = gauge frame.
     poses: (n,4,4) camera->world.  Returns a System.
-    assoc: optional callable (i, j, poses, own) -> association that replaces this oracle's own
-    association ``own`` of the directed pair i -> j (association.replay of decisions taken by
-    another implementation, which the caller has checked against ``own``); None keeps the
+    assoc: optional association.CheckedReplay: another implementation's decisions, checked
+    against this oracle's own (ties may differ) and replayed in place of them; None keeps the
     oracle's decisions.
     pmap: optional order-preserving map (e.g. a process pool's, initialised with init_worker(frames))
     over the directed pairs; each pair is evaluated alone and the sums are taken in pair order.
@@ -187,9 +202,9 @@ def assemble(frames, intr, poses, sparse_pairs, dense_pairs, params: SolveParams
             for (i, j) in ((a, b), (b, a)):
                 asc = None
                 if assoc is not None:
-                    own = association.associate(frames[i], frames[j], association.relative_transform(R[i], t[i], R[j], t[j]),
-                                                intr, params.tau_dist, params.tau_normal)
-                    asc = {k: v for k, v in assoc(i, j, poses, own).items() if k in ("valid", "nx", "ny", "bx", "by")}
+                    # checked replay (dense_pair compares the fetched decisions with its own)
+                    asc = ("replay", np.asarray(assoc.fetch(i, j, poses)), assoc.W, assoc.H, assoc.eps,
+                           assoc.check_poses(i, j))
                 tasks.append((i, j, poses[i], poses[j], intr, params.tau_dist, params.tau_normal, wg, wp, asc))
                 order.append((i, j))
         if pmap is not None:
@@ -199,6 +214,8 @@ def assemble(frames, intr, poses, sparse_pairs, dense_pairs, params: SolveParams
         else:
             results = (dense_pair(frames, tk) for tk in tasks)
         for (i, j), res in zip(order, results):
+            if res["check"] is not None:
+                assoc.record(*res["check"], i, j)
             S.n_dense += res["k"]
             S.e_geo += res["e_geo"]
             S.e_photo += res["e_photo"]

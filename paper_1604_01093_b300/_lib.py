@@ -150,6 +150,8 @@ def lib():
         "bf_build_system": (I, [P, P, I, P, ctypes.POINTER(SolveParams), P, P, P, P]),
         "bf_get_frame_planes": (I, [P, I, P]),
         "bf_debug_association": (I, [P, I, I, P, P, ctypes.POINTER(SolveParams), P]),
+        "bf_debug_record_association": (I, [P, I]),
+        "bf_debug_recorded_association": (I, [P, I, I, I, P, P, P]),
         "bf_device_bytes": (ctypes.c_size_t, [P]),
         "bf_set_profiling": (I, [P, I]),
         "bf_get_profile": (I, [P, ctypes.POINTER(Profile)]),
@@ -187,7 +189,8 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_last_error", "bf_add_frames", "bf_add_correspondences", "bf_add_correspondences_batch",
            "bf_remove_pair", "bf_set_profiling", "bf_get_profile", "bf_reset_profile",
            "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
-           "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association", "bf_device_bytes",
+           "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association",
+           "bf_debug_record_association", "bf_debug_recorded_association", "bf_device_bytes",
            "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait",
            "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk", "bf_default_keypoint_params",
            "bf_filter_keypoints", "bf_selftest_wait_timeout", "bf_default_tsdf_config", "bf_tsdf_init",
@@ -470,6 +473,19 @@ class Context:
         pj = np.ascontiguousarray(pose_j, dtype=np.float64).reshape(16)
         self._check(lib().bf_debug_association(self.h, i, j, _ptr(pi), _ptr(pj), ctypes.byref(p), _ptr(out)))
         return out
+
+    def record_association(self, on=True):
+        """Debug: record the association of every dense evaluation of the next single-problem solves."""
+        self._check(lib().bf_debug_record_association(self.h, 1 if on else 0))
+
+    def recorded_association(self, evaluation, i, j):
+        """(targets (H*W int32), pose_i (4x4), pose_j (4x4)) of directed pair i -> j at a recorded
+        dense evaluation of the last recorded solve."""
+        out = np.zeros(self.W * self.H, dtype=np.int32)
+        pi = np.zeros(16)
+        pj = np.zeros(16)
+        self._check(lib().bf_debug_recorded_association(self.h, evaluation, i, j, _ptr(out), _ptr(pi), _ptr(pj)))
+        return out, pi.reshape(4, 4), pj.reshape(4, 4)
 
     # --------------------------------------------------------------- serving
     def serve_start(self, n_slots=2, max_batch=64, max_queue=1024):

@@ -187,6 +187,19 @@ struct bf_ctx {
   };
   std::vector<Rec> recs;
   size_t rec_used = 0;
+  // association recording (debug): while on, single-problem solves run kernel by kernel and keep
+  // the association of every dense evaluation and the poses it used (the last solve's, on the host)
+  bool assoc_rec = false;
+  int *rec_dev = nullptr;
+  double *rec_pose_dev = nullptr;
+  size_t rec_dev_n = 0, rec_pose_n = 0;  // capacities (ints, doubles)
+  struct AssocRecord {
+    std::vector<int> ids;              // frame ids of the solve, in its local order
+    std::vector<int> dp_src, dp_dst;   // directed pairs (local frame indices)
+    int n_eval = 0;                    // dense evaluations: n_gn linearisations + the final energy
+    std::vector<int> tgt;              // n_eval x n_dp x H x W
+    std::vector<double> pose;          // n_eval x n_frames x 12
+  } rec_last;
 };
 
 // ------------------------------------------------------------------------------- helpers
@@ -499,6 +512,8 @@ extern "C" bf_status bf_destroy(bf_ctx *c) {
   cudaFree(c->slot_dev);
   cudaFree(c->cP);
   cudaFree(c->cQ);
+  cudaFree(c->rec_dev);
+  cudaFree(c->rec_pose_dev);
   free_exec(c, c->main);
   for (auto &r : c->recs) {
     cudaEventDestroy(r.a);
@@ -1098,6 +1113,11 @@ struct DevSolve {
   int *derr;       // set by the staged dense kernel if its bulk copies did not land
   int coop_grid;   // > 0: one large problem solved by the cooperative PCG
   int cluster;     // > 0: one large problem solved on a thread-block cluster of this many CTAs
+  // association recording (debug, bf_debug_record_association): per dense evaluation e, the
+  // targets of every directed pair (n_dp x H x W ints from rec + e n_dp H W) and the poses it
+  // was evaluated at (n_frames x 12 doubles from rec_pose + e n_frames 12); nullptr when off
+  int *rec = nullptr;
+  double *rec_pose = nullptr;
 };
 
 // The cooperative multi-CTA PCG serves single-problem solves with at least this many free frames.
@@ -1438,7 +1458,7 @@ static cudaStream_t side_stream(bf_ctx *c) {
 // stream (a parallel branch of the captured graph), where it fills the SMs the dense launch's
 // last wave leaves idle, and the merge waits for both.
 template <typename Acc>
-void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, int mode) {
+void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, int mode, int *rec = nullptr) {
   const Tables &t = D.t;
   cudaStream_t side = t.n_segs > 0 ? side_stream(c) : nullptr;
   if (side) {
@@ -1451,9 +1471,9 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
   run_k(c, BF_K_DENSE, [&] {
     if (t.n_wi > 0)
       return launch_dense_staged<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
-                                      (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, c->ex->st);
+                                      (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, rec, c->ex->st);
     return launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
-                             (float)(wd * prm.w_photo), (Acc *)D.dpart, nullptr, c->ex->st);
+                             (float)(wd * prm.w_photo), (Acc *)D.dpart, rec, c->ex->st);
   });
   run_k(c, BF_K_SPARSE, [&] {
     return launch_sparse<Acc>(mode, t, c->cP, c->cQ, D.pairM, (float)prm.w_sparse, (Acc *)D.spart, D.srmax,
@@ -1533,9 +1553,16 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
   if (D.persistent) return run_gn_batch<Acc>(c, prm, D);
   const Tables &t = D.t;
   run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
+  const size_t rec_n = (size_t)T.n_dp * c->cfg.width * c->cfg.height;
+  auto record_poses = [&](int e) {
+    if (D.rec_pose)
+      cudaMemcpyAsync(D.rec_pose + (size_t)e * T.n_frames * 12, D.pose, (size_t)T.n_frames * 12 * sizeof(double),
+                      cudaMemcpyDeviceToDevice, c->ex->st);
+  };
   for (int k = 0; k < prm.n_gn; ++k) {
     const double wd = wdense_at(prm, k);
-    linearise<Acc>(c, D, prm, wd, MODE_ACCUM);
+    record_poses(k);
+    linearise<Acc>(c, D, prm, wd, MODE_ACCUM, D.rec ? D.rec + (size_t)k * rec_n : nullptr);
     run_k(c, BF_K_ASSEMBLE, [&] {
       return launch_assemble<Acc>(t, (const Acc *)D.pairblk, prm.precond, (Acc *)D.Dd, (Acc *)D.rhs, D.Df, D.Minv,
                                   D.vflags, c->ex->st);
@@ -1586,7 +1613,8 @@ bf_status run_gn(bf_ctx *c, const HostTables &T, const bf_solve_params &prm, Dev
     if (!po.pairM) run_k(c, BF_K_XFORM, [&] { return launch_pair_xform(t, D.pose, D.pairM, c->ex->st); });
   }
   const double wd = prm.n_gn > 0 ? wdense_at(prm, prm.n_gn - 1) : prm.w_dense;
-  linearise<Acc>(c, D, prm, wd, MODE_ENERGY);
+  record_poses(prm.n_gn);
+  linearise<Acc>(c, D, prm, wd, MODE_ENERGY, D.rec ? D.rec + (size_t)prm.n_gn * rec_n : nullptr);
   run_k(c, BF_K_ENERGY, [&] {
     return launch_energy_reduce<Acc>(t, (const Acc *)D.pairen, D.energy + (size_t)prm.n_gn * T.n_prob * PAIREN, c->ex->st);
   });
@@ -1675,6 +1703,7 @@ struct SolveJob {
   std::vector<int> sizes;  // frames per problem
   size_t n_pose = 0, n_en = 0, o_en = 0, o_vf = 0, o_pf = 0, o_sm = 0, o_sa = 0, o_ce = 0;
   std::chrono::steady_clock::time_point t0;
+  bool rec = false;  // the dense evaluations are being recorded (bf_debug_record_association)
 };
 
 // Phase 1 (context lock held): build the tables, upload, enqueue the Gauss-Newton loop and the
@@ -1721,9 +1750,9 @@ static int tune_tile(bf_ctx *c, const std::vector<Problem> &probs, const bf_solv
       cudaEventRecord(e0, c->ex->st);
       if (D.t.n_wi > 0) {
         if (mixed) launch_dense_staged<double>(MODE_ACCUM, D.t, frame_store(c), c->intr, D.pairM, g, 1.f, 0.1f,
-                                               (double *)D.dpart, D.derr, c->ex->st);
+                                               (double *)D.dpart, D.derr, nullptr, c->ex->st);
         else launch_dense_staged<float>(MODE_ACCUM, D.t, frame_store(c), c->intr, D.pairM, g, 1.f, 0.1f,
-                                        (float *)D.dpart, D.derr, c->ex->st);
+                                        (float *)D.dpart, D.derr, nullptr, c->ex->st);
       } else {
         if (mixed) launch_dense<double>(MODE_ACCUM, D.t, frame_store(c), c->intr, D.pairM, g, 1.f, 0.1f,
                                         (double *)D.dpart, nullptr, c->ex->st);
@@ -1754,6 +1783,11 @@ bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_s
   J.ex = c->ex;
   bf_solve_params prm = prm_in;
   if (prm.tile_px == BF_TILE_AUTOTUNE) prm.tile_px = tune_tile(c, probs, prm);
+  const bool recording = c->assoc_rec && probs.size() == 1 && c->ex == &c->main;
+  if (recording) {  // kernel by kernel, so that every dense launch gets its own slab of the record
+    prm.use_graph = 0;
+    prm.persistent = 0;
+  }
   J.prm = prm;
   J.sizes.clear();
   for (const Problem &P : probs) J.sizes.push_back((int)P.ids.size());
@@ -1766,6 +1800,29 @@ bf_status enqueue_solve(bf_ctx *c, const std::vector<Problem> &probs, const bf_s
   s = prepare(c, T, prm.n_gn, acc_size, false, D, prm.pcg_variant, prm.sparse_mode == BF_SPARSE_MATFREE,
               prm.persistent != 0);
   if (s) return s;
+  D.rec = nullptr;
+  D.rec_pose = nullptr;
+  if (recording) {
+    const size_t n_eval = (size_t)prm.n_gn + 1;
+    const size_t ni = n_eval * T.n_dp * c->cfg.width * c->cfg.height, nd = n_eval * T.n_frames * 12;
+    if (ni > c->rec_dev_n) {
+      cudaFree(c->rec_dev);
+      c->rec_dev = nullptr;
+      c->rec_dev_n = 0;
+      CK(cudaMalloc(&c->rec_dev, std::max<size_t>(ni, 1) * sizeof(int)), "association record");
+      c->rec_dev_n = ni;
+    }
+    if (nd > c->rec_pose_n) {
+      cudaFree(c->rec_pose_dev);
+      c->rec_pose_dev = nullptr;
+      c->rec_pose_n = 0;
+      CK(cudaMalloc(&c->rec_pose_dev, std::max<size_t>(nd, 1) * sizeof(double)), "pose record");
+      c->rec_pose_n = nd;
+    }
+    D.rec = c->rec_dev;
+    D.rec_pose = c->rec_pose_dev;
+    J.rec = true;
+  }
   if (prm.use_graph && !c->prof) {
     s = run_gn_graph(c, T, prm, D, mixed);
   } else {
@@ -1885,6 +1942,18 @@ bf_status solve_once(bf_ctx *c, const std::vector<Problem> &probs, const bf_solv
   bf_status s = enqueue_solve(c, probs, prm, J);
   if (s) return s;
   CK(cudaStreamSynchronize(c->ex->st), "solve");
+  if (J.rec) {  // the recorded association of every dense evaluation and the poses it used
+    const HostTables &T = J.T;
+    bf_ctx::AssocRecord &R = c->rec_last;
+    R.ids = probs[0].ids;
+    R.dp_src.assign(T.dp_src.begin(), T.dp_src.begin() + T.n_dp);
+    R.dp_dst.assign(T.dp_dst.begin(), T.dp_dst.begin() + T.n_dp);
+    R.n_eval = J.prm.n_gn + 1;
+    R.tgt.resize((size_t)R.n_eval * T.n_dp * c->cfg.width * c->cfg.height);
+    R.pose.resize((size_t)R.n_eval * T.n_frames * 12);
+    CK(cudaMemcpy(R.tgt.data(), c->rec_dev, R.tgt.size() * sizeof(int), cudaMemcpyDeviceToHost), "record");
+    CK(cudaMemcpy(R.pose.data(), c->rec_pose_dev, R.pose.size() * sizeof(double), cudaMemcpyDeviceToHost), "record");
+  }
   return finish_solve(c, J, out, stats);
 }
 
@@ -2729,6 +2798,53 @@ extern "C" bf_status bf_debug_association(bf_ctx *c, int frame_i, int frame_j, c
   CK(cudaGetLastError(), "association launch");
   CK(cudaMemcpyAsync(out_target, D.assoc, HW * sizeof(int), cudaMemcpyDeviceToHost, c->ex->st), "association");
   CK(cudaStreamSynchronize(c->ex->st), "association");
+  return BF_OK;
+}
+
+extern "C" bf_status bf_debug_record_association(bf_ctx *c, int enable) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  c->assoc_rec = enable != 0;
+  if (!c->assoc_rec) {
+    cudaFree(c->rec_dev);
+    cudaFree(c->rec_pose_dev);
+    cudaGetLastError();
+    c->rec_dev = nullptr;
+    c->rec_pose_dev = nullptr;
+    c->rec_dev_n = c->rec_pose_n = 0;
+    c->rec_last = bf_ctx::AssocRecord();
+  }
+  return BF_OK;
+}
+
+extern "C" bf_status bf_debug_recorded_association(bf_ctx *c, int eval, int frame_i, int frame_j,
+                                                   int32_t *out_target, double *pose_i, double *pose_j) {
+  if (!c) return BF_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(c->mu);
+  const bf_ctx::AssocRecord &R = c->rec_last;
+  if (!out_target) return fail(c, BF_ERR_INVALID_ARG, "bf_debug_recorded_association: null output");
+  if (R.n_eval == 0) return fail(c, BF_ERR_NOT_FOUND, "bf_debug_recorded_association: nothing recorded");
+  if (eval < 0 || eval >= R.n_eval)
+    return fail(c, BF_ERR_INVALID_ARG, "bf_debug_recorded_association: evaluation index out of range");
+  const int n = (int)R.ids.size(), n_dp = (int)R.dp_src.size();
+  int li = -1, lj = -1;
+  for (int k = 0; k < n; ++k) {
+    if (R.ids[k] == frame_i) li = k;
+    if (R.ids[k] == frame_j) lj = k;
+  }
+  int d = -1;
+  for (int k = 0; k < n_dp && li >= 0 && lj >= 0; ++k)
+    if (R.dp_src[k] == li && R.dp_dst[k] == lj) d = k;
+  if (d < 0) return fail(c, BF_ERR_NOT_FOUND, "bf_debug_recorded_association: pair not in the recorded solve");
+  const size_t HW = (size_t)c->cfg.width * c->cfg.height;
+  std::memcpy(out_target, R.tgt.data() + ((size_t)eval * n_dp + d) * HW, HW * sizeof(int32_t));
+  auto pose16 = [&](int l, double *o) {
+    const double *p = R.pose.data() + ((size_t)eval * n + l) * 12;
+    const double m[16] = {p[0], p[1], p[2], p[9], p[3], p[4], p[5], p[10], p[6], p[7], p[8], p[11], 0, 0, 0, 1};
+    std::memcpy(o, m, sizeof(m));
+  };
+  if (pose_i) pose16(li, pose_i);
+  if (pose_j) pose16(lj, pose_j);
   return BF_OK;
 }
 

@@ -454,7 +454,7 @@ bool dense_staged_fits(int W, int H, int storage);
 int dense_staged_smem(int W, int H, int storage);
 template <typename Part>
 int launch_dense_staged(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
-                        float w_geo, float w_photo, Part *part, int *err, cudaStream_t st);
+                        float w_geo, float w_photo, Part *part, int *err, int *rec, cudaStream_t st);
 template <typename Part>
 int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                   float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st);

@@ -31,37 +31,50 @@ struct DenseOcc {
   static constexpr int value = (KIND == BF_STORE_FP32 && MODE == MODE_ACCUM) ? 3 : 4;
 };
 
-template <int MODE, int KIND, typename Part>
+// REC (debug): the association of every source pixel is also written to assoc[d * H * W + px].
+template <int MODE, int KIND, typename Part, bool REC>
 __global__ void __launch_bounds__(DENSE_BS, DenseOcc<MODE, KIND>::value)
     k_dense(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo, float w_photo,
             Part *__restrict__ part, int *__restrict__ assoc) {
   extern __shared__ float ktab[];  // kx[W], ky[H]
   __shared__ float red[DENSE_BS / 32][NPD];
-  dense_tile<MODE, KIND, Part>(blockIdx.x, t, fs, in, pairM, g, w_geo, w_photo, part, assoc, ktab, red);
+  dense_tile<MODE, KIND, Part, false, REC>(blockIdx.x, t, fs, in, pairM, g, w_geo, w_photo, part, assoc, ktab, red);
 }
 
-template <int MODE, typename Part>
+template <int MODE, typename Part, bool REC>
 static void dense_go(int kind, int n, size_t ks, cudaStream_t st, const Tables &t, const FrameStore &fs,
                      const Intr &in, const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *assoc) {
   if (kind == BF_STORE_BF16)
-    k_dense<MODE, BF_STORE_BF16, Part><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    k_dense<MODE, BF_STORE_BF16, Part, REC><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else if (kind == BF_STORE_FP16)
-    k_dense<MODE, BF_STORE_FP16, Part><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    k_dense<MODE, BF_STORE_FP16, Part, REC><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else
-    k_dense<MODE, BF_STORE_FP32, Part><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    k_dense<MODE, BF_STORE_FP32, Part, REC><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
 }
 
+// assoc: MODE_ASSOC's output; in the other modes nullptr, or (debug) the buffer that records the
+// association of every source pixel of every directed pair (H * W ints per directed pair).
 template <typename Part>
 int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                   float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st) {
   if (t.n_tiles == 0) return 0;
   const size_t ks = (size_t)(in.W + in.H) * sizeof(float);
-  if (mode == MODE_ACCUM)
-    dense_go<MODE_ACCUM>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
-  else if (mode == MODE_ENERGY)
-    dense_go<MODE_ENERGY>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
-  else
-    dense_go<MODE_ASSOC>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+  if (mode == MODE_ACCUM) {
+    if (assoc)
+      dense_go<MODE_ACCUM, Part, true>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    else
+      dense_go<MODE_ACCUM, Part, false>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part,
+                                        nullptr);
+  } else if (mode == MODE_ENERGY) {
+    if (assoc)
+      dense_go<MODE_ENERGY, Part, true>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part,
+                                        assoc);
+    else
+      dense_go<MODE_ENERGY, Part, false>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part,
+                                         nullptr);
+  } else {
+    dense_go<MODE_ASSOC, Part, false>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+  }
   return 1;
 }
 
@@ -110,10 +123,10 @@ __device__ __forceinline__ void quad_reduce_store(float (&acc)[N], float (*red)[
   asm volatile("bar.sync %0, 128;" ::"r"(1 + quad) : "memory");  // red reused by the next pair
 }
 
-template <int MODE, int KIND, typename Part>
+template <int MODE, int KIND, typename Part, bool REC>
 __global__ void __launch_bounds__(STG_BS, 1)
     k_dense_staged(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo,
-                   float w_photo, Part *__restrict__ part, int *__restrict__ err) {
+                   float w_photo, Part *__restrict__ part, int *__restrict__ err, int *__restrict__ rec) {
   extern __shared__ __align__(128) float4 stg[];
   __shared__ __align__(8) unsigned long long bar;
   __shared__ float red[STG_QUADS][4][NPD];
@@ -179,7 +192,8 @@ __global__ void __launch_bounds__(STG_BS, 1)
         if (w.px + 128 < HW) a_next = As[w.px + 128];
         const int px = w.px;
         auto srcI = [&]() { return Bs[px].x; };
-        eval_pixel<MODE>(a, w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
+        const int tgt = eval_pixel<MODE>(a, w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
+        if (REC) rec[(long long)d * HW + px] = tgt;
       }
     } else {
       const uint4 *__restrict__ Ps = fs.P16 + so;
@@ -191,7 +205,9 @@ __global__ void __launch_bounds__(STG_BS, 1)
         const uint4 r = r_next;
         if (w.px + 128 < HW) r_next = Ps[w.px + 128];
         auto srcI = [&]() { return unpack16_i<KIND>(r).x; };
-        eval_pixel<MODE>(unpack16_dn<KIND>(r), w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
+        const int tgt = eval_pixel<MODE>(unpack16_dn<KIND>(r), w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo,
+                                         w_photo, acc);
+        if (REC) rec[(long long)d * HW + w.px] = tgt;
       }
     }
     float sums[NPD];
@@ -200,43 +216,58 @@ __global__ void __launch_bounds__(STG_BS, 1)
   }
 }
 
-template <int MODE, int KIND, typename Part>
+template <int MODE, int KIND, typename Part, bool REC>
 static void staged_go(int n, int smem, cudaStream_t st, const Tables &t, const FrameStore &fs, const Intr &in,
-                      const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *err) {
+                      const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *err, int *rec) {
   static PerDevice attr;  // one per instantiation, set once per device
   attr.get(0, [] {
-    cudaFuncSetAttribute(k_dense_staged<MODE, KIND, Part>, cudaFuncAttributeMaxDynamicSharedMemorySize, STG_MAX_SMEM);
+    cudaFuncSetAttribute(k_dense_staged<MODE, KIND, Part, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         STG_MAX_SMEM);
     return 1LL;
   });
-  k_dense_staged<MODE, KIND, Part><<<n, STG_BS, smem, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, err);
+  k_dense_staged<MODE, KIND, Part, REC><<<n, STG_BS, smem, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, err, rec);
 }
 
-template <int MODE, typename Part>
+template <int MODE, typename Part, bool REC>
 static void staged_kind(int kind, int n, int smem, cudaStream_t st, const Tables &t, const FrameStore &fs,
-                        const Intr &in, const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *err) {
+                        const Intr &in, const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *err,
+                        int *rec) {
   if (kind == BF_STORE_BF16)
-    staged_go<MODE, BF_STORE_BF16, Part>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
+    staged_go<MODE, BF_STORE_BF16, Part, REC>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err, rec);
   else if (kind == BF_STORE_FP16)
-    staged_go<MODE, BF_STORE_FP16, Part>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
+    staged_go<MODE, BF_STORE_FP16, Part, REC>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err, rec);
   else
-    staged_go<MODE, BF_STORE_FP32, Part>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
+    staged_go<MODE, BF_STORE_FP32, Part, REC>(n, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err, rec);
 }
 
+// rec: nullptr, or (debug) the buffer that records the association of every source pixel of every
+// directed pair (H * W ints per directed pair).
 template <typename Part>
 int launch_dense_staged(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
-                        float w_geo, float w_photo, Part *part, int *err, cudaStream_t st) {
+                        float w_geo, float w_photo, Part *part, int *err, int *rec, cudaStream_t st) {
   if (t.n_wi == 0) return 0;
   const int smem = dense_staged_smem(in.W, in.H, fs.storage);
-  if (mode == MODE_ACCUM)
-    staged_kind<MODE_ACCUM, Part>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
-  else
-    staged_kind<MODE_ENERGY, Part>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part, err);
+  if (mode == MODE_ACCUM) {
+    if (rec)
+      staged_kind<MODE_ACCUM, Part, true>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part,
+                                          err, rec);
+    else
+      staged_kind<MODE_ACCUM, Part, false>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part,
+                                           err, nullptr);
+  } else {
+    if (rec)
+      staged_kind<MODE_ENERGY, Part, true>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part,
+                                           err, rec);
+    else
+      staged_kind<MODE_ENERGY, Part, false>(fs.storage, t.n_wi, smem, st, t, fs, in, pairM, g, w_geo, w_photo, part,
+                                            err, nullptr);
+  }
   return 1;
 }
 template int launch_dense_staged<float>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates,
-                                        float, float, float *, int *, cudaStream_t);
+                                        float, float, float *, int *, int *, cudaStream_t);
 template int launch_dense_staged<double>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates,
-                                         float, float, double *, int *, cudaStream_t);
+                                         float, float, double *, int *, int *, cudaStream_t);
 
 template int launch_dense<float>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
                                   float, float *, int *, cudaStream_t);

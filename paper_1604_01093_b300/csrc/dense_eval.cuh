@@ -138,7 +138,11 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
   const float Y1 = FMA(X.R12, dz, FMA(X.R11, dy, FMA(X.R10, dx, X.t1)));
   const float Y2 = FMA(X.R22, dz, FMA(X.R21, dy, FMA(X.R20, dx, X.t2)));
   if (!(Y2 > 0.f)) return -1;
-  const float iz = __frcp_rn(Y2);
+  // the hardware reciprocal (rcp.approx: one MUFU instruction, about 1 ulp): the correctly rounded
+  // __frcp_rn added a refinement and a slow-path test to every pixel.  Its ulp moves u by ~1e-5 px,
+  // inside the FP32 tie windows of the decisions
+  float iz;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iz) : "f"(Y2));
   const float ux = FMA(in.fx, FM(Y0, iz), in.cx);
   const float uy = FMA(in.fy, FM(Y1, iz), in.cy);
   // nearest pixel floor(u + 0.5) on the 3-pixel interior, 3 <= n <= W - 4 (inside the image without a
@@ -219,7 +223,9 @@ constexpr int DENSE_BS = 256;
 // One dense tile (work item = consecutive source pixels of one directed pair), evaluated by a
 // CTA of DENSE_BS threads.  ktab: shared memory for kx[W] then ky[H]; red: the reduction's shared
 // memory.  Ends with the CTA's partial record written by threads < NPD.
-template <int MODE, int KIND, typename Part, bool CG = false>
+// REC (debug): also write every source pixel's associated target pixel (or -1) to
+// assoc[d * H * W + px], d the tile's directed pair; MODE_ASSOC always does.
+template <int MODE, int KIND, typename Part, bool CG = false, bool REC = false>
 __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const FrameStore &fs, const Intr &in,
                                            const float *__restrict__ pairM, const Gates &g, float w_geo,
                                            float w_photo, Part *__restrict__ part, int *__restrict__ assoc,
@@ -251,7 +257,7 @@ __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const Fram
       const int px = w.px;
       auto srcI = [&]() { return Bs[px].x; };
       const int tgt = eval_pixel<MODE>(a, w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo, w_photo, acc);
-      if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
+      if (MODE == MODE_ASSOC || REC) assoc[(long long)d * HW + w.px] = tgt;
     }
   } else {
     const uint4 *__restrict__ Ps = fs.P16 + (long long)ss * HW;
@@ -266,7 +272,7 @@ __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const Fram
       auto srcI = [&]() { return unpack16_i<KIND>(r).x; };
       const int tgt = eval_pixel<MODE>(unpack16_dn<KIND>(r), w.x, w.y, X, in, kx, ky, g, loadA, loadB, srcI, w_geo,
                                        w_photo, acc);
-      if (MODE == MODE_ASSOC) assoc[w.px] = tgt;
+      if (MODE == MODE_ASSOC || REC) assoc[(long long)d * HW + w.px] = tgt;
     }
   }
   if (MODE != MODE_ASSOC) {

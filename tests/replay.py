@@ -27,3 +27,47 @@ def from_ctx(ctx, frame_ids, W, H, storage=None, **params):
 
     eps = (association.EPS_PX, association.EPS_D, EPS_N_STORAGE[storage])
     return association.CheckedReplay(fetch, W, H, eps)
+
+
+class Recorded(association.CheckedReplay):
+    """The decisions the library took in its last recorded solve on ``ctx`` (bf_debug_record_association),
+    per dense evaluation: the oracle checks each against its own FP64 association at the poses the
+    library evaluated at, then replays it in its own Gauss-Newton loop (at its own poses), so that
+    every iteration of both solves sums the same pixels."""
+
+    def __init__(self, ctx, frame_ids, W, H, storage=None):
+        super().__init__(self._fetch, W, H, (association.EPS_PX, association.EPS_D, EPS_N_STORAGE[storage]))
+        self.ctx, self.ids = ctx, [int(f) for f in frame_ids]
+        self._key, self._val = None, None
+
+    def _get(self, i, j):
+        key = (self.iteration, i, j)
+        if key != self._key:
+            self._key, self._val = key, self.ctx.recorded_association(self.iteration, self.ids[i], self.ids[j])
+        return self._val
+
+    def _fetch(self, i, j, poses):
+        return self._get(i, j)[0]
+
+    def check_poses(self, i, j):
+        _, Pi, Pj = self._get(i, j)
+        return Pi, Pj
+
+
+def recorded_solve(ctx, frame_ids, solve, oracle_frames, intr, init, sparse_pairs, params, storage=None, pmap=None,
+                   frame_keys=None):
+    """Run ``solve()`` (one single-problem solve on ctx) with the association recorded, then the
+    oracle's Gauss-Newton solve from ``init`` on the recorded decisions.  Returns (the library's
+    stats, its poses of frame_ids, the oracle's result with ``.replay`` = the Recorded provider)."""
+    from oracle import solver
+    ctx.record_association(True)
+    try:
+        st = solve()
+        poses = ctx.get_poses(frame_ids)
+        rep = Recorded(ctx, frame_ids, intr["W"], intr["H"], storage)
+        ref = solver.gauss_newton(oracle_frames, intr, init, sparse_pairs, params, assoc=rep, pmap=pmap,
+                                  frame_keys=frame_keys)
+    finally:
+        ctx.record_association(False)
+    ref.replay = rep
+    return st, poses, ref

@@ -36,9 +36,9 @@ def test_bf16_160x120_chunk_matches_oracle(bf):
     for k, (i, j) in enumerate(prob.pairs):
         p, q = prob.pair_corr(k)
         ctx.add_correspondences(int(i), int(j), p, q)
-    rep = replay.from_ctx(ctx, range(n), intr["W"], intr["H"], storage="bf16")
-    ref = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)), prm, assoc=rep)
-    st = ctx.solve_local(0, list(range(n)), n_gn=3, n_pcg=10, w_dense=0.5)
+    ids = list(range(n))
+    st, _, ref = replay.recorded_solve(ctx, ids, lambda: ctx.solve_local(0, ids, n_gn=3, n_pcg=10, w_dense=0.5), fr,
+                                       prob.intr, prob.init, solver.sparse_pairs_for(prob, ids), prm, storage="bf16")
     rel = np.abs(np.array(st["energy"]) - ref.energy) / np.abs(ref.energy)
     assert rel.max() <= 1e-5, rel
     P = ctx.get_poses(list(range(n)))

@@ -114,12 +114,12 @@ def test_matfree_global_matches_oracle(bf, small_global):
     prob = small_global
     n = prob.n_frames
     fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in range(n)]
-    rep = replay.from_ctx(make_ctx(bf, prob), range(n), prob.intr["W"], prob.intr["H"])
-    ref = solver.gauss_newton(fr, prob.intr, prob.init, solver.sparse_pairs_for(prob, range(n)),
-                              SolveParams(n_gn=4, n_pcg=20, w_dense=0.5), assoc=rep)
     ctx = make_ctx(bf, prob)
-    st = ctx.solve_global(list(range(n)), n_gn=4, n_pcg=20, w_dense=0.5, sparse_mode=MATFREE)
-    compare_oracle(st, ctx.get_poses(list(range(n))), ref, "global48 matrix-free")
+    ids = list(range(n))
+    st, P, ref = replay.recorded_solve(
+        ctx, ids, lambda: ctx.solve_global(ids, n_gn=4, n_pcg=20, w_dense=0.5, sparse_mode=MATFREE), fr, prob.intr,
+        prob.init, solver.sparse_pairs_for(prob, ids), SolveParams(n_gn=4, n_pcg=20, w_dense=0.5))
+    compare_oracle(st, P, ref, "global48 matrix-free")
 
 
 def test_matfree_chunk_matches_oracle(bf, cfg1):
@@ -128,11 +128,11 @@ def test_matfree_chunk_matches_oracle(bf, cfg1):
     d = cfg1.solve
     prm = SolveParams(n_gn=d["n_gn"], n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"],
                       w_photo=d["w_photo"], w_geo=d["w_geo"])
-    rep = replay.from_ctx(make_ctx(bf, cfg1), range(n), cfg1.intr["W"], cfg1.intr["H"])
-    ref = solver.gauss_newton(fr, cfg1.intr, cfg1.init, solver.sparse_pairs_for(cfg1, range(n)), prm, assoc=rep)
     ctx = make_ctx(bf, cfg1)
-    st = ctx.solve_local(0, list(range(n)), sparse_mode=MATFREE, **d)
-    compare_oracle(st, ctx.get_poses(list(range(n))), ref, "cfg1 matrix-free")
+    ids = list(range(n))
+    st, P, ref = replay.recorded_solve(ctx, ids, lambda: ctx.solve_local(0, ids, sparse_mode=MATFREE, **d), fr,
+                                       cfg1.intr, cfg1.init, solver.sparse_pairs_for(cfg1, ids), prm)
+    compare_oracle(st, P, ref, "cfg1 matrix-free")
 
 
 def test_matfree_rejects_cluster_kernel_and_unknown_modes(bf, cfg1):

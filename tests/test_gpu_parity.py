@@ -6,8 +6,10 @@ Tolerances (the accuracy targets, and ones derived from the FP32 evaluation):
 * association: the library decides in FP32, the oracle in FP64 (Sec. 4.3 as written); they
   must agree on every pixel except ties (a decision within FP32 rounding of its threshold),
   and the ties that do flip stay below 1e-4 of the valid residuals;
-* everything that compares arithmetic (normal equations, energies, solves) runs the oracle on
-  the library's checked decisions (tests/replay.py), so both sides sum the same pixels;
+* everything that compares arithmetic runs the oracle on the library's checked decisions
+  (tests/replay.py): the normal equations at given poses on the decisions bf_debug_association
+  returns there, the solves on the decisions the library recorded at every Gauss-Newton iteration
+  (bf_debug_record_association), so both sides sum the same pixels at every step;
 * assembled normal equations: FP32 per-pixel evaluation with FP64 merging, so entries
   agree to ~1e-6 of the block's scale; tested at 2e-5 of the largest entry of A (b: of
   the largest entry of b).
@@ -211,50 +213,43 @@ def compare_solve(res_gpu, poses_gpu, res_or, label):
         assert rot <= ROT_TOL and tr <= TRANS_TOL, (label, k, rot, tr)
 
 
-def oracle_solve(bf, prob, frames, ids, prm, precision=0, **ctx_kw):
-    """The oracle's Gauss-Newton solve of frames ids from their initial poses, on the library's
-    checked association decisions (fetched from a fresh context at the oracle's poses)."""
-    ctx = make_ctx(bf, prob, **ctx_kw)
-    rep = replay.from_ctx(ctx, ids, prob.intr["W"], prob.intr["H"])
-    res = solver.gauss_newton(frames, prob.intr, prob.init[list(ids)], solver.sparse_pairs_for(prob, ids), prm,
-                              assoc=rep)
-    res.replay = rep
-    ctx.close()
-    return res
+def recorded(bf, prob, ids, solve_kw, prm, local=True, ctx=None, frames=None, chunk_id=0, **ctx_kw):
+    """The library's solve of frames ids (recorded) and the oracle's solve on its decisions."""
+    ctx = ctx or make_ctx(bf, prob, **ctx_kw)
+    ids = [int(f) for f in ids]
+    if frames is None:
+        frames = [ofr.Frame(prob.depth[f], prob.lum[f], prob.intr) for f in ids]
+    if local:
+        solve = lambda: ctx.solve_local(chunk_id, ids, **solve_kw)  # noqa: E731
+    else:
+        solve = lambda: ctx.solve_global(ids, **solve_kw)  # noqa: E731
+    return replay.recorded_solve(ctx, ids, solve, frames, prob.intr, prob.init[ids],
+                                 solver.sparse_pairs_for(prob, ids), prm)
 
 
-@pytest.fixture(scope="module")
-def cfg1_oracle(bf, cfg1, cfg1_frames):
-    return oracle_solve(bf, cfg1, cfg1_frames, list(range(11)), oracle_params(cfg1.solve))
+def test_local_solve_matches_oracle(bf, cfg1, cfg1_frames):
+    st, poses, ref = recorded(bf, cfg1, range(11), dict(cfg1.solve), oracle_params(cfg1.solve), frames=cfg1_frames)
+    compare_solve(st, poses, ref, "cfg1 mixed")
+    assert st["r_max_pair"] == tuple(ref.r_max_pair) or abs(st["r_max"] - ref.r_max) < 1e-6
+    assert abs(st["r_max"] - ref.r_max) <= 1e-5 * ref.r_max
+    assert st["n_dense"] == ref.n_dense
+    assert ref.replay.n_flips <= FLIP_BUDGET * ref.replay.n_valid
 
 
-def test_local_solve_matches_oracle(bf, cfg1, cfg1_oracle):
-    ctx = make_ctx(bf, cfg1)
-    st = ctx.solve_local(0, list(range(11)), **{k: v for k, v in cfg1.solve.items()})
-    poses = ctx.get_poses(list(range(11)))
-    compare_solve(st, poses, cfg1_oracle, "cfg1 mixed")
-    assert st["r_max_pair"] == tuple(cfg1_oracle.r_max_pair) or abs(st["r_max"] - cfg1_oracle.r_max) < 1e-6
-    assert abs(st["r_max"] - cfg1_oracle.r_max) <= 1e-5 * cfg1_oracle.r_max
-    assert st["n_dense"] == cfg1_oracle.n_dense
-
-
-def test_local_solve_fp32_path_matches_oracle(bf, cfg1, cfg1_oracle):
+def test_local_solve_fp32_path_matches_oracle(bf, cfg1, cfg1_frames):
     """The plain FP32 path (FP32 merges and PCG scalars): the same accuracy targets as the mixed
     path, so the two are compared at equal accuracy."""
-    ctx = make_ctx(bf, cfg1)
-    st = ctx.solve_local(0, list(range(11)), precision=1, **{k: v for k, v in cfg1.solve.items()})
-    compare_solve(st, ctx.get_poses(list(range(11))), cfg1_oracle, "cfg1 plain FP32")
+    st, poses, ref = recorded(bf, cfg1, range(11), dict(cfg1.solve, precision=1), oracle_params(cfg1.solve),
+                              frames=cfg1_frames)
+    compare_solve(st, poses, ref, "cfg1 plain FP32")
 
 
 @pytest.mark.parametrize("seed,n", [(5, 3), (6, 7)])
 def test_short_chunks_match_oracle(bf, seed, n):
     prob = synth.chunk_problem(seed, n, 80, 60, (50, 120), name=f"chunk{n}")
-    fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in range(n)]
-    prm = SolveParams(n_gn=3, n_pcg=8, w_dense=0.5)
-    ref = oracle_solve(bf, prob, fr, list(range(n)), prm)
-    ctx = make_ctx(bf, prob)
-    st = ctx.solve_local(7, list(range(n)), n_gn=3, n_pcg=8, w_dense=0.5)
-    compare_solve(st, ctx.get_poses(list(range(n))), ref, f"chunk{n}")
+    st, poses, ref = recorded(bf, prob, range(n), dict(n_gn=3, n_pcg=8, w_dense=0.5),
+                              SolveParams(n_gn=3, n_pcg=8, w_dense=0.5))
+    compare_solve(st, poses, ref, f"chunk{n}")
 
 
 def test_batched_equals_alone(bf):
@@ -279,12 +274,9 @@ def small_global():
 def test_global_solve_matches_oracle(bf, small_global):
     prob = small_global
     n = prob.n_frames
-    fr = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr) for k in range(n)]
-    prm = SolveParams(n_gn=4, n_pcg=20, w_dense=0.5)
-    ref = oracle_solve(bf, prob, fr, list(range(n)), prm)
-    ctx = make_ctx(bf, prob)
-    st = ctx.solve_global(list(range(n)), n_gn=4, n_pcg=20, w_dense=0.5)
-    compare_solve(st, ctx.get_poses(list(range(n))), ref, "global48")
+    st, poses, ref = recorded(bf, prob, range(n), dict(n_gn=4, n_pcg=20, w_dense=0.5),
+                              SolveParams(n_gn=4, n_pcg=20, w_dense=0.5), local=False)
+    compare_solve(st, poses, ref, "global48")
     assert st["n_pairs"] == len(prob.pairs)
 
 
@@ -458,19 +450,22 @@ def batch320():
 
 
 def test_batched_chunks_320x240_match_oracle(bf, batch320):
-    """Full-resolution chunks (320x240, tiled dense kernel) solved in one batch; the two smallest
-    chunks are checked against the oracle."""
+    """Full-resolution chunks (320x240, tiled dense kernel) solved in one batch (CUDA graph); the two
+    smallest chunks are solved again alone with the association recorded (bitwise the batch's
+    result) and checked against the oracle's solve on those decisions."""
     prob = batch320
     ctx = make_ctx(bf, prob, max_frames_hint=prob.n_frames)
     lists = [c.tolist() for c in prob.chunks]
-    stats = ctx.solve_local_batch(list(range(len(lists))), lists, n_gn=3, n_pcg=8, use_graph=1)
+    kw = dict(n_gn=3, n_pcg=8)
+    stats = ctx.solve_local_batch(list(range(len(lists))), lists, use_graph=1, **kw)
+    P_batch = [ctx.get_poses(lst) for lst in lists]
     order = sorted(range(len(lists)), key=lambda k: len(lists[k]))[:2]
-    prm = SolveParams(n_gn=3, n_pcg=8)
     for k in order:
-        ids = lists[k]
-        fr = [ofr.Frame(prob.depth[f], prob.lum[f], prob.intr) for f in ids]
-        ref = oracle_solve(bf, prob, fr, ids, prm, max_frames_hint=prob.n_frames)
-        compare_solve(stats[k], ctx.get_poses(ids), ref, f"chunk {k} at 320x240")
+        st, poses, ref = recorded(bf, prob, lists[k], kw, SolveParams(**kw), ctx=ctx, chunk_id=1000 + k)
+        np.testing.assert_array_equal(poses, P_batch[k])
+        assert st["energy"] == stats[k]["energy"]
+        compare_solve(st, poses, ref, f"chunk {k} at 320x240")
+        assert ref.replay.n_flips <= FLIP_BUDGET * ref.replay.n_valid
 
 
 @pytest.mark.parametrize("which", [0, 1, 2])
@@ -510,15 +505,16 @@ def test_workspace_growth_reuploads_tables(bf):
     assert st["energy"] == ref["energy"] and st["flags"] == 0
 
 
-def test_autotuned_decomposition(bf, cfg1, cfg1_oracle):
+def test_autotuned_decomposition(bf, cfg1, cfg1_frames):
     """tile_px = BF_TILE_AUTOTUNE times the candidate decompositions once, keeps the fastest, and
     then gives the same result as asking for that decomposition explicitly; the solve matches the
     oracle like any other."""
     ctx = make_ctx(bf, cfg1)
     assert ctx.tuned_tile_px() is None
-    st = ctx.solve_local(0, list(range(11)), tile_px=bf._lib.BF_TILE_AUTOTUNE, **dict(cfg1.solve))
+    st, poses, ref = recorded(bf, cfg1, range(11), dict(cfg1.solve, tile_px=bf._lib.BF_TILE_AUTOTUNE),
+                              oracle_params(cfg1.solve), ctx=ctx, frames=cfg1_frames)
     chosen = ctx.tuned_tile_px()
     assert chosen == 0 or 256 <= chosen <= 4800
-    compare_solve(st, ctx.get_poses(list(range(11))), cfg1_oracle, "autotuned")
+    compare_solve(st, poses, ref, "autotuned")
     again = make_ctx(bf, cfg1).solve_local(0, list(range(11)), tile_px=chosen, **dict(cfg1.solve))
     assert again["energy"] == st["energy"]

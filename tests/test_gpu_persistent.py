@@ -99,20 +99,26 @@ def test_persistent_repeatable(bf, batch80):
 
 
 def test_persistent_matches_oracle(bf, batch320):
+    """The persistent launch on 320x240 chunks; the two smallest chunks are solved again alone with
+    the association recorded (bitwise the persistent result, same tiles) and checked against the
+    oracle's solve on those decisions."""
     prob = batch320
     ctx = make_ctx(bf, prob)
-    stats, poses = solve_batch(ctx, prob, n_gn=3, n_pcg=8, tile_px=19200, persistent=1, use_graph=1)
+    kw = dict(n_gn=3, n_pcg=8, tile_px=19200)
+    stats, poses = solve_batch(ctx, prob, persistent=1, use_graph=1, **kw)
     lists = [c.tolist() for c in prob.chunks]
     prm = SolveParams(n_gn=3, n_pcg=8)
     for k in sorted(range(len(lists)), key=lambda k: len(lists[k]))[:2]:
         ids = lists[k]
         fr = [ofr.Frame(prob.depth[f], prob.lum[f], prob.intr) for f in ids]
-        rep = replay.from_ctx(ctx, ids, prob.intr["W"], prob.intr["H"])
-        ref = solver.gauss_newton(fr, prob.intr, prob.init[ids], solver.sparse_pairs_for(prob, ids), prm, assoc=rep)
-        rel = np.abs(np.array(stats[k]["energy"]) - ref.energy) / np.abs(ref.energy)
+        st, P, ref = replay.recorded_solve(ctx, ids, lambda: ctx.solve_local(2000 + k, ids, **kw), fr, prob.intr,
+                                           prob.init[ids], solver.sparse_pairs_for(prob, ids), prm)
+        assert st["energy"] == stats[k]["energy"]
+        np.testing.assert_array_equal(P, poses[k])
+        rel = np.abs(np.array(st["energy"]) - ref.energy) / np.abs(ref.energy)
         assert rel.max() <= ENERGY_RTOL, (k, rel)
         for f in range(len(ids)):
-            rot, tr = lie.pose_error(poses[k][f], ref.poses[f])
+            rot, tr = lie.pose_error(P[f], ref.poses[f])
             assert rot <= ROT_TOL and tr <= TRANS_TOL, (k, f, rot, tr)
 
 

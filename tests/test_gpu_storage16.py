@@ -127,12 +127,11 @@ def test_local_solve_bf16_matches_oracle(bf, cfg1, tile_px):
     d = cfg1.solve
     prm = SolveParams(n_gn=d["n_gn"], n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"],
                       w_photo=d["w_photo"], w_geo=d["w_geo"])
-    rctx = make_ctx(bf, cfg1, "bf16")
-    rep = replay.from_ctx(rctx, range(11), cfg1.intr["W"], cfg1.intr["H"], storage="bf16")
-    ref = solver.gauss_newton(fr, cfg1.intr, cfg1.init, solver.sparse_pairs_for(cfg1, range(11)), prm, assoc=rep)
     ctx = make_ctx(bf, cfg1, "bf16")
-    st = ctx.solve_local(0, list(range(11)), tile_px=tile_px, **dict(d))
-    poses = ctx.get_poses(list(range(11)))
+    ids = list(range(11))
+    st, poses, ref = replay.recorded_solve(ctx, ids, lambda: ctx.solve_local(0, ids, tile_px=tile_px, **dict(d)), fr,
+                                           cfg1.intr, cfg1.init, solver.sparse_pairs_for(cfg1, ids), prm,
+                                           storage="bf16")
     rel = np.abs(np.array(st["energy"]) - ref.energy) / np.abs(ref.energy)
     assert rel.max() <= 1e-5, rel
     for k in range(11):

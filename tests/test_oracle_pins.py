@@ -789,6 +789,17 @@ def test_checked_replay_accepts_ties_and_rejects_other_disagreements(room_frames
     S2 = system.assemble(fr, intr, P0, sp, [(0, 1)], prm, 0.5, assoc=fetch)
     np.testing.assert_array_equal(S.A, S2.A)
     assert S.energy == S2.energy and fetch.calls == 2
+    # the same on a process pool: the workers check and replay, the sums stay in pair order
+    with system.frame_pool(fr, 2) as pool:
+        S3 = system.assemble([None] * len(fr), intr, P0, sp, [(0, 1)], prm, 0.5, assoc=fetch,
+                             pmap=lambda f, tasks: pool.map(f, tasks))
+        np.testing.assert_array_equal(S.A, S3.A)
+        np.testing.assert_array_equal(S.b, S3.b)
+        assert S.energy == S3.energy and fetch.calls == 4
+        bad = association.CheckedReplay(lambda i, j, p: np.full(W * H, -1), W, H)
+        with pytest.raises(AssertionError):
+            system.assemble([None] * len(fr), intr, P0, sp, [(0, 1)], prm, 0.5, assoc=bad,
+                            pmap=lambda f, tasks: pool.map(f, tasks))
 
 
 def test_chunk_validation_flags_a_misaligned_frame(room_frames):
@@ -1040,3 +1051,64 @@ def test_global300_golden_is_the_oracles_output():
     np.testing.assert_allclose(res.energy[0], gold["energy"][0], rtol=1e-12)
     np.testing.assert_allclose(np.stack([P[:3, :].ravel() for P in res.poses]), np.array(gold["iterates"]["1"]),
                                rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------- planted mistakes
+class _CrossSwapped:
+    """Stand-in for numpy inside residuals.py whose cross product takes its operands the wrong way
+    round (everything else is numpy's)."""
+
+    def __getattr__(self, name):
+        return getattr(np, name)
+
+    @staticmethod
+    def cross(a, b, *args, **kw):
+        return np.cross(b, a, *args, **kw)
+
+
+def test_planted_mistakes_fail_the_pins(monkeypatch, room_frames):
+    """Four plausible mistakes planted in the oracle, one at a time: each makes a pin fail."""
+    # 1. wrong cross-product order in the residual Jacobians
+    with monkeypatch.context() as m:
+        m.setattr(residuals, "np", _CrossSwapped())
+        with pytest.raises(AssertionError):
+            test_dense_geo_jacobian_finite_differences(room_frames)
+    # 2. a dropped Jacobian term: the photometric residual's dependence on frame j's rotation
+    orig_terms = residuals.dense_terms
+
+    def dropped(*a, **kw):
+        d = orig_terms(*a, **kw)
+        d["J_photo_j"][:, :3] = 0.0
+        return d
+
+    with monkeypatch.context() as m:
+        m.setattr(residuals, "dense_terms", dropped)
+        with pytest.raises(AssertionError):
+            test_dense_photo_jacobian_finite_differences(room_frames)
+    # 3. a transposed rotation in the pair transform (R_i^T R_j instead of R_j^T R_i)
+    orig_rel = association.relative_transform
+
+    def transposed(Ri, ti, Rj, tj):
+        R, t = orig_rel(Ri, ti, Rj, tj)
+        return R.T, t
+
+    with monkeypatch.context() as m:
+        m.setattr(association, "relative_transform", transposed)
+        with pytest.raises(AssertionError):
+            test_plane_geo_residual_zero_for_any_pair()
+    # 4. a corrupted gradient magnitude (|gx| + |gy| instead of the Euclidean norm)
+    orig_grad = frames.intensity_gradient
+
+    def l1(L):
+        I, Ix, Iy = orig_grad(L)
+        L = np.asarray(L, dtype=np.float64)
+        gx = 0.5 * (L[1:-1, 2:] - L[1:-1, :-2])
+        gy = 0.5 * (L[2:, 1:-1] - L[:-2, 1:-1])
+        I = I.copy()
+        I[1:-1, 1:-1] = np.abs(gx) + np.abs(gy)
+        return I, Ix, Iy
+
+    with monkeypatch.context() as m:
+        m.setattr(frames, "intensity_gradient", l1)
+        with pytest.raises(AssertionError):
+            test_intensity_gradient_closed_forms()
