@@ -63,8 +63,11 @@ DENSE_FLOPS_PER_PX = 122.8
 # (cold cache); set to None whenever the dense kernel changes until it is captured again.
 # 300-keyframe 80x60 workload, k_dense_staged:
 DENSE_TRAFFIC_BYTES = None
-# 256-chunk 320x240 batch, k_dense (tiled, autotuned decomposition):
-DENSE_TRAFFIC_BYTES_CHUNKS = None
+# 256-chunk 320x240 batch, k_dense (tiled, autotuned decomposition): one launch of the 32-chunk batch
+# (the same chunk distribution, 1496 directed pairs = 114.9 M directed source pixels) read 514.6 MB and
+# wrote 3.3 MB (ncu, one launch, the current kernel); scaled by directed source pixels to the
+# 256-chunk launch (1007.5 M): DRAM traffic is the frames' unique bytes, which grow with the batch
+DENSE_TRAFFIC_BYTES_CHUNKS = (514.63e6 + 3.33e6) * 1007.5 / 114.9
 # untimed warm-up floor after the W warm-up steps (seconds of repeated steps)
 WARMUP_MIN_S = 0.5
 # B300 FP32 peak: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock
@@ -106,6 +109,8 @@ def parse():
                     help="run only the 300-keyframe 80x60 global solve leg (one JSON line)")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving leg (one JSON line)")
     ap.add_argument("--serving-seconds", type=float, default=8.0, help="length of the served session")
+    ap.add_argument("--persistent", action="store_true",
+                    help="time the batch as one persistent launch (half-frame tiles) instead of the launch sequence")
     ap.add_argument("--chunks", type=int, default=256,
                     help="chunks in the timed batch (a smaller batch for profiling captures; the line then names it)")
     ap.add_argument("--large-only", action="store_true",
@@ -411,8 +416,10 @@ def run_ours(args, rank, world, local_rank):
     all_ids = list(range(prob.n_frames))
     precision = bf.BF_PREC_FP32 if args.precision == "fp32" else bf.BF_PREC_MIXED
     common = {k: prm[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
+    if args.persistent and args.tile_px == -1:
+        args.tile_px = PERSISTENT_TILE_PX
     params = bf.default_params(precision=precision, use_graph=0 if args.no_graph else 1, tile_px=args.tile_px,
-                               pcg_variant=args.pcg_variant, **common)
+                               pcg_variant=args.pcg_variant, persistent=1 if args.persistent else 0, **common)
     storage = STORAGE_CODES[args.storage](bf)
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
                      stream=stream.cuda_stream, max_frames_hint=prob.n_frames, storage=storage)
@@ -499,7 +506,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = alg_bytes / (dense_ms / 1000.0) / 1e9
     flops = DENSE_FLOPS_PER_PX * units
     achieved_tf = flops / (dense_ms / 1000.0) / 1e12
-    traffic = DENSE_TRAFFIC_BYTES_CHUNKS if (args.storage == "fp32" and args.tile_px == bf.BF_TILE_AUTOTUNE) else None
+    traffic = DENSE_TRAFFIC_BYTES_CHUNKS if (args.storage == "fp32" and args.tile_px == bf.BF_TILE_AUTOTUNE and
+                                             args.chunks == 256) else None
     tot = sum(v["ms"] for v in prof["kernels"].values())
     kernel_share = {k: round(v["ms"] / max(tot, 1e-9), 4) for k, v in prof["kernels"].items() if v["count"]}
     lat_ms = [t for t in times]  # every chunk of a step completes with its batch: its latency is the step
@@ -542,6 +550,8 @@ def run_ours(args, rank, world, local_rank):
                                              gn_per_step, stream)
         line["persistent"] = chunk_persistent_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn_per_step,
                                                   stats, stream)
+        line["compensated_sums"] = chunk_compensated_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common,
+                                                         gn_per_step, stats, stream, tuned)
         ctx.close()
         line["bf16_storage"] = chunk_batch_leg(bf, torch, dev, stream, prob=prob, storage="bf16")
         line["global300"] = global300_leg(bf, torch, dev, stream, args)
@@ -637,6 +647,36 @@ def chunk_persistent_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn
                 abs(a["energy"][-1] - b["energy"][-1]) / abs(b["energy"][-1]) for a, b in zip(sk, ref_stats))}
 
 
+def chunk_compensated_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn_per_step, ref_stats, stream, tile,
+                          steps=3):
+    """The same batch with compensated (Kahan) per-thread sums in the dense kernel (same tiles)."""
+    pc = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, tile_px=tile, compensated=1, **common)
+
+    def run(p):
+        ctx.add_frames(0, depth_d, lum_d)
+        return ctx.solve_local_batch(cids, lists, p)
+
+    run(pc)
+    ts = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sc = run(pc)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ctx.reset_profile()
+    ctx.set_profiling(True)
+    run(bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, tile_px=tile, compensated=1, **common))
+    dense = ctx.profile()["kernels"]["dense"]
+    ctx.set_profiling(False)
+    return {"value": gn_per_step / (statistics.mean(ts) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(ts),
+            "tile_px": tile, "dense_avg_launch_ms": dense["ms"] / max(dense["count"], 1),
+            "final_energy_max_rel_diff_vs_plain_sums": max(
+                abs(a["energy"][-1] - b["energy"][-1]) / abs(b["energy"][-1]) for a, b in zip(sc, ref_stats))}
+
+
 def global300_leg(bf, torch, dev, stream, args, steps=10, warmup=3):
     """The 300-keyframe 80x60 global solve (8 GN x 20 PCG, mixed precision, CUDA graph; its frames
     fit in L2): GN iterations/s, end to end from host buffers, the plain FP32 path, BF16 storage,
@@ -689,7 +729,10 @@ def global300_leg(bf, torch, dev, stream, args, steps=10, warmup=3):
     while time.perf_counter() - t_w < WARMUP_MIN_S:
         step()
     torch.cuda.synchronize(dev)
+    clocks = Clocks(dev.index if dev.index is not None else 0)
+    clocks.start()
     times, st, _ = timed(step, steps)
+    clk = clocks.stop()
     _, _, prof = timed(lambda: step(prof_params), 3, profile=True)
     n_gn = prm["n_gn"]
     n_dp = 2 * st["n_dense_pairs"]
@@ -701,7 +744,7 @@ def global300_leg(bf, torch, dev, stream, args, steps=10, warmup=3):
            "pairs": int(len(prob.pairs)), "dense_pairs": st["n_dense_pairs"], "correspondences": prob.n_corr,
            "n_gn": n_gn, "n_pcg": prm["n_pcg"], "precision": "mixed", "cuda_graph": True,
            "value": n_gn / (statistics.mean(times) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(times),
-           "l2": "256 MB buffer written between timed steps (inputs < L2)",
+           "l2": "256 MB buffer written between timed steps (inputs < L2)", "clocks": clk,
            "initial_energy": st["energy"][0], "final_energy": st["energy"][-1],
            "dense_kernel": {"kernel": "k_dense_staged", "avg_launch_ms": dense_ms, "directed_px_per_launch": units,
                             "fp32_TFLOPs": DENSE_FLOPS_PER_PX * units / (dense_ms / 1000.0) / 1e12,

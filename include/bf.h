@@ -137,6 +137,11 @@ typedef struct {
    * sparse blocks; otherwise the launch sequence runs.  A wait inside it that runs out ends
    * the solve with BF_ERR_TIMEOUT. */
   int persistent;
+  /* 1: the dense term's per-thread FP32 sums are compensated (Kahan): each run of additions errs by
+   * O(ulp) instead of O(n ulp), at about twice the dense kernel's instructions; always the tiled
+   * dense kernel; not with persistent.  0 (default): plain FP32 runs of at most tile_px / 256
+   * pixels per thread. */
+  int compensated;
 } bf_solve_params;
 
 enum { BF_SPARSE_BLOCKS = 0, BF_SPARSE_MATFREE = 1 };

@@ -49,7 +49,7 @@ class SolveParams(ctypes.Structure):
                 ("dense_on", ctypes.c_int), ("warm_start", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int), ("pcg_variant", ctypes.c_int),
                 ("prune_rmax", ctypes.c_double), ("prune_rounds", ctypes.c_int),
-                ("sparse_mode", ctypes.c_int), ("persistent", ctypes.c_int)]
+                ("sparse_mode", ctypes.c_int), ("persistent", ctypes.c_int), ("compensated", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):

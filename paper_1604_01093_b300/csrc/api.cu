@@ -887,7 +887,7 @@ static inline bool axes_within(const Pose12 &Pa, const Pose12 &Pb, double cos_ma
 // 4800-pixel tiles
 static void dense_decomposition(const bf_ctx *c, const bf_solve_params &prm, bool &staged, int &tile_px) {
   const int HW = c->cfg.width * c->cfg.height;
-  staged = prm.tile_px == 0 && dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage);
+  staged = prm.tile_px == 0 && !prm.compensated && dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage);
   tile_px = prm.tile_px > 0 ? prm.tile_px : (staged ? HW : std::min(HW, 4800));
 }
 
@@ -1473,7 +1473,7 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
       return launch_dense_staged<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
                                       (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, rec, c->ex->st);
     return launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
-                             (float)(wd * prm.w_photo), (Acc *)D.dpart, rec, c->ex->st);
+                             (float)(wd * prm.w_photo), (Acc *)D.dpart, rec, c->ex->st, prm.compensated != 0);
   });
   run_k(c, BF_K_SPARSE, [&] {
     return launch_sparse<Acc>(mode, t, c->cP, c->cQ, D.pairM, (float)prm.w_sparse, (Acc *)D.spart, D.srmax,
@@ -1686,6 +1686,9 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
   if (!(p->prune_rmax >= 0) || !std::isfinite(p->prune_rmax) || p->prune_rounds < 0 || p->prune_rounds > 100000)
     return fail(c, BF_ERR_INVALID_ARG, "prune_rmax must be finite and >= 0, prune_rounds >= 0");
   if (p->persistent != 0 && p->persistent != 1) return fail(c, BF_ERR_INVALID_ARG, "persistent must be 0 or 1");
+  if (p->compensated != 0 && p->compensated != 1) return fail(c, BF_ERR_INVALID_ARG, "compensated must be 0 or 1");
+  if (p->compensated && p->persistent)
+    return fail(c, BF_ERR_INVALID_ARG, "compensated sums are not available in the persistent launch");
   if (p->sparse_mode != BF_SPARSE_BLOCKS && p->sparse_mode != BF_SPARSE_MATFREE)
     return fail(c, BF_ERR_INVALID_ARG, "unknown sparse_mode");
   if (p->sparse_mode == BF_SPARSE_MATFREE && p->pcg_variant == BF_PCG_CLUSTER)

@@ -26,54 +26,63 @@ namespace bf {
 // Residency: with FP32 frames the accumulating pixel loop needs about 80 registers, so 3 CTAs
 // per SM (24 warps, no spills; 4 CTAs at 64 registers spill and run about 9 % slower); the 16-bit
 // unpacking path runs faster at 4 CTAs per SM.
-template <int MODE, int KIND>
+template <int MODE, int KIND, bool COMP = false>
 struct DenseOcc {
-  static constexpr int value = (KIND == BF_STORE_FP32 && MODE == MODE_ACCUM) ? 3 : 4;
+  // compensated sums hold twice the accumulators: 2 CTAs per SM (up to 128 registers, no spills)
+  static constexpr int value = COMP ? 2 : (KIND == BF_STORE_FP32 && MODE == MODE_ACCUM) ? 3 : 4;
 };
 
 // REC (debug): the association of every source pixel is also written to assoc[d * H * W + px].
-template <int MODE, int KIND, typename Part, bool REC>
-__global__ void __launch_bounds__(DENSE_BS, DenseOcc<MODE, KIND>::value)
+// COMP: compensated per-thread sums (bf_solve_params.compensated).
+template <int MODE, int KIND, typename Part, bool REC, bool COMP>
+__global__ void __launch_bounds__(DENSE_BS, DenseOcc<MODE, KIND, COMP>::value)
     k_dense(Tables t, FrameStore fs, Intr in, const float *__restrict__ pairM, Gates g, float w_geo, float w_photo,
             Part *__restrict__ part, int *__restrict__ assoc) {
   extern __shared__ float ktab[];  // kx[W], ky[H]
   __shared__ float red[DENSE_BS / 32][NPD];
-  dense_tile<MODE, KIND, Part, false, REC>(blockIdx.x, t, fs, in, pairM, g, w_geo, w_photo, part, assoc, ktab, red);
+  dense_tile<MODE, KIND, Part, false, REC, COMP>(blockIdx.x, t, fs, in, pairM, g, w_geo, w_photo, part, assoc, ktab,
+                                                 red);
 }
 
-template <int MODE, typename Part, bool REC>
+template <int MODE, typename Part, bool REC, bool COMP>
 static void dense_go(int kind, int n, size_t ks, cudaStream_t st, const Tables &t, const FrameStore &fs,
                      const Intr &in, const float *pairM, Gates g, float w_geo, float w_photo, Part *part, int *assoc) {
   if (kind == BF_STORE_BF16)
-    k_dense<MODE, BF_STORE_BF16, Part, REC><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    k_dense<MODE, BF_STORE_BF16, Part, REC, COMP>
+        <<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else if (kind == BF_STORE_FP16)
-    k_dense<MODE, BF_STORE_FP16, Part, REC><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    k_dense<MODE, BF_STORE_FP16, Part, REC, COMP>
+        <<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   else
-    k_dense<MODE, BF_STORE_FP32, Part, REC><<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    k_dense<MODE, BF_STORE_FP32, Part, REC, COMP>
+        <<<n, DENSE_BS, ks, st>>>(t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
 }
 
 // assoc: MODE_ASSOC's output; in the other modes nullptr, or (debug) the buffer that records the
 // association of every source pixel of every directed pair (H * W ints per directed pair).
+// comp: compensated per-thread sums (not combined with recording).
 template <typename Part>
 int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
-                  float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st) {
+                  float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st, bool comp) {
   if (t.n_tiles == 0) return 0;
   const size_t ks = (size_t)(in.W + in.H) * sizeof(float);
+  const int n = t.n_tiles, sg = fs.storage;
   if (mode == MODE_ACCUM) {
     if (assoc)
-      dense_go<MODE_ACCUM, Part, true>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+      dense_go<MODE_ACCUM, Part, true, false>(sg, n, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    else if (comp)
+      dense_go<MODE_ACCUM, Part, false, true>(sg, n, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, nullptr);
     else
-      dense_go<MODE_ACCUM, Part, false>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part,
-                                        nullptr);
+      dense_go<MODE_ACCUM, Part, false, false>(sg, n, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, nullptr);
   } else if (mode == MODE_ENERGY) {
     if (assoc)
-      dense_go<MODE_ENERGY, Part, true>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part,
-                                        assoc);
+      dense_go<MODE_ENERGY, Part, true, false>(sg, n, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    else if (comp)
+      dense_go<MODE_ENERGY, Part, false, true>(sg, n, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, nullptr);
     else
-      dense_go<MODE_ENERGY, Part, false>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part,
-                                         nullptr);
+      dense_go<MODE_ENERGY, Part, false, false>(sg, n, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, nullptr);
   } else {
-    dense_go<MODE_ASSOC, Part, false>(fs.storage, t.n_tiles, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
+    dense_go<MODE_ASSOC, Part, false, false>(sg, n, ks, st, t, fs, in, pairM, g, w_geo, w_photo, part, assoc);
   }
   return 1;
 }
@@ -270,8 +279,8 @@ template int launch_dense_staged<double>(int, const Tables &, const FrameStore &
                                          float, float, double *, int *, int *, cudaStream_t);
 
 template int launch_dense<float>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
-                                  float, float *, int *, cudaStream_t);
+                                  float, float *, int *, cudaStream_t, bool);
 template int launch_dense<double>(int, const Tables &, const FrameStore &, const Intr &, const float *, Gates, float,
-                                   float, double *, int *, cudaStream_t);
+                                   float, double *, int *, cudaStream_t, bool);
 
 }  // namespace bf

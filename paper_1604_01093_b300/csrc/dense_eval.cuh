@@ -2,6 +2,8 @@
 // persistent batched solve of solve.cu (per-pixel association, residuals, Jacobians and the
 // per-tile reduction; the design notes are at the top of dense.cu).
 #pragma once
+#include <type_traits>
+
 #include "bf_internal.cuh"
 
 namespace bf {
@@ -57,6 +59,12 @@ struct DAcc {
     a[D_E1] = e1;
     a[D_CNT] = cnt;
   }
+  __device__ __forceinline__ void add_energy(float r_g, float r_p) {
+    e0 = __fmaf_rn(r_g, r_g, e0);
+    e1 = __fmaf_rn(r_p, r_p, e1);
+    cnt += 1.f;
+  }
+  __device__ __forceinline__ void add_row(float w, float r, V3 v, V3 c);
 };
 
 // Accumulate one dense residual row (weight w, residual r, Jacobian [v x t - c, v, c, -v]).
@@ -82,6 +90,59 @@ __device__ __forceinline__ void accum_vc(DAcc &A, float w, float r, V3 v, V3 c) 
   A.g[1] = __ffma2_rn(R2, WU23, A.g[1]);
   A.g[2] = __ffma2_rn(R2, WU45, A.g[2]);
 }
+__device__ __forceinline__ void DAcc::add_row(float w, float r, V3 v, V3 c) { accum_vc(*this, w, r, v, c); }
+
+// The same sums with compensated (Kahan) FP32 addition: every sum carries the rounding error of
+// its additions in a second register and subtracts it from the next term, so a run of n additions
+// errs by O(ulp) instead of O(n ulp).  Each term (w u_i u_j, r w u_i, r^2, 1) is formed by one
+// rounded multiplication and added with four rounded additions; about 2.3x the instructions and
+// twice the registers of DAcc (an accuracy option, bf_solve_params.compensated).
+struct DAccK {
+  float s[NPD], c[NPD];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < NPD; ++k) s[k] = c[k] = 0.f;
+  }
+  __device__ __forceinline__ void add(int k, float t) {
+    const float y = __fsub_rn(t, c[k]);
+    const float n = __fadd_rn(s[k], y);
+    c[k] = __fsub_rn(__fsub_rn(n, s[k]), y);
+    s[k] = n;
+  }
+  __device__ __forceinline__ void to_array(float (&a)[NPD]) const {
+#pragma unroll
+    for (int k = 0; k < NPD; ++k) a[k] = s[k];
+  }
+  __device__ __forceinline__ void add_energy(float r_g, float r_p) {
+    add(D_E0, __fmul_rn(r_g, r_g));
+    add(D_E1, __fmul_rn(r_p, r_p));
+    add(D_CNT, 1.f);
+  }
+  // u = (v, c): VV, VC, CC and the gradients in the NPD layout of DAcc::to_array
+  __device__ __forceinline__ void add_row(float w, float r, V3 v, V3 cc) {
+    const float u[6] = {v.x, v.y, v.z, cc.x, cc.y, cc.z};
+    float wu[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) wu[i] = __fmul_rn(w, u[i]);
+    int vv = D_VV, vc = D_VC, ccx = D_CC;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) add(vv++, __fmul_rn(wu[i], u[j]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 3; j < 6; ++j) add(vc++, __fmul_rn(wu[i], u[j]));
+#pragma unroll
+    for (int i = 3; i < 6; ++i)
+#pragma unroll
+      for (int j = i; j < 6; ++j) add(ccx++, __fmul_rn(wu[i], u[j]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) add(D_GV + i, __fmul_rn(r, wu[i]));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) add(D_GC + i, __fmul_rn(r, wu[3 + i]));
+  }
+};
 
 // Fixed-order CTA reduction of N values; thread k < N writes out[k].
 // Fixed-order CTA reduction of N <= 32 values; thread k < N writes out[k].  red: shared memory
@@ -124,10 +185,10 @@ __device__ __forceinline__ PairXf load_xf(const float *M) {
 // residual rows' contributions to acc.  a = source (D, n); loadA / loadB read the target's
 // (D, n) and (I, Ix, Iy); srcI() gives the source pixel's I.  Returns the associated target
 // pixel or -1.
-template <int MODE, typename LA, typename LB, typename LI>
+template <int MODE, typename LA, typename LB, typename LI, typename AccT>
 __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const PairXf &X, const Intr &in,
                                           const float *kx, const float *ky, const Gates &g, LA loadA, LB loadB,
-                                          LI srcI, float w_geo, float w_photo, DAcc &acc) {
+                                          LI srcI, float w_geo, float w_photo, AccT &acc) {
   if (!(a.x > 0.f && normal_valid(a))) return -1;
   const int W = in.W, H = in.H;
   const float z = a.x;
@@ -183,17 +244,15 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
   const float gxI = w00 * c00.y + w01 * c01.y + w10 * c10.y + w11 * c11.y;
   const float gyI = w00 * c00.z + w01 * c01.z + w10 * c10.z + w11 * c11.z;
   const float r_p = srcI() - Ij;
-  acc.e0 = __fmaf_rn(r_g, r_g, acc.e0);
-  acc.e1 = __fmaf_rn(r_p, r_p, acc.e1);
-  acc.cnt += 1.f;
+  acc.add_energy(r_g, r_p);
   if (MODE == MODE_ACCUM) {
     // geometric: v = m, c = m x q
     const V3 m{m0, m1, m2}, q{qx, qy, qz};
-    accum_vc(acc, w_geo, r_g, m, cross3(m, q));
+    acc.add_row(w_geo, r_g, m, cross3(m, q));
     // photometric: v = g = d r_p / d y = -grad I^T Jpi(y), c = g x y
     const float gfx = gxI * in.fx * iz, gfy = gyI * in.fy * iz;
     const V3 gv{-gfx, -gfy, (gfx * Y0 + gfy * Y1) * iz};
-    accum_vc(acc, w_photo, r_p, gv, cross3(gv, V3{Y0, Y1, Y2}));
+    acc.add_row(w_photo, r_p, gv, cross3(gv, V3{Y0, Y1, Y2}));
   }
   return tpx;
 }
@@ -224,8 +283,9 @@ constexpr int DENSE_BS = 256;
 // CTA of DENSE_BS threads.  ktab: shared memory for kx[W] then ky[H]; red: the reduction's shared
 // memory.  Ends with the CTA's partial record written by threads < NPD.
 // REC (debug): also write every source pixel's associated target pixel (or -1) to
-// assoc[d * H * W + px], d the tile's directed pair; MODE_ASSOC always does.
-template <int MODE, int KIND, typename Part, bool CG = false, bool REC = false>
+// assoc[d * H * W + px], d the tile's directed pair; MODE_ASSOC always does.  COMP: compensated
+// per-thread sums (DAccK) instead of DAcc.
+template <int MODE, int KIND, typename Part, bool CG = false, bool REC = false, bool COMP = false>
 __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const FrameStore &fs, const Intr &in,
                                            const float *__restrict__ pairM, const Gates &g, float w_geo,
                                            float w_photo, Part *__restrict__ part, int *__restrict__ assoc,
@@ -240,7 +300,7 @@ __device__ __forceinline__ void dense_tile(int tile, const Tables &t, const Fram
   float *kx = ktab, *ky = ktab + W;
   for (int k = threadIdx.x; k < W + H; k += DENSE_BS) ktab[k] = k < W ? fs.kx[k] : fs.ky[k - W];
   __syncthreads();
-  DAcc acc;
+  typename std::conditional<COMP, DAccK, DAcc>::type acc;
   acc.zero();
   if (KIND == BF_STORE_FP32) {
     const float4 *__restrict__ As = fs.A + (long long)ss * HW;

@@ -88,3 +88,45 @@ def test_batch_chunk_320x240(bf):
                                  ("fp32_arith_bf16_storage", bf.BF_STORE_BF16, {"precision": bf.BF_PREC_FP32})])
     check(table, ["fp32_arith_fp32_storage"])
     assert np.isfinite(table["fp32_arith_bf16_storage"]["translation_m"])
+
+
+def test_compensated_sums_320x240(bf):
+    """Normal equations of a 5-frame 320x240 chunk at perturbed poses (mixed precision: tile sums
+    merged in FP64, so the FP32 per-thread runs are the main rounding source), with tiles of a
+    whole frame (runs of 300 pixels per thread), of half a frame and of 4800 pixels (runs of 19),
+    each with plain and with compensated per-thread sums, against the oracle on the same (checked)
+    decisions.  Printed with -s; every variant within the parity tolerance, and compensation does
+    not make the long runs less accurate."""
+    import replay
+    from oracle import solver, system
+    prob = synth.chunk_batch(57, n_chunks=6, W=320, H=240, length=(5, 5), n_corr=(100, 200), name="batch320")
+    ids = [int(f) for f in prob.chunks[0]]
+    intr = prob.intr
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], max_frames_hint=prob.n_frames)
+    ctx.add_frames(0, prob.depth, prob.lum)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, prob.p_i, prob.p_j)
+    rng = np.random.default_rng(4)
+    poses = prob.gt[ids].copy()
+    for k in range(1, len(ids)):
+        R, t = lie.apply_update(poses[k][:3, :3], poses[k][:3, 3], np.r_[rng.normal(0, 0.005, 3), rng.normal(0, 0.01, 3)])
+        poses[k] = lie.to44(R, t)
+    fr = [ofr.Frame(prob.depth[f], prob.lum[f], intr) for f in ids]
+    prm = SolveParams(w_sparse=0.0, w_dense=1.0, w_photo=0.1, w_geo=1.0)
+    sp = solver.sparse_pairs_for(prob, ids)
+    S = system.assemble(fr, intr, poses, sp, system.dense_pair_set(poses, sp, prm.max_angle_deg), prm, 1.0,
+                        assoc=replay.from_ctx(ctx, ids, intr["W"], intr["H"]))
+    table = {}
+    for tile in (76800, 38400, 4800):
+        for comp in (0, 1):
+            g = ctx.build_system(ids, poses, w_sparse=0.0, w_dense=1.0, w_photo=0.1, w_geo=1.0, tile_px=tile,
+                                 compensated=comp, precision=bf.BF_PREC_MIXED)
+            assert g["n_dense"] == S.n_dense
+            table[f"tile{tile}_{'compensated' if comp else 'plain'}"] = {
+                "A": float(np.abs(g["A"] - S.A).max() / np.abs(S.A).max()),
+                "b": float(np.abs(g["b"] - S.b).max() / np.abs(S.b).max()),
+                "energy": abs(g["energy"] - S.energy) / S.energy}
+    print(json.dumps(table, indent=1))
+    for v in table.values():
+        assert v["A"] <= 2e-5 and v["b"] <= 2e-5 and v["energy"] <= TOL["energy_rel"]
+    long_plain, long_comp = table["tile76800_plain"], table["tile76800_compensated"]
+    assert long_comp["A"] <= 1.5 * long_plain["A"] and long_comp["energy"] <= 1.5 * long_plain["energy"] + 1e-9

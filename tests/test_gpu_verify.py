@@ -79,8 +79,6 @@ def test_verify_pairs_matches_oracle(bf, cfg1, kind):
         ref = verification.verify_pair(fr[i], fr[j], rel, cfg1.intr)
         assert within_bounds(ref, "ij", g["n_ij"], g["err_ij"]), (i, j, g, ref)
         assert within_bounds(ref, "ji", g["n_ji"], g["err_ji"]), (i, j, g, ref)
-        # the ties (decisions within the FP32 rounding windows, ~0.1 % of the pixels) stay few
-        assert ref.tie_ij + ref.tie_ji <= 5e-3 * max(ref.n_ij + ref.n_ji, 1000)
         # validity where no way of deciding the ties could change it
         lo, hi = mean_bounds(ref)
         n_lo = ref.bounds("ij")[0] + ref.bounds("ji")[0]
