@@ -61,8 +61,9 @@ def dense_bytes_per_px(storage):
 DENSE_FLOPS_PER_PX = 122.8
 # DRAM bytes (read + write) of one dense ACCUM launch from an ncu capture of the current kernel
 # (cold cache); set to None whenever the dense kernel changes until it is captured again.
-# 300-keyframe 80x60 workload, k_dense_staged:
-DENSE_TRAFFIC_BYTES = None
+# 300-keyframe 80x60 workload, k_dense_staged: two launches read 46.44 / 46.43 MB and wrote
+# 0.12 / 0.01 MB (ncu, the current kernel): the frames' unique bytes, which stay in L2
+DENSE_TRAFFIC_BYTES = 46.50e6
 # 256-chunk 320x240 batch, k_dense (tiled, autotuned decomposition): one launch of the 32-chunk batch
 # (the same chunk distribution, 1496 directed pairs = 114.9 M directed source pixels) read 514.6 MB and
 # wrote 3.3 MB (ncu, one launch, the current kernel); scaled by directed source pixels to the
@@ -108,7 +109,8 @@ def parse():
     ap.add_argument("--global-only", action="store_true",
                     help="run only the 300-keyframe 80x60 global solve leg (one JSON line)")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving leg (one JSON line)")
-    ap.add_argument("--serving-seconds", type=float, default=8.0, help="length of the served session")
+    ap.add_argument("--serving-seconds", type=float, default=20.0,
+                    help="length of the serving session (the full-length stream is 600 s)")
     ap.add_argument("--persistent", action="store_true",
                     help="time the batch as one persistent launch (half-frame tiles) instead of the launch sequence")
     ap.add_argument("--chunks", type=int, default=256,
@@ -1126,30 +1128,83 @@ def chunk_batch_leg(bf, torch, dev, stream, steps=3, warmup=1, n_chunks=256, pro
 SERVING_HBM_BUDGET = 40 * 1024 ** 3
 
 
-def serving_leg(bf, torch, dev, chunk_prob=None, seconds=8.0, rate=30.0, seed=1604):
-    """Serving: Poisson arrivals of chunk requests (320x240, 3-11 frames, 6 GN x 10 PCG) at `rate`
-    per second for `seconds`, and after every 10th chunk a global request over the first k
-    keyframes of the 300-keyframe 80x60 corridor (k grows from 100 to 300; 8 GN x 20 PCG).
-    served: continuous batching (2 slots, batches of up to 16, chunk solves on high-priority
-    streams, FP32 chunk arithmetic, FP64-merged global solves); plain: the same arrivals served one
-    request at a time by the plain FP32 path (1 slot, batch 1).  Latency = submit -> completion;
-    p50 / p99 per request kind."""
+def _serve_session(cctx, gctx, arrivals, cparams, gparams, lib):
+    """Submit every request at its arrival time to the serving loops; latency = submit ->
+    completion, as the library measures it."""
+    ct, gt = [], []
+    t0 = time.perf_counter()
+    for ta, kind, ids, cid in arrivals:
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0002)
+        if kind == "chunk":
+            ct.append(cctx.submit(ids, chunk_id=cid, params=cparams))
+        else:
+            gt.append(gctx.submit(ids, kind=lib.BF_REQ_GLOBAL, params=gparams))
+    clat = [cctx.wait(t)[1]["ms"] for t in ct]
+    glat = [gctx.wait(t)[1]["ms"] for t in gt]
+    return clat, glat, time.perf_counter() - t0
+
+
+def _plain_session(cctx, gctx, arrivals, cparams, gparams):
+    """The plain path: one host loop takes the requests in arrival order and calls
+    bf_solve_local / bf_solve_global for each (synchronous: results on the host when the call
+    returns); latency = arrival -> return, so a request that arrives while another is being
+    solved waits for it."""
+    clat, glat = [], []
+    t0 = time.perf_counter()
+    for ta, kind, ids, cid in arrivals:
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.0002)
+        if kind == "chunk":
+            cctx.solve_local(cid, ids, params=cparams)
+            clat.append(1000.0 * (time.perf_counter() - t0 - ta))
+        else:
+            gctx.solve_global(ids, params=gparams)
+            glat.append(1000.0 * (time.perf_counter() - t0 - ta))
+    return clat, glat, time.perf_counter() - t0
+
+
+def serving_leg(bf, torch, dev, chunk_prob=None, seconds=20.0, rate=30.0, seed=1604):
+    """The serving stream: Poisson arrivals of chunk requests (320x240, 3-11 frames, 6 GN x 10 PCG)
+    at `rate` per second for `seconds`, and with every 10th chunk a global request over the first k
+    keyframes of a 2000-keyframe 80x60 loop (8 GN x 20 PCG), k growing linearly from 100 to 2000
+    over the session (over 10 minutes at full length; a shorter session compresses the growth).
+    served: the library's serving loops on two persistent contexts (chunks: 2 slots, continuous
+    batching up to 16, high-priority streams, FP32 arithmetic; globals: 1 slot, low-priority
+    stream, FP64-merged mixed precision), admission by a 40 GB HBM budget per context, frames,
+    correspondences and solve workspaces resident.  plain: the same arrivals served one request at
+    a time, in arrival order, by synchronous calls of the plain FP32 path.  Then a chunk-only
+    stream at 600 requests/s, both ways.  p50 / p99 per request kind and over all requests."""
     import synth
     chunk_prob = chunk_prob or synth.cfg3()
-    global_prob = synth.cfg2()
+    t_gen = time.perf_counter()
+    global_prob = synth.cfg4_global()
+    t_gen = time.perf_counter() - t_gen
     rng = np.random.default_rng(seed)
     n_req = int(seconds * rate)
-    gaps = rng.exponential(1.0 / rate, size=n_req)
-    ci, gi = chunk_prob.intr, global_prob.intr
+    t_arr = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     lists = [c.tolist() for c in chunk_prob.chunks]
+    arrivals, ks = [], []
+    for r in range(n_req):
+        arrivals.append((float(t_arr[r]), "chunk", lists[r % len(lists)], r))
+        if r % 10 == 9:
+            k = int(round(100 + 1900 * r / max(1, n_req - 1)))
+            ks.append(k)
+            arrivals.append((float(t_arr[r]), "global", list(range(k)), 0))
+    hi_rate, hi_n = 600.0, 1200
+    h_arr = np.cumsum(rng.exponential(1.0 / hi_rate, size=hi_n))
+    burst = [(float(h_arr[r]), "chunk", lists[r % len(lists)], 300000 + r) for r in range(hi_n)]
+    ci, gi = chunk_prob.intr, global_prob.intr
     pc = {k: chunk_prob.solve[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
     pg = {k: global_prob.solve[k] for k in ("n_gn", "n_pcg", "w_sparse", "w_dense", "w_photo", "w_geo")}
-    out = {"arrival_rate_per_s": rate, "seconds": seconds, "chunk_requests": n_req,
-           "global_requests": n_req // 10, "chunk_workload": chunk_prob.name, "global_workload": global_prob.name,
-           "hbm_budget_bytes_per_context": SERVING_HBM_BUDGET}
-    for name, slots, batch, cprec, gprec in (("served", 2, 16, bf.BF_PREC_FP32, bf.BF_PREC_MIXED),
-                                             ("plain_fp32", 1, 1, bf.BF_PREC_FP32, bf.BF_PREC_FP32)):
-        # admission by a 40 GB HBM budget (each context; batches that would exceed it are split)
+    q = lambda v, f: float(v[min(len(v) - 1, int(f * len(v)))]) if v else None  # noqa: E731
+    out = {"arrival_rate_per_s": rate, "seconds": seconds, "chunk_requests": n_req, "global_requests": len(ks),
+           "global_keyframes": [ks[0], ks[-1]] if ks else None, "chunk_workload": chunk_prob.name,
+           "global_workload": f"{global_prob.name}: {global_prob.n_frames} keyframes, {len(global_prob.pairs)} pairs, "
+                              f"{global_prob.n_corr} correspondences (prefixes of k keyframes)",
+           "global_generation_s": round(t_gen, 1), "hbm_budget_bytes_per_context": SERVING_HBM_BUDGET}
+    for name in ("served", "plain_fp32"):
+        served = name == "served"
         cctx = bf.Context(ci["W"], ci["H"], ci["fx"], ci["fy"], ci["cx"], ci["cy"], max_frames_hint=chunk_prob.n_frames,
                           hbm_budget_bytes=SERVING_HBM_BUDGET)
         cctx.add_frames(0, torch.from_numpy(chunk_prob.depth).to(dev), torch.from_numpy(chunk_prob.lum).to(dev))
@@ -1160,60 +1215,45 @@ def serving_leg(bf, torch, dev, chunk_prob=None, seconds=8.0, rate=30.0, seed=16
         gctx.add_frames(0, global_prob.depth, global_prob.lum, init_pose=global_prob.init)
         gctx.add_correspondences_batch(global_prob.pairs, global_prob.corr_off, global_prob.p_i, global_prob.p_j)
         torch.cuda.synchronize(dev)
-        cctx.serve_start(n_slots=slots, max_batch=batch, max_queue=4096)
-        gctx.serve_start(n_slots=1, max_batch=1, max_queue=4096)
-        cparams = bf.default_params(precision=cprec, **pc)
-        gparams = bf.default_params(precision=gprec, **pg)
-        # warm-up (not timed): every slot allocates its workspace and pinned staging on first use
-        warm = [cctx.submit(lists[k % len(lists)], chunk_id=100000 + k, params=cparams) for k in range(4 * slots)]
-        warm.append(gctx.submit(list(range(100)), kind=bf._lib.BF_REQ_GLOBAL, params=gparams))
-        for t in warm[:-1]:
-            cctx.wait(t)
-        gctx.wait(warm[-1])
-        ct, gt = [], []
-        t0 = time.perf_counter()
-        t_next = t0
-        for r in range(n_req):
-            t_next += gaps[r]
-            while time.perf_counter() < t_next:
-                time.sleep(0.0002)
-            ct.append(cctx.submit(lists[r % len(lists)], chunk_id=r, params=cparams))
-            if r % 10 == 9:
-                k = int(100 + 200 * r / max(1, n_req - 1))
-                gt.append(gctx.submit(list(range(k)), kind=bf._lib.BF_REQ_GLOBAL, params=gparams))
-        clat = [cctx.wait(t)[1]["ms"] for t in ct]
-        glat = [gctx.wait(t)[1]["ms"] for t in gt]
-        wall = time.perf_counter() - t0
-        cctx.serve_stop()
-        gctx.serve_stop()
+        cparams = bf.default_params(precision=bf.BF_PREC_FP32, **pc)
+        gparams = bf.default_params(precision=bf.BF_PREC_MIXED if served else bf.BF_PREC_FP32, **pg)
+        if served:
+            cctx.serve_start(n_slots=2, max_batch=16, max_queue=100000)
+            gctx.serve_start(n_slots=1, max_batch=1, max_queue=100000)
+            # warm-up (not timed): every slot allocates its workspace and pinned staging on first use
+            warm = [cctx.submit(lists[k % len(lists)], chunk_id=100000 + k, params=cparams) for k in range(8)]
+            for k in (100, 2000):
+                gctx.wait(gctx.submit(list(range(k)), kind=bf._lib.BF_REQ_GLOBAL, params=gparams))
+            for t in warm:
+                cctx.wait(t)
+            clat, glat, wall = _serve_session(cctx, gctx, arrivals, cparams, gparams, bf._lib)
+            for t in [cctx.submit(lists[k % len(lists)], chunk_id=200000 + k, params=cparams) for k in range(8)]:
+                cctx.wait(t)
+            hlat, _, hwall = _serve_session(cctx, None, burst, cparams, None, bf._lib)
+            cctx.serve_stop()
+            gctx.serve_stop()
+        else:
+            for k in range(8):
+                cctx.solve_local(100000 + k, lists[k % len(lists)], params=cparams)
+            for k in (100, 2000):
+                gctx.solve_global(list(range(k)), params=gparams)
+            clat, glat, wall = _plain_session(cctx, gctx, arrivals, cparams, gparams)
+            hlat, _, hwall = _plain_session(cctx, None, burst, cparams, None)
         gctx.close()
-        # a heavier chunk-only stream, where requests overlap and batching pays
-        hi_rate, hi_n = 600.0, 1200
-        hgaps = rng.exponential(1.0 / hi_rate, size=hi_n)
-        cctx.serve_start(n_slots=slots, max_batch=batch, max_queue=100000)
-        for t in [cctx.submit(lists[k % len(lists)], chunk_id=200000 + k, params=cparams) for k in range(4 * slots)]:
-            cctx.wait(t)
-        ht = []
-        th0 = time.perf_counter()
-        t_next = th0
-        for r in range(hi_n):
-            t_next += hgaps[r]
-            while time.perf_counter() < t_next:
-                time.sleep(0.0001)
-            ht.append(cctx.submit(lists[r % len(lists)], chunk_id=300000 + r, params=cparams))
-        hlat = sorted(cctx.wait(t)[1]["ms"] for t in ht)
-        hwall = time.perf_counter() - th0
-        cctx.serve_stop()
         cctx.close()
+        allat = sorted(clat + glat)
         clat.sort()
         glat.sort()
-        q = lambda v, f: v[min(len(v) - 1, int(f * len(v)))] if v else None  # noqa: E731
+        hlat.sort()
         out[name] = {"chunk_p50_ms": q(clat, 0.5), "chunk_p99_ms": q(clat, 0.99), "global_p50_ms": q(glat, 0.5),
-                     "global_p99_ms": q(glat, 0.99), "solves_per_s": (len(clat) + len(glat)) / wall,
-                     "wall_s": wall, "slots": slots, "max_batch": batch,
+                     "global_p99_ms": q(glat, 0.99), "all_p50_ms": q(allat, 0.5), "all_p99_ms": q(allat, 0.99),
+                     "global_max_ms": glat[-1] if glat else None, "solves_per_s": len(allat) / wall, "wall_s": wall,
                      "chunk_only_600_per_s": {"p50_ms": q(hlat, 0.5), "p99_ms": q(hlat, 0.99),
                                               "solves_per_s": len(hlat) / hwall, "requests": len(hlat)},
-                     "precision": {"chunk": "fp32", "global": "mixed" if gprec == bf.BF_PREC_MIXED else "fp32"}}
+                     "precision": {"chunk": "fp32", "global": "mixed" if served else "fp32"},
+                     "form": ("serving loops: chunks 2 slots x batches of up to 16 on high-priority streams, globals "
+                              "1 slot on a low-priority stream" if served else
+                              "one host loop, requests in arrival order, synchronous bf_solve_local / bf_solve_global")}
     return out
 
 

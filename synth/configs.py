@@ -192,6 +192,16 @@ def cfg5():
     return large_global_problem(seed_for(5))
 
 
+def cfg4_global():
+    """The serving stream's global keyframe set: 2000 keyframes at 80x60 along one loop of the
+    large ring corridor (pairs as in the large global workload, 64-256 correspondences per pair,
+    5 % outliers), 8 GN x 20 PCG per solve.  A global request solves the first k keyframes, k
+    growing from 100 to 2000 over a session."""
+    p = large_global_problem(seed_for(4), 2000, 80, 60, n_corr=(64, 256), outlier_frac=0.05, name="global2000_80x60")
+    p.solve = dict(n_gn=8, n_pcg=20, w_sparse=1.0, w_dense=0.5, w_photo=0.1, w_geo=1.0)
+    return p
+
+
 def cfg2():
     """Global solve: 300 keyframes at 80x60 along a ~60 m loop, overlap > 30 %, 8 GN x 20 PCG."""
     return global_problem(seed_for(2), 300, 80, 60, name="global300_80x60")
