@@ -1130,19 +1130,21 @@ SERVING_HBM_BUDGET = 40 * 1024 ** 3
 
 def _serve_session(cctx, gctx, arrivals, cparams, gparams, lib):
     """Submit every request at its arrival time to the serving loops; latency = submit ->
-    completion, as the library measures it."""
+    completion, as the library measures it; the session ends at the last completion (submit time
+    + latency), not when this thread has collected every result."""
     ct, gt = [], []
     t0 = time.perf_counter()
     for ta, kind, ids, cid in arrivals:
         while time.perf_counter() - t0 < ta:
             time.sleep(0.0002)
         if kind == "chunk":
-            ct.append(cctx.submit(ids, chunk_id=cid, params=cparams))
+            ct.append((time.perf_counter(), cctx.submit(ids, chunk_id=cid, params=cparams)))
         else:
-            gt.append(gctx.submit(ids, kind=lib.BF_REQ_GLOBAL, params=gparams))
-    clat = [cctx.wait(t)[1]["ms"] for t in ct]
-    glat = [gctx.wait(t)[1]["ms"] for t in gt]
-    return clat, glat, time.perf_counter() - t0
+            gt.append((time.perf_counter(), gctx.submit(ids, kind=lib.BF_REQ_GLOBAL, params=gparams)))
+    cres = [(ts, cctx.wait(t)[1]["ms"]) for ts, t in ct]
+    gres = [(ts, gctx.wait(t)[1]["ms"]) for ts, t in gt]
+    end = max(ts + 1e-3 * ms for ts, ms in cres + gres)
+    return [ms for _, ms in cres], [ms for _, ms in gres], end - t0
 
 
 def _plain_session(cctx, gctx, arrivals, cparams, gparams):

@@ -128,6 +128,15 @@ __device__ void merge_problem(const BatchArgs &a, int p, BatchSmem<Acc> &sm) {
 
 // Item handlers.  All but the dense tile are compiled on their own (not inlined into the dispatch
 // loop), so the loop's register allocation is the dense tile's, as in k_dense.
+// The count after a dense tile, out of line: the item is read back from shared memory, so that
+// nothing of it stays live in registers across the tile's pixel loop (fewer spills there).
+template <typename Acc>
+__device__ __noinline__ void item_dense_done(const BatchArgs &a, const BatchQueue &q, BatchSmem<Acc> &sm) {
+  volatile int *vi = (volatile int *)&sm.item;
+  const int4 it = make_int4(vi[0], vi[1], vi[2], vi[3]);
+  finish_part<Acc>(a, q, it.y, it.z, it.x == IT_EDENSE, sm);
+}
+
 template <typename Acc, int KIND>
 __device__ __forceinline__ void item_dense(const BatchArgs &a, const BatchQueue &q, int4 it, float *ktab,
                                         BatchSmem<Acc> &sm) {
@@ -138,7 +147,7 @@ __device__ __forceinline__ void item_dense(const BatchArgs &a, const BatchQueue 
   else
     dense_tile<MODE_ACCUM, KIND, Acc, true>(it.w, a.t, a.fs, a.in, a.pairM, a.gates, a.wg[it.z], a.wp[it.z],
                                             (Acc *)a.dpart, nullptr, ktab, sm.u.dred);
-  finish_part<Acc>(a, q, it.y, it.z, fin, sm);
+  item_dense_done<Acc>(sm.args, sm.queue, sm);
 }
 
 template <typename Acc>

@@ -181,63 +181,73 @@ __device__ __forceinline__ PairXf load_xf(const float *M) {
   return PairXf{M[0], M[1], M[2], M[3], M[4], M[5], M[6], M[7], M[8], M[9], M[10], M[11]};
 }
 
-// Evaluate source pixel (x, y) of a directed pair: association, gates and (MODE_ACCUM) the
-// residual rows' contributions to acc.  a = source (D, n); loadA / loadB read the target's
-// (D, n) and (I, Ix, Iy); srcI() gives the source pixel's I.  Returns the associated target
-// pixel or -1.
-template <int MODE, typename LA, typename LB, typename LI, typename AccT>
-__device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const PairXf &X, const Intr &in,
-                                          const float *kx, const float *ky, const Gates &g, LA loadA, LB loadB,
-                                          LI srcI, float w_geo, float w_photo, AccT &acc) {
-  if (!(a.x > 0.f && normal_valid(a))) return -1;
+// The association of a source pixel up to the target addresses (the first half of eval_pixel):
+// y = R d + t, its projection u, the nearest target pixel (tx, ty) and the rotated source normal
+// m.  False where the pixel has no association without reading the target (invalid source, y
+// behind the camera, nearest pixel off the 3-pixel interior).
+struct PixA {
+  float Y0, Y1, Y2, iz, ux, uy, m0, m1, m2;
+  int tx, ty;
+};
+
+__device__ __forceinline__ bool assoc_front(const float4 a, int x, int y, const PairXf &X, const Intr &in,
+                                            const float *kx, const float *ky, PixA &s) {
+  if (!(a.x > 0.f && normal_valid(a))) return false;
   const int W = in.W, H = in.H;
   const float z = a.x;
   // ---- association decisions, explicitly rounded FP32 in a fixed order: products, sums and
   // fused multiply-adds (one rounding of a*b + c), y = R d + t accumulated from t ----
   const float dx = FM(kx[x], z), dy = FM(ky[y], z), dz = z;
-  const float Y0 = FMA(X.R02, dz, FMA(X.R01, dy, FMA(X.R00, dx, X.t0)));
-  const float Y1 = FMA(X.R12, dz, FMA(X.R11, dy, FMA(X.R10, dx, X.t1)));
-  const float Y2 = FMA(X.R22, dz, FMA(X.R21, dy, FMA(X.R20, dx, X.t2)));
-  if (!(Y2 > 0.f)) return -1;
+  s.Y0 = FMA(X.R02, dz, FMA(X.R01, dy, FMA(X.R00, dx, X.t0)));
+  s.Y1 = FMA(X.R12, dz, FMA(X.R11, dy, FMA(X.R10, dx, X.t1)));
+  s.Y2 = FMA(X.R22, dz, FMA(X.R21, dy, FMA(X.R20, dx, X.t2)));
+  if (!(s.Y2 > 0.f)) return false;
   // the hardware reciprocal (rcp.approx: one MUFU instruction, about 1 ulp): the correctly rounded
   // __frcp_rn added a refinement and a slow-path test to every pixel.  Its ulp moves u by ~1e-5 px,
   // inside the FP32 tie windows of the decisions
-  float iz;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iz) : "f"(Y2));
-  const float ux = FMA(in.fx, FM(Y0, iz), in.cx);
-  const float uy = FMA(in.fy, FM(Y1, iz), in.cy);
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s.iz) : "f"(s.Y2));
+  s.ux = FMA(in.fx, FM(s.Y0, s.iz), in.cx);
+  s.uy = FMA(in.fy, FM(s.Y1, s.iz), in.cy);
   // nearest pixel floor(u + 0.5) on the 3-pixel interior, 3 <= n <= W - 4 (inside the image without a
   // test of its own).  Then the bilinear taps floor(u), floor(u) + 1 lie on the 2-pixel interior where
   // grad I is defined (floor(u) >= n - 1 and floor(u) + 1 <= n + 1), and every threshold on u sits at
   // a half-integer, which an integer projection (every pixel of an identity relative pose) never hits
-  const float nxf = floorf(FA(ux, 0.5f)), nyf = floorf(FA(uy, 0.5f));
-  if (!(nxf >= 3.f && nxf <= (float)(W - 4) && nyf >= 3.f && nyf <= (float)(H - 4))) return -1;
-  const float bxf = floorf(ux), byf = floorf(uy);
-  const int tx = (int)nxf, ty = (int)nyf;
-  const int bx = (int)bxf, by = (int)byf;
-  const int tpx = ty * W + tx, b0 = by * W + bx;
-  // issue the target reads together: nearest (D, n) and the four (I, Ix, Iy) taps
-  const float4 b = loadA(tpx);
-  float4 c00, c01, c10, c11;
-  if (MODE != MODE_ASSOC) {
-    c00 = loadB(b0);
-    c01 = loadB(b0 + 1);
-    c10 = loadB(b0 + W);
-    c11 = loadB(b0 + W + 1);
-  }
+  const float nxf = floorf(FA(s.ux, 0.5f)), nyf = floorf(FA(s.uy, 0.5f));
+  if (!(nxf >= 3.f && nxf <= (float)(W - 4) && nyf >= 3.f && nyf <= (float)(H - 4))) return false;
+  s.tx = (int)nxf;
+  s.ty = (int)nyf;
+  s.m0 = FMA(X.R02, a.w, FMA(X.R01, a.z, FM(X.R00, a.y)));
+  s.m1 = FMA(X.R12, a.w, FMA(X.R11, a.z, FM(X.R10, a.y)));
+  s.m2 = FMA(X.R22, a.w, FMA(X.R21, a.z, FM(X.R20, a.y)));
+  return true;
+}
+
+// Bilinear base tap floor(u) as a pixel index.
+__device__ __forceinline__ int assoc_tap0(const PixA &s, int W) {
+  return (int)floorf(s.uy) * W + (int)floorf(s.ux);
+}
+
+// The second half: the gates on the nearest target record b = (D, n), then (MODE_ACCUM) the
+// residual rows' contributions to acc.  c00..c11 = the bilinear taps' (I, Ix, Iy); srcI() gives
+// the source pixel's I.  Returns the associated target pixel or -1.
+template <int MODE, typename LI, typename AccT>
+__device__ __forceinline__ int assoc_back(const PixA &s, const float4 b, const float4 c00, const float4 c01,
+                                          const float4 c10, const float4 c11, const Intr &in, const float *kx,
+                                          const float *ky, const Gates &g, LI srcI, float w_geo, float w_photo,
+                                          AccT &acc) {
   if (!(b.x > 0.f && normal_valid(b))) return -1;
-  const float qx = FM(kx[tx], b.x), qy = FM(ky[ty], b.x), qz = b.x;
-  const float ex = FS(Y0, qx), ey = FS(Y1, qy), ez = FS(Y2, qz);
+  const float qx = FM(kx[s.tx], b.x), qy = FM(ky[s.ty], b.x), qz = b.x;
+  const float ex = FS(s.Y0, qx), ey = FS(s.Y1, qy), ez = FS(s.Y2, qz);
   const float dist2 = FMA(ez, ez, FMA(ey, ey, FM(ex, ex)));
-  const float m0 = FMA(X.R02, a.w, FMA(X.R01, a.z, FM(X.R00, a.y)));
-  const float m1 = FMA(X.R12, a.w, FMA(X.R11, a.z, FM(X.R10, a.y)));
-  const float m2 = FMA(X.R22, a.w, FMA(X.R21, a.z, FM(X.R20, a.y)));
-  const float ndot = FMA(m2, b.w, FMA(m1, b.z, FM(m0, b.y)));
+  const float ndot = FMA(s.m2, b.w, FMA(s.m1, b.z, FM(s.m0, b.y)));
   if (!(dist2 < g.tau_d2 && ndot > g.tau_n)) return -1;
+  const int tpx = s.ty * in.W + s.tx;
   if (MODE == MODE_ASSOC) return tpx;
   // ---- residuals and Jacobians (free FP32) in camera-j coordinates ----
+  const float m0 = s.m0, m1 = s.m1, m2 = s.m2, Y0 = s.Y0, Y1 = s.Y1, Y2 = s.Y2, iz = s.iz;
   const float r_g = m0 * ex + m1 * ey + m2 * ez;
-  const float wx = ux - bxf, wy = uy - byf;
+  const float bxf = floorf(s.ux), byf = floorf(s.uy);
+  const float wx = s.ux - bxf, wy = s.uy - byf;
   const float w00 = (1.f - wx) * (1.f - wy), w01 = wx * (1.f - wy);
   const float w10 = (1.f - wx) * wy, w11 = wx * wy;
   const float Ij = w00 * c00.x + w01 * c01.x + w10 * c10.x + w11 * c11.x;
@@ -255,6 +265,30 @@ __device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const Pa
     acc.add_row(w_photo, r_p, gv, cross3(gv, V3{Y0, Y1, Y2}));
   }
   return tpx;
+}
+
+// Evaluate source pixel (x, y) of a directed pair: association, gates and (MODE_ACCUM) the
+// residual rows' contributions to acc.  a = source (D, n); loadA / loadB read the target's
+// (D, n) and (I, Ix, Iy); srcI() gives the source pixel's I.  Returns the associated target
+// pixel or -1.
+template <int MODE, typename LA, typename LB, typename LI, typename AccT>
+__device__ __forceinline__ int eval_pixel(const float4 a, int x, int y, const PairXf &X, const Intr &in,
+                                          const float *kx, const float *ky, const Gates &g, LA loadA, LB loadB,
+                                          LI srcI, float w_geo, float w_photo, AccT &acc) {
+  PixA s;
+  if (!assoc_front(a, x, y, X, in, kx, ky, s)) return -1;
+  const int W = in.W;
+  const int b0 = assoc_tap0(s, W);
+  // issue the target reads together: nearest (D, n) and the four (I, Ix, Iy) taps
+  const float4 b = loadA(s.ty * W + s.tx);
+  float4 c00, c01, c10, c11;
+  if (MODE != MODE_ASSOC) {
+    c00 = loadB(b0);
+    c01 = loadB(b0 + 1);
+    c10 = loadB(b0 + W);
+    c11 = loadB(b0 + W + 1);
+  }
+  return assoc_back<MODE>(s, b, c00, c01, c10, c11, in, kx, ky, g, srcI, w_geo, w_photo, acc);
 }
 
 // Pixel walk of one thread: px = start, start + stride, ... with (x, y) advanced incrementally.
