@@ -122,6 +122,8 @@ def parse():
                     help="run only the pruning / verification / key-point / TSDF legs (one JSON line)")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "bf16", "fp16"],
                     help="frame storage of the timed workload (16-bit: normals, I, grad I)")
+    ap.add_argument("--dense-tc", type=int, default=0, choices=[0, 1, 3],
+                    help="form the dense sums on the tensor cores (1: TF32 operands, 3: three TF32 products)")
     ap.add_argument("--pcg-variant", type=int, default=0, choices=[0, 1, 2, 3],
                     help="PCG kernel: 0 auto, 1 one CTA per problem, 2 grid-cooperative, 3 cluster")
     return ap.parse_args()
@@ -421,7 +423,8 @@ def run_ours(args, rank, world, local_rank):
     if args.persistent and args.tile_px == -1:
         args.tile_px = PERSISTENT_TILE_PX
     params = bf.default_params(precision=precision, use_graph=0 if args.no_graph else 1, tile_px=args.tile_px,
-                               pcg_variant=args.pcg_variant, persistent=1 if args.persistent else 0, **common)
+                               pcg_variant=args.pcg_variant, persistent=1 if args.persistent else 0,
+                               dense_tc=args.dense_tc, **common)
     storage = STORAGE_CODES[args.storage](bf)
     ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=local_rank,
                      stream=stream.cuda_stream, max_frames_hint=prob.n_frames, storage=storage)
@@ -490,7 +493,7 @@ def run_ours(args, rank, world, local_rank):
     # per-kernel device times: a pass kernel by kernel with CUDA events around every launch on the
     # context's stream (the graph replay above carries no events); same decomposition as the graph
     prof_params = bf.default_params(precision=precision, use_graph=0, tile_px=args.tile_px,
-                                    pcg_variant=args.pcg_variant, **common)
+                                    pcg_variant=args.pcg_variant, dense_tc=args.dense_tc, **common)
     _, _, prof = timed(lambda: step(prof_params), 2, profile=True)
     tuned = ctx.tuned_tile_px() if args.tile_px == bf.BF_TILE_AUTOTUNE else args.tile_px
     HW = intr["W"] * intr["H"]
@@ -554,6 +557,9 @@ def run_ours(args, rank, world, local_rank):
                                                   stats, stream)
         line["compensated_sums"] = chunk_compensated_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common,
                                                          gn_per_step, stats, stream, tuned)
+        line["tensor_core_sums"] = {
+            f"dense_tc{tc}": chunk_compensated_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn_per_step,
+                                                   stats, stream, tuned, dense_tc=tc) for tc in (3, 1)}
         ctx.close()
         line["bf16_storage"] = chunk_batch_leg(bf, torch, dev, stream, prob=prob, storage="bf16")
         line["global300"] = global300_leg(bf, torch, dev, stream, args)
@@ -650,9 +656,11 @@ def chunk_persistent_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn
 
 
 def chunk_compensated_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, gn_per_step, ref_stats, stream, tile,
-                          steps=3):
-    """The same batch with compensated (Kahan) per-thread sums in the dense kernel (same tiles)."""
-    pc = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, tile_px=tile, compensated=1, **common)
+                          steps=3, **variant):
+    """The same batch with another form of the dense sums (same tiles): compensated (Kahan)
+    per-thread sums by default, or the variant given (dense_tc = 1 or 3: tensor-core sums)."""
+    variant = variant or {"compensated": 1}
+    pc = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=1, tile_px=tile, **variant, **common)
 
     def run(p):
         ctx.add_frames(0, depth_d, lum_d)
@@ -670,12 +678,12 @@ def chunk_compensated_leg(bf, torch, ctx, depth_d, lum_d, cids, lists, common, g
         ts.append(e0.elapsed_time(e1))
     ctx.reset_profile()
     ctx.set_profiling(True)
-    run(bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, tile_px=tile, compensated=1, **common))
+    run(bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, tile_px=tile, **variant, **common))
     dense = ctx.profile()["kernels"]["dense"]
     ctx.set_profiling(False)
     return {"value": gn_per_step / (statistics.mean(ts) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(ts),
             "tile_px": tile, "dense_avg_launch_ms": dense["ms"] / max(dense["count"], 1),
-            "final_energy_max_rel_diff_vs_plain_sums": max(
+            "final_energy_max_rel_diff_vs_fp32_fma_sums": max(
                 abs(a["energy"][-1] - b["energy"][-1]) / abs(b["energy"][-1]) for a, b in zip(sc, ref_stats))}
 
 

@@ -142,6 +142,14 @@ typedef struct {
    * dense kernel; not with persistent.  0 (default): plain FP32 runs of at most tile_px / 256
    * pixels per thread. */
   int compensated;
+  /* Tensor-core dense sums (a measured alternative, not the default): 1 or 3 forms each dense
+   * tile's J^T W J and J^T W r sums with tcgen05 MMAs (TF32 operands, FP32 accumulators in tensor
+   * memory) instead of per-thread FP32 fused multiply-adds; 1 rounds the operands to TF32, 3
+   * splits each into two TF32 parts and adds three products (close to FP32 products).  The
+   * association and the residuals are unchanged.  Always the tiled dense kernel; not with
+   * persistent or compensated; a solve that records its association uses the FP32 sums.  0
+   * (default): off. */
+  int dense_tc;
 } bf_solve_params;
 
 enum { BF_SPARSE_BLOCKS = 0, BF_SPARSE_MATFREE = 1 };
@@ -298,6 +306,16 @@ bf_status bf_debug_record_association(bf_ctx *ctx, int enable);
  * nothing was recorded or the pair was not a dense pair of the recorded solve. */
 bf_status bf_debug_recorded_association(bf_ctx *ctx, int eval, int frame_i, int frame_j, int32_t *out_target,
                                         double *pose_i, double *pose_j);
+
+/* Debug probe of the tensor-core dense sums (no counterpart in the paper): stages given rows
+ * exactly as the tcgen05 dense kernel does and returns its whole 64 x 64 FP32 accumulator as
+ * held in tensor memory.  fa, fb: host arrays [8][n_rows][8] (subset, row, feature) of the A
+ * (weighted) and B rows, n_rows a positive multiple of 64 up to 65536; passes 1 or 3 (as
+ * bf_solve_params.dense_tc); out: host array [128][64], tensor-memory lane x column (lanes that
+ * hold no accumulator row come back as the tensor memory held them).  Runs one CTA on the
+ * current device with its own temporary device buffers; synchronous.  BF_ERR_INVALID_ARG for
+ * bad arguments, BF_ERR_TIMEOUT if a bounded wait gave up, BF_ERR_CUDA on a CUDA error. */
+bf_status bf_debug_tc_probe(int n_rows, int passes, const float *fa, const float *fb, float *out);
 
 /*
  * Kernel accounting.  Every kernel the context launches is counted; with profiling enabled the

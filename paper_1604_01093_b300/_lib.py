@@ -49,7 +49,8 @@ class SolveParams(ctypes.Structure):
                 ("dense_on", ctypes.c_int), ("warm_start", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("tile_px", ctypes.c_int), ("pcg_variant", ctypes.c_int),
                 ("prune_rmax", ctypes.c_double), ("prune_rounds", ctypes.c_int),
-                ("sparse_mode", ctypes.c_int), ("persistent", ctypes.c_int), ("compensated", ctypes.c_int)]
+                ("sparse_mode", ctypes.c_int), ("persistent", ctypes.c_int), ("compensated", ctypes.c_int),
+                ("dense_tc", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -152,6 +153,7 @@ def lib():
         "bf_debug_association": (I, [P, I, I, P, P, ctypes.POINTER(SolveParams), P]),
         "bf_debug_record_association": (I, [P, I]),
         "bf_debug_recorded_association": (I, [P, I, I, I, P, P, P]),
+        "bf_debug_tc_probe": (I, [I, I, P, P, P]),
         "bf_device_bytes": (ctypes.c_size_t, [P]),
         "bf_set_profiling": (I, [P, I]),
         "bf_get_profile": (I, [P, ctypes.POINTER(Profile)]),
@@ -190,7 +192,7 @@ EXPORTS = ["bf_default_config", "bf_default_params", "bf_status_string", "bf_cre
            "bf_remove_pair", "bf_set_profiling", "bf_get_profile", "bf_reset_profile",
            "bf_clear_correspondences", "bf_solve_local", "bf_solve_local_batch", "bf_solve_global",
            "bf_get_poses", "bf_build_system", "bf_get_frame_planes", "bf_debug_association",
-           "bf_debug_record_association", "bf_debug_recorded_association", "bf_device_bytes",
+           "bf_debug_record_association", "bf_debug_recorded_association", "bf_debug_tc_probe", "bf_device_bytes",
            "bf_dense_pair_noalloc", "bf_serve_start", "bf_serve_stop", "bf_submit", "bf_wait",
            "bf_default_verify_params", "bf_verify_pairs", "bf_validate_chunk", "bf_default_keypoint_params",
            "bf_filter_keypoints", "bf_selftest_wait_timeout", "bf_default_tsdf_config", "bf_tsdf_init",
@@ -529,3 +531,16 @@ def dense_pair_noalloc(depth_i, lum_i, depth_j, lum_j, pose_i, pose_j, out, widt
                                      stream)
     if st != BF_OK:
         raise BFError(st, "bf_dense_pair_noalloc failed")
+
+
+def tc_probe(fa, fb, passes=3):
+    """bf_debug_tc_probe: fa, fb host arrays (8, n_rows, 8); returns the (128, 64) accumulator."""
+    fa = np.ascontiguousarray(fa, dtype=np.float32)
+    fb = np.ascontiguousarray(fb, dtype=np.float32)
+    if fa.shape != fb.shape or fa.ndim != 3 or fa.shape[0] != 8 or fa.shape[2] != 8:
+        raise ValueError("fa and fb must both be (8, n_rows, 8)")
+    out = np.zeros((128, 64), np.float32)
+    st = lib().bf_debug_tc_probe(fa.shape[1], passes, _ptr(fa), _ptr(fb), _ptr(out))
+    if st != BF_OK:
+        raise BFError(st, "bf_debug_tc_probe failed")
+    return out

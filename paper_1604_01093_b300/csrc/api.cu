@@ -887,7 +887,8 @@ static inline bool axes_within(const Pose12 &Pa, const Pose12 &Pb, double cos_ma
 // 4800-pixel tiles
 static void dense_decomposition(const bf_ctx *c, const bf_solve_params &prm, bool &staged, int &tile_px) {
   const int HW = c->cfg.width * c->cfg.height;
-  staged = prm.tile_px == 0 && !prm.compensated && dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage);
+  staged = prm.tile_px == 0 && !prm.compensated && !prm.dense_tc &&
+           dense_staged_fits(c->cfg.width, c->cfg.height, c->cfg.storage);
   tile_px = prm.tile_px > 0 ? prm.tile_px : (staged ? HW : std::min(HW, 4800));
 }
 
@@ -1472,6 +1473,9 @@ void linearise(bf_ctx *c, DevSolve &D, const bf_solve_params &prm, double wd, in
     if (t.n_wi > 0)
       return launch_dense_staged<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
                                       (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, rec, c->ex->st);
+    if (prm.dense_tc && mode == MODE_ACCUM && !rec)
+      return launch_dense_tc<Acc>(t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
+                                  (float)(wd * prm.w_photo), (Acc *)D.dpart, D.derr, prm.dense_tc, c->ex->st);
     return launch_dense<Acc>(mode, t, frame_store(c), c->intr, D.pairM, g, (float)(wd * prm.w_geo),
                              (float)(wd * prm.w_photo), (Acc *)D.dpart, rec, c->ex->st, prm.compensated != 0);
   });
@@ -1689,6 +1693,10 @@ bf_status check_params(bf_ctx *c, const bf_solve_params *p) {
   if (p->compensated != 0 && p->compensated != 1) return fail(c, BF_ERR_INVALID_ARG, "compensated must be 0 or 1");
   if (p->compensated && p->persistent)
     return fail(c, BF_ERR_INVALID_ARG, "compensated sums are not available in the persistent launch");
+  if (p->dense_tc != 0 && p->dense_tc != 1 && p->dense_tc != 3)
+    return fail(c, BF_ERR_INVALID_ARG, "dense_tc must be 0, 1 or 3");
+  if (p->dense_tc && (p->persistent || p->compensated))
+    return fail(c, BF_ERR_INVALID_ARG, "dense_tc is not available with persistent or compensated");
   if (p->sparse_mode != BF_SPARSE_BLOCKS && p->sparse_mode != BF_SPARSE_MATFREE)
     return fail(c, BF_ERR_INVALID_ARG, "unknown sparse_mode");
   if (p->sparse_mode == BF_SPARSE_MATFREE && p->pcg_variant == BF_PCG_CLUSTER)

@@ -458,6 +458,11 @@ int launch_dense_staged(int mode, const Tables &t, const FrameStore &fs, const I
 template <typename Part>
 int launch_dense(int mode, const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g,
                   float w_geo, float w_photo, Part *part, int *assoc, cudaStream_t st, bool comp = false);
+// Tensor-core form of the dense ACCUM launch over the tiled decomposition (passes 1 or 3); sets
+// *err if one of its bounded waits gave up.
+template <typename Part>
+int launch_dense_tc(const Tables &t, const FrameStore &fs, const Intr &in, const float *pairM, Gates g, float w_geo,
+                    float w_photo, Part *part, int *err, int passes, cudaStream_t st);
 template <typename Part>
 int launch_sparse(int mode, const Tables &t, const float4 *P, const float4 *Q, const float *pairM, float w_sparse,
                    Part *part, float *seg_rmax, int *seg_rarg, cudaStream_t st);

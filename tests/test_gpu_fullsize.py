@@ -22,10 +22,14 @@
   moves a chunk's energy by up to ~1e-5: a residual at the 0.15 m distance gate).
 * The 2000-keyframe 160x120 solve (BF16 frame storage, tiled dense kernel, its PCG): its first
   Gauss-Newton step against the stored step of the oracle on its own decisions, on the same
-  BF16-rounded planes: energies 1e-5, the poses of every 32nd keyframe 1e-4 rad and 1e-4 m (the
-  ties decided the other way, a few per million pixels, move this 12k-unknown step by ~3e-5 m;
-  the replayed single steps above show the exact protocol at full size); its error against the
-  oracle on the unrounded frames is printed.
+  BF16-rounded planes: energies 1e-5; the poses of all 2000 keyframes, the 99th percentile within
+  1e-4 m and every keyframe within 1e-3 rad and 1e-3 m (the ties decided the other way, 7.6e-6
+  of the valid pixels, move a weakly connected stretch of the loop, keyframes 1130-1142 with 14-18
+  pairs each, by up to 3.1e-4 m; elsewhere the steps agree to a few 1e-5 m).  With
+  BF_SLOW_TESTS=1 the oracle's step on the library's own (checked) decisions is computed here
+  (about four minutes on the host cores) and every keyframe is held to 1e-4 rad and 1e-5 m
+  (measured 2.3e-6 rad, 8.6e-6 m).  The step's error against the oracle on the unrounded frames
+  is printed.
 
 The stored results are written by the make_*_oracle.py scripts beside them from the oracle and
 the seeded scene generator alone.
@@ -52,6 +56,7 @@ LOOP_ROT_TOL, LOOP_TRANS_TOL = 2e-2, 2e-2
 LOOP_REC_TOL = 2e-2
 # a single step compared with the oracle on its own decisions (no replay): see the module docstring
 STEP_TRANS_TOL_OWN = 1e-4
+STEP2000_OWN_TOL, STEP2000_OWN_P99_TRANS = 1e-3, 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -349,16 +354,51 @@ def test_global2000_first_step_matches_oracle(bf, global2000, golden2000):
         rel = np.abs(np.array(st["energy"]) - gold_e) / gold_e
         P = ctx.get_poses(g["frames_kept"])
         rot, tr = worst_pose_error(P, poses44(g["poses"]))
+        trs = [lie.pose_error(a, b)[1] for a, b in zip(P, poses44(g["poses"]))]
+        p99 = float(np.quantile(trs, 0.99))
         print(f"2000 keyframes, BF16 storage vs oracle on {ref_name} planes: energy {rel.max():.2e}, "
-              f"poses {rot:.2e} rad {tr:.2e} m")
+              f"poses {rot:.2e} rad {tr:.2e} m (99th percentile {p99:.2e} m)")
         if ref_name == "bf16":
             assert rel.max() <= ENERGY_RTOL, rel
-            # the oracle decided on its own here (no replay): the few thousand ties of 0.93 G directed
-            # pixels decided the other way move this step of a 12k-unknown loop by a few 1e-5 m
-            assert rot <= ROT_TOL and tr <= STEP_TRANS_TOL_OWN, (rot, tr)
+            # the oracle decided on its own here (no replay): see the module docstring
+            assert rot <= STEP2000_OWN_TOL and tr <= STEP2000_OWN_TOL, (rot, tr)
+            assert p99 <= STEP2000_OWN_P99_TRANS, p99
     gold_e = np.array(golden2000["bf16"]["energy"])
     ctx.add_frames(0, depth, lum, init_pose=prob.init)
     full = ctx.solve_global(ids, n_gn=d["n_gn"], **common)
     assert abs(full["energy"][0] - gold_e[0]) <= ENERGY_RTOL * gold_e[0]
     assert abs(full["energy"][1] - gold_e[1]) <= ENERGY_RTOL * gold_e[1]
     assert full["energy"][-1] < full["energy"][0]
+
+
+@pytest.mark.skipif(os.environ.get("BF_SLOW_TESTS") != "1", reason="slow (about four minutes): BF_SLOW_TESTS=1")
+def test_global2000_first_step_on_library_decisions(bf, global2000):
+    """The 2000-keyframe first Gauss-Newton step against the oracle's step on the library's own
+    association decisions (fetched at the oracle's poses and checked: ties only), every keyframe."""
+    import torch
+    prob = global2000
+    d = prob.solve
+    ids = list(range(prob.n_frames))
+    frames = [ofr.Frame(prob.depth[k], prob.lum[k], prob.intr, storage="bf16") for k in ids]
+    intr = prob.intr
+    dev = torch.device("cuda", 0)
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"],
+                     max_frames_hint=prob.n_frames, storage=bf.BF_STORE_BF16)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
+                                  torch.from_numpy(prob.p_j).to(dev))
+    ctx.add_frames(0, torch.from_numpy(prob.depth).to(dev), torch.from_numpy(prob.lum).to(dev), init_pose=prob.init)
+    kw = dict(n_pcg=d["n_pcg"], w_sparse=d["w_sparse"], w_dense=d["w_dense"], w_photo=d["w_photo"], w_geo=d["w_geo"])
+    st = ctx.solve_global(ids, n_gn=1, use_graph=1, tile_px=bf.BF_TILE_AUTOTUNE, **kw)
+    P = ctx.get_poses(ids)
+    rep = replay.from_ctx(ctx, ids, intr["W"], intr["H"], storage="bf16")
+    with system.frame_pool(frames, None) as pool:
+        ref = solver.gauss_newton(frames, intr, prob.init, solver.sparse_pairs_for(prob, ids),
+                                  SolveParams(n_gn=1, **kw), assoc=rep,
+                                  pmap=lambda f, tasks: pool.map(f, tasks, chunksize=64))
+    rel = np.abs(np.array(st["energy"]) - np.array(ref.energy)) / np.array(ref.energy)
+    rot, tr = worst_pose_error(P, ref.poses)
+    print(f"2000 keyframes on the library's decisions: energy {rel.max():.2e}, poses {rot:.2e} rad {tr:.2e} m, "
+          f"flips {rep.n_flips} of {rep.n_valid}")
+    assert rel.max() <= ENERGY_RTOL and rot <= ROT_TOL and tr <= TRANS_TOL, (rel.max(), rot, tr)
+    assert rep.n_flips <= 1e-4 * rep.n_valid
+    ctx.close()
