@@ -546,7 +546,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_extras and rank == 0:
         line["e2e"] = chunk_e2e_leg(bf, torch, ctx, prob, stream, cids, lists, params, all_ids, timed,
-                                    max(3, args.steps // 2))
+                                    max(3, args.steps // 2), storage=storage)
         # restore the device-resident correspondences
         ctx.clear_correspondences()
         ctx.add_correspondences_batch(prob.pairs, prob.corr_off, torch.from_numpy(prob.p_i).to(dev),
@@ -574,20 +574,24 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
-def chunk_e2e_leg(bf, torch, ctx, prob, stream, cids, lists, params, all_ids, timed, steps):
+def chunk_e2e_leg(bf, torch, ctx, prob, stream, cids, lists, params, all_ids, timed, steps, storage=None):
     """The batch end to end through the C ABI from pinned host buffers: every step uploads the raw
-    frames and the correspondences, solves, and reads every frame's pose back."""
+    frames and the correspondences, solves, and reads every frame's pose back.  value: two
+    contexts on two streams driven by two host threads, each running whole steps, so that one
+    step's uploads overlap the other's solve (host clock around all steps of both); serial: one
+    context, one step after another (CUDA events around each step)."""
+    import threading
     depth_h = torch.from_numpy(prob.depth).pin_memory()
     lum_h = torch.from_numpy(prob.lum).pin_memory()
     pi_h = torch.from_numpy(prob.p_i).pin_memory()
     pj_h = torch.from_numpy(prob.p_j).pin_memory()
 
-    def step_e2e():
-        ctx.add_frames(0, depth_h, lum_h)
-        ctx.clear_correspondences()
-        ctx.add_correspondences_batch(prob.pairs, prob.corr_off, pi_h, pj_h)
-        s = ctx.solve_local_batch(cids, lists, params)
-        ctx.get_poses(all_ids)
+    def step_e2e(c=ctx):
+        c.add_frames(0, depth_h, lum_h)
+        c.clear_correspondences()
+        c.add_correspondences_batch(prob.pairs, prob.corr_off, pi_h, pj_h)
+        s = c.solve_local_batch(cids, lists, params)
+        c.get_poses(all_ids)
         return s
 
     for _ in range(2):
@@ -597,10 +601,42 @@ def chunk_e2e_leg(bf, torch, ctx, prob, stream, cids, lists, params, all_ids, ti
         prob.corr_off.nbytes
     d2h = prob.n_frames * 16 * 8
     gn = params.n_gn * len(lists)
-    return {"value": gn / (statistics.mean(te) / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(te),
+    serial = {"value": gn / (statistics.mean(te) / 1000.0), "ms_per_step": statistics.mean(te)}
+    # two contexts, two streams, two host threads
+    intr = prob.intr
+    stream2 = torch.cuda.Stream(stream.device)
+    ctx2 = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], device=stream.device.index,
+                      stream=stream2.cuda_stream, max_frames_hint=prob.n_frames,
+                      storage=storage if storage is not None else bf.BF_STORE_FP32)
+    for _ in range(2):
+        step_e2e(ctx2)
+    errors = []
+
+    def run(c, k):
+        try:
+            for _ in range(k):
+                step_e2e(c)
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    torch.cuda.synchronize(stream.device)
+    t0 = time.perf_counter()
+    threads = [threading.Thread(target=run, args=(c, steps)) for c in (ctx, ctx2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    torch.cuda.synchronize(stream.device)
+    wall = time.perf_counter() - t0
+    ctx2.close()
+    if errors:
+        raise errors[0]
+    return {"value": 2 * steps * gn / wall, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": 1000.0 * wall / (2 * steps), "serial": serial,
             "note": "pinned host depth, luminance and correspondences uploaded, poses of all frames read back, "
-                    "every step; per-chunk statistics also come back each step"}
+                    "every step; per-chunk statistics also come back each step.  value: two contexts on two "
+                    "streams, one host thread each, whole steps in parallel (one step's uploads overlap the "
+                    "other's solve), host clock around all 2 x steps; serial: one context, step after step"}
 
 
 def chunk_plain_leg(bf, torch, ctx, dev, prob, depth_d, lum_d, cids, lists, common, gn_per_step, stream, steps=2):
