@@ -1,4 +1,4 @@
-"""GPU association replay for the parity tests (Sec. 4.3 dense matching; the survey's protocol).
+"""GPU association replay for the parity tests (Sec. 4.3 dense matching).
 
 The library takes its association decisions in FP32 and the oracle in FP64, so a few decisions
 per million (those within FP32 rounding of a threshold: a projection next to a pixel boundary, a
