@@ -644,7 +644,7 @@ def chunk_plain_leg(bf, torch, ctx, dev, prob, depth_d, lum_d, cids, lists, comm
     """The plain path: one FP32 solve per chunk, kernel by kernel (no batching, no graph); chunk-solve
     latency = call -> poses on the host."""
     pp = bf.default_params(precision=bf.BF_PREC_FP32, use_graph=0, **common)
-    lat, tot = [], []
+    lat, tot, done = [], [], []
     for rep in range(steps + 1):
         ctx.add_frames(0, depth_d, lum_d)
         torch.cuda.synchronize(dev)
@@ -655,11 +655,17 @@ def chunk_plain_leg(bf, torch, ctx, dev, prob, depth_d, lum_d, cids, lists, comm
             ctx.get_poses(lst)
             if rep:
                 lat.append(1000.0 * (time.perf_counter() - t1))
+                done.append(1000.0 * (time.perf_counter() - t0))
         if rep:
             tot.append(time.perf_counter() - t0)
     return {"value": gn_per_step / statistics.mean(tot), "unit": UNIT, "ms_per_step": 1000.0 * statistics.mean(tot),
             "solves_per_s": len(lists) / statistics.mean(tot), "chunk_latency_p50_ms": quantile(lat, 0.5),
-            "chunk_latency_p99_ms": quantile(lat, 0.99), "precision": "fp32", "cuda_graph": False,
+            "chunk_latency_p99_ms": quantile(lat, 0.99),
+            "all_at_once": {"p50_ms": quantile(done, 0.5), "p99_ms": quantile(done, 0.99),
+                            "note": "the step's chunks all requested at its start and served one call after "
+                                    "another: each chunk's completion time from the start (compare with "
+                                    "chunk_latency.batched_*)"},
+            "precision": "fp32", "cuda_graph": False,
             "note": "same chunks, one bf_solve_local per chunk (host clock around each call)"}
 
 
