@@ -7,6 +7,7 @@ operands and FP32 accumulators in tensor memory).
 * the normal equations of a 5-frame 320x240 chunk at perturbed poses against the oracle on the
   same decisions, both forms (dense_tc = 3: three TF32 products; dense_tc = 1: TF32 operands)
   within the parity tolerance of the FP32 sums (the table is printed with -s);
+* ragged tiles (shorter than one staging round, or ending inside one) against the FP32 sums;
 * a batched solve with dense_tc = 3 against the same solve with the FP32 sums.
 """
 import json
@@ -125,6 +126,25 @@ def test_normal_equations_match_oracle_320x240(bf, chunk320):
     for name in ("dense_tc3_mixed", "dense_tc1_mixed", "dense_tc0_mixed"):
         v = table[name]
         assert v["A"] <= 2e-5 and v["b"] <= 2e-5 and v["energy"] <= 1e-5, (name, v)
+    ctx.close()
+
+
+@pytest.mark.parametrize("tile", [1100, 97])
+def test_ragged_tiles(bf, chunk320, tile):
+    """Tiles that end mid-iteration (1100 = 4 x 256 + 76 pixels, 97 < one iteration): the threads
+    past the tile's end stage zero rows."""
+    prob, ids, poses = chunk320
+    intr = prob.intr
+    ctx = bf.Context(intr["W"], intr["H"], intr["fx"], intr["fy"], intr["cx"], intr["cy"], max_frames_hint=prob.n_frames)
+    ctx.add_frames(0, prob.depth, prob.lum)
+    ctx.add_correspondences_batch(prob.pairs, prob.corr_off, prob.p_i, prob.p_j)
+    kw = dict(w_sparse=0.0, w_dense=1.0, w_photo=0.1, w_geo=1.0, precision=bf.BF_PREC_MIXED)
+    g0 = ctx.build_system(ids, poses, tile_px=tile, dense_tc=0, **kw)
+    g3 = ctx.build_system(ids, poses, tile_px=tile, dense_tc=3, **kw)
+    assert g3["n_dense"] == g0["n_dense"]
+    np.testing.assert_allclose(g3["A"], g0["A"], rtol=0, atol=2e-5 * np.abs(g0["A"]).max())
+    np.testing.assert_allclose(g3["b"], g0["b"], rtol=0, atol=2e-5 * np.abs(g0["b"]).max())
+    assert abs(g3["energy"] - g0["energy"]) <= 1e-5 * g0["energy"]
     ctx.close()
 
 
