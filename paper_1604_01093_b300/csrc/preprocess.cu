@@ -52,10 +52,13 @@ __device__ __forceinline__ float4 depth_normal(const float *__restrict__ Df, int
   return a;
 }
 
-// Pass 1: validity, normals, I.  One thread per pixel of n frames.
-__global__ void k_pre1(const float *__restrict__ depth, const float *__restrict__ lum, int n,
-                       const int *__restrict__ slots, FrameStore fs, float4 *__restrict__ A,
-                       float4 *__restrict__ B, float dmin, float dmax) {
+// FP32 storage, one pass (one thread per pixel of n frames): (D, n) into A and (I, grad I, L)
+// into B.  grad I on the 2-pixel interior from the neighbours' I recomputed from the luminance
+// (the same function as the pixel's own I, so the same values a second pass over the stored I
+// would read); one read of depth and luminance and one write of A and B per pixel.
+__global__ void k_pre32(const float *__restrict__ depth, const float *__restrict__ lum, int n,
+                        const int *__restrict__ slots, FrameStore fs, float4 *__restrict__ A,
+                        float4 *__restrict__ B, float dmin, float dmax) {
   const int W = fs.W, H = fs.H;
   const long long HW = (long long)W * H;
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,26 +69,15 @@ __global__ void k_pre1(const float *__restrict__ depth, const float *__restrict_
   const float *Df = depth + (long long)f * HW;
   const float *Lf = lum + (long long)f * HW;
   const float4 a = depth_normal(Df, pix, x, y, fs, dmin, dmax);
-  const float I = (x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2) ? lum_grad_mag(Lf, pix, W) : 0.f;
+  float I = 0.f, Ix = 0.f, Iy = 0.f;
+  if (x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2) I = lum_grad_mag(Lf, pix, W);
+  if (x >= 2 && x <= W - 3 && y >= 2 && y <= H - 3) {
+    Ix = 0.5f * (lum_grad_mag(Lf, pix + 1, W) - lum_grad_mag(Lf, pix - 1, W));
+    Iy = 0.5f * (lum_grad_mag(Lf, pix + W, W) - lum_grad_mag(Lf, pix - W, W));
+  }
   const long long o = (long long)slots[f] * HW + pix;
   A[o] = a;
-  B[o] = make_float4(I, 0.f, 0.f, Lf[pix]);  // w: the intensity itself (dense verification)
-}
-
-// Pass 2: grad I on the 2-pixel interior.
-__global__ void k_pre2(int n, const int *__restrict__ slots, int W, int H, float4 *__restrict__ B) {
-  const long long HW = (long long)W * H;
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)n * HW) return;
-  const int f = (int)(idx / HW);
-  const int pix = (int)(idx - (long long)f * HW);
-  const int y = pix / W, x = pix - y * W;
-  if (x < 2 || x > W - 3 || y < 2 || y > H - 3) return;
-  float4 *Bf = B + (long long)slots[f] * HW;
-  float4 b = Bf[pix];
-  b.y = 0.5f * (Bf[pix + 1].x - Bf[pix - 1].x);
-  b.z = 0.5f * (Bf[pix + W].x - Bf[pix - W].x);
-  Bf[pix] = b;
+  B[o] = make_float4(I, Ix, Iy, Lf[pix]);  // w: the intensity itself (dense verification)
 }
 
 // 16-bit storage: one pass writes the packed record (depth FP32, normal, I, grad I rounded to
@@ -131,9 +123,8 @@ int launch_preprocess(const float *depth, const float *lum, int n, const int *sl
     k_pre16<BF_STORE_FP16><<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, P16, C16, dmin, dmax);
     return 1;
   }
-  k_pre1<<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, A, B, dmin, dmax);
-  k_pre2<<<grid, bs, 0, st>>>(n, slots_dev, fs.W, fs.H, B);
-  return 2;
+  k_pre32<<<grid, bs, 0, st>>>(depth, lum, n, slots_dev, fs, A, B, dmin, dmax);
+  return 1;
 }
 
 // Correspondences into the pool as (p, w) / (q, 0) float4 pairs; swap exchanges p and q so that
