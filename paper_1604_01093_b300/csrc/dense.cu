@@ -23,13 +23,14 @@
 
 namespace bf {
 
-// Residency: with FP32 frames the accumulating pixel loop needs about 80 registers, so 3 CTAs
-// per SM (24 warps, no spills; 4 CTAs at 64 registers spill and run about 9 % slower); the 16-bit
-// unpacking path runs faster at 4 CTAs per SM.
+// Residency: 4 CTAs per SM (32 warps, 64 registers) for every storage: the accumulating pixel
+// loop would like about 80 registers and spills 44-60 bytes at 64, but the extra warps hide more
+// of the target gathers' latency (FP32 frames, 256-chunk 320x240 batch: 8.02 ms per launch at 4
+// CTAs vs 8.18 ms at 3 without spills; BF16: 7.58 vs 8.18 ms).
 template <int MODE, int KIND, bool COMP = false>
 struct DenseOcc {
   // compensated sums hold twice the accumulators: 2 CTAs per SM (up to 128 registers, no spills)
-  static constexpr int value = COMP ? 2 : (KIND == BF_STORE_FP32 && MODE == MODE_ACCUM) ? 3 : 4;
+  static constexpr int value = COMP ? 2 : 4;
 };
 
 // REC (debug): the association of every source pixel is also written to assoc[d * H * W + px].
