@@ -65,10 +65,11 @@ DENSE_FLOPS_PER_PX = 122.8
 # 0.13 / 0.01 MB (ncu, the current kernel): the frames' unique bytes, which stay in L2
 DENSE_TRAFFIC_BYTES = 46.50e6
 # 256-chunk 320x240 batch, k_dense (tiled, autotuned decomposition): one launch of the 32-chunk batch
-# (the same chunk distribution, 1496 directed pairs = 114.9 M directed source pixels) read 514.85 MB and
-# wrote 3.27 MB (ncu, one launch, the current kernel); scaled by directed source pixels to the
+# (the same chunk distribution, 1496 directed pairs = 114.9 M directed source pixels) read 523.63 MB and
+# wrote 9.80 MB (ncu, one launch, the current kernel: 4 CTAs per SM, register spills included);
+# scaled by directed source pixels to the
 # 256-chunk launch (1007.5 M): DRAM traffic is the frames' unique bytes, which grow with the batch
-DENSE_TRAFFIC_BYTES_CHUNKS = (514.85e6 + 3.27e6) * 1007.5 / 114.9
+DENSE_TRAFFIC_BYTES_CHUNKS = (523.63e6 + 9.80e6) * 1007.5 / 114.9
 # untimed warm-up floor after the W warm-up steps (seconds of repeated steps)
 WARMUP_MIN_S = 0.5
 # B300 FP32 peak: 148 SMs x 128 FP32 lanes x 2 flop x max SM clock
