@@ -1225,7 +1225,7 @@ def serving_leg(bf, torch, dev, chunk_prob=None, seconds=20.0, rate=30.0, seed=1
     over the session (over 10 minutes at full length; a shorter session compresses the growth).
     served: the library's serving loops on two persistent contexts (chunks: 2 slots, continuous
     batching up to 16, high-priority streams, FP32 arithmetic; globals: 1 slot, low-priority
-    stream, FP64-merged mixed precision), admission by a 40 GB HBM budget per context, frames,
+    stream, FP64-merged mixed precision, cluster PCG), admission by a 40 GB HBM budget per context, frames,
     correspondences and solve workspaces resident.  plain: the same arrivals served one request at
     a time, in arrival order, by synchronous calls of the plain FP32 path.  Then a chunk-only
     stream at 600 requests/s, both ways.  p50 / p99 per request kind and over all requests."""
@@ -1270,7 +1270,11 @@ def serving_leg(bf, torch, dev, chunk_prob=None, seconds=20.0, rate=30.0, seed=1
         gctx.add_correspondences_batch(global_prob.pairs, global_prob.corr_off, global_prob.p_i, global_prob.p_j)
         torch.cuda.synchronize(dev)
         cparams = bf.default_params(precision=bf.BF_PREC_FP32, **pc)
-        gparams = bf.default_params(precision=bf.BF_PREC_MIXED if served else bf.BF_PREC_FP32, **pg)
+        # served globals run the 16-CTA cluster PCG, which leaves the other SMs to the chunk solves
+        # running beside them (the grid-cooperative kernel AUTO picks for >= 1000 keyframes is faster
+        # alone but holds every SM); the plain path, one request at a time, keeps AUTO
+        gparams = (bf.default_params(precision=bf.BF_PREC_MIXED, pcg_variant=bf.BF_PCG_CLUSTER, **pg) if served
+                   else bf.default_params(precision=bf.BF_PREC_FP32, **pg))
         if served:
             cctx.serve_start(n_slots=2, max_batch=16, max_queue=100000)
             gctx.serve_start(n_slots=1, max_batch=1, max_queue=100000)
@@ -1305,6 +1309,7 @@ def serving_leg(bf, torch, dev, chunk_prob=None, seconds=20.0, rate=30.0, seed=1
                      "chunk_only_600_per_s": {"p50_ms": q(hlat, 0.5), "p99_ms": q(hlat, 0.99),
                                               "solves_per_s": len(hlat) / hwall, "requests": len(hlat)},
                      "precision": {"chunk": "fp32", "global": "mixed" if served else "fp32"},
+                     "global_pcg": "cluster" if served else "auto",
                      "form": ("serving loops: chunks 2 slots x batches of up to 16 on high-priority streams, globals "
                               "1 slot on a low-priority stream" if served else
                               "one host loop, requests in arrival order, synchronous bf_solve_local / bf_solve_global")}
